@@ -1,0 +1,283 @@
+"""FP64 CPU oracle of the WENO-C operator -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never imports it; the two implementations share no code.
+
+The arithmetic lives in ``wenoc_oracle.c`` (plain C, FP64, no fused
+multiply-add); this module compiles it with gcc and wraps it with ctypes and
+numpy arrays.  Every function cites the paper passage it follows in the C
+source.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wenoc_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+MAXP = 8
+BC = {"periodic": 0, "reflective": 1, "outflow": 2}
+FLUX = {"hll": 0, "hllc": 1}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP over pencils, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", "-o", _LIB, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("n", ctypes.c_int * 3),
+        ("dx", ctypes.c_double * 3),
+        ("N", ctypes.c_int),
+        ("gamma", ctypes.c_double * MAXP),
+        ("pinf", ctypes.c_double * MAXP),
+        ("D", ctypes.c_double * MAXP),
+        ("pmin", ctypes.c_double * MAXP),
+        ("flux", ctypes.c_int),
+        ("weights", ctypes.c_int),
+        ("js_eps", ctypes.c_double),
+        ("coupled", ctypes.c_int),
+        ("limiter", ctypes.c_int),
+        ("energy_limiter", ctypes.c_int),
+        ("bc", ctypes.c_int * 6),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        gp = ctypes.POINTER(_Grid)
+        for name, args in {
+            "or_rhs": [gp, dp, dp],
+            "or_rk3_step": [gp, dp, ctypes.c_double, ctypes.c_double, dp],
+            "or_faces": [gp, ctypes.c_int, dp, dp, dp, dp],
+            "or_limit": [gp, ctypes.c_long, dp, dp, dp, dp, dp, dp],
+            "or_cons_to_prim": [gp, ctypes.c_long, dp, dp],
+            "or_prim_to_cons": [gp, ctypes.c_long, dp, dp],
+            "or_psi": [gp, ctypes.c_long, dp, dp],
+            "or_sound_speed": [gp, ctypes.c_long, dp, dp],
+            "or_max_rate": [gp, dp, dp],
+            "or_flux": [gp, ctypes.c_int, dp, dp, dp, dp, dp, dp],
+            "or_weno5_parts": [dp, dp, dp],
+            "or_wenow_weights": [dp, dp],
+            "or_wenojs_weights": [dp, ctypes.c_double, dp],
+            "or_nv": [gp],
+            "or_num_threads": [],
+        }.items():
+            f = getattr(_lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise OracleError(f"{what} returned status {rc}")
+
+
+@dataclass
+class Grid:
+    """Uniform grid + materials.  ``shape`` is (nx,), (nx, ny) or (nx, ny, nz)."""
+    shape: tuple
+    dx: tuple
+    gamma: list
+    pinf: list
+    D: list = None
+    pmin: list = None
+    flux: str = "hll"
+    bc: tuple = ("periodic",) * 6
+    weights: str = "w"          # "w" (Eq. 15) or "js" (comparator)
+    js_eps: float = 1e-6
+    coupled: bool = True        # Eq. 16
+    limiter: bool = True        # Eq. 17-20
+    energy_limiter: bool = True  # Eq. 21
+    _c: _Grid = field(default=None, repr=False)
+
+    def __post_init__(self):
+        N = len(self.gamma)
+        if self.D is None:
+            self.D = [0.0] * N
+        if self.pmin is None:
+            self.pmin = default_pmin(self.pinf)
+        g = _Grid()
+        g.dim = len(self.shape)
+        for a in range(3):
+            g.n[a] = self.shape[a] if a < g.dim else 1
+            g.dx[a] = self.dx[a] if a < g.dim else 1.0
+        g.N = N
+        for p in range(N):
+            g.gamma[p] = self.gamma[p]
+            g.pinf[p] = self.pinf[p]
+            g.D[p] = self.D[p]
+            g.pmin[p] = self.pmin[p]
+        g.flux = FLUX[self.flux]
+        g.weights = 0 if self.weights == "w" else 1
+        g.js_eps = self.js_eps
+        g.coupled = int(self.coupled)
+        g.limiter = int(self.limiter)
+        g.energy_limiter = int(self.energy_limiter)
+        for k in range(6):
+            g.bc[k] = BC[self.bc[k]] if isinstance(self.bc[k], str) else int(self.bc[k])
+        self._c = g
+
+    @property
+    def N(self):
+        return len(self.gamma)
+
+    @property
+    def dim(self):
+        return len(self.shape)
+
+    @property
+    def nv(self):
+        return 2 * self.N + self.dim + 1
+
+    @property
+    def ncell(self):
+        return int(np.prod(self.shape))
+
+    def state_shape(self):
+        # [NV][nz][ny][nx]: x fastest
+        return (self.nv,) + tuple(reversed(self.shape))
+
+    def ref(self):
+        return ctypes.byref(self._c)
+
+
+def default_pmin(pinf):
+    """Minimum pressures of Eq. 9 when the caller gives none: -(1 - 1e-3) Pinf_p
+    for stiffened phases and 0 for ideal gases (the paper leaves them to the
+    user, Sec. 2.2.2)."""
+    return [-(1.0 - 1e-3) * pi if pi > 0 else 0.0 for pi in pinf]
+
+
+def rhs(g: Grid, U: np.ndarray) -> np.ndarray:
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    L = np.empty_like(U)
+    _check(lib().or_rhs(g.ref(), _p(U), _p(L)), "or_rhs")
+    return L
+
+
+def rk3_step(g: Grid, U: np.ndarray, cfl: float = 0.5, dt: float = 0.0):
+    """One SSP-RK3 step; returns (U_new, dt_used)."""
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    out = ctypes.c_double(0.0)
+    _check(lib().or_rk3_step(g.ref(), _p(U), cfl, dt, ctypes.byref(out)), "or_rk3_step")
+    return U, out.value
+
+
+def faces(g: Grid, U: np.ndarray, direction: int):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    UL = np.empty_like(U)
+    UR = np.empty_like(U)
+    TH = np.empty((3,) + U.shape[1:], dtype=np.float64)
+    _check(lib().or_faces(g.ref(), direction, _p(U), _p(UL), _p(UR), _p(TH)), "or_faces")
+    return UL, UR, TH
+
+
+def limit(g: Grid, Ubar, VL, VR):
+    """Eq. 17-21 on raw primitive face values of independent cells ([NV][n])."""
+    Ubar, VL, VR = (np.ascontiguousarray(a, dtype=np.float64) for a in (Ubar, VL, VR))
+    n = Ubar.shape[1]
+    UL = np.empty_like(Ubar)
+    UR = np.empty_like(Ubar)
+    TH = np.empty((3, n))
+    _check(lib().or_limit(g.ref(), n, _p(Ubar), _p(VL), _p(VR), _p(UL), _p(UR), _p(TH)),
+           "or_limit")
+    return UL, UR, TH
+
+
+def _cellwise(fname, g, A, nout=None):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    flat = A.reshape(A.shape[0], -1)
+    n = flat.shape[1]
+    out = np.empty((nout, n) if nout else flat.shape)
+    _check(getattr(lib(), fname)(g.ref(), n, _p(flat), _p(out)), fname)
+    return out
+
+
+def cons_to_prim(g, U):
+    return _cellwise("or_cons_to_prim", g, U).reshape(np.shape(U))
+
+
+def prim_to_cons(g, V):
+    return _cellwise("or_prim_to_cons", g, V).reshape(np.shape(V))
+
+
+def psi(g, U):
+    return _cellwise("or_psi", g, U, 1)[0].reshape(np.shape(U)[1:])
+
+
+def sound_speed(g, U):
+    return _cellwise("or_sound_speed", g, U, 1)[0].reshape(np.shape(U)[1:])
+
+
+def max_rate(g, U):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    out = ctypes.c_double(0.0)
+    _check(lib().or_max_rate(g.ref(), _p(U), ctypes.byref(out)), "or_max_rate")
+    return out.value
+
+
+def flux(g: Grid, direction, UL, VL, UR, VR):
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (UL, VL, UR, VR)]
+    F = np.empty(g.nv)
+    uh = ctypes.c_double(0.0)
+    _check(lib().or_flux(g.ref(), direction, *[_p(a) for a in arrs], _p(F), ctypes.byref(uh)),
+           "or_flux")
+    return F, uh.value
+
+
+def weno5_parts(f):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    q = np.empty(3)
+    b = np.empty(3)
+    lib().or_weno5_parts(_p(f), _p(q), _p(b))
+    return q, b
+
+
+def wenow_weights(beta):
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    w = np.empty(3)
+    lib().or_wenow_weights(_p(beta), _p(w))
+    return w
+
+
+def wenojs_weights(beta, eps):
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    w = np.empty(3)
+    lib().or_wenojs_weights(_p(beta), eps, _p(w))
+    return w
+
+
+def num_threads():
+    return lib().or_num_threads()

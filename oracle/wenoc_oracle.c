@@ -1,0 +1,735 @@
+/*
+ * wenoc_oracle.c -- plain, slow, FP64 CPU oracle of the WENO-C finite-volume
+ * operator of Huang, "Consistent and bound-preserving finite-volume WENO
+ * scheme for compressible two-/N-phase flows with Phase-Field mechanism".
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this library.  It shares no code, header
+ * or constant table with the CUDA path; it is the definition the CUDA path is
+ * compared against.  Everything is FP64, evaluated literally, one cell and one
+ * face at a time, in the order the paper states the steps (Eq. 15 -> Eq. 16 ->
+ * Eq. 17/18 -> Eq. 19 -> Eq. 20 -> Eq. 21 -> flux -> Eq. 3 -> SSP-RK3).
+ * Build with -ffp-contract=off so that no fused multiply-add changes the
+ * rounding of the plain expressions below.
+ *
+ * Readings where the paper is silent or ambiguous (each one is listed in the
+ * design notes of the repository):
+ *  R1  WENO5 candidates, ideal weights and smoothness indicators are the
+ *      uniform-mesh Jiang-Shu ones (Sec. 3.1 cites them; only the r = 1 case
+ *      is printed, Eq. 11).  The right-face value f^R_{i-1/2} uses the mirrored
+ *      stencil.
+ *  R2  Eq. 15 with IS_k = 0 < IS_s: the ratio is infinite, so omega_s = 0.
+ *  R3  Eq. 18: theta = 1 whenever min(f^C, f^L, f^R) >= f_min (this covers the
+ *      printed 0/0 and x/0 cases); theta is clamped to [0, 1] (the paper states
+ *      theta in [0, 1]) when the cell average itself is below f_min.
+ *  R4  f_min = 0 for both the masses and the volume fractions (positivity).
+ *  R5  psi of Eq. 9 with the Eq. 26 equation of state; the minimum pressures
+ *      P_min are inputs.  theta^(psi) uses psi(U^C) with U^C from inverting
+ *      Eq. 6 (N_quad = 4, w_1 = w_4 = 1/12, Sec. 4.2).
+ *  R6  The Riemann solver receives, for each face state, the conservative
+ *      vector U and the primitive vector V with U = psi_{V->U}(V).  When the
+ *      energy limiter leaves the state unchanged (theta^(psi) = 1) V is the
+ *      reconstructed primitive state; otherwise V is recovered from the
+ *      limited U by Eq. 27.
+ *  R7  HLL uses the Davis wave-speed estimates; HLLC is Toro's, with the
+ *      masses and the volume fractions both scaled by (S_K-u_K)/(S_K-S*) in
+ *      the star state (keeps mass/fraction consistency).  u-hat is the
+ *      volume-fraction flux with alpha = 1 on both sides (Sec. 2.2.1).
+ *  R8  Mixture sound speed of Eq. 2 for K_p = 0 (Allaire et al.), with the
+ *      stiffened-gas phasic rho_p c_p^2 = gamma_p (P + Pinf_p).
+ *  R9  Boundary cells: periodic copy; reflective mirror with the normal
+ *      momentum negated; outflow zero-gradient copy.
+ *  R10 Time step dt = CFL / max_cells sum_d (|u_d| + c) / dx_d, taken from U^n.
+ *  R11 Eq. 19 assumes S > 0.  When the positivity step has limited every
+ *      fraction of a face to zero (S = 0) the cell keeps its averages on both
+ *      faces (theta = 0, first order) for the masses and the fractions.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_MAXP 8
+#define OR_MAXV (2 * OR_MAXP + 4)
+
+enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_INADMISSIBLE = 3, OR_ERR_NAN = 4 };
+enum { OR_BC_PERIODIC = 0, OR_BC_REFLECTIVE = 1, OR_BC_OUTFLOW = 2 };
+enum { OR_FLUX_HLL = 0, OR_FLUX_HLLC = 1 };
+enum { OR_WEIGHTS_W = 0, OR_WEIGHTS_JS = 1 };
+
+typedef struct {
+  int dim;              /* 1, 2 or 3 */
+  int n[3];             /* interior cells per axis (1 for unused axes) */
+  double dx[3];         /* uniform cell sizes */
+  int N;                /* number of phases */
+  double gamma[OR_MAXP], pinf[OR_MAXP], D[OR_MAXP], pmin[OR_MAXP];
+  int flux;             /* OR_FLUX_HLL / OR_FLUX_HLLC */
+  int weights;          /* OR_WEIGHTS_W (Eq. 15) or OR_WEIGHTS_JS (Eq. 12 form) */
+  double js_eps;        /* epsilon of the JS comparator */
+  int coupled;          /* 1: Eq. 16 coupling (WENO-C); 0: own weights per variable */
+  int limiter;          /* 1: Eq. 17-20 applied; 0: skipped */
+  int energy_limiter;   /* 1: Eq. 21 applied; 0: skipped */
+  int bc[6];            /* lo/hi per axis: OR_BC_* */
+} or_grid;
+
+/* ---- state layout ---------------------------------------------------------
+ * U = [ (alpha rho)_1..N, (rho u)_1..d, rho E, alpha_1..N ]   (Eq. 1)
+ * V = [ (alpha rho)_1..N,  u_1..d,       P,    alpha_1..N ]   (Sec. 2.2.2)
+ */
+static int nv(const or_grid *g) { return 2 * g->N + g->dim + 1; }
+#define IMASS(p) (p)
+#define IMOM(g, j) ((g)->N + (j))
+#define IENE(g) ((g)->N + (g)->dim)
+#define IALF(g, p) ((g)->N + (g)->dim + 1 + (p))
+
+int or_nv(const or_grid *g) { return nv(g); }
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* Eq. 26: A_p = 1/(gamma_p - 1), B_p = gamma_p Pinf_p / (gamma_p - 1). */
+static double eos_A(const or_grid *g, int p) { return 1.0 / (g->gamma[p] - 1.0); }
+static double eos_B(const or_grid *g, int p) {
+  return g->gamma[p] * g->pinf[p] / (g->gamma[p] - 1.0);
+}
+
+/* Mixture rules (Sec. 2.1) and the pressure of Eq. 27. */
+static int cons_to_prim(const or_grid *g, const double *U, double *V) {
+  int N = g->N, d = g->dim;
+  double rho = 0.0;
+  for (int p = 0; p < N; p++) rho += U[IMASS(p)];
+  if (!(rho > 0.0)) return OR_ERR_INADMISSIBLE;
+  double mm = 0.0;
+  for (int j = 0; j < d; j++) mm += U[IMOM(g, j)] * U[IMOM(g, j)];
+  double sA = 0.0, sB = 0.0, sD = 0.0;
+  for (int p = 0; p < N; p++) {
+    sA += eos_A(g, p) * U[IALF(g, p)];
+    sB += eos_B(g, p) * U[IALF(g, p)];
+    sD += g->D[p] * U[IMASS(p)];
+  }
+  double P = (U[IENE(g)] - 0.5 * mm / rho - sB - sD) / sA;
+  for (int p = 0; p < N; p++) {
+    V[IMASS(p)] = U[IMASS(p)];
+    V[IALF(g, p)] = U[IALF(g, p)];
+  }
+  for (int j = 0; j < d; j++) V[IMOM(g, j)] = U[IMOM(g, j)] / rho;
+  V[IENE(g)] = P;
+  return isfinite(P) ? OR_OK : OR_ERR_NAN;
+}
+
+/* psi_{V->U}: rho = sum (alpha rho)_p, rho u, and rho E from Eq. 26. */
+static void prim_to_cons(const or_grid *g, const double *V, double *U) {
+  int N = g->N, d = g->dim;
+  double rho = 0.0;
+  for (int p = 0; p < N; p++) rho += V[IMASS(p)];
+  double uu = 0.0;
+  for (int j = 0; j < d; j++) uu += V[IMOM(g, j)] * V[IMOM(g, j)];
+  double P = V[IENE(g)];
+  double e = 0.0;
+  for (int p = 0; p < N; p++)
+    e += V[IALF(g, p)] * (eos_A(g, p) * P + eos_B(g, p)) + g->D[p] * V[IMASS(p)];
+  for (int p = 0; p < N; p++) {
+    U[IMASS(p)] = V[IMASS(p)];
+    U[IALF(g, p)] = V[IALF(g, p)];
+  }
+  for (int j = 0; j < d; j++) U[IMOM(g, j)] = rho * V[IMOM(g, j)];
+  U[IENE(g)] = e + 0.5 * rho * uu;
+}
+
+/* Eq. 9 with Eq. 26: psi = rho E - |rho u|^2 / (2 rho)
+ *                         - sum_p [ alpha_p (A_p Pmin_p + B_p) + D_p (alpha rho)_p ]. */
+static double psi_energy(const or_grid *g, const double *U) {
+  int N = g->N, d = g->dim;
+  double rho = 0.0;
+  for (int p = 0; p < N; p++) rho += U[IMASS(p)];
+  double mm = 0.0;
+  for (int j = 0; j < d; j++) mm += U[IMOM(g, j)] * U[IMOM(g, j)];
+  double s = 0.0;
+  for (int p = 0; p < N; p++)
+    s += U[IALF(g, p)] * (eos_A(g, p) * g->pmin[p] + eos_B(g, p)) + g->D[p] * U[IMASS(p)];
+  /* a face whose masses were all limited to zero carries rho u = 0: the
+   * kinetic term tends to zero with rho */
+  double ke = rho > 0.0 ? 0.5 * mm / rho : 0.0;
+  return U[IENE(g)] - ke - s;
+}
+
+/* ---- WENO5 building blocks (R1) ------------------------------------------
+ * f[0..4] = cell averages f_{i-2..i+2}; values at x_{i+1/2} of the three
+ * quadratic candidates of sub-stencils s = {i-2..i}, {i-1..i+1}, {i..i+2},
+ * and their smoothness indicators. */
+void or_weno5_parts(const double *f, double *q, double *beta) {
+  q[0] = (2.0 * f[0] - 7.0 * f[1] + 11.0 * f[2]) / 6.0;
+  q[1] = (-f[1] + 5.0 * f[2] + 2.0 * f[3]) / 6.0;
+  q[2] = (2.0 * f[2] + 5.0 * f[3] - f[4]) / 6.0;
+  double a, b;
+  a = f[0] - 2.0 * f[1] + f[2];
+  b = f[0] - 4.0 * f[1] + 3.0 * f[2];
+  beta[0] = 13.0 / 12.0 * a * a + 0.25 * b * b;
+  a = f[1] - 2.0 * f[2] + f[3];
+  b = f[1] - f[3];
+  beta[1] = 13.0 / 12.0 * a * a + 0.25 * b * b;
+  a = f[2] - 2.0 * f[3] + f[4];
+  b = 3.0 * f[2] - 4.0 * f[3] + f[4];
+  beta[2] = 13.0 / 12.0 * a * a + 0.25 * b * b;
+}
+
+static const double weno5_d[3] = {0.1, 0.6, 0.3};
+
+/* Eq. 15: omega_s = d_s / (d_s + sum_{k != s} d_k (IS^(s,k))^2),
+ * IS^(s,k) = 1 if IS_s = IS_k = 0, else IS_s / IS_k (R2 for IS_k = 0). */
+void or_wenow_weights(const double *beta, double *w) {
+  for (int s = 0; s < 3; s++) {
+    double den = weno5_d[s];
+    int infinite = 0;
+    for (int k = 0; k < 3; k++) {
+      if (k == s) continue;
+      double r;
+      if (beta[s] == 0.0 && beta[k] == 0.0) r = 1.0;
+      else if (beta[k] == 0.0) { infinite = 1; r = 0.0; }
+      else r = beta[s] / beta[k];
+      den += weno5_d[k] * r * r;
+    }
+    w[s] = infinite ? 0.0 : weno5_d[s] / den;
+  }
+}
+
+/* WENO-JS comparator (Eq. 12 in the fifth-order form): w_s ~ d_s/(IS_s+eps)^2. */
+void or_wenojs_weights(const double *beta, double eps, double *w) {
+  double a[3], s = 0.0;
+  for (int k = 0; k < 3; k++) {
+    a[k] = weno5_d[k] / ((beta[k] + eps) * (beta[k] + eps));
+    s += a[k];
+  }
+  for (int k = 0; k < 3; k++) w[k] = a[k] / s;
+}
+
+static void weights(const or_grid *g, const double *beta, double *w) {
+  if (g->weights == OR_WEIGHTS_JS) or_wenojs_weights(beta, g->js_eps, w);
+  else or_wenow_weights(beta, w);
+}
+
+/* Eq. 10: f^L = sum_s omega_s f^(s). */
+static double combine(const double *w, const double *q) {
+  return w[0] * q[0] + w[1] * q[1] + w[2] * q[2];
+}
+
+/* Eq. 6 inverted for U^C with N_quad = 4 Gauss-Lobatto points, w_1 = 1/12. */
+static double center_value(double fbar, double fL, double fR) {
+  const double w1 = 1.0 / 12.0;
+  return (fbar - w1 * fR - w1 * fL) / (1.0 - 2.0 * w1);
+}
+
+/* Eq. 18 with the explicit interior value f^C (R3). */
+static double theta_lower(double fbar, double fC, double fL, double fR, double fmin) {
+  double m = fC;
+  if (fL < m) m = fL;
+  if (fR < m) m = fR;
+  if (m >= fmin) return 1.0;
+  if (fbar <= fmin) return 0.0;
+  double t = (fbar - fmin) / (fbar - m);
+  return t < 1.0 ? t : 1.0;
+}
+
+static double theta_pos(double fbar, double fL, double fR) {
+  return theta_lower(fbar, center_value(fbar, fL, fR), fL, fR, 0.0);
+}
+
+/* The limiter chain of WENO-C for one cell and one direction.
+ * Ubar: cell average (conservative).  VL, VR: reconstructed primitive values
+ * at x_{i+1/2} (left state of that face) and x_{i-1/2} (right state), modified
+ * in place by Eq. 17-20.  UL, UR: final conservative face states (Eq. 21).
+ * VfL, VfR: primitive face states handed to the Riemann solver (R6).
+ * th (optional, 3 values): min_p theta_p of Eq. 17, theta_i of Eq. 20,
+ * theta^(psi) of Eq. 21. */
+static int limit_chain(const or_grid *g, const double *Ubar, double *VL, double *VR,
+                       double *UL, double *UR, double *VfL, double *VfR, double *th) {
+  int N = g->N, nvar = nv(g);
+  double th17 = 1.0, th20 = 1.0, thpsi = 1.0;
+  if (g->limiter) {
+    /* Eq. 17-18: positivity of (alpha rho)_p and alpha_p with a common theta_p. */
+    for (int p = 0; p < N; p++) {
+      double mb = Ubar[IMASS(p)], ab = Ubar[IALF(g, p)];
+      double t1 = theta_pos(mb, VL[IMASS(p)], VR[IMASS(p)]);
+      double t2 = theta_pos(ab, VL[IALF(g, p)], VR[IALF(g, p)]);
+      double tp = t1 < t2 ? t1 : t2;
+      if (tp < th17) th17 = tp;
+      VL[IMASS(p)] = mb + tp * (VL[IMASS(p)] - mb);
+      VR[IMASS(p)] = mb + tp * (VR[IMASS(p)] - mb);
+      VL[IALF(g, p)] = ab + tp * (VL[IALF(g, p)] - ab);
+      VR[IALF(g, p)] = ab + tp * (VR[IALF(g, p)] - ab);
+    }
+    /* Eq. 19: unity sum of the volume fractions on each face. */
+    double SL = 0.0, SR = 0.0;
+    for (int p = 0; p < N; p++) {
+      SL += VL[IALF(g, p)];
+      SR += VR[IALF(g, p)];
+    }
+    if (!(SL > 0.0) || !(SR > 0.0)) {
+      /* R11: every fraction of a face was limited to zero, so Eq. 19 has no
+       * sum to divide by; the cell falls back to its averages (theta = 0). */
+      for (int p = 0; p < N; p++) {
+        VL[IMASS(p)] = VR[IMASS(p)] = Ubar[IMASS(p)];
+        VL[IALF(g, p)] = VR[IALF(g, p)] = Ubar[IALF(g, p)];
+      }
+      th17 = 0.0;
+      SL = SR = 1.0;
+    }
+    for (int p = 0; p < N; p++) {
+      VL[IMASS(p)] = VL[IMASS(p)] / SL;
+      VL[IALF(g, p)] = VL[IALF(g, p)] / SL;
+      VR[IMASS(p)] = VR[IMASS(p)] / SR;
+      VR[IALF(g, p)] = VR[IALF(g, p)] / SR;
+    }
+    /* Eq. 20: theta_i = min_p theta_p recomputed from the normalised faces. */
+    for (int p = 0; p < N; p++) {
+      double t1 = theta_pos(Ubar[IMASS(p)], VL[IMASS(p)], VR[IMASS(p)]);
+      double t2 = theta_pos(Ubar[IALF(g, p)], VL[IALF(g, p)], VR[IALF(g, p)]);
+      double tp = t1 < t2 ? t1 : t2;
+      if (tp < th20) th20 = tp;
+    }
+    for (int p = 0; p < N; p++) {
+      double mb = Ubar[IMASS(p)], ab = Ubar[IALF(g, p)];
+      VL[IMASS(p)] = mb + th20 * (VL[IMASS(p)] - mb);
+      VR[IMASS(p)] = mb + th20 * (VR[IMASS(p)] - mb);
+      VL[IALF(g, p)] = ab + th20 * (VL[IALF(g, p)] - ab);
+      VR[IALF(g, p)] = ab + th20 * (VR[IALF(g, p)] - ab);
+    }
+  }
+  /* V -> U at both faces. */
+  prim_to_cons(g, VL, UL);
+  prim_to_cons(g, VR, UR);
+  if (g->energy_limiter) {
+    /* Eq. 21 with psi evaluated at Ubar, U^L, U^R and U^C (R5). */
+    double UC[OR_MAXV];
+    for (int v = 0; v < nvar; v++) UC[v] = center_value(Ubar[v], UL[v], UR[v]);
+    double pb = psi_energy(g, Ubar);
+    double pL = psi_energy(g, UL), pR = psi_energy(g, UR), pC = psi_energy(g, UC);
+    thpsi = theta_lower(pb, pC, pL, pR, 0.0);
+    if (thpsi < 1.0) {
+      for (int v = 0; v < nvar; v++) {
+        UL[v] = Ubar[v] + thpsi * (UL[v] - Ubar[v]);
+        UR[v] = Ubar[v] + thpsi * (UR[v] - Ubar[v]);
+      }
+    }
+  }
+  if (thpsi < 1.0) {
+    int e1 = cons_to_prim(g, UL, VfL), e2 = cons_to_prim(g, UR, VfR);
+    if (e1) return e1;
+    if (e2) return e2;
+  } else {
+    memcpy(VfL, VL, sizeof(double) * nvar);
+    memcpy(VfR, VR, sizeof(double) * nvar);
+  }
+  if (th) {
+    th[0] = th17;
+    th[1] = th20;
+    th[2] = thpsi;
+  }
+  return OR_OK;
+}
+
+/* Reconstruction of cell i in one direction: Ust = conservative averages of
+ * cells i-2..i+2 (NV each).  Outputs the limited face states of the cell. */
+static int recon_cell(const or_grid *g, const double *Ust, double *UL, double *UR,
+                      double *VfL, double *VfR, double *th) {
+  int N = g->N, d = g->dim, nvar = nv(g);
+  double Vst[5][OR_MAXV];
+  for (int k = 0; k < 5; k++) {
+    int e = cons_to_prim(g, Ust + k * nvar, Vst[k]);
+    if (e) return e;
+  }
+  double qL[OR_MAXV][3], bL[OR_MAXV][3], qR[OR_MAXV][3], bR[OR_MAXV][3];
+  for (int v = 0; v < nvar; v++) {
+    double f[5], fm[5];
+    for (int k = 0; k < 5; k++) {
+      f[k] = Vst[k][v];
+      fm[k] = Vst[4 - k][v];
+    }
+    or_weno5_parts(f, qL[v], bL[v]);
+    or_weno5_parts(fm, qR[v], bR[v]);
+  }
+  double VL[OR_MAXV], VR[OR_MAXV], w[3];
+  for (int p = 0; p < N; p++) {
+    /* Eq. 16: the weights of (alpha rho)_p reconstruct both (alpha rho)_p and alpha_p. */
+    weights(g, bL[IMASS(p)], w);
+    VL[IMASS(p)] = combine(w, qL[IMASS(p)]);
+    if (!g->coupled) weights(g, bL[IALF(g, p)], w);
+    VL[IALF(g, p)] = combine(w, qL[IALF(g, p)]);
+    weights(g, bR[IMASS(p)], w);
+    VR[IMASS(p)] = combine(w, qR[IMASS(p)]);
+    if (!g->coupled) weights(g, bR[IALF(g, p)], w);
+    VR[IALF(g, p)] = combine(w, qR[IALF(g, p)]);
+  }
+  /* u and P: each reconstructed with its own WENO-W weights (Sec. 3.3). */
+  for (int v = N; v <= N + d; v++) {
+    weights(g, bL[v], w);
+    VL[v] = combine(w, qL[v]);
+    weights(g, bR[v], w);
+    VR[v] = combine(w, qR[v]);
+  }
+  return limit_chain(g, Ust + 2 * nvar, VL, VR, UL, UR, VfL, VfR, th);
+}
+
+/* Mixture sound speed, Eq. 2 with K_p = 0 (R8). */
+static double sound_speed(const or_grid *g, const double *U, const double *V) {
+  int N = g->N;
+  double rho = 0.0, num = 0.0, den = 0.0, P = V[IENE(g)];
+  for (int p = 0; p < N; p++) {
+    rho += U[IMASS(p)];
+    double Aa = eos_A(g, p) * U[IALF(g, p)];
+    num += Aa * (g->gamma[p] * (P + g->pinf[p]));
+    den += Aa;
+  }
+  double rhoc2 = num / den;
+  return sqrt(rhoc2 / rho);
+}
+
+/* Physical flux of Eq. 1 (hyperbolic part) in direction dir. */
+static void phys_flux(const or_grid *g, int dir, const double *U, const double *V, double *F) {
+  int N = g->N, d = g->dim;
+  double un = V[IMOM(g, dir)], P = V[IENE(g)];
+  for (int p = 0; p < N; p++) {
+    F[IMASS(p)] = U[IMASS(p)] * un;
+    F[IALF(g, p)] = U[IALF(g, p)] * un;
+  }
+  for (int j = 0; j < d; j++) F[IMOM(g, j)] = U[IMOM(g, j)] * un + (j == dir ? P : 0.0);
+  F[IENE(g)] = un * (U[IENE(g)] + P);
+}
+
+/* HLL / HLLC numerical flux and the consistent face velocity u-hat (R7). */
+int or_flux(const or_grid *g, int dir, const double *UL, const double *VL, const double *UR,
+            const double *VR, double *F, double *uhat) {
+  int N = g->N, d = g->dim, nvar = nv(g);
+  double uL = VL[IMOM(g, dir)], uR = VR[IMOM(g, dir)];
+  double cL = sound_speed(g, UL, VL), cR = sound_speed(g, UR, VR);
+  double sL = fmin(uL - cL, uR - cR);
+  double sR = fmax(uL + cL, uR + cR);
+  double FL[OR_MAXV], FR[OR_MAXV];
+  phys_flux(g, dir, UL, VL, FL);
+  phys_flux(g, dir, UR, VR, FR);
+  if (sL >= 0.0) {
+    memcpy(F, FL, sizeof(double) * nvar);
+    *uhat = uL;
+    return OR_OK;
+  }
+  if (sR <= 0.0) {
+    memcpy(F, FR, sizeof(double) * nvar);
+    *uhat = uR;
+    return OR_OK;
+  }
+  if (g->flux == OR_FLUX_HLL) {
+    for (int v = 0; v < nvar; v++)
+      F[v] = (sR * FL[v] - sL * FR[v] + sL * sR * (UR[v] - UL[v])) / (sR - sL);
+    *uhat = (sR * uL * 1.0 - sL * uR * 1.0 + sL * sR * (1.0 - 1.0)) / (sR - sL);
+    return OR_OK;
+  }
+  /* HLLC */
+  double rL = 0.0, rR = 0.0;
+  for (int p = 0; p < N; p++) {
+    rL += UL[IMASS(p)];
+    rR += UR[IMASS(p)];
+  }
+  double PL = VL[IENE(g)], PR = VR[IENE(g)];
+  double sS = (PR - PL + rL * uL * (sL - uL) - rR * uR * (sR - uR)) /
+              (rL * (sL - uL) - rR * (sR - uR));
+  const double *UK, *VK, *FK;
+  double sK, rK, uK;
+  if (sS >= 0.0) { UK = UL; VK = VL; FK = FL; sK = sL; rK = rL; uK = uL; }
+  else { UK = UR; VK = VR; FK = FR; sK = sR; rK = rR; uK = uR; }
+  double chi = (sK - uK) / (sK - sS);
+  double Us[OR_MAXV];
+  for (int p = 0; p < N; p++) {
+    Us[IMASS(p)] = UK[IMASS(p)] * chi;
+    Us[IALF(g, p)] = UK[IALF(g, p)] * chi;
+  }
+  for (int j = 0; j < d; j++) Us[IMOM(g, j)] = rK * chi * (j == dir ? sS : VK[IMOM(g, j)]);
+  Us[IENE(g)] = chi * (UK[IENE(g)] + (sS - uK) * (rK * sS + VK[IENE(g)] / (sK - uK)));
+  for (int v = 0; v < nvar; v++) F[v] = FK[v] + sK * (Us[v] - UK[v]);
+  *uhat = uK * 1.0 + sK * (1.0 * chi - 1.0);
+  return OR_OK;
+}
+
+/* Boundary index map (R9).  Returns the interior index and sets *flip when the
+ * normal momentum must be negated. */
+static int bc_map(int j, int n, int bclo, int bchi, int *flip) {
+  *flip = 0;
+  if (j < 0) {
+    if (bclo == OR_BC_PERIODIC) return ((j % n) + n) % n;
+    if (bclo == OR_BC_REFLECTIVE) { *flip = 1; return -1 - j; }
+    return 0;
+  }
+  if (j >= n) {
+    if (bchi == OR_BC_PERIODIC) return j % n;
+    if (bchi == OR_BC_REFLECTIVE) { *flip = 1; return 2 * n - 1 - j; }
+    return n - 1;
+  }
+  return j;
+}
+
+static long ncells(const or_grid *g) { return (long)g->n[0] * g->n[1] * g->n[2]; }
+
+static void load_cell(const or_grid *g, const double *U, long cell, double *out) {
+  long nc = ncells(g);
+  for (int v = 0; v < nv(g); v++) out[v] = U[(long)v * nc + cell];
+}
+
+/* Limited face states of every cell of one pencil along dir (cells -1..n).
+ * base = linear index of the pencil's cell 0, stride = index step along dir. */
+static int pencil_faces(const or_grid *g, int dir, const double *U, long base, long stride,
+                        double *FLs, double *FRs, double *VLs, double *VRs, double *TH) {
+  int n = g->n[dir], nvar = nv(g);
+  double Ust[5 * OR_MAXV];
+  for (int i = -1; i <= n; i++) {
+    for (int k = 0; k < 5; k++) {
+      int flip;
+      int jj = bc_map(i - 2 + k, n, g->bc[2 * dir], g->bc[2 * dir + 1], &flip);
+      load_cell(g, U, base + jj * stride, Ust + k * nvar);
+      if (flip) Ust[k * nvar + IMOM(g, dir)] = -Ust[k * nvar + IMOM(g, dir)];
+    }
+    int e = recon_cell(g, Ust, FLs + (i + 1) * nvar, FRs + (i + 1) * nvar,
+                       VLs + (i + 1) * nvar, VRs + (i + 1) * nvar,
+                       TH ? TH + 3 * (i + 1) : NULL);
+    if (e) return e;
+  }
+  return OR_OK;
+}
+
+/* One direction's contribution to dU/dt (Eq. 3), added into Lout. */
+static int rhs_dir(const or_grid *g, int dir, const double *U, double *Lout) {
+  int nvar = nv(g), N = g->N, d = g->dim;
+  int n = g->n[dir];
+  long nc = ncells(g);
+  long stride = dir == 0 ? 1 : (dir == 1 ? g->n[0] : (long)g->n[0] * g->n[1]);
+  long npencil = nc / n;
+  double dx = g->dx[dir];
+  int err = OR_OK;
+#pragma omp parallel
+  {
+    double *FLs = malloc(sizeof(double) * nvar * (n + 2));
+    double *FRs = malloc(sizeof(double) * nvar * (n + 2));
+    double *VLs = malloc(sizeof(double) * nvar * (n + 2));
+    double *VRs = malloc(sizeof(double) * nvar * (n + 2));
+    double *Fx = malloc(sizeof(double) * nvar * (n + 1));
+    double *uh = malloc(sizeof(double) * (n + 1));
+#pragma omp for schedule(dynamic, 4)
+    for (long pc = 0; pc < npencil; pc++) {
+      /* pencil pc -> linear index of its first cell */
+      long base;
+      if (dir == 0) base = pc * n;
+      else if (dir == 1) base = (pc / g->n[0]) * ((long)g->n[0] * n) + pc % g->n[0];
+      else base = pc;
+      int e = pencil_faces(g, dir, U, base, stride, FLs, FRs, VLs, VRs, NULL);
+      /* face m sits between cell m-1 (left state) and cell m (right state) */
+      for (int m = 0; m <= n && !e; m++)
+        e = or_flux(g, dir, FLs + m * nvar, VLs + m * nvar, FRs + (m + 1) * nvar,
+                    VRs + (m + 1) * nvar, Fx + m * nvar, uh + m);
+      if (e) {
+#pragma omp critical
+        err = e;
+        continue;
+      }
+      for (int m = 0; m < n; m++) {
+        long cell = base + m * stride;
+        for (int v = 0; v < nvar; v++)
+          Lout[v * nc + cell] += -(Fx[(m + 1) * nvar + v] - Fx[m * nvar + v]) / dx;
+        /* H^HB(Ubar) div(u-hat): alpha_p (1 + K_p), K_p = 0 */
+        for (int p = 0; p < N; p++) {
+          double ab = U[(long)IALF(g, p) * nc + cell];
+          Lout[(long)IALF(g, p) * nc + cell] += ab * (1.0 + 0.0) * (uh[m + 1] - uh[m]) / dx;
+        }
+      }
+    }
+    free(FLs); free(FRs); free(VLs); free(VRs); free(Fx); free(uh);
+  }
+  (void)d;
+  return err;
+}
+
+static int check_grid(const or_grid *g) {
+  if (g->dim < 1 || g->dim > 3 || g->N < 1 || g->N > OR_MAXP) return OR_ERR_ARG;
+  for (int a = 0; a < 3; a++) {
+    if (g->n[a] < 1) return OR_ERR_ARG;
+    if (a < g->dim && g->n[a] < 3) return OR_ERR_ARG;
+    if (a >= g->dim && g->n[a] != 1) return OR_ERR_ARG;
+  }
+  return OR_OK;
+}
+
+/* dU/dt of the hyperbolic step (Eq. 3), summed over the directions. */
+int or_rhs(const or_grid *g, const double *U, double *L) {
+  int e = check_grid(g);
+  if (e) return e;
+  long tot = ncells(g) * nv(g);
+  for (long k = 0; k < tot; k++) L[k] = 0.0;
+  for (int dir = 0; dir < g->dim; dir++) {
+    e = rhs_dir(g, dir, U, L);
+    if (e) return e;
+  }
+  for (long k = 0; k < tot; k++)
+    if (!isfinite(L[k])) return OR_ERR_NAN;
+  return OR_OK;
+}
+
+/* Limited face states of every interior cell along dir (for the pins):
+ * UL = U^L_{i+1/2}, UR = U^R_{i-1/2}, [NV][cells]; TH = [3][cells] or NULL. */
+int or_faces(const or_grid *g, int dir, const double *U, double *ULo, double *URo, double *THo) {
+  int e = check_grid(g);
+  if (e) return e;
+  int nvar = nv(g), n = g->n[dir];
+  long nc = ncells(g);
+  long stride = dir == 0 ? 1 : (dir == 1 ? g->n[0] : (long)g->n[0] * g->n[1]);
+  long npencil = nc / n;
+  double *FLs = malloc(sizeof(double) * nvar * (n + 2));
+  double *FRs = malloc(sizeof(double) * nvar * (n + 2));
+  double *VLs = malloc(sizeof(double) * nvar * (n + 2));
+  double *VRs = malloc(sizeof(double) * nvar * (n + 2));
+  double *TH = malloc(sizeof(double) * 3 * (n + 2));
+  for (long pc = 0; pc < npencil && !e; pc++) {
+    long base;
+    if (dir == 0) base = pc * n;
+    else if (dir == 1) base = (pc / g->n[0]) * ((long)g->n[0] * n) + pc % g->n[0];
+    else base = pc;
+    e = pencil_faces(g, dir, U, base, stride, FLs, FRs, VLs, VRs, TH);
+    for (int m = 0; m < n && !e; m++) {
+      long cell = base + m * stride;
+      for (int v = 0; v < nvar; v++) {
+        ULo[v * nc + cell] = FLs[(m + 1) * nvar + v];
+        URo[v * nc + cell] = FRs[(m + 1) * nvar + v];
+      }
+      if (THo)
+        for (int t = 0; t < 3; t++) THo[t * nc + cell] = TH[3 * (m + 1) + t];
+    }
+  }
+  free(FLs); free(FRs); free(VLs); free(VRs); free(TH);
+  return e;
+}
+
+/* Eq. 17-21 alone on given raw primitive faces of ncell independent cells.
+ * Ubar [NV][ncell] conservative averages; VLraw, VRraw [NV][ncell] primitive
+ * values at x_{i+1/2} and x_{i-1/2}; outputs ULo, URo [NV][ncell] and
+ * THo [3][ncell] (may be NULL). */
+int or_limit(const or_grid *g, long ncell, const double *Ubar, const double *VLraw,
+             const double *VRraw, double *ULo, double *URo, double *THo) {
+  int nvar = nv(g);
+  for (long c = 0; c < ncell; c++) {
+    double Ub[OR_MAXV], VL[OR_MAXV], VR[OR_MAXV], UL[OR_MAXV], UR[OR_MAXV];
+    double VfL[OR_MAXV], VfR[OR_MAXV], th[3];
+    for (int v = 0; v < nvar; v++) {
+      Ub[v] = Ubar[v * ncell + c];
+      VL[v] = VLraw[v * ncell + c];
+      VR[v] = VRraw[v * ncell + c];
+    }
+    int e = limit_chain(g, Ub, VL, VR, UL, UR, VfL, VfR, th);
+    if (e) return e;
+    for (int v = 0; v < nvar; v++) {
+      ULo[v * ncell + c] = UL[v];
+      URo[v * ncell + c] = UR[v];
+    }
+    if (THo)
+      for (int t = 0; t < 3; t++) THo[t * ncell + c] = th[t];
+  }
+  return OR_OK;
+}
+
+int or_cons_to_prim(const or_grid *g, long ncell, const double *U, double *V) {
+  int nvar = nv(g);
+  for (long c = 0; c < ncell; c++) {
+    double u[OR_MAXV], w[OR_MAXV];
+    for (int v = 0; v < nvar; v++) u[v] = U[v * ncell + c];
+    int e = cons_to_prim(g, u, w);
+    if (e) return e;
+    for (int v = 0; v < nvar; v++) V[v * ncell + c] = w[v];
+  }
+  return OR_OK;
+}
+
+int or_prim_to_cons(const or_grid *g, long ncell, const double *V, double *U) {
+  int nvar = nv(g);
+  for (long c = 0; c < ncell; c++) {
+    double u[OR_MAXV], w[OR_MAXV];
+    for (int v = 0; v < nvar; v++) w[v] = V[v * ncell + c];
+    prim_to_cons(g, w, u);
+    for (int v = 0; v < nvar; v++) U[v * ncell + c] = u[v];
+  }
+  return OR_OK;
+}
+
+int or_psi(const or_grid *g, long ncell, const double *U, double *psi) {
+  int nvar = nv(g);
+  for (long c = 0; c < ncell; c++) {
+    double u[OR_MAXV];
+    for (int v = 0; v < nvar; v++) u[v] = U[v * ncell + c];
+    psi[c] = psi_energy(g, u);
+  }
+  return OR_OK;
+}
+
+int or_sound_speed(const or_grid *g, long ncell, const double *U, double *c) {
+  int nvar = nv(g);
+  for (long k = 0; k < ncell; k++) {
+    double u[OR_MAXV], w[OR_MAXV];
+    for (int v = 0; v < nvar; v++) u[v] = U[v * ncell + k];
+    int e = cons_to_prim(g, u, w);
+    if (e) return e;
+    c[k] = sound_speed(g, u, w);
+  }
+  return OR_OK;
+}
+
+/* R10: the largest sum_d (|u_d| + c)/dx_d over the cells. */
+int or_max_rate(const or_grid *g, const double *U, double *rate) {
+  int nvar = nv(g);
+  long nc = ncells(g);
+  double best = 0.0;
+  for (long k = 0; k < nc; k++) {
+    double u[OR_MAXV], w[OR_MAXV];
+    for (int v = 0; v < nvar; v++) u[v] = U[v * nc + k];
+    int e = cons_to_prim(g, u, w);
+    if (e) return e;
+    double c = sound_speed(g, u, w), r = 0.0;
+    for (int j = 0; j < g->dim; j++) r += (fabs(w[IMOM(g, j)]) + c) / g->dx[j];
+    if (r > best) best = r;
+  }
+  *rate = best;
+  return OR_OK;
+}
+
+/* One third-order SSP (TVD) Runge-Kutta step of Shu & Osher, in place.
+ * dt_fixed > 0 gives the time step; otherwise dt = cfl / max rate (R10). */
+int or_rk3_step(const or_grid *g, double *U, double cfl, double dt_fixed, double *dt_used) {
+  int e = check_grid(g);
+  if (e) return e;
+  long tot = ncells(g) * nv(g);
+  double dt = dt_fixed;
+  if (!(dt > 0.0)) {
+    double rate;
+    e = or_max_rate(g, U, &rate);
+    if (e) return e;
+    dt = cfl / rate;
+  }
+  double *U0 = malloc(sizeof(double) * tot), *U1 = malloc(sizeof(double) * tot);
+  double *L = malloc(sizeof(double) * tot);
+  memcpy(U0, U, sizeof(double) * tot);
+  e = or_rhs(g, U0, L);
+  if (!e) {
+    for (long k = 0; k < tot; k++) U1[k] = U0[k] + dt * L[k];
+    e = or_rhs(g, U1, L);
+  }
+  if (!e) {
+    for (long k = 0; k < tot; k++) U1[k] = 0.75 * U0[k] + 0.25 * U1[k] + 0.25 * dt * L[k];
+    e = or_rhs(g, U1, L);
+  }
+  if (!e)
+    for (long k = 0; k < tot; k++)
+      U[k] = 1.0 / 3.0 * U0[k] + 2.0 / 3.0 * U1[k] + 2.0 / 3.0 * dt * L[k];
+  free(U0); free(U1); free(L);
+  if (dt_used) *dt_used = dt;
+  return e;
+}

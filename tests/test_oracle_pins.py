@@ -1,0 +1,427 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms,
+definitions written from a different route (Jiang-Shu smoothness integrals,
+the printed Eq. 22 polynomial and the Gauss-Lobatto nodes), limits, algebraic
+identities, invariants the paper states, and values the paper prints
+(tests/golden/paper_values.json).  No GPU is needed.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_00746_b300 import inputs
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+D_IDEAL = np.array([0.1, 0.6, 0.3])
+
+
+def cell_averages(coeffs, edges):
+    """Exact cell averages of the polynomial sum c_k x^k between edges."""
+    P = np.polynomial.Polynomial(coeffs).integ()
+    return (P(edges[1:]) - P(edges[:-1])) / np.diff(edges)
+
+
+# ---------------------------------------------------------------- WENO5 parts
+@pytest.mark.parametrize("seed", range(5))
+def test_candidates_reproduce_quadratics_and_ideal_weights_quartics(seed):
+    """Each candidate is exact for degree <= 2; the ideal weights d = (1, 6, 3)/10
+    recombine them exactly for degree <= 4 (Sec. 3.1, Eq. 10 with r = 2)."""
+    rng = np.random.default_rng(seed)
+    h = 10.0 ** rng.uniform(-3, 0)
+    x0 = rng.uniform(-1, 1)
+    edges = x0 + h * (np.arange(6) - 2.5)          # cells i-2..i+2, cell i centred at x0
+    xf = x0 + 0.5 * h                               # x_{i+1/2}
+    c2 = rng.normal(size=3)
+    q, _ = oracle.weno5_parts(cell_averages(c2, edges))
+    exact = np.polynomial.Polynomial(c2)(xf)
+    assert np.allclose(q, exact, rtol=1e-11, atol=1e-12 * np.abs(c2).sum())
+    c4 = rng.normal(size=5)
+    q, _ = oracle.weno5_parts(cell_averages(c4, edges))
+    exact = np.polynomial.Polynomial(c4)(xf)
+    assert abs(D_IDEAL @ q - exact) <= 1e-10 * max(1.0, abs(exact))
+    # a plain cubic defeats single candidates (so the first check has teeth)
+    c3 = np.array([0, 0, 0, 1.0])
+    q, _ = oracle.weno5_parts(cell_averages(c3, edges))
+    assert np.abs(q - np.polynomial.Polynomial(c3)(xf)).max() > 1e-6 * h ** 3
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_smoothness_indicators_match_jiang_shu_integrals(seed):
+    """IS_s = sum_{l=1,2} h^(2l-1) int_{I_i} (d^l p_s/dx^l)^2 dx, with p_s the
+    quadratic whose cell averages on sub-stencil s are the data (Jiang-Shu
+    definition, cited in Sec. 3.1)."""
+    rng = np.random.default_rng(100 + seed)
+    h = 0.1
+    f = rng.normal(size=5) * 10.0 ** rng.uniform(-2, 2)
+    edges = h * (np.arange(6) - 2.5)
+    _, beta = oracle.weno5_parts(f)
+    for s in range(3):
+        cells = [s, s + 1, s + 2]
+        # columns: cell averages of 1, x, x^2 on the sub-stencil cells
+        A = np.array([[cell_averages(np.eye(3)[k], edges[c:c + 2])[0] for k in range(3)]
+                      for c in cells])
+        coef = np.linalg.solve(A, f[cells])
+        p = np.polynomial.Polynomial(coef)
+        a, b = -0.5 * h, 0.5 * h
+        val = 0.0
+        for l in (1, 2):
+            dp2 = (p.deriv(l) ** 2).integ()
+            val += h ** (2 * l - 1) * (dp2(b) - dp2(a))
+        assert beta[s] == pytest.approx(val, rel=1e-9, abs=1e-12 * np.abs(f).max() ** 2)
+
+
+# ---------------------------------------------------------------- Eq. 15
+def test_wenow_weight_limits():
+    """Eq. 15 special cases: all IS equal to zero -> ideal weights; zero IS
+    stencils take all the weight in proportion to d (infinite ratios)."""
+    assert np.allclose(oracle.wenow_weights([0.0, 0.0, 0.0]), D_IDEAL, rtol=1e-15)
+    assert np.array_equal(oracle.wenow_weights([0.0, 2.0, 3.0]), [1.0, 0.0, 0.0])
+    assert np.array_equal(oracle.wenow_weights([5.0, 0.0, 3.0]), [0.0, 1.0, 0.0])
+    w = oracle.wenow_weights([0.0, 7.0, 0.0])
+    assert w[1] == 0.0 and w[0] == pytest.approx(0.1 / 0.4) and w[2] == pytest.approx(0.3 / 0.4)
+    w = oracle.wenow_weights([1.0, 1.0, 1.0])
+    assert np.allclose(w, D_IDEAL, rtol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_wenow_equals_eps_free_js_form(seed):
+    """For positive IS, dividing Eq. 15 by (IS_s)^2 gives
+    omega_s = (d_s/IS_s^2) / sum_k (d_k/IS_k^2): the JS form with eps = 0."""
+    rng = np.random.default_rng(seed)
+    for _ in range(200):
+        beta = 10.0 ** rng.uniform(-30, 30, size=3)
+        a = D_IDEAL / beta ** 2
+        assert np.allclose(oracle.wenow_weights(beta), a / a.sum(), rtol=1e-13, atol=1e-300)
+
+
+def _recon(f, weights):
+    q, b = oracle.weno5_parts(np.asarray(f, dtype=np.float64))
+    w = weights(b)
+    return w @ q
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_wenow_scale_invariance(seed):
+    """Sec. 3.3: with Eq. 15, g = a f + b reconstructs to g^L = a f^L + b for any
+    a (no epsilon).  Stencils mix smooth and discontinuous data."""
+    rng = np.random.default_rng(seed)
+    for _ in range(300):
+        f = rng.normal(size=5)
+        if rng.uniform() < 0.5:
+            f[rng.integers(1, 5):] += rng.normal() * 10
+        a = 10.0 ** rng.uniform(-6, 6) * rng.choice([-1, 1])
+        b = rng.normal() * 10.0 ** rng.uniform(-3, 3)
+        fL = _recon(f, oracle.wenow_weights)
+        gL = _recon(a * f + b, oracle.wenow_weights)
+        scale = abs(a) * np.abs(f).max() + abs(b)
+        assert abs(gL - (a * fL + b)) <= 1e-12 * scale
+
+
+def test_wenojs_linear_map_and_printed_ratio():
+    """Eq. 14: JS gives g^L(eps) = a f^L(eps/a^2) + b, and the paper's worked
+    number eps/rho_1^2 = 0.6898 (Sec. 3.2).  JS is therefore not invariant."""
+    gold = GOLD["js_eps_over_a2"]
+    eps, a = gold["eps"], gold["a"]
+    assert round(eps / a ** 2, gold["printed_digits"]) == gold["value"]
+    f = np.array([0.0, 0.0, 0.0, 1.0, 1.0])          # an interface in alpha_1
+    b = 0.0
+    gL = _recon(a * f + b, lambda be: oracle.wenojs_weights(be, eps))
+    fL_scaled = _recon(f, lambda be: oracle.wenojs_weights(be, eps / a ** 2))
+    assert gL == pytest.approx(a * fL_scaled + b, rel=1e-12)
+    fL = _recon(f, lambda be: oracle.wenojs_weights(be, eps))
+    assert abs(gL - a * fL) > 1e-3 * a        # inconsistent mass vs fraction
+    assert _recon(a * f, oracle.wenow_weights) == pytest.approx(a * _recon(f, oracle.wenow_weights), rel=1e-13)
+
+
+# ---------------------------------------------------------------- helpers
+def grid_of(case, **kw):
+    return oracle.Grid(case.shape, case.dx, case.gamma, case.pinf, case.D,
+                       flux=kw.pop("flux", case.flux), bc=case.bc, **kw)
+
+
+def random_1d_case(n, N, seed, sharp=True):
+    """Random admissible 1-D N-phase state with constant phasic densities."""
+    rng = np.random.default_rng(seed)
+    x = (np.arange(n) + 0.5) / n
+    alpha = []
+    rem = np.ones(n)
+    for p in range(N - 1):
+        c = rng.uniform(0.1, 0.9)
+        w = rng.uniform(0.3, 3.0) / n if not sharp else 1e-9
+        s = 0.5 * (1 + np.tanh((0.12 - np.abs(x - c)) / w)) * rng.uniform(0.5, 1.0)
+        a = rem * s
+        alpha.append(a)
+        rem = rem - a
+    alpha.append(rem)
+    rho = 10.0 ** rng.uniform(-3, 3, size=N)
+    gam = rng.uniform(1.2, 6.0, size=N)
+    pinf = np.where(rng.uniform(size=N) < 0.5, 0.0, 10.0 ** rng.uniform(3, 8, size=N))
+    P = 1e5 * (1 + 0.5 * np.sin(2 * np.pi * x * rng.integers(1, 4)))
+    u = rng.normal() * 10 + np.sin(2 * np.pi * x)
+    V = inputs._assemble(alpha, list(rho), [u], P)
+    return inputs.Case("rand", (n,), (1.0 / n,), list(gam), list(pinf), [0.0] * N, V,
+                       ("periodic",) * 6, flux="hll"), rho
+
+
+# ---------------------------------------------------------------- consistency
+@pytest.mark.parametrize("N,seed", [(2, 0), (3, 1), (4, 2)])
+def test_mass_fraction_consistency_at_faces(N, seed):
+    """Sec. 2.2.2 / Eq. 16: rho_p constant in the stencil gives
+    (alpha rho)_p^{L,R} = rho_p alpha_p^{L,R}, after the whole limiter chain."""
+    case, rho = random_1d_case(120, N, seed)
+    g = grid_of(case)
+    U = oracle.prim_to_cons(g, case.V)
+    UL, UR, TH = oracle.faces(g, U, 0)
+    for p in range(N):
+        for F in (UL, UR):
+            m, a = F[p], F[N + 2 + p]
+            assert np.allclose(m, rho[p] * a, rtol=1e-13, atol=1e-15 * rho[p])
+
+
+# ---------------------------------------------------------------- admissibility
+ULP1 = 2.0 ** -52
+
+
+def check_admissible(g, UL, UR, Ub, N, d, tol_sum):
+    """Eq. 8 at the faces.  The convex blends f + theta (f' - f) of Eq. 17, 20
+    and 21 round, so the upper bound 1 of the fractions holds to 2 ulp."""
+    for F in (UL, UR):
+        assert (F[:N] >= 0).all()
+        alpha = F[N + d + 1:]
+        assert (alpha >= 0).all() and (alpha <= 1 + 2 * ULP1).all()
+        assert np.abs(alpha.sum(0) - 1.0).max() <= tol_sum
+        assert (oracle.psi(g, F) >= -1e-9 * np.abs(F[N + d])).all()
+
+
+@pytest.mark.parametrize("N,seed", [(2, 3), (3, 4), (5, 5)])
+def test_limiter_chain_admissible_on_random_faces(N, seed):
+    """Eq. 17-21 on adversarial raw faces: masses >= 0, fractions in [0, 1],
+    unity sum to rounding, psi >= 0 at both faces and at the interior value
+    U^C of Eq. 6, thetas in [0, 1], masses and fractions scaled together."""
+    d = 2
+    Vb, VL, VR = inputs.random_admissible_stencils(4000, N, d, seed=seed)
+    rng = np.random.default_rng(seed)
+    gam = list(rng.uniform(1.2, 6.0, size=N))
+    pinf = list(np.where(rng.uniform(size=N) < 0.5, 0.0, 10.0 ** rng.uniform(3, 8, size=N)))
+    g = oracle.Grid((8, 8), (1.0, 1.0), gam, pinf)
+    Ub = oracle.prim_to_cons(g, Vb)
+    # keep only cells whose average is admissible (psi >= 0)
+    keep = oracle.psi(g, Ub) > 0
+    Ub, VL, VR = Ub[:, keep], VL[:, keep], VR[:, keep]
+    UL, UR, TH = oracle.limit(g, Ub, VL, VR)
+    assert ((TH >= 0) & (TH <= 1)).all()
+    assert (TH < 1).any(axis=1).all(), "every limiter stage must be exercised"
+    check_admissible(g, UL, UR, Ub, N, d, tol_sum=4 * N * 2.0 ** -53)
+    UC = (Ub - (UL + UR) / 12.0) / (5.0 / 6.0)
+    assert (UC[:N] >= -1e-12 * np.abs(Ub[:N]).max(0)).all()
+    assert (UC[N + d + 1:] >= -1e-12).all()
+    assert (oracle.psi(g, UC) >= -1e-8 * np.abs(Ub[N + d])).all()
+
+
+def test_faces_of_random_states_admissible():
+    for N, seed in [(2, 7), (3, 8), (4, 9)]:
+        case, _ = random_1d_case(200, N, seed)
+        g = grid_of(case)
+        U = oracle.prim_to_cons(g, case.V)
+        UL, UR, TH = oracle.faces(g, U, 0)
+        check_admissible(g, UL, UR, U, N, 1, tol_sum=4 * N * 2.0 ** -53)
+
+
+# ---------------------------------------------------------------- Eq. 6 / Eq. 22
+def test_interior_value_matches_eq22_polynomial():
+    """The interior value f^C used by Eq. 18 equals the mean of the printed
+    quartic of Eq. 22 at the two interior Gauss-Lobatto nodes +-dx/(2 sqrt 5);
+    pinned through theta, which the oracle reports: a raw face pair that makes
+    f^C the only negative value gives theta = fbar / (fbar - f^C)."""
+    gold = GOLD["eq22_coefficients"]
+    rng = np.random.default_rng(11)
+    g = oracle.Grid((4,), (1.0,), [1.4, 1.4], [0.0, 0.0])
+    N, d = 2, 1
+    for _ in range(50):
+        h = 1.0
+        fb = rng.uniform(0.01, 0.07)               # fraction average of phase 1
+        fL, fR = rng.uniform(0.35, 0.6, size=2)    # raw faces with fL + fR > 12 fb
+        nb = rng.uniform(0, 1, size=2)             # neighbour averages (any values)
+        vals = {"up": nb[0], "i": fb, "dn": nb[1], "L": fL, "R": fR}
+        B = []
+        for k in range(5):
+            e = gold[f"B{k}"]
+            row = np.array(e["row"], dtype=float)
+            s = row @ np.array([vals["up"], vals["i"], vals["dn"], vals["L"], vals["R"]])
+            B.append(e["pre"][0] / e["pre"][1] * s / h ** e["dxpow"])
+        poly = np.polynomial.Polynomial(B)
+        # Eq. 22 reproduces the data (checks the printed coefficients)
+        assert poly(0.5) == pytest.approx(fL, abs=1e-12)
+        assert poly(-0.5) == pytest.approx(fR, abs=1e-12)
+        I = poly.integ()
+        assert I(0.5) - I(-0.5) == pytest.approx(fb, abs=1e-12)
+        assert I(1.5) - I(0.5) == pytest.approx(nb[0], abs=1e-12)
+        assert I(-0.5) - I(-1.5) == pytest.approx(nb[1], abs=1e-12)
+        a = 0.5 / np.sqrt(5.0)
+        fC = 0.5 * (poly(a) + poly(-a))
+        if fC >= 0:
+            continue
+        Vb = np.array([fb * 1.0, (1 - fb) * 1.0, 0.0, 1e5, fb, 1 - fb])[:, None]
+        VL = np.array([fL, 1 - fL, 0.0, 1e5, fL, 1 - fL])[:, None]
+        VR = np.array([fR, 1 - fR, 0.0, 1e5, fR, 1 - fR])[:, None]
+        Ub = oracle.prim_to_cons(g, Vb)
+        _, _, TH = oracle.limit(g, Ub, VL, VR)
+        assert TH[0, 0] == pytest.approx(fb / (fb - fC), rel=1e-12)
+
+
+def test_gauss_lobatto_weight_printed():
+    """Sec. 4.2 prints w^(1) = 1/12 for N_quad = 4; the 4-point Gauss-Lobatto
+    rule with weight 1/12 at the ends integrates quartics exactly."""
+    w1 = GOLD["gauss_lobatto_w1"]["value"]
+    a = 0.5 / np.sqrt(5.0)
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        p = np.polynomial.Polynomial(rng.normal(size=5))
+        I = p.integ()
+        quad = w1 * (p(-0.5) + p(0.5)) + (0.5 - w1) * (p(-a) + p(a))
+        assert quad == pytest.approx(I(0.5) - I(-0.5), abs=1e-13)
+
+
+# ---------------------------------------------------------------- EOS, flux
+def test_pressure_and_sound_speed_closed_forms():
+    """Eq. 26-27 and Eq. 2 for a pure stiffened gas: rho E = (P + gamma Pinf)/(gamma-1)
+    + rho u^2/2 and c^2 = gamma (P + Pinf) / rho."""
+    g = oracle.Grid((4,), (1.0,), [4.4, 1.4], [6e8, 0.0])
+    rho, u, P = 1000.0, 3.0, 2.5e5
+    V = np.array([rho, 0.0, u, P, 1.0, 0.0])[:, None]
+    U = oracle.prim_to_cons(g, V)
+    assert U[3, 0] == pytest.approx((P + 4.4 * 6e8) / 3.4 + 0.5 * rho * u * u, rel=1e-15)
+    assert oracle.cons_to_prim(g, U)[3, 0] == pytest.approx(P, rel=1e-9)
+    assert oracle.sound_speed(g, U)[0] == pytest.approx(np.sqrt(4.4 * (P + 6e8) / rho), rel=1e-14)
+    # an ideal-gas mixture with equal gammas is an ideal gas of the total density
+    g2 = oracle.Grid((4,), (1.0,), [1.4, 1.4], [0.0, 0.0])
+    V2 = np.array([0.3, 0.5, 1.0, 1e5, 0.4, 0.6])[:, None]
+    U2 = oracle.prim_to_cons(g2, V2)
+    assert oracle.sound_speed(g2, U2)[0] == pytest.approx(np.sqrt(1.4 * 1e5 / 0.8), rel=1e-14)
+
+
+@pytest.mark.parametrize("flux", ["hll", "hllc"])
+def test_flux_consistency_and_uhat(flux):
+    """F(U, U) = physical flux of Eq. 1; u-hat = u for equal states; the sum of
+    the fraction fluxes equals u-hat (Sec. 2.2.1: alpha = 1 gives u-hat)."""
+    rng = np.random.default_rng(5)
+    g = oracle.Grid((4, 4, 4), (1.0,) * 3, [1.4, 4.4, 6.1], [0.0, 6e8, 2e9], flux=flux)
+    N, d = 3, 3
+    for _ in range(100):
+        a = rng.dirichlet([1, 1, 1])
+        rho = np.array([1.0, 1000.0, 1050.0])
+        u = rng.normal(size=3) * 100
+        P = 10 ** rng.uniform(4, 8)
+        V = np.concatenate([a * rho, u, [P], a])
+        U = oracle.prim_to_cons(g, V[:, None])[:, 0]
+        for dr in range(3):
+            F, uh = oracle.flux(g, dr, U, V, U, V)
+            Fp = np.concatenate([U[:N] * u[dr], U[N:N + d] * u[dr] + P * (np.arange(3) == dr),
+                                 [u[dr] * (U[N + d] + P)], U[N + d + 1:] * u[dr]])
+            assert np.allclose(F, Fp, rtol=1e-12, atol=1e-12 * np.abs(Fp).max())
+            assert uh == pytest.approx(u[dr], rel=1e-12, abs=1e-12)
+        # distinct states: sum of fraction fluxes = u-hat
+        a2 = rng.dirichlet([1, 1, 1])
+        V2 = np.concatenate([a2 * rho * 1.1, u + rng.normal(size=3) * 50, [P * 1.5], a2])
+        U2 = oracle.prim_to_cons(g, V2[:, None])[:, 0]
+        F, uh = oracle.flux(g, 0, U, V, U2, V2)
+        assert F[N + d + 1:].sum() == pytest.approx(uh, rel=1e-12, abs=1e-9)
+
+
+# ---------------------------------------------------------------- whole operator
+def test_reduction_absent_phase_bit_identical():
+    """Sec. 3.4 (consistency of reduction): an N-phase run with one phase absent
+    (alpha = alpha rho = 0 exactly) reproduces the (N-1)-phase run bit for bit."""
+    c2 = inputs.interface_advection_1d(n=64)
+    c3 = inputs.interface_advection_1d(n=64, absent_phase=True)
+    g2, g3 = grid_of(c2), grid_of(c3)
+    U2 = oracle.prim_to_cons(g2, c2.V)
+    U3 = oracle.prim_to_cons(g3, c3.V)
+    keep = [0, 1, 3, 4, 5, 6]          # m1 m2 (m3) ru E a1 a2 (a3)
+    absent = [2, 7]
+    assert np.array_equal(U3[keep], U2)
+    L2, L3 = oracle.rhs(g2, U2), oracle.rhs(g3, U3)
+    assert np.array_equal(L3[keep], L2) and not L3[absent].any()
+    for _ in range(5):
+        U2, dt2 = oracle.rk3_step(g2, U2, cfl=0.5)
+        U3, dt3 = oracle.rk3_step(g3, U3, cfl=0.5)
+        assert dt2 == dt3
+        assert np.array_equal(U3[keep], U2) and not U3[absent].any()
+
+
+def test_reduction_five_phase_table1_2d():
+    """Table 1 five-phase advection (phase 5 absent) vs the four-phase run."""
+    c5 = inputs.multiphase_advection_2d(n=24, nphase=5)
+    c4 = inputs.multiphase_advection_2d(n=24, nphase=4)
+    g5, g4 = grid_of(c5), grid_of(c4)
+    rows = GOLD["table1_five_phase"]["rows"]
+    assert c5.gamma == [r[1] for r in rows] and c5.D == [r[3] for r in rows]
+    U5, U4 = oracle.prim_to_cons(g5, c5.V), oracle.prim_to_cons(g4, c4.V)
+    keep = [0, 1, 2, 3, 5, 6, 7, 8, 9, 10, 11]
+    for _ in range(3):
+        U5, _ = oracle.rk3_step(g5, U5, dt=1e-3)
+        U4, _ = oracle.rk3_step(g4, U4, dt=1e-3)
+    assert np.array_equal(U5[keep], U4) and not U5[[4, 12]].any()
+
+
+def test_equilibrium_isolated_interface_1d():
+    """Eq. 1 keeps u and P uniform across an isolated interface (Sec. 2.2.2);
+    the scheme keeps them to round-off.  Pressure error is measured against
+    the pressure scale P0 + max Pinf that rho E carries (one ulp of rho E is
+    ~1e-16 of that scale)."""
+    c = inputs.interface_advection_1d(n=200)
+    g = grid_of(c)
+    U = oracle.prim_to_cons(g, c.V)
+    scale = 1e5 + max(c.pinf)
+    for k in range(20):
+        U, _ = oracle.rk3_step(g, U, cfl=0.5)
+    V = oracle.cons_to_prim(g, U)
+    assert np.abs(V[2] - 1.0).max() < 1e-12
+    assert np.abs(V[3] - 1e5).max() / scale < 1e-13
+    assert np.abs(V[4:].sum(0) - 1).max() < 1e-14
+    assert V[4:].min() >= 0 and V[4:].max() <= 1
+
+
+def test_equilibrium_and_conservation_five_phase_2d():
+    """Five-phase advection (Sec. 4.1.2): u, P uniform; sum alpha = 1; phase 5
+    stays 0; mass, momentum, energy conserved on the periodic box."""
+    c = inputs.multiphase_advection_2d(n=32, nphase=5)
+    g = grid_of(c)
+    U = oracle.prim_to_cons(g, c.V)
+    tot0 = U.reshape(U.shape[0], -1).sum(1)
+    for _ in range(10):
+        U, _ = oracle.rk3_step(g, U, dt=1e-3)
+    V = oracle.cons_to_prim(g, U)
+    tot = U.reshape(U.shape[0], -1).sum(1)
+    N = 5
+    cons = list(range(N)) + [N, N + 1, N + 2]
+    for v in cons:
+        assert abs(tot[v] - tot0[v]) <= 1e-13 * np.abs(U[v]).sum() + 1e-300
+    assert np.abs(V[N:N + 2] - 1.0).max() < 1e-12
+    assert np.abs(V[N + 2] - 4.819e-5).max() / (4.819e-5 + 0.476) < 1e-13
+    assert np.abs(V[N + 3:].sum(0) - 1).max() < 1e-14
+    assert not V[4].any() and not V[N + 3 + 4].any()
+
+
+@pytest.mark.slow
+def test_fifth_order_on_smooth_advection():
+    """Sec. 4.1.4: WENO-C is fifth order on alpha_1 = 0.2 (3 + sin 2 pi x),
+    dt = dx^(5/3), t = 1."""
+    errs = []
+    ns = [20, 40, 80]
+    for n in ns:
+        c = inputs.smooth_advection_1d(n)
+        g = grid_of(c)
+        U = oracle.prim_to_cons(g, c.V)
+        dt = c.meta["dt"]
+        nstep = int(np.ceil(1.0 / dt))
+        dt = 1.0 / nstep
+        for _ in range(nstep):
+            U, _ = oracle.rk3_step(g, U, dt=dt)
+        errs.append(np.abs(U[4] - inputs.smooth_alpha_average(n, 1.0)).mean())
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates[-1] > 4.8, (errs, rates)  # observed 4.997, 5.002 (20 -> 80 cells)
