@@ -1,0 +1,149 @@
+/*
+ * wenoc.h -- C ABI of the B300 WENO-C finite-volume operator.
+ *
+ * The operator is the hyperbolic step of the N-phase Euler/Phase-Field model
+ * of Huang, "Consistent and bound-preserving finite-volume WENO scheme for
+ * compressible two-/N-phase flows with Phase-Field mechanism":
+ *     dU/dt + div F^HB(U^L, U^R) = H^HB(U) div u_hat            (Eq. 3)
+ * with fifth-order WENO-C reconstruction (Eq. 15-21), an HLL or HLLC flux with
+ * the consistent face velocity u_hat (Sec. 2.2.1), and third-order SSP
+ * Runge-Kutta time stepping (Sec. 4).
+ *
+ * State layout (every array in this header): structure of arrays, FP64,
+ *     U[v * ncell + cell],  cell = (k * ny + j) * nx + i   (x fastest)
+ * with v over U = [(alpha rho)_1..N, (rho u)_1..d, rho E, alpha_1..N] (Eq. 1)
+ * or V = [(alpha rho)_1..N, u_1..d, P, alpha_1..N] (primitive, Sec. 2.2.2).
+ * Only interior cells are stored; boundary cells are produced on the fly
+ * from the boundary condition of each side.
+ *
+ * Memory and ownership: the library allocates no device memory.  Every
+ * device pointer belongs to the caller and must stay valid for the calls
+ * that use it; host pointers are read or written only during the call.
+ * All device work is enqueued on the caller's CUDA stream (a cudaStream_t
+ * passed as void*, NULL = legacy default stream); calls return as soon as
+ * the work is enqueued unless stated otherwise.
+ *
+ * Errors: every entry point returns a wc_status and never aborts.  Argument
+ * errors are detected on the host before any launch.  Problems found by the
+ * kernels (an inadmissible state: non-positive density, non-finite pressure)
+ * set bits in a device status word that wc_sync_status() reads.
+ */
+#ifndef WENOC_H
+#define WENOC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WC_MAX_PHASE 8
+
+typedef enum {
+  WC_OK = 0,
+  WC_ERR_ARG = 1,          /* invalid argument (checked on the host) */
+  WC_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  WC_ERR_INADMISSIBLE = 3, /* a kernel met a state outside the admissible set */
+  WC_ERR_NAN = 4,          /* a kernel produced a non-finite value */
+  WC_ERR_UNSUPPORTED = 5,  /* combination not built (e.g. phase count) */
+  WC_ERR_STATE = 6         /* call order: state or workspace not bound */
+} wc_status;
+
+enum { WC_BC_PERIODIC = 0, WC_BC_REFLECTIVE = 1, WC_BC_OUTFLOW = 2 };
+enum { WC_FLUX_HLL = 0, WC_FLUX_HLLC = 1 };
+enum { WC_PREC_FP64 = 0, WC_PREC_MIXED = 1 };
+
+/* Grid, materials and scheme options.  Materials follow the stiffened-gas
+ * equation of state of Eq. 26: A_p = 1/(gamma_p-1), B_p = gamma_p Pinf_p /
+ * (gamma_p-1), D_p; pmin[p] is the phasic minimum pressure of the energy
+ * constraint psi (Eq. 9). */
+typedef struct {
+  int dim;                    /* 1, 2 or 3 */
+  int n[3];                   /* interior cells per axis; 1 on unused axes */
+  double dx[3];               /* uniform cell size per axis (Sec. 3.5) */
+  int nphase;                 /* N, 1..5 built */
+  double gamma[WC_MAX_PHASE];
+  double pinf[WC_MAX_PHASE];
+  double D[WC_MAX_PHASE];
+  double pmin[WC_MAX_PHASE];
+  int flux;                   /* WC_FLUX_HLL (Sec. 4.2) or WC_FLUX_HLLC (Sec. 4.1) */
+  int precision;              /* WC_PREC_FP64 or WC_PREC_MIXED (FP32 smoothness
+                                 indicators, reconstruction and flux; FP64
+                                 pressure, limiter factors, unity sum, update) */
+  int energy_limiter;         /* 1: Eq. 21 applied (default); 0: skipped */
+  int bc[6];                  /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi: WC_BC_* */
+  int seg;                    /* cells per thread along a sweep; 0 = automatic */
+  int block;                  /* threads per block of the sweep; 0 = automatic */
+} wc_grid_desc;
+
+typedef struct wc_grid wc_grid;
+
+/* Creates a grid handle from desc (copied).  Host only, no device work. */
+wc_status wc_init_grid(const wc_grid_desc *desc, wc_grid **out);
+void wc_destroy(wc_grid *g);
+
+/* Number of variables 2N+d+1 and of interior cells. */
+int wc_nvar(const wc_grid *g);
+long wc_ncell(const wc_grid *g);
+
+/* Device scratch that wc_rk_step needs: three state-sized FP64 buffers
+ * (two Runge-Kutta stages and the direction accumulator) plus 256 bytes. */
+size_t wc_workspace_bytes(const wc_grid *g);
+
+/* Binds the caller's device state array U_dev ([NV][ncell] FP64, advanced in
+ * place by wc_rk_step) and a device workspace of at least
+ * wc_workspace_bytes(g) bytes (256-byte aligned). */
+wc_status wc_set_state(wc_grid *g, double *U_dev, void *workspace_dev, size_t ws_bytes);
+
+/* Copies a host state (pinned memory recommended) into / out of the bound
+ * device state, asynchronously on stream. */
+wc_status wc_upload_state(wc_grid *g, const double *U_host, void *stream);
+wc_status wc_download_state(const wc_grid *g, double *U_host, void *stream);
+
+/* psi_{V->U} and psi_{U->V} (mixture rules, Eq. 26, Eq. 27) on device arrays
+ * of ncell cells laid out [NV][ncell]; ncell = wc_ncell(g). */
+wc_status wc_prim_to_cons(const wc_grid *g, const double *V_dev, double *U_dev, void *stream);
+wc_status wc_cons_to_prim(const wc_grid *g, const double *U_dev, double *V_dev, void *stream);
+
+/* L = dU/dt of the hyperbolic step (Eq. 3) for the state U_dev (not the bound
+ * state), summed over the directions; L_dev is overwritten. */
+wc_status wc_rhs(wc_grid *g, const double *U_dev, double *L_dev, void *stream);
+
+/* Time step from the bound state: dt = cfl / max_cells sum_d (|u_d| + c)/dx_d,
+ * written to dt_dev (one double, device). */
+wc_status wc_compute_dt(wc_grid *g, double cfl, double *dt_dev, void *stream);
+
+/* nsteps steps of SSP-RK3 (Shu-Osher form) on the bound state, in place.
+ * dt_fixed > 0 fixes the step; otherwise each step takes dt from cfl and
+ * the state at its start (computed on the device, no host synchronisation).
+ * When dt_host is not NULL the call synchronises the stream at the end and
+ * writes the last step's dt there. */
+wc_status wc_rk_step(wc_grid *g, double cfl, double dt_fixed, int nsteps, double *dt_host,
+                     void *stream);
+
+/* The limiter chain of WENO-C alone (Eq. 17-21) in direction dir on ncell
+ * independent cells: Ubar [NV][ncell] conservative cell averages, VL / VR
+ * [NV][ncell] raw reconstructed primitive values at x_{i+1/2} and x_{i-1/2};
+ * outputs UL / UR [NV][ncell] limited conservative face states and, when
+ * theta is not NULL, theta [3][ncell] = (min_p theta_p of Eq. 17, theta_i of
+ * Eq. 20, theta^(psi) of Eq. 21).  All pointers are device pointers. */
+wc_status wc_limit(const wc_grid *g, int dir, long ncell, const double *Ubar, const double *VL,
+                   const double *VR, double *UL, double *UR, double *theta, void *stream);
+
+/* Synchronises the stream, reads and clears the device status word; returns
+ * WC_OK or the first kernel-detected error. */
+wc_status wc_sync_status(wc_grid *g, void *stream);
+
+/* Copies the last error message into buf (NUL-terminated). */
+void wc_last_error(const wc_grid *g, char *buf, size_t n);
+
+/* Measured FP64 peak helper: runs a dependent-free DFMA loop of iters
+ * iterations on blocks x threads threads and returns the flop count
+ * (2 per DFMA) through *flops; time it with events on the stream. */
+wc_status wc_fp64_peak_kernel(int blocks, int threads, int iters, double *sink_dev,
+                              double *flops, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WENOC_H */

@@ -1,0 +1,377 @@
+// wenoc_api.cu -- host side of the C ABI declared in include/wenoc.h.
+// Argument checks, grid descriptors, Runge-Kutta stage orchestration and
+// kernel dispatch.  The library allocates no device memory: the caller binds
+// its state array and a workspace.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/wenoc.h"
+#include "wenoc_kernels.cuh"
+
+using namespace wc;
+
+struct wc_grid {
+  wc_grid_desc d;
+  Mat mat;
+  int nv;
+  long ncell;
+  double* U = nullptr;       // bound state (caller's device memory)
+  char* ws = nullptr;        // bound workspace
+  size_t ws_bytes = 0;
+  double* B1 = nullptr;      // stage buffers
+  double* B2 = nullptr;
+  double* Lacc = nullptr;    // direction accumulator
+  unsigned* status = nullptr;
+  unsigned long long* rate = nullptr;
+  double* dt = nullptr;
+  char err[256];
+};
+
+static wc_status fail(wc_grid* g, wc_status s, const char* msg) {
+  if (g) snprintf(g->err, sizeof(g->err), "%s", msg);
+  return s;
+}
+
+static wc_status cuda_fail(wc_grid* g, cudaError_t e, const char* where) {
+  if (g) snprintf(g->err, sizeof(g->err), "%s: %s", where, cudaGetErrorString(e));
+  return WC_ERR_CUDA;
+}
+
+static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ------------------------------------------------------------------ dispatch
+#define WC_DISPATCH(N, D, EXPR)                                        \
+  switch ((N) * 4 + (D)) {                                             \
+    case 1 * 4 + 1: { constexpr int N_ = 1, D_ = 1; EXPR; } break;     \
+    case 1 * 4 + 2: { constexpr int N_ = 1, D_ = 2; EXPR; } break;     \
+    case 1 * 4 + 3: { constexpr int N_ = 1, D_ = 3; EXPR; } break;     \
+    case 2 * 4 + 1: { constexpr int N_ = 2, D_ = 1; EXPR; } break;     \
+    case 2 * 4 + 2: { constexpr int N_ = 2, D_ = 2; EXPR; } break;     \
+    case 2 * 4 + 3: { constexpr int N_ = 2, D_ = 3; EXPR; } break;     \
+    case 3 * 4 + 1: { constexpr int N_ = 3, D_ = 1; EXPR; } break;     \
+    case 3 * 4 + 2: { constexpr int N_ = 3, D_ = 2; EXPR; } break;     \
+    case 3 * 4 + 3: { constexpr int N_ = 3, D_ = 3; EXPR; } break;     \
+    case 4 * 4 + 1: { constexpr int N_ = 4, D_ = 1; EXPR; } break;     \
+    case 4 * 4 + 2: { constexpr int N_ = 4, D_ = 2; EXPR; } break;     \
+    case 4 * 4 + 3: { constexpr int N_ = 4, D_ = 3; EXPR; } break;     \
+    case 5 * 4 + 1: { constexpr int N_ = 5, D_ = 1; EXPR; } break;     \
+    case 5 * 4 + 2: { constexpr int N_ = 5, D_ = 2; EXPR; } break;     \
+    case 5 * 4 + 3: { constexpr int N_ = 5, D_ = 3; EXPR; } break;     \
+    default: break;                                                    \
+  }
+
+static int grid_blocks(long n, int threads) {
+  long b = (n + threads - 1) / threads;
+  if (b > 148L * 64) b = 148L * 64;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// ------------------------------------------------------------------ init
+extern "C" wc_status wc_init_grid(const wc_grid_desc* desc, wc_grid** out) {
+  if (!desc || !out) return WC_ERR_ARG;
+  *out = nullptr;
+  const wc_grid_desc& d = *desc;
+  if (d.dim < 1 || d.dim > 3) return WC_ERR_ARG;
+  if (d.nphase < 1 || d.nphase > 5) return WC_ERR_UNSUPPORTED;
+  for (int a = 0; a < 3; a++) {
+    if (a < d.dim && (d.n[a] < 3 || !(d.dx[a] > 0.0))) return WC_ERR_ARG;
+    if (a >= d.dim && d.n[a] != 1) return WC_ERR_ARG;
+  }
+  for (int k = 0; k < 2 * d.dim; k++)
+    if (d.bc[k] < 0 || d.bc[k] > 2) return WC_ERR_ARG;
+  for (int a = 0; a < d.dim; a++)
+    if ((d.bc[2 * a] == WC_BC_PERIODIC) != (d.bc[2 * a + 1] == WC_BC_PERIODIC)) return WC_ERR_ARG;
+  if (d.flux != WC_FLUX_HLL && d.flux != WC_FLUX_HLLC) return WC_ERR_ARG;
+  if (d.precision != WC_PREC_FP64 && d.precision != WC_PREC_MIXED) return WC_ERR_UNSUPPORTED;
+  if (d.seg < 0 || d.block < 0 || d.block > 128 || (d.block % 32) != 0) return WC_ERR_ARG;
+  for (int p = 0; p < d.nphase; p++)
+    if (!(d.gamma[p] > 1.0) || !(d.pinf[p] >= 0.0)) return WC_ERR_ARG;
+  wc_grid* g = new (std::nothrow) wc_grid();
+  if (!g) return WC_ERR_ARG;
+  g->d = d;
+  g->nv = 2 * d.nphase + d.dim + 1;
+  g->ncell = (long)d.n[0] * d.n[1] * d.n[2];
+  Mat& m = g->mat;
+  memset(&m, 0, sizeof(m));
+  m.N = d.nphase;
+  for (int p = 0; p < d.nphase; p++) {
+    m.A[p] = 1.0 / (d.gamma[p] - 1.0);
+    m.B[p] = d.gamma[p] * d.pinf[p] / (d.gamma[p] - 1.0);
+    m.D[p] = d.D[p];
+    m.pinf[p] = d.pinf[p];
+    m.Ag[p] = m.A[p] * d.gamma[p];
+    m.Apmin[p] = m.A[p] * d.pmin[p];
+    m.Cmin[p] = m.A[p] * d.pmin[p] + m.B[p];
+    if (d.D[p] != 0.0) m.hasD = 1;
+  }
+  g->err[0] = 0;
+  *out = g;
+  return WC_OK;
+}
+
+extern "C" void wc_destroy(wc_grid* g) { delete g; }
+extern "C" int wc_nvar(const wc_grid* g) { return g ? g->nv : 0; }
+extern "C" long wc_ncell(const wc_grid* g) { return g ? g->ncell : 0; }
+
+extern "C" size_t wc_workspace_bytes(const wc_grid* g) {
+  if (!g) return 0;
+  size_t state = (size_t)g->nv * g->ncell * sizeof(double);
+  state = (state + 255) / 256 * 256;
+  return 3 * state + 256;
+}
+
+extern "C" wc_status wc_set_state(wc_grid* g, double* U_dev, void* ws, size_t ws_bytes) {
+  if (!g || !U_dev) return WC_ERR_ARG;
+  if (ws && ws_bytes < wc_workspace_bytes(g)) return fail(g, WC_ERR_ARG, "workspace too small");
+  if (ws && (reinterpret_cast<uintptr_t>(ws) & 255)) return fail(g, WC_ERR_ARG, "workspace not 256-byte aligned");
+  if (reinterpret_cast<uintptr_t>(U_dev) & 7) return fail(g, WC_ERR_ARG, "state not 8-byte aligned");
+  g->U = U_dev;
+  g->ws = (char*)ws;
+  g->ws_bytes = ws_bytes;
+  if (ws) {
+    size_t state = (size_t)g->nv * g->ncell * sizeof(double);
+    state = (state + 255) / 256 * 256;
+    g->B1 = (double*)(g->ws);
+    g->B2 = (double*)(g->ws + state);
+    g->Lacc = (double*)(g->ws + 2 * state);
+    char* tail = g->ws + 3 * state;
+    g->rate = (unsigned long long*)tail;
+    g->dt = (double*)(tail + 8);
+    g->status = (unsigned*)(tail + 16);
+    // the workspace comes uninitialised: clear rate, dt and the status word
+    cudaError_t e = cudaMemset(tail, 0, 256);
+    if (e != cudaSuccess) return cuda_fail(g, e, "workspace clear");
+  } else {
+    g->B1 = g->B2 = g->Lacc = nullptr;
+    g->rate = nullptr;
+    g->dt = nullptr;
+    g->status = nullptr;
+  }
+  return WC_OK;
+}
+
+extern "C" wc_status wc_upload_state(wc_grid* g, const double* U_host, void* stream) {
+  if (!g || !U_host) return WC_ERR_ARG;
+  if (!g->U) return fail(g, WC_ERR_STATE, "no state bound");
+  cudaError_t e = cudaMemcpyAsync(g->U, U_host, (size_t)g->nv * g->ncell * sizeof(double),
+                                  cudaMemcpyHostToDevice, S(stream));
+  return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "upload");
+}
+
+extern "C" wc_status wc_download_state(const wc_grid* g, double* U_host, void* stream) {
+  if (!g || !U_host) return WC_ERR_ARG;
+  if (!g->U) return WC_ERR_STATE;
+  cudaError_t e = cudaMemcpyAsync(U_host, g->U, (size_t)g->nv * g->ncell * sizeof(double),
+                                  cudaMemcpyDeviceToHost, S(stream));
+  return e == cudaSuccess ? WC_OK : WC_ERR_CUDA;
+}
+
+extern "C" wc_status wc_prim_to_cons(const wc_grid* gc, const double* V, double* U, void* stream) {
+  wc_grid* g = const_cast<wc_grid*>(gc);
+  if (!g || !V || !U) return WC_ERR_ARG;
+  int blocks = grid_blocks(g->ncell, 256);
+  WC_DISPATCH(g->d.nphase, g->d.dim,
+              (k_prim_to_cons<N_, D_><<<blocks, 256, 0, S(stream)>>>(V, U, g->ncell, g->mat)));
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "prim_to_cons");
+}
+
+extern "C" wc_status wc_cons_to_prim(const wc_grid* gc, const double* U, double* V, void* stream) {
+  wc_grid* g = const_cast<wc_grid*>(gc);
+  if (!g || !V || !U) return WC_ERR_ARG;
+  int blocks = grid_blocks(g->ncell, 256);
+  WC_DISPATCH(g->d.nphase, g->d.dim,
+              (k_cons_to_prim<N_, D_><<<blocks, 256, 0, S(stream)>>>(U, V, g->ncell, g->mat)));
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "cons_to_prim");
+}
+
+// ------------------------------------------------------------------ sweeps
+static int auto_seg(const wc_grid* g, int dir) {
+  if (g->d.seg > 0) return g->d.seg;
+  long npencil = g->ncell / g->d.n[dir];
+  // about one full wave of resident threads (148 SMs x 256 threads)
+  long want = 148L * 256;
+  long seg = g->ncell / (want > 0 ? want : 1);
+  int s = 8;
+  while (s < seg && s < 64) s *= 2;
+  (void)npencil;
+  return s;
+}
+
+static int sweep_block(const wc_grid* g) { return g->d.block > 0 ? g->d.block : 64; }
+
+static SweepArgs make_args(const wc_grid* g, int dir, const double* U, double* L) {
+  SweepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.U = U;
+  a.L = L;
+  a.ncell = g->ncell;
+  a.nx = g->d.n[0];
+  a.ny = g->d.n[1];
+  a.nz = g->d.n[2];
+  a.dir = dir;
+  a.n = g->d.n[dir];
+  a.stride = dir == 0 ? 1 : (dir == 1 ? (long)a.nx : (long)a.nx * a.ny);
+  a.npencil = g->ncell / a.n;
+  a.seg = auto_seg(g, dir);
+  a.nseg = (a.n + a.seg - 1) / a.seg;
+  a.inv_dx = 1.0 / g->d.dx[dir];
+  a.bclo = g->d.bc[2 * dir];
+  a.bchi = g->d.bc[2 * dir + 1];
+  a.hllc = g->d.flux == WC_FLUX_HLLC;
+  a.energy_limiter = g->d.energy_limiter;
+  a.status = g->status;
+  return a;
+}
+
+static cudaError_t launch(const wc_grid* g, const SweepArgs& a, cudaStream_t st) {
+  if (g->d.precision == WC_PREC_MIXED)
+    return launch_sweep_mixed(g->d.nphase, g->d.dim, a, g->mat, sweep_block(g), st);
+  return launch_sweep_fp64(g->d.nphase, g->d.dim, a, g->mat, sweep_block(g), st);
+}
+
+extern "C" wc_status wc_rhs(wc_grid* g, const double* U, double* L, void* stream) {
+  if (!g || !U || !L) return WC_ERR_ARG;
+  if (!g->status) return fail(g, WC_ERR_STATE, "wc_rhs needs a bound workspace (status word)");
+  for (int dir = 0; dir < g->d.dim; dir++) {
+    SweepArgs a = make_args(g, dir, U, L);
+    a.mode = dir == 0 ? 0 : 1;
+    cudaError_t e = launch(g, a, S(stream));
+    if (e != cudaSuccess) return cuda_fail(g, e, "sweep");
+  }
+  return WC_OK;
+}
+
+static wc_status launch_rate(wc_grid* g, const double* U, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(g->rate, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "memset");
+  int blocks = grid_blocks(g->ncell, 256);
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  double i0 = 1.0 / g->d.dx[0];
+  double i1 = g->d.dim > 1 ? 1.0 / g->d.dx[1] : 0.0;
+  double i2 = g->d.dim > 2 ? 1.0 / g->d.dx[2] : 0.0;
+  WC_DISPATCH(g->d.nphase, g->d.dim,
+              (k_max_rate<N_, D_><<<blocks, 256, 0, st>>>(U, g->ncell, g->mat, i0, i1, i2,
+                                                          g->rate, g->status)));
+  e = cudaGetLastError();
+  return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "max_rate");
+}
+
+extern "C" wc_status wc_compute_dt(wc_grid* g, double cfl, double* dt_dev, void* stream) {
+  if (!g || !dt_dev || !(cfl > 0.0)) return WC_ERR_ARG;
+  if (!g->U || !g->ws) return fail(g, WC_ERR_STATE, "state/workspace not bound");
+  wc_status s = launch_rate(g, g->U, S(stream));
+  if (s) return s;
+  k_dt_from_rate<<<1, 32, 0, S(stream)>>>((const double*)g->rate, cfl, dt_dev);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "dt");
+}
+
+// One SSP-RK3 stage: dst = r0 U0 + r1 src + r2 dt L(src).
+static wc_status stage(wc_grid* g, const double* src, double* dst, double r0, double r1,
+                       double r2, double cfl, double dt_fixed, cudaStream_t st) {
+  int D = g->d.dim;
+  for (int dir = 0; dir < D; dir++) {
+    SweepArgs a = make_args(g, dir, src, g->Lacc);
+    a.U0 = g->U;
+    a.Uout = dst;
+    a.rate = (const double*)g->rate;
+    a.cfl = cfl;
+    a.dt_fixed = dt_fixed;
+    a.rk0 = r0;
+    a.rk1 = r1;
+    a.rk2 = r2;
+    if (D == 1) a.mode = 3;
+    else a.mode = dir == 0 ? 0 : (dir < D - 1 ? 1 : 2);
+    cudaError_t e = launch(g, a, st);
+    if (e != cudaSuccess) return cuda_fail(g, e, "sweep");
+  }
+  return WC_OK;
+}
+
+extern "C" wc_status wc_rk_step(wc_grid* g, double cfl, double dt_fixed, int nsteps,
+                                double* dt_host, void* stream) {
+  if (!g || nsteps < 0) return WC_ERR_ARG;
+  if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return fail(g, WC_ERR_ARG, "need cfl > 0 or dt > 0");
+  if (!g->U || !g->ws) return fail(g, WC_ERR_STATE, "state/workspace not bound");
+  cudaStream_t st = S(stream);
+  for (int s = 0; s < nsteps; s++) {
+    if (!(dt_fixed > 0.0)) {
+      wc_status r = launch_rate(g, g->U, st);
+      if (r) return r;
+    }
+    wc_status r;
+    if ((r = stage(g, g->U, g->B1, 0.0, 1.0, 1.0, cfl, dt_fixed, st))) return r;
+    if ((r = stage(g, g->B1, g->B2, 0.75, 0.25, 0.25, cfl, dt_fixed, st))) return r;
+    if ((r = stage(g, g->B2, g->U, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, cfl, dt_fixed, st))) return r;
+  }
+  if (dt_host) {
+    if (dt_fixed > 0.0) {
+      *dt_host = dt_fixed;
+    } else {
+      double rate = 0.0;
+      cudaError_t e = cudaMemcpyAsync(&rate, g->rate, sizeof(double), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(g, e, "dt readback");
+      *dt_host = cfl / rate;
+    }
+  }
+  return WC_OK;
+}
+
+extern "C" wc_status wc_limit(const wc_grid* gc, int dir, long ncell, const double* Ubar,
+                              const double* VL, const double* VR, double* UL, double* UR,
+                              double* theta, void* stream) {
+  wc_grid* g = const_cast<wc_grid*>(gc);
+  if (!g || !Ubar || !VL || !VR || !UL || !UR || ncell < 0) return WC_ERR_ARG;
+  if (dir < 0 || dir >= g->d.dim) return fail(g, WC_ERR_ARG, "bad direction");
+  if (ncell == 0) return WC_OK;
+  int blocks = grid_blocks(ncell, 128);
+  WC_DISPATCH(g->d.nphase, g->d.dim,
+              (k_limit<N_, D_><<<blocks, 128, 0, S(stream)>>>(Ubar, VL, VR, UL, UR, theta, ncell,
+                                                              g->mat, g->d.energy_limiter)));
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "limit");
+}
+
+extern "C" wc_status wc_sync_status(wc_grid* g, void* stream) {
+  if (!g) return WC_ERR_ARG;
+  if (!g->status) return WC_ERR_STATE;
+  unsigned st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, g->status, sizeof(unsigned), cudaMemcpyDeviceToHost, S(stream));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S(stream));
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->status, 0, sizeof(unsigned), S(stream));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S(stream));
+  if (e != cudaSuccess) return cuda_fail(g, e, "status");
+  if (st & ST_INADMISSIBLE) return fail(g, WC_ERR_INADMISSIBLE, "inadmissible state met by a kernel");
+  if (st & ST_NAN) return fail(g, WC_ERR_NAN, "non-finite value produced by a kernel");
+  return WC_OK;
+}
+
+extern "C" void wc_last_error(const wc_grid* g, char* buf, size_t n) {
+  if (!buf || n == 0) return;
+  snprintf(buf, n, "%s", g ? g->err : "null grid");
+}
+
+// ------------------------------------------------------------------ FP64 peak probe
+__global__ void k_fp64_peak(int iters, double* sink) {
+  double x0 = threadIdx.x * 1e-3, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
+  double x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+  const double a = 0.999999, b = 1e-7;
+  for (int i = 0; i < iters; i++) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  double s = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+  if (s == 12345.678) sink[0] = s;  // keeps the loop alive
+}
+
+extern "C" wc_status wc_fp64_peak_kernel(int blocks, int threads, int iters, double* sink,
+                                         double* flops, void* stream) {
+  if (blocks < 1 || threads < 32 || threads > 1024 || iters < 1 || !sink) return WC_ERR_ARG;
+  k_fp64_peak<<<blocks, threads, 0, S(stream)>>>(iters, sink);
+  if (flops) *flops = 2.0 * 8.0 * (double)iters * blocks * threads;
+  return cudaGetLastError() == cudaSuccess ? WC_OK : WC_ERR_CUDA;
+}

@@ -1,0 +1,607 @@
+// wenoc_device.cuh -- device building blocks of the WENO-C operator for
+// sm_103a: equation of state (Eq. 26-27), WENO5 smoothness indicators and
+// candidates, the relative-smoothness weights (Eq. 15), the coupled
+// reconstruction (Eq. 16), the limiter chain (Eq. 17-21) and the HLL/HLLC
+// fluxes with the consistent face velocity.
+//
+// Precision is a template choice: T is the type of the reconstruction
+// (smoothness indicators, weights, candidates) and TF the type of the flux
+// components.  The limiter factors, the unity-sum normalisation, the
+// primitive-to-conservative map, the pressure recovery and every
+// accumulation are FP64 in all modes.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wc {
+
+constexpr int MAXP = 8;
+
+// Status bits set by kernels (read by wc_sync_status).
+enum : unsigned { ST_INADMISSIBLE = 1u, ST_NAN = 2u };
+
+struct Mat {
+  int N;
+  int hasD;                 // any D_p != 0
+  double A[MAXP];           // 1/(gamma-1)
+  double B[MAXP];           // gamma Pinf/(gamma-1)
+  double D[MAXP];
+  double pinf[MAXP];
+  double Ag[MAXP];          // A gamma (mixture sound speed, Eq. 2, K = 0)
+  double Cmin[MAXP];        // A Pmin + B: alpha_p rho_p e_p(Pmin_p, rho_p) per alpha_p
+  double Apmin[MAXP];       // A Pmin
+};
+
+template <int N, int D>
+struct Idx {
+  static constexpr int NV = 2 * N + D + 1;
+  static constexpr int E = N + D;
+  __host__ __device__ static constexpr int M(int p) { return p; }
+  __host__ __device__ static constexpr int U(int j) { return N + j; }
+  __host__ __device__ static constexpr int A(int p) { return N + D + 1 + p; }
+};
+
+// ------------------------------------------------------------------ EOS
+// Mixture rules and Eq. 27.  V gets u and P; masses and fractions are copies.
+template <int N, int D>
+__device__ __forceinline__ void cons_to_prim(const Mat& m, const double* U, double* V) {
+  using I = Idx<N, D>;
+  double rho = U[0];
+#pragma unroll
+  for (int p = 1; p < N; p++) rho += U[p];
+  double inv = 1.0 / rho;
+  double mm = 0.0;
+#pragma unroll
+  for (int j = 0; j < D; j++) mm = fma(U[I::U(j)], U[I::U(j)], mm);
+  double sA = 0.0, sB = 0.0, sD = 0.0;
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    sA = fma(m.A[p], U[I::A(p)], sA);
+    sB = fma(m.B[p], U[I::A(p)], sB);
+    if (m.hasD) sD = fma(m.D[p], U[p], sD);
+  }
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    V[p] = U[p];
+    V[I::A(p)] = U[I::A(p)];
+  }
+#pragma unroll
+  for (int j = 0; j < D; j++) V[I::U(j)] = U[I::U(j)] * inv;
+  V[I::E] = (U[I::E] - 0.5 * mm * inv - sB - sD) / sA;
+}
+
+// psi_{V->U} for one face: rho, rho u, rho E (Eq. 26).  Masses/fractions copied.
+template <int N, int D>
+__device__ __forceinline__ void prim_to_cons(const Mat& m, const double* V, double* U) {
+  using I = Idx<N, D>;
+  double rho = V[0];
+#pragma unroll
+  for (int p = 1; p < N; p++) rho += V[p];
+  double uu = 0.0;
+#pragma unroll
+  for (int j = 0; j < D; j++) uu = fma(V[I::U(j)], V[I::U(j)], uu);
+  double P = V[I::E];
+  double e = 0.0;
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    e = fma(V[I::A(p)], fma(m.A[p], P, m.B[p]), e);
+    if (m.hasD) e = fma(m.D[p], V[p], e);
+  }
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    U[p] = V[p];
+    U[I::A(p)] = V[I::A(p)];
+  }
+#pragma unroll
+  for (int j = 0; j < D; j++) U[I::U(j)] = rho * V[I::U(j)];
+  U[I::E] = fma(0.5 * rho, uu, e);
+}
+
+// psi of Eq. 9 for a state given by its primitive values: with rho E from
+// Eq. 26 the kinetic and D terms cancel and psi = sum_p alpha_p A_p (P - Pmin_p).
+template <int N, int D>
+__device__ __forceinline__ double psi_prim(const Mat& m, const double* alpha, double P) {
+  double s = 0.0;
+#pragma unroll
+  for (int p = 0; p < N; p++) s = fma(alpha[p], fma(m.A[p], P, -m.Apmin[p]), s);
+  return s;
+}
+
+// psi of Eq. 9 from a conservative vector (used for the interior value U^C).
+template <int N, int D>
+__device__ __forceinline__ double psi_cons(const Mat& m, const double* U) {
+  using I = Idx<N, D>;
+  double rho = U[0];
+#pragma unroll
+  for (int p = 1; p < N; p++) rho += U[p];
+  double mm = 0.0;
+#pragma unroll
+  for (int j = 0; j < D; j++) mm = fma(U[I::U(j)], U[I::U(j)], mm);
+  double s = 0.0;
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    s = fma(U[I::A(p)], m.Cmin[p], s);
+    if (m.hasD) s = fma(m.D[p], U[p], s);
+  }
+  double ke = rho > 0.0 ? 0.5 * mm / rho : 0.0;
+  return U[I::E] - ke - s;
+}
+
+// ------------------------------------------------------------------ WENO5
+// The stencil f_{i-2..i+2} enters as differences from the centre value,
+// da = f_{i-2} - f_i, db = f_{i-1} - f_i, dd = f_{i+1} - f_i, de = f_{i+2} - f_i,
+// so a constant stencil reconstructs to f_i exactly in any precision.
+template <typename T>
+struct Stencil {
+  T c, da, db, dd, de;
+};
+template <typename T>
+__device__ __forceinline__ Stencil<T> stencil(T a, T b, T c, T d, T e) {
+  return Stencil<T>{c, a - c, b - c, d - c, e - c};
+}
+
+// Smoothness indicators of the three sub-stencils (Jiang-Shu), scaled by 12
+// (13 t1^2 + 3 t2^2); Eq. 15 uses only their ratios.  The mirrored stencil of
+// the right face has the same three values in reverse order.
+template <typename T>
+__device__ __forceinline__ void smoothness(const Stencil<T>& s, T& b0, T& b1, T& b2) {
+  T t1 = s.da - T(2) * s.db, t2 = s.da - T(4) * s.db;
+  b0 = T(13) * t1 * t1 + T(3) * t2 * t2;
+  t1 = s.db + s.dd;
+  t2 = s.db - s.dd;
+  b1 = T(13) * t1 * t1 + T(3) * t2 * t2;
+  t1 = s.de - T(2) * s.dd;
+  t2 = s.de - T(4) * s.dd;
+  b2 = T(13) * t1 * t1 + T(3) * t2 * t2;
+}
+
+template <typename T> __device__ __forceinline__ T tiny_norm();
+template <> __device__ __forceinline__ double tiny_norm<double>() { return 1e-290; }
+template <> __device__ __forceinline__ float tiny_norm<float>() { return 1e-30f; }
+
+// Eq. 15 with ideal weights (dA, dB, dC) = (0.1, 0.6, 0.3) for the
+// indicators (bA, bB, bC) in that order.
+//  * all indicators positive and in range: Eq. 15 divided through by IS_s^2
+//    is omega_s = (d_s prod_{k!=s} IS_k^2) / sum_t (d_t prod_{k!=t} IS_k^2),
+//    evaluated on the indicators scaled by 1/max;
+//  * some indicators zero: the zero stencils share the weight in proportion
+//    to d (the others have infinite ratios, so omega = 0);
+//  * indicators or products outside the normal range of T: the ratio form of
+//    Eq. 15 itself.
+template <typename T>
+__device__ __forceinline__ void wenow_weights(T bA, T bB, T bC, T& wA, T& wB, T& wC) {
+  const T dA = T(0.1), dB = T(0.6), dC = T(0.3);
+  if (bA > T(0) && bB > T(0) && bC > T(0)) {
+    T mx = bA > bB ? bA : bB;
+    mx = mx > bC ? mx : bC;
+    if (mx >= tiny_norm<T>()) {
+      T r = T(1) / mx;
+      T xA = bA * r, xB = bB * r, xC = bC * r;
+      T sA = xA * xA, sB = xB * xB, sC = xC * xC;
+      T aA = dA * sB * sC, aB = dB * sA * sC, aC = dC * sA * sB;
+      T sum = aA + aB + aC;
+      if (sum >= tiny_norm<T>()) {
+        T inv = T(1) / sum;
+        wA = aA * inv;
+        wB = aB * inv;
+        wC = aC * inv;
+        return;
+      }
+    }
+    T rAB = bA / bB, rAC = bA / bC, rBC = bB / bC;
+    wA = dA / (dA + dB * rAB * rAB + dC * rAC * rAC);
+    T rBA = bB / bA;
+    wB = dB / (dB + dA * rBA * rBA + dC * rBC * rBC);
+    T rCA = bC / bA, rCB = bC / bB;
+    wC = dC / (dC + dA * rCA * rCA + dB * rCB * rCB);
+    return;
+  }
+  T zA = bA == T(0) ? dA : T(0);
+  T zB = bB == T(0) ? dB : T(0);
+  T zC = bC == T(0) ? dC : T(0);
+  T inv = T(1) / (zA + zB + zC);
+  wA = zA * inv;
+  wB = zB * inv;
+  wC = zC * inv;
+}
+
+template <typename T>
+struct W6 {
+  T L0, L1, L2, R0, R1, R2;
+};
+
+// Relative-smoothness weights of both faces of cell i.
+template <typename T>
+__device__ __forceinline__ W6<T> weights_of(const Stencil<T>& s) {
+  T b0, b1, b2;
+  smoothness(s, b0, b1, b2);
+  W6<T> w;
+  wenow_weights(b0, b1, b2, w.L0, w.L1, w.L2);
+  // mirrored sub-stencils: {i..i+2} (ideal 0.1), {i-1..i+1}, {i-2..i}
+  wenow_weights(b2, b1, b0, w.R0, w.R1, w.R2);
+  return w;
+}
+
+// Eq. 10 at x_{i+1/2} (fL) and x_{i-1/2} (fR): the candidates' values minus
+// f_i, times 6, are 2da-7db, 2dd-db, 5dd-de (left face) and the mirror images.
+template <typename T>
+__device__ __forceinline__ void reconstruct(const W6<T>& w, const Stencil<T>& s, T& fL, T& fR) {
+  const T sixth = T(1) / T(6);
+  T qL0 = T(2) * s.da - T(7) * s.db, qL1 = T(2) * s.dd - s.db, qL2 = T(5) * s.dd - s.de;
+  T qR0 = T(2) * s.de - T(7) * s.dd, qR1 = T(2) * s.db - s.dd, qR2 = T(5) * s.db - s.da;
+  fL = s.c + (w.L0 * qL0 + w.L1 * qL1 + w.L2 * qL2) * sixth;
+  fR = s.c + (w.R0 * qR0 + w.R1 * qR1 + w.R2 * qR2) * sixth;
+}
+
+// ------------------------------------------------------------------ limiters
+// Eq. 18 (f_min = 0) with f^C from Eq. 6 inverted (N_quad = 4, w = 1/12):
+// theta = 1 when min(f^C, f^L, f^R) >= 0, else fbar / (fbar - min), clamped
+// to [0, 1].
+__device__ __forceinline__ double theta_pos(double fb, double fL, double fR) {
+  double fC = (fb - (fL + fR) * (1.0 / 12.0)) * 1.2;
+  double m = fmin(fC, fmin(fL, fR));
+  if (m >= 0.0) return 1.0;
+  if (fb <= 0.0) return 0.0;
+  return fmin(fb / (fb - m), 1.0);
+}
+
+__device__ __forceinline__ double theta_lower(double fb, double fC, double fL, double fR) {
+  double m = fmin(fC, fmin(fL, fR));
+  if (m >= 0.0) return 1.0;
+  if (fb <= 0.0) return 0.0;
+  return fmin(fb / (fb - m), 1.0);
+}
+
+// A face state handed to the Riemann solver: conservative U and the primitive
+// velocity and pressure of the same state.
+template <int N, int D>
+struct Face {
+  double U[Idx<N, D>::NV];
+  double u[D];
+  double P;
+};
+
+// The limiter chain for one cell: Ub cell average (FP64, conservative), Pb
+// its pressure; mL/aL (mR/aR) reconstructed masses and fractions at
+// x_{i+1/2} (x_{i-1/2}); uL, PL (uR, PR) reconstructed velocity and pressure.
+// Produces the two limited face states.  th (optional) receives
+// (min_p theta_p of Eq. 17, theta_i of Eq. 20, theta^(psi) of Eq. 21).
+template <int N, int D>
+__device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, double Pb,
+                                            double* mL, double* aL, double* mR, double* aR,
+                                            const double* uL, double PL, const double* uR,
+                                            double PR, int energy_limiter, Face<N, D>& FL,
+                                            Face<N, D>& FR, double* th) {
+  using I = Idx<N, D>;
+  double th17 = 1.0;
+  // Eq. 17-18: common theta_p for (alpha rho)_p and alpha_p
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    double mb = Ub[p], ab = Ub[I::A(p)];
+    double tp = fmin(theta_pos(mb, mL[p], mR[p]), theta_pos(ab, aL[p], aR[p]));
+    if (tp < 1.0) {
+      mL[p] = fma(tp, mL[p] - mb, mb);
+      mR[p] = fma(tp, mR[p] - mb, mb);
+      aL[p] = fma(tp, aL[p] - ab, ab);
+      aR[p] = fma(tp, aR[p] - ab, ab);
+      th17 = fmin(th17, tp);
+    }
+  }
+  // Eq. 19: unity sum on each face
+  double SL = aL[0], SR = aR[0];
+#pragma unroll
+  for (int p = 1; p < N; p++) {
+    SL += aL[p];
+    SR += aR[p];
+  }
+  if (!(SL > 0.0) || !(SR > 0.0)) {
+    // every fraction of a face limited to zero: first order for the cell
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      mL[p] = mR[p] = Ub[p];
+      aL[p] = aR[p] = Ub[I::A(p)];
+    }
+    th17 = 0.0;
+  } else {
+    if (SL != 1.0) {
+      double r = 1.0 / SL;
+#pragma unroll
+      for (int p = 0; p < N; p++) {
+        mL[p] *= r;
+        aL[p] *= r;
+      }
+    }
+    if (SR != 1.0) {
+      double r = 1.0 / SR;
+#pragma unroll
+      for (int p = 0; p < N; p++) {
+        mR[p] *= r;
+        aR[p] *= r;
+      }
+    }
+  }
+  // Eq. 20: theta_i = min_p theta_p recomputed on the normalised faces
+  double thi = 1.0;
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    double tp = fmin(theta_pos(Ub[p], mL[p], mR[p]), theta_pos(Ub[I::A(p)], aL[p], aR[p]));
+    thi = fmin(thi, tp);
+  }
+  if (thi < 1.0) {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      double mb = Ub[p], ab = Ub[I::A(p)];
+      mL[p] = fma(thi, mL[p] - mb, mb);
+      mR[p] = fma(thi, mR[p] - mb, mb);
+      aL[p] = fma(thi, aL[p] - ab, ab);
+      aR[p] = fma(thi, aR[p] - ab, ab);
+    }
+  }
+  // V -> U at both faces
+  double VL[I::NV], VR[I::NV];
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    VL[p] = mL[p];
+    VR[p] = mR[p];
+    VL[I::A(p)] = aL[p];
+    VR[I::A(p)] = aR[p];
+  }
+#pragma unroll
+  for (int j = 0; j < D; j++) {
+    VL[I::U(j)] = uL[j];
+    VR[I::U(j)] = uR[j];
+  }
+  VL[I::E] = PL;
+  VR[I::E] = PR;
+  prim_to_cons<N, D>(m, VL, FL.U);
+  prim_to_cons<N, D>(m, VR, FR.U);
+#pragma unroll
+  for (int j = 0; j < D; j++) {
+    FL.u[j] = uL[j];
+    FR.u[j] = uR[j];
+  }
+  FL.P = PL;
+  FR.P = PR;
+  double thpsi = 1.0;
+  if (energy_limiter) {
+    // Eq. 21: theta^(psi) from psi at the average, both faces and U^C
+    double UC[I::NV];
+#pragma unroll
+    for (int v = 0; v < I::NV; v++) UC[v] = (Ub[v] - (FL.U[v] + FR.U[v]) * (1.0 / 12.0)) * 1.2;
+    double pb = psi_prim<N, D>(m, Ub + I::A(0), Pb);
+    double pL = psi_prim<N, D>(m, aL, PL);
+    double pR = psi_prim<N, D>(m, aR, PR);
+    double pC = psi_cons<N, D>(m, UC);
+    thpsi = theta_lower(pb, pC, pL, pR);
+    if (thpsi < 1.0) {
+#pragma unroll
+      for (int v = 0; v < I::NV; v++) {
+        FL.U[v] = fma(thpsi, FL.U[v] - Ub[v], Ub[v]);
+        FR.U[v] = fma(thpsi, FR.U[v] - Ub[v], Ub[v]);
+      }
+      double W[I::NV];
+      cons_to_prim<N, D>(m, FL.U, W);
+#pragma unroll
+      for (int j = 0; j < D; j++) FL.u[j] = W[I::U(j)];
+      FL.P = W[I::E];
+      cons_to_prim<N, D>(m, FR.U, W);
+#pragma unroll
+      for (int j = 0; j < D; j++) FR.u[j] = W[I::U(j)];
+      FR.P = W[I::E];
+    }
+  }
+  if (th) {
+    th[0] = th17;
+    th[1] = thi;
+    th[2] = thpsi;
+  }
+}
+
+// ------------------------------------------------------------------ fluxes
+// Mixture sound speed of Eq. 2 with K_p = 0: rho c^2 = sum A g alpha (P+Pinf)
+// / sum A alpha.
+template <int N, int D, typename TF>
+__device__ __forceinline__ TF sound_speed(const Mat& m, const double* U, TF rho, TF P) {
+  using I = Idx<N, D>;
+  TF num = TF(0), den = TF(0);
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    TF a = TF(U[I::A(p)]);
+    num = num + TF(m.Ag[p]) * a * (P + TF(m.pinf[p]));
+    den = den + TF(m.A[p]) * a;
+  }
+  return sqrt(num / (den * rho));
+}
+
+// HLL or HLLC flux across the face between the left state L (from cell i) and
+// the right state R (from cell i+1), direction dir, and u_hat, the flux of a
+// volume fraction equal to one on both sides (Sec. 2.2.1).
+//
+// Both solvers are linear in (U, F) component by component for given wave
+// speeds.  The flux is assembled from that linearity so that it keeps
+// equilibrium and consistency in any precision TF:
+//  * fraction and mass fluxes and u_hat are FP64 (their sums over the phases
+//    match u_hat and the density flux to FP64 rounding);
+//  * with ub = (u_L + u_R)/2 and Pb = (P_L + P_R)/2, rho u_j = ub_j rho +
+//    rho (u_j - ub_j) and E_r = rho E - sum B alpha - sum D (alpha rho)
+//    = Pb sum A alpha + |ub|^2 rho / 2 + Et, so
+//      F^{rho u_j} = ub_j F^rho + F[rho (u_j - ub_j)] + delta_jn F[P],
+//      F^{rho E}   = sum_p (B_p + Pb A_p) F^{alpha_p} + sum_p D_p F^{(alpha rho)_p}
+//                    + |ub|^2 F^rho / 2 + F[Et];
+//    the bracketed remainders vanish exactly for uniform u and P, so an
+//    isolated interface keeps u and P uniform whatever TF is;
+//  * wave speeds, the HLLC contact speed and the remainders are in TF.
+// HLL is written as F_L + k ((F_L - F_R) + s_R (U_R - U_L)), k = s_L/(s_R - s_L),
+// which returns F_L exactly for equal states.
+template <int N, int D, typename TF>
+__device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const Face<N, D>& L,
+                                        const Face<N, D>& R, double* F, double& uhat) {
+  using I = Idx<N, D>;
+  double rLd = L.U[0], rRd = R.U[0];
+#pragma unroll
+  for (int p = 1; p < N; p++) {
+    rLd += L.U[p];
+    rRd += R.U[p];
+  }
+  double uLd = L.u[0], uRd = R.u[0];
+#pragma unroll
+  for (int j = 1; j < D; j++)
+    if (j == dir) {
+      uLd = L.u[j];
+      uRd = R.u[j];
+    }
+  double ub[D];
+#pragma unroll
+  for (int j = 0; j < D; j++) ub[j] = 0.5 * (L.u[j] + R.u[j]);
+  const double dPd = L.P - R.P;  // exact when P_L, P_R are close
+  const TF rL = TF(rLd), rR = TF(rRd), uL = TF(uLd), uR = TF(uRd);
+  const TF PL = TF(L.P), PR = TF(R.P);
+  const TF cL = sound_speed<N, D, TF>(m, L.U, rL, PL);
+  const TF cR = sound_speed<N, D, TF>(m, R.U, rR, PR);
+  const TF sL = fmin(uL - cL, uR - cR);
+  const TF sR = fmax(uL + cL, uR + cR);
+  // remainder energy Et_K = sum A alpha_K (P_K - Pb) + rho_K (|u_K|^2 - |ub|^2)/2
+  TF AaL = TF(0), AaR = TF(0);
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    AaL += TF(m.A[p]) * TF(L.U[I::A(p)]);
+    AaR += TF(m.A[p]) * TF(R.U[I::A(p)]);
+  }
+  TF wL[D], wR[D];
+  TF kinL = TF(0), kinR = TF(0);
+#pragma unroll
+  for (int j = 0; j < D; j++) {
+    wL[j] = TF(L.u[j] - ub[j]);
+    wR[j] = TF(R.u[j] - ub[j]);
+    kinL += wL[j] * TF(L.u[j] + ub[j]);
+    kinR += wR[j] * TF(R.u[j] + ub[j]);
+  }
+  const TF halfdP = TF(0.5 * dPd);
+  const TF EtL = halfdP * AaL + TF(0.5) * rL * kinL;
+  const TF EtR = -halfdP * AaR + TF(0.5) * rR * kinR;
+
+  double Frho = 0.0;
+  if (!hllc) {
+    // ---------------- HLL
+    double kd, sRd;
+    TF k;
+    if (sL >= TF(0)) {
+      k = TF(0);
+    } else if (sR <= TF(0)) {
+      k = TF(-1);  // F_L + (-1)((F_L - F_R) + s_R (U_R - U_L)) with s_R = 0
+    } else {
+      k = sL / (sR - sL);
+    }
+    const TF sRu = (sR <= TF(0)) ? TF(0) : sR;
+    kd = double(k);
+    sRd = double(sRu);
+    uhat = uLd + kd * (uLd - uRd);
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      double aL = L.U[I::A(p)], aR = R.U[I::A(p)];
+      double fl = aL * uLd, fr = aR * uRd;
+      F[I::A(p)] = fl + kd * ((fl - fr) + sRd * (aR - aL));
+      double mL = L.U[p], mR = R.U[p];
+      fl = mL * uLd;
+      fr = mR * uRd;
+      double fm = fl + kd * ((fl - fr) + sRd * (mR - mL));
+      F[p] = fm;
+      Frho += fm;
+    }
+    // momentum remainders and pressure part
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+      TF qL = rL * wL[j], qR = rR * wR[j];
+      TF fl = qL * uL, fr = qR * uR;
+      TF fw = fl + k * ((fl - fr) + sRu * (qR - qL));
+      double f = ub[j] * Frho + double(fw);
+      if (j == dir) f += L.P + kd * dPd;
+      F[I::U(j)] = f;
+    }
+    // energy remainder
+    TF gl = uL * (EtL + PL), gr = uR * (EtR + PR);
+    TF g = gl + k * ((gl - gr) + sRu * (EtR - EtL));
+    double fe = double(g);
+    double ub2 = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; j++) ub2 = fma(ub[j], ub[j], ub2);
+    const double Pb = L.P - 0.5 * dPd;
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      fe = fma(fma(m.A[p], Pb, m.B[p]), F[I::A(p)], fe);
+      if (m.hasD) fe = fma(m.D[p], F[p], fe);
+    }
+    F[I::E] = fma(0.5 * ub2, Frho, fe);
+    return;
+  }
+  // ---------------- HLLC
+  double ubn = ub[0];
+#pragma unroll
+  for (int j = 1; j < D; j++)
+    if (j == dir) ubn = ub[j];
+  bool left;
+  TF sK, chi, sS;
+  double sSd;  // contact speed in FP64 (ub_n + correction) for the momentum flux
+  if (sL >= TF(0) || sR <= TF(0)) {
+    left = sL >= TF(0);
+    sK = TF(0);
+    chi = TF(1);
+    sS = left ? uL : uR;
+    sSd = left ? uLd : uRd;
+  } else {
+    // contact speed relative to ub_n (exact for uniform u and P)
+    TF num = TF(-dPd) + rL * TF(uLd - ubn) * (sL - uL) - rR * TF(uRd - ubn) * (sR - uR);
+    TF den = rL * (sL - uL) - rR * (sR - uR);
+    TF rel = num / den;
+    sS = TF(ubn) + rel;
+    sSd = ubn + double(rel);
+    left = sS >= TF(0);
+    sK = left ? sL : sR;
+    TF uK = left ? uL : uR;
+    // u_K - S* = (u_K - ub_n) - rel
+    TF uKmS = TF((left ? uLd : uRd) - ubn) - rel;
+    chi = (sK - uK) / (sK - uK + uKmS);
+  }
+  const TF uK = left ? uL : uR, rK = left ? rL : rR, PK = left ? PL : PR;
+  const TF EtK = left ? EtL : EtR;
+  const double uKd = left ? uLd : uRd;
+  // u_hat = u_K + s_K (chi - 1)
+  uhat = uKd + double(sK * (chi - TF(1)));
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    double aK = left ? L.U[I::A(p)] : R.U[I::A(p)];
+    double mK = left ? L.U[p] : R.U[p];
+    F[I::A(p)] = aK * uhat;
+    F[p] = mK * uhat;
+    Frho += F[p];
+  }
+  const TF uKmS = uK - sS;
+#pragma unroll
+  for (int j = 0; j < D; j++) {
+    if (j == dir) {
+      // S* F^rho + P_K + rho_K (u_K - s_K)(u_K - S*)
+      double f = sSd * Frho + (left ? L.P : R.P);
+      f += double(rK * (uK - sK) * uKmS);
+      F[I::U(j)] = f;
+    } else {
+      F[I::U(j)] = (left ? L.u[j] : R.u[j]) * Frho;
+    }
+  }
+  // remainder energy with the HLLC star state
+  TF Es = chi * (EtK + (sS - uK) * (rK * sS + PK / (sK - uK)));
+  if (sK == TF(0)) Es = EtK;
+  TF g = uK * (EtK + PK) + sK * (Es - EtK);
+  double fe = double(g);
+  double ub2 = 0.0;
+#pragma unroll
+  for (int j = 0; j < D; j++) ub2 = fma(ub[j], ub[j], ub2);
+  const double Pb = L.P - 0.5 * dPd;
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    fe = fma(fma(m.A[p], Pb, m.B[p]), F[I::A(p)], fe);
+    if (m.hasD) fe = fma(m.D[p], F[p], fe);
+  }
+  F[I::E] = fma(0.5 * ub2, Frho, fe);
+}
+
+}  // namespace wc

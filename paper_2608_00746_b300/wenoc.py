@@ -1,0 +1,250 @@
+"""Thin Python binding of the C ABI in ``include/wenoc.h``.
+
+Argument marshalling only: every step of the operator runs in the CUDA
+library ``libwenoc.so`` built in-tree for sm_103a.  PyTorch supplies device
+memory (the caller's state and workspace tensors) and the CUDA stream.  There
+is no CPU fallback: importing this module without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwenoc.so")
+
+MAX_PHASE = 8
+BC = {"periodic": 0, "reflective": 1, "outflow": 2}
+FLUX = {"hll": 0, "hllc": 1}
+PREC = {"fp64": 0, "mixed": 1}
+STATUS = {0: "WC_OK", 1: "WC_ERR_ARG", 2: "WC_ERR_CUDA", 3: "WC_ERR_INADMISSIBLE",
+          4: "WC_ERR_NAN", 5: "WC_ERR_UNSUPPORTED", 6: "WC_ERR_STATE"}
+
+
+class WcError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("n", ctypes.c_int * 3),
+        ("dx", ctypes.c_double * 3),
+        ("nphase", ctypes.c_int),
+        ("gamma", ctypes.c_double * MAX_PHASE),
+        ("pinf", ctypes.c_double * MAX_PHASE),
+        ("D", ctypes.c_double * MAX_PHASE),
+        ("pmin", ctypes.c_double * MAX_PHASE),
+        ("flux", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("energy_limiter", ctypes.c_int),
+        ("bc", ctypes.c_int * 6),
+        ("seg", ctypes.c_int),
+        ("block", ctypes.c_int),
+    ]
+
+
+# name -> (restype, argtypes)
+_VP = ctypes.c_void_p
+_SIGS = {
+    "wc_init_grid": (ctypes.c_int, [ctypes.POINTER(GridDesc), ctypes.POINTER(_VP)]),
+    "wc_destroy": (None, [_VP]),
+    "wc_nvar": (ctypes.c_int, [_VP]),
+    "wc_ncell": (ctypes.c_long, [_VP]),
+    "wc_workspace_bytes": (ctypes.c_size_t, [_VP]),
+    "wc_set_state": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_size_t]),
+    "wc_upload_state": (ctypes.c_int, [_VP, _VP, _VP]),
+    "wc_download_state": (ctypes.c_int, [_VP, _VP, _VP]),
+    "wc_prim_to_cons": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "wc_cons_to_prim": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "wc_rhs": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "wc_compute_dt": (ctypes.c_int, [_VP, ctypes.c_double, _VP, _VP]),
+    "wc_rk_step": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_double), _VP]),
+    "wc_limit": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_long, _VP, _VP, _VP, _VP, _VP, _VP,
+                                _VP]),
+    "wc_sync_status": (ctypes.c_int, [_VP, _VP]),
+    "wc_last_error": (None, [_VP, ctypes.c_char_p, ctypes.c_size_t]),
+    "wc_fp64_peak_kernel": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
+                                           ctypes.POINTER(ctypes.c_double), _VP]),
+}
+
+_lib = None
+
+
+def lib():
+    """Loads ``libwenoc.so``; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run python -m paper_2608_00746_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def default_pmin(pinf):
+    """Minimum phasic pressures of Eq. 9 when none are given: -(1 - 1e-3) Pinf_p
+    for stiffened phases, 0 for ideal gases."""
+    return [-(1.0 - 1e-3) * p if p > 0 else 0.0 for p in pinf]
+
+
+class Grid:
+    """Handle of one uniform grid with its materials and scheme options."""
+
+    def __init__(self, shape, dx, gamma, pinf, D=None, pmin=None, flux="hll",
+                 bc=("periodic",) * 6, precision="fp64", energy_limiter=True, seg=0, block=0):
+        N = len(gamma)
+        d = GridDesc()
+        d.dim = len(shape)
+        for a in range(3):
+            d.n[a] = int(shape[a]) if a < d.dim else 1
+            d.dx[a] = float(dx[a]) if a < d.dim else 1.0
+        d.nphase = N
+        D = list(D) if D is not None else [0.0] * N
+        pmin = list(pmin) if pmin is not None else default_pmin(pinf)
+        for p in range(N):
+            d.gamma[p], d.pinf[p], d.D[p], d.pmin[p] = gamma[p], pinf[p], D[p], pmin[p]
+        d.flux = FLUX[flux]
+        d.precision = PREC[precision]
+        d.energy_limiter = int(bool(energy_limiter))
+        for k in range(6):
+            d.bc[k] = BC[bc[k]] if isinstance(bc[k], str) else int(bc[k])
+        d.seg = int(seg)
+        d.block = int(block)
+        self.desc = d
+        self.shape = tuple(shape)
+        h = _VP()
+        self._check(lib().wc_init_grid(ctypes.byref(d), ctypes.byref(h)), None)
+        self.h = h
+        self.nv = lib().wc_nvar(h)
+        self.ncell = lib().wc_ncell(h)
+        self.U = None
+        self.ws = None
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and _lib is not None:
+            _lib.wc_destroy(h)
+            self.h = None
+
+    def _check(self, st, h="self"):
+        if st != 0:
+            msg = ""
+            if h is not None and getattr(self, "h", None) is not None:
+                buf = ctypes.create_string_buffer(256)
+                lib().wc_last_error(self.h, buf, 256)
+                msg = buf.value.decode()
+            raise WcError(st, msg)
+
+    @property
+    def state_shape(self):
+        return (self.nv,) + tuple(reversed(self.shape))
+
+    def workspace_bytes(self):
+        return lib().wc_workspace_bytes(self.h)
+
+    def new_workspace(self, device="cuda"):
+        n = (self.workspace_bytes() + 7) // 8
+        return torch.empty(n, dtype=torch.float64, device=device)
+
+    def bind(self, U, workspace=None):
+        """Binds the device state tensor (advanced in place by rk_step)."""
+        if workspace is None:
+            workspace = self.new_workspace(U.device)
+        self.U, self.ws = U, workspace
+        self._check(lib().wc_set_state(self.h, _ptr(U), _ptr(workspace),
+                                       workspace.numel() * 8))
+        return self
+
+    def prim_to_cons(self, V, U=None, stream=None):
+        U = torch.empty_like(V) if U is None else U
+        self._check(lib().wc_prim_to_cons(self.h, _ptr(V), _ptr(U), _stream(stream)))
+        return U
+
+    def cons_to_prim(self, U, V=None, stream=None):
+        V = torch.empty_like(U) if V is None else V
+        self._check(lib().wc_cons_to_prim(self.h, _ptr(U), _ptr(V), _stream(stream)))
+        return V
+
+    def rhs(self, U, L=None, stream=None):
+        L = torch.empty_like(U) if L is None else L
+        self._check(lib().wc_rhs(self.h, _ptr(U), _ptr(L), _stream(stream)))
+        return L
+
+    def compute_dt(self, cfl, out=None, stream=None):
+        out = torch.empty(1, dtype=torch.float64, device="cuda") if out is None else out
+        self._check(lib().wc_compute_dt(self.h, cfl, _ptr(out), _stream(stream)))
+        return out
+
+    def rk_step(self, cfl=0.0, dt=0.0, nsteps=1, want_dt=False, stream=None):
+        dth = ctypes.c_double(0.0)
+        self._check(lib().wc_rk_step(self.h, float(cfl), float(dt), int(nsteps),
+                                     ctypes.byref(dth) if want_dt else None, _stream(stream)))
+        return dth.value if want_dt else None
+
+    def upload(self, U_host, stream=None):
+        self._check(lib().wc_upload_state(self.h, ctypes.c_void_p(U_host.data_ptr()),
+                                          _stream(stream)))
+
+    def download(self, U_host, stream=None):
+        self._check(lib().wc_download_state(self.h, ctypes.c_void_p(U_host.data_ptr()),
+                                            _stream(stream)))
+
+    def limit(self, direction, Ubar, VL, VR, stream=None, want_theta=True):
+        n = Ubar.shape[1]
+        UL = torch.empty_like(Ubar)
+        UR = torch.empty_like(Ubar)
+        TH = torch.empty((3, n), dtype=torch.float64, device=Ubar.device) if want_theta else None
+        self._check(lib().wc_limit(self.h, direction, n, _ptr(Ubar), _ptr(VL), _ptr(VR),
+                                   _ptr(UL), _ptr(UR), _ptr(TH), _stream(stream)))
+        return UL, UR, TH
+
+    def sync_status(self, stream=None):
+        self._check(lib().wc_sync_status(self.h, _stream(stream)))
+
+
+def fp64_peak(blocks=148 * 8, threads=256, iters=20000, reps=5):
+    """Measured FP64 FMA throughput (flop/s) of this GPU with the library's
+    probe kernel, CUDA events on the current stream, best of ``reps``."""
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    fl = ctypes.c_double(0.0)
+    best = 0.0
+    for r in range(reps + 1):
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        st = lib().wc_fp64_peak_kernel(blocks, threads, iters, _ptr(sink), ctypes.byref(fl),
+                                       _stream(s))
+        e1.record(s)
+        torch.cuda.synchronize()
+        if st != 0:
+            raise WcError(st, "fp64 peak probe")
+        if r > 0:
+            best = max(best, fl.value / (e0.elapsed_time(e1) * 1e-3))
+    return best

@@ -1,0 +1,129 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+FP64 mode tolerance 1e-12 relative:
+ * states after Runge-Kutta steps: max |U - U_or| over the grid relative to
+   the largest |U_or| of the variable's group (each mass, the momentum
+   vector, the energy, each fraction);
+ * dU/dt: the change over one CFL-1 time step, max |L - L_or| / max_rate,
+   relative to the same group scale.  (dU/dt itself is a difference of
+   nearly equal fluxes; transverse momentum derivatives are pure round-off
+   noise in these cases, so a per-variable max-|L| scale is meaningless.)
+The inputs are identical bytes on both sides (the oracle's conservative map
+of the seeded primitive state).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_00746_b300 import inputs
+
+from gpu_util import SMALL_CASES, grids, rel_err_per_var, rhs_err, state_err, to_dev
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.mark.parametrize("name", sorted(SMALL_CASES))
+def test_rhs_parity_fp64(gpu, name):
+    case = SMALL_CASES[name]()
+    go, gg = grids(case)
+    U = oracle.prim_to_cons(go, case.V)
+    L_or = oracle.rhs(go, U)
+    Ud = to_dev(U)
+    gg.bind(Ud)
+    L = gg.rhs(Ud).cpu().numpy()
+    gg.sync_status()
+    err = rhs_err(L, L_or, U, oracle.max_rate(go, U), case.N, case.dim)
+    assert (err <= TOL).all(), (name, err)
+
+
+@pytest.mark.parametrize("flux", ["hll", "hllc"])
+def test_rhs_parity_both_fluxes_3d(gpu, flux):
+    case = SMALL_CASES["spheres_3d_ragged"]()
+    go, gg = grids(case, flux=flux)
+    U = oracle.prim_to_cons(go, case.V)
+    L_or = oracle.rhs(go, U)
+    Ud = to_dev(U)
+    gg.bind(Ud)
+    err = rhs_err(gg.rhs(Ud).cpu().numpy(), L_or, U, oracle.max_rate(go, U), case.N, case.dim)
+    assert (err <= TOL).all(), err
+
+
+@pytest.mark.parametrize("name", ["slab_1d_hllc", "shock_bubble_2d_ragged", "spheres_3d_ragged"])
+def test_rk3_parity_fp64(gpu, name):
+    case = SMALL_CASES[name]()
+    go, gg = grids(case)
+    U = oracle.prim_to_cons(go, case.V)
+    Ud = to_dev(U)
+    gg.bind(Ud)
+    cfl = case.cfl or 0.2
+    for step in range(5):
+        U, dt_or = oracle.rk3_step(go, U, cfl=cfl)
+        dt = gg.rk_step(cfl=cfl, want_dt=True)
+        assert dt == pytest.approx(dt_or, rel=1e-13)
+        err = state_err(Ud.cpu().numpy(), U, case.N, case.dim)
+        assert (err <= TOL).all(), (step, err)
+    gg.sync_status()
+
+
+def test_prim_cons_parity(gpu):
+    case = SMALL_CASES["spheres_3d_ragged"]()
+    go, gg = grids(case)
+    V = case.V
+    U_or = oracle.prim_to_cons(go, V)
+    U = gg.prim_to_cons(to_dev(V)).cpu().numpy()
+    assert (rel_err_per_var(U, U_or) <= 1e-15).all()
+    V_or = oracle.cons_to_prim(go, U_or)
+    V2 = gg.cons_to_prim(to_dev(U_or)).cpu().numpy()
+    assert (rel_err_per_var(V2, V_or) <= 1e-12).all()
+
+
+@pytest.mark.parametrize("N,seed", [(2, 0), (3, 1), (5, 2)])
+def test_limit_parity(gpu, N, seed):
+    """wc_limit (Eq. 17-21 alone) on adversarial raw faces vs the oracle.
+    Cells where every fraction of a face is limited to zero (S = 0 in exact
+    arithmetic, the oracle's first-order fallback, theta_17 = 0) sit on a
+    rounding knife edge and are compared separately below."""
+    d = 2
+    Vb, VL, VR = inputs.random_admissible_stencils(3001, N, d, seed=seed)
+    rng = np.random.default_rng(seed)
+    gam = list(rng.uniform(1.2, 6.0, size=N))
+    pinf = list(np.where(rng.uniform(size=N) < 0.5, 0.0, 10.0 ** rng.uniform(3, 8, size=N)))
+    go = oracle.Grid((8, 8), (1.0, 1.0), gam, pinf)
+    from paper_2608_00746_b300 import wenoc
+    gg = wenoc.Grid((8, 8), (1.0, 1.0), gam, pinf)
+    Ub = oracle.prim_to_cons(go, Vb)
+    keep = oracle.psi(go, Ub) > 0
+    Ub, VL, VR = (np.ascontiguousarray(a[:, keep]) for a in (Ub, VL, VR))
+    UL_or, UR_or, TH_or = oracle.limit(go, Ub, VL, VR)
+    UL, UR, TH = gg.limit(0, to_dev(Ub), to_dev(VL), to_dev(VR))
+    UL, UR, TH = UL.cpu().numpy(), UR.cpu().numpy(), TH.cpu().numpy()
+    # knife edge: a face sum S that is zero in exact arithmetic (either side
+    # took the fallback, or normalised by a rounding-level S)
+    ok = (TH_or[0] > 0) & (TH[0] > 0) & (TH_or[1] > 1e-8) & (TH[1] > 1e-8)
+    assert ok.mean() > 0.9
+    d = 2
+    for A, B in ((UL, UL_or), (UR, UR_or)):
+        err = state_err(A[:, ok], B[:, ok], N, d)
+        assert (err <= 1e-12).all(), err
+    assert np.abs(TH - TH_or)[:, ok].max() <= 1e-11
+
+
+def test_limit_degenerate_face_exact(gpu):
+    """Both fractions of the left face limited exactly to zero (S = 0): the
+    cell keeps its averages for masses and fractions (first-order fallback).
+    The numbers are exact in binary so both implementations take the branch."""
+    from paper_2608_00746_b300 import wenoc
+    go = oracle.Grid((8,), (1.0,), [1.4, 1.4], [0.0, 0.0])
+    gg = wenoc.Grid((8,), (1.0,), [1.4, 1.4], [0.0, 0.0])
+    # averages alpha = (0.5, 0.5); raw left faces -0.5 each, right faces 0.5
+    Vb = np.array([[0.5], [0.5], [0.0], [1.0], [0.5], [0.5]])
+    VL = np.array([[-0.5], [-0.5], [0.0], [1.0], [-0.5], [-0.5]])
+    VR = np.array([[0.5], [0.5], [0.0], [1.0], [0.5], [0.5]])
+    Ub = oracle.prim_to_cons(go, Vb)
+    UL_or, UR_or, TH_or = oracle.limit(go, Ub, VL, VR)
+    UL, UR, TH = gg.limit(0, to_dev(Ub), to_dev(VL), to_dev(VR))
+    assert TH_or[0, 0] == 0.0 and TH.cpu().numpy()[0, 0] == 0.0
+    for A, B in ((UL.cpu().numpy(), UL_or), (UR.cpu().numpy(), UR_or)):
+        assert np.allclose(A, B, rtol=1e-14, atol=1e-14)
+        assert np.allclose(B[[0, 1, 4, 5]], Ub[[0, 1, 4, 5]], rtol=1e-15)
