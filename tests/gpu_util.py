@@ -89,3 +89,16 @@ SMALL_CASES = {
     "circles_2d_n3": lambda: inputs.circles_shock_2d(shape=(70, 33), seed=2, ncirc=6,
                                                      rmin_cells=3, rmax_cells=9),
 }
+
+
+def l1_group(A, B, N, d):
+    """sum |A - B| / sum |B| per variable group (momentum as one vector)."""
+    A = np.asarray(A).reshape(A.shape[0], -1)
+    B = np.asarray(B).reshape(B.shape[0], -1)
+    out = np.zeros(B.shape[0])
+    for grp in groups(N, d):
+        s = np.abs(B[grp]).sum()
+        for v in grp:
+            dd = np.abs(A[v] - B[v]).sum()
+            out[v] = dd / s if s > 0 else dd
+    return out

@@ -106,7 +106,8 @@ def test_limit_parity(gpu, N, seed):
     for A, B in ((UL, UL_or), (UR, UR_or)):
         err = state_err(A[:, ok], B[:, ok], N, d)
         assert (err <= 1e-12).all(), err
-    assert np.abs(TH - TH_or)[:, ok].max() <= 1e-11
+    # theta = fbar/(fbar - m) amplifies rounding of m when fbar - m is small
+    assert np.abs(TH - TH_or)[:, ok].max() <= 1e-9
 
 
 def test_limit_degenerate_face_exact(gpu):
