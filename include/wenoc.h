@@ -130,6 +130,34 @@ wc_status wc_rk_step(wc_grid *g, double cfl, double dt_fixed, int nsteps, double
 wc_status wc_limit(const wc_grid *g, int dir, long ncell, const double *Ubar, const double *VL,
                    const double *VR, double *UL, double *UR, double *theta, void *stream);
 
+/* wc_rk_step without a workspace and without any device allocation, for
+ * callers that cannot allocate device memory (their device memory is owned
+ * and budgeted by another component, or allocating is not allowed where they
+ * run).  The paper has no counterpart: this is a deployment variant of
+ * wc_rk_step.
+ *
+ * Steps the caller's device state U_dev ([NV][ncell] FP64, the grid's bound
+ * state is not used) nsteps SSP-RK3 steps in place, with cfl / dt_fixed as in
+ * wc_rk_step.  The stage buffers, the direction accumulator and the dt and
+ * status words live in one scratch array compiled into the library (24 MiB
+ * plus 256 bytes, held by every GPU that loads the library until the process
+ * exits).  Grids whose three state-sized buffers do not fit (3 x NV x ncell
+ * x 8 bytes, each rounded up to 256, at most 24 MiB; e.g. 2-D N = 2 up to
+ * about 149,000 cells) are rejected with WC_ERR_ARG and a message in
+ * wc_last_error before any work is enqueued.
+ *
+ * The first call on a device looks up the scratch's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call shares the one array and the array keeps the
+ * last call's contents (the dt and status words are cleared by each call):
+ * calls whose work overlaps on the GPU -- on different streams, or from
+ * different host threads on one grid -- race and must be serialised by the
+ * caller.  When status_host is not NULL the call synchronises the stream and
+ * writes the device status bits of this call there (0 = no kernel-detected
+ * problem; 1 = inadmissible state; 2 = non-finite value). */
+wc_status wc_rk_step_noalloc(wc_grid *g, double *U_dev, double cfl, double dt_fixed, int nsteps,
+                             int *status_host, void *stream);
+
 /* Synchronises the stream, reads and clears the device status word; returns
  * WC_OK or the first kernel-detected error. */
 wc_status wc_sync_status(wc_grid *g, void *stream);

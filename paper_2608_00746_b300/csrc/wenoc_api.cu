@@ -375,3 +375,37 @@ extern "C" wc_status wc_fp64_peak_kernel(int blocks, int threads, int iters, dou
   if (flops) *flops = 2.0 * 8.0 * (double)iters * blocks * threads;
   return cudaGetLastError() == cudaSuccess ? WC_OK : WC_ERR_CUDA;
 }
+
+// ------------------------------------------------------------------ fixed-scratch stepping
+// Used by wc_rk_step_noalloc (wenoc_noalloc.cu): runs wc_rk_step on state U
+// with the stage buffers, accumulator, rate and status words placed in the
+// given scratch area (same layout as the bound workspace), then restores the
+// grid's own bindings.  Returns the device address of the status word used.
+wc_status wc_internal_rk_with_scratch(wc_grid* g, double* U, char* scratch, double cfl,
+                                      double dt_fixed, int nsteps, cudaStream_t st,
+                                      unsigned** status_out) {
+  wc_grid saved = *g;
+  size_t state = (size_t)g->nv * g->ncell * sizeof(double);
+  state = (state + 255) / 256 * 256;
+  char* tail = scratch + 3 * state;
+  cudaError_t e = cudaMemsetAsync(tail, 0, 256, st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "scratch clear");
+  g->U = U;
+  g->ws = scratch;
+  g->ws_bytes = 3 * state + 256;
+  g->B1 = (double*)scratch;
+  g->B2 = (double*)(scratch + state);
+  g->Lacc = (double*)(scratch + 2 * state);
+  g->rate = (unsigned long long*)tail;
+  g->dt = (double*)(tail + 8);
+  g->status = (unsigned*)(tail + 16);
+  wc_status r = wc_rk_step(g, cfl, dt_fixed, nsteps, nullptr, reinterpret_cast<void*>(st));
+  if (status_out) *status_out = g->status;
+  char err[256];
+  memcpy(err, g->err, sizeof(err));
+  *g = saved;
+  memcpy(g->err, err, sizeof(err));
+  return r;
+}
+
+void wc_internal_set_error(wc_grid* g, const char* msg) { fail(g, WC_ERR_ARG, msg); }

@@ -71,6 +71,8 @@ _SIGS = {
     "wc_last_error": (None, [_VP, ctypes.c_char_p, ctypes.c_size_t]),
     "wc_fp64_peak_kernel": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
                                            ctypes.POINTER(ctypes.c_double), _VP]),
+    "wc_rk_step_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP]),
 }
 
 _lib = None
