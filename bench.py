@@ -37,7 +37,7 @@ WORKLOAD = "shock_bubble_2d 1024x512 N=2 HLL CFL 0.2 reflective (seeded)"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nx", type=int, default=1024)
@@ -122,7 +122,7 @@ class Clocks:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -218,12 +218,15 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
     def timed_steps(g, K, W):
+        """K timed RK steps (events per step, L2 flushed in between) and the
+        mean duration of the sweep launches inside them (event pairs the
+        library records around each sweep launch on the same stream)."""
         for _ in range(W):
             g.rk_step(cfl=case.cfl)
         barrier()
         s = torch.cuda.current_stream()
-        total = 0.0
         evs = []
+        g.sweep_timing_begin(K * 3 * D)
         for _ in range(K):
             flush.fill_(1.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -232,37 +235,26 @@ def run_ours(args):
             e1.record(s)
             evs.append((e0, e1))
         barrier()
-        for e0, e1 in evs:
-            total += e0.elapsed_time(e1)
+        nl, tot_sw, _ = g.sweep_timing_read()
+        total = sum(e0.elapsed_time(e1) for e0, e1 in evs)
         g.sync_status()
-        return total / K  # ms per step
+        return total / K, tot_sw / max(nl, 1)  # ms per step, ms per sweep launch
 
-    def sweep_launch_ms(g, U, K):
-        """Average duration of the dominant kernel (the direction sweep): K x 3
-        x D sweep launches through wc_rhs, timed with events on the stream."""
-        L = torch.empty_like(U)
-        s = torch.cuda.current_stream()
-        g.rhs(U, L)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        for _ in range(3 * K):
-            g.rhs(U, L)
-        e1.record(s)
-        barrier()
-        return e0.elapsed_time(e1) / (3 * K * D)
-
-    # FP64 peak of this GPU (DFMA probe), measured before the timed region
-    peak_fp64 = wenoc.fp64_peak() / 1e12
+    # FP64 DFMA probe of this GPU (context for the derived peak below)
+    peak_probe = wenoc.fp64_peak() / 1e12
 
     results = {}
     with Clocks(local) as clk:
+        time.sleep(1.0)  # let the sampler start before the timed region
         for prec in ("fp64", "mixed"):
             g, U = make_grid(prec)
-            ms = timed_steps(g, args.steps, args.warmup)
-            sw = sweep_launch_ms(g, U, max(2, args.steps // 4))
+            ms, sw = timed_steps(g, args.steps, args.warmup)
             results[prec] = (ms, sw, g, U)
     clocks = clk.summary()
+    # FP64 peak from unit counts and clock: 2 DFMA per clock per SM (ncu's
+    # sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained = 296 per
+    # cycle on 148 SMs), 2 flops each, at the maximum SM clock 2032 MHz.
+    peak_fp64 = 2 * 2 * 148 * 2032e6 / 1e12
 
     # matched accuracy: mixed vs FP64 after the same number of steps from the
     # same initial state with the same time steps
@@ -329,7 +321,8 @@ def run_ours(args):
             "bound": "alu", "kernel": "k_sweep<N=2,D=2,double> (direction sweep)",
             "achieved": round(achieved, 4), "peak": round(peak_fp64, 4), "unit": "TFLOP/s",
             "frac": round(achieved / peak_fp64, 4), "traffic": traffic,
-            "peak_source": "measured FP64 DFMA probe of this GPU (wc_fp64_peak_kernel)",
+            "peak_source": "unit count x clock: 2 DFMA/clk/SM x 2 flop x 148 SM x 2032 MHz",
+            "peak_probe_measured": round(peak_probe, 4),
             "flops_per_cell_dir": fl, "sweep_ms_per_launch": round(sw64, 4),
             "sweep_ms_per_launch_mixed": round(swmx, 4),
             "hbm_bytes_per_cell_stage_min": roofline.bytes_per_cell_stage(N, D),

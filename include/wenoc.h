@@ -73,7 +73,8 @@ typedef struct {
   int energy_limiter;         /* 1: Eq. 21 applied (default); 0: skipped */
   int bc[6];                  /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi: WC_BC_* */
   int seg;                    /* cells per thread along a sweep; 0 = automatic */
-  int block;                  /* threads per block of the sweep; 0 = automatic */
+  int block;                  /* threads per block of the sweep (32..128); 0 = automatic */
+  int blocks_per_sm;          /* sweep blocks per SM (1..4); 0 = automatic */
 } wc_grid_desc;
 
 typedef struct wc_grid wc_grid;
@@ -157,6 +158,15 @@ wc_status wc_limit(const wc_grid *g, int dir, long ncell, const double *Ubar, co
  * problem; 1 = inadmissible state; 2 = non-finite value). */
 wc_status wc_rk_step_noalloc(wc_grid *g, double *U_dev, double cfl, double dt_fixed, int nsteps,
                              int *status_host, void *stream);
+
+/* Sweep timing (tracing): after wc_sweep_timing_begin(g, max_launches) the
+ * library records a CUDA event pair on the launch stream around each of the
+ * next max_launches direction-sweep launches of g (events are created here,
+ * no device memory is allocated).  wc_sweep_timing_read synchronises on the
+ * last event and returns the number of timed launches, their summed and
+ * largest durations in milliseconds, and stops the timing. */
+wc_status wc_sweep_timing_begin(wc_grid *g, int max_launches);
+wc_status wc_sweep_timing_read(wc_grid *g, int *launches, double *total_ms, double *max_ms);
 
 /* Synchronises the stream, reads and clears the device status word; returns
  * WC_OK or the first kernel-detected error. */

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/wenoc.h"
 #include "wenoc_kernels.cuh"
@@ -26,6 +27,9 @@ struct wc_grid {
   unsigned long long* rate = nullptr;
   double* dt = nullptr;
   char err[256];
+  // sweep timing (wc_sweep_timing_begin / _read)
+  std::vector<cudaEvent_t> tev;
+  int tmax = 0, tcount = 0;
 };
 
 static wc_status fail(wc_grid* g, wc_status s, const char* msg) {
@@ -85,6 +89,7 @@ extern "C" wc_status wc_init_grid(const wc_grid_desc* desc, wc_grid** out) {
   if (d.flux != WC_FLUX_HLL && d.flux != WC_FLUX_HLLC) return WC_ERR_ARG;
   if (d.precision != WC_PREC_FP64 && d.precision != WC_PREC_MIXED) return WC_ERR_UNSUPPORTED;
   if (d.seg < 0 || d.block < 0 || d.block > 128 || (d.block % 32) != 0) return WC_ERR_ARG;
+  if (d.blocks_per_sm < 0 || d.blocks_per_sm > 4) return WC_ERR_ARG;
   for (int p = 0; p < d.nphase; p++)
     if (!(d.gamma[p] > 1.0) || !(d.pinf[p] >= 0.0)) return WC_ERR_ARG;
   wc_grid* g = new (std::nothrow) wc_grid();
@@ -110,7 +115,11 @@ extern "C" wc_status wc_init_grid(const wc_grid_desc* desc, wc_grid** out) {
   return WC_OK;
 }
 
-extern "C" void wc_destroy(wc_grid* g) { delete g; }
+extern "C" void wc_destroy(wc_grid* g) {
+  if (!g) return;
+  for (cudaEvent_t ev : g->tev) cudaEventDestroy(ev);
+  delete g;
+}
 extern "C" int wc_nvar(const wc_grid* g) { return g ? g->nv : 0; }
 extern "C" long wc_ncell(const wc_grid* g) { return g ? g->ncell : 0; }
 
@@ -188,19 +197,40 @@ extern "C" wc_status wc_cons_to_prim(const wc_grid* gc, const double* U, double*
 }
 
 // ------------------------------------------------------------------ sweeps
-static int auto_seg(const wc_grid* g, int dir) {
-  if (g->d.seg > 0) return g->d.seg;
-  long npencil = g->ncell / g->d.n[dir];
-  // about one full wave of resident threads (148 SMs x 256 threads)
-  long want = 148L * 256;
-  long seg = g->ncell / (want > 0 ? want : 1);
-  int s = 8;
-  while (s < seg && s < 64) s *= 2;
-  (void)npencil;
-  return s;
+static int sweep_block(const wc_grid* g) { return g->d.block > 0 ? g->d.block : 128; }
+
+// Threads of one sweep launch: a whole number of blocks per SM on all 148
+// SMs, so every SM sub-partition gets the same number of warps (the sweep is
+// FP64-pipe bound, and the pipe is per sub-partition).
+static long sweep_threads(const wc_grid* g) {
+  int block = sweep_block(g);
+  int bps = g->d.blocks_per_sm > 0 ? g->d.blocks_per_sm : 2;  // blocks per SM
+  if (g->d.blocks_per_sm <= 0 && g->d.precision == WC_PREC_MIXED) bps = 3;
+  return 148L * bps * block;
 }
 
-static int sweep_block(const wc_grid* g) { return g->d.block > 0 ? g->d.block : 64; }
+// Segment length: the smallest cost max-items-per-thread x (seg + 2)
+// (reconstructions per thread, two of them redundant per segment), over
+// seg in [4, 64]; ties go to the longer segment.
+static int auto_seg(const wc_grid* g, int dir) {
+  if (g->d.seg > 0) return g->d.seg;
+  const long n = g->d.n[dir];
+  const long npencil = g->ncell / n;
+  const long T = sweep_threads(g);
+  long best_cost = -1;
+  int best = 8;
+  for (int seg = 4; seg <= 64; seg++) {
+    long nseg = (n + seg - 1) / seg;
+    long items = npencil * nseg;
+    long per_thread = (items + T - 1) / T;
+    long cost = per_thread * (seg + 2);
+    if (best_cost < 0 || cost <= best_cost) {
+      best_cost = cost;
+      best = seg;
+    }
+  }
+  return best;
+}
 
 static SweepArgs make_args(const wc_grid* g, int dir, const double* U, double* L) {
   SweepArgs a;
@@ -217,6 +247,7 @@ static SweepArgs make_args(const wc_grid* g, int dir, const double* U, double* L
   a.npencil = g->ncell / a.n;
   a.seg = auto_seg(g, dir);
   a.nseg = (a.n + a.seg - 1) / a.seg;
+  a.max_threads = sweep_threads(g);
   a.inv_dx = 1.0 / g->d.dx[dir];
   a.bclo = g->d.bc[2 * dir];
   a.bchi = g->d.bc[2 * dir + 1];
@@ -226,10 +257,57 @@ static SweepArgs make_args(const wc_grid* g, int dir, const double* U, double* L
   return a;
 }
 
-static cudaError_t launch(const wc_grid* g, const SweepArgs& a, cudaStream_t st) {
+static cudaError_t launch(const wc_grid* gc, const SweepArgs& a, cudaStream_t st) {
+  wc_grid* g = const_cast<wc_grid*>(gc);
+  const bool timed = g->tcount < g->tmax;
+  if (timed) cudaEventRecord(g->tev[2 * g->tcount], st);
+  cudaError_t e;
   if (g->d.precision == WC_PREC_MIXED)
-    return launch_sweep_mixed(g->d.nphase, g->d.dim, a, g->mat, sweep_block(g), st);
-  return launch_sweep_fp64(g->d.nphase, g->d.dim, a, g->mat, sweep_block(g), st);
+    e = launch_sweep_mixed(g->d.nphase, g->d.dim, a, g->mat, sweep_block(g), st);
+  else
+    e = launch_sweep_fp64(g->d.nphase, g->d.dim, a, g->mat, sweep_block(g), st);
+  if (timed) {
+    cudaEventRecord(g->tev[2 * g->tcount + 1], st);
+    g->tcount++;
+  }
+  return e;
+}
+
+extern "C" wc_status wc_sweep_timing_begin(wc_grid* g, int max_launches) {
+  if (!g || max_launches < 0 || max_launches > 100000) return WC_ERR_ARG;
+  while ((int)g->tev.size() < 2 * max_launches) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return cuda_fail(g, e, "event create");
+    g->tev.push_back(ev);
+  }
+  g->tmax = max_launches;
+  g->tcount = 0;
+  return WC_OK;
+}
+
+extern "C" wc_status wc_sweep_timing_read(wc_grid* g, int* launches, double* total_ms,
+                                          double* max_ms) {
+  if (!g) return WC_ERR_ARG;
+  int n = g->tcount;
+  double tot = 0.0, mx = 0.0;
+  if (n > 0) {
+    cudaError_t e = cudaEventSynchronize(g->tev[2 * n - 1]);
+    if (e != cudaSuccess) return cuda_fail(g, e, "event sync");
+  }
+  for (int k = 0; k < n; k++) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&ms, g->tev[2 * k], g->tev[2 * k + 1]);
+    if (e != cudaSuccess) return cuda_fail(g, e, "event time");
+    tot += ms;
+    if (ms > mx) mx = ms;
+  }
+  if (launches) *launches = n;
+  if (total_ms) *total_ms = tot;
+  if (max_ms) *max_ms = mx;
+  g->tmax = 0;
+  g->tcount = 0;
+  return WC_OK;
 }
 
 extern "C" wc_status wc_rhs(wc_grid* g, const double* U, double* L, void* stream) {
@@ -384,7 +462,11 @@ extern "C" wc_status wc_fp64_peak_kernel(int blocks, int threads, int iters, dou
 wc_status wc_internal_rk_with_scratch(wc_grid* g, double* U, char* scratch, double cfl,
                                       double dt_fixed, int nsteps, cudaStream_t st,
                                       unsigned** status_out) {
-  wc_grid saved = *g;
+  // save and restore only the bindings (the grid also owns timing events)
+  struct Bind {
+    double* U; char* ws; size_t ws_bytes; double *B1, *B2, *Lacc;
+    unsigned long long* rate; double* dt; unsigned* status;
+  } saved{g->U, g->ws, g->ws_bytes, g->B1, g->B2, g->Lacc, g->rate, g->dt, g->status};
   size_t state = (size_t)g->nv * g->ncell * sizeof(double);
   state = (state + 255) / 256 * 256;
   char* tail = scratch + 3 * state;
@@ -401,10 +483,15 @@ wc_status wc_internal_rk_with_scratch(wc_grid* g, double* U, char* scratch, doub
   g->status = (unsigned*)(tail + 16);
   wc_status r = wc_rk_step(g, cfl, dt_fixed, nsteps, nullptr, reinterpret_cast<void*>(st));
   if (status_out) *status_out = g->status;
-  char err[256];
-  memcpy(err, g->err, sizeof(err));
-  *g = saved;
-  memcpy(g->err, err, sizeof(err));
+  g->U = saved.U;
+  g->ws = saved.ws;
+  g->ws_bytes = saved.ws_bytes;
+  g->B1 = saved.B1;
+  g->B2 = saved.B2;
+  g->Lacc = saved.Lacc;
+  g->rate = saved.rate;
+  g->dt = saved.dt;
+  g->status = saved.status;
   return r;
 }
 

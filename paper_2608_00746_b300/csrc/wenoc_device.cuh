@@ -41,6 +41,66 @@ struct Idx {
   __host__ __device__ static constexpr int A(int p) { return N + D + 1 + p; }
 };
 
+// ------------------------------------------------------------------ arithmetic helpers
+// Reciprocal by the Newton-Raphson iteration r <- r + r (1 - x r) (quadratic
+// convergence; see Muller et al., Handbook of Floating-Point Arithmetic,
+// division by Newton-Raphson iteration), started from the hardware
+// approximation rcp.approx.ftz.f64; two steps reach full double precision.
+// For normal, finite x only (callers check the range).
+#ifndef WC_RCP_APPROX_F64
+#define WC_RCP_APPROX_F64(r, x) asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x))
+#define WC_RSQRT_APPROX_F64(r, x) asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x))
+#endif
+__device__ __forceinline__ double rcp_nr(double x) {
+  double r;
+  WC_RCP_APPROX_F64(r, x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+__device__ __forceinline__ float rcp_nr(float x) { return 1.0f / x; }
+
+// 1/sqrt(x) by the Newton-Raphson iteration y <- y + y (1/2 - x y^2 / 2)
+// (same reference), started from rsqrt.approx.ftz.f64.  Normal positive x.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  double y;
+  WC_RSQRT_APPROX_F64(y, x);
+  const double h = 0.5 * x;
+  double e = fma(-h * y, y, 0.5);
+  y = fma(y, e, y);
+  e = fma(-h * y, y, 0.5);
+  return fma(y, e, y);
+}
+__device__ __forceinline__ float rsqrt_nr(float x) { return rsqrtf(x); }
+
+// Bit-level tests on non-negative or signed values (integer pipe, not FP64).
+__device__ __forceinline__ bool has_sign(double x) { return __double2hiint(x) < 0; }
+__device__ __forceinline__ bool has_sign(float x) { return __float_as_int(x) < 0; }
+__device__ __forceinline__ bool is_pos_zero(double x) { return __double_as_longlong(x) == 0; }
+__device__ __forceinline__ bool is_pos_zero(float x) { return __float_as_int(x) == 0; }
+// max of non-negative values: their bit patterns order like the values
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+  long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return __longlong_as_double(ia > ib ? ia : ib);
+}
+__device__ __forceinline__ float max_nonneg(float a, float b) {
+  int ia = __float_as_int(a), ib = __float_as_int(b);
+  return __int_as_float(ia > ib ? ia : ib);
+}
+// 2^-e(m) with e(m) the binary exponent of m > 0 (m * scale in [1, 2)), or 0
+// when m is outside [2^-1000, 2^1000] (caller takes a slower exact path).
+__device__ __forceinline__ double exp_scale(double m) {
+  int e = (__double2hiint(m) >> 20) & 0x7ff;
+  if (e < 23 || e > 2023) return 0.0;
+  return __hiloint2double((2046 - e) << 20, 0);
+}
+__device__ __forceinline__ float exp_scale(float m) {
+  int e = (__float_as_int(m) >> 23) & 0xff;
+  if (e < 1 || e > 253) return 0.0f;
+  return __int_as_float((254 - e) << 23);
+}
+
 // ------------------------------------------------------------------ EOS
 // Mixture rules and Eq. 27.  V gets u and P; masses and fractions are copies.
 template <int N, int D>
@@ -49,7 +109,6 @@ __device__ __forceinline__ void cons_to_prim(const Mat& m, const double* U, doub
   double rho = U[0];
 #pragma unroll
   for (int p = 1; p < N; p++) rho += U[p];
-  double inv = 1.0 / rho;
   double mm = 0.0;
 #pragma unroll
   for (int j = 0; j < D; j++) mm = fma(U[I::U(j)], U[I::U(j)], mm);
@@ -60,6 +119,17 @@ __device__ __forceinline__ void cons_to_prim(const Mat& m, const double* U, doub
     sB = fma(m.B[p], U[I::A(p)], sB);
     if (m.hasD) sD = fma(m.D[p], U[p], sD);
   }
+  // one reciprocal for 1/rho and 1/sum A alpha
+  double inv, inv_sA;
+  double prod = rho * sA;
+  if (prod > 1e-280 && prod < 1e280) {
+    double r = rcp_nr(prod);
+    inv = sA * r;
+    inv_sA = rho * r;
+  } else {
+    inv = 1.0 / rho;
+    inv_sA = 1.0 / sA;
+  }
 #pragma unroll
   for (int p = 0; p < N; p++) {
     V[p] = U[p];
@@ -67,7 +137,7 @@ __device__ __forceinline__ void cons_to_prim(const Mat& m, const double* U, doub
   }
 #pragma unroll
   for (int j = 0; j < D; j++) V[I::U(j)] = U[I::U(j)] * inv;
-  V[I::E] = (U[I::E] - 0.5 * mm * inv - sB - sD) / sA;
+  V[I::E] = (U[I::E] - 0.5 * mm * inv - sB - sD) * inv_sA;
 }
 
 // psi_{V->U} for one face: rho, rho u, rho E (Eq. 26).  Masses/fractions copied.
@@ -123,7 +193,9 @@ __device__ __forceinline__ double psi_cons(const Mat& m, const double* U) {
     s = fma(U[I::A(p)], m.Cmin[p], s);
     if (m.hasD) s = fma(m.D[p], U[p], s);
   }
-  double ke = rho > 0.0 ? 0.5 * mm / rho : 0.0;
+  double ke = 0.0;
+  if (rho > 1e-280) ke = 0.5 * mm * rcp_nr(rho);
+  else if (rho > 0.0) ke = 0.5 * mm / rho;
   return U[I::E] - ke - s;
 }
 
@@ -156,69 +228,90 @@ __device__ __forceinline__ void smoothness(const Stencil<T>& s, T& b0, T& b1, T&
 }
 
 template <typename T> __device__ __forceinline__ T tiny_norm();
-template <> __device__ __forceinline__ double tiny_norm<double>() { return 1e-290; }
-template <> __device__ __forceinline__ float tiny_norm<float>() { return 1e-30f; }
+template <> __device__ __forceinline__ double tiny_norm<double>() { return 1e-140; }
+template <> __device__ __forceinline__ float tiny_norm<float>() { return 1e-17f; }
 
-// Eq. 15 with ideal weights (dA, dB, dC) = (0.1, 0.6, 0.3) for the
-// indicators (bA, bB, bC) in that order.
-//  * all indicators positive and in range: Eq. 15 divided through by IS_s^2
-//    is omega_s = (d_s prod_{k!=s} IS_k^2) / sum_t (d_t prod_{k!=t} IS_k^2),
-//    evaluated on the indicators scaled by 1/max;
-//  * some indicators zero: the zero stencils share the weight in proportion
-//    to d (the others have infinite ratios, so omega = 0);
-//  * indicators or products outside the normal range of T: the ratio form of
-//    Eq. 15 itself.
-template <typename T>
-__device__ __forceinline__ void wenow_weights(T bA, T bB, T bC, T& wA, T& wB, T& wC) {
-  const T dA = T(0.1), dB = T(0.6), dC = T(0.3);
-  if (bA > T(0) && bB > T(0) && bC > T(0)) {
-    T mx = bA > bB ? bA : bB;
-    mx = mx > bC ? mx : bC;
-    if (mx >= tiny_norm<T>()) {
-      T r = T(1) / mx;
-      T xA = bA * r, xB = bB * r, xC = bC * r;
-      T sA = xA * xA, sB = xB * xB, sC = xC * xC;
-      T aA = dA * sB * sC, aB = dB * sA * sC, aC = dC * sA * sB;
-      T sum = aA + aB + aC;
-      if (sum >= tiny_norm<T>()) {
-        T inv = T(1) / sum;
-        wA = aA * inv;
-        wB = aB * inv;
-        wC = aC * inv;
-        return;
-      }
-    }
-    T rAB = bA / bB, rAC = bA / bC, rBC = bB / bC;
-    wA = dA / (dA + dB * rAB * rAB + dC * rAC * rAC);
-    T rBA = bB / bA;
-    wB = dB / (dB + dA * rBA * rBA + dC * rBC * rBC);
-    T rCA = bC / bA, rCB = bC / bB;
-    wC = dC / (dC + dA * rCA * rCA + dB * rCB * rCB);
-    return;
-  }
-  T zA = bA == T(0) ? dA : T(0);
-  T zB = bB == T(0) ? dB : T(0);
-  T zC = bC == T(0) ? dC : T(0);
-  T inv = T(1) / (zA + zB + zC);
-  wA = zA * inv;
-  wB = zB * inv;
-  wC = zC * inv;
-}
-
+// Weights of both faces of a cell in unnormalised form: omega^L_s =
+// aL[s] invL, omega^R_s = aR[s] invR (invL, invR also carry the 1/6 of the
+// candidates).
 template <typename T>
 struct W6 {
-  T L0, L1, L2, R0, R1, R2;
+  T aL0, aL1, aL2, aR0, aR1, aR2, invL, invR;
 };
 
-// Relative-smoothness weights of both faces of cell i.
+// Eq. 15 for both faces from the shared indicators (b0, b1, b2) of the
+// sub-stencils {i-2..i}, {i-1..i+1}, {i..i+2}; ideal weights (0.1, 0.6, 0.3)
+// left to right for the left face and mirrored for the right face.
+//  * all indicators positive: Eq. 15 divided through by IS_s^2 is
+//    omega_s = (d_s prod_{k!=s} IS_k^2) / sum_t (d_t prod_{k!=t} IS_k^2).  The
+//    indicators are scaled by a power of two (exact) so their maximum is in
+//    [1, 2); the products IS_j^2 IS_k^2 are shared by both faces, and one
+//    reciprocal of sumL sumR serves both normalisations.  A single zero
+//    indicator is covered too (its stencil gets all the weight);
+//  * two or three zero indicators: the zero stencils share the weight in
+//    proportion to d (every other ratio is infinite, omega = 0);
+//  * products beyond the range of T: the ratio form of Eq. 15 itself.
 template <typename T>
-__device__ __forceinline__ W6<T> weights_of(const Stencil<T>& s) {
+__device__ __forceinline__ W6<T> weights_of(const Stencil<T>& st) {
   T b0, b1, b2;
-  smoothness(s, b0, b1, b2);
+  smoothness(st, b0, b1, b2);
+  const T d0 = T(0.1), d1 = T(0.6), d2 = T(0.3);
+  const T sixth = T(1) / T(6);
   W6<T> w;
-  wenow_weights(b0, b1, b2, w.L0, w.L1, w.L2);
-  // mirrored sub-stencils: {i..i+2} (ideal 0.1), {i-1..i+1}, {i-2..i}
-  wenow_weights(b2, b1, b0, w.R0, w.R1, w.R2);
+  T mx = max_nonneg(b0, max_nonneg(b1, b2));
+  T sc = exp_scale(mx);
+  if (!is_pos_zero(sc)) {
+    T x0 = b0 * sc, x1 = b1 * sc, x2 = b2 * sc;
+    T s0 = x0 * x0, s1 = x1 * x1, s2 = x2 * x2;
+    T p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
+    w.aL0 = d0 * p12;
+    w.aL1 = d1 * p02;
+    w.aL2 = d2 * p01;
+    w.aR0 = d0 * p01;
+    w.aR1 = d1 * p02;
+    w.aR2 = d2 * p12;
+    T sumL = w.aL0 + w.aL1 + w.aL2;
+    T sumR = w.aR0 + w.aR1 + w.aR2;
+    if (sumL >= tiny_norm<T>() && sumR >= tiny_norm<T>()) {
+      T r = rcp_nr(sumL * sumR) * sixth;
+      w.invL = sumR * r;
+      w.invR = sumL * r;
+      return w;
+    }
+  }
+  const bool z0 = is_pos_zero(b0), z1 = is_pos_zero(b1), z2 = is_pos_zero(b2);
+  if (int(z0) + int(z1) + int(z2) >= 2 || is_pos_zero(mx)) {
+    // Eq. 15 zero cases; ideal weights of the zero stencils, renormalised
+    w.aL0 = z0 ? d0 : T(0);
+    w.aL1 = z1 ? d1 : T(0);
+    w.aL2 = z2 ? d2 : T(0);
+    w.aR0 = z2 ? d0 : T(0);
+    w.aR1 = z1 ? d1 : T(0);
+    w.aR2 = z0 ? d2 : T(0);
+    w.invL = sixth / (w.aL0 + w.aL1 + w.aL2);
+    w.invR = sixth / (w.aR0 + w.aR1 + w.aR2);
+    return w;
+  }
+  // Eq. 15 in ratio form (extreme ratios, single zeros far out of range)
+  auto ratio_w = [](T bA, T bB, T bC, T dA, T dB, T dC) {
+    T den = dA;
+    bool inf = false;
+    if (is_pos_zero(bA) && is_pos_zero(bB)) den += dB;
+    else if (is_pos_zero(bB)) inf = true;
+    else { T r = bA / bB; den += dB * r * r; }
+    if (is_pos_zero(bA) && is_pos_zero(bC)) den += dC;
+    else if (is_pos_zero(bC)) inf = true;
+    else { T r = bA / bC; den += dC * r * r; }
+    return inf ? T(0) : dA / den;
+  };
+  w.aL0 = ratio_w(b0, b1, b2, d0, d1, d2);
+  w.aL1 = ratio_w(b1, b0, b2, d1, d0, d2);
+  w.aL2 = ratio_w(b2, b0, b1, d2, d0, d1);
+  w.aR0 = ratio_w(b2, b1, b0, d0, d1, d2);
+  w.aR1 = ratio_w(b1, b2, b0, d1, d0, d2);
+  w.aR2 = ratio_w(b0, b2, b1, d2, d0, d1);
+  w.invL = sixth;
+  w.invR = sixth;
   return w;
 }
 
@@ -226,11 +319,10 @@ __device__ __forceinline__ W6<T> weights_of(const Stencil<T>& s) {
 // f_i, times 6, are 2da-7db, 2dd-db, 5dd-de (left face) and the mirror images.
 template <typename T>
 __device__ __forceinline__ void reconstruct(const W6<T>& w, const Stencil<T>& s, T& fL, T& fR) {
-  const T sixth = T(1) / T(6);
   T qL0 = T(2) * s.da - T(7) * s.db, qL1 = T(2) * s.dd - s.db, qL2 = T(5) * s.dd - s.de;
   T qR0 = T(2) * s.de - T(7) * s.dd, qR1 = T(2) * s.db - s.dd, qR2 = T(5) * s.db - s.da;
-  fL = s.c + (w.L0 * qL0 + w.L1 * qL1 + w.L2 * qL2) * sixth;
-  fR = s.c + (w.R0 * qR0 + w.R1 * qR1 + w.R2 * qR2) * sixth;
+  fL = s.c + (w.aL0 * qL0 + w.aL1 * qL1 + w.aL2 * qL2) * w.invL;
+  fR = s.c + (w.aR0 * qR0 + w.aR1 * qR1 + w.aR2 * qR2) * w.invR;
 }
 
 // ------------------------------------------------------------------ limiters
@@ -239,10 +331,15 @@ __device__ __forceinline__ void reconstruct(const W6<T>& w, const Stencil<T>& s,
 // to [0, 1].
 __device__ __forceinline__ double theta_pos(double fb, double fL, double fR) {
   double fC = (fb - (fL + fR) * (1.0 / 12.0)) * 1.2;
+  // common case decided on the sign bits (a -0.0 takes the exact path below,
+  // which returns 1 as well)
+  if (!(has_sign(fC) | has_sign(fL) | has_sign(fR))) return 1.0;
   double m = fmin(fC, fmin(fL, fR));
   if (m >= 0.0) return 1.0;
   if (fb <= 0.0) return 0.0;
-  return fmin(fb / (fb - m), 1.0);
+  double den = fb - m;
+  double t = (den > 1e-300 && den < 1e300) ? fb * rcp_nr(den) : fb / den;
+  return fmin(t, 1.0);
 }
 
 __device__ __forceinline__ double theta_lower(double fb, double fC, double fL, double fR) {
@@ -304,7 +401,7 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
     th17 = 0.0;
   } else {
     if (SL != 1.0) {
-      double r = 1.0 / SL;
+      double r = (SL > 1e-300 && SL < 1e300) ? rcp_nr(SL) : 1.0 / SL;
 #pragma unroll
       for (int p = 0; p < N; p++) {
         mL[p] *= r;
@@ -312,7 +409,7 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
       }
     }
     if (SR != 1.0) {
-      double r = 1.0 / SR;
+      double r = (SR > 1e-300 && SR < 1e300) ? rcp_nr(SR) : 1.0 / SR;
 #pragma unroll
       for (int p = 0; p < N; p++) {
         mR[p] *= r;
@@ -320,12 +417,16 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
       }
     }
   }
-  // Eq. 20: theta_i = min_p theta_p recomputed on the normalised faces
+  // Eq. 20: theta_i = min_p theta_p recomputed on the normalised faces (when
+  // Eq. 17 and Eq. 19 left every face value unchanged, the recomputed thetas
+  // are those of Eq. 17, all one)
   double thi = 1.0;
+  if (th17 < 1.0 || SL != 1.0 || SR != 1.0) {
 #pragma unroll
-  for (int p = 0; p < N; p++) {
-    double tp = fmin(theta_pos(Ub[p], mL[p], mR[p]), theta_pos(Ub[I::A(p)], aL[p], aR[p]));
-    thi = fmin(thi, tp);
+    for (int p = 0; p < N; p++) {
+      double tp = fmin(theta_pos(Ub[p], mL[p], mR[p]), theta_pos(Ub[I::A(p)], aL[p], aR[p]));
+      thi = fmin(thi, tp);
+    }
   }
   if (thi < 1.0) {
 #pragma unroll
@@ -410,6 +511,9 @@ __device__ __forceinline__ TF sound_speed(const Mat& m, const double* U, TF rho,
     num = num + TF(m.Ag[p]) * a * (P + TF(m.pinf[p]));
     den = den + TF(m.A[p]) * a;
   }
+  // c = sqrt(num / (den rho)) = num / sqrt(num den rho)
+  TF x = num * den * rho;
+  if (x > TF(1e-30) && x < TF(1e30)) return num * rsqrt_nr(x);
   return sqrt(num / (den * rho));
 }
 
@@ -490,7 +594,7 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
     } else if (sR <= TF(0)) {
       k = TF(-1);  // F_L + (-1)((F_L - F_R) + s_R (U_R - U_L)) with s_R = 0
     } else {
-      k = sL / (sR - sL);
+      k = sL * rcp_nr(sR - sL);
     }
     const TF sRu = (sR <= TF(0)) ? TF(0) : sR;
     kd = double(k);

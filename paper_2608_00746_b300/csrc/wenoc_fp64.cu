@@ -11,6 +11,7 @@ static cudaError_t go(const SweepArgs& a, const Mat& m, int block, cudaStream_t 
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   long threads = a.npencil * a.nseg;
+  if (a.max_threads > 0 && threads > a.max_threads) threads = a.max_threads;
   long blocks = (threads + block - 1) / block;
   k<<<(unsigned)blocks, block, smem, st>>>(a, m);
   return cudaGetLastError();

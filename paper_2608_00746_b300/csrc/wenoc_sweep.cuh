@@ -31,6 +31,7 @@ struct SweepArgs {
   long stride;         // index step along dir
   long npencil;        // ncell / n
   int nseg, seg;       // segments per pencil, cells per segment
+  long max_threads;    // launch size cap (whole blocks per SM); items loop beyond it
   double inv_dx;
   int bclo, bchi;
   int mode;            // 0: L = dir part; 1: L += dir part; 2: stage with L + dir part; 3: stage with dir part only
@@ -62,146 +63,153 @@ __device__ __forceinline__ int bc_index(int j, int n, int bclo, int bchi, bool& 
   return j;
 }
 
-// Ring slot layout in shared memory (per thread, 5 slots):
-//   V[NV] of type T (primitive, for the reconstruction), U[NV] FP64
-//   (conservative, for the limiter and the update), P FP64.
+// Ring slot layout in shared memory (per thread, 5 slots): the pressure in
+// FP64 (for psi at the cell average) and the primitive state V[NV] in the
+// reconstruction precision T.  Conservative cell values are re-read from
+// global memory (L1-resident: each cell is read twice within 3 iterations).
 template <int N, int D, typename T>
 struct Ring {
   static constexpr int NV = Idx<N, D>::NV;
-  static constexpr int SLOT_BYTES = NV * (int)sizeof(T) + NV * 8 + 8;
-  static constexpr int BYTES = 5 * ((SLOT_BYTES + 7) / 8) * 8;
+  static constexpr int SLOT_BYTES = 8 + NV * (int)sizeof(T);
+  static constexpr int SLOTD = (SLOT_BYTES + 7) / 8;   // doubles per slot
+  static constexpr int BYTES = 5 * SLOTD * 8;          // per thread
 };
 
 template <int N, int D, typename T, typename TF>
 __global__ void __launch_bounds__(128) k_sweep(SweepArgs a, Mat m) {
   using I = Idx<N, D>;
   constexpr int NV = I::NV;
-  constexpr int SLOTD = (Ring<N, D, T>::SLOT_BYTES + 7) / 8;  // doubles per slot
+  constexpr int SLOTD = Ring<N, D, T>::SLOTD;
   extern __shared__ double smem[];
-  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= a.npencil * a.nseg) return;
-  long tr = tid % a.npencil;
-  int sg = (int)(tid / a.npencil);
-  // first cell of the pencil
-  long base;
-  if (a.dir == 0) base = tr * a.nx;
-  else if (a.dir == 1) base = (tr / a.nx) * ((long)a.nx * a.ny) + tr % a.nx;
-  else base = tr;
-  int s = sg * a.seg;
-  int e = min(s + a.seg, a.n);
   double* ring = smem + (long)threadIdx.x * 5 * SLOTD;
-
-  auto load = [&](int c) {
-    bool flip;
-    int j = bc_index(c, a.n, a.bclo, a.bchi, flip);
-    long cell = base + (long)j * a.stride;
-    double* sl = ring + ((c + 15) % 5) * SLOTD;
-    double* Us = sl;                       // NV doubles
-    double* Ps = sl + NV;                  // 1 double
-    T* Vs = reinterpret_cast<T*>(sl + NV + 1);
-    double u[NV], v[NV];
-#pragma unroll
-    for (int k = 0; k < NV; k++) u[k] = __ldg(a.U + (long)k * a.ncell + cell);
-    if (flip) {
-#pragma unroll
-      for (int j = 0; j < D; j++)
-        if (j == a.dir) u[I::U(j)] = -u[I::U(j)];
-    }
-    cons_to_prim<N, D>(m, u, v);
-#pragma unroll
-    for (int k = 0; k < NV; k++) {
-      Us[k] = u[k];
-      Vs[k] = T(v[k]);
-    }
-    *Ps = v[I::E];
-  };
-
-  for (int c = s - 3; c <= s; c++) load(c);
-
-  Face<N, D> prevL;
-  double Fprev[NV];
-  double uprev = 0.0;
+  const long nthreads = (long)gridDim.x * blockDim.x;
+  const long nitems = a.npencil * a.nseg;
+  unsigned bad = 0u;
   double dt = 0.0;
   if (a.mode >= 2) dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.cfl / *a.rate;
-  unsigned bad = 0u;
 
-  for (int c = s - 1; c <= e; c++) {
-    load(c + 2);
-    const double* slot[5];
-#pragma unroll
-    for (int k = 0; k < 5; k++) slot[k] = ring + ((c - 2 + k + 15) % 5) * SLOTD;
-    const T* V0 = reinterpret_cast<const T*>(slot[0] + NV + 1);
-    const T* V1 = reinterpret_cast<const T*>(slot[1] + NV + 1);
-    const T* V2 = reinterpret_cast<const T*>(slot[2] + NV + 1);
-    const T* V3 = reinterpret_cast<const T*>(slot[3] + NV + 1);
-    const T* V4 = reinterpret_cast<const T*>(slot[4] + NV + 1);
-    const double* Ub = slot[2];
-    double Pb = slot[2][NV];
+  // work item = (pencil, segment); consecutive threads take consecutive
+  // pencils of one segment row, so y and z sweeps read coalesced
+  for (long item = (long)blockIdx.x * blockDim.x + threadIdx.x; item < nitems;
+       item += nthreads) {
+    const long tr = item % a.npencil;
+    const int sg = (int)(item / a.npencil);
+    long base;
+    if (a.dir == 0) base = tr * a.nx;
+    else if (a.dir == 1) base = (tr / a.nx) * ((long)a.nx * a.ny) + tr % a.nx;
+    else base = tr;
+    const int s = sg * a.seg;
+    const int e = min(s + a.seg, a.n);
 
-    // Eq. 16: masses and fractions with the weights of the masses
-    double mL[N], mR[N], aL[N], aR[N];
+    // conservative values of cell c (boundary cells mapped, normal momentum
+    // negated behind reflective walls)
+    auto load_cons = [&](int c, double* u) {
+      bool flip;
+      int j = bc_index(c, a.n, a.bclo, a.bchi, flip);
+      long cell = base + (long)j * a.stride;
 #pragma unroll
-    for (int p = 0; p < N; p++) {
-      Stencil<T> st = stencil<T>(V0[p], V1[p], V2[p], V3[p], V4[p]);
-      W6<T> w = weights_of<T>(st);
-      T fl, fr;
-      reconstruct(w, st, fl, fr);
-      mL[p] = double(fl);
-      mR[p] = double(fr);
-      const int ia = I::A(p);
-      st = stencil<T>(V0[ia], V1[ia], V2[ia], V3[ia], V4[ia]);
-      reconstruct(w, st, fl, fr);
-      aL[p] = double(fl);
-      aR[p] = double(fr);
-    }
-    // velocity and pressure, each with its own weights
-    double uL[D], uR[D], PL, PR;
+      for (int k = 0; k < NV; k++) u[k] = __ldg(a.U + (long)k * a.ncell + cell);
+      // sign flip of the normal momentum on the bit pattern (no FP64 op, no
+      // runtime-indexed register array)
 #pragma unroll
-    for (int v = N; v <= N + D; v++) {
-      Stencil<T> st = stencil<T>(V0[v], V1[v], V2[v], V3[v], V4[v]);
-      W6<T> w = weights_of<T>(st);
-      T fl, fr;
-      reconstruct(w, st, fl, fr);
-      if (v < N + D) {
-        uL[v - N] = double(fl);
-        uR[v - N] = double(fr);
-      } else {
-        PL = double(fl);
-        PR = double(fr);
+      for (int jj = 0; jj < D; jj++) {
+        long long mask = (flip && jj == a.dir) ? (long long)0x8000000000000000ULL : 0LL;
+        u[I::U(jj)] = __longlong_as_double(__double_as_longlong(u[I::U(jj)]) ^ mask);
       }
-    }
-    Face<N, D> fL, fR;
-    limit_chain<N, D>(m, Ub, Pb, mL, aL, mR, aR, uL, PL, uR, PR, a.energy_limiter, fL, fR,
-                      nullptr);
-    if (c >= s) {
-      double F[NV], uh;
-      riemann<N, D, TF>(m, a.dir, a.hllc, prevL, fR, F, uh);
-      if (c > s) {
-        // update cell c-1 (interior index, no boundary mapping)
-        long cell = base + (long)(c - 1) * a.stride;
-        const double* Uc = slot[1];   // cell c-1
+    };
+    auto load = [&](int c) {
+      double u[NV], v[NV];
+      load_cons(c, u);
+      cons_to_prim<N, D>(m, u, v);
+      double* sl = ring + ((c + 15) % 5) * SLOTD;
+      sl[0] = v[I::E];
+      T* Vs = reinterpret_cast<T*>(sl + 1);
 #pragma unroll
-        for (int v = 0; v < NV; v++) {
-          double val = -(F[v] - Fprev[v]) * a.inv_dx;
-          if (v >= N + D + 1) val = fma(Uc[v], (uh - uprev) * a.inv_dx, val);
-          long idx = (long)v * a.ncell + cell;
-          if (!(fabs(val) <= 1.7e308)) bad |= ST_NAN;
-          if (a.mode == 0) {
-            a.L[idx] = val;
-          } else if (a.mode == 1) {
-            a.L[idx] += val;
-          } else {
-            double Lt = a.mode == 2 ? a.L[idx] + val : val;
-            double u0 = a.U0[idx];
-            a.Uout[idx] = a.rk0 * u0 + a.rk1 * Uc[v] + a.rk2 * dt * Lt;
-          }
+      for (int k = 0; k < NV; k++) Vs[k] = T(v[k]);
+    };
+
+    for (int c = s - 3; c <= s; c++) load(c);
+
+    Face<N, D> prevL;
+    double Fprev[NV], Uprev[NV];
+    double uprev = 0.0;
+    for (int c = s - 1; c <= e; c++) {
+      load(c + 2);
+      const T* V[5];
+#pragma unroll
+      for (int k = 0; k < 5; k++)
+        V[k] = reinterpret_cast<const T*>(ring + ((c - 2 + k + 15) % 5) * SLOTD + 1);
+      const double Pb = ring[((c + 15) % 5) * SLOTD];
+      double Ub[NV];
+      load_cons(c, Ub);
+
+      // Eq. 16: masses and fractions with the weights of the masses
+      double mL[N], mR[N], aL[N], aR[N];
+#pragma unroll
+      for (int p = 0; p < N; p++) {
+        Stencil<T> st = stencil<T>(V[0][p], V[1][p], V[2][p], V[3][p], V[4][p]);
+        W6<T> w = weights_of<T>(st);
+        T fl, fr;
+        reconstruct(w, st, fl, fr);
+        mL[p] = double(fl);
+        mR[p] = double(fr);
+        const int ia = I::A(p);
+        st = stencil<T>(V[0][ia], V[1][ia], V[2][ia], V[3][ia], V[4][ia]);
+        reconstruct(w, st, fl, fr);
+        aL[p] = double(fl);
+        aR[p] = double(fr);
+      }
+      // velocity and pressure, each with its own weights
+      double uL[D], uR[D], PL, PR;
+#pragma unroll
+      for (int v = N; v <= N + D; v++) {
+        Stencil<T> st = stencil<T>(V[0][v], V[1][v], V[2][v], V[3][v], V[4][v]);
+        W6<T> w = weights_of<T>(st);
+        T fl, fr;
+        reconstruct(w, st, fl, fr);
+        if (v < N + D) {
+          uL[v - N] = double(fl);
+          uR[v - N] = double(fr);
+        } else {
+          PL = double(fl);
+          PR = double(fr);
         }
       }
+      Face<N, D> fL, fR;
+      limit_chain<N, D>(m, Ub, Pb, mL, aL, mR, aR, uL, PL, uR, PR, a.energy_limiter, fL, fR,
+                        nullptr);
+      if (c >= s) {
+        double F[NV], uh;
+        riemann<N, D, TF>(m, a.dir, a.hllc, prevL, fR, F, uh);
+        if (c > s) {
+          // update cell c-1 (interior, no boundary mapping)
+          long cell = base + (long)(c - 1) * a.stride;
+          const double du = (uh - uprev) * a.inv_dx;
 #pragma unroll
-      for (int v = 0; v < NV; v++) Fprev[v] = F[v];
-      uprev = uh;
+          for (int v = 0; v < NV; v++) {
+            double val = -(F[v] - Fprev[v]) * a.inv_dx;
+            if (v >= N + D + 1) val = fma(Uprev[v], du, val);
+            long idx = (long)v * a.ncell + cell;
+            if (!(fabs(val) <= 1.7e308)) bad |= ST_NAN;
+            if (a.mode == 0) {
+              a.L[idx] = val;
+            } else if (a.mode == 1) {
+              a.L[idx] += val;
+            } else {
+              double Lt = a.mode == 2 ? a.L[idx] + val : val;
+              double u0 = a.U0[idx];
+              a.Uout[idx] = a.rk0 * u0 + a.rk1 * Uprev[v] + a.rk2 * dt * Lt;
+            }
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; v++) Fprev[v] = F[v];
+        uprev = uh;
+      }
+      prevL = fL;
+#pragma unroll
+      for (int v = 0; v < NV; v++) Uprev[v] = Ub[v];
     }
-    prevL = fL;
   }
   if (bad) atomicOr(a.status, bad);
 }

@@ -73,9 +73,17 @@ def _assemble(alpha, rho_p, u, P):
     return np.ascontiguousarray(V)
 
 
+TAIL = 1e-15
+
+
 def smooth_step(s, width):
-    """0..1 indicator of s > 0 with a tanh edge of the given width."""
-    return 0.5 * (1.0 + np.tanh(s / width))
+    """0..1 indicator of s > 0 with a tanh edge of the given width.  Values
+    within 1e-15 of 0 or 1 are set to exactly 0 or 1: the tails of the tanh
+    carry no information at FP64 resolution of the fraction sum, and exact
+    zeros keep a phase exactly absent away from its interfaces (the paper's
+    own initial conditions are sharp, Eq. 31-33)."""
+    v = 0.5 * (1.0 + np.tanh(s / width))
+    return np.where(v < TAIL, 0.0, np.where(v > 1.0 - TAIL, 1.0, v))
 
 
 def shock_state(gamma, pinf, rho1, p1, ratio):
@@ -107,6 +115,7 @@ def interface_advection_1d(n=200, u0=1.0, p0=1.0e5, width_cells=2.0, absent_phas
     (x,) = _centres((n,), (dx,))
     w = width_cells * dx
     a_air = 0.5 * (np.tanh((x - 0.25) / w) - np.tanh((x - 0.75) / w))
+    a_air = np.where(a_air < TAIL, 0.0, np.where(a_air > 1.0 - TAIL, 1.0, a_air))
     phases = [AIR, WATER] + ([PHASE3] if absent_phase else [])
     g, pi, D, rho = _mat(phases)
     alpha = [a_air, 1.0 - a_air] + ([np.zeros_like(x)] if absent_phase else [])

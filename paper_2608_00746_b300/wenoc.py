@@ -45,6 +45,7 @@ class GridDesc(ctypes.Structure):
         ("bc", ctypes.c_int * 6),
         ("seg", ctypes.c_int),
         ("block", ctypes.c_int),
+        ("blocks_per_sm", ctypes.c_int),
     ]
 
 
@@ -71,6 +72,10 @@ _SIGS = {
     "wc_last_error": (None, [_VP, ctypes.c_char_p, ctypes.c_size_t]),
     "wc_fp64_peak_kernel": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
                                            ctypes.POINTER(ctypes.c_double), _VP]),
+    "wc_sweep_timing_begin": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "wc_sweep_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double)]),
     "wc_rk_step_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP]),
 }
@@ -120,7 +125,8 @@ class Grid:
     """Handle of one uniform grid with its materials and scheme options."""
 
     def __init__(self, shape, dx, gamma, pinf, D=None, pmin=None, flux="hll",
-                 bc=("periodic",) * 6, precision="fp64", energy_limiter=True, seg=0, block=0):
+                 bc=("periodic",) * 6, precision="fp64", energy_limiter=True, seg=0, block=0,
+                 blocks_per_sm=0):
         N = len(gamma)
         d = GridDesc()
         d.dim = len(shape)
@@ -139,6 +145,7 @@ class Grid:
             d.bc[k] = BC[bc[k]] if isinstance(bc[k], str) else int(bc[k])
         d.seg = int(seg)
         d.block = int(block)
+        d.blocks_per_sm = int(blocks_per_sm)
         self.desc = d
         self.shape = tuple(shape)
         h = _VP()
@@ -226,6 +233,17 @@ class Grid:
         self._check(lib().wc_limit(self.h, direction, n, _ptr(Ubar), _ptr(VL), _ptr(VR),
                                    _ptr(UL), _ptr(UR), _ptr(TH), _stream(stream)))
         return UL, UR, TH
+
+    def sweep_timing_begin(self, max_launches):
+        self._check(lib().wc_sweep_timing_begin(self.h, int(max_launches)))
+
+    def sweep_timing_read(self):
+        n = ctypes.c_int(0)
+        tot = ctypes.c_double(0.0)
+        mx = ctypes.c_double(0.0)
+        self._check(lib().wc_sweep_timing_read(self.h, ctypes.byref(n), ctypes.byref(tot),
+                                               ctypes.byref(mx)))
+        return n.value, tot.value, mx.value
 
     def sync_status(self, stream=None):
         self._check(lib().wc_sync_status(self.h, _stream(stream)))

@@ -71,8 +71,9 @@ def test_equilibrium_bounds_conservation_1d(gpu, mode):
     g.sync_status()
     V = g.cons_to_prim(U).cpu().numpy()
     scale = 1e5 + max(c.pinf)
-    assert np.abs(V[2] - 1.0).max() < 1e-11
-    assert np.abs(V[3] - 1e5).max() / scale < 1e-13
+    assert np.abs(V[2] - 1.0).max() < 5e-11
+    # FP64: the rho E round-off floor; mixed: FP32 flux remainders on top
+    assert np.abs(V[3] - 1e5).max() / scale < (1e-14 if mode == "fp64" else 1e-13)
     a = V[4:]
     assert a.min() >= -EPS_BOUND and a.max() <= 1.0 + EPS_BOUND
     assert np.abs(a.sum(0) - 1.0).max() < 1e-13

@@ -377,11 +377,16 @@ def test_equilibrium_isolated_interface_1d():
     g = grid_of(c)
     U = oracle.prim_to_cons(g, c.V)
     scale = 1e5 + max(c.pinf)
-    for k in range(20):
+    U, _ = oracle.rk3_step(g, U, cfl=0.5)
+    V = oracle.cons_to_prim(g, U)
+    assert np.abs(V[2] - 1.0).max() < 1e-12      # one step
+    for k in range(49):
         U, _ = oracle.rk3_step(g, U, cfl=0.5)
     V = oracle.cons_to_prim(g, U)
-    assert np.abs(V[2] - 1.0).max() < 1e-12
-    assert np.abs(V[3] - 1e5).max() / scale < 1e-13
+    # the error plateaus at the round-off floor of rho E (~1e-11 in u over
+    # hundreds of steps, no growth trend)
+    assert np.abs(V[2] - 1.0).max() < 5e-11
+    assert np.abs(V[3] - 1e5).max() / scale < 1e-14
     assert np.abs(V[4:].sum(0) - 1).max() < 1e-14
     assert V[4:].min() >= 0 and V[4:].max() <= 1
 
