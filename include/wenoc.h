@@ -159,6 +159,65 @@ wc_status wc_limit(const wc_grid *g, int dir, long ncell, const double *Ubar, co
 wc_status wc_rk_step_noalloc(wc_grid *g, double *U_dev, double cfl, double dt_fixed, int nsteps,
                              int *status_host, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched AMR-like patches.  npatch independent unit-cube patches, patch p
+ * with edge[p] cells per axis (cell size 1/edge[p]), 3-D, all sharing one set
+ * of materials.  Every face of every patch is an outflow boundary (zero-
+ * gradient boundary cells, three deep -- the stencil reach of WENO5 plus the
+ * neighbour face); the uniform-mesh operator is applied on each patch as on
+ * one level of a block-structured mesh (Sec. 3.5).  The pooled state is
+ * [NV][ncell_total] with patch p's cells at [offset(p), offset(p) + e^3)
+ * in x-fastest order.  One persistent launch per RK stage processes all
+ * patches; CTAs take whole patches, largest first. */
+typedef struct {
+  int nphase;
+  double gamma[WC_MAX_PHASE];
+  double pinf[WC_MAX_PHASE];
+  double D[WC_MAX_PHASE];
+  double pmin[WC_MAX_PHASE];
+  int flux;            /* WC_FLUX_HLL or WC_FLUX_HLLC */
+  int precision;       /* WC_PREC_FP64 or WC_PREC_MIXED */
+  int energy_limiter;  /* 1: Eq. 21 applied */
+  int npatch;
+} wc_patches_desc;
+
+typedef struct wc_patches wc_patches;
+
+/* Host only: copies desc and edges[npatch] (3..1024), builds offsets and the
+ * largest-first order. */
+wc_status wc_patches_init(const wc_patches_desc *desc, const int *edges, wc_patches **out);
+void wc_patches_destroy(wc_patches *g);
+long wc_patches_ncell(const wc_patches *g);
+long wc_patches_offset(const wc_patches *g, int patch);
+/* Four pooled state buffers (two stages, accumulator, autotune backup) plus
+ * the patch table. */
+size_t wc_patches_workspace_bytes(const wc_patches *g);
+/* Binds the pooled device state and workspace (256-byte aligned), uploads
+ * the patch table on stream and synchronises it. */
+wc_status wc_patches_set_state(wc_patches *g, double *U_dev, void *workspace_dev,
+                               size_t ws_bytes, void *stream);
+/* Schedule: threads per CTA (32/64/96/128), CTAs per SM (1..16), dynamic
+ * queue (1) or static round-robin (0). */
+wc_status wc_patches_set_schedule(wc_patches *g, int block, int ctas_per_sm, int dynamic);
+/* nsteps SSP-RK3 steps of every patch, one global dt (cfl, or dt_fixed > 0)
+ * from all patches.  use_graph = 1 captures one step (rate reduction, queue
+ * reset, three stage launches) into a CUDA graph on the first call and
+ * replays it; stream must then be a created stream, not the legacy default. */
+wc_status wc_patches_rk_step(wc_patches *g, double cfl, double dt_fixed, int nsteps,
+                             int use_graph, void *stream);
+/* psi_{V->U} (Eq. 26) on the pooled [NV][ncell_total] arrays. */
+wc_status wc_patches_prim_to_cons(const wc_patches *g, const double *V_dev, double *U_dev,
+                                  void *stream);
+/* dU/dt of every patch for the pooled state U_dev into L_dev (Eq. 3). */
+wc_status wc_patches_rhs(wc_patches *g, const double *U_dev, double *L_dev, void *stream);
+wc_status wc_patches_sync_status(wc_patches *g, void *stream);
+/* Times every candidate schedule (block 64/128 x CTAs per SM 2/3/4/6 x
+ * dynamic/static) over `steps` steps on a copy of the bound state (the state
+ * is restored), applies and returns the fastest. */
+wc_status wc_patches_autotune(wc_patches *g, double cfl, int steps, void *stream, int *block,
+                              int *ctas_per_sm, int *dynamic, double *ms_per_step);
+void wc_patches_last_error(const wc_patches *g, char *buf, size_t n);
+
 /* Sweep timing (tracing): after wc_sweep_timing_begin(g, max_launches) the
  * library records a CUDA event pair on the launch stream around each of the
  * next max_launches direction-sweep launches of g (events are created here,

@@ -75,10 +75,129 @@ struct Ring {
   static constexpr int BYTES = 5 * SLOTD * 8;          // per thread
 };
 
+// March through cells [s, e) of one pencil (first cell at index `base`,
+// step `a.stride`, `a.n` cells, boundary conditions a.bclo/a.bchi):
+// reconstruct, limit, solve the Riemann problems and update per a.mode.
+// `ring` is this thread's five-slot stencil ring in shared memory.
 template <int N, int D, typename T, typename TF>
-__global__ void __launch_bounds__(128) k_sweep(SweepArgs a, Mat m) {
+__device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, long base, int s,
+                                              int e, double* ring, double dt, unsigned& bad) {
   using I = Idx<N, D>;
   constexpr int NV = I::NV;
+  constexpr int SLOTD = Ring<N, D, T>::SLOTD;
+  // conservative values of cell c (boundary cells mapped, normal momentum
+  // negated behind reflective walls)
+  auto load_cons = [&](int c, double* u) {
+    bool flip;
+    int j = bc_index(c, a.n, a.bclo, a.bchi, flip);
+    long cell = base + (long)j * a.stride;
+#pragma unroll
+    for (int k = 0; k < NV; k++) u[k] = __ldg(a.U + (long)k * a.ncell + cell);
+    // sign flip of the normal momentum on the bit pattern (no FP64 op, no
+    // runtime-indexed register array)
+#pragma unroll
+    for (int jj = 0; jj < D; jj++) {
+      long long mask = (flip && jj == a.dir) ? (long long)0x8000000000000000ULL : 0LL;
+      u[I::U(jj)] = __longlong_as_double(__double_as_longlong(u[I::U(jj)]) ^ mask);
+    }
+  };
+  auto load = [&](int c) {
+    double u[NV], v[NV];
+    load_cons(c, u);
+    cons_to_prim<N, D>(m, u, v);
+    double* sl = ring + ((c + 15) % 5) * SLOTD;
+    sl[0] = v[I::E];
+    T* Vs = reinterpret_cast<T*>(sl + 1);
+#pragma unroll
+    for (int k = 0; k < NV; k++) Vs[k] = T(v[k]);
+  };
+
+  for (int c = s - 3; c <= s; c++) load(c);
+
+  Face<N, D> prevL;
+  double Fprev[NV], Uprev[NV];
+  double uprev = 0.0;
+  for (int c = s - 1; c <= e; c++) {
+    load(c + 2);
+    const T* V[5];
+#pragma unroll
+    for (int k = 0; k < 5; k++)
+      V[k] = reinterpret_cast<const T*>(ring + ((c - 2 + k + 15) % 5) * SLOTD + 1);
+    const double Pb = ring[((c + 15) % 5) * SLOTD];
+    double Ub[NV];
+    load_cons(c, Ub);
+
+    // Eq. 16: masses and fractions with the weights of the masses
+    double mL[N], mR[N], aL[N], aR[N];
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      Stencil<T> st = stencil<T>(V[0][p], V[1][p], V[2][p], V[3][p], V[4][p]);
+      W6<T> w = weights_of<T>(st);
+      T fl, fr;
+      reconstruct(w, st, fl, fr);
+      mL[p] = double(fl);
+      mR[p] = double(fr);
+      const int ia = I::A(p);
+      st = stencil<T>(V[0][ia], V[1][ia], V[2][ia], V[3][ia], V[4][ia]);
+      reconstruct(w, st, fl, fr);
+      aL[p] = double(fl);
+      aR[p] = double(fr);
+    }
+    // velocity and pressure, each with its own weights
+    double uL[D], uR[D], PL, PR;
+#pragma unroll
+    for (int v = N; v <= N + D; v++) {
+      Stencil<T> st = stencil<T>(V[0][v], V[1][v], V[2][v], V[3][v], V[4][v]);
+      W6<T> w = weights_of<T>(st);
+      T fl, fr;
+      reconstruct(w, st, fl, fr);
+      if (v < N + D) {
+        uL[v - N] = double(fl);
+        uR[v - N] = double(fr);
+      } else {
+        PL = double(fl);
+        PR = double(fr);
+      }
+    }
+    Face<N, D> fL, fR;
+    limit_chain<N, D>(m, Ub, Pb, mL, aL, mR, aR, uL, PL, uR, PR, a.energy_limiter, fL, fR,
+                      nullptr);
+    if (c >= s) {
+      double F[NV], uh;
+      riemann<N, D, TF>(m, a.dir, a.hllc, prevL, fR, F, uh);
+      if (c > s) {
+        // update cell c-1 (interior, no boundary mapping)
+        long cell = base + (long)(c - 1) * a.stride;
+        const double du = (uh - uprev) * a.inv_dx;
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          double val = -(F[v] - Fprev[v]) * a.inv_dx;
+          if (v >= N + D + 1) val = fma(Uprev[v], du, val);
+          long idx = (long)v * a.ncell + cell;
+          if (!(fabs(val) <= 1.7e308)) bad |= ST_NAN;
+          if (a.mode == 0) {
+            a.L[idx] = val;
+          } else if (a.mode == 1) {
+            a.L[idx] += val;
+          } else {
+            double Lt = a.mode == 2 ? a.L[idx] + val : val;
+            double u0 = a.U0[idx];
+            a.Uout[idx] = a.rk0 * u0 + a.rk1 * Uprev[v] + a.rk2 * dt * Lt;
+          }
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < NV; v++) Fprev[v] = F[v];
+      uprev = uh;
+    }
+    prevL = fL;
+#pragma unroll
+    for (int v = 0; v < NV; v++) Uprev[v] = Ub[v];
+  }
+}
+
+template <int N, int D, typename T, typename TF>
+__global__ void __launch_bounds__(128) k_sweep(SweepArgs a, Mat m) {
   constexpr int SLOTD = Ring<N, D, T>::SLOTD;
   extern __shared__ double smem[];
   double* ring = smem + (long)threadIdx.x * 5 * SLOTD;
@@ -100,116 +219,7 @@ __global__ void __launch_bounds__(128) k_sweep(SweepArgs a, Mat m) {
     else base = tr;
     const int s = sg * a.seg;
     const int e = min(s + a.seg, a.n);
-
-    // conservative values of cell c (boundary cells mapped, normal momentum
-    // negated behind reflective walls)
-    auto load_cons = [&](int c, double* u) {
-      bool flip;
-      int j = bc_index(c, a.n, a.bclo, a.bchi, flip);
-      long cell = base + (long)j * a.stride;
-#pragma unroll
-      for (int k = 0; k < NV; k++) u[k] = __ldg(a.U + (long)k * a.ncell + cell);
-      // sign flip of the normal momentum on the bit pattern (no FP64 op, no
-      // runtime-indexed register array)
-#pragma unroll
-      for (int jj = 0; jj < D; jj++) {
-        long long mask = (flip && jj == a.dir) ? (long long)0x8000000000000000ULL : 0LL;
-        u[I::U(jj)] = __longlong_as_double(__double_as_longlong(u[I::U(jj)]) ^ mask);
-      }
-    };
-    auto load = [&](int c) {
-      double u[NV], v[NV];
-      load_cons(c, u);
-      cons_to_prim<N, D>(m, u, v);
-      double* sl = ring + ((c + 15) % 5) * SLOTD;
-      sl[0] = v[I::E];
-      T* Vs = reinterpret_cast<T*>(sl + 1);
-#pragma unroll
-      for (int k = 0; k < NV; k++) Vs[k] = T(v[k]);
-    };
-
-    for (int c = s - 3; c <= s; c++) load(c);
-
-    Face<N, D> prevL;
-    double Fprev[NV], Uprev[NV];
-    double uprev = 0.0;
-    for (int c = s - 1; c <= e; c++) {
-      load(c + 2);
-      const T* V[5];
-#pragma unroll
-      for (int k = 0; k < 5; k++)
-        V[k] = reinterpret_cast<const T*>(ring + ((c - 2 + k + 15) % 5) * SLOTD + 1);
-      const double Pb = ring[((c + 15) % 5) * SLOTD];
-      double Ub[NV];
-      load_cons(c, Ub);
-
-      // Eq. 16: masses and fractions with the weights of the masses
-      double mL[N], mR[N], aL[N], aR[N];
-#pragma unroll
-      for (int p = 0; p < N; p++) {
-        Stencil<T> st = stencil<T>(V[0][p], V[1][p], V[2][p], V[3][p], V[4][p]);
-        W6<T> w = weights_of<T>(st);
-        T fl, fr;
-        reconstruct(w, st, fl, fr);
-        mL[p] = double(fl);
-        mR[p] = double(fr);
-        const int ia = I::A(p);
-        st = stencil<T>(V[0][ia], V[1][ia], V[2][ia], V[3][ia], V[4][ia]);
-        reconstruct(w, st, fl, fr);
-        aL[p] = double(fl);
-        aR[p] = double(fr);
-      }
-      // velocity and pressure, each with its own weights
-      double uL[D], uR[D], PL, PR;
-#pragma unroll
-      for (int v = N; v <= N + D; v++) {
-        Stencil<T> st = stencil<T>(V[0][v], V[1][v], V[2][v], V[3][v], V[4][v]);
-        W6<T> w = weights_of<T>(st);
-        T fl, fr;
-        reconstruct(w, st, fl, fr);
-        if (v < N + D) {
-          uL[v - N] = double(fl);
-          uR[v - N] = double(fr);
-        } else {
-          PL = double(fl);
-          PR = double(fr);
-        }
-      }
-      Face<N, D> fL, fR;
-      limit_chain<N, D>(m, Ub, Pb, mL, aL, mR, aR, uL, PL, uR, PR, a.energy_limiter, fL, fR,
-                        nullptr);
-      if (c >= s) {
-        double F[NV], uh;
-        riemann<N, D, TF>(m, a.dir, a.hllc, prevL, fR, F, uh);
-        if (c > s) {
-          // update cell c-1 (interior, no boundary mapping)
-          long cell = base + (long)(c - 1) * a.stride;
-          const double du = (uh - uprev) * a.inv_dx;
-#pragma unroll
-          for (int v = 0; v < NV; v++) {
-            double val = -(F[v] - Fprev[v]) * a.inv_dx;
-            if (v >= N + D + 1) val = fma(Uprev[v], du, val);
-            long idx = (long)v * a.ncell + cell;
-            if (!(fabs(val) <= 1.7e308)) bad |= ST_NAN;
-            if (a.mode == 0) {
-              a.L[idx] = val;
-            } else if (a.mode == 1) {
-              a.L[idx] += val;
-            } else {
-              double Lt = a.mode == 2 ? a.L[idx] + val : val;
-              double u0 = a.U0[idx];
-              a.Uout[idx] = a.rk0 * u0 + a.rk1 * Uprev[v] + a.rk2 * dt * Lt;
-            }
-          }
-        }
-#pragma unroll
-        for (int v = 0; v < NV; v++) Fprev[v] = F[v];
-        uprev = uh;
-      }
-      prevL = fL;
-#pragma unroll
-      for (int v = 0; v < NV; v++) Uprev[v] = Ub[v];
-    }
+    sweep_segment<N, D, T, TF>(a, m, base, s, e, ring, dt, bad);
   }
   if (bad) atomicOr(a.status, bad);
 }

@@ -49,6 +49,20 @@ class GridDesc(ctypes.Structure):
     ]
 
 
+class PatchesDesc(ctypes.Structure):
+    _fields_ = [
+        ("nphase", ctypes.c_int),
+        ("gamma", ctypes.c_double * MAX_PHASE),
+        ("pinf", ctypes.c_double * MAX_PHASE),
+        ("D", ctypes.c_double * MAX_PHASE),
+        ("pmin", ctypes.c_double * MAX_PHASE),
+        ("flux", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("energy_limiter", ctypes.c_int),
+        ("npatch", ctypes.c_int),
+    ]
+
+
 # name -> (restype, argtypes)
 _VP = ctypes.c_void_p
 _SIGS = {
@@ -76,6 +90,25 @@ _SIGS = {
     "wc_sweep_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double)]),
+    "wc_patches_init": (ctypes.c_int, [ctypes.POINTER(PatchesDesc), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(_VP)]),
+    "wc_patches_destroy": (None, [_VP]),
+    "wc_patches_ncell": (ctypes.c_long, [_VP]),
+    "wc_patches_offset": (ctypes.c_long, [_VP, ctypes.c_int]),
+    "wc_patches_workspace_bytes": (ctypes.c_size_t, [_VP]),
+    "wc_patches_set_state": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "wc_patches_set_schedule": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "wc_patches_rk_step": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_int, _VP]),
+    "wc_patches_rhs": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "wc_patches_prim_to_cons": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "wc_patches_sync_status": (ctypes.c_int, [_VP, _VP]),
+    "wc_patches_autotune": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int, _VP,
+                                           ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "wc_patches_last_error": (None, [_VP, ctypes.c_char_p, ctypes.c_size_t]),
     "wc_rk_step_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP]),
 }
@@ -268,3 +301,95 @@ def fp64_peak(blocks=148 * 8, threads=256, iters=20000, reps=5):
         if r > 0:
             best = max(best, fl.value / (e0.elapsed_time(e1) * 1e-3))
     return best
+
+
+class Patches:
+    """Batched independent cube patches (pooled state, one persistent launch
+    per Runge-Kutta stage)."""
+
+    def __init__(self, edges, gamma, pinf, D=None, pmin=None, flux="hll", precision="mixed",
+                 energy_limiter=True):
+        N = len(gamma)
+        d = PatchesDesc()
+        d.nphase = N
+        D = list(D) if D is not None else [0.0] * N
+        pmin = list(pmin) if pmin is not None else default_pmin(pinf)
+        for p in range(N):
+            d.gamma[p], d.pinf[p], d.D[p], d.pmin[p] = gamma[p], pinf[p], D[p], pmin[p]
+        d.flux = FLUX[flux]
+        d.precision = PREC[precision]
+        d.energy_limiter = int(bool(energy_limiter))
+        d.npatch = len(edges)
+        self.edges = [int(e) for e in edges]
+        arr = (ctypes.c_int * len(edges))(*self.edges)
+        h = _VP()
+        st = lib().wc_patches_init(ctypes.byref(d), arr, ctypes.byref(h))
+        if st != 0:
+            raise WcError(st, "wc_patches_init")
+        self.h = h
+        self.nv = 2 * N + 4
+        self.ncell = lib().wc_patches_ncell(h)
+        self.offsets = [lib().wc_patches_offset(h, p) for p in range(len(edges))]
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and _lib is not None:
+            _lib.wc_patches_destroy(h)
+            self.h = None
+
+    def _check(self, st):
+        if st != 0:
+            buf = ctypes.create_string_buffer(256)
+            lib().wc_patches_last_error(self.h, buf, 256)
+            raise WcError(st, buf.value.decode())
+
+    def pack(self, states):
+        """Pooled [NV][ncell] array (host numpy) from per-patch [NV][e][e][e]."""
+        import numpy as np
+        out = np.empty((self.nv, self.ncell))
+        for p, S in enumerate(states):
+            o = self.offsets[p]
+            out[:, o:o + S[0].size] = S.reshape(self.nv, -1)
+        return out
+
+    def unpack(self, pooled, p):
+        e = self.edges[p]
+        o = self.offsets[p]
+        return pooled[:, o:o + e ** 3].reshape(self.nv, e, e, e)
+
+    def bind(self, U, stream=None):
+        n = (lib().wc_patches_workspace_bytes(self.h) + 7) // 8
+        self.ws = torch.empty(n, dtype=torch.float64, device=U.device)
+        self.U = U
+        self._check(lib().wc_patches_set_state(self.h, _ptr(U), _ptr(self.ws), n * 8,
+                                               _stream(stream)))
+        return self
+
+    def set_schedule(self, block, ctas_per_sm, dynamic):
+        self._check(lib().wc_patches_set_schedule(self.h, block, ctas_per_sm, int(dynamic)))
+
+    def rk_step(self, cfl=0.0, dt=0.0, nsteps=1, use_graph=False, stream=None):
+        self._check(lib().wc_patches_rk_step(self.h, float(cfl), float(dt), int(nsteps),
+                                             int(use_graph), _stream(stream)))
+
+    def prim_to_cons(self, V, U=None, stream=None):
+        U = torch.empty_like(V) if U is None else U
+        self._check(lib().wc_patches_prim_to_cons(self.h, _ptr(V), _ptr(U), _stream(stream)))
+        return U
+
+    def rhs(self, U, L=None, stream=None):
+        L = torch.empty_like(U) if L is None else L
+        self._check(lib().wc_patches_rhs(self.h, _ptr(U), _ptr(L), _stream(stream)))
+        return L
+
+    def sync_status(self, stream=None):
+        self._check(lib().wc_patches_sync_status(self.h, _stream(stream)))
+
+    def autotune(self, cfl, steps=3, stream=None):
+        b, c, d = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        ms = ctypes.c_double(0.0)
+        self._check(lib().wc_patches_autotune(self.h, float(cfl), int(steps), _stream(stream),
+                                              ctypes.byref(b), ctypes.byref(c),
+                                              ctypes.byref(d), ctypes.byref(ms)))
+        return {"block": b.value, "ctas_per_sm": c.value, "dynamic": d.value,
+                "ms_per_step": ms.value}

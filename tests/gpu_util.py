@@ -40,28 +40,43 @@ def groups(N, d):
     return g + [[N + d + 1 + p] for p in range(N)]
 
 
-def state_err(A, B, N, d):
-    """max |A - B| over a group / max |B| over that group, per variable."""
+def momentum_floor(go, U):
+    """Acoustic momentum scale max(rho c) of a state: the momentum group's
+    scale when the fluid is (nearly) at rest."""
+    N = go.N
+    rho = np.asarray(U)[:N].sum(0)
+    return float((rho * oracle.sound_speed(go, U)).max())
+
+
+def state_err(A, B, N, d, mom_floor=0.0):
+    """max |A - B| over a group / max |B| over that group, per variable; the
+    momentum group's scale is at least mom_floor."""
     A = np.asarray(A).reshape(A.shape[0], -1)
     B = np.asarray(B).reshape(B.shape[0], -1)
     out = np.zeros(B.shape[0])
     for grp in groups(N, d):
         scale = np.abs(B[grp]).max()
+        if grp[0] == N:
+            scale = max(scale, mom_floor)
         for v in grp:
             d_ = np.abs(A[v] - B[v]).max()
             out[v] = d_ / scale if scale > 0 else d_
     return out
 
 
-def rhs_err(L, L_or, U, rate, N, d):
+def rhs_err(L, L_or, U, rate, N, d, mom_floor=0.0):
     """dU/dt error over one CFL-1 time step (dt = 1/rate) relative to the
-    group's state magnitude: max |L - L_or| dt / max |U|."""
+    group's state magnitude: max |L - L_or| dt / max |U| (momentum scale at
+    least mom_floor)."""
     L = np.asarray(L).reshape(L.shape[0], -1)
     L_or = np.asarray(L_or).reshape(L_or.shape[0], -1)
     U = np.asarray(U).reshape(U.shape[0], -1)
     out = np.zeros(U.shape[0])
     for grp in groups(N, d):
-        scale = np.abs(U[grp]).max() * rate
+        scale = np.abs(U[grp]).max()
+        if grp[0] == N:
+            scale = max(scale, mom_floor)
+        scale *= rate
         for v in grp:
             d_ = np.abs(L[v] - L_or[v]).max()
             out[v] = d_ / scale if scale > 0 else d_

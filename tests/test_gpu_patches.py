@@ -1,0 +1,118 @@
+"""Batched AMR-like patches (config-4 shape, reduced count): every patch
+against the FP64 oracle run on that patch as its own grid (outflow
+boundaries, cell size 1/edge), one persistent launch per stage, graph
+capture, schedules and the autotuner."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2608_00746_b300 import inputs, wenoc
+
+from gpu_util import l1_group, momentum_floor, rhs_err, state_err, to_dev
+
+pytestmark = pytest.mark.gpu
+N, D = 3, 3
+
+
+def batch(npatch=24, seed=3):
+    edges, states, (g, pi, Dm) = inputs.patch_batch(npatch=npatch, seed=seed)
+    return [int(e) for e in edges], states, g, pi, Dm
+
+
+def oracle_grid(e, g, pi, Dm):
+    return oracle.Grid((e, e, e), (1.0 / e,) * 3, g, pi, Dm, flux="hll", bc=("outflow",) * 6)
+
+
+def pooled_cons(P, edges, states, g, pi, Dm):
+    Us = [oracle.prim_to_cons(oracle_grid(e, g, pi, Dm), S) for e, S in zip(edges, states)]
+    return P.pack(Us), Us
+
+
+def test_patch_rhs_parity_fp64(gpu):
+    edges, states, g, pi, Dm = batch()
+    assert set(edges) == {8, 12, 16, 24, 32} or len(set(edges)) >= 3
+    P = wenoc.Patches(edges, g, pi, Dm, precision="fp64")
+    U, Us = pooled_cons(P, edges, states, g, pi, Dm)
+    Ud = to_dev(U)
+    P.bind(Ud)
+    L = P.rhs(Ud).cpu().numpy()
+    P.sync_status()
+    for p, e in enumerate(edges):
+        go = oracle_grid(e, g, pi, Dm)
+        L_or = oracle.rhs(go, Us[p])
+        err = rhs_err(P.unpack(L, p), L_or, Us[p], oracle.max_rate(go, Us[p]), N, D,
+                      mom_floor=momentum_floor(go, Us[p]))
+        assert (err <= 1e-12).all(), (p, e, err)
+
+
+def test_patch_rk_parity_fp64_graph_and_schedules(gpu):
+    edges, states, g, pi, Dm = batch(npatch=16, seed=5)
+    P = wenoc.Patches(edges, g, pi, Dm, precision="fp64")
+    U, Us = pooled_cons(P, edges, states, g, pi, Dm)
+    grids = [oracle_grid(e, g, pi, Dm) for e in edges]
+    # global dt: cfl / max over patches of the CFL rate
+    rate = max(oracle.max_rate(go, Up) for go, Up in zip(grids, Us))
+    dt = 0.2 / rate
+    outs = []
+    s = torch.cuda.Stream()
+    for sched, graph in [((64, 4, 1), False), ((128, 2, 0), False), ((64, 3, 1), True)]:
+        Ud = to_dev(U)
+        with torch.cuda.stream(s):
+            P.bind(Ud, stream=s)
+            P.set_schedule(*sched)
+            P.rk_step(dt=dt, nsteps=2, use_graph=graph, stream=s)
+        s.synchronize()
+        P.sync_status(stream=s)
+        outs.append(Ud.cpu().numpy())
+    # the CFL time step computed on the device over all patches (first step)
+    Uc = to_dev(U)
+    with torch.cuda.stream(s):
+        P.bind(Uc, stream=s)
+        P.rk_step(cfl=0.2, nsteps=1, use_graph=True, stream=s)
+    s.synchronize()
+    U1 = Uc.cpu().numpy()
+    for p, (go, Up) in enumerate(zip(grids, Us)):
+        Uo, _ = oracle.rk3_step(go, Up, dt=dt)
+        assert (state_err(P.unpack(U1, p), Uo, N, D, mom_floor=momentum_floor(go, Uo))
+                <= 1e-12).all()
+    # bit-identical whatever the schedule or the graph
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    for p, (go, Up) in enumerate(zip(grids, Us)):
+        Uo = Up
+        for _ in range(2):
+            Uo, _ = oracle.rk3_step(go, Uo, dt=dt)
+        err = state_err(P.unpack(outs[0], p), Uo, N, D, mom_floor=momentum_floor(go, Uo))
+        assert (err <= 1e-12).all(), (p, err)
+
+
+def test_patch_mixed_l1_and_bounds(gpu):
+    edges, states, g, pi, Dm = batch(npatch=12, seed=7)
+    P64 = wenoc.Patches(edges, g, pi, Dm, precision="fp64")
+    Pmx = wenoc.Patches(edges, g, pi, Dm, precision="mixed")
+    U, _ = pooled_cons(P64, edges, states, g, pi, Dm)
+    A, B = to_dev(U), to_dev(U)
+    P64.bind(A)
+    Pmx.bind(B)
+    for _ in range(5):
+        P64.rk_step(dt=2e-7)
+        Pmx.rk_step(dt=2e-7)
+    torch.cuda.synchronize()
+    P64.sync_status()
+    Pmx.sync_status()
+    a, b = A.cpu().numpy(), B.cpu().numpy()
+    assert (l1_group(b, a, N, D) <= 1e-5).all()
+    frac = b[N + D + 1:]
+    assert frac.min() >= -4 * 2.0 ** -52 and frac.max() <= 1 + 4 * 2.0 ** -52
+
+
+def test_patch_autotune_restores_state(gpu):
+    edges, states, g, pi, Dm = batch(npatch=40, seed=9)
+    P = wenoc.Patches(edges, g, pi, Dm, precision="mixed")
+    U, _ = pooled_cons(P, edges, states, g, pi, Dm)
+    Ud = to_dev(U)
+    P.bind(Ud)
+    best = P.autotune(cfl=0.2, steps=1)
+    assert best["block"] in (64, 128) and best["ctas_per_sm"] in (2, 3, 4, 6)
+    assert best["ms_per_step"] > 0
+    assert np.array_equal(Ud.cpu().numpy(), U)
