@@ -110,6 +110,18 @@ wc_status wc_cons_to_prim(const wc_grid *g, const double *U_dev, double *V_dev, 
  * state), summed over the directions; L_dev is overwritten. */
 wc_status wc_rhs(wc_grid *g, const double *U_dev, double *L_dev, void *stream);
 
+/* L = dU/dt of the Phase-Field step (Eq. 5), + div F^PF, for the state U_dev
+ * and the auxiliary fields Q_dev [N][ncell] of Eq. 4 (given; the Q-map solve
+ * is not part of this library).  Face gradients are central differences of
+ * Q; the face states are the WENO-C reconstructions of U.  The numerical
+ * flux (not printed in the paper, which cites it) is the bound-preserving
+ * upwinding J_p = max(G,0) a_R (1-a_L) + min(G,0) a_L (1-a_R) of
+ * phi_p (1 - phi_p) grad Q_p, masses alike with (alpha rho)_p in the outgoing
+ * factor, corrected to sum_p J_p = 0 in proportion to the face fractions;
+ * momentum and energy as in the last line of Eq. 1. */
+wc_status wc_rhs_pf(wc_grid *g, const double *U_dev, const double *Q_dev, double *L_dev,
+                    void *stream);
+
 /* Time step from the bound state: dt = cfl / max_cells sum_d (|u_d| + c)/dx_d,
  * written to dt_dev (one double, device). */
 wc_status wc_compute_dt(wc_grid *g, double cfl, double *dt_dev, void *stream);

@@ -68,6 +68,8 @@ def lib():
         for name, args in {
             "or_rhs": [gp, dp, dp],
             "or_rk3_step": [gp, dp, ctypes.c_double, ctypes.c_double, dp],
+            "or_pf_rhs": [gp, dp, dp, dp],
+            "or_pf_flux": [gp, ctypes.c_int, dp, dp, dp, dp, dp, dp],
             "or_faces": [gp, ctypes.c_int, dp, dp, dp, dp],
             "or_limit": [gp, ctypes.c_long, dp, dp, dp, dp, dp, dp],
             "or_cons_to_prim": [gp, ctypes.c_long, dp, dp],
@@ -185,6 +187,22 @@ def rhs(g: Grid, U: np.ndarray) -> np.ndarray:
     L = np.empty_like(U)
     _check(lib().or_rhs(g.ref(), _p(U), _p(L)), "or_rhs")
     return L
+
+
+def pf_rhs(g: Grid, U: np.ndarray, Q: np.ndarray) -> np.ndarray:
+    """dU/dt of the Phase-Field step (Eq. 5) for the auxiliary fields Q [N][...]."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    L = np.empty_like(U)
+    _check(lib().or_pf_rhs(g.ref(), _p(U), _p(Q), _p(L)), "or_pf_rhs")
+    return L
+
+
+def pf_flux(g: Grid, direction, UL, VL, UR, VR, G):
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (UL, VL, UR, VR, G)]
+    F = np.empty(g.nv)
+    lib().or_pf_flux(g.ref(), direction, *[_p(a) for a in arrs], _p(F))
+    return F
 
 
 def rk3_step(g: Grid, U: np.ndarray, cfl: float = 0.5, dt: float = 0.0):

@@ -40,6 +40,17 @@
  *  R9  Boundary cells: periodic copy; reflective mirror with the normal
  *      momentum negated; outflow zero-gradient copy.
  *  R10 Time step dt = CFL / max_cells sum_d (|u_d| + c) / dx_d, taken from U^n.
+ *  R12 Phase-Field flux of Eq. 5 (its numerical form is not printed in the
+ *      paper; parity unpinned beyond its invariants).  Given Q_p at cells,
+ *      G_p = (Q_{p,R} - Q_{p,L})/dx at the face; with J_p = phi_p(1-phi_p)
+ *      grad Q_p (implied by Eq. 4) discretised bound-preservingly as
+ *      J_p = max(G_p,0) a_R (1 - a_L) + min(G_p,0) a_L (1 - a_R), the mass flux
+ *      is the same with (alpha rho) in the outgoing factor, then
+ *      sum_p J_p = 0 is enforced by removing sum_q J_q in proportion to the
+ *      face fractions (a_L + a_R)/2 (masses with (alpha rho)_face); momentum
+ *      and energy follow Eq. 1: sum_p F^{m_p} u_face and
+ *      sum_p [F^{m_p} |u|^2/2 + F^{a_p} (A_p P + B_p) + D_p F^{m_p}], u_face and
+ *      P_face the averages of the two face states.
  *  R11 Eq. 19 assumes S > 0.  When the positivity step has limited every
  *      fraction of a face to zero (S = 0) the cell keeps its averages on both
  *      faces (theta = 0, first order) for the masses and the fractions.
@@ -552,6 +563,52 @@ static int rhs_dir(const or_grid *g, int dir, const double *U, double *Lout) {
   return err;
 }
 
+/* R12: Phase-Field flux at one face (Eq. 5), direction dir, from the face
+ * states (UL, VL) of the left cell and (UR, VR) of the right cell and the face
+ * gradients G[p] of Q_p.  F is the flux vector of Eq. 1 (last line). */
+void or_pf_flux(const or_grid *g, int dir, const double *UL, const double *VL, const double *UR,
+                const double *VR, const double *G, double *F) {
+  int N = g->N, d = g->dim, nvar = nv(g);
+  double J[OR_MAXP], M[OR_MAXP];
+  double sumJ = 0.0, suma = 0.0;
+  for (int p = 0; p < N; p++) {
+    double aL = UL[IALF(g, p)], aR = UR[IALF(g, p)];
+    double mL = UL[IMASS(p)], mR = UR[IMASS(p)];
+    double gp = G[p] > 0.0 ? G[p] : 0.0, gm = G[p] < 0.0 ? G[p] : 0.0;
+    J[p] = gp * aR * (1.0 - aL) + gm * aL * (1.0 - aR);
+    M[p] = gp * mR * (1.0 - aL) + gm * mL * (1.0 - aR);
+    sumJ += J[p];
+    suma += 0.5 * (aL + aR);
+  }
+  for (int p = 0; p < N; p++) {
+    double af = 0.5 * (UL[IALF(g, p)] + UR[IALF(g, p)]);
+    double mf = 0.5 * (UL[IMASS(p)] + UR[IMASS(p)]);
+    J[p] = J[p] - sumJ * af / suma;
+    M[p] = M[p] - sumJ * mf / suma;
+  }
+  for (int v = 0; v < nvar; v++) F[v] = 0.0;
+  double P = 0.5 * (VL[IENE(g)] + VR[IENE(g)]);
+  double uu = 0.0;
+  double u[3];
+  for (int j = 0; j < d; j++) {
+    u[j] = 0.5 * (VL[IMOM(g, j)] + VR[IMOM(g, j)]);
+    uu += u[j] * u[j];
+  }
+  double msum = 0.0, e = 0.0;
+  for (int p = 0; p < N; p++) {
+    F[IMASS(p)] = M[p];
+    F[IALF(g, p)] = J[p];
+    msum += M[p];
+    e += J[p] * (eos_A(g, p) * P + eos_B(g, p)) + g->D[p] * M[p];
+  }
+  for (int j = 0; j < d; j++) F[IMOM(g, j)] = msum * u[j];
+  F[IENE(g)] = msum * 0.5 * uu + e;
+  (void)dir;
+}
+
+/* dU/dt of the Phase-Field step (Eq. 5) for Q [N][cells]: +sum_d dF^PF/dx_d. */
+int or_pf_rhs(const or_grid *g, const double *U, const double *Q, double *L);
+
 static int check_grid(const or_grid *g) {
   if (g->dim < 1 || g->dim > 3 || g->N < 1 || g->N > OR_MAXP) return OR_ERR_ARG;
   for (int a = 0; a < 3; a++) {
@@ -575,6 +632,50 @@ int or_rhs(const or_grid *g, const double *U, double *L) {
   for (long k = 0; k < tot; k++)
     if (!isfinite(L[k])) return OR_ERR_NAN;
   return OR_OK;
+}
+
+int or_pf_rhs(const or_grid *g, const double *U, const double *Q, double *L) {
+  int e = check_grid(g);
+  if (e) return e;
+  int nvar = nv(g), N = g->N;
+  long nc = ncells(g);
+  for (long k = 0; k < nc * nvar; k++) L[k] = 0.0;
+  for (int dir = 0; dir < g->dim; dir++) {
+    int n = g->n[dir];
+    long stride = dir == 0 ? 1 : (dir == 1 ? g->n[0] : (long)g->n[0] * g->n[1]);
+    long npencil = nc / n;
+    double dx = g->dx[dir];
+    double *FLs = malloc(sizeof(double) * nvar * (n + 2));
+    double *FRs = malloc(sizeof(double) * nvar * (n + 2));
+    double *VLs = malloc(sizeof(double) * nvar * (n + 2));
+    double *VRs = malloc(sizeof(double) * nvar * (n + 2));
+    double *Fx = malloc(sizeof(double) * nvar * (n + 1));
+    for (long pc = 0; pc < npencil && !e; pc++) {
+      long base;
+      if (dir == 0) base = pc * n;
+      else if (dir == 1) base = (pc / g->n[0]) * ((long)g->n[0] * n) + pc % g->n[0];
+      else base = pc;
+      e = pencil_faces(g, dir, U, base, stride, FLs, FRs, VLs, VRs, NULL);
+      for (int m = 0; m <= n && !e; m++) {
+        /* face between cells m-1 and m; Q of the two cells (boundary mapped) */
+        int f1, f2;
+        int jl = bc_map(m - 1, n, g->bc[2 * dir], g->bc[2 * dir + 1], &f1);
+        int jr = bc_map(m, n, g->bc[2 * dir], g->bc[2 * dir + 1], &f2);
+        double G[OR_MAXP];
+        for (int p = 0; p < N; p++)
+          G[p] = (Q[(long)p * nc + base + jr * stride] - Q[(long)p * nc + base + jl * stride]) / dx;
+        or_pf_flux(g, dir, FLs + m * nvar, VLs + m * nvar, FRs + (m + 1) * nvar,
+                   VRs + (m + 1) * nvar, G, Fx + m * nvar);
+      }
+      for (int m = 0; m < n && !e; m++) {
+        long cell = base + m * stride;
+        for (int v = 0; v < nvar; v++)
+          L[v * nc + cell] += (Fx[(m + 1) * nvar + v] - Fx[m * nvar + v]) / dx;
+      }
+    }
+    free(FLs); free(FRs); free(VLs); free(VRs); free(Fx);
+  }
+  return e;
 }
 
 /* Limited face states of every interior cell along dir (for the pins):

@@ -322,6 +322,21 @@ extern "C" wc_status wc_rhs(wc_grid* g, const double* U, double* L, void* stream
   return WC_OK;
 }
 
+extern "C" wc_status wc_rhs_pf(wc_grid* g, const double* U, const double* Q, double* L,
+                               void* stream) {
+  if (!g || !U || !Q || !L) return WC_ERR_ARG;
+  if (!g->status) return fail(g, WC_ERR_STATE, "wc_rhs_pf needs a bound workspace (status word)");
+  for (int dir = 0; dir < g->d.dim; dir++) {
+    SweepArgs a = make_args(g, dir, U, L);
+    a.mode = dir == 0 ? 0 : 1;
+    a.kind = 1;
+    a.Q = Q;
+    cudaError_t e = launch(g, a, S(stream));
+    if (e != cudaSuccess) return cuda_fail(g, e, "pf sweep");
+  }
+  return WC_OK;
+}
+
 static wc_status launch_rate(wc_grid* g, const double* U, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(g->rate, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return cuda_fail(g, e, "memset");

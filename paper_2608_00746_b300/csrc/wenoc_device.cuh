@@ -708,4 +708,55 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
   F[I::E] = fma(0.5 * ub2, Frho, fe);
 }
 
+// ------------------------------------------------------------------ Phase-Field flux
+// Numerical Phase-Field flux of Eq. 5 at the face between L (from cell i) and
+// R (from cell i+1), given the face gradients G[p] = (Q_{p,i+1} - Q_{p,i})/dx
+// of the auxiliary variables of Eq. 4.  J_p = phi_p (1 - phi_p) grad Q_p is
+// upwinded so that it takes phase p only from the side that has it and gives
+// it only to the side with room for it:
+//   J_p = max(G_p,0) a_R (1 - a_L) + min(G_p,0) a_L (1 - a_R),
+// the mass flux has (alpha rho)_p in the outgoing factor (consistent with
+// the fractions), and sum_p J_p = 0 is restored by removing sum_q J_q in
+// proportion to the face fractions (masses in proportion to the face
+// masses), which leaves an absent phase untouched.  Momentum and energy
+// follow the last line of Eq. 1 with the mean face velocity and pressure.
+template <int N, int D>
+__device__ __forceinline__ void pf_flux(const Mat& m, const Face<N, D>& L, const Face<N, D>& R,
+                                        const double* G, double* F) {
+  using I = Idx<N, D>;
+  double J[N], M[N];
+  double sumJ = 0.0, suma = 0.0;
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    const double aL = L.U[I::A(p)], aR = R.U[I::A(p)];
+    const double gp = fmax(G[p], 0.0), gm = fmin(G[p], 0.0);
+    J[p] = gp * aR * (1.0 - aL) + gm * aL * (1.0 - aR);
+    M[p] = gp * R.U[p] * (1.0 - aL) + gm * L.U[p] * (1.0 - aR);
+    sumJ += J[p];
+    suma += 0.5 * (aL + aR);
+  }
+  const double r = sumJ / suma;
+  double msum = 0.0, e = 0.0;
+  const double P = 0.5 * (L.P + R.P);
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    J[p] -= r * (0.5 * (L.U[I::A(p)] + R.U[I::A(p)]));
+    M[p] -= r * (0.5 * (L.U[p] + R.U[p]));
+    F[p] = M[p];
+    F[I::A(p)] = J[p];
+    msum += M[p];
+    e = fma(J[p], fma(m.A[p], P, m.B[p]), e);
+    if (m.hasD) e = fma(m.D[p], M[p], e);
+  }
+  double uu = 0.0;
+#pragma unroll
+  for (int j = 0; j < D; j++) {
+    const double u = 0.5 * (L.u[j] + R.u[j]);
+    F[I::U(j)] = msum * u;
+    uu = fma(u, u, uu);
+  }
+  F[I::E] = fma(msum, 0.5 * uu, e);
+}
+
 }  // namespace wc
+

@@ -80,6 +80,8 @@ __global__ void __launch_bounds__(128) k_patch_stage(PatchArgs pa, Mat m) {
       a.nseg = 1;
       a.seg = e;
       a.max_threads = 0;
+      a.Q = nullptr;
+      a.kind = 0;
       a.inv_dx = (double)e;  // unit-cube patch: dx = 1/e
       a.bclo = a.bchi = BC_OUTFLOW;
       if (pa.rhs_only) a.mode = dir == 0 ? 0 : 1;

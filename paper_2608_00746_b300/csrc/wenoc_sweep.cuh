@@ -32,6 +32,8 @@ struct SweepArgs {
   long npencil;        // ncell / n
   int nseg, seg;       // segments per pencil, cells per segment
   long max_threads;    // launch size cap (whole blocks per SM); items loop beyond it
+  const double* Q;     // Phase-Field auxiliary fields [N][ncell] (kind 1)
+  int kind;            // 0: hyperbolic step (Eq. 3); 1: Phase-Field step (Eq. 5)
   double inv_dx;
   int bclo, bchi;
   int mode;            // 0: L = dir part; 1: L += dir part; 2: stage with L + dir part; 3: stage with dir part only
@@ -117,6 +119,15 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
   Face<N, D> prevL;
   double Fprev[NV], Uprev[NV];
   double uprev = 0.0;
+  double Qprev[N], Qcur[N];
+  auto load_q = [&](int c, double* q) {
+    bool flip;
+    int j = bc_index(c, a.n, a.bclo, a.bchi, flip);
+    long cell = base + (long)j * a.stride;
+#pragma unroll
+    for (int p = 0; p < N; p++) q[p] = __ldg(a.Q + (long)p * a.ncell + cell);
+  };
+  if (a.kind == 1) load_q(s - 1, Qprev);
   for (int c = s - 1; c <= e; c++) {
     load(c + 2);
     const T* V[5];
@@ -162,17 +173,26 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
     Face<N, D> fL, fR;
     limit_chain<N, D>(m, Ub, Pb, mL, aL, mR, aR, uL, PL, uR, PR, a.energy_limiter, fL, fR,
                       nullptr);
+    if (a.kind == 1) load_q(c, Qcur);
     if (c >= s) {
-      double F[NV], uh;
-      riemann<N, D, TF>(m, a.dir, a.hllc, prevL, fR, F, uh);
+      double F[NV], uh = 0.0;
+      if (a.kind == 1) {
+        double G[N];
+#pragma unroll
+        for (int p = 0; p < N; p++) G[p] = (Qcur[p] - Qprev[p]) * a.inv_dx;
+        pf_flux<N, D>(m, prevL, fR, G, F);
+      } else {
+        riemann<N, D, TF>(m, a.dir, a.hllc, prevL, fR, F, uh);
+      }
       if (c > s) {
         // update cell c-1 (interior, no boundary mapping)
         long cell = base + (long)(c - 1) * a.stride;
         const double du = (uh - uprev) * a.inv_dx;
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-          double val = -(F[v] - Fprev[v]) * a.inv_dx;
-          if (v >= N + D + 1) val = fma(Uprev[v], du, val);
+          // Eq. 3: -div F + alpha (1 + K) div u_hat;  Eq. 5: +div F^PF
+          double val = (a.kind == 1 ? 1.0 : -1.0) * (F[v] - Fprev[v]) * a.inv_dx;
+          if (a.kind == 0 && v >= N + D + 1) val = fma(Uprev[v], du, val);
           long idx = (long)v * a.ncell + cell;
           if (!(fabs(val) <= 1.7e308)) bad |= ST_NAN;
           if (a.mode == 0) {
@@ -193,6 +213,10 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
     prevL = fL;
 #pragma unroll
     for (int v = 0; v < NV; v++) Uprev[v] = Ub[v];
+    if (a.kind == 1) {
+#pragma unroll
+      for (int p = 0; p < N; p++) Qprev[p] = Qcur[p];
+    }
   }
 }
 

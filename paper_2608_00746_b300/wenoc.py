@@ -78,6 +78,7 @@ _SIGS = {
     "wc_cons_to_prim": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "wc_rhs": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "wc_compute_dt": (ctypes.c_int, [_VP, ctypes.c_double, _VP, _VP]),
+    "wc_rhs_pf": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "wc_rk_step": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_double), _VP]),
     "wc_limit": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_long, _VP, _VP, _VP, _VP, _VP, _VP,
@@ -237,6 +238,12 @@ class Grid:
     def rhs(self, U, L=None, stream=None):
         L = torch.empty_like(U) if L is None else L
         self._check(lib().wc_rhs(self.h, _ptr(U), _ptr(L), _stream(stream)))
+        return L
+
+    def rhs_pf(self, U, Q, L=None, stream=None):
+        """Phase-Field step operator (Eq. 5) for auxiliary fields Q [N][...]."""
+        L = torch.empty_like(U) if L is None else L
+        self._check(lib().wc_rhs_pf(self.h, _ptr(U), _ptr(Q), _ptr(L), _stream(stream)))
         return L
 
     def compute_dt(self, cfl, out=None, stream=None):

@@ -430,3 +430,54 @@ def test_fifth_order_on_smooth_advection():
         errs.append(np.abs(U[4] - inputs.smooth_alpha_average(n, 1.0)).mean())
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert rates[-1] > 4.8, (errs, rates)  # observed 4.997, 5.002 (20 -> 80 cells)
+
+
+# ---------------------------------------------------------------- Phase-Field step (Eq. 5)
+# The numerical Phase-Field flux is not printed in the paper (it cites it), so
+# its formula is a reading; these tests pin the properties the paper requires
+# of it (Sec. 2.2.1-2.2.2): no flux without a Q gradient, no fictitious phase,
+# sum of fractions kept, mass/fraction consistency, equilibrium,
+# conservation and bounds.
+def _pf_case(seed, N=3, n=64):
+    case, rho = random_1d_case(n, N, seed)
+    g = grid_of(case)
+    U = oracle.prim_to_cons(g, case.V)
+    rng = np.random.default_rng(seed)
+    Q = rng.normal(size=(N, n)) * 0.05
+    return case, g, U, Q, rho
+
+
+def test_pf_no_gradient_no_flux():
+    case, g, U, Q, _ = _pf_case(1)
+    Qc = np.ones_like(Q) * 3.7
+    assert not oracle.pf_rhs(g, U, Qc).any()
+
+
+def test_pf_fraction_sum_consistency_and_conservation():
+    for seed in range(4):
+        case, g, U, Q, rho = _pf_case(seed)
+        N = case.N
+        L = oracle.pf_rhs(g, U, Q)
+        La = L[N + 2:]
+        scale = np.abs(La).max()
+        assert np.abs(La.sum(0)).max() <= 1e-13 * scale            # sum_p J_p = 0
+        for p in range(N):                                         # rho_p const
+            assert np.allclose(L[p], rho[p] * La[p], rtol=1e-12, atol=1e-13 * rho[p] * scale)
+        tot = L.sum(1)                                             # periodic: conserved
+        assert np.all(np.abs(tot) <= 1e-12 * np.abs(L).sum(1) + 1e-300)
+
+
+def test_pf_absent_phase_and_equilibrium():
+    c = inputs.interface_advection_1d(n=80, absent_phase=True)
+    g = grid_of(c)
+    U = oracle.prim_to_cons(g, c.V)
+    rng = np.random.default_rng(5)
+    Q = rng.normal(size=(3, 80)) * 0.02
+    L = oracle.pf_rhs(g, U, Q)
+    assert not L[[2, 7]].any()                                     # no fictitious phase
+    lam = 0.2 / (np.abs(np.diff(Q, axis=1)).max() / c.dx[0] / c.dx[0])
+    V = oracle.cons_to_prim(g, U + lam * L)
+    assert np.abs(V[3] - 1.0).max() < 1e-12                        # u uniform
+    assert np.abs(V[4] - 1e5).max() / (1e5 + 6e8) < 1e-14          # P uniform
+    a = V[5:7]
+    assert a.min() >= 0.0 and a.max() <= 1.0 + 4 * 2.0 ** -52       # bounds
