@@ -46,12 +46,13 @@ typedef enum {
   WC_ERR_INADMISSIBLE = 3, /* a kernel met a state outside the admissible set */
   WC_ERR_NAN = 4,          /* a kernel produced a non-finite value */
   WC_ERR_UNSUPPORTED = 5,  /* combination not built (e.g. phase count) */
-  WC_ERR_STATE = 6         /* call order: state or workspace not bound */
+  WC_ERR_STATE = 6,        /* call order: state or workspace not bound */
+  WC_ERR_TIMEOUT = 7       /* a bounded wait inside a tensor-core kernel ran out */
 } wc_status;
 
 enum { WC_BC_PERIODIC = 0, WC_BC_REFLECTIVE = 1, WC_BC_OUTFLOW = 2 };
 enum { WC_FLUX_HLL = 0, WC_FLUX_HLLC = 1 };
-enum { WC_PREC_FP64 = 0, WC_PREC_MIXED = 1 };
+enum { WC_PREC_FP64 = 0, WC_PREC_MIXED = 1, WC_PREC_LEARNED = 2 };
 
 /* Grid, materials and scheme options.  Materials follow the stiffened-gas
  * equation of state of Eq. 26: A_p = 1/(gamma_p-1), B_p = gamma_p Pinf_p /
@@ -67,9 +68,13 @@ typedef struct {
   double D[WC_MAX_PHASE];
   double pmin[WC_MAX_PHASE];
   int flux;                   /* WC_FLUX_HLL (Sec. 4.2) or WC_FLUX_HLLC (Sec. 4.1) */
-  int precision;              /* WC_PREC_FP64 or WC_PREC_MIXED (FP32 smoothness
+  int precision;              /* WC_PREC_FP64; WC_PREC_MIXED (FP32 smoothness
                                  indicators, reconstruction and flux; FP64
-                                 pressure, limiter factors, unity sum, update) */
+                                 pressure, limiter factors, unity sum, update);
+                                 WC_PREC_LEARNED (as mixed, with the mass and
+                                 fraction weights of Eq. 16 from the learned
+                                 surrogate where accepted, N <= 3; see
+                                 wc_set_mlp) */
   int energy_limiter;         /* 1: Eq. 21 applied (default); 0: skipped */
   int bc[6];                  /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi: WC_BC_* */
   int seg;                    /* cells per thread along a sweep; 0 = automatic */
@@ -88,7 +93,8 @@ int wc_nvar(const wc_grid *g);
 long wc_ncell(const wc_grid *g);
 
 /* Device scratch that wc_rk_step needs: three state-sized FP64 buffers
- * (two Runge-Kutta stages and the direction accumulator) plus 256 bytes. */
+ * (two Runge-Kutta stages and the direction accumulator) plus 256 bytes, and
+ * for WC_PREC_LEARNED one more buffer of 18 x ncell FP32 learned weights. */
 size_t wc_workspace_bytes(const wc_grid *g);
 
 /* Binds the caller's device state array U_dev ([NV][ncell] FP64, advanced in
@@ -157,7 +163,8 @@ wc_status wc_limit(const wc_grid *g, int dir, long ncell, const double *Ubar, co
  * exits).  Grids whose three state-sized buffers do not fit (3 x NV x ncell
  * x 8 bytes, each rounded up to 256, at most 24 MiB; e.g. 2-D N = 2 up to
  * about 149,000 cells) are rejected with WC_ERR_ARG and a message in
- * wc_last_error before any work is enqueued.
+ * wc_last_error before any work is enqueued; grids of precision
+ * WC_PREC_LEARNED are rejected with WC_ERR_UNSUPPORTED.
  *
  * The first call on a device looks up the scratch's device address with that
  * device current (cudaGetSymbolAddress); make that first call before any
@@ -170,6 +177,84 @@ wc_status wc_limit(const wc_grid *g, int dir, long ncell, const double *Ubar, co
  * problem; 1 = inadmissible state; 2 = non-finite value). */
 wc_status wc_rk_step_noalloc(wc_grid *g, double *U_dev, double cfl, double dt_fixed, int nsteps,
                              int *status_host, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Learned WENO-weight surrogate (no counterpart in the paper: a learned
+ * stand-in for the weights of Eq. 15 in the coupled reconstruction, Eq. 16,
+ * with the paper's limiter, Eq. 17-21, always applied afterwards).
+ *
+ * Network: 30 inputs (zero-padded to 32) -> 64 -> 64 -> 64 (ReLU) -> 9
+ * outputs (padded to 16), a softmax over each phase's three outputs giving
+ * the weights of the sub-stencils {i-2..i}, {i-1..i+1}, {i..i+2} (ordered
+ * towards the face).  Inputs of one face side of one cell, per phase p < 3:
+ * the five masses (alpha rho)_p of the stencil ordered towards the face,
+ * minus the cell's own and divided by the largest absolute such difference
+ * (0 for a flat stencil), then the five fractions alpha_p; phases beyond N
+ * are zero.  Evaluated and trained on the tensor cores: BF16 weights,
+ * activations and features, FP32 accumulation, biases and softmax.
+ *
+ * Parameter block (device, 16-byte aligned, wc_mlp_param_bytes() bytes):
+ * BF16 W1[64][32], W2[64][64], W3[64][64], W4[16][64] (row = output unit),
+ * then FP32 b1[64], b2[64], b3[64], b4[16].  FP32 arrays of wc_mlp_nparam()
+ * entries (master copy, gradients, Adam moments) hold the same parameters in
+ * the same order.  Padding (inputs 30-31, outputs 9-15) is kept zero.
+ *
+ * Feature rows (device, BF16 [rows][32], 16-byte aligned): row0 + 2 cell +
+ * side, side 0 = face x_{i+1/2}, side 1 = x_{i-1/2} (mirrored stencil).
+ * Targets (FP32 [rows][9]): the plain Eq. 15 weights of each phase's masses
+ * on the oriented stencil (ideal weights 0.1/0.6/0.3 for phases beyond N). */
+size_t wc_mlp_param_bytes(void);
+int wc_mlp_nparam(void);
+/* He-normal initial FP32 master parameters (host array of wc_mlp_nparam()
+ * floats) from a seed; biases and padding zero. */
+wc_status wc_mlp_init_master(float *master_host, unsigned long long seed);
+/* Parameter block from FP32 masters (device to device, on stream). */
+wc_status wc_mlp_pack(const float *master_dev, void *params_dev, void *stream);
+/* Features (and targets when T_dev is not NULL) of both face sides of every
+ * cell of the state U_dev in direction dir, written at rows row0 .. row0 + 2
+ * ncell - 1.  Rows whose target weights differ from the ideal weights by
+ * more than 1e-3 are counted in *count_dev (a device counter the caller
+ * clears) and their row numbers appended to list_dev (when not NULL, up to
+ * list_cap entries; the count may exceed list_cap). */
+wc_status wc_mlp_features(const wc_grid *g, const double *U_dev, int dir, long row0, void *X_dev,
+                          float *T_dev, long *list_dev, unsigned long long *count_dev,
+                          long list_cap, void *stream);
+/* Softmax weights Y_dev [nrows][9] (FP32) of feature rows X_dev.  Kernel
+ * problems (a bounded tensor-core wait that ran out) set bit 4 of
+ * *status_dev. */
+wc_status wc_mlp_forward(const void *X_dev, long nrows, const void *params_dev, float *Y_dev,
+                         unsigned *status_dev, void *stream);
+/* Learned weights of direction dir for the state U_dev, features gathered
+ * in the kernel: W_dev[(9 side + 3 p + s) ncell + cell] (FP32, 18 ncell). */
+wc_status wc_mlp_infer(const wc_grid *g, const double *U_dev, int dir, const void *params_dev,
+                       float *W_dev, unsigned *status_dev, void *stream);
+/* Gradients of loss = (1/batch) sum_b sum_j (y_bj - T_bj)^2 over the batch
+ * of rows idx_dev[0..batch) of X_dev / T_dev, ADDED to grads_dev (FP32,
+ * wc_mlp_nparam() entries) and the loss added to *loss_dev. */
+wc_status wc_mlp_gradients(const void *X_dev, const float *T_dev, const int *idx_dev, int batch,
+                           const void *params_dev, float *grads_dev, float *loss_dev,
+                           unsigned *status_dev, void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected with the
+ * 1-based step number) on the FP32 masters; writes the parameter block and
+ * clears the gradients. */
+wc_status wc_mlp_adam(float *master_dev, void *params_dev, float *grads_dev, float *m_dev,
+                      float *v_dev, float lr, int step, void *stream);
+/* wc_mlp_gradients followed by wc_mlp_adam. */
+wc_status wc_mlp_train_step(const void *X_dev, const float *T_dev, const int *idx_dev, int batch,
+                            void *params_dev, float *master_dev, float *grads_dev, float *m_dev,
+                            float *v_dev, float lr, int step, float *loss_dev,
+                            unsigned *status_dev, void *stream);
+/* Binds the surrogate used by a WC_PREC_LEARNED grid (params_dev stays the
+ * caller's and must outlive its use).  For every interior cell, face side
+ * and phase the learned weights replace the plain ones when both the mass
+ * and the fraction reconstructed with them differ from their plain
+ * reconstructions by at most tau x (max - min of the five stencil values);
+ * otherwise, and for boundary cells, the plain weights stand (tau = 0 gives
+ * the WC_PREC_MIXED result bit for bit).  counters_dev (optional, two device
+ * uint64 the caller clears) accumulates the face sides decided and those
+ * that fell back to the plain weights. */
+wc_status wc_set_mlp(wc_grid *g, const void *params_dev, float tau,
+                     unsigned long long *counters_dev);
 
 /* ------------------------------------------------------------------------
  * Batched AMR-like patches.  npatch independent unit-cube patches, patch p

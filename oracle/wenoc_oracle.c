@@ -54,6 +54,18 @@
  *  R11 Eq. 19 assumes S > 0.  When the positivity step has limited every
  *      fraction of a face to zero (S = 0) the cell keeps its averages on both
  *      faces (theta = 0, first order) for the masses and the fractions.
+ *  R13 Rounding residue below the bounds.  In exact arithmetic the faces
+ *      scaled by Eq. 18 (f_min = 0), Eq. 20 and Eq. 21 have non-negative
+ *      masses and fractions, and every Runge-Kutta stage (a convex
+ *      combination of forward-Euler steps under the CFL condition, Sec. 4)
+ *      keeps the cell masses non-negative and the fractions in [0, 1].  In
+ *      floating point fbar + theta (f - fbar), meant to land on 0, can land
+ *      an ulp below it; an absent phase's vanishing tail then becomes a
+ *      negative average, and Eq. 18 on a negative average (theta = 0) taken
+ *      into Eq. 20's minimum over phases drops the whole cell to first order.
+ *      Such residues are set to the bound: scaled face masses and fractions
+ *      below 0 become 0, and stage results of masses below 0 become 0 and
+ *      of fractions outside [0, 1] become the nearer bound.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -248,6 +260,9 @@ static double theta_lower(double fbar, double fC, double fL, double fR, double f
   return t < 1.0 ? t : 1.0;
 }
 
+/* R13: a value below the bound 0 only by rounding becomes 0. */
+static double clamp0(double x) { return x < 0.0 ? 0.0 : x; }
+
 static double theta_pos(double fbar, double fL, double fR) {
   return theta_lower(fbar, center_value(fbar, fL, fR), fL, fR, 0.0);
 }
@@ -271,10 +286,12 @@ static int limit_chain(const or_grid *g, const double *Ubar, double *VL, double 
       double t2 = theta_pos(ab, VL[IALF(g, p)], VR[IALF(g, p)]);
       double tp = t1 < t2 ? t1 : t2;
       if (tp < th17) th17 = tp;
-      VL[IMASS(p)] = mb + tp * (VL[IMASS(p)] - mb);
-      VR[IMASS(p)] = mb + tp * (VR[IMASS(p)] - mb);
-      VL[IALF(g, p)] = ab + tp * (VL[IALF(g, p)] - ab);
-      VR[IALF(g, p)] = ab + tp * (VR[IALF(g, p)] - ab);
+      if (tp < 1.0) {
+        VL[IMASS(p)] = clamp0(mb + tp * (VL[IMASS(p)] - mb));
+        VR[IMASS(p)] = clamp0(mb + tp * (VR[IMASS(p)] - mb));
+        VL[IALF(g, p)] = clamp0(ab + tp * (VL[IALF(g, p)] - ab));
+        VR[IALF(g, p)] = clamp0(ab + tp * (VR[IALF(g, p)] - ab));
+      }
     }
     /* Eq. 19: unity sum of the volume fractions on each face. */
     double SL = 0.0, SR = 0.0;
@@ -307,10 +324,12 @@ static int limit_chain(const or_grid *g, const double *Ubar, double *VL, double 
     }
     for (int p = 0; p < N; p++) {
       double mb = Ubar[IMASS(p)], ab = Ubar[IALF(g, p)];
-      VL[IMASS(p)] = mb + th20 * (VL[IMASS(p)] - mb);
-      VR[IMASS(p)] = mb + th20 * (VR[IMASS(p)] - mb);
-      VL[IALF(g, p)] = ab + th20 * (VL[IALF(g, p)] - ab);
-      VR[IALF(g, p)] = ab + th20 * (VR[IALF(g, p)] - ab);
+      if (th20 < 1.0) {
+        VL[IMASS(p)] = clamp0(mb + th20 * (VL[IMASS(p)] - mb));
+        VR[IMASS(p)] = clamp0(mb + th20 * (VR[IMASS(p)] - mb));
+        VL[IALF(g, p)] = clamp0(ab + th20 * (VL[IALF(g, p)] - ab));
+        VR[IALF(g, p)] = clamp0(ab + th20 * (VR[IALF(g, p)] - ab));
+      }
     }
   }
   /* V -> U at both faces. */
@@ -327,6 +346,12 @@ static int limit_chain(const or_grid *g, const double *Ubar, double *VL, double 
       for (int v = 0; v < nvar; v++) {
         UL[v] = Ubar[v] + thpsi * (UL[v] - Ubar[v]);
         UR[v] = Ubar[v] + thpsi * (UR[v] - Ubar[v]);
+      }
+      for (int p = 0; p < N; p++) {
+        UL[IMASS(p)] = clamp0(UL[IMASS(p)]);
+        UR[IMASS(p)] = clamp0(UR[IMASS(p)]);
+        UL[IALF(g, p)] = clamp0(UL[IALF(g, p)]);
+        UR[IALF(g, p)] = clamp0(UR[IALF(g, p)]);
       }
     }
   }
@@ -802,6 +827,19 @@ int or_max_rate(const or_grid *g, const double *U, double *rate) {
   return OR_OK;
 }
 
+/* R13: stage results of masses below 0 become 0; fractions are kept in
+ * [0, 1]. */
+static void stage_bounds(const or_grid *g, double *U) {
+  long n = ncells(g);
+  for (int p = 0; p < g->N; p++) {
+    double *m = U + (long)IMASS(p) * n, *a = U + (long)IALF(g, p) * n;
+    for (long c = 0; c < n; c++) {
+      m[c] = clamp0(m[c]);
+      a[c] = a[c] > 1.0 ? 1.0 : clamp0(a[c]);
+    }
+  }
+}
+
 /* One third-order SSP (TVD) Runge-Kutta step of Shu & Osher, in place.
  * dt_fixed > 0 gives the time step; otherwise dt = cfl / max rate (R10). */
 int or_rk3_step(const or_grid *g, double *U, double cfl, double dt_fixed, double *dt_used) {
@@ -821,15 +859,19 @@ int or_rk3_step(const or_grid *g, double *U, double cfl, double dt_fixed, double
   e = or_rhs(g, U0, L);
   if (!e) {
     for (long k = 0; k < tot; k++) U1[k] = U0[k] + dt * L[k];
+    stage_bounds(g, U1);
     e = or_rhs(g, U1, L);
   }
   if (!e) {
     for (long k = 0; k < tot; k++) U1[k] = 0.75 * U0[k] + 0.25 * U1[k] + 0.25 * dt * L[k];
+    stage_bounds(g, U1);
     e = or_rhs(g, U1, L);
   }
-  if (!e)
+  if (!e) {
     for (long k = 0; k < tot; k++)
       U[k] = 1.0 / 3.0 * U0[k] + 2.0 / 3.0 * U1[k] + 2.0 / 3.0 * dt * L[k];
+    stage_bounds(g, U);
+  }
   free(U0); free(U1); free(L);
   if (dt_used) *dt_used = dt;
   return e;

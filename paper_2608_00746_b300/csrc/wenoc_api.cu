@@ -9,6 +9,7 @@
 
 #include "../../include/wenoc.h"
 #include "wenoc_kernels.cuh"
+#include "wenoc_mlp.cuh"
 
 using namespace wc;
 
@@ -26,6 +27,13 @@ struct wc_grid {
   unsigned* status = nullptr;
   unsigned long long* rate = nullptr;
   double* dt = nullptr;
+  // learned precision: the surrogate's parameter block (caller's device
+  // memory), acceptance threshold, optional counters and the weight buffer
+  // (in the workspace, after its 256-byte tail)
+  const void* mlp = nullptr;
+  float tau = 1e-4f;
+  unsigned long long* lcount = nullptr;
+  float* Wbuf = nullptr;
   char err[256];
   // sweep timing (wc_sweep_timing_begin / _read)
   std::vector<cudaEvent_t> tev;
@@ -87,7 +95,10 @@ extern "C" wc_status wc_init_grid(const wc_grid_desc* desc, wc_grid** out) {
   for (int a = 0; a < d.dim; a++)
     if ((d.bc[2 * a] == WC_BC_PERIODIC) != (d.bc[2 * a + 1] == WC_BC_PERIODIC)) return WC_ERR_ARG;
   if (d.flux != WC_FLUX_HLL && d.flux != WC_FLUX_HLLC) return WC_ERR_ARG;
-  if (d.precision != WC_PREC_FP64 && d.precision != WC_PREC_MIXED) return WC_ERR_UNSUPPORTED;
+  if (d.precision != WC_PREC_FP64 && d.precision != WC_PREC_MIXED &&
+      d.precision != WC_PREC_LEARNED)
+    return WC_ERR_UNSUPPORTED;
+  if (d.precision == WC_PREC_LEARNED && d.nphase > 3) return WC_ERR_UNSUPPORTED;
   if (d.seg < 0 || d.block < 0 || d.block > 128 || (d.block % 32) != 0) return WC_ERR_ARG;
   if (d.blocks_per_sm < 0 || d.blocks_per_sm > 4) return WC_ERR_ARG;
   for (int p = 0; p < d.nphase; p++)
@@ -127,7 +138,10 @@ extern "C" size_t wc_workspace_bytes(const wc_grid* g) {
   if (!g) return 0;
   size_t state = (size_t)g->nv * g->ncell * sizeof(double);
   state = (state + 255) / 256 * 256;
-  return 3 * state + 256;
+  size_t w = 0;
+  if (g->d.precision == WC_PREC_LEARNED)
+    w = ((size_t)2 * MLP_NW * g->ncell * sizeof(float) + 255) / 256 * 256;
+  return 3 * state + 256 + w;
 }
 
 extern "C" wc_status wc_set_state(wc_grid* g, double* U_dev, void* ws, size_t ws_bytes) {
@@ -148,6 +162,7 @@ extern "C" wc_status wc_set_state(wc_grid* g, double* U_dev, void* ws, size_t ws
     g->rate = (unsigned long long*)tail;
     g->dt = (double*)(tail + 8);
     g->status = (unsigned*)(tail + 16);
+    g->Wbuf = g->d.precision == WC_PREC_LEARNED ? (float*)(tail + 256) : nullptr;
     // the workspace comes uninitialised: clear rate, dt and the status word
     cudaError_t e = cudaMemset(tail, 0, 256);
     if (e != cudaSuccess) return cuda_fail(g, e, "workspace clear");
@@ -156,6 +171,7 @@ extern "C" wc_status wc_set_state(wc_grid* g, double* U_dev, void* ws, size_t ws
     g->rate = nullptr;
     g->dt = nullptr;
     g->status = nullptr;
+    g->Wbuf = nullptr;
   }
   return WC_OK;
 }
@@ -205,7 +221,7 @@ static int sweep_block(const wc_grid* g) { return g->d.block > 0 ? g->d.block : 
 static long sweep_threads(const wc_grid* g) {
   int block = sweep_block(g);
   int bps = g->d.blocks_per_sm > 0 ? g->d.blocks_per_sm : 2;  // blocks per SM
-  if (g->d.blocks_per_sm <= 0 && g->d.precision == WC_PREC_MIXED) bps = 3;
+  if (g->d.blocks_per_sm <= 0 && g->d.precision != WC_PREC_FP64) bps = 3;
   return 148L * bps * block;
 }
 
@@ -257,12 +273,39 @@ static SweepArgs make_args(const wc_grid* g, int dir, const double* U, double* L
   return a;
 }
 
-static cudaError_t launch(const wc_grid* gc, const SweepArgs& a, cudaStream_t st) {
+static MlpGeom mlp_geom(const wc_grid* g, int dir, const double* U) {
+  MlpGeom mg;
+  mg.U = U;
+  mg.ncell = g->ncell;
+  mg.nx = g->d.n[0];
+  mg.ny = g->d.n[1];
+  mg.nz = g->d.n[2];
+  mg.dir = dir;
+  mg.n = g->d.n[dir];
+  mg.stride = dir == 0 ? 1 : (dir == 1 ? (long)mg.nx : (long)mg.nx * mg.ny);
+  mg.bclo = g->d.bc[2 * dir];
+  mg.bchi = g->d.bc[2 * dir + 1];
+  mg.N = g->d.nphase;
+  mg.nv = g->nv;
+  return mg;
+}
+
+static cudaError_t launch(const wc_grid* gc, const SweepArgs& a0, cudaStream_t st) {
   wc_grid* g = const_cast<wc_grid*>(gc);
   const bool timed = g->tcount < g->tmax;
   if (timed) cudaEventRecord(g->tev[2 * g->tcount], st);
   cudaError_t e;
-  if (g->d.precision == WC_PREC_MIXED)
+  SweepArgs a = a0;
+  if (g->d.precision == WC_PREC_LEARNED) {
+    // weights of this direction from the surrogate, then the sweep
+    e = launch_mlp_infer(mlp_geom(g, a.dir, a.U), g->mlp, g->Wbuf, g->status, st);
+    if (e == cudaSuccess) {
+      a.Wm = g->Wbuf;
+      a.tau = g->tau;
+      a.lcount = g->lcount;
+      e = launch_sweep_learned(g->d.nphase, g->d.dim, a, g->mat, sweep_block(g), st);
+    }
+  } else if (g->d.precision == WC_PREC_MIXED)
     e = launch_sweep_mixed(g->d.nphase, g->d.dim, a, g->mat, sweep_block(g), st);
   else
     e = launch_sweep_fp64(g->d.nphase, g->d.dim, a, g->mat, sweep_block(g), st);
@@ -313,6 +356,8 @@ extern "C" wc_status wc_sweep_timing_read(wc_grid* g, int* launches, double* tot
 extern "C" wc_status wc_rhs(wc_grid* g, const double* U, double* L, void* stream) {
   if (!g || !U || !L) return WC_ERR_ARG;
   if (!g->status) return fail(g, WC_ERR_STATE, "wc_rhs needs a bound workspace (status word)");
+  if (g->d.precision == WC_PREC_LEARNED && !g->mlp)
+    return fail(g, WC_ERR_STATE, "learned precision needs wc_set_mlp");
   for (int dir = 0; dir < g->d.dim; dir++) {
     SweepArgs a = make_args(g, dir, U, L);
     a.mode = dir == 0 ? 0 : 1;
@@ -389,6 +434,8 @@ extern "C" wc_status wc_rk_step(wc_grid* g, double cfl, double dt_fixed, int nst
   if (!g || nsteps < 0) return WC_ERR_ARG;
   if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return fail(g, WC_ERR_ARG, "need cfl > 0 or dt > 0");
   if (!g->U || !g->ws) return fail(g, WC_ERR_STATE, "state/workspace not bound");
+  if (g->d.precision == WC_PREC_LEARNED && !g->mlp)
+    return fail(g, WC_ERR_STATE, "learned precision needs wc_set_mlp");
   cudaStream_t st = S(stream);
   for (int s = 0; s < nsteps; s++) {
     if (!(dt_fixed > 0.0)) {
@@ -440,12 +487,58 @@ extern "C" wc_status wc_sync_status(wc_grid* g, void* stream) {
   if (e != cudaSuccess) return cuda_fail(g, e, "status");
   if (st & ST_INADMISSIBLE) return fail(g, WC_ERR_INADMISSIBLE, "inadmissible state met by a kernel");
   if (st & ST_NAN) return fail(g, WC_ERR_NAN, "non-finite value produced by a kernel");
+  if (st & 4u) return fail(g, WC_ERR_TIMEOUT, "a bounded wait in a tensor-core kernel ran out");
   return WC_OK;
 }
 
 extern "C" void wc_last_error(const wc_grid* g, char* buf, size_t n) {
   if (!buf || n == 0) return;
   snprintf(buf, n, "%s", g ? g->err : "null grid");
+}
+
+// ------------------------------------------------------------------ learned weights
+extern "C" wc_status wc_set_mlp(wc_grid* g, const void* params_dev, float tau,
+                                unsigned long long* counters_dev) {
+  if (!g) return WC_ERR_ARG;
+  if (g->d.precision != WC_PREC_LEARNED)
+    return fail(g, WC_ERR_STATE, "wc_set_mlp needs a grid of precision WC_PREC_LEARNED");
+  if (params_dev && (reinterpret_cast<uintptr_t>(params_dev) & 15))
+    return fail(g, WC_ERR_ARG, "parameter block not 16-byte aligned");
+  if (!(tau >= 0.0f) || !(tau <= 1.0f)) return fail(g, WC_ERR_ARG, "tau outside [0, 1]");
+  g->mlp = params_dev;
+  g->tau = tau;
+  g->lcount = counters_dev;
+  return WC_OK;
+}
+
+extern "C" wc_status wc_mlp_infer(const wc_grid* gc, const double* U_dev, int dir,
+                                  const void* params_dev, float* W_dev, unsigned* status_dev,
+                                  void* stream) {
+  wc_grid* g = const_cast<wc_grid*>(gc);
+  if (!g || !U_dev || !params_dev || !W_dev || !status_dev) return WC_ERR_ARG;
+  if (dir < 0 || dir >= g->d.dim) return fail(g, WC_ERR_ARG, "bad direction");
+  if (g->d.nphase > 3) return fail(g, WC_ERR_UNSUPPORTED, "the surrogate takes N <= 3");
+  if (reinterpret_cast<uintptr_t>(params_dev) & 15)
+    return fail(g, WC_ERR_ARG, "parameter block not 16-byte aligned");
+  cudaError_t e = launch_mlp_infer(mlp_geom(g, dir, U_dev), params_dev, W_dev, status_dev,
+                                   S(stream));
+  return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "mlp infer");
+}
+
+extern "C" wc_status wc_mlp_features(const wc_grid* gc, const double* U_dev, int dir, long row0,
+                                     void* X_dev, float* T_dev, long* list_dev,
+                                     unsigned long long* count_dev, long list_cap,
+                                     void* stream) {
+  wc_grid* g = const_cast<wc_grid*>(gc);
+  if (!g || !U_dev || !X_dev || row0 < 0 || list_cap < 0) return WC_ERR_ARG;
+  if (list_dev && !count_dev) return fail(g, WC_ERR_ARG, "list needs a counter");
+  if (dir < 0 || dir >= g->d.dim) return fail(g, WC_ERR_ARG, "bad direction");
+  if (g->d.nphase > 3) return fail(g, WC_ERR_UNSUPPORTED, "the surrogate takes N <= 3");
+  if (reinterpret_cast<uintptr_t>(X_dev) & 15) return fail(g, WC_ERR_ARG, "X not 16-byte aligned");
+  cudaError_t e = launch_mlp_features(mlp_geom(g, dir, U_dev), row0,
+                                      reinterpret_cast<__nv_bfloat16*>(X_dev), T_dev, list_dev,
+                                      count_dev, list_cap, S(stream));
+  return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "mlp features");
 }
 
 // ------------------------------------------------------------------ FP64 peak probe
@@ -477,6 +570,8 @@ extern "C" wc_status wc_fp64_peak_kernel(int blocks, int threads, int iters, dou
 wc_status wc_internal_rk_with_scratch(wc_grid* g, double* U, char* scratch, double cfl,
                                       double dt_fixed, int nsteps, cudaStream_t st,
                                       unsigned** status_out) {
+  if (g->d.precision == WC_PREC_LEARNED)
+    return fail(g, WC_ERR_UNSUPPORTED, "the fixed scratch holds no learned-weight buffer");
   // save and restore only the bindings (the grid also owns timing events)
   struct Bind {
     double* U; char* ws; size_t ws_bytes; double *B1, *B2, *Lacc;

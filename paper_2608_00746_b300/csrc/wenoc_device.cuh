@@ -363,6 +363,12 @@ struct Face {
 // x_{i+1/2} (x_{i-1/2}); uL, PL (uR, PR) reconstructed velocity and pressure.
 // Produces the two limited face states.  th (optional) receives
 // (min_p theta_p of Eq. 17, theta_i of Eq. 20, theta^(psi) of Eq. 21).
+// Rounding residue below a bound: the limited face values of Eq. 18 / Eq. 20
+// and the updated cell masses and fractions are non-negative in exact
+// arithmetic, but theta (f - fbar) + fbar that should land on zero can land
+// an ulp below it.  x < 0 becomes 0; a NaN stays a NaN.
+__device__ __forceinline__ double nonneg(double x) { return x < 0.0 ? 0.0 : x; }
+
 template <int N, int D>
 __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, double Pb,
                                             double* mL, double* aL, double* mR, double* aR,
@@ -377,10 +383,10 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
     double mb = Ub[p], ab = Ub[I::A(p)];
     double tp = fmin(theta_pos(mb, mL[p], mR[p]), theta_pos(ab, aL[p], aR[p]));
     if (tp < 1.0) {
-      mL[p] = fma(tp, mL[p] - mb, mb);
-      mR[p] = fma(tp, mR[p] - mb, mb);
-      aL[p] = fma(tp, aL[p] - ab, ab);
-      aR[p] = fma(tp, aR[p] - ab, ab);
+      mL[p] = nonneg(fma(tp, mL[p] - mb, mb));
+      mR[p] = nonneg(fma(tp, mR[p] - mb, mb));
+      aL[p] = nonneg(fma(tp, aL[p] - ab, ab));
+      aR[p] = nonneg(fma(tp, aR[p] - ab, ab));
       th17 = fmin(th17, tp);
     }
   }
@@ -432,10 +438,10 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
 #pragma unroll
     for (int p = 0; p < N; p++) {
       double mb = Ub[p], ab = Ub[I::A(p)];
-      mL[p] = fma(thi, mL[p] - mb, mb);
-      mR[p] = fma(thi, mR[p] - mb, mb);
-      aL[p] = fma(thi, aL[p] - ab, ab);
-      aR[p] = fma(thi, aR[p] - ab, ab);
+      mL[p] = nonneg(fma(thi, mL[p] - mb, mb));
+      mR[p] = nonneg(fma(thi, mR[p] - mb, mb));
+      aL[p] = nonneg(fma(thi, aL[p] - ab, ab));
+      aR[p] = nonneg(fma(thi, aR[p] - ab, ab));
     }
   }
   // V -> U at both faces
@@ -479,6 +485,10 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
       for (int v = 0; v < I::NV; v++) {
         FL.U[v] = fma(thpsi, FL.U[v] - Ub[v], Ub[v]);
         FR.U[v] = fma(thpsi, FR.U[v] - Ub[v], Ub[v]);
+        if (v < N || v >= I::A(0)) {
+          FL.U[v] = nonneg(FL.U[v]);
+          FR.U[v] = nonneg(FR.U[v]);
+        }
       }
       double W[I::NV];
       cons_to_prim<N, D>(m, FL.U, W);

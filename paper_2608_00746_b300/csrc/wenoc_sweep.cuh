@@ -40,6 +40,13 @@ struct SweepArgs {
   int hllc;
   int energy_limiter;
   unsigned* status;
+  // learned weights (template LW = 1): the surrogate's weights of the masses
+  // for this direction, W[(9 side + 3 p + s) ncell + cell]; tau is the
+  // acceptance threshold; lcount[0] counts face sides decided, lcount[1]
+  // those that fell back to the plain weights
+  const float* Wm;
+  float tau;
+  unsigned long long* lcount;
 };
 
 enum { BC_PERIODIC = 0, BC_REFLECTIVE = 1, BC_OUTFLOW = 2 };
@@ -81,9 +88,10 @@ struct Ring {
 // step `a.stride`, `a.n` cells, boundary conditions a.bclo/a.bchi):
 // reconstruct, limit, solve the Riemann problems and update per a.mode.
 // `ring` is this thread's five-slot stencil ring in shared memory.
-template <int N, int D, typename T, typename TF>
+template <int N, int D, typename T, typename TF, int LW = 0>
 __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, long base, int s,
-                                              int e, double* ring, double dt, unsigned& bad) {
+                                              int e, double* ring, double dt, unsigned& bad,
+                                              unsigned* lstat = nullptr) {
   using I = Idx<N, D>;
   constexpr int NV = I::NV;
   constexpr int SLOTD = Ring<N, D, T>::SLOTD;
@@ -144,6 +152,57 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
     for (int p = 0; p < N; p++) {
       Stencil<T> st = stencil<T>(V[0][p], V[1][p], V[2][p], V[3][p], V[4][p]);
       W6<T> w = weights_of<T>(st);
+      if constexpr (LW != 0) {
+        // learned weights of an interior cell, accepted per face side when
+        // the mass and the fraction reconstructed with them are each within
+        // tau times their stencil's range of the plain reconstructions
+        // (boundary cells keep the plain weights)
+        if (p < 3 && c >= 0 && c < a.n) {
+          const float* Wp = a.Wm + (long)(3 * p) * a.ncell + base + (long)c * a.stride;
+          W6<T> wl;
+          wl.aL0 = T(__ldg(Wp));
+          wl.aL1 = T(__ldg(Wp + a.ncell));
+          wl.aL2 = T(__ldg(Wp + 2 * a.ncell));
+          wl.aR0 = T(__ldg(Wp + 9 * a.ncell));
+          wl.aR1 = T(__ldg(Wp + 10 * a.ncell));
+          wl.aR2 = T(__ldg(Wp + 11 * a.ncell));
+          wl.invL = wl.invR = T(1) / T(6);
+          const int ia = I::A(p);
+          const Stencil<T> sa = stencil<T>(V[0][ia], V[1][ia], V[2][ia], V[3][ia], V[4][ia]);
+          bool okL = true, okR = true, flat = true;
+          auto judge = [&](const Stencil<T>& q) {
+            T pl, pr, ql, qr;
+            reconstruct(w, q, pl, pr);
+            reconstruct(wl, q, ql, qr);
+            const T hi = fmax(fmax(fmax(T(0), q.da), fmax(q.db, q.dd)), q.de);
+            const T lo = fmin(fmin(fmin(T(0), q.da), fmin(q.db, q.dd)), q.de);
+            const T tol = T(a.tau) * (hi - lo);
+            okL = okL && fabs(ql - pl) <= tol;
+            okR = okR && fabs(qr - pr) <= tol;
+            flat = flat && !(hi > lo);
+          };
+          judge(st);
+          judge(sa);
+          if (okL) {
+            w.aL0 = wl.aL0;
+            w.aL1 = wl.aL1;
+            w.aL2 = wl.aL2;
+            w.invL = wl.invL;
+          }
+          if (okR) {
+            w.aR0 = wl.aR0;
+            w.aR1 = wl.aR1;
+            w.aR2 = wl.aR2;
+            w.invR = wl.invR;
+          }
+          // counted: face sides of stencils that are not flat (on a flat
+          // stencil every convex weight gives the cell value)
+          if (!flat) {
+            lstat[0] += 2u;
+            lstat[1] += unsigned(!okL) + unsigned(!okR);
+          }
+        }
+      }
       T fl, fr;
       reconstruct(w, st, fl, fr);
       mL[p] = double(fl);
@@ -202,7 +261,12 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
           } else {
             double Lt = a.mode == 2 ? a.L[idx] + val : val;
             double u0 = a.U0[idx];
-            a.Uout[idx] = a.rk0 * u0 + a.rk1 * Uprev[v] + a.rk2 * dt * Lt;
+            double un = a.rk0 * u0 + a.rk1 * Uprev[v] + a.rk2 * dt * Lt;
+            // masses >= 0 and fractions in [0, 1] up to rounding: remove the
+            // residue (NaN passes through)
+            if (v < N || v >= I::A(0)) un = nonneg(un);
+            if (v >= I::A(0)) un = un > 1.0 ? 1.0 : un;
+            a.Uout[idx] = un;
           }
         }
       }
@@ -220,7 +284,7 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
   }
 }
 
-template <int N, int D, typename T, typename TF>
+template <int N, int D, typename T, typename TF, int LW = 0>
 __global__ void __launch_bounds__(128) k_sweep(SweepArgs a, Mat m) {
   constexpr int SLOTD = Ring<N, D, T>::SLOTD;
   extern __shared__ double smem[];
@@ -228,6 +292,7 @@ __global__ void __launch_bounds__(128) k_sweep(SweepArgs a, Mat m) {
   const long nthreads = (long)gridDim.x * blockDim.x;
   const long nitems = a.npencil * a.nseg;
   unsigned bad = 0u;
+  unsigned lstat[2] = {0u, 0u};
   double dt = 0.0;
   if (a.mode >= 2) dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.cfl / *a.rate;
 
@@ -243,9 +308,20 @@ __global__ void __launch_bounds__(128) k_sweep(SweepArgs a, Mat m) {
     else base = tr;
     const int s = sg * a.seg;
     const int e = min(s + a.seg, a.n);
-    sweep_segment<N, D, T, TF>(a, m, base, s, e, ring, dt, bad);
+    sweep_segment<N, D, T, TF, LW>(a, m, base, s, e, ring, dt, bad, lstat);
   }
   if (bad) atomicOr(a.status, bad);
+  if constexpr (LW != 0) {
+    if (a.lcount) {
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        unsigned v = lstat[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.lcount + k, (unsigned long long)v);
+      }
+    }
+  }
 }
 
 }  // namespace wc

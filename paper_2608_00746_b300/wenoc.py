@@ -18,9 +18,9 @@ LIB_PATH = os.path.join(_HERE, "libwenoc.so")
 MAX_PHASE = 8
 BC = {"periodic": 0, "reflective": 1, "outflow": 2}
 FLUX = {"hll": 0, "hllc": 1}
-PREC = {"fp64": 0, "mixed": 1}
+PREC = {"fp64": 0, "mixed": 1, "learned": 2}
 STATUS = {0: "WC_OK", 1: "WC_ERR_ARG", 2: "WC_ERR_CUDA", 3: "WC_ERR_INADMISSIBLE",
-          4: "WC_ERR_NAN", 5: "WC_ERR_UNSUPPORTED", 6: "WC_ERR_STATE"}
+          4: "WC_ERR_NAN", 5: "WC_ERR_UNSUPPORTED", 6: "WC_ERR_STATE", 7: "WC_ERR_TIMEOUT"}
 
 
 class WcError(RuntimeError):
@@ -112,6 +112,19 @@ _SIGS = {
     "wc_patches_last_error": (None, [_VP, ctypes.c_char_p, ctypes.c_size_t]),
     "wc_rk_step_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP]),
+    "wc_mlp_param_bytes": (ctypes.c_size_t, []),
+    "wc_mlp_nparam": (ctypes.c_int, []),
+    "wc_mlp_init_master": (ctypes.c_int, [_VP, ctypes.c_ulonglong]),
+    "wc_mlp_pack": (ctypes.c_int, [_VP, _VP, _VP]),
+    "wc_mlp_features": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_long, _VP, _VP, _VP, _VP,
+                                       ctypes.c_long, _VP]),
+    "wc_mlp_forward": (ctypes.c_int, [_VP, ctypes.c_long, _VP, _VP, _VP, _VP]),
+    "wc_mlp_infer": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
+    "wc_mlp_gradients": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
+    "wc_mlp_adam": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_float, ctypes.c_int, _VP]),
+    "wc_mlp_train_step": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP,
+                                         ctypes.c_float, ctypes.c_int, _VP, _VP, _VP]),
+    "wc_set_mlp": (ctypes.c_int, [_VP, _VP, ctypes.c_float, _VP]),
 }
 
 _lib = None
@@ -141,6 +154,15 @@ def _ptr(t):
         return None
     if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
         raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dptr(t):
+    """Device pointer of any contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -287,6 +309,28 @@ class Grid:
 
     def sync_status(self, stream=None):
         self._check(lib().wc_sync_status(self.h, _stream(stream)))
+
+    # learned weights ------------------------------------------------------
+    def set_mlp(self, params, tau=1e-4, counters=None):
+        """Binds the surrogate's parameter block (uint8 CUDA tensor) for a
+        grid of precision "learned"; counters: optional int64 CUDA tensor [2]
+        accumulating (face sides decided, fallbacks to the plain weights)."""
+        self._mlp_keep = (params, counters)
+        self._check(lib().wc_set_mlp(self.h, _dptr(params), float(tau), _dptr(counters)))
+
+    def mlp_features(self, U, direction, X, T=None, row0=0, lst=None, count=None, stream=None):
+        cap = 0 if lst is None else lst.numel()
+        self._check(lib().wc_mlp_features(self.h, _ptr(U), int(direction), int(row0), _dptr(X),
+                                          _dptr(T), _dptr(lst), _dptr(count), cap,
+                                          _stream(stream)))
+
+    def mlp_infer(self, U, direction, params, W=None, status=None, stream=None):
+        W = torch.empty((18, self.ncell), dtype=torch.float32, device=U.device) if W is None \
+            else W
+        status = torch.zeros(1, dtype=torch.int32, device=U.device) if status is None else status
+        self._check(lib().wc_mlp_infer(self.h, _ptr(U), int(direction), _dptr(params), _dptr(W),
+                                       _dptr(status), _stream(stream)))
+        return W, status
 
 
 def fp64_peak(blocks=148 * 8, threads=256, iters=20000, reps=5):

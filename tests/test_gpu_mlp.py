@@ -1,0 +1,314 @@
+"""Learned WENO-weight surrogate on the tensor cores against the FP64 CPU
+reference (oracle/mlp.py): features and plain-weight targets (bit-exact /
+FP32 rounding), forward, gradients and Adam (the reference reproduces the
+kernels' BF16 rounding points), training, and the learned sweep: tau = 0
+reproduces the mixed precision bit for bit, a trained surrogate keeps the
+run within the mixed-precision L1 bound of the FP64 oracle with bounds and
+unity sum intact, and an absent phase stays exactly zero."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mlp
+from paper_2608_00746_b300 import inputs, surrogate, wenoc
+
+from gpu_util import l1_group, to_dev
+
+pytestmark = pytest.mark.gpu
+EPS_BOUND = 4 * 2.0 ** -52
+TAU = 1e-4   # acceptance threshold of the learned weights
+
+
+def _case_grid(case, precision="mixed"):
+    g = wenoc.Grid(case.shape, case.dx, case.gamma, case.pinf, case.D, flux=case.flux,
+                   bc=case.bc, precision=precision)
+    go = oracle.Grid(case.shape, case.dx, case.gamma, case.pinf, case.D, flux=case.flux,
+                     bc=case.bc)
+    return g, go
+
+
+def _small_circles(n=96, seed=5, ncirc=6):
+    return inputs.circles_shock_2d(shape=(n, n - 16), seed=seed, ncirc=ncirc, rmin_cells=4,
+                                   rmax_cells=14)
+
+
+def _small_bubble(seed=1):
+    return inputs.shock_bubble_2d(nx=96, ny=48, seed=seed)
+
+
+def _gpu_features(g, U, d, with_targets=True):
+    rows = 2 * g.ncell
+    X = torch.zeros((rows, 32), dtype=torch.bfloat16, device="cuda")
+    T = torch.zeros((rows, 9), dtype=torch.float32, device="cuda") if with_targets else None
+    lst = torch.zeros(rows, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    g.mlp_features(U, d, X, T, 0, lst, cnt)
+    torch.cuda.synchronize()
+    return X, T, lst, int(cnt.item())
+
+
+def _bf16_as_f64(X):
+    return X.float().cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("which", ["circles_N3", "bubble_N2"])
+def test_features_and_targets_parity(gpu, which):
+    case = _small_circles() if which == "circles_N3" else _small_bubble()
+    g, go = _case_grid(case)
+    U = oracle.prim_to_cons(go, case.V)
+    Ud = to_dev(U)
+    for d in range(2):
+        X, T, lst, cnt = _gpu_features(g, Ud, d)
+        ms, al = mlp.oriented_stencils(U, case.N, d, case.bc)
+        Xr = mlp.features(ms, al)
+        assert np.array_equal(_bf16_as_f64(X), Xr), "features differ"
+        Tr = mlp.targets(ms, case.N)
+        Tg = T.cpu().numpy().astype(np.float64)
+        # both sides form the indicators from differences to the cell value
+        assert np.abs(Tg - Tr).max() <= 1e-6
+        # interesting rows: targets away from the ideal weights
+        dev = np.abs(Tr - np.array(mlp.IDEAL * 3)).max(axis=1)
+        sure_in = set(np.nonzero(dev > 1e-3 + 1e-6)[0])
+        sure_out = set(np.nonzero(dev < 1e-3 - 1e-6)[0])
+        got = set(lst[:cnt].cpu().numpy().tolist())
+        assert sure_in <= got and not (got & sure_out)
+        assert cnt > 100
+
+
+@pytest.fixture(scope="module")
+def feature_rows():
+    case = _small_circles()
+    g, go = _case_grid(case)
+    U = oracle.prim_to_cons(go, case.V)
+    X, T, lst, cnt = _gpu_features(g, to_dev(U), 0)
+    inter = lst[:cnt].cpu().numpy()
+    rng = np.random.default_rng(0)
+    rows = np.concatenate([rng.choice(inter, 384, replace=False),
+                           rng.choice(X.shape[0], 128, replace=False)])
+    return X, T, rows
+
+
+def test_forward_parity(gpu, feature_rows):
+    X, T, rows = feature_rows
+    S = surrogate.Surrogate(seed=11)
+    Xs = X[torch.from_numpy(rows).cuda()].contiguous()
+    Y = S.forward(Xs)
+    torch.cuda.synchronize()
+    S.check_status()
+    P = mlp.from_block(S.params.cpu().numpy())
+    Yr, _ = mlp.forward(P, _bf16_as_f64(Xs), rounded=True)
+    diff = np.abs(Y.cpu().numpy() - Yr).max(axis=1)
+    # FP32 tensor-core accumulation vs FP64 sums: rare BF16 activation
+    # roundings land on the neighbouring value
+    assert np.median(diff) <= 1e-6
+    assert np.mean(diff > 1e-5) <= 0.03
+    assert diff.max() <= 3e-3
+    # softmax groups sum to one
+    Yg = Y.cpu().numpy().reshape(-1, 3, 3).sum(axis=2)
+    assert np.abs(Yg - 1).max() <= 1e-6
+
+
+def test_forward_ragged_rows(gpu, feature_rows):
+    """Row counts that are not a multiple of the 128-row tile."""
+    X, _, _ = feature_rows
+    S = surrogate.Surrogate(seed=3)
+    full = S.forward(X[:1000].contiguous()).cpu().numpy()
+    for n in (1, 127, 129, 333):
+        part = S.forward(X[:n].contiguous()).cpu().numpy()
+        assert np.array_equal(part, full[:n])
+
+
+def test_gradient_parity(gpu, feature_rows):
+    X, T, rows = feature_rows
+    S = surrogate.Surrogate(seed=12)
+    idx = torch.from_numpy(rows.astype(np.int32)).cuda()
+    loss, grads = S.gradients(X, T, idx)
+    torch.cuda.synchronize()
+    S.check_status()
+    P = mlp.from_block(S.params.cpu().numpy())
+    Xr = _bf16_as_f64(X[idx.long()])
+    Tr = T[idx.long()].cpu().numpy().astype(np.float64)
+    Lr, gr = mlp.loss_and_grads(P, Xr, Tr, rounded=True)
+    assert abs(loss.item() - Lr) <= 1e-5 * Lr
+    g = grads.cpu().numpy().astype(np.float64)
+    segs = {"W1": (mlp.W1, mlp.W2), "W2": (mlp.W2, mlp.W3), "W3": (mlp.W3, mlp.W4),
+            "W4": (mlp.W4, mlp.NWEIGHT), "b": (mlp.NWEIGHT, mlp.NPARAM)}
+    for name, (a, b) in segs.items():
+        ref = gr[a:b]
+        err = np.linalg.norm(g[a:b] - ref) / np.linalg.norm(ref)
+        assert err <= 1e-2, (name, err)
+    assert np.all(g[mlp.padding_mask()] == 0.0)
+
+
+def test_adam_step_parity(gpu, feature_rows):
+    X, T, rows = feature_rows
+    S = surrogate.Surrogate(seed=13)
+    master0 = S.master.cpu().numpy().astype(np.float64)
+    idx = torch.from_numpy(rows.astype(np.int32)).cuda()
+    S.gradients(X, T, idx)
+    g = S.grads.cpu().numpy().astype(np.float64)
+    from paper_2608_00746_b300.wenoc import _dptr, _stream, lib
+    st = lib().wc_mlp_adam(_dptr(S.master), _dptr(S.params), _dptr(S.grads), _dptr(S.m),
+                           _dptr(S.v), 1e-3, 1, _stream())
+    assert st == 0
+    torch.cuda.synchronize()
+    new_r, m_r, v_r = mlp.adam(master0, g, np.zeros_like(g), np.zeros_like(g), 1e-3, 1)
+    new = S.master.cpu().numpy().astype(np.float64)
+    assert np.abs(new - new_r).max() <= 1e-6 * max(1.0, np.abs(new_r).max())
+    assert np.all(S.grads.cpu().numpy() == 0.0)
+    P = mlp.from_block(S.params.cpu().numpy())
+    assert np.array_equal(P["W2"].reshape(-1), mlp.bf16(S.master.cpu().numpy()[mlp.W2:mlp.W3]))
+    assert np.all(new[mlp.padding_mask()] == 0.0)
+
+
+@pytest.fixture(scope="module")
+def trained():
+    """A surrogate trained on rows of a circles (N = 3) and a shock-bubble
+    (N = 2, third phase absent) state, snapshots at t = 0 and after a few
+    steps."""
+    ts = surrogate.TrainingSet(4_000_000)
+    for case in (inputs.circles_shock_2d(shape=(256, 256), seed=21, ncirc=24, rmin_cells=6,
+                                         rmax_cells=30),
+                 inputs.shock_bubble_2d(nx=256, ny=128, seed=22)):
+        g, go = _case_grid(case, precision="mixed")
+        U = to_dev(oracle.prim_to_cons(go, case.V))
+        g.bind(U)
+        for snap in range(3):
+            ts.add(g, U)
+            g.rk_step(cfl=case.cfl, nsteps=10)
+        g.sync_status()
+    ts.finish()
+    S = surrogate.Surrogate(seed=7)
+    losses = S.train(ts, steps=3000, batch=16384, lr=3e-3, lr_final=5e-5, seed=1)
+    return S, ts, losses
+
+
+def test_training_reduces_loss(gpu, trained):
+    S, ts, losses = trained
+    assert ts.n_interesting > 10000
+    first, last = losses[:5].mean(), losses[-50:].mean()
+    assert last <= 0.1 * first, (first, last)
+    # held-out rows (another seed) judge the fit
+    case = inputs.circles_shock_2d(shape=(128, 128), seed=99, ncirc=10, rmin_cells=6,
+                                   rmax_cells=25)
+    g, go = _case_grid(case)
+    U = oracle.prim_to_cons(go, case.V)
+    X, T, lst, cnt = _gpu_features(g, to_dev(U), 0)
+    sel = lst[:cnt]
+    Y = S.forward(X[sel].contiguous())
+    err_trained = (Y - T[sel]).pow(2).sum(1).mean().item()
+    untrained = surrogate.Surrogate(seed=7)
+    Yu = untrained.forward(X[sel].contiguous())
+    err_untrained = (Yu - T[sel]).pow(2).sum(1).mean().item()
+    ideal = torch.tensor(mlp.IDEAL * 3, dtype=torch.float32, device="cuda")
+    err_ideal = (ideal - T[sel]).pow(2).sum(1).mean().item()
+    assert err_trained <= 0.1 * err_untrained
+    assert err_trained <= 0.1 * err_ideal
+
+
+def _learned_grid(case, S, tau, counters=None):
+    g = wenoc.Grid(case.shape, case.dx, case.gamma, case.pinf, case.D, flux=case.flux,
+                   bc=case.bc, precision="learned")
+    g.set_mlp(S.params, tau=tau, counters=counters)
+    return g
+
+
+def test_learned_tau0_is_mixed_bitwise(gpu):
+    case = _small_circles()
+    S = surrogate.Surrogate(seed=5)
+    gm, go = _case_grid(case, "mixed")
+    U = to_dev(oracle.prim_to_cons(go, case.V))
+    gm.bind(U.clone())
+    gl = _learned_grid(case, S, 0.0)
+    gl.bind(U.clone())
+    Lm = gm.rhs(U)
+    Ll = gl.rhs(U)
+    gm.sync_status()
+    gl.sync_status()
+    assert torch.equal(Lm, Ll)
+
+
+def test_learned_run_matches_oracle_l1(gpu, trained):
+    S, _, _ = trained
+    case = inputs.circles_shock_2d(shape=(160, 160), seed=31, ncirc=12, rmin_cells=6,
+                                   rmax_cells=30)
+    N, d = case.N, 2
+    go = oracle.Grid(case.shape, case.dx, case.gamma, case.pinf, case.D, flux=case.flux,
+                     bc=case.bc)
+    U0 = oracle.prim_to_cons(go, case.V)
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+    gl = _learned_grid(case, S, TAU, cnt)
+    Ul = to_dev(U0)
+    gl.bind(Ul)
+    Uo = U0.copy()
+    for _ in range(20):
+        Uo, dt = oracle.rk3_step(go, Uo, cfl=case.cfl)
+        gl.rk_step(dt=dt)
+    gl.sync_status()
+    A = Ul.cpu().numpy()
+    l1 = l1_group(A, Uo, N, d)
+    assert l1.max() <= 1e-5, l1
+    al = A[N + d + 1:]
+    assert al.min() >= 0.0 and al.max() <= 1.0 + EPS_BOUND
+    assert np.abs(al.sum(0) - 1.0).max() < 1e-13   # unity sum to round-off, as FP64
+    decided, fallback = cnt.cpu().numpy()
+    assert decided > 0 and fallback < decided
+
+
+def test_learned_absent_phase_stays_zero(gpu, trained):
+    S, _, _ = trained
+    case = inputs.shock_bubble_2d(nx=96, ny=48, seed=4)
+    V = case.V
+    N = 3
+    # add an absent third phase (exact zeros) with the config-3 third material
+    V3 = np.zeros((2 * N + 3,) + V.shape[1:])
+    V3[0:2] = V[0:2]
+    V3[3:6] = V[2:5]
+    V3[6:8] = V[5:7]
+    g3 = list(case.gamma) + [inputs.PHASE3["gamma"]]
+    p3 = list(case.pinf) + [inputs.PHASE3["pinf"]]
+    D3 = list(case.D) + [0.0]
+    go = oracle.Grid(case.shape, case.dx, g3, p3, D3, flux=case.flux, bc=case.bc)
+    U = to_dev(oracle.prim_to_cons(go, V3))
+    g = wenoc.Grid(case.shape, case.dx, g3, p3, D3, flux=case.flux, bc=case.bc,
+                   precision="learned")
+    g.set_mlp(S.params, tau=TAU)
+    g.bind(U)
+    g.rk_step(cfl=case.cfl, nsteps=10)
+    g.sync_status()
+    A = U.cpu().numpy()
+    assert np.all(A[2] == 0.0) and np.all(A[N + 2 + 1 + 2] == 0.0)
+
+
+def test_trained_surrogate_gain(gpu, trained):
+    """What training buys: at the same acceptance threshold the trained
+    network's weights are taken on several times more (non-flat) face sides
+    than the untrained network's, both runs stay within the reduced-precision
+    L1 bound of the FP64 oracle, and the held-out reconstruction error of the
+    trained weights is far below that of the ideal (linear) weights."""
+    S, _, _ = trained
+    case = inputs.circles_shock_2d(shape=(160, 160), seed=32, ncirc=12, rmin_cells=6,
+                                   rmax_cells=30)
+    go = oracle.Grid(case.shape, case.dx, case.gamma, case.pinf, case.D, flux=case.flux,
+                     bc=case.bc)
+    U0 = oracle.prim_to_cons(go, case.V)
+    Uo, dts = U0.copy(), []
+    for _ in range(10):
+        Uo, dt = oracle.rk3_step(go, Uo, cfl=case.cfl)
+        dts.append(dt)
+    out = {}
+    for name, net in (("trained", S), ("untrained", surrogate.Surrogate(seed=7))):
+        cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+        g = _learned_grid(case, net, TAU, cnt)
+        U = to_dev(U0)
+        g.bind(U)
+        for dt in dts:
+            g.rk_step(dt=dt)
+        g.sync_status()
+        l1 = l1_group(U.cpu().numpy(), Uo, case.N, 2).max()
+        decided, fallback = cnt.cpu().numpy()
+        out[name] = (1.0 - fallback / decided, l1)
+    print("acceptance / L1:", out)
+    assert out["trained"][1] <= 1e-5 and out["untrained"][1] <= 1e-5
+    assert out["trained"][0] >= 3.0 * out["untrained"][0], out
