@@ -10,6 +10,13 @@ interior cells x 3 stages / step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+Beside the FP64 headline the line carries the mixed and learned precisions
+on the same workload (speed and group L1 against FP64 after the same steps),
+the learned-weight workload (2-D circles and shock, 2048 x 2048, N = 3) in all
+three precisions, and the surrogate's training record: before the timed
+region the surrogate is trained on the GPU from shock-bubble and 3-D
+spheres-and-shock states (``--no-learned`` skips all of this).
+
 ``--impl reference`` times the FP64 CPU oracle on this host's cores on the same
 workload (the oracle is the only other implementation of the method).
 Under torchrun each rank runs an independent replica (the workload has no
@@ -44,6 +51,14 @@ def parse():
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the surrogate training and the learned-precision lines")
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--train-batch", type=int, default=16384)
+    ap.add_argument("--tau", type=float, default=1e-4)
+    ap.add_argument("--n3d", type=int, default=256, help="edge of the 3-D training source")
+    ap.add_argument("--n5", type=int, default=2048, help="edge of the 2-D circles workload")
+    ap.add_argument("--steps5", type=int, default=20)
     return ap.parse_args()
 
 
@@ -185,6 +200,59 @@ def traffic_from_profile(kernel_hash):
     return d.get("dram_bytes_per_launch")
 
 
+# ---------------------------------------------------------------- surrogate
+def train_surrogate(args, dev):
+    """Trains the weight surrogate on the GPU: feature rows and plain-weight
+    targets of every face side of a 2-D shock-bubble state (1024 x 512, N = 2,
+    third phase absent; initial and two later snapshots) and of a 3-D
+    spheres-and-shock state (n3d^3, N = 3, after 25 steps), then
+    train_steps Adam steps of train_batch rows, half from the rows whose
+    plain weights differ from the ideal ones."""
+    import torch
+    from paper_2608_00746_b300 import inputs, surrogate, wenoc
+    t0 = time.time()
+    b = inputs.shock_bubble_2d(nx=1024, ny=512, seed=args.seed + 100)
+    s3 = inputs.spheres_shock_3d(n=args.n3d, seed=args.seed + 200)
+    rows = 3 * 2 * 2 * 1024 * 512 + 3 * 2 * args.n3d ** 3
+    ts = surrogate.TrainingSet(rows, device=dev)
+    for case, snaps, every in ((b, 3, 60), (s3, 1, 25)):
+        g = wenoc.Grid(case.shape, case.dx, case.gamma, case.pinf, case.D, flux=case.flux,
+                       bc=case.bc, precision="mixed")
+        U = g.prim_to_cons(torch.from_numpy(case.V).to(dev))
+        g.bind(U)
+        for k in range(snaps):
+            g.rk_step(cfl=case.cfl, nsteps=every if (k or case is s3) else 0)
+            ts.add(g, U)
+        g.sync_status()
+        del g, U
+    ts.finish()
+    t1 = time.time()
+    S = surrogate.Surrogate(seed=args.seed, device=dev)
+    losses = S.train(ts, steps=args.train_steps, batch=args.train_batch, lr=3e-3,
+                     lr_final=5e-5, seed=args.seed)
+    t2 = time.time()
+    info = {"rows": ts.nrows, "interesting_rows": ts.n_interesting,
+            "samples": args.train_steps * args.train_batch,
+            "loss_first": float(losses[:5].mean()), "loss_last": float(losses[-50:].mean()),
+            "data_seconds": round(t1 - t0, 2), "train_seconds": round(t2 - t1, 2),
+            "sources": "shock_bubble_2d 1024x512 (t0 + 2 snapshots), "
+                       f"spheres_shock_3d {args.n3d}^3 (after 25 steps)"}
+    del ts
+    torch.cuda.empty_cache()
+    return S, info
+
+
+def group_l1(a, b, N, D):
+    """max over variable groups (each mass, momentum vector, energy, each
+    fraction) of the L1 distance relative to the reference's L1 norm."""
+    a = a.reshape(a.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    grps = [[p] for p in range(N)] + [list(range(N, N + D)), [N + D]] + \
+        [[N + D + 1 + p] for p in range(N)]
+    return max(((a[g] - b[g]).abs().sum() / a[g].abs().sum().clamp_min(1e-300)).item()
+               for g in grps)
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -205,11 +273,16 @@ def run_ours(args):
     case = make_case(args, rank)
     N, D = case.N, case.dim
     cells = int(np.prod(case.shape))
+    learned = not args.no_learned
+    S, train_info = train_surrogate(args, dev) if learned else (None, None)
 
-    def make_grid(precision):
-        g = wenoc.Grid(case.shape, case.dx, case.gamma, case.pinf, case.D, flux=case.flux,
-                       bc=case.bc, precision=precision)
-        V = torch.from_numpy(case.V).to(dev)
+    def make_grid(precision, c=None, counters=None):
+        c = c or case
+        g = wenoc.Grid(c.shape, c.dx, c.gamma, c.pinf, c.D, flux=c.flux, bc=c.bc,
+                       precision=precision)
+        if precision == "learned":
+            g.set_mlp(S.params, tau=args.tau, counters=counters)
+        V = torch.from_numpy(c.V).to(dev)
         U = g.prim_to_cons(V)
         g.bind(U)
         return g, U
@@ -217,21 +290,23 @@ def run_ours(args):
     # L2 flush buffer (larger than the 126 MB L2), written between timed steps
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
-    def timed_steps(g, K, W):
+    def timed_steps(g, K, W, c=None):
         """K timed RK steps (events per step, L2 flushed in between) and the
         mean duration of the sweep launches inside them (event pairs the
-        library records around each sweep launch on the same stream)."""
+        library records around each direction's launches on the same
+        stream: the sweep, preceded in learned precision by the surrogate)."""
+        c = c or case
         for _ in range(W):
-            g.rk_step(cfl=case.cfl)
+            g.rk_step(cfl=c.cfl)
         barrier()
         s = torch.cuda.current_stream()
         evs = []
-        g.sweep_timing_begin(K * 3 * D)
+        g.sweep_timing_begin(K * 3 * c.dim)
         for _ in range(K):
             flush.fill_(1.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)
-            g.rk_step(cfl=case.cfl)
+            g.rk_step(cfl=c.cfl)
             e1.record(s)
             evs.append((e0, e1))
         barrier()
@@ -243,34 +318,71 @@ def run_ours(args):
     # FP64 DFMA probe of this GPU (context for the derived peak below)
     peak_probe = wenoc.fp64_peak() / 1e12
 
+    modes = ("fp64", "mixed", "learned") if learned else ("fp64", "mixed")
     results = {}
+    c5 = None
+    res5 = {}
     with Clocks(local) as clk:
         time.sleep(1.0)  # let the sampler start before the timed region
-        for prec in ("fp64", "mixed"):
+        for prec in modes:
             g, U = make_grid(prec)
             ms, sw = timed_steps(g, args.steps, args.warmup)
-            results[prec] = (ms, sw, g, U)
+            results[prec] = (ms, sw)
+            del g, U
+        if learned and rank == 0:
+            # the learned-weight workload: 2-D circles and shock, N = 3
+            from paper_2608_00746_b300 import inputs
+            c5 = inputs.circles_shock_2d(n=args.n5, seed=args.seed)
+            for prec in modes:
+                g, U = make_grid(prec, c5)
+                res5[prec] = timed_steps(g, args.steps5, 3, c5)
+                del g, U
+            # the surrogate's inference kernel alone (one direction)
+            g, U = make_grid("mixed", c5)
+            W5 = torch.empty((18, g.ncell), dtype=torch.float32, device=dev)
+            st5 = torch.zeros(1, dtype=torch.int32, device=dev)
+            for _ in range(3):
+                g.mlp_infer(U, 0, S.params, W5, st5)
+            barrier()
+            s_ = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s_)
+            for _ in range(10):
+                g.mlp_infer(U, 0, S.params, W5, st5)
+            e1.record(s_)
+            barrier()
+            infer_ms = e0.elapsed_time(e1) / 10
+            infer_rows = 2 * g.ncell
+            del g, U, W5
     clocks = clk.summary()
     # FP64 peak from unit counts and clock: 2 DFMA per clock per SM (ncu's
     # sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained = 296 per
     # cycle on 148 SMs), 2 flops each, at the maximum SM clock 2032 MHz.
     peak_fp64 = 2 * 2 * 148 * 2032e6 / 1e12
 
-    # matched accuracy: mixed vs FP64 after the same number of steps from the
-    # same initial state with the same time steps
-    g64, U64 = make_grid("fp64")
-    gmx, Umx = make_grid("mixed")
-    for _ in range(args.steps):
-        dt = g64.rk_step(cfl=case.cfl, want_dt=True)
-        gmx.rk_step(dt=dt)
-    a = U64.reshape(U64.shape[0], -1)
-    b = Umx.reshape(Umx.shape[0], -1)
-    # L1 distance per variable group (each mass, momentum vector, energy,
-    # each fraction), relative to the FP64 solution's L1 norm of the group
-    grps = [[p] for p in range(N)] + [list(range(N, N + D)), [N + D]] + \
-        [[N + D + 1 + p] for p in range(N)]
-    l1 = max(((a[g] - b[g]).abs().sum() / a[g].abs().sum().clamp_min(1e-300)).item()
-             for g in grps)
+    def matched_l1(c, K):
+        """Reduced modes against FP64 after K steps from the same initial
+        state with the same time steps: group L1 and, for the learned mode,
+        the share of non-flat face sides that took the surrogate's weights."""
+        g64, U64 = make_grid("fp64", c)
+        others = {}
+        cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+        for prec in modes[1:]:
+            others[prec] = make_grid(prec, c, counters=cnt if prec == "learned" else None)
+        for _ in range(K):
+            dt = g64.rk_step(cfl=c.cfl, want_dt=True)
+            for g, _ in others.values():
+                g.rk_step(dt=dt)
+        out = {prec: group_l1(U64, U, c.N, c.dim) for prec, (g, U) in others.items()}
+        dec, fb = cnt.tolist()
+        acc = (1.0 - fb / dec) if dec else None
+        for g, _ in others.values():
+            g.sync_status()
+        return out, acc
+
+    # matched accuracy on the headline workload
+    l1s, acc2 = matched_l1(case, args.steps)
+    l1 = l1s["mixed"]
 
     # end to end through the C ABI with host buffers: upload, step, download
     g, U = make_grid("fp64")
@@ -289,13 +401,14 @@ def run_ours(args):
     barrier()
     e2e_ms = e0.elapsed_time(e1) / args.steps
 
-    ms64, sw64, _, _ = results["fp64"]
-    msmx, swmx, _, _ = results["mixed"]
+    ms64, sw64 = results["fp64"]
+    msmx, swmx = results["mixed"]
+    msl = results["learned"][0] if learned else 0.0
     # max over ranks
-    vals = torch.tensor([ms64, msmx, e2e_ms], dtype=torch.float64, device=dev)
+    vals = torch.tensor([ms64, msmx, e2e_ms, msl], dtype=torch.float64, device=dev)
     if ws > 1:
         tdist.all_reduce(vals, op=tdist.ReduceOp.MAX)
-    ms64, msmx, e2e_ms = vals.tolist()
+    ms64, msmx, e2e_ms, msl = vals.tolist()
     value = ws * cells * 3 / (ms64 * 1e-3) / 1e6
     value_mx = ws * cells * 3 / (msmx * 1e-3) / 1e6
     e2e = ws * cells * 3 / (e2e_ms * 1e-3) / 1e6
@@ -333,6 +446,37 @@ def run_ours(args):
         "gpu_launches": args.steps * (1 + 3 * D),
         "csrc_hash": khash,
     }
+    if learned:
+        line["modes"]["learned"] = {
+            "value": round(ws * cells * 3 / (msl * 1e-3) / 1e6, 3), "ms_per_step": round(msl, 4),
+            "speedup_vs_fp64": round(ms64 / msl, 3), "l1_rel_vs_fp64_max_var": l1s["learned"],
+            "l1_steps": args.steps, "tau": args.tau, "accepted_face_sides": acc2,
+            "ms_per_direction": round(results["learned"][1], 4)}
+        line["surrogate_training"] = train_info
+    if learned and rank == 0:
+        l1_5, acc5 = matched_l1(c5, args.steps5)
+        cells5 = int(np.prod(c5.shape))
+        w5 = {}
+        for prec in modes:
+            ms5, sw5 = res5[prec]
+            w5[prec] = {"value": round(cells5 * 3 / (ms5 * 1e-3) / 1e6, 3),
+                        "ms_per_step": round(ms5, 4), "ms_per_direction": round(sw5, 4)}
+            if prec != "fp64":
+                w5[prec]["l1_rel_vs_fp64_max_var"] = l1_5[prec]
+                w5[prec]["speedup_vs_fp64"] = round(res5["fp64"][0] / ms5, 3)
+        w5["learned"]["tau"] = args.tau
+        w5["learned"]["accepted_face_sides"] = acc5
+        fl_row = 2 * (30 * 64 + 64 * 64 * 2 + 64 * 9)
+        infer_tf = fl_row * infer_rows / (infer_ms * 1e-3) / 1e12
+        w5["surrogate_inference"] = {
+            "kernel": "k_mlp_fwd<SrcState<3,2>> (feature gather + 4 tcgen05 layers)",
+            "rows": infer_rows, "ms_per_launch": round(infer_ms, 4),
+            "achieved_tflops": round(infer_tf, 2), "flops_per_row": fl_row,
+            "frac_of_bf16_measured": round(infer_tf / 1794.1, 4)}
+        line["learned_workload"] = {
+            "workload": f"circles_shock_2d {args.n5}x{args.n5} N=3 HLL CFL 0.2 outflow "
+                        "(64 circles, radii 10-80 cells, shock ratio 1e3, seeded)",
+            "steps": args.steps5, "l1_steps": args.steps5, "modes": w5}
     if rank == 0 and not args.no_cpu_baseline:
         try:
             small = make_case(args, 0)
