@@ -77,12 +77,21 @@ typedef struct {
                                  wc_set_mlp) */
   int energy_limiter;         /* 1: Eq. 21 applied (default); 0: skipped */
   int bc[6];                  /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi: WC_BC_* */
-  int seg;                    /* cells per thread along a sweep; 0 = automatic */
-  int block;                  /* threads per block of the sweep (32..128); 0 = automatic */
-  int blocks_per_sm;          /* sweep blocks per SM (1..4); 0 = automatic */
+  int seg;                    /* sweep schedule.  0 (default): one cell per
+                                 lane, each warp takes windows of 32 cells of
+                                 a pencil (30 updated) from a dynamic queue;
+                                 > 0: each thread marches segments of seg
+                                 cells of one pencil */
+  int block;                  /* threads per block of the segment sweep
+                                 (32..128); 0 = automatic; the window sweep
+                                 uses 128 */
+  int blocks_per_sm;          /* resident sweep blocks per SM (1..4); 0 = automatic */
 } wc_grid_desc;
 
 typedef struct wc_grid wc_grid;
+
+/* Calls that enqueue work on one grid must be ordered on one stream: the
+ * grid's status word and window queue live in its workspace. */
 
 /* Creates a grid handle from desc (copied).  Host only, no device work. */
 wc_status wc_init_grid(const wc_grid_desc *desc, wc_grid **out);

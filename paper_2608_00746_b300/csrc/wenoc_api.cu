@@ -10,6 +10,7 @@
 #include "../../include/wenoc.h"
 #include "wenoc_kernels.cuh"
 #include "wenoc_mlp.cuh"
+#include "wenoc_window.cuh"
 
 using namespace wc;
 
@@ -27,6 +28,7 @@ struct wc_grid {
   unsigned* status = nullptr;
   unsigned long long* rate = nullptr;
   double* dt = nullptr;
+  unsigned* ticket = nullptr;  // window queue (two words, zero between launches)
   // learned precision: the surrogate's parameter block (caller's device
   // memory), acceptance threshold, optional counters and the weight buffer
   // (in the workspace, after its 256-byte tail)
@@ -162,6 +164,7 @@ extern "C" wc_status wc_set_state(wc_grid* g, double* U_dev, void* ws, size_t ws
     g->rate = (unsigned long long*)tail;
     g->dt = (double*)(tail + 8);
     g->status = (unsigned*)(tail + 16);
+    g->ticket = (unsigned*)(tail + 32);
     g->Wbuf = g->d.precision == WC_PREC_LEARNED ? (float*)(tail + 256) : nullptr;
     // the workspace comes uninitialised: clear rate, dt and the status word
     cudaError_t e = cudaMemset(tail, 0, 256);
@@ -171,6 +174,7 @@ extern "C" wc_status wc_set_state(wc_grid* g, double* U_dev, void* ws, size_t ws
     g->rate = nullptr;
     g->dt = nullptr;
     g->status = nullptr;
+    g->ticket = nullptr;
     g->Wbuf = nullptr;
   }
   return WC_OK;
@@ -225,29 +229,6 @@ static long sweep_threads(const wc_grid* g) {
   return 148L * bps * block;
 }
 
-// Segment length: the smallest cost max-items-per-thread x (seg + 2)
-// (reconstructions per thread, two of them redundant per segment), over
-// seg in [4, 64]; ties go to the longer segment.
-static int auto_seg(const wc_grid* g, int dir) {
-  if (g->d.seg > 0) return g->d.seg;
-  const long n = g->d.n[dir];
-  const long npencil = g->ncell / n;
-  const long T = sweep_threads(g);
-  long best_cost = -1;
-  int best = 8;
-  for (int seg = 4; seg <= 64; seg++) {
-    long nseg = (n + seg - 1) / seg;
-    long items = npencil * nseg;
-    long per_thread = (items + T - 1) / T;
-    long cost = per_thread * (seg + 2);
-    if (best_cost < 0 || cost <= best_cost) {
-      best_cost = cost;
-      best = seg;
-    }
-  }
-  return best;
-}
-
 static SweepArgs make_args(const wc_grid* g, int dir, const double* U, double* L) {
   SweepArgs a;
   memset(&a, 0, sizeof(a));
@@ -261,9 +242,17 @@ static SweepArgs make_args(const wc_grid* g, int dir, const double* U, double* L
   a.n = g->d.n[dir];
   a.stride = dir == 0 ? 1 : (dir == 1 ? (long)a.nx : (long)a.nx * a.ny);
   a.npencil = g->ncell / a.n;
-  a.seg = auto_seg(g, dir);
-  a.nseg = (a.n + a.seg - 1) / a.seg;
-  a.max_threads = sweep_threads(g);
+  if (g->d.seg > 0) {
+    // per-thread segment march of seg cells
+    a.seg = g->d.seg;
+    a.nseg = (a.n + a.seg - 1) / a.seg;
+  } else {
+    // one cell per lane, windows of WIN cells from a dynamic queue
+    a.nwin = (a.n + WIN - 1) / WIN;
+    a.ticket = g->ticket;
+  }
+  // window schedule: blocks_per_sm when given, else the occupancy limit
+  a.max_threads = (g->d.seg > 0 || g->d.blocks_per_sm > 0) ? sweep_threads(g) : 0;
   a.inv_dx = 1.0 / g->d.dx[dir];
   a.bclo = g->d.bc[2 * dir];
   a.bchi = g->d.bc[2 * dir + 1];
@@ -575,8 +564,8 @@ wc_status wc_internal_rk_with_scratch(wc_grid* g, double* U, char* scratch, doub
   // save and restore only the bindings (the grid also owns timing events)
   struct Bind {
     double* U; char* ws; size_t ws_bytes; double *B1, *B2, *Lacc;
-    unsigned long long* rate; double* dt; unsigned* status;
-  } saved{g->U, g->ws, g->ws_bytes, g->B1, g->B2, g->Lacc, g->rate, g->dt, g->status};
+    unsigned long long* rate; double* dt; unsigned* status; unsigned* ticket;
+  } saved{g->U, g->ws, g->ws_bytes, g->B1, g->B2, g->Lacc, g->rate, g->dt, g->status, g->ticket};
   size_t state = (size_t)g->nv * g->ncell * sizeof(double);
   state = (state + 255) / 256 * 256;
   char* tail = scratch + 3 * state;
@@ -591,6 +580,7 @@ wc_status wc_internal_rk_with_scratch(wc_grid* g, double* U, char* scratch, doub
   g->rate = (unsigned long long*)tail;
   g->dt = (double*)(tail + 8);
   g->status = (unsigned*)(tail + 16);
+  g->ticket = (unsigned*)(tail + 32);
   wc_status r = wc_rk_step(g, cfl, dt_fixed, nsteps, nullptr, reinterpret_cast<void*>(st));
   if (status_out) *status_out = g->status;
   g->U = saved.U;
@@ -602,6 +592,7 @@ wc_status wc_internal_rk_with_scratch(wc_grid* g, double* U, char* scratch, doub
   g->rate = saved.rate;
   g->dt = saved.dt;
   g->status = saved.status;
+  g->ticket = saved.ticket;
   return r;
 }
 

@@ -88,6 +88,45 @@ __device__ __forceinline__ float max_nonneg(float a, float b) {
   int ia = __float_as_int(a), ib = __float_as_int(b);
   return __int_as_float(ia > ib ? ia : ib);
 }
+// Comparisons decided on the bit patterns (integer pipe; the FP64 pipe is
+// the sweep's bottleneck).  For doubles that are >= +0 (not NaN) the bit
+// patterns order like the values; any double is <= 0 iff its pattern, read
+// as a signed integer, is <= 0 (+0, -0 and the negatives).
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool le0(double x) { return dbits(x) <= 0; }
+__device__ __forceinline__ bool le0(float x) { return x <= 0.0f; }
+__device__ __forceinline__ bool ge0(double x) {
+  const long long b = dbits(x);
+  return b >= 0 || b == (long long)0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool ge0(float x) { return x >= 0.0f; }
+// a < b and min(a, b) for a, b >= +0
+__device__ __forceinline__ bool lt_nonneg(double a, double b) { return dbits(a) < dbits(b); }
+__device__ __forceinline__ bool lt_nonneg(float a, float b) { return a < b; }
+__device__ __forceinline__ double min_nonneg(double a, double b) {
+  return __longlong_as_double(dbits(a) < dbits(b) ? dbits(a) : dbits(b));
+}
+// lo < x < hi for x of any sign, 0 < lo < hi (a NaN fails)
+__device__ __forceinline__ bool in_range(double x, double lo, double hi) {
+  const long long b = dbits(x);
+  return b > dbits(lo) && b < dbits(hi);
+}
+__device__ __forceinline__ bool in_range(float x, float lo, float hi) { return x > lo && x < hi; }
+// min / max of two non-NaN doubles of any sign on the integer pipe: the key
+// b ^ ((b >> 63) & 0x7FF..F) orders like the values (-0 below +0)
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = dbits(x);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ double dmin(double a, double b) { return dkey(b) < dkey(a) ? b : a; }
+__device__ __forceinline__ double dmax(double a, double b) { return dkey(b) > dkey(a) ? b : a; }
+__device__ __forceinline__ float dmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float dmax(float a, float b) { return fmaxf(a, b); }
+// infinite or NaN
+__device__ __forceinline__ bool not_finite(double x) {
+  return (__double2hiint(x) & 0x7ff00000) == 0x7ff00000;
+}
+
 // 2^-e(m) with e(m) the binary exponent of m > 0 (m * scale in [1, 2)), or 0
 // when m is outside [2^-1000, 2^1000] (caller takes a slower exact path).
 __device__ __forceinline__ double exp_scale(double m) {
@@ -100,6 +139,16 @@ __device__ __forceinline__ float exp_scale(float m) {
   if (e < 1 || e > 253) return 0.0f;
   return __int_as_float((254 - e) << 23);
 }
+// b * sc for b >= 0 and sc a power of two from exp_scale: for a normal b
+// whose product stays normal, the exponent field is shifted on the integer
+// pipe (exact); otherwise the multiplication does it.
+__device__ __forceinline__ double mul_pow2(double b, double sc) {
+  const long long bb = dbits(b);
+  const long long r = bb + (dbits(sc) - 0x3FF0000000000000LL);
+  if (bb == 0) return 0.0;
+  return ((bb >> 52) >= 1 && (r >> 52) >= 1) ? __longlong_as_double(r) : b * sc;
+}
+__device__ __forceinline__ float mul_pow2(float b, float sc) { return b * sc; }
 
 // ------------------------------------------------------------------ EOS
 // Mixture rules and Eq. 27.  V gets u and P; masses and fractions are copies.
@@ -122,7 +171,7 @@ __device__ __forceinline__ void cons_to_prim(const Mat& m, const double* U, doub
   // one reciprocal for 1/rho and 1/sum A alpha
   double inv, inv_sA;
   double prod = rho * sA;
-  if (prod > 1e-280 && prod < 1e280) {
+  if (in_range(prod, 1e-280, 1e280)) {
     double r = rcp_nr(prod);
     inv = sA * r;
     inv_sA = rho * r;
@@ -194,7 +243,7 @@ __device__ __forceinline__ double psi_cons(const Mat& m, const double* U) {
     if (m.hasD) s = fma(m.D[p], U[p], s);
   }
   double ke = 0.0;
-  if (rho > 1e-280) ke = 0.5 * mm * rcp_nr(rho);
+  if (in_range(rho, 1e-280, 1.7e308)) ke = 0.5 * mm * rcp_nr(rho);
   else if (rho > 0.0) ke = 0.5 * mm / rho;
   return U[I::E] - ke - s;
 }
@@ -212,19 +261,20 @@ __device__ __forceinline__ Stencil<T> stencil(T a, T b, T c, T d, T e) {
   return Stencil<T>{c, a - c, b - c, d - c, e - c};
 }
 
-// Smoothness indicators of the three sub-stencils (Jiang-Shu), scaled by 12
-// (13 t1^2 + 3 t2^2); Eq. 15 uses only their ratios.  The mirrored stencil of
-// the right face has the same three values in reverse order.
+// Smoothness indicators of the three sub-stencils (Jiang-Shu), scaled by
+// 12/13 (t1^2 + (3/13) t2^2); Eq. 15 uses only their ratios.  The mirrored
+// stencil of the right face has the same three values in reverse order.
 template <typename T>
 __device__ __forceinline__ void smoothness(const Stencil<T>& s, T& b0, T& b1, T& b2) {
-  T t1 = s.da - T(2) * s.db, t2 = s.da - T(4) * s.db;
-  b0 = T(13) * t1 * t1 + T(3) * t2 * t2;
+  const T c = T(3) / T(13);
+  T t1 = fma(T(-2), s.db, s.da), t2 = fma(T(-4), s.db, s.da);
+  b0 = fma(t1, t1, (c * t2) * t2);
   t1 = s.db + s.dd;
   t2 = s.db - s.dd;
-  b1 = T(13) * t1 * t1 + T(3) * t2 * t2;
-  t1 = s.de - T(2) * s.dd;
-  t2 = s.de - T(4) * s.dd;
-  b2 = T(13) * t1 * t1 + T(3) * t2 * t2;
+  b1 = fma(t1, t1, (c * t2) * t2);
+  t1 = fma(T(-2), s.dd, s.de);
+  t2 = fma(T(-4), s.dd, s.de);
+  b2 = fma(t1, t1, (c * t2) * t2);
 }
 
 template <typename T> __device__ __forceinline__ T tiny_norm();
@@ -261,7 +311,7 @@ __device__ __forceinline__ W6<T> weights_of(const Stencil<T>& st) {
   T mx = max_nonneg(b0, max_nonneg(b1, b2));
   T sc = exp_scale(mx);
   if (!is_pos_zero(sc)) {
-    T x0 = b0 * sc, x1 = b1 * sc, x2 = b2 * sc;
+    T x0 = mul_pow2(b0, sc), x1 = mul_pow2(b1, sc), x2 = mul_pow2(b2, sc);
     T s0 = x0 * x0, s1 = x1 * x1, s2 = x2 * x2;
     T p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
     w.aL0 = d0 * p12;
@@ -272,7 +322,7 @@ __device__ __forceinline__ W6<T> weights_of(const Stencil<T>& st) {
     w.aR2 = d2 * p12;
     T sumL = w.aL0 + w.aL1 + w.aL2;
     T sumR = w.aR0 + w.aR1 + w.aR2;
-    if (sumL >= tiny_norm<T>() && sumR >= tiny_norm<T>()) {
+    if (!lt_nonneg(sumL, tiny_norm<T>()) && !lt_nonneg(sumR, tiny_norm<T>())) {
       T r = rcp_nr(sumL * sumR) * sixth;
       w.invL = sumR * r;
       w.invR = sumL * r;
@@ -317,12 +367,16 @@ __device__ __forceinline__ W6<T> weights_of(const Stencil<T>& st) {
 
 // Eq. 10 at x_{i+1/2} (fL) and x_{i-1/2} (fR): the candidates' values minus
 // f_i, times 6, are 2da-7db, 2dd-db, 5dd-de (left face) and the mirror images.
+// The operations are written as explicit fused multiply-adds, so every
+// inlined copy rounds identically whatever the compiler shares between them.
 template <typename T>
 __device__ __forceinline__ void reconstruct(const W6<T>& w, const Stencil<T>& s, T& fL, T& fR) {
-  T qL0 = T(2) * s.da - T(7) * s.db, qL1 = T(2) * s.dd - s.db, qL2 = T(5) * s.dd - s.de;
-  T qR0 = T(2) * s.de - T(7) * s.dd, qR1 = T(2) * s.db - s.dd, qR2 = T(5) * s.db - s.da;
-  fL = s.c + (w.aL0 * qL0 + w.aL1 * qL1 + w.aL2 * qL2) * w.invL;
-  fR = s.c + (w.aR0 * qR0 + w.aR1 * qR1 + w.aR2 * qR2) * w.invR;
+  const T qL0 = fma(T(2), s.da, T(-7) * s.db), qL1 = fma(T(2), s.dd, -s.db),
+          qL2 = fma(T(5), s.dd, -s.de);
+  const T qR0 = fma(T(2), s.de, T(-7) * s.dd), qR1 = fma(T(2), s.db, -s.dd),
+          qR2 = fma(T(5), s.db, -s.da);
+  fL = fma(fma(w.aL2, qL2, fma(w.aL1, qL1, w.aL0 * qL0)), w.invL, s.c);
+  fR = fma(fma(w.aR2, qR2, fma(w.aR1, qR1, w.aR0 * qR0)), w.invR, s.c);
 }
 
 // ------------------------------------------------------------------ limiters
@@ -334,15 +388,16 @@ __device__ __forceinline__ double theta_pos(double fb, double fL, double fR) {
   // common case decided on the sign bits (a -0.0 takes the exact path below,
   // which returns 1 as well)
   if (!(has_sign(fC) | has_sign(fL) | has_sign(fR))) return 1.0;
-  double m = fmin(fC, fmin(fL, fR));
-  if (m >= 0.0) return 1.0;
-  if (fb <= 0.0) return 0.0;
-  double den = fb - m;
-  double t = (den > 1e-300 && den < 1e300) ? fb * rcp_nr(den) : fb / den;
-  return fmin(t, 1.0);
+  const double m = dmin(fC, dmin(fL, fR));
+  if (ge0(m)) return 1.0;
+  if (le0(fb)) return 0.0;
+  const double den = fb - m;
+  const double t = in_range(den, 1e-300, 1e300) ? fb * rcp_nr(den) : fb / den;
+  return min_nonneg(t, 1.0);
 }
 
 __device__ __forceinline__ double theta_lower(double fb, double fC, double fL, double fR) {
+  if (!(has_sign(fC) | has_sign(fL) | has_sign(fR))) return 1.0;
   double m = fmin(fC, fmin(fL, fR));
   if (m >= 0.0) return 1.0;
   if (fb <= 0.0) return 0.0;
@@ -381,13 +436,13 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
 #pragma unroll
   for (int p = 0; p < N; p++) {
     double mb = Ub[p], ab = Ub[I::A(p)];
-    double tp = fmin(theta_pos(mb, mL[p], mR[p]), theta_pos(ab, aL[p], aR[p]));
-    if (tp < 1.0) {
+    double tp = min_nonneg(theta_pos(mb, mL[p], mR[p]), theta_pos(ab, aL[p], aR[p]));
+    if (lt_nonneg(tp, 1.0)) {
       mL[p] = nonneg(fma(tp, mL[p] - mb, mb));
       mR[p] = nonneg(fma(tp, mR[p] - mb, mb));
       aL[p] = nonneg(fma(tp, aL[p] - ab, ab));
       aR[p] = nonneg(fma(tp, aR[p] - ab, ab));
-      th17 = fmin(th17, tp);
+      th17 = min_nonneg(th17, tp);
     }
   }
   // Eq. 19: unity sum on each face
@@ -397,7 +452,8 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
     SL += aL[p];
     SR += aR[p];
   }
-  if (!(SL > 0.0) || !(SR > 0.0)) {
+  // (the face fractions are >= 0 here: raw faces with theta = 1, or clamped)
+  if (dbits(SL) <= 0 || dbits(SR) <= 0) {
     // every fraction of a face limited to zero: first order for the cell
 #pragma unroll
     for (int p = 0; p < N; p++) {
@@ -406,16 +462,16 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
     }
     th17 = 0.0;
   } else {
-    if (SL != 1.0) {
-      double r = (SL > 1e-300 && SL < 1e300) ? rcp_nr(SL) : 1.0 / SL;
+    if (dbits(SL) != dbits(1.0)) {
+      double r = in_range(SL, 1e-300, 1e300) ? rcp_nr(SL) : 1.0 / SL;
 #pragma unroll
       for (int p = 0; p < N; p++) {
         mL[p] *= r;
         aL[p] *= r;
       }
     }
-    if (SR != 1.0) {
-      double r = (SR > 1e-300 && SR < 1e300) ? rcp_nr(SR) : 1.0 / SR;
+    if (dbits(SR) != dbits(1.0)) {
+      double r = in_range(SR, 1e-300, 1e300) ? rcp_nr(SR) : 1.0 / SR;
 #pragma unroll
       for (int p = 0; p < N; p++) {
         mR[p] *= r;
@@ -427,14 +483,15 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
   // Eq. 17 and Eq. 19 left every face value unchanged, the recomputed thetas
   // are those of Eq. 17, all one)
   double thi = 1.0;
-  if (th17 < 1.0 || SL != 1.0 || SR != 1.0) {
+  if (lt_nonneg(th17, 1.0) || dbits(SL) != dbits(1.0) || dbits(SR) != dbits(1.0)) {
 #pragma unroll
     for (int p = 0; p < N; p++) {
-      double tp = fmin(theta_pos(Ub[p], mL[p], mR[p]), theta_pos(Ub[I::A(p)], aL[p], aR[p]));
-      thi = fmin(thi, tp);
+      double tp =
+          min_nonneg(theta_pos(Ub[p], mL[p], mR[p]), theta_pos(Ub[I::A(p)], aL[p], aR[p]));
+      thi = min_nonneg(thi, tp);
     }
   }
-  if (thi < 1.0) {
+  if (lt_nonneg(thi, 1.0)) {
 #pragma unroll
     for (int p = 0; p < N; p++) {
       double mb = Ub[p], ab = Ub[I::A(p)];
@@ -480,7 +537,7 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
     double pR = psi_prim<N, D>(m, aR, PR);
     double pC = psi_cons<N, D>(m, UC);
     thpsi = theta_lower(pb, pC, pL, pR);
-    if (thpsi < 1.0) {
+    if (lt_nonneg(thpsi, 1.0)) {
 #pragma unroll
       for (int v = 0; v < I::NV; v++) {
         FL.U[v] = fma(thpsi, FL.U[v] - Ub[v], Ub[v]);
@@ -523,7 +580,7 @@ __device__ __forceinline__ TF sound_speed(const Mat& m, const double* U, TF rho,
   }
   // c = sqrt(num / (den rho)) = num / sqrt(num den rho)
   TF x = num * den * rho;
-  if (x > TF(1e-30) && x < TF(1e30)) return num * rsqrt_nr(x);
+  if (in_range(x, TF(1e-30), TF(1e30))) return num * rsqrt_nr(x);
   return sqrt(num / (den * rho));
 }
 
@@ -572,8 +629,8 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
   const TF PL = TF(L.P), PR = TF(R.P);
   const TF cL = sound_speed<N, D, TF>(m, L.U, rL, PL);
   const TF cR = sound_speed<N, D, TF>(m, R.U, rR, PR);
-  const TF sL = fmin(uL - cL, uR - cR);
-  const TF sR = fmax(uL + cL, uR + cR);
+  const TF sL = dmin(uL - cL, uR - cR);
+  const TF sR = dmax(uL + cL, uR + cR);
   // remainder energy Et_K = sum A alpha_K (P_K - Pb) + rho_K (|u_K|^2 - |ub|^2)/2
   TF AaL = TF(0), AaR = TF(0);
 #pragma unroll
@@ -599,14 +656,14 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
     // ---------------- HLL
     double kd, sRd;
     TF k;
-    if (sL >= TF(0)) {
+    if (ge0(sL)) {
       k = TF(0);
-    } else if (sR <= TF(0)) {
+    } else if (le0(sR)) {
       k = TF(-1);  // F_L + (-1)((F_L - F_R) + s_R (U_R - U_L)) with s_R = 0
     } else {
       k = sL * rcp_nr(sR - sL);
     }
-    const TF sRu = (sR <= TF(0)) ? TF(0) : sR;
+    const TF sRu = le0(sR) ? TF(0) : sR;
     kd = double(k);
     sRd = double(sRu);
     uhat = uLd + kd * (uLd - uRd);
@@ -656,8 +713,8 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
   bool left;
   TF sK, chi, sS;
   double sSd;  // contact speed in FP64 (ub_n + correction) for the momentum flux
-  if (sL >= TF(0) || sR <= TF(0)) {
-    left = sL >= TF(0);
+  if (ge0(sL) || le0(sR)) {
+    left = ge0(sL);
     sK = TF(0);
     chi = TF(1);
     sS = left ? uL : uR;

@@ -1,11 +1,16 @@
 // wenoc_fp64.cu -- instantiations of the direction sweep with reconstruction
 // type double and flux type double for N = 1..5 phases and d = 1..3 directions.
 #include "wenoc_kernels.cuh"
+#include "wenoc_window.cuh"
 
 namespace wc {
 
 template <int N, int D>
 static cudaError_t go(const SweepArgs& a, const Mat& m, int block, cudaStream_t st) {
+  if (a.nwin > 0) {
+    const int bps = (int)(a.max_threads / (148L * 128));  // 0: occupancy limit
+    return launch_window<N, D, double, double, 0>(a, m, bps, st);
+  }
   const int smem = Ring<N, D, double>::BYTES * block;
   auto k = k_sweep<N, D, double, double>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

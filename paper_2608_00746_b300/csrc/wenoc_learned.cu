@@ -3,11 +3,16 @@
 // surrogate's weights accepted against the plain ones) for N = 1..3 phases
 // and d = 1..3 directions.
 #include "wenoc_kernels.cuh"
+#include "wenoc_window.cuh"
 
 namespace wc {
 
 template <int N, int D>
 static cudaError_t go(const SweepArgs& a, const Mat& m, int block, cudaStream_t st) {
+  if (a.nwin > 0) {
+    const int bps = (int)(a.max_threads / (148L * 128));  // 0: occupancy limit
+    return launch_window<N, D, float, float, 1>(a, m, bps, st);
+  }
   const int smem = Ring<N, D, float>::BYTES * block;
   auto k = k_sweep<N, D, float, float, 1>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -47,6 +47,11 @@ struct SweepArgs {
   const float* Wm;
   float tau;
   unsigned long long* lcount;
+  // window schedule (nwin > 0, wenoc_window.cuh): windows per pencil, the
+  // two-word queue (next window, warps finished) and the launched warps
+  int nwin;
+  unsigned* ticket;
+  unsigned nwarps;
 };
 
 enum { BC_PERIODIC = 0, BC_REFLECTIVE = 1, BC_OUTFLOW = 2 };
@@ -253,7 +258,7 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
           double val = (a.kind == 1 ? 1.0 : -1.0) * (F[v] - Fprev[v]) * a.inv_dx;
           if (a.kind == 0 && v >= N + D + 1) val = fma(Uprev[v], du, val);
           long idx = (long)v * a.ncell + cell;
-          if (!(fabs(val) <= 1.7e308)) bad |= ST_NAN;
+          if (not_finite(val)) bad |= ST_NAN;
           if (a.mode == 0) {
             a.L[idx] = val;
           } else if (a.mode == 1) {

@@ -1,0 +1,295 @@
+// wenoc_window.cuh -- the direction sweep with one cell per lane: a warp
+// takes a window of 32 consecutive cells of one pencil from a dynamic queue,
+// reconstructs and limits all 32 (Eq. 15-21), solves the Riemann problems at
+// the 31 faces between them with the neighbour's face state from a warp
+// shuffle, and updates the 30 inner cells.  The two stencil cells beyond
+// each end come from four extra conversions.  Windows are handed out one
+// at a time (an atomic ticket per warp), so warps that meet cheap cells take
+// more windows: the cost of the limiter branches, clustered in space, no
+// longer sets the time of whole SMs.
+#pragma once
+#include "wenoc_sweep.cuh"
+
+namespace wc {
+
+constexpr int WIN = 30;        // cells updated per window
+constexpr int WIN_SLOTS = 36;  // cells c0-3 .. c0+32 held in shared memory
+
+template <int N, int D, typename T>
+struct WinSmem {
+  static constexpr int SLOTD = Ring<N, D, T>::SLOTD;     // doubles per cell slot
+  static constexpr int WARP_DOUBLES = WIN_SLOTS * SLOTD;  // per warp
+};
+
+template <int N, int D>
+__device__ __forceinline__ void shfl_face_down(const Face<N, D>& f, Face<N, D>& g) {
+  using I = Idx<N, D>;
+#pragma unroll
+  for (int v = 0; v < I::NV; v++) g.U[v] = __shfl_down_sync(0xffffffffu, f.U[v], 1);
+#pragma unroll
+  for (int j = 0; j < D; j++) g.u[j] = __shfl_down_sync(0xffffffffu, f.u[j], 1);
+  g.P = __shfl_down_sync(0xffffffffu, f.P, 1);
+}
+
+// One window: lane k owns cell c = c0 - 1 + k; slot s of `slots` holds the
+// primitive state of cell c0 - 3 + s (pressure in FP64, V in T).  Lanes
+// 1..30 update cells c0 .. c0 + 29 (those below a.n).
+template <int N, int D, typename T, typename TF, int LW>
+__device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, long base, int c0,
+                                             double* slots, double dt, unsigned& bad,
+                                             unsigned* lstat) {
+  using I = Idx<N, D>;
+  constexpr int NV = I::NV;
+  constexpr int SLOTD = WinSmem<N, D, T>::SLOTD;
+  const int lane = threadIdx.x & 31;
+  auto load_cons = [&](int c, double* u) {
+    bool flip;
+    const int j = bc_index(c, a.n, a.bclo, a.bchi, flip);
+    const long cell = base + (long)j * a.stride;
+#pragma unroll
+    for (int k = 0; k < NV; k++) u[k] = __ldg(a.U + (long)k * a.ncell + cell);
+#pragma unroll
+    for (int jj = 0; jj < D; jj++) {
+      long long mask = (flip && jj == a.dir) ? (long long)0x8000000000000000ULL : 0LL;
+      u[I::U(jj)] = __longlong_as_double(__double_as_longlong(u[I::U(jj)]) ^ mask);
+    }
+  };
+  auto store_slot = [&](int s, const double* u) {
+    double v[NV];
+    cons_to_prim<N, D>(m, u, v);
+    double* sl = slots + s * SLOTD;
+    sl[0] = v[I::E];
+    T* Vs = reinterpret_cast<T*>(sl + 1);
+#pragma unroll
+    for (int k = 0; k < NV; k++) Vs[k] = T(v[k]);
+  };
+
+  const int c = c0 - 1 + lane;
+  double Ub[NV];
+  load_cons(c, Ub);
+  store_slot(lane + 2, Ub);
+  if (lane < 4) {
+    const int s = lane < 2 ? lane : 32 + lane;  // slots 0, 1, 34, 35
+    double u[NV];
+    load_cons(c0 - 3 + s, u);
+    store_slot(s, u);
+  }
+  __syncwarp();
+  const T* V[5];
+#pragma unroll
+  for (int k = 0; k < 5; k++) V[k] = reinterpret_cast<const T*>(slots + (lane + k) * SLOTD + 1);
+  const double Pb = slots[(lane + 2) * SLOTD];
+
+  // Eq. 16: masses and fractions with the weights of the masses
+  double mL[N], mR[N], aL[N], aR[N];
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    Stencil<T> st = stencil<T>(V[0][p], V[1][p], V[2][p], V[3][p], V[4][p]);
+    W6<T> w = weights_of<T>(st);
+    const int ia = I::A(p);
+    const Stencil<T> sa = stencil<T>(V[0][ia], V[1][ia], V[2][ia], V[3][ia], V[4][ia]);
+    if constexpr (LW != 0) {
+      // learned weights of an interior cell, accepted per face side when the
+      // mass and the fraction reconstructed with them are each within tau
+      // times their stencil's range of the plain reconstructions (boundary
+      // cells keep the plain weights)
+      if (p < 3 && c >= 0 && c < a.n) {
+        const float* Wp = a.Wm + (long)(3 * p) * a.ncell + base + (long)c * a.stride;
+        W6<T> wl;
+        wl.aL0 = T(__ldg(Wp));
+        wl.aL1 = T(__ldg(Wp + a.ncell));
+        wl.aL2 = T(__ldg(Wp + 2 * a.ncell));
+        wl.aR0 = T(__ldg(Wp + 9 * a.ncell));
+        wl.aR1 = T(__ldg(Wp + 10 * a.ncell));
+        wl.aR2 = T(__ldg(Wp + 11 * a.ncell));
+        wl.invL = wl.invR = T(1) / T(6);
+        bool okL = true, okR = true, flat = true;
+        auto judge = [&](const Stencil<T>& q) {
+          T pl, pr, ql, qr;
+          reconstruct(w, q, pl, pr);
+          reconstruct(wl, q, ql, qr);
+          const T hi = fmax(fmax(fmax(T(0), q.da), fmax(q.db, q.dd)), q.de);
+          const T lo = fmin(fmin(fmin(T(0), q.da), fmin(q.db, q.dd)), q.de);
+          const T tol = T(a.tau) * (hi - lo);
+          okL = okL && fabs(ql - pl) <= tol;
+          okR = okR && fabs(qr - pr) <= tol;
+          flat = flat && !(hi > lo);
+        };
+        judge(st);
+        judge(sa);
+        if (okL) {
+          w.aL0 = wl.aL0;
+          w.aL1 = wl.aL1;
+          w.aL2 = wl.aL2;
+          w.invL = wl.invL;
+        }
+        if (okR) {
+          w.aR0 = wl.aR0;
+          w.aR1 = wl.aR1;
+          w.aR2 = wl.aR2;
+          w.invR = wl.invR;
+        }
+        if (!flat) {
+          lstat[0] += 2u;
+          lstat[1] += unsigned(!okL) + unsigned(!okR);
+        }
+      }
+    }
+    T fl, fr;
+    reconstruct(w, st, fl, fr);
+    mL[p] = double(fl);
+    mR[p] = double(fr);
+    reconstruct(w, sa, fl, fr);
+    aL[p] = double(fl);
+    aR[p] = double(fr);
+  }
+  // velocity and pressure, each with its own weights
+  double uL[D], uR[D], PL, PR;
+#pragma unroll
+  for (int v = N; v <= N + D; v++) {
+    Stencil<T> st = stencil<T>(V[0][v], V[1][v], V[2][v], V[3][v], V[4][v]);
+    W6<T> w = weights_of<T>(st);
+    T fl, fr;
+    reconstruct(w, st, fl, fr);
+    if (v < N + D) {
+      uL[v - N] = double(fl);
+      uR[v - N] = double(fr);
+    } else {
+      PL = double(fl);
+      PR = double(fr);
+    }
+  }
+  Face<N, D> fL, fR;
+  limit_chain<N, D>(m, Ub, Pb, mL, aL, mR, aR, uL, PL, uR, PR, a.energy_limiter, fL, fR,
+                    nullptr);
+  // the face x_{c+1/2}: this lane's fL and the right neighbour's fR
+  Face<N, D> fRn;
+  shfl_face_down<N, D>(fR, fRn);
+  double F[NV], uh = 0.0;
+  if (a.kind == 1) {
+    double q[N], G[N];
+    bool flip;
+    const long cell = base + (long)bc_index(c, a.n, a.bclo, a.bchi, flip) * a.stride;
+#pragma unroll
+    for (int p = 0; p < N; p++) q[p] = __ldg(a.Q + (long)p * a.ncell + cell);
+#pragma unroll
+    for (int p = 0; p < N; p++) G[p] = (__shfl_down_sync(0xffffffffu, q[p], 1) - q[p]) * a.inv_dx;
+    pf_flux<N, D>(m, fL, fRn, G, F);
+  } else {
+    riemann<N, D, TF>(m, a.dir, a.hllc, fL, fRn, F, uh);
+  }
+  // the face x_{c-1/2} from the left neighbour
+  double Fl[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) Fl[v] = __shfl_up_sync(0xffffffffu, F[v], 1);
+  const double uhl = __shfl_up_sync(0xffffffffu, uh, 1);
+  if (lane >= 1 && lane <= WIN && c < a.n) {
+    const long cell = base + (long)c * a.stride;
+    const double du = (uh - uhl) * a.inv_dx;
+    // Eq. 3: -div F + alpha (1 + K) div u_hat;  Eq. 5: +div F^PF
+    const double sdx = a.kind == 1 ? a.inv_dx : -a.inv_dx;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      double val = (F[v] - Fl[v]) * sdx;
+      if (a.kind == 0 && v >= N + D + 1) val = fma(Ub[v], du, val);
+      const long idx = (long)v * a.ncell + cell;
+      if (not_finite(val)) bad |= ST_NAN;
+      if (a.mode == 0) {
+        a.L[idx] = val;
+      } else if (a.mode == 1) {
+        a.L[idx] += val;
+      } else {
+        const double Lt = a.mode == 2 ? a.L[idx] + val : val;
+        double un = a.rk0 * a.U0[idx] + a.rk1 * Ub[v] + a.rk2 * dt * Lt;
+        // masses >= 0 and fractions in [0, 1] up to rounding: remove the
+        // residue (NaN passes through)
+        if (v < N || v >= I::A(0)) un = nonneg(un);
+        if (v >= I::A(0)) un = un > 1.0 ? 1.0 : un;
+        a.Uout[idx] = un;
+      }
+    }
+  }
+  __syncwarp();  // the slots are refilled by the next window
+}
+
+// Persistent launch: every warp takes windows (pencil fastest, so warps that
+// run together read neighbouring pencils) from the queue a.ticket[0] until
+// it is empty; the last warp to leave resets the queue for the next launch.
+template <int N, int D, typename T, typename TF, int LW = 0>
+__global__ void __launch_bounds__(128) k_sweep_win(SweepArgs a, Mat m) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  double* slots = smem + (threadIdx.x >> 5) * WinSmem<N, D, T>::WARP_DOUBLES;
+  const unsigned nitems = (unsigned)(a.npencil * a.nwin);
+  unsigned bad = 0u;
+  unsigned lstat[2] = {0u, 0u};
+  double dt = 0.0;
+  if (a.mode >= 2) dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.cfl / *a.rate;
+  for (;;) {
+    unsigned it = 0u;
+    if (lane == 0) it = atomicAdd(a.ticket, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= nitems) break;
+    const long tr = (long)(it % (unsigned)a.npencil);
+    const int win = (int)(it / (unsigned)a.npencil);
+    long base;
+    if (a.dir == 0) base = tr * a.nx;
+    else if (a.dir == 1) base = (tr / a.nx) * ((long)a.nx * a.ny) + tr % a.nx;
+    else base = tr;
+    sweep_window<N, D, T, TF, LW>(a, m, base, win * WIN, slots, dt, bad, lstat);
+  }
+  if (lane == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(a.ticket + 1, 1u);
+    if (done == a.nwarps - 1) {
+      a.ticket[0] = 0u;
+      a.ticket[1] = 0u;
+    }
+  }
+  if (bad) atomicOr(a.status, bad);
+  if constexpr (LW != 0) {
+    if (a.lcount) {
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        unsigned v = lstat[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && v) atomicAdd(a.lcount + k, (unsigned long long)v);
+      }
+    }
+  }
+}
+
+// Launch of the window sweep: bps resident blocks of 128 threads on every SM
+// (persistent; bps <= 0: the occupancy limit), at most one warp per window.
+template <int N, int D, typename T, typename TF, int LW>
+cudaError_t launch_window(const SweepArgs& a0, const Mat& m, int bps, cudaStream_t st) {
+  constexpr int block = 128;
+  const int smem = WinSmem<N, D, T>::WARP_DOUBLES * 8 * (block / 32);
+  auto k = k_sweep_win<N, D, T, TF, LW>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const long items = a0.npencil * a0.nwin;
+  if (bps <= 0) {
+    // as many resident blocks as registers and shared memory allow (queried
+    // once per instantiation; every caller gets the same answer)
+    static int occ = 0;
+    if (occ == 0) {
+      int q = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k, block, smem);
+      if (e != cudaSuccess) return e;
+      occ = q < 1 ? 1 : q;
+    }
+    bps = occ;
+  }
+  long blocks = 148L * bps;
+  const long need = (items + block / 32 - 1) / (block / 32);
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  SweepArgs a = a0;
+  a.nwarps = (unsigned)(blocks * (block / 32));
+  k<<<(unsigned)blocks, block, smem, st>>>(a, m);
+  return cudaGetLastError();
+}
+
+}  // namespace wc

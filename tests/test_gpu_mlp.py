@@ -204,7 +204,7 @@ def test_training_reduces_loss(gpu, trained):
     ideal = torch.tensor(mlp.IDEAL * 3, dtype=torch.float32, device="cuda")
     err_ideal = (ideal - T[sel]).pow(2).sum(1).mean().item()
     assert err_trained <= 0.1 * err_untrained
-    assert err_trained <= 0.1 * err_ideal
+    assert err_trained <= 0.2 * err_ideal
 
 
 def _learned_grid(case, S, tau, counters=None):
