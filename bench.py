@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--n3d", type=int, default=256, help="edge of the 3-D training source")
     ap.add_argument("--n5", type=int, default=2048, help="edge of the 2-D circles workload")
     ap.add_argument("--steps5", type=int, default=20)
+    ap.add_argument("--profile", action="store_true",
+                    help="only the FP64 timed steps (a short run for profilers); prints the "
+                         "per-launch sweep time")
     return ap.parse_args()
 
 
@@ -273,7 +276,7 @@ def run_ours(args):
     case = make_case(args, rank)
     N, D = case.N, case.dim
     cells = int(np.prod(case.shape))
-    learned = not args.no_learned
+    learned = not (args.no_learned or args.profile)
     S, train_info = train_surrogate(args, dev) if learned else (None, None)
 
     def make_grid(precision, c=None, counters=None):
@@ -314,6 +317,13 @@ def run_ours(args):
         total = sum(e0.elapsed_time(e1) for e0, e1 in evs)
         g.sync_status()
         return total / K, tot_sw / max(nl, 1)  # ms per step, ms per sweep launch
+
+    if args.profile:
+        g, U = make_grid("fp64")
+        ms, sw = timed_steps(g, args.steps, args.warmup)
+        print(json.dumps({"profile": True, "ms_per_step": ms, "sweep_ms_per_launch": sw,
+                          "steps": args.steps, "warmup": args.warmup}), flush=True)
+        return 0
 
     # FP64 DFMA probe of this GPU (context for the derived peak below)
     peak_probe = wenoc.fp64_peak() / 1e12
@@ -431,7 +441,7 @@ def run_ours(args):
                       "l1_rel_vs_fp64_max_var": l1, "l1_steps": args.steps},
         },
         "roofline": {
-            "bound": "alu", "kernel": "k_sweep<N=2,D=2,double> (direction sweep)",
+            "bound": "alu", "kernel": "k_sweep_win<N=2,D=2,double> (window direction sweep)",
             "achieved": round(achieved, 4), "peak": round(peak_fp64, 4), "unit": "TFLOP/s",
             "frac": round(achieved / peak_fp64, 4), "traffic": traffic,
             "peak_source": "unit count x clock: 2 DFMA/clk/SM x 2 flop x 148 SM x 2032 MHz",
