@@ -260,7 +260,7 @@ def group_l1(a, b, N, D):
 def run_ours(args):
     import torch
     import torch.distributed as tdist
-    from paper_2608_00746_b300 import roofline, wenoc
+    from paper_2608_00746_b300 import replicas, roofline, wenoc
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -414,14 +414,11 @@ def run_ours(args):
     ms64, sw64 = results["fp64"]
     msmx, swmx = results["mixed"]
     msl = results["learned"][0] if learned else 0.0
-    # max over ranks
-    vals = torch.tensor([ms64, msmx, e2e_ms, msl], dtype=torch.float64, device=dev)
-    if ws > 1:
-        tdist.all_reduce(vals, op=tdist.ReduceOp.MAX)
-    ms64, msmx, e2e_ms, msl = vals.tolist()
-    value = ws * cells * 3 / (ms64 * 1e-3) / 1e6
-    value_mx = ws * cells * 3 / (msmx * 1e-3) / 1e6
-    e2e = ws * cells * 3 / (e2e_ms * 1e-3) / 1e6
+    # max over ranks (replicas: the job takes as long as the slowest rank)
+    ms64, msmx, e2e_ms, msl = replicas.max_over_ranks([ms64, msmx, e2e_ms, msl], device=dev)
+    value = replicas.weak_value(ws, cells, 3, ms64)
+    value_mx = replicas.weak_value(ws, cells, 3, msmx)
+    e2e = replicas.weak_value(ws, cells, 3, e2e_ms)
 
     fl = roofline.flops_per_cell_dir(N, D, hllc=False)
     achieved = fl * cells / (sw64 * 1e-3) / 1e12
@@ -458,7 +455,7 @@ def run_ours(args):
     }
     if learned:
         line["modes"]["learned"] = {
-            "value": round(ws * cells * 3 / (msl * 1e-3) / 1e6, 3), "ms_per_step": round(msl, 4),
+            "value": round(replicas.weak_value(ws, cells, 3, msl), 3), "ms_per_step": round(msl, 4),
             "speedup_vs_fp64": round(ms64 / msl, 3), "l1_rel_vs_fp64_max_var": l1s["learned"],
             "l1_steps": args.steps, "tau": args.tau, "accepted_face_sides": acc2,
             "ms_per_direction": round(results["learned"][1], 4)}

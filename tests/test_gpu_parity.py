@@ -128,3 +128,20 @@ def test_limit_degenerate_face_exact(gpu):
     for A, B in ((UL.cpu().numpy(), UL_or), (UR.cpu().numpy(), UR_or)):
         assert np.allclose(A, B, rtol=1e-14, atol=1e-14)
         assert np.allclose(B[[0, 1, 4, 5]], Ub[[0, 1, 4, 5]], rtol=1e-15)
+
+
+@pytest.mark.parametrize("seg", [5, 14])
+@pytest.mark.parametrize("name", ["slab_1d_hllc", "shock_bubble_2d_ragged", "spheres_3d_ragged"])
+def test_rhs_parity_segment_schedule(gpu, name, seg):
+    """The per-thread segment march (seg > 0; the batched patches use it) is
+    held to the same tolerance as the default window schedule."""
+    case = SMALL_CASES[name]()
+    go, gg = grids(case, seg=seg)
+    U = oracle.prim_to_cons(go, case.V)
+    L_or = oracle.rhs(go, U)
+    Ud = to_dev(U)
+    gg.bind(Ud)
+    L = gg.rhs(Ud).cpu().numpy()
+    gg.sync_status()
+    err = rhs_err(L, L_or, U, oracle.max_rate(go, U), case.N, case.dim)
+    assert (err <= TOL).all(), (name, seg, err)
