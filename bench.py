@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="only the FP64 timed steps (a short run for profilers); prints the "
                          "per-launch sweep time")
+    ap.add_argument("--profile-mlp", action="store_true",
+                    help="only the surrogate kernels on the circles state (inference of one "
+                         "direction, one training step of train_batch rows), for profilers")
     return ap.parse_args()
 
 
@@ -499,10 +502,54 @@ def run_ours(args):
     return 0
 
 
+def run_profile_mlp(args):
+    """Surrogate kernels alone (untrained network: the timing does not depend
+    on the weights): 3 + 5 inference launches of direction 0 of the circles
+    state and one training step, events around each group."""
+    import torch
+    from paper_2608_00746_b300 import inputs, surrogate, wenoc
+    dev = torch.device("cuda", 0)
+    c5 = inputs.circles_shock_2d(n=args.n5, seed=args.seed)
+    g = wenoc.Grid(c5.shape, c5.dx, c5.gamma, c5.pinf, c5.D, flux=c5.flux, bc=c5.bc,
+                   precision="mixed")
+    U = g.prim_to_cons(torch.from_numpy(c5.V).to(dev))
+    g.bind(U)
+    S = surrogate.Surrogate(seed=args.seed, device=dev)
+    W = torch.empty((18, g.ncell), dtype=torch.float32, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        g.mlp_infer(U, 0, S.params, W, st)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    for _ in range(5):
+        g.mlp_infer(U, 0, S.params, W, st)
+    e[1].record()
+    ts = surrogate.TrainingSet(2 * g.ncell, device=dev)
+    ts.add(g, U, directions=[0])
+    ts.finish()
+    idx = torch.randint(0, ts.nrows, (args.train_batch,), dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    e[2].record()
+    S.train_step(ts.X, ts.T, idx, 1e-3)
+    e[3].record()
+    torch.cuda.synchronize()
+    S.check_status()
+    rows = 2 * g.ncell
+    infer_ms = e[0].elapsed_time(e[1]) / 5
+    print(json.dumps({"profile_mlp": True, "rows": rows, "infer_ms": infer_ms,
+                      "infer_tflops": 21376 * rows / (infer_ms * 1e-3) / 1e12,
+                      "train_step_ms": e[2].elapsed_time(e[3]), "batch": args.train_batch}),
+          flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_mlp:
+        return run_profile_mlp(args)
     return run_ours(args)
 
 

@@ -10,8 +10,7 @@ reading fixed here is the definition the GPU path is checked against:
 
 * inputs per face side (stencil ordered towards the face) and phase p < 3:
   the five masses minus the cell's own, divided by the largest absolute such
-  difference (0 when the stencil is flat, i.e. that difference is at most
-  1e-300), then the five fractions; unused
+  difference (0 when the stencil is flat), then the five fractions; unused
   phases and inputs 30, 31 are zero.  Eq. 15 depends only on ratios of the
   smoothness indicators, which are quadratic in f, so the weights of a
   stencil f and of a f + b (a != 0) coincide and the scaling loses nothing;
@@ -26,7 +25,9 @@ reading fixed here is the definition the GPU path is checked against:
   and fraction reconstructions (``loss_and_grads``); Adam (Kingma & Ba, beta1 0.9, beta2 0.999, eps 1e-8, bias
   corrected) on FP32 master parameters.
 
-The GPU stores features, weights, hidden activations and the back-propagated
+Rounding of the features (see ``features``): differences in FP64, exact
+power-of-two scaling, FP32 normalisation, BF16 storage.  The GPU stores
+features, weights, hidden activations and the back-propagated
 deltas that enter a product in BF16 and accumulates in FP32.  ``rounded=True``
 reproduces those rounding points here (BF16 = round to nearest even of the
 FP32 value) with every sum in FP64; ``rounded=False`` is the plain FP64
@@ -56,20 +57,58 @@ def bf16(x):
     return b.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+TINY = 2.0 ** -126   # feature values below this magnitude become zero
+
+
+def to_f32_flush(x):
+    """FP64 -> FP32, nearest even; magnitudes below 2^-126 become 0."""
+    x = np.asarray(x, dtype=np.float64)
+    y = x.astype(np.float32)
+    y[np.abs(x) < TINY] = 0.0
+    return y
+
+
+def bf16_direct(x):
+    """FP64 rounded once to 8 significant bits (BF16), nearest even;
+    magnitudes below 2^-126 become 0.  Value-based: x = m 2^e with
+    |m| in [1/2, 1) is rounded to a multiple of 2^(e-8)."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    nz = np.abs(x) >= TINY
+    _, e = np.frexp(x[nz])
+    q = np.ldexp(1.0, e - 8)
+    out[nz] = np.round(x[nz] / q) * q
+    return out
+
+
 def features(ms, als):
     """Inputs of rows of oriented stencils: ms, als [rows][P][5] (P <= 3
-    phases, masses and fractions) -> [rows][32] (BF16 values as float64)."""
+    phases, masses and fractions) -> [rows][32] (BF16 values as float64).
+    Masses: differences d_k to the cell value in FP64 (subnormal d_k count as
+    zero); when max |d_k| >= 2^-1022 they are scaled by the power of two that
+    brings max |d_k| into [1, 2) (exact) and rounded to FP32 (below 2^-126:
+    0), divided in FP32 by the largest magnitude and rounded to BF16;
+    otherwise the stencil is flat (zeros).  Fractions: rounded once from FP64
+    to BF16 (below 2^-126: 0)."""
     ms = np.asarray(ms, dtype=np.float64)
     als = np.asarray(als, dtype=np.float64)
     rows, P = ms.shape[0], ms.shape[1]
     X = np.zeros((rows, IN))
     for p in range(P):
         d = ms[:, p, :] - ms[:, p, 2:3]
+        d[:, 2] = 0.0
+        d[np.abs(d) < 2.0 ** -1022] = 0.0
         mx = np.max(np.abs(d), axis=1, keepdims=True)
-        big = mx > 1e-300   # smaller deviations count as flat
-        r = np.where(big, 1.0 / np.where(big, mx, 1.0), 0.0)
-        X[:, 10 * p:10 * p + 5] = bf16(d * r)
-        X[:, 10 * p + 5:10 * p + 10] = bf16(als[:, p, :])
+        live = mx > 0.0
+        _, e = np.frexp(np.where(live, mx, 1.0))
+        ds = np.where(live, d * np.ldexp(1.0, 1 - e), 0.0)
+        d32 = to_f32_flush(ds)
+        m32 = np.max(np.abs(d32), axis=1, keepdims=True)
+        big = m32 > np.float32(0.0)
+        r = np.where(big, np.float32(1.0) / np.where(big, m32, np.float32(1.0)),
+                     np.float32(0.0)).astype(np.float32)
+        X[:, 10 * p:10 * p + 5] = bf16((d32 * r).astype(np.float32))
+        X[:, 10 * p + 5:10 * p + 10] = bf16_direct(als[:, p, :])
     return X
 
 

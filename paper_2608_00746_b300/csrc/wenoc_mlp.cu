@@ -71,6 +71,34 @@ __device__ __forceinline__ void get_row(const unsigned char* src, int row, float
     v[k] = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(src + cm_offset(row, k, K)));
 }
 
+// relu(a) and relu(b) rounded to BF16 (nearest even) and packed, a in the
+// low half.
+__device__ __forceinline__ uint32_t bf16x2_relu(float a, float b) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+  return d;
+}
+
+// Hidden-layer epilogue of this thread's row: 64 accumulator columns from
+// tensor memory, + bias, ReLU, BF16, into row `row` of a [128][64] operand.
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bias,
+                                                unsigned char* out, int row) {
+#pragma unroll
+  for (int c = 0; c < MLP_H; c += 32) {
+    float h[32];
+    tmem_ld32(taddr + c, h);
+#pragma unroll
+    for (int k = 0; k < 32; k += 8) {
+      uint4 q;
+      q.x = bf16x2_relu(h[k] + bias[c + k], h[k + 1] + bias[c + k + 1]);
+      q.y = bf16x2_relu(h[k + 2] + bias[c + k + 2], h[k + 3] + bias[c + k + 3]);
+      q.z = bf16x2_relu(h[k + 4] + bias[c + k + 4], h[k + 5] + bias[c + k + 5]);
+      q.w = bf16x2_relu(h[k + 6] + bias[c + k + 6], h[k + 7] + bias[c + k + 7]);
+      *reinterpret_cast<uint4*>(out + cm_offset(row, c + k, MLP_H)) = q;
+    }
+  }
+}
+
 struct MmaSync {
   uint64_t* bar;
   uint32_t phase;
@@ -122,13 +150,8 @@ __device__ __forceinline__ bool fwd_layer(uint32_t a_in, uint32_t b_w, const flo
     umma_commit(ms.bar);
   }
   if (!ms.wait()) return false;
-  float h[MLP_H];
-#pragma unroll
-  for (int c = 0; c < MLP_H; c += 16) tmem_ld16(tm + lane_off + c, h + c);
-#pragma unroll
-  for (int j = 0; j < MLP_H; j++) h[j] = fmaxf(h[j] + bias[j], 0.0f);
   // the MMA that read `out` (in place for inference) has completed
-  put_row<MLP_H>(out, threadIdx.x, h);
+  hidden_epilogue(tm + lane_off, bias, out, threadIdx.x);
   operands_ready();
   return true;
 }
@@ -226,38 +249,6 @@ __device__ __forceinline__ void gather_stencil(const MlpGeom& g, long cell, int 
   }
 }
 
-// Rows 2 cell + side of one sweep direction, features gathered from the
-// state, weights written structure-of-arrays: W[(9 side + j) ncell + cell].
-template <int N, int D>
-struct SrcState {
-  MlpGeom g;
-  float* W;
-  __device__ __forceinline__ long rows() const { return 2 * g.ncell; }
-  __device__ __forceinline__ void load(long row, unsigned char* sX) const {
-    __align__(16) __nv_bfloat16 x[MLP_IN];
-    if (row < 2 * g.ncell) {
-      double ms[N][5], as[N][5];
-      gather_stencil<N, D>(g, row >> 1, (int)(row & 1), ms, as);
-      mlp_features<N>(ms, as, x);
-    } else {
-#pragma unroll
-      for (int k = 0; k < MLP_IN; k++) x[k] = __float2bfloat16(0.0f);
-    }
-#pragma unroll
-    for (int c = 0; c < 4; c++)
-      *reinterpret_cast<uint4*>(sX + cm_offset(threadIdx.x, c * 8, MLP_IN)) =
-          reinterpret_cast<const uint4*>(x)[c];
-  }
-  __device__ __forceinline__ void store(long row, const float* y) const {
-    if (row < 2 * g.ncell) {
-      const long cell = row >> 1;
-      const int side = (int)(row & 1);
-#pragma unroll
-      for (int j = 0; j < 3 * N; j++) W[(long)(MLP_NW * side + j) * g.ncell + cell] = y[j];
-    }
-  }
-};
-
 // ------------------------------------------------------------------ inference
 template <class Src>
 __global__ void __launch_bounds__(128) k_mlp_fwd(Src src, const void* params, unsigned* status) {
@@ -297,6 +288,121 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(Src src, const void* params, un
     if (t == 0) atomicOr(status, ST_TIMEOUT);
   }
   tile_teardown(tm, 64);
+}
+
+// Inference of one sweep direction straight from the state: each iteration
+// takes 128 cells, thread t gathers cell t's stencil once and builds the
+// features of both its face sides (tile A: side 0 rows, tile B: side 1
+// rows); the two tiles' MMAs of a layer are issued back to back into
+// tensor-memory columns [0, 64) and [64, 128) and share one commit.
+// Weights go to W[(9 side + j) ncell + cell].
+// The features ([128][32] per tile) are built in the activation buffers
+// themselves: layer 1 reads them before its epilogue overwrites them, which
+// keeps the CTA at 56 KB of shared memory (4 CTAs per SM).
+struct Infer2Smem {
+  static constexpr int W1 = 0, W2 = W1 + 64 * 32 * 2, W3 = W2 + 64 * 64 * 2,
+                       W4 = W3 + 64 * 64 * 2, AA = W4 + 16 * 64 * 2, AB = AA + 128 * 64 * 2,
+                       BIAS = AB + 128 * 64 * 2, BYTES = BIAS + MLP_NBIAS * 4;
+};
+
+template <int K>
+__device__ __forceinline__ bool fwd_layer2(uint32_t aA, uint32_t aB, uint32_t b_w,
+                                           const float* bias, unsigned char* outA,
+                                           unsigned char* outB, uint32_t tm, uint32_t lane_off,
+                                           MmaSync& ms) {
+  if (threadIdx.x == 0) {
+    umma_tile(tm, aA, b_w, MLP_H, K, 0);
+    umma_tile(tm + 64, aB, b_w, MLP_H, K, 0);
+    umma_commit(ms.bar);
+  }
+  if (!ms.wait()) return false;
+  hidden_epilogue(tm + lane_off, bias, outA, threadIdx.x);
+  hidden_epilogue(tm + lane_off + 64, bias, outB, threadIdx.x);
+  operands_ready();
+  return true;
+}
+
+template <int N, int D>
+__global__ void __launch_bounds__(128) k_mlp_infer2(MlpGeom g, const void* params, float* W,
+                                                    unsigned* status) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tbase;
+  const int t = threadIdx.x;
+  {
+    const MlpPtrs P = mlp_ptrs(params);
+    stage_matrix<64, 32, false>(sm + Infer2Smem::W1, P.W + MLP_W1);
+    stage_matrix<64, 64, false>(sm + Infer2Smem::W2, P.W + MLP_W2);
+    stage_matrix<64, 64, false>(sm + Infer2Smem::W3, P.W + MLP_W3);
+    stage_matrix<16, 64, false>(sm + Infer2Smem::W4, P.W + MLP_W4);
+    float* sb = reinterpret_cast<float*>(sm + Infer2Smem::BIAS);
+    for (int i = t; i < MLP_NBIAS; i += blockDim.x) sb[i] = P.b[i];
+  }
+  tile_setup(&tbase, &bar, 128);
+  operands_ready();
+  const uint32_t tm = tbase, lane_off = (uint32_t)(32 * (t >> 5)) << 16;
+  const float* sb = reinterpret_cast<const float*>(sm + Infer2Smem::BIAS);
+  unsigned char* sAA = sm + Infer2Smem::AA;
+  unsigned char* sAB = sm + Infer2Smem::AB;
+  const uint32_t aAA = smem_u32(sAA), aAB = smem_u32(sAB);
+  MmaSync ms{&bar, 0u};
+  bool ok = true;
+  const long nit = (g.ncell + 127) / 128;
+  for (long it = blockIdx.x; it < nit && ok; it += gridDim.x) {
+    const long cell = it * 128 + t;
+    __align__(16) __nv_bfloat16 x0[MLP_IN], x1[MLP_IN];
+    if (cell < g.ncell) {
+      double mstc[N][5], astc[N][5];
+      gather_stencil<N, D>(g, cell, 0, mstc, astc);
+      mlp_features2<N>(mstc, astc, x0, x1);
+    } else {
+#pragma unroll
+      for (int k = 0; k < MLP_IN; k++) x0[k] = x1[k] = __float2bfloat16(0.0f);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      *reinterpret_cast<uint4*>(sAA + cm_offset(t, c * 8, MLP_IN)) =
+          reinterpret_cast<const uint4*>(x0)[c];
+      *reinterpret_cast<uint4*>(sAB + cm_offset(t, c * 8, MLP_IN)) =
+          reinterpret_cast<const uint4*>(x1)[c];
+    }
+    operands_ready();
+    ok = fwd_layer2<MLP_IN>(aAA, aAB, smem_u32(sm + Infer2Smem::W1), sb + MLP_B1, sAA, sAB, tm,
+                            lane_off, ms) &&
+         fwd_layer2<MLP_H>(aAA, aAB, smem_u32(sm + Infer2Smem::W2), sb + MLP_B2, sAA, sAB, tm,
+                           lane_off, ms) &&
+         fwd_layer2<MLP_H>(aAA, aAB, smem_u32(sm + Infer2Smem::W3), sb + MLP_B3, sAA, sAB, tm,
+                           lane_off, ms);
+    if (ok) {
+      if (t == 0) {
+        umma_tile(tm, aAA, smem_u32(sm + Infer2Smem::W4), MLP_OUT, MLP_H, 0);
+        umma_tile(tm + 64, aAB, smem_u32(sm + Infer2Smem::W4), MLP_OUT, MLP_H, 0);
+        umma_commit(ms.bar);
+      }
+      ok = ms.wait();
+    }
+    if (ok) {
+#pragma unroll
+      for (int side = 0; side < 2; side++) {
+        float z[MLP_OUT], y[MLP_NW];
+        tmem_ld16(tm + lane_off + 64 * side, z);
+#pragma unroll
+        for (int j = 0; j < MLP_OUT; j++) z[j] += sb[MLP_B4 + j];
+        softmax3(z, y);
+        if (cell < g.ncell) {
+#pragma unroll
+          for (int j = 0; j < 3 * N; j++) W[(long)(MLP_NW * side + j) * g.ncell + cell] = y[j];
+        }
+      }
+      // the next iteration's MMAs overwrite the accumulator only after every
+      // thread has read it (barrier in operands_ready)
+    }
+  }
+  if (!ok) {
+    ms.drain();
+    if (t == 0) atomicOr(status, ST_TIMEOUT);
+  }
+  tile_teardown(tm, 128);
 }
 
 // ------------------------------------------------------------------ training
@@ -574,10 +680,10 @@ __global__ void k_mlp_features(MlpGeom g, long row0, __nv_bfloat16* X, float* T,
     const long cell = r >> 1;
     const int side = (int)(r & 1);
     double ms[N][5], as[N][5];
-    gather_stencil<N, D>(g, cell, side, ms, as);
+    gather_stencil<N, D>(g, cell, 0, ms, as);
     const long row = row0 + r;
     __align__(16) __nv_bfloat16 x[MLP_IN];
-    mlp_features<N>(ms, as, x);
+    mlp_features2<N>(ms, as, side == 0 ? x : nullptr, side == 1 ? x : nullptr);
 #pragma unroll
     for (int c = 0; c < 4; c++)
       reinterpret_cast<uint4*>(X + row * MLP_IN)[c] = reinterpret_cast<const uint4*>(x)[c];
@@ -588,8 +694,10 @@ __global__ void k_mlp_features(MlpGeom g, long row0, __nv_bfloat16* X, float* T,
     for (int p = 0; p < MLP_MAXP; p++) {
       double w[3] = {ideal[0], ideal[1], ideal[2]};
       if (p < N) {
-        const Stencil<double> st =
-            stencil<double>(ms[p][0], ms[p][1], ms[p][2], ms[p][3], ms[p][4]);
+        // the stencil ordered towards this side's face
+        const int o = side == 0 ? 0 : 4;
+        const Stencil<double> st = stencil<double>(ms[p][o], ms[p][o ? 3 : 1], ms[p][2],
+                                                   ms[p][o ? 1 : 3], ms[p][o ? 0 : 4]);
         const W6<double> wt = weights_of<double>(st);
         const double s6 = 6.0 * wt.invL;
         w[0] = wt.aL0 * s6;
@@ -624,13 +732,13 @@ cudaError_t launch_mlp_forward(const __nv_bfloat16* X, long nrows, const void* p
 template <int N, int D>
 static cudaError_t infer_nd(const MlpGeom& g, const void* params, float* W, unsigned* status,
                             cudaStream_t st) {
-  auto k = k_mlp_fwd<SrcState<N, D>>;
+  auto k = k_mlp_infer2<N, D>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       FwdSmem::BYTES);
+                                       Infer2Smem::BYTES);
   if (e != cudaSuccess) return e;
-  const long ntile = (2 * g.ncell + 127) / 128;
-  const int grid = (int)std::max(1L, std::min(ntile, 148L * 4));
-  k<<<grid, 128, FwdSmem::BYTES, st>>>(SrcState<N, D>{g, W}, params, status);
+  const long nit = (g.ncell + 127) / 128;
+  const int grid = (int)std::max(1L, std::min(nit, 148L * 4));
+  k<<<grid, 128, Infer2Smem::BYTES, st>>>(g, params, W, status);
   return cudaGetLastError();
 }
 

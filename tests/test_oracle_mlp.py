@@ -87,6 +87,23 @@ def test_bf16_round_to_nearest_even():
     assert mlp.bf16(0.0) == 0.0
 
 
+def test_bf16_direct_rounding():
+    """One rounding from FP64 to 8 significant bits: equal to the FP32 route
+    where FP32 holds the value exactly; ties to even; tiny values flushed."""
+    rng = np.random.default_rng(5)
+    f32 = rng.standard_normal(1000).astype(np.float32).astype(np.float64)
+    assert np.array_equal(mlp.bf16_direct(f32), mlp.bf16(f32))
+    u = 2.0 ** -7
+    assert mlp.bf16_direct(1.0 + u / 2) == 1.0
+    assert mlp.bf16_direct(1.0 + 1.5 * u) == 1.0 + 2 * u
+    # just above a tie rounds up: a case where rounding through FP32 first
+    # (to the tie) would round down
+    x = 1.0 + u / 2 + 2.0 ** -40
+    assert mlp.bf16_direct(x) == 1.0 + u and mlp.bf16(x) == 1.0
+    assert mlp.bf16_direct(2.0 ** -127) == 0.0 and mlp.bf16_direct(2.0 ** -126) == 2.0 ** -126
+    assert mlp.to_f32_flush(np.array([2.0 ** -127, 1.0 / 3.0]))[0] == 0.0
+
+
 def test_adam_first_step_is_signed_lr():
     rng = np.random.default_rng(2)
     master = rng.normal(size=mlp.NPARAM)
@@ -109,7 +126,7 @@ def test_features_affine_invariance_and_flat_stencil():
     assert np.all(np.abs(X[:, [0, 1, 3, 4, 10, 11, 13, 14]]) <= 1.0)
     assert np.all(X[:, [2, 12, 22]] == 0.0)
     assert np.all(X[:, 30:] == 0.0)
-    assert np.array_equal(X[:, 5:10], mlp.bf16(al[:, 0, :]))
+    assert np.array_equal(X[:, 5:10], mlp.bf16_direct(al[:, 0, :]))
     flat = np.full((1, 3, 5), 7.5)
     Xf = mlp.features(flat, np.full((1, 3, 5), 0.25))
     assert np.all(Xf[0, [0, 1, 2, 3, 4]] == 0.0)
