@@ -53,6 +53,7 @@ class _Grid(ctypes.Structure):
         ("limiter", ctypes.c_int),
         ("energy_limiter", ctypes.c_int),
         ("bc", ctypes.c_int * 6),
+        ("consistent", ctypes.c_int),
     ]
 
 
@@ -122,6 +123,7 @@ class Grid:
     coupled: bool = True        # Eq. 16
     limiter: bool = True        # Eq. 17-20
     energy_limiter: bool = True  # Eq. 21
+    scheme: str = "c"           # "c": Eq. 19 (WENO-C); "cl": Eq. 23-25 (WENO-CL)
     _c: _Grid = field(default=None, repr=False)
 
     def __post_init__(self):
@@ -149,6 +151,7 @@ class Grid:
         g.energy_limiter = int(self.energy_limiter)
         for k in range(6):
             g.bc[k] = BC[self.bc[k]] if isinstance(self.bc[k], str) else int(self.bc[k])
+        g.consistent = {"c": 0, "cl": 1}[self.scheme]
         self._c = g
 
     @property

@@ -54,6 +54,13 @@
  *  R11 Eq. 19 assumes S > 0.  When the positivity step has limited every
  *      fraction of a face to zero (S = 0) the cell keeps its averages on both
  *      faces (theta = 0, first order) for the masses and the fractions.
+ *  R14 WENO-CL (Sec. 3.4, Eq. 23-25) replaces Eq. 19.  The gradients S of
+ *      Eq. 24 enter Eq. 23 and Eq. 25 only through ratios and through
+ *      theta S dx/2, so the common factor 2/dx is dropped: S_p = f_face -
+ *      fbar.  p-hat is the first phase of largest |S^(alpha_p)|.  When every
+ *      S^(alpha_p) of a face is zero the faces are left as they are; a
+ *      ratio x/0 with x != 0 is +-infinity before the clamp to [0, 1].
+ *      Eq. 20 and Eq. 21 follow as in WENO-C.
  *  R13 Rounding residue below the bounds.  In exact arithmetic the faces
  *      scaled by Eq. 18 (f_min = 0), Eq. 20 and Eq. 21 have non-negative
  *      masses and fractions, and every Runge-Kutta stage (a convex
@@ -95,6 +102,7 @@ typedef struct {
   int limiter;          /* 1: Eq. 17-20 applied; 0: skipped */
   int energy_limiter;   /* 1: Eq. 21 applied; 0: skipped */
   int bc[6];            /* lo/hi per axis: OR_BC_* */
+  int consistent;       /* 0: Eq. 19 (WENO-C); 1: Eq. 23-25 (WENO-CL) */
 } or_grid;
 
 /* ---- state layout ---------------------------------------------------------
@@ -274,6 +282,37 @@ static double theta_pos(double fbar, double fL, double fR) {
  * VfL, VfR: primitive face states handed to the Riemann solver (R6).
  * th (optional, 3 values): min_p theta_p of Eq. 17, theta_i of Eq. 20,
  * theta^(psi) of Eq. 21. */
+static double clamp01(double x) { return x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x); }
+
+/* Eq. 23-25 on one face (V holds the face's primitive values): with
+ * S_p = alpha_p,face - alpha_p,bar (R14), p-hat = argmax |S_p|,
+ * S-hat = S_phat - sum_p S_p, theta_phat = clamp(S-hat / S_phat) and
+ * theta_p = clamp(S_phat / S-hat) otherwise; the phase's mass and fraction
+ * both move to fbar + theta (f_face - fbar). */
+static void consistent_limiter(const or_grid *g, const double *Ubar, double *V) {
+  int N = g->N, ph = 0;
+  double S[OR_MAXP], sum = 0.0, best = -1.0;
+  for (int p = 0; p < N; p++) {
+    S[p] = V[IALF(g, p)] - Ubar[IALF(g, p)];
+    sum += S[p];
+    if (fabs(S[p]) > best) {
+      best = fabs(S[p]);
+      ph = p;
+    }
+  }
+  if (S[ph] == 0.0) return; /* every gradient is zero */
+  double Shat = S[ph] - sum;
+  for (int p = 0; p < N; p++) {
+    double th;
+    if (p == ph) th = clamp01(Shat / S[ph]);
+    else if (Shat == 0.0) th = S[ph] > 0.0 ? 1.0 : 0.0; /* S_phat / 0 = +-inf */
+    else th = clamp01(S[ph] / Shat);
+    double mb = Ubar[IMASS(p)], ab = Ubar[IALF(g, p)];
+    V[IMASS(p)] = clamp0(mb + th * (V[IMASS(p)] - mb));
+    V[IALF(g, p)] = clamp0(ab + th * (V[IALF(g, p)] - ab));
+  }
+}
+
 static int limit_chain(const or_grid *g, const double *Ubar, double *VL, double *VR,
                        double *UL, double *UR, double *VfL, double *VfR, double *th) {
   int N = g->N, nvar = nv(g);
@@ -293,6 +332,11 @@ static int limit_chain(const or_grid *g, const double *Ubar, double *VL, double 
         VR[IALF(g, p)] = clamp0(ab + tp * (VR[IALF(g, p)] - ab));
       }
     }
+    if (g->consistent) {
+      /* Eq. 23-25 (WENO-CL, R14) on each face instead of Eq. 19. */
+      consistent_limiter(g, Ubar, VL);
+      consistent_limiter(g, Ubar, VR);
+    } else {
     /* Eq. 19: unity sum of the volume fractions on each face. */
     double SL = 0.0, SR = 0.0;
     for (int p = 0; p < N; p++) {
@@ -314,6 +358,7 @@ static int limit_chain(const or_grid *g, const double *Ubar, double *VL, double 
       VL[IALF(g, p)] = VL[IALF(g, p)] / SL;
       VR[IMASS(p)] = VR[IMASS(p)] / SR;
       VR[IALF(g, p)] = VR[IALF(g, p)] / SR;
+    }
     }
     /* Eq. 20: theta_i = min_p theta_p recomputed from the normalised faces. */
     for (int p = 0; p < N; p++) {

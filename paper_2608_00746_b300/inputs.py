@@ -193,6 +193,24 @@ def multiphase_advection_2d(n=100, nphase=5, width_cells=1.0):
                 flux="hllc", cfl=0.0, meta=dict(dt=1e-3))
 
 
+def miscible_advection_2d(n=100, width_cells=1.0):
+    """Four-phase advection with a non-zero, non-unity constant fraction
+    (Sec. 4.1.3): doubly periodic [-0.5, 0.5]^2, u = (1, 1), P = 4.819e-5,
+    alpha_1 = 0.8 inside the circle (0, 0, 0.2) and alpha_2 = 0.8 outside
+    (smoothed edge), alpha_3 = 0.2 everywhere, alpha_4 = 0 (absent); the
+    first four phases of Table 1."""
+    dx = 1.0 / n
+    x, y = _centres((n, n), (dx, dx), lo=(-0.5, -0.5))
+    s = smooth_step(0.2 - np.sqrt(x ** 2 + y ** 2), width_cells * dx)
+    alpha = [0.8 * s, 0.8 * (1.0 - s), np.full((n, n), 0.2), np.zeros((n, n))]
+    mats = TABLE1[:4]
+    V = _assemble(alpha, [m[0] for m in mats], [np.ones((n, n)), np.ones((n, n))],
+                  np.full((n, n), 4.819e-5))
+    return Case("miscible_advection_2d", (n, n), (dx, dx), [m[1] for m in mats],
+                [m[2] for m in mats], [m[3] for m in mats], V, ("periodic",) * 6,
+                flux="hllc", cfl=0.0, meta=dict(dt=1e-3))
+
+
 # ----------------------------------------------------------------------------
 # Config 2: 2-D shock-bubble (N = 2, reflective walls)
 # ----------------------------------------------------------------------------

@@ -481,3 +481,58 @@ def test_pf_absent_phase_and_equilibrium():
     assert np.abs(V[4] - 1e5).max() / (1e5 + 6e8) < 1e-14          # P uniform
     a = V[5:7]
     assert a.min() >= 0.0 and a.max() <= 1.0 + 4 * 2.0 ** -52       # bounds
+
+
+# ---------------------------------------------------------------- WENO-CL (Sec. 3.4, Eq. 23-25)
+def test_weno_cl_keeps_constant_fraction_weno_c_does_not():
+    """The four-phase test of Sec. 4.1.3: alpha_3 = 0.2 everywhere stays 0.2
+    to round-off with the consistent limiter, WENO-C's Eq. 19 moves it; both
+    keep the unity sum, the absent phase and equilibrium."""
+    c = inputs.miscible_advection_2d(n=50)
+    err = {}
+    for scheme in ("c", "cl"):
+        go = oracle.Grid(c.shape, c.dx, c.gamma, c.pinf, c.D, flux=c.flux, bc=c.bc,
+                         scheme=scheme)
+        U = oracle.prim_to_cons(go, c.V)
+        for _ in range(20):
+            U, _ = oracle.rk3_step(go, U, dt=c.meta["dt"])
+        V = oracle.cons_to_prim(go, U)
+        a = V[7:]
+        err[scheme] = np.abs(a[2] - 0.2).max()
+        assert np.abs(a.sum(0) - 1.0).max() < 1e-11
+        assert np.all(a[3] == 0.0)
+        assert np.abs(V[4] - 1.0).max() < 1e-10 and np.abs(V[5] - 1.0).max() < 1e-10
+    assert err["cl"] <= 1e-15, err
+    assert err["c"] > 1e-11, err
+
+
+def test_weno_cl_faces_sum_to_average_and_stay_bounded():
+    """Sum_p theta_p S_p = 0 (Eq. 25): the limited face fractions sum to the
+    cell's fraction sum without any division, and stay in [0, 1]; two phases
+    whose raw faces already sum to one (up to rounding) are left as Eq. 19
+    leaves them, up to that rounding divided by the face gradient."""
+    d = 2
+    g, pi = [1.4, 4.4, 6.1], [0.0, 6e8, 2e9]
+    for N, seed in ((3, 11), (2, 12)):
+        Vb, VL, VR = inputs.random_admissible_stencils(2000, N, d, seed=seed)
+        a0 = N + d + 1
+        if N == 2:
+            VL[a0 + 1] = 1.0 - VL[a0]
+            VR[a0 + 1] = 1.0 - VR[a0]
+        go = oracle.Grid((8, 8), (1.0, 1.0), g[:N], pi[:N], scheme="cl")
+        goc = oracle.Grid((8, 8), (1.0, 1.0), g[:N], pi[:N], scheme="c")
+        Ub = oracle.prim_to_cons(go, Vb)
+        keep = oracle.psi(go, Ub) > 0
+        Ub, VL, VR = Ub[:, keep], VL[:, keep], VR[:, keep]
+        UL, UR, TH = oracle.limit(go, Ub, VL, VR)
+        sb = Ub[a0:a0 + N].sum(0)
+        for F in (UL, UR):
+            fa = F[a0:a0 + N]
+            assert np.abs(fa.sum(0) - sb).max() < 1e-14
+            assert fa.min() >= 0.0 and fa.max() <= 1.0 + 4 * 2.0 ** -52
+        if N == 2:
+            L2, R2, T2 = oracle.limit(goc, Ub, VL, VR)
+            ok = (TH[0] == 1.0) & (T2[0] == 1.0) & (TH[2] == 1.0)
+            assert ok.sum() > 100
+            assert np.allclose(UL[:, ok], L2[:, ok], rtol=1e-10, atol=0)
+            assert np.allclose(UR[:, ok], R2[:, ok], rtol=1e-10, atol=0)
