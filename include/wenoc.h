@@ -53,6 +53,7 @@ typedef enum {
 enum { WC_BC_PERIODIC = 0, WC_BC_REFLECTIVE = 1, WC_BC_OUTFLOW = 2 };
 enum { WC_FLUX_HLL = 0, WC_FLUX_HLLC = 1 };
 enum { WC_PREC_FP64 = 0, WC_PREC_MIXED = 1, WC_PREC_LEARNED = 2 };
+enum { WC_SCHEME_C = 0, WC_SCHEME_CL = 1 };
 
 /* Grid, materials and scheme options.  Materials follow the stiffened-gas
  * equation of state of Eq. 26: A_p = 1/(gamma_p-1), B_p = gamma_p Pinf_p /
@@ -86,6 +87,9 @@ typedef struct {
                                  (32..128); 0 = automatic; the window sweep
                                  uses 128 */
   int blocks_per_sm;          /* resident sweep blocks per SM (1..4); 0 = automatic */
+  int scheme;                 /* WC_SCHEME_C: unity sum by Eq. 19 (WENO-C,
+                                 default); WC_SCHEME_CL: the consistent limiter
+                                 of Eq. 23-25 instead (WENO-CL, Sec. 3.4) */
 } wc_grid_desc;
 
 typedef struct wc_grid wc_grid;

@@ -103,6 +103,7 @@ extern "C" wc_status wc_init_grid(const wc_grid_desc* desc, wc_grid** out) {
   if (d.precision == WC_PREC_LEARNED && d.nphase > 3) return WC_ERR_UNSUPPORTED;
   if (d.seg < 0 || d.block < 0 || d.block > 128 || (d.block % 32) != 0) return WC_ERR_ARG;
   if (d.blocks_per_sm < 0 || d.blocks_per_sm > 4) return WC_ERR_ARG;
+  if (d.scheme != WC_SCHEME_C && d.scheme != WC_SCHEME_CL) return WC_ERR_ARG;
   for (int p = 0; p < d.nphase; p++)
     if (!(d.gamma[p] > 1.0) || !(d.pinf[p] >= 0.0)) return WC_ERR_ARG;
   wc_grid* g = new (std::nothrow) wc_grid();
@@ -113,6 +114,7 @@ extern "C" wc_status wc_init_grid(const wc_grid_desc* desc, wc_grid** out) {
   Mat& m = g->mat;
   memset(&m, 0, sizeof(m));
   m.N = d.nphase;
+  m.cl = d.scheme == WC_SCHEME_CL;
   for (int p = 0; p < d.nphase; p++) {
     m.A[p] = 1.0 / (d.gamma[p] - 1.0);
     m.B[p] = d.gamma[p] * d.pinf[p] / (d.gamma[p] - 1.0);

@@ -30,6 +30,7 @@ struct Mat {
   double Ag[MAXP];          // A gamma (mixture sound speed, Eq. 2, K = 0)
   double Cmin[MAXP];        // A Pmin + B: alpha_p rho_p e_p(Pmin_p, rho_p) per alpha_p
   double Apmin[MAXP];       // A Pmin
+  int cl;                   // 1: WENO-CL (Eq. 23-25 instead of Eq. 19)
 };
 
 template <int N, int D>
@@ -379,6 +380,31 @@ __device__ __forceinline__ void reconstruct(const W6<T>& w, const Stencil<T>& s,
   fR = fma(fma(w.aR2, qR2, fma(w.aR1, qR1, w.aR0 * qR0)), w.invR, s.c);
 }
 
+// Mass and fraction faces of the reduced-precision path: the weighted
+// candidate offsets (Eq. 10 minus the cell value) in T, added to the cell
+// value in FP64, so a flat stencil reconstructs to the FP64 cell value
+// exactly (a constant fraction stays constant) and the FP32 rounding is
+// relative to the stencil's variation, not to the values.  (Velocity and
+// pressure keep the value form: FP64 noise of a uniform field below the FP32
+// resolution then gives exactly uniform faces, which equilibrium needs.)
+template <typename T>
+__device__ __forceinline__ void offsets(const W6<T>& w, const Stencil<T>& s, T& oL, T& oR) {
+  const T qL0 = fma(T(2), s.da, T(-7) * s.db), qL1 = fma(T(2), s.dd, -s.db),
+          qL2 = fma(T(5), s.dd, -s.de);
+  const T qR0 = fma(T(2), s.de, T(-7) * s.dd), qR1 = fma(T(2), s.db, -s.dd),
+          qR2 = fma(T(5), s.db, -s.da);
+  oL = fma(w.aL2, qL2, fma(w.aL1, qL1, w.aL0 * qL0)) * w.invL;
+  oR = fma(w.aR2, qR2, fma(w.aR1, qR1, w.aR0 * qR0)) * w.invR;
+}
+template <typename T>
+__device__ __forceinline__ void reconstruct_offset(const W6<T>& w, const Stencil<T>& s,
+                                                   double cd, double& fL, double& fR) {
+  T oL, oR;
+  offsets(w, s, oL, oR);
+  fL = cd + double(oL);
+  fR = cd + double(oR);
+}
+
 // ------------------------------------------------------------------ limiters
 // Eq. 18 (f_min = 0) with f^C from Eq. 6 inverted (N_quad = 4, w = 1/12):
 // theta = 1 when min(f^C, f^L, f^R) >= 0, else fbar / (fbar - min), clamped
@@ -424,6 +450,53 @@ struct Face {
 // an ulp below it.  x < 0 becomes 0; a NaN stays a NaN.
 __device__ __forceinline__ double nonneg(double x) { return x < 0.0 ? 0.0 : x; }
 
+// Eq. 23-25 (WENO-CL) on one face: S_p = alpha_p,face - alpha_p,bar (the
+// factor 2/dx of Eq. 24 cancels), p-hat the first phase of largest |S_p|,
+// S-hat = S_phat - sum_p S_p, theta_phat = clamp(S-hat / S_phat),
+// theta_p = clamp(S_phat / S-hat) for the others (x/0 = +-infinity before
+// the clamp), masses and fractions moved to fbar + theta (f - fbar).
+// Returns whether a face value moved.
+template <int N, int D>
+__device__ __forceinline__ bool consistent_face(const double* Ub, double* mf, double* af) {
+  using I = Idx<N, D>;
+  double S[N], sum = 0.0, Sph = 0.0;
+  long long best = -1;
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    S[p] = af[p] - Ub[I::A(p)];
+    sum += S[p];
+    const long long b = dbits(S[p]) & 0x7FFFFFFFFFFFFFFFLL;
+    if (b > best) {
+      best = b;
+      Sph = S[p];
+    }
+  }
+  if (best == 0) return false;  // every gradient is zero
+  const double Shat = Sph - sum;
+  const double a1 = fabs(Sph), a2 = fabs(Shat);
+  const double th_ph = in_range(a1, 1e-300, 1e300) ? Shat * rcp_nr(Sph) : Shat / Sph;
+  double th_o;
+  if (dbits(a2) == 0) th_o = has_sign(Sph) ? 0.0 : 1.0;
+  else th_o = in_range(a2, 1e-300, 1e300) ? Sph * rcp_nr(Shat) : Sph / Shat;
+  const double tph = th_ph < 0.0 ? 0.0 : (th_ph > 1.0 ? 1.0 : th_ph);
+  const double to = th_o < 0.0 ? 0.0 : (th_o > 1.0 ? 1.0 : th_o);
+  bool moved = false, seen = false;
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    // p-hat is the first phase whose |S| is the largest
+    const bool is_ph = !seen && (dbits(S[p]) & 0x7FFFFFFFFFFFFFFFLL) == best;
+    seen = seen || is_ph;
+    const double th = is_ph ? tph : to;
+    if (lt_nonneg(th, 1.0)) {
+      const double mb = Ub[p], ab = Ub[I::A(p)];
+      mf[p] = nonneg(fma(th, mf[p] - mb, mb));
+      af[p] = nonneg(fma(th, af[p] - ab, ab));
+      moved = true;
+    }
+  }
+  return moved;
+}
+
 template <int N, int D>
 __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, double Pb,
                                             double* mL, double* aL, double* mR, double* aR,
@@ -445,8 +518,16 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
       th17 = min_nonneg(th17, tp);
     }
   }
+  bool cl_moved = false;
+  double SL = 1.0, SR = 1.0;
+  if (m.cl) {
+    // Eq. 23-25 (WENO-CL) instead of Eq. 19
+    cl_moved = consistent_face<N, D>(Ub, mL, aL);
+    cl_moved = consistent_face<N, D>(Ub, mR, aR) || cl_moved;
+  } else {
   // Eq. 19: unity sum on each face
-  double SL = aL[0], SR = aR[0];
+  SL = aL[0];
+  SR = aR[0];
 #pragma unroll
   for (int p = 1; p < N; p++) {
     SL += aL[p];
@@ -479,11 +560,13 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
       }
     }
   }
+  }
   // Eq. 20: theta_i = min_p theta_p recomputed on the normalised faces (when
   // Eq. 17 and Eq. 19 left every face value unchanged, the recomputed thetas
   // are those of Eq. 17, all one)
   double thi = 1.0;
-  if (lt_nonneg(th17, 1.0) || dbits(SL) != dbits(1.0) || dbits(SR) != dbits(1.0)) {
+  if (lt_nonneg(th17, 1.0) || cl_moved || dbits(SL) != dbits(1.0) ||
+      dbits(SR) != dbits(1.0)) {
 #pragma unroll
     for (int p = 0; p < N; p++) {
       double tp =

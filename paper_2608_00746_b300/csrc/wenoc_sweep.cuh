@@ -12,6 +12,8 @@
 // and updates the previous cell.  Boundary cells come from the boundary
 // condition on the fly (no ghost storage).
 #pragma once
+#include <type_traits>
+
 #include "wenoc_device.cuh"
 
 namespace wc {
@@ -150,6 +152,9 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
     const double Pb = ring[((c + 15) % 5) * SLOTD];
     double Ub[NV];
     load_cons(c, Ub);
+    // reduced precision: mass and fraction faces = FP64 cell value (a
+    // conservative and primitive variable alike) + offset in T
+    constexpr bool OFFSET = !std::is_same<T, double>::value;
 
     // Eq. 16: masses and fractions with the weights of the masses
     double mL[N], mR[N], aL[N], aR[N];
@@ -177,8 +182,8 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
           bool okL = true, okR = true, flat = true;
           auto judge = [&](const Stencil<T>& q) {
             T pl, pr, ql, qr;
-            reconstruct(w, q, pl, pr);
-            reconstruct(wl, q, ql, qr);
+            offsets(w, q, pl, pr);
+            offsets(wl, q, ql, qr);
             const T hi = fmax(fmax(fmax(T(0), q.da), fmax(q.db, q.dd)), q.de);
             const T lo = fmin(fmin(fmin(T(0), q.da), fmin(q.db, q.dd)), q.de);
             const T tol = T(a.tau) * (hi - lo);
@@ -208,15 +213,20 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
           }
         }
       }
-      T fl, fr;
-      reconstruct(w, st, fl, fr);
-      mL[p] = double(fl);
-      mR[p] = double(fr);
       const int ia = I::A(p);
-      st = stencil<T>(V[0][ia], V[1][ia], V[2][ia], V[3][ia], V[4][ia]);
-      reconstruct(w, st, fl, fr);
-      aL[p] = double(fl);
-      aR[p] = double(fr);
+      const Stencil<T> sa = stencil<T>(V[0][ia], V[1][ia], V[2][ia], V[3][ia], V[4][ia]);
+      if constexpr (OFFSET) {
+        reconstruct_offset(w, st, Ub[p], mL[p], mR[p]);
+        reconstruct_offset(w, sa, Ub[ia], aL[p], aR[p]);
+      } else {
+        T fl, fr;
+        reconstruct(w, st, fl, fr);
+        mL[p] = double(fl);
+        mR[p] = double(fr);
+        reconstruct(w, sa, fl, fr);
+        aL[p] = double(fl);
+        aR[p] = double(fr);
+      }
     }
     // velocity and pressure, each with its own weights
     double uL[D], uR[D], PL, PR;
@@ -224,14 +234,17 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
     for (int v = N; v <= N + D; v++) {
       Stencil<T> st = stencil<T>(V[0][v], V[1][v], V[2][v], V[3][v], V[4][v]);
       W6<T> w = weights_of<T>(st);
-      T fl, fr;
-      reconstruct(w, st, fl, fr);
+      // velocity and pressure in value form in every precision: a uniform
+      // field (FP64 noise below the FP32 resolution) gives uniform faces
+      T tl, tr;
+      reconstruct(w, st, tl, tr);
+      const double fl = double(tl), fr = double(tr);
       if (v < N + D) {
-        uL[v - N] = double(fl);
-        uR[v - N] = double(fr);
+        uL[v - N] = fl;
+        uR[v - N] = fr;
       } else {
-        PL = double(fl);
-        PR = double(fr);
+        PL = fl;
+        PR = fr;
       }
     }
     Face<N, D> fL, fR;

@@ -8,6 +8,8 @@
 // more windows: the cost of the limiter branches, clustered in space, no
 // longer sets the time of whole SMs.
 #pragma once
+#include <type_traits>
+
 #include "wenoc_sweep.cuh"
 
 namespace wc {
@@ -54,8 +56,7 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
       u[I::U(jj)] = __longlong_as_double(__double_as_longlong(u[I::U(jj)]) ^ mask);
     }
   };
-  auto store_slot = [&](int s, const double* u) {
-    double v[NV];
+  auto store_slot = [&](int s, const double* u, double* v) {
     cons_to_prim<N, D>(m, u, v);
     double* sl = slots + s * SLOTD;
     sl[0] = v[I::E];
@@ -63,16 +64,19 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
 #pragma unroll
     for (int k = 0; k < NV; k++) Vs[k] = T(v[k]);
   };
+  // reduced precision: mass and fraction faces = FP64 cell value (a
+  // conservative and primitive variable alike) + offset in T
+  constexpr bool OFFSET = !std::is_same<T, double>::value;
 
   const int c = c0 - 1 + lane;
-  double Ub[NV];
+  double Ub[NV], Vtmp[NV];
   load_cons(c, Ub);
-  store_slot(lane + 2, Ub);
+  store_slot(lane + 2, Ub, Vtmp);
   if (lane < 4) {
     const int s = lane < 2 ? lane : 32 + lane;  // slots 0, 1, 34, 35
-    double u[NV];
+    double u[NV], v[NV];
     load_cons(c0 - 3 + s, u);
-    store_slot(s, u);
+    store_slot(s, u, v);
   }
   __syncwarp();
   const T* V[5];
@@ -105,9 +109,10 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
         wl.invL = wl.invR = T(1) / T(6);
         bool okL = true, okR = true, flat = true;
         auto judge = [&](const Stencil<T>& q) {
+          // offsets from the cell value with the plain and the learned weights
           T pl, pr, ql, qr;
-          reconstruct(w, q, pl, pr);
-          reconstruct(wl, q, ql, qr);
+          offsets(w, q, pl, pr);
+          offsets(wl, q, ql, qr);
           const T hi = fmax(fmax(fmax(T(0), q.da), fmax(q.db, q.dd)), q.de);
           const T lo = fmin(fmin(fmin(T(0), q.da), fmin(q.db, q.dd)), q.de);
           const T tol = T(a.tau) * (hi - lo);
@@ -135,13 +140,18 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
         }
       }
     }
-    T fl, fr;
-    reconstruct(w, st, fl, fr);
-    mL[p] = double(fl);
-    mR[p] = double(fr);
-    reconstruct(w, sa, fl, fr);
-    aL[p] = double(fl);
-    aR[p] = double(fr);
+    if constexpr (OFFSET) {
+      reconstruct_offset(w, st, Ub[p], mL[p], mR[p]);
+      reconstruct_offset(w, sa, Ub[ia], aL[p], aR[p]);
+    } else {
+      T fl, fr;
+      reconstruct(w, st, fl, fr);
+      mL[p] = double(fl);
+      mR[p] = double(fr);
+      reconstruct(w, sa, fl, fr);
+      aL[p] = double(fl);
+      aR[p] = double(fr);
+    }
   }
   // velocity and pressure, each with its own weights
   double uL[D], uR[D], PL, PR;
@@ -149,14 +159,17 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
   for (int v = N; v <= N + D; v++) {
     Stencil<T> st = stencil<T>(V[0][v], V[1][v], V[2][v], V[3][v], V[4][v]);
     W6<T> w = weights_of<T>(st);
-    T fl, fr;
-    reconstruct(w, st, fl, fr);
+      // velocity and pressure in value form in every precision: a uniform
+      // field (FP64 noise below the FP32 resolution) gives uniform faces
+      T tl, tr;
+      reconstruct(w, st, tl, tr);
+      const double fl = double(tl), fr = double(tr);
     if (v < N + D) {
-      uL[v - N] = double(fl);
-      uR[v - N] = double(fr);
+      uL[v - N] = fl;
+      uR[v - N] = fr;
     } else {
-      PL = double(fl);
-      PR = double(fr);
+      PL = fl;
+      PR = fr;
     }
   }
   Face<N, D> fL, fR;
