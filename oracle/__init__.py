@@ -54,6 +54,7 @@ class _Grid(ctypes.Structure):
         ("energy_limiter", ctypes.c_int),
         ("bc", ctypes.c_int * 6),
         ("consistent", ctypes.c_int),
+        ("kmodel", ctypes.c_int),
     ]
 
 
@@ -124,6 +125,7 @@ class Grid:
     limiter: bool = True        # Eq. 17-20
     energy_limiter: bool = True  # Eq. 21
     scheme: str = "c"           # "c": Eq. 19 (WENO-C); "cl": Eq. 23-25 (WENO-CL)
+    kmodel: str = "allaire"     # K_p of Eq. 2-3: "allaire" (0) or "kapila" (R15)
     _c: _Grid = field(default=None, repr=False)
 
     def __post_init__(self):
@@ -152,6 +154,7 @@ class Grid:
         for k in range(6):
             g.bc[k] = BC[self.bc[k]] if isinstance(self.bc[k], str) else int(self.bc[k])
         g.consistent = {"c": 0, "cl": 1}[self.scheme]
+        g.kmodel = {"allaire": 0, "kapila": 1}[self.kmodel]
         self._c = g
 
     @property

@@ -61,6 +61,13 @@
  *      S^(alpha_p) of a face is zero the faces are left as they are; a
  *      ratio x/0 with x != 0 is +-infinity before the clamp to [0, 1].
  *      Eq. 20 and Eq. 21 follow as in WENO-C.
+ *  R15 Kapila model (Sec. 2.1): K_p = rho c^2 / (rho_p c_p^2) - 1.  Put into
+ *      Eq. 2 this is an identity for any rho c^2; the constraint
+ *      sum_p alpha_p K_p = 0 stated with Eq. 2 fixes it: 1 / (rho c^2) =
+ *      sum_p alpha_p / (rho_p c_p^2) (Wood), rho_p c_p^2 = gamma_p (P +
+ *      Pinf_p).  The source factor alpha_p (1 + K_p) of Eq. 3 is evaluated
+ *      at the cell average (as for K_p = 0); the wave speeds and the time
+ *      step use this mixture sound speed.
  *  R13 Rounding residue below the bounds.  In exact arithmetic the faces
  *      scaled by Eq. 18 (f_min = 0), Eq. 20 and Eq. 21 have non-negative
  *      masses and fractions, and every Runge-Kutta stage (a convex
@@ -103,6 +110,7 @@ typedef struct {
   int energy_limiter;   /* 1: Eq. 21 applied; 0: skipped */
   int bc[6];            /* lo/hi per axis: OR_BC_* */
   int consistent;       /* 0: Eq. 19 (WENO-C); 1: Eq. 23-25 (WENO-CL) */
+  int kmodel;           /* K_p of Eq. 2-3: 0 Allaire (K_p = 0); 1 Kapila (R15) */
 } or_grid;
 
 /* ---- state layout ---------------------------------------------------------
@@ -458,18 +466,33 @@ static int recon_cell(const or_grid *g, const double *Ust, double *UL, double *U
   return limit_chain(g, Ust + 2 * nvar, VL, VR, UL, UR, VfL, VfR, th);
 }
 
-/* Mixture sound speed, Eq. 2 with K_p = 0 (R8). */
-static double sound_speed(const or_grid *g, const double *U, const double *V) {
+/* rho c^2 of the mixture for the pressure P and fractions alpha: Eq. 2 with
+ * K_p = 0 (R8), or Wood's formula for the Kapila model (R15). */
+static double mixture_rhoc2(const or_grid *g, const double *alpha, double P) {
   int N = g->N;
-  double rho = 0.0, num = 0.0, den = 0.0, P = V[IENE(g)];
+  if (g->kmodel) {
+    double s = 0.0;
+    for (int p = 0; p < N; p++) s += alpha[p] / (g->gamma[p] * (P + g->pinf[p]));
+    return 1.0 / s;
+  }
+  double num = 0.0, den = 0.0;
   for (int p = 0; p < N; p++) {
-    rho += U[IMASS(p)];
-    double Aa = eos_A(g, p) * U[IALF(g, p)];
+    double Aa = eos_A(g, p) * alpha[p];
     num += Aa * (g->gamma[p] * (P + g->pinf[p]));
     den += Aa;
   }
-  double rhoc2 = num / den;
-  return sqrt(rhoc2 / rho);
+  return num / den;
+}
+
+/* Mixture sound speed (R8, R15). */
+static double sound_speed(const or_grid *g, const double *U, const double *V) {
+  int N = g->N;
+  double rho = 0.0, alpha[OR_MAXP];
+  for (int p = 0; p < N; p++) {
+    rho += U[IMASS(p)];
+    alpha[p] = U[IALF(g, p)];
+  }
+  return sqrt(mixture_rhoc2(g, alpha, V[IENE(g)]) / rho);
 }
 
 /* Physical flux of Eq. 1 (hyperbolic part) in direction dir. */
@@ -620,10 +643,21 @@ static int rhs_dir(const or_grid *g, int dir, const double *U, double *Lout) {
         long cell = base + m * stride;
         for (int v = 0; v < nvar; v++)
           Lout[v * nc + cell] += -(Fx[(m + 1) * nvar + v] - Fx[m * nvar + v]) / dx;
-        /* H^HB(Ubar) div(u-hat): alpha_p (1 + K_p), K_p = 0 */
+        /* H^HB(Ubar) div(u-hat): alpha_p (1 + K_p) at the cell average */
+        double onepk[OR_MAXP];
+        for (int p = 0; p < N; p++) onepk[p] = 1.0;
+        if (g->kmodel) {
+          double uc[OR_MAXV], vc[OR_MAXV], alpha[OR_MAXP];
+          for (int v = 0; v < nvar; v++) uc[v] = U[(long)v * nc + cell];
+          cons_to_prim(g, uc, vc);
+          for (int p = 0; p < N; p++) alpha[p] = uc[IALF(g, p)];
+          double rhoc2 = mixture_rhoc2(g, alpha, vc[IENE(g)]);
+          for (int p = 0; p < N; p++)
+            onepk[p] = rhoc2 / (g->gamma[p] * (vc[IENE(g)] + g->pinf[p]));
+        }
         for (int p = 0; p < N; p++) {
           double ab = U[(long)IALF(g, p) * nc + cell];
-          Lout[(long)IALF(g, p) * nc + cell] += ab * (1.0 + 0.0) * (uh[m + 1] - uh[m]) / dx;
+          Lout[(long)IALF(g, p) * nc + cell] += ab * onepk[p] * (uh[m + 1] - uh[m]) / dx;
         }
       }
     }

@@ -536,3 +536,57 @@ def test_weno_cl_faces_sum_to_average_and_stay_bounded():
             assert ok.sum() > 100
             assert np.allclose(UL[:, ok], L2[:, ok], rtol=1e-10, atol=0)
             assert np.allclose(UR[:, ok], R2[:, ok], rtol=1e-10, atol=0)
+
+
+# ---------------------------------------------------------------- Kapila model (Sec. 2.1, Eq. 2-3)
+def test_kapila_wood_speed_air_water_half():
+    """K_p = rho c^2/(rho_p c_p^2) - 1 with sum alpha_p K_p = 0 is Wood's
+    mixture speed: a 50/50 air/water mixture at 1 bar sounds at about 24 m/s
+    (the textbook minimum of bubbly water), far below the K_p = 0 speed."""
+    g = [1.4, 4.4]
+    pi = [0.0, 6e8]
+    V = np.array([[0.5 * 1.2], [0.5 * 1000.0], [0.0], [1e5], [0.5], [0.5]])
+    gk = oracle.Grid((1,), (1.0,), g, pi, kmodel="kapila")
+    ga = oracle.Grid((1,), (1.0,), g, pi, kmodel="allaire")
+    ck = oracle.sound_speed(gk, oracle.prim_to_cons(gk, V))[0]
+    ca = oracle.sound_speed(ga, oracle.prim_to_cons(ga, V))[0]
+    assert 23.0 < ck < 24.5, ck
+    assert ca > 20 * ck
+
+
+def test_kapila_reduces_to_allaire_for_one_material():
+    """Two phases of the same material (and one phase alone): K_p = 0, so the
+    Kapila rhs equals the Allaire rhs to round-off."""
+    c = inputs.interface_advection_1d(n=64)
+    gam, pin = [c.gamma[1]] * 2, [c.pinf[1]] * 2
+    V = c.V.copy()
+    V[0] *= 1000.0  # both phases water-dense
+    ga = oracle.Grid(c.shape, c.dx, gam, pin, flux="hllc")
+    gk = oracle.Grid(c.shape, c.dx, gam, pin, flux="hllc", kmodel="kapila")
+    V[2] += 0.1 * np.sin(2 * np.pi * np.arange(64) / 64)  # a divergent velocity field
+    U = oracle.prim_to_cons(ga, V)
+    La, Lk = oracle.rhs(ga, U), oracle.rhs(gk, U)
+    assert np.allclose(Lk, La, rtol=1e-12, atol=1e-12 * np.abs(La).max())
+
+
+def test_kapila_keeps_unity_sum_and_absent_phase():
+    """sum_p alpha_p (1 + K_p) = 1 makes sum_p d(alpha_p)/dt = 0 with the
+    u-hat of Sec. 2.2.1; an absent phase gets no source (factor alpha_p)."""
+    c = inputs.spheres_shock_3d(shape=(20, 16, 12), seed=1, nsph=4, rmin_cells=2, rmax_cells=5)
+    gk = oracle.Grid(c.shape, c.dx, c.gamma, c.pinf, c.D, flux="hll", bc=c.bc, kmodel="kapila")
+    ga = oracle.Grid(c.shape, c.dx, c.gamma, c.pinf, c.D, flux="hll", bc=c.bc)
+    U = oracle.prim_to_cons(gk, c.V)
+    Lk, La = oracle.rhs(gk, U), oracle.rhs(ga, U)
+    N = c.N
+    a0 = N + 3 + 1
+    rate = oracle.max_rate(gk, U)
+    assert np.abs(Lk[a0:a0 + N].sum(0)).max() / rate < 1e-13
+    assert np.abs(Lk[a0:] - La[a0:]).max() > 1e-6 * np.abs(La[a0:]).max()  # the models differ
+    # absent phase
+    V2 = c.V.copy()
+    V2[a0 + 2] = 0.0
+    V2[2] = 0.0
+    V2[a0 + 1] = 1.0 - V2[a0]
+    U2 = oracle.prim_to_cons(gk, V2)
+    L2 = oracle.rhs(gk, U2)
+    assert np.all(L2[2] == 0.0) and np.all(L2[a0 + 2] == 0.0)
