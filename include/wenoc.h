@@ -54,6 +54,7 @@ enum { WC_BC_PERIODIC = 0, WC_BC_REFLECTIVE = 1, WC_BC_OUTFLOW = 2 };
 enum { WC_FLUX_HLL = 0, WC_FLUX_HLLC = 1 };
 enum { WC_PREC_FP64 = 0, WC_PREC_MIXED = 1, WC_PREC_LEARNED = 2 };
 enum { WC_SCHEME_C = 0, WC_SCHEME_CL = 1 };
+enum { WC_KMODEL_ALLAIRE = 0, WC_KMODEL_KAPILA = 1 };
 
 /* Grid, materials and scheme options.  Materials follow the stiffened-gas
  * equation of state of Eq. 26: A_p = 1/(gamma_p-1), B_p = gamma_p Pinf_p /
@@ -90,6 +91,11 @@ typedef struct {
   int scheme;                 /* WC_SCHEME_C: unity sum by Eq. 19 (WENO-C,
                                  default); WC_SCHEME_CL: the consistent limiter
                                  of Eq. 23-25 instead (WENO-CL, Sec. 3.4) */
+  int kmodel;                 /* K_p of Eq. 2-3: WC_KMODEL_ALLAIRE (K_p = 0,
+                                 default) or WC_KMODEL_KAPILA (K_p = rho c^2 /
+                                 (rho_p c_p^2) - 1 with Wood's mixture speed
+                                 1/(rho c^2) = sum_p alpha_p/(rho_p c_p^2),
+                                 which sum_p alpha_p K_p = 0 implies) */
 } wc_grid_desc;
 
 typedef struct wc_grid wc_grid;

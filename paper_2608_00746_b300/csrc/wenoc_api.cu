@@ -104,6 +104,7 @@ extern "C" wc_status wc_init_grid(const wc_grid_desc* desc, wc_grid** out) {
   if (d.seg < 0 || d.block < 0 || d.block > 128 || (d.block % 32) != 0) return WC_ERR_ARG;
   if (d.blocks_per_sm < 0 || d.blocks_per_sm > 4) return WC_ERR_ARG;
   if (d.scheme != WC_SCHEME_C && d.scheme != WC_SCHEME_CL) return WC_ERR_ARG;
+  if (d.kmodel != WC_KMODEL_ALLAIRE && d.kmodel != WC_KMODEL_KAPILA) return WC_ERR_ARG;
   for (int p = 0; p < d.nphase; p++)
     if (!(d.gamma[p] > 1.0) || !(d.pinf[p] >= 0.0)) return WC_ERR_ARG;
   wc_grid* g = new (std::nothrow) wc_grid();
@@ -115,11 +116,13 @@ extern "C" wc_status wc_init_grid(const wc_grid_desc* desc, wc_grid** out) {
   memset(&m, 0, sizeof(m));
   m.N = d.nphase;
   m.cl = d.scheme == WC_SCHEME_CL;
+  m.kapila = d.kmodel == WC_KMODEL_KAPILA;
   for (int p = 0; p < d.nphase; p++) {
     m.A[p] = 1.0 / (d.gamma[p] - 1.0);
     m.B[p] = d.gamma[p] * d.pinf[p] / (d.gamma[p] - 1.0);
     m.D[p] = d.D[p];
     m.pinf[p] = d.pinf[p];
+    m.gam[p] = d.gamma[p];
     m.Ag[p] = m.A[p] * d.gamma[p];
     m.Apmin[p] = m.A[p] * d.pmin[p];
     m.Cmin[p] = m.A[p] * d.pmin[p] + m.B[p];

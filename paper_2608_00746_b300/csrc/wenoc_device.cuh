@@ -31,6 +31,8 @@ struct Mat {
   double Cmin[MAXP];        // A Pmin + B: alpha_p rho_p e_p(Pmin_p, rho_p) per alpha_p
   double Apmin[MAXP];       // A Pmin
   int cl;                   // 1: WENO-CL (Eq. 23-25 instead of Eq. 19)
+  int kapila;               // K_p of Eq. 2-3: 0 Allaire (K_p = 0), 1 Kapila (Wood speed)
+  double gam[MAXP];         // gamma_p
 };
 
 template <int N, int D>
@@ -648,12 +650,56 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
   }
 }
 
+// 1 / (rho_p c_p^2) = 1 / (gamma_p (P + Pinf_p)) of the stiffened gas
+template <typename TF>
+__device__ __forceinline__ TF inv_rhoc2_phase(const Mat& m, int p, TF P) {
+  const TF x = TF(m.gam[p]) * (P + TF(m.pinf[p]));
+  if constexpr (sizeof(TF) == 8) {
+    return in_range(x, 1e-300, 1e300) ? rcp_nr(x) : 1.0 / x;
+  } else {
+    return TF(1) / x;
+  }
+}
+
+// Source factors alpha_p (1 + K_p) of Eq. 3 at a cell average (alpha from the
+// conservative state U, pressure P): alpha_p for K_p = 0; for the Kapila
+// model alpha_p rho c^2 / (rho_p c_p^2) with Wood's rho c^2.
+template <int N, int D>
+__device__ __forceinline__ void source_factors(const Mat& m, const double* U, double P,
+                                               double* f) {
+  using I = Idx<N, D>;
+  if (!m.kapila) {
+#pragma unroll
+    for (int p = 0; p < N; p++) f[p] = U[I::A(p)];
+    return;
+  }
+  double r[N], sw = 0.0;
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    r[p] = inv_rhoc2_phase<double>(m, p, P);
+    sw = fma(U[I::A(p)], r[p], sw);
+  }
+  const double rhoc2 = in_range(sw, 1e-300, 1e300) ? rcp_nr(sw) : 1.0 / sw;
+#pragma unroll
+  for (int p = 0; p < N; p++) f[p] = U[I::A(p)] * (r[p] * rhoc2);
+}
+
 // ------------------------------------------------------------------ fluxes
 // Mixture sound speed of Eq. 2 with K_p = 0: rho c^2 = sum A g alpha (P+Pinf)
 // / sum A alpha.
 template <int N, int D, typename TF>
 __device__ __forceinline__ TF sound_speed(const Mat& m, const double* U, TF rho, TF P) {
   using I = Idx<N, D>;
+  if (m.kapila) {
+    // Kapila model: K_p = rho c^2 / (rho_p c_p^2) - 1 with sum alpha_p K_p = 0
+    // gives Wood's 1 / (rho c^2) = sum_p alpha_p / (rho_p c_p^2)
+    TF sw = TF(0);
+#pragma unroll
+    for (int p = 0; p < N; p++) sw = sw + TF(U[I::A(p)]) * inv_rhoc2_phase<TF>(m, p, P);
+    const TF xw = rho * sw;
+    if (in_range(xw, TF(1e-30), TF(1e30))) return rsqrt_nr(xw);
+    return TF(1) / sqrt(xw);
+  }
   TF num = TF(0), den = TF(0);
 #pragma unroll
   for (int p = 0; p < N; p++) {

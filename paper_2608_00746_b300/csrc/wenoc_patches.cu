@@ -120,6 +120,7 @@ extern "C" wc_status wc_patches_init(const wc_patches_desc* desc, const int* edg
     m.B[p] = d.gamma[p] * d.pinf[p] / (d.gamma[p] - 1.0);
     m.D[p] = d.D[p];
     m.pinf[p] = d.pinf[p];
+    m.gam[p] = d.gamma[p];
     m.Ag[p] = m.A[p] * d.gamma[p];
     m.Apmin[p] = m.A[p] * d.pmin[p];
     m.Cmin[p] = m.A[p] * d.pmin[p] + m.B[p];

@@ -132,7 +132,7 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
   for (int c = s - 3; c <= s; c++) load(c);
 
   Face<N, D> prevL;
-  double Fprev[NV], Uprev[NV];
+  double Fprev[NV], Uprev[NV], sfprev[N];
   double uprev = 0.0;
   double Qprev[N], Qcur[N];
   auto load_q = [&](int c, double* q) {
@@ -269,7 +269,7 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
         for (int v = 0; v < NV; v++) {
           // Eq. 3: -div F + alpha (1 + K) div u_hat;  Eq. 5: +div F^PF
           double val = (a.kind == 1 ? 1.0 : -1.0) * (F[v] - Fprev[v]) * a.inv_dx;
-          if (a.kind == 0 && v >= N + D + 1) val = fma(Uprev[v], du, val);
+          if (a.kind == 0 && v >= N + D + 1) val = fma(sfprev[v - (N + D + 1)], du, val);
           long idx = (long)v * a.ncell + cell;
           if (not_finite(val)) bad |= ST_NAN;
           if (a.mode == 0) {
@@ -295,6 +295,8 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
     prevL = fL;
 #pragma unroll
     for (int v = 0; v < NV; v++) Uprev[v] = Ub[v];
+    // source factors alpha_p (1 + K_p) of this cell, used when it is updated
+    source_factors<N, D>(m, Ub, Pb, sfprev);
     if (a.kind == 1) {
 #pragma unroll
       for (int p = 0; p < N; p++) Qprev[p] = Qcur[p];

@@ -201,10 +201,12 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
     const double du = (uh - uhl) * a.inv_dx;
     // Eq. 3: -div F + alpha (1 + K) div u_hat;  Eq. 5: +div F^PF
     const double sdx = a.kind == 1 ? a.inv_dx : -a.inv_dx;
+    double sf[N];
+    source_factors<N, D>(m, Ub, Pb, sf);
 #pragma unroll
     for (int v = 0; v < NV; v++) {
       double val = (F[v] - Fl[v]) * sdx;
-      if (a.kind == 0 && v >= N + D + 1) val = fma(Ub[v], du, val);
+      if (a.kind == 0 && v >= N + D + 1) val = fma(sf[v - (N + D + 1)], du, val);
       const long idx = (long)v * a.ncell + cell;
       if (not_finite(val)) bad |= ST_NAN;
       if (a.mode == 0) {

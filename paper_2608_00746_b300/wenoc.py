@@ -20,6 +20,7 @@ BC = {"periodic": 0, "reflective": 1, "outflow": 2}
 FLUX = {"hll": 0, "hllc": 1}
 PREC = {"fp64": 0, "mixed": 1, "learned": 2}
 SCHEME = {"c": 0, "cl": 1}
+KMODEL = {"allaire": 0, "kapila": 1}
 STATUS = {0: "WC_OK", 1: "WC_ERR_ARG", 2: "WC_ERR_CUDA", 3: "WC_ERR_INADMISSIBLE",
           4: "WC_ERR_NAN", 5: "WC_ERR_UNSUPPORTED", 6: "WC_ERR_STATE", 7: "WC_ERR_TIMEOUT"}
 
@@ -48,6 +49,7 @@ class GridDesc(ctypes.Structure):
         ("block", ctypes.c_int),
         ("blocks_per_sm", ctypes.c_int),
         ("scheme", ctypes.c_int),
+        ("kmodel", ctypes.c_int),
     ]
 
 
@@ -184,7 +186,7 @@ class Grid:
 
     def __init__(self, shape, dx, gamma, pinf, D=None, pmin=None, flux="hll",
                  bc=("periodic",) * 6, precision="fp64", energy_limiter=True, seg=0, block=0,
-                 blocks_per_sm=0, scheme="c"):
+                 blocks_per_sm=0, scheme="c", kmodel="allaire"):
         N = len(gamma)
         d = GridDesc()
         d.dim = len(shape)
@@ -205,6 +207,7 @@ class Grid:
         d.block = int(block)
         d.blocks_per_sm = int(blocks_per_sm)
         d.scheme = SCHEME[scheme]
+        d.kmodel = KMODEL[kmodel]
         self.desc = d
         self.shape = tuple(shape)
         h = _VP()

@@ -1,0 +1,118 @@
+"""The Kapila model (K_p = rho c^2/(rho_p c_p^2) - 1, Wood's mixture speed)
+on the GPU against the oracle's Kapila model: rhs and Runge-Kutta parity at
+1e-12 in FP64 (the time step comes from the Wood speed), an absent phase
+bit-identical to the run without it, bounds and the unity sum of the rhs,
+the isolated interface in equilibrium, and the mixed-precision L1 bound."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2608_00746_b300 import inputs, wenoc
+
+from gpu_util import SMALL_CASES, l1_group, momentum_floor, rhs_err, state_err, to_dev
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def _grids(case, precision="fp64"):
+    go = oracle.Grid(case.shape, case.dx, case.gamma, case.pinf, case.D, flux=case.flux,
+                     bc=case.bc, kmodel="kapila")
+    g = wenoc.Grid(case.shape, case.dx, case.gamma, case.pinf, case.D, flux=case.flux,
+                   bc=case.bc, precision=precision, kmodel="kapila")
+    return go, g
+
+
+@pytest.mark.parametrize("name", ["slab_1d_hllc", "shock_bubble_2d_ragged", "spheres_3d_ragged",
+                                  "circles_2d_n3", "five_phase_2d"])
+def test_kapila_rhs_parity(gpu, name):
+    case = SMALL_CASES[name]()
+    go, g = _grids(case)
+    U = oracle.prim_to_cons(go, case.V)
+    dt = case.meta.get("dt") if case.meta else None
+    for _ in range(2):
+        U, _ = oracle.rk3_step(go, U, cfl=case.cfl or 0.2, dt=dt or 0.0)
+    Ud = to_dev(U)
+    g.bind(Ud)
+    L = g.rhs(Ud).cpu().numpy()
+    g.sync_status()
+    err = rhs_err(L, oracle.rhs(go, U), U, oracle.max_rate(go, U), case.N, case.dim,
+                  momentum_floor(go, U))
+    assert (err <= TOL).all(), (name, err)
+
+
+@pytest.mark.parametrize("name", ["shock_bubble_2d_ragged", "spheres_3d_ragged"])
+def test_kapila_rk_parity(gpu, name):
+    case = SMALL_CASES[name]()
+    go, g = _grids(case)
+    U = oracle.prim_to_cons(go, case.V)
+    Ud = to_dev(U)
+    g.bind(Ud)
+    for _ in range(5):
+        U, dt_or = oracle.rk3_step(go, U, cfl=0.2)
+        dt = g.rk_step(cfl=0.2, want_dt=True)
+        assert dt == pytest.approx(dt_or, rel=1e-13)
+    g.sync_status()
+    err = state_err(Ud.cpu().numpy(), U, case.N, case.dim, momentum_floor(go, U))
+    assert (err <= TOL).all(), err
+    V = g.cons_to_prim(Ud).cpu().numpy()
+    a0 = case.N + case.dim + 1
+    a = V[a0:]
+    assert a.min() >= 0.0 and a.max() <= 1.0
+    # the rhs keeps sum_p alpha_p (sum_p alpha_p (1 + K_p) = 1); over whole
+    # stages the stiff source of a dilute phase (1 + K_air ~ 2e4 in water)
+    # can overshoot below zero, and removing that residue moves the sum
+    L = g.rhs(Ud).cpu().numpy()
+    rate = oracle.max_rate(go, U)
+    assert np.abs(L[a0:].sum(0)).max() / rate < 1e-13
+
+
+def test_kapila_absent_phase_bit_identical(gpu):
+    case = inputs.shock_bubble_2d(nx=64, ny=32, seed=2)
+    N = 3
+    V3 = np.zeros((2 * N + 3,) + case.V.shape[1:])
+    V3[0:2], V3[3:6], V3[6:8] = case.V[0:2], case.V[2:5], case.V[5:7]
+    g3 = list(case.gamma) + [inputs.PHASE3["gamma"]]
+    p3 = list(case.pinf) + [inputs.PHASE3["pinf"]]
+    D3 = list(case.D) + [0.0]
+    res = []
+    for gam, pin, Dm, V in ((case.gamma, case.pinf, case.D, case.V), (g3, p3, D3, V3)):
+        go = oracle.Grid(case.shape, case.dx, gam, pin, Dm, flux=case.flux, bc=case.bc)
+        g = wenoc.Grid(case.shape, case.dx, gam, pin, Dm, flux=case.flux, bc=case.bc,
+                       kmodel="kapila")
+        U = to_dev(oracle.prim_to_cons(go, V))
+        g.bind(U)
+        g.rk_step(dt=2e-7, nsteps=10)
+        g.sync_status()
+        res.append(U)
+    U2, U3 = res
+    keep = [0, 1, 3, 4, 5, 6, 7]
+    assert torch.equal(U3[keep], U2) and not U3[[2, 8]].any()
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_kapila_interface_equilibrium(gpu, mode):
+    c = inputs.interface_advection_1d(n=200)
+    go, g = _grids(c, precision=mode)
+    U = to_dev(oracle.prim_to_cons(go, c.V))
+    g.bind(U)
+    g.rk_step(cfl=0.5, nsteps=50)
+    g.sync_status()
+    V = g.cons_to_prim(U).cpu().numpy()
+    assert np.abs(V[2] - 1.0).max() < 5e-11
+    assert np.abs(V[3] - 1e5).max() / (1e5 + max(c.pinf)) < 1e-13
+
+
+def test_kapila_mixed_l1_vs_fp64_oracle(gpu):
+    case = inputs.shock_bubble_2d(nx=128, ny=64, seed=5)
+    go, g = _grids(case, precision="mixed")
+    U0 = oracle.prim_to_cons(go, case.V)
+    U = to_dev(U0)
+    g.bind(U)
+    Uo = U0.copy()
+    for _ in range(10):
+        Uo, dt = oracle.rk3_step(go, Uo, cfl=0.2)
+        g.rk_step(dt=dt)
+    g.sync_status()
+    assert (l1_group(U.cpu().numpy(), Uo, case.N, case.dim) <= 1e-5).all()
