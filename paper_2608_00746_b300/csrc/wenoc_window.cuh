@@ -159,11 +159,11 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
   for (int v = N; v <= N + D; v++) {
     Stencil<T> st = stencil<T>(V[0][v], V[1][v], V[2][v], V[3][v], V[4][v]);
     W6<T> w = weights_of<T>(st);
-      // velocity and pressure in value form in every precision: a uniform
-      // field (FP64 noise below the FP32 resolution) gives uniform faces
-      T tl, tr;
-      reconstruct(w, st, tl, tr);
-      const double fl = double(tl), fr = double(tr);
+    // velocity and pressure in value form in every precision: a uniform
+    // field (FP64 noise below the FP32 resolution) gives uniform faces
+    T tl, tr;
+    reconstruct(w, st, tl, tr);
+    const double fl = double(tl), fr = double(tr);
     if (v < N + D) {
       uL[v - N] = fl;
       uR[v - N] = fr;
