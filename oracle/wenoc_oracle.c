@@ -78,8 +78,22 @@
  *      negative average, and Eq. 18 on a negative average (theta = 0) taken
  *      into Eq. 20's minimum over phases drops the whole cell to first order.
  *      Such residues are set to the bound: scaled face masses and fractions
- *      below 0 become 0, and stage results of masses below 0 become 0 and
- *      of fractions outside [0, 1] become the nearer bound.
+ *      below 0 become 0, and stage results outside the bounds by at most
+ *      2^-48 of their scale (the cell's density before the stage for a
+ *      mass, 1 for a fraction) become the bound.  A larger excursion is not
+ *      rounding: at a time step above the sufficient CFL bound of Sec. 4.2
+ *      (the paper's own tests run so) the scheme itself can leave the bounds
+ *      slightly; that value stays, the next limiter (theta = 0 on a negative
+ *      average) takes the cell to first order, and no clamp breaks the
+ *      consistency of (alpha_p rho_p) and alpha_p or the pressure
+ *      equilibrium (Sec. 4.1.1: WENO-C keeps both at round-off).
+ *  R16 Comparison schemes (Sec. 3.2, Sec. 4.1.1: WENO-JS and WENO-W without
+ *      Eq. 16-21).  Each primitive variable is reconstructed with its own
+ *      weights and the faces go to the Riemann solver unlimited.  Without
+ *      the limiters nothing keeps the stages inside the bounds, so values
+ *      outside them are overshoots of the scheme, not rounding residue:
+ *      R13's stage clamp is not applied (clamping alpha_1 at 1 while
+ *      (alpha_1 rho_1) overshoots would itself break consistency).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -276,8 +290,10 @@ static double theta_lower(double fbar, double fC, double fL, double fR, double f
   return t < 1.0 ? t : 1.0;
 }
 
-/* R13: a value below the bound 0 only by rounding becomes 0. */
-static double clamp0(double x) { return x < 0.0 ? 0.0 : x; }
+/* R13: fbar + theta (f - fbar) below the bound 0 is rounding residue when
+ * fbar >= 0 and becomes 0; with fbar < 0 (theta = 0, a stage that left the
+ * bound) the value is fbar itself and stays. */
+static double clamp0(double x, double fbar) { return x < 0.0 && fbar >= 0.0 ? 0.0 : x; }
 
 static double theta_pos(double fbar, double fL, double fR) {
   return theta_lower(fbar, center_value(fbar, fL, fR), fL, fR, 0.0);
@@ -316,8 +332,8 @@ static void consistent_limiter(const or_grid *g, const double *Ubar, double *V) 
     else if (Shat == 0.0) th = S[ph] > 0.0 ? 1.0 : 0.0; /* S_phat / 0 = +-inf */
     else th = clamp01(S[ph] / Shat);
     double mb = Ubar[IMASS(p)], ab = Ubar[IALF(g, p)];
-    V[IMASS(p)] = clamp0(mb + th * (V[IMASS(p)] - mb));
-    V[IALF(g, p)] = clamp0(ab + th * (V[IALF(g, p)] - ab));
+    V[IMASS(p)] = clamp0(mb + th * (V[IMASS(p)] - mb), mb);
+    V[IALF(g, p)] = clamp0(ab + th * (V[IALF(g, p)] - ab), ab);
   }
 }
 
@@ -334,10 +350,10 @@ static int limit_chain(const or_grid *g, const double *Ubar, double *VL, double 
       double tp = t1 < t2 ? t1 : t2;
       if (tp < th17) th17 = tp;
       if (tp < 1.0) {
-        VL[IMASS(p)] = clamp0(mb + tp * (VL[IMASS(p)] - mb));
-        VR[IMASS(p)] = clamp0(mb + tp * (VR[IMASS(p)] - mb));
-        VL[IALF(g, p)] = clamp0(ab + tp * (VL[IALF(g, p)] - ab));
-        VR[IALF(g, p)] = clamp0(ab + tp * (VR[IALF(g, p)] - ab));
+        VL[IMASS(p)] = clamp0(mb + tp * (VL[IMASS(p)] - mb), mb);
+        VR[IMASS(p)] = clamp0(mb + tp * (VR[IMASS(p)] - mb), mb);
+        VL[IALF(g, p)] = clamp0(ab + tp * (VL[IALF(g, p)] - ab), ab);
+        VR[IALF(g, p)] = clamp0(ab + tp * (VR[IALF(g, p)] - ab), ab);
       }
     }
     if (g->consistent) {
@@ -378,10 +394,10 @@ static int limit_chain(const or_grid *g, const double *Ubar, double *VL, double 
     for (int p = 0; p < N; p++) {
       double mb = Ubar[IMASS(p)], ab = Ubar[IALF(g, p)];
       if (th20 < 1.0) {
-        VL[IMASS(p)] = clamp0(mb + th20 * (VL[IMASS(p)] - mb));
-        VR[IMASS(p)] = clamp0(mb + th20 * (VR[IMASS(p)] - mb));
-        VL[IALF(g, p)] = clamp0(ab + th20 * (VL[IALF(g, p)] - ab));
-        VR[IALF(g, p)] = clamp0(ab + th20 * (VR[IALF(g, p)] - ab));
+        VL[IMASS(p)] = clamp0(mb + th20 * (VL[IMASS(p)] - mb), mb);
+        VR[IMASS(p)] = clamp0(mb + th20 * (VR[IMASS(p)] - mb), mb);
+        VL[IALF(g, p)] = clamp0(ab + th20 * (VL[IALF(g, p)] - ab), ab);
+        VR[IALF(g, p)] = clamp0(ab + th20 * (VR[IALF(g, p)] - ab), ab);
       }
     }
   }
@@ -401,10 +417,10 @@ static int limit_chain(const or_grid *g, const double *Ubar, double *VL, double 
         UR[v] = Ubar[v] + thpsi * (UR[v] - Ubar[v]);
       }
       for (int p = 0; p < N; p++) {
-        UL[IMASS(p)] = clamp0(UL[IMASS(p)]);
-        UR[IMASS(p)] = clamp0(UR[IMASS(p)]);
-        UL[IALF(g, p)] = clamp0(UL[IALF(g, p)]);
-        UR[IALF(g, p)] = clamp0(UR[IALF(g, p)]);
+        UL[IMASS(p)] = clamp0(UL[IMASS(p)], Ubar[IMASS(p)]);
+        UR[IMASS(p)] = clamp0(UR[IMASS(p)], Ubar[IMASS(p)]);
+        UL[IALF(g, p)] = clamp0(UL[IALF(g, p)], Ubar[IALF(g, p)]);
+        UR[IALF(g, p)] = clamp0(UR[IALF(g, p)], Ubar[IALF(g, p)]);
       }
     }
   }
@@ -906,15 +922,29 @@ int or_max_rate(const or_grid *g, const double *U, double *rate) {
   return OR_OK;
 }
 
-/* R13: stage results of masses below 0 become 0; fractions are kept in
- * [0, 1]. */
-static void stage_bounds(const or_grid *g, double *U) {
+/* R13: stage results outside the bounds by no more than the rounding of the
+ * stage sum -- 2^-48 of the scale, the cell's density before the stage for a
+ * mass and 1 for a fraction -- are set to the bound.  Larger excursions (a
+ * time step above the sufficient CFL bound of Sec. 4.2) are the scheme's
+ * own and stay; the limiter of the next stage treats them (Eq. 18, theta = 0
+ * on a negative average).  R16: no bound is restored without Eq. 17-20. */
+#define OR_STAGE_TOL 0x1p-48
+static void cell_density(const or_grid *g, const double *U, double *rho) {
+  long n = ncells(g);
+  for (long c = 0; c < n; c++) rho[c] = 0.0;
+  for (int p = 0; p < g->N; p++)
+    for (long c = 0; c < n; c++) rho[c] += U[(long)IMASS(p) * n + c];
+}
+
+static void stage_bounds(const or_grid *g, const double *rho_in, double *U) {
+  if (!g->limiter) return;
   long n = ncells(g);
   for (int p = 0; p < g->N; p++) {
     double *m = U + (long)IMASS(p) * n, *a = U + (long)IALF(g, p) * n;
     for (long c = 0; c < n; c++) {
-      m[c] = clamp0(m[c]);
-      a[c] = a[c] > 1.0 ? 1.0 : clamp0(a[c]);
+      if (m[c] < 0.0 && m[c] >= -OR_STAGE_TOL * rho_in[c]) m[c] = 0.0;
+      if (a[c] < 0.0 && a[c] >= -OR_STAGE_TOL) a[c] = 0.0;
+      if (a[c] > 1.0 && a[c] <= 1.0 + OR_STAGE_TOL) a[c] = 1.0;
     }
   }
 }
@@ -933,25 +963,28 @@ int or_rk3_step(const or_grid *g, double *U, double cfl, double dt_fixed, double
     dt = cfl / rate;
   }
   double *U0 = malloc(sizeof(double) * tot), *U1 = malloc(sizeof(double) * tot);
-  double *L = malloc(sizeof(double) * tot);
+  double *L = malloc(sizeof(double) * tot), *rho = malloc(sizeof(double) * ncells(g));
   memcpy(U0, U, sizeof(double) * tot);
   e = or_rhs(g, U0, L);
   if (!e) {
+    cell_density(g, U0, rho);
     for (long k = 0; k < tot; k++) U1[k] = U0[k] + dt * L[k];
-    stage_bounds(g, U1);
+    stage_bounds(g, rho, U1);
     e = or_rhs(g, U1, L);
   }
   if (!e) {
+    cell_density(g, U1, rho);
     for (long k = 0; k < tot; k++) U1[k] = 0.75 * U0[k] + 0.25 * U1[k] + 0.25 * dt * L[k];
-    stage_bounds(g, U1);
+    stage_bounds(g, rho, U1);
     e = or_rhs(g, U1, L);
   }
   if (!e) {
+    cell_density(g, U1, rho);
     for (long k = 0; k < tot; k++)
       U[k] = 1.0 / 3.0 * U0[k] + 2.0 / 3.0 * U1[k] + 2.0 / 3.0 * dt * L[k];
-    stage_bounds(g, U);
+    stage_bounds(g, rho, U);
   }
-  free(U0); free(U1); free(L);
+  free(U0); free(U1); free(L); free(rho);
   if (dt_used) *dt_used = dt;
   return e;
 }

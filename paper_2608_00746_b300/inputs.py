@@ -193,6 +193,22 @@ def multiphase_advection_2d(n=100, nphase=5, width_cells=1.0):
                 flux="hllc", cfl=0.0, meta=dict(dt=1e-3))
 
 
+def two_phase_advection_2d(n=100, width_cells=1.0):
+    """Sec. 4.1.1: doubly periodic [-0.5, 0.5]^2, an air circle (phase 1,
+    rho 1.204e-3, gamma 1.4) of radius 0.2 at the origin in water (phase 2,
+    rho 1, gamma 6.12, Pinf 0.1631), u = (1, 1), P = 4.819e-5, dt = 1e-3
+    (one period = 1000 steps on the paper's 100^2 grid)."""
+    dx = 1.0 / n
+    x, y = _centres((n, n), (dx, dx), lo=(-0.5, -0.5))
+    s = smooth_step(0.2 - np.sqrt(x ** 2 + y ** 2), width_cells * dx)
+    rho = (1.204e-3, 1.0)
+    V = _assemble([s, 1.0 - s], rho, [np.ones((n, n)), np.ones((n, n))],
+                  np.full((n, n), 4.819e-5))
+    return Case("two_phase_advection_2d", (n, n), (dx, dx), [1.4, 6.12], [0.0, 0.1631],
+                [0.0, 0.0], V, ("periodic",) * 6, flux="hllc", cfl=0.0,
+                meta=dict(dt=1e-3, rho=rho))
+
+
 def miscible_advection_2d(n=100, width_cells=1.0):
     """Four-phase advection with a non-zero, non-unity constant fraction
     (Sec. 4.1.3): doubly periodic [-0.5, 0.5]^2, u = (1, 1), P = 4.819e-5,

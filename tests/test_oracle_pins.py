@@ -590,3 +590,50 @@ def test_kapila_keeps_unity_sum_and_absent_phase():
     U2 = oracle.prim_to_cons(gk, V2)
     L2 = oracle.rhs(gk, U2)
     assert np.all(L2[2] == 0.0) and np.all(L2[a0 + 2] == 0.0)
+
+
+# ---------------------------------------------------------------- Sec. 4.1.1 scheme ordering
+COMPARATORS = {
+    "js": dict(weights="js", coupled=False, limiter=False, energy_limiter=False),
+    "w": dict(weights="w", coupled=False, limiter=False, energy_limiter=False),
+    "c": dict(),
+}
+
+
+def _two_phase_consistency(kw, n=50, steps=200):
+    """Max over cells of (alpha_1 rho_1)/rho_1 - alpha_1 after ``steps`` steps
+    of the Sec. 4.1.1 air-circle advection, plus the final state."""
+    case = inputs.two_phase_advection_2d(n=n)
+    g = grid_of(case, **kw)
+    U = oracle.prim_to_cons(g, case.V)
+    for _ in range(steps):
+        U, _ = oracle.rk3_step(g, U, dt=case.meta["dt"])
+    rho1 = case.meta["rho"][0]
+    return np.abs(U[0] / rho1 - U[5]).max(), U, g
+
+
+def test_two_phase_advection_scheme_ordering():
+    """Sec. 4.1.1 (the consistency-error history): WENO-JS fails consistency
+    (Eq. 14 with a = rho_1, eps/a^2 = 0.69), WENO-W removes it up to round-off
+    (the paper: about nine orders of magnitude below JS), WENO-C reduces it
+    further.  A dropped epsilon, an uncoupled WENO-C or a clamp that moves
+    alpha_1 without (alpha_1 rho_1) each fails one of the bounds."""
+    e = {k: _two_phase_consistency(kw)[0] for k, kw in COMPARATORS.items()}
+    assert e["js"] > 1e-2
+    assert e["w"] < 1e-11 and e["w"] < 1e-9 * e["js"]
+    assert e["c"] < 1e-13 and e["c"] < 0.5 * e["w"]
+
+
+def test_two_phase_advection_js_oscillates_in_mass_not_fraction():
+    """Sec. 3.2 / Fig. 1: with JS the mass (alpha_1 rho_1)/rho_1 overshoots
+    far more than alpha_1 (eps/rho_1^2 = 0.69 keeps non-smooth stencils of
+    the mass); WENO-C keeps both in [0, 1] and u, P uniform."""
+    _, U, g = _two_phase_consistency(COMPARATORS["js"])
+    over_m = max(-(U[0] / 1.204e-3).min(), (U[0] / 1.204e-3).max() - 1.0)
+    over_a = max(-U[5].min(), U[5].max() - 1.0)
+    assert over_m > 1e-2 and over_m > 30.0 * over_a
+    _, U, g = _two_phase_consistency(COMPARATORS["c"])
+    assert U[5:7].min() >= 0.0 and U[5:7].max() <= 1.0
+    V = oracle.cons_to_prim(g, U)
+    assert np.abs(V[2:4] - 1.0).max() < 1e-12
+    assert np.abs(V[4] / 4.819e-5 - 1.0).max() < 1e-8
