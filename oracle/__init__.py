@@ -70,7 +70,7 @@ def lib():
         for name, args in {
             "or_rhs": [gp, dp, dp],
             "or_rk3_step": [gp, dp, ctypes.c_double, ctypes.c_double, dp],
-            "or_pf_rhs": [gp, dp, dp, dp],
+            "or_pf_rhs": [gp, dp, dp, ctypes.c_double, dp],
             "or_pf_flux": [gp, ctypes.c_int, dp, dp, dp, dp, dp, dp],
             "or_faces": [gp, ctypes.c_int, dp, dp, dp, dp],
             "or_limit": [gp, ctypes.c_long, dp, dp, dp, dp, dp, dp],
@@ -195,12 +195,13 @@ def rhs(g: Grid, U: np.ndarray) -> np.ndarray:
     return L
 
 
-def pf_rhs(g: Grid, U: np.ndarray, Q: np.ndarray) -> np.ndarray:
-    """dU/dt of the Phase-Field step (Eq. 5) for the auxiliary fields Q [N][...]."""
+def pf_rhs(g: Grid, U: np.ndarray, Q: np.ndarray, dt_limit: float = 0.0) -> np.ndarray:
+    """dU/dt of the Phase-Field step (Eq. 5) for the auxiliary fields Q [N][...];
+    dt_limit > 0 limits the face gradients for that time step (R17)."""
     U = np.ascontiguousarray(U, dtype=np.float64)
     Q = np.ascontiguousarray(Q, dtype=np.float64)
     L = np.empty_like(U)
-    _check(lib().or_pf_rhs(g.ref(), _p(U), _p(Q), _p(L)), "or_pf_rhs")
+    _check(lib().or_pf_rhs(g.ref(), _p(U), _p(Q), float(dt_limit), _p(L)), "or_pf_rhs")
     return L
 
 

@@ -42,7 +42,9 @@
  *  R10 Time step dt = CFL / max_cells sum_d (|u_d| + c) / dx_d, taken from U^n.
  *  R12 Phase-Field flux of Eq. 5 (its numerical form is not printed in the
  *      paper; parity unpinned beyond its invariants).  Given Q_p at cells,
- *      G_p = (Q_{p,R} - Q_{p,L})/dx at the face; with J_p = phi_p(1-phi_p)
+ *      G_p = (Q_{p,R} - Q_{p,L})/dx at the face (0 on a face where both
+ *      cells have phi_p (1 - phi_p) <= 0: Eq. 4 does not couple it, R17);
+ *      with J_p = phi_p(1-phi_p)
  *      grad Q_p (implied by Eq. 4) discretised bound-preservingly as
  *      J_p = max(G_p,0) a_R (1 - a_L) + min(G_p,0) a_L (1 - a_R), the mass flux
  *      is the same with (alpha rho) in the outgoing factor, then
@@ -78,9 +80,9 @@
  *      negative average, and Eq. 18 on a negative average (theta = 0) taken
  *      into Eq. 20's minimum over phases drops the whole cell to first order.
  *      Such residues are set to the bound: scaled face masses and fractions
- *      below 0 become 0, and stage results outside the bounds by at most
- *      2^-48 of their scale (the cell's density before the stage for a
- *      mass, 1 for a fraction) become the bound.  A larger excursion is not
+ *      below 0 become 0 when the cell average is non-negative, and stage
+ *      results outside the bounds by at most 2^-48 of the magnitudes of the
+ *      stage sum's terms become the bound.  A larger excursion is not
  *      rounding: at a time step above the sufficient CFL bound of Sec. 4.2
  *      (the paper's own tests run so) the scheme itself can leave the bounds
  *      slightly; that value stays, the next limiter (theta = 0 on a negative
@@ -726,8 +728,9 @@ void or_pf_flux(const or_grid *g, int dir, const double *UL, const double *VL, c
   (void)dir;
 }
 
-/* dU/dt of the Phase-Field step (Eq. 5) for Q [N][cells]: +sum_d dF^PF/dx_d. */
-int or_pf_rhs(const or_grid *g, const double *U, const double *Q, double *L);
+/* dU/dt of the Phase-Field step (Eq. 5) for Q [N][cells]: +sum_d dF^PF/dx_d;
+ * dt_limit > 0 limits the face gradients for that time step (R17). */
+int or_pf_rhs(const or_grid *g, const double *U, const double *Q, double dt_limit, double *L);
 
 static int check_grid(const or_grid *g) {
   if (g->dim < 1 || g->dim > 3 || g->N < 1 || g->N > OR_MAXP) return OR_ERR_ARG;
@@ -754,7 +757,7 @@ int or_rhs(const or_grid *g, const double *U, double *L) {
   return OR_OK;
 }
 
-int or_pf_rhs(const or_grid *g, const double *U, const double *Q, double *L) {
+int or_pf_rhs(const or_grid *g, const double *U, const double *Q, double dt_limit, double *L) {
   int e = check_grid(g);
   if (e) return e;
   int nvar = nv(g), N = g->N;
@@ -782,8 +785,23 @@ int or_pf_rhs(const or_grid *g, const double *U, const double *Q, double *L) {
         int jl = bc_map(m - 1, n, g->bc[2 * dir], g->bc[2 * dir + 1], &f1);
         int jr = bc_map(m, n, g->bc[2 * dir], g->bc[2 * dir + 1], &f2);
         double G[OR_MAXP];
-        for (int p = 0; p < N; p++)
-          G[p] = (Q[(long)p * nc + base + jr * stride] - Q[(long)p * nc + base + jl * stride]) / dx;
+        for (int p = 0; p < N; p++) {
+          /* R17: G = 0 on a face that Eq. 4 does not couple, c_f = 0 (both
+           * cells with phi (1 - phi) <= 0) */
+          double al = U[(long)IALF(g, p) * nc + base + jl * stride];
+          double ar = U[(long)IALF(g, p) * nc + base + jr * stride];
+          int coupled = al * (1.0 - al) > 0.0 || ar * (1.0 - ar) > 0.0;
+          G[p] = coupled ? (Q[(long)p * nc + base + jr * stride] -
+                            Q[(long)p * nc + base + jl * stride]) / dx
+                         : 0.0;
+          /* R17: |G| <= dx / (12 d dt), the Phase-Field step's sufficient
+           * condition for bounds with R12's flux */
+          if (dt_limit > 0.0) {
+            double gmax = dx / (12.0 * g->dim * dt_limit);
+            if (G[p] > gmax) G[p] = gmax;
+            if (G[p] < -gmax) G[p] = -gmax;
+          }
+        }
         or_pf_flux(g, dir, FLs + m * nvar, VLs + m * nvar, FRs + (m + 1) * nvar,
                    VRs + (m + 1) * nvar, G, Fx + m * nvar);
       }
@@ -922,30 +940,30 @@ int or_max_rate(const or_grid *g, const double *U, double *rate) {
   return OR_OK;
 }
 
-/* R13: stage results outside the bounds by no more than the rounding of the
- * stage sum -- 2^-48 of the scale, the cell's density before the stage for a
- * mass and 1 for a fraction -- are set to the bound.  Larger excursions (a
- * time step above the sufficient CFL bound of Sec. 4.2) are the scheme's
- * own and stay; the limiter of the next stage treats them (Eq. 18, theta = 0
- * on a negative average).  R16: no bound is restored without Eq. 17-20. */
+/* One Runge-Kutta stage, out = a U0 + b U1 + c dt L, element by element.
+ * R13: a mass or fraction of the result outside its bound (0; 1 for a
+ * fraction) by no more than the rounding of this sum, 2^-48 of the sum of
+ * the terms' magnitudes, is set to the bound.  A larger excursion (a time
+ * step above the sufficient CFL bound of Sec. 4.2) is the scheme's own and
+ * stays; the limiter of the next stage treats it (Eq. 18: theta = 0 on a
+ * negative average).  A mass and a fraction of one phase have terms in the
+ * ratio rho_p, so they are kept or clamped together.  R16: no bound is
+ * restored without Eq. 17-20. */
 #define OR_STAGE_TOL 0x1p-48
-static void cell_density(const or_grid *g, const double *U, double *rho) {
-  long n = ncells(g);
-  for (long c = 0; c < n; c++) rho[c] = 0.0;
-  for (int p = 0; p < g->N; p++)
-    for (long c = 0; c < n; c++) rho[c] += U[(long)IMASS(p) * n + c];
-}
-
-static void stage_bounds(const or_grid *g, const double *rho_in, double *U) {
-  if (!g->limiter) return;
-  long n = ncells(g);
-  for (int p = 0; p < g->N; p++) {
-    double *m = U + (long)IMASS(p) * n, *a = U + (long)IALF(g, p) * n;
-    for (long c = 0; c < n; c++) {
-      if (m[c] < 0.0 && m[c] >= -OR_STAGE_TOL * rho_in[c]) m[c] = 0.0;
-      if (a[c] < 0.0 && a[c] >= -OR_STAGE_TOL) a[c] = 0.0;
-      if (a[c] > 1.0 && a[c] <= 1.0 + OR_STAGE_TOL) a[c] = 1.0;
+static void rk_stage(const or_grid *g, double a, const double *U0, double b, const double *U1,
+                     double c, double dt, const double *L, double *out) {
+  long n = ncells(g), tot = n * nv(g);
+  for (long k = 0; k < tot; k++) {
+    double t0 = a * U0[k], t1 = b * U1[k], t2 = c * dt * L[k];
+    double x = t0 + t1 + t2;
+    int v = (int)(k / n);
+    int bounded = g->limiter && (v < g->N || v >= IALF(g, 0));
+    if (bounded) {
+      double tol = OR_STAGE_TOL * (fabs(t0) + fabs(t1) + fabs(t2));
+      if (x < 0.0 && -x <= tol) x = 0.0;
+      if (v >= IALF(g, 0) && x > 1.0 && x - 1.0 <= tol) x = 1.0;
     }
+    out[k] = x;
   }
 }
 
@@ -963,28 +981,19 @@ int or_rk3_step(const or_grid *g, double *U, double cfl, double dt_fixed, double
     dt = cfl / rate;
   }
   double *U0 = malloc(sizeof(double) * tot), *U1 = malloc(sizeof(double) * tot);
-  double *L = malloc(sizeof(double) * tot), *rho = malloc(sizeof(double) * ncells(g));
+  double *L = malloc(sizeof(double) * tot);
   memcpy(U0, U, sizeof(double) * tot);
   e = or_rhs(g, U0, L);
   if (!e) {
-    cell_density(g, U0, rho);
-    for (long k = 0; k < tot; k++) U1[k] = U0[k] + dt * L[k];
-    stage_bounds(g, rho, U1);
+    rk_stage(g, 1.0, U0, 0.0, U0, 1.0, dt, L, U1);
     e = or_rhs(g, U1, L);
   }
   if (!e) {
-    cell_density(g, U1, rho);
-    for (long k = 0; k < tot; k++) U1[k] = 0.75 * U0[k] + 0.25 * U1[k] + 0.25 * dt * L[k];
-    stage_bounds(g, rho, U1);
+    rk_stage(g, 0.75, U0, 0.25, U1, 0.25, dt, L, U1);
     e = or_rhs(g, U1, L);
   }
-  if (!e) {
-    cell_density(g, U1, rho);
-    for (long k = 0; k < tot; k++)
-      U[k] = 1.0 / 3.0 * U0[k] + 2.0 / 3.0 * U1[k] + 2.0 / 3.0 * dt * L[k];
-    stage_bounds(g, rho, U);
-  }
-  free(U0); free(U1); free(L); free(rho);
+  if (!e) rk_stage(g, 1.0 / 3.0, U0, 2.0 / 3.0, U1, 2.0 / 3.0, dt, L, U);
+  free(U0); free(U1); free(L);
   if (dt_used) *dt_used = dt;
   return e;
 }
