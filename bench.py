@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--n3d", type=int, default=256, help="edge of the 3-D training source")
     ap.add_argument("--n5", type=int, default=2048, help="edge of the 2-D circles workload")
     ap.add_argument("--steps5", type=int, default=20)
+    ap.add_argument("--n-adv", type=int, default=2048,
+                    help="edge of the Sec. 4.1.1 advection grid that times the scheme variants")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the scheme variants (WENO-CL, WENO-W, WENO-JS, Kapila)")
     ap.add_argument("--profile", action="store_true",
                     help="only the FP64 timed steps (a short run for profilers); prints the "
                          "per-launch sweep time")
@@ -282,10 +286,10 @@ def run_ours(args):
     learned = not (args.no_learned or args.profile)
     S, train_info = train_surrogate(args, dev) if learned else (None, None)
 
-    def make_grid(precision, c=None, counters=None):
+    def make_grid(precision, c=None, counters=None, scheme="c", kmodel="allaire"):
         c = c or case
         g = wenoc.Grid(c.shape, c.dx, c.gamma, c.pinf, c.D, flux=c.flux, bc=c.bc,
-                       precision=precision)
+                       precision=precision, scheme=scheme, kmodel=kmodel)
         if precision == "learned":
             g.set_mlp(S.params, tau=args.tau, counters=counters)
         V = torch.from_numpy(c.V).to(dev)
@@ -296,14 +300,15 @@ def run_ours(args):
     # L2 flush buffer (larger than the 126 MB L2), written between timed steps
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
-    def timed_steps(g, K, W, c=None):
+    def timed_steps(g, K, W, c=None, dt=0.0):
         """K timed RK steps (events per step, L2 flushed in between) and the
         mean duration of the sweep launches inside them (event pairs the
         library records around each direction's launches on the same
-        stream: the sweep, preceded in learned precision by the surrogate)."""
+        stream: the sweep, preceded in learned precision by the surrogate).
+        dt > 0: fixed time step, else from the CFL number on the device."""
         c = c or case
         for _ in range(W):
-            g.rk_step(cfl=c.cfl)
+            g.rk_step(cfl=c.cfl, dt=dt)
         barrier()
         s = torch.cuda.current_stream()
         evs = []
@@ -312,7 +317,7 @@ def run_ours(args):
             flush.fill_(1.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)
-            g.rk_step(cfl=c.cfl)
+            g.rk_step(cfl=c.cfl, dt=dt)
             e1.record(s)
             evs.append((e0, e1))
         barrier()
@@ -367,6 +372,7 @@ def run_ours(args):
             infer_ms = e0.elapsed_time(e1) / 10
             infer_rows = 2 * g.ncell
             del g, U, W5
+        variants = run_variants(args, rank, make_grid, timed_steps)
     clocks = clk.summary()
     # FP64 peak from unit counts and clock: 2 DFMA per clock per SM (ncu's
     # sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained = 296 per
@@ -487,6 +493,8 @@ def run_ours(args):
             "workload": f"circles_shock_2d {args.n5}x{args.n5} N=3 HLL CFL 0.2 outflow "
                         "(64 circles, radii 10-80 cells, shock ratio 1e3, seeded)",
             "steps": args.steps5, "l1_steps": args.steps5, "modes": w5}
+    if variants:
+        line["scheme_variants"] = variants
     if rank == 0 and not args.no_cpu_baseline:
         try:
             small = make_case(args, 0)
@@ -500,6 +508,41 @@ def run_ours(args):
     if ws > 1:
         tdist.destroy_process_group()
     return 0
+
+
+def run_variants(args, rank, make_grid, timed_steps):
+    """The scheme variants, each on its own workload, FP64, same timing as the
+    headline: WENO-C, WENO-CL and the WENO-W / WENO-JS comparison schemes on
+    the Sec. 4.1.1 air-circle advection (n^2, dt = 0.1 n^-1, the paper's
+    1e-3 at n = 100) with the consistency error after the run; the Kapila
+    model on the headline shock-bubble."""
+    if args.no_variants or rank != 0:
+        return None
+    from paper_2608_00746_b300 import inputs
+    out = {}
+    cA = inputs.two_phase_advection_2d(n=args.n_adv)
+    dtA = 0.1 / args.n_adv
+    cells = args.n_adv ** 2
+    rho1 = cA.meta["rho"][0]
+    adv = {"workload": f"two_phase_advection_2d {args.n_adv}x{args.n_adv} N=2 HLLC periodic "
+                       f"dt {dtA:.3g} (Sec. 4.1.1 layout)", "steps": args.steps}
+    for scheme in ("c", "cl", "w", "js"):
+        g, U = make_grid("fp64", cA, scheme=scheme)
+        ms, sw = timed_steps(g, args.steps, 3, cA, dt=dtA)
+        cons = (U[0] / rho1 - U[5]).abs().max().item()
+        adv[scheme] = {"value": round(cells * 3 / (ms * 1e-3) / 1e6, 3),
+                       "ms_per_step": round(ms, 4), "ms_per_direction": round(sw, 4),
+                       "consistency_error_max": cons}
+        del g, U
+    out["advection"] = adv
+    g, U = make_grid("fp64", kmodel="kapila")
+    ms, sw = timed_steps(g, args.steps, 3)
+    cells_h = int(np.prod(g.shape))
+    out["kapila"] = {"workload": "headline shock-bubble, K_p of the Kapila model",
+                     "value": round(cells_h * 3 / (ms * 1e-3) / 1e6, 3),
+                     "ms_per_step": round(ms, 4), "ms_per_direction": round(sw, 4)}
+    del g, U
+    return out
 
 
 def run_profile_mlp(args):

@@ -53,7 +53,7 @@ typedef enum {
 enum { WC_BC_PERIODIC = 0, WC_BC_REFLECTIVE = 1, WC_BC_OUTFLOW = 2 };
 enum { WC_FLUX_HLL = 0, WC_FLUX_HLLC = 1 };
 enum { WC_PREC_FP64 = 0, WC_PREC_MIXED = 1, WC_PREC_LEARNED = 2 };
-enum { WC_SCHEME_C = 0, WC_SCHEME_CL = 1 };
+enum { WC_SCHEME_C = 0, WC_SCHEME_CL = 1, WC_SCHEME_W = 2, WC_SCHEME_JS = 3 };
 enum { WC_KMODEL_ALLAIRE = 0, WC_KMODEL_KAPILA = 1 };
 
 /* Grid, materials and scheme options.  Materials follow the stiffened-gas
@@ -90,12 +90,22 @@ typedef struct {
   int blocks_per_sm;          /* resident sweep blocks per SM (1..4); 0 = automatic */
   int scheme;                 /* WC_SCHEME_C: unity sum by Eq. 19 (WENO-C,
                                  default); WC_SCHEME_CL: the consistent limiter
-                                 of Eq. 23-25 instead (WENO-CL, Sec. 3.4) */
+                                 of Eq. 23-25 instead (WENO-CL, Sec. 3.4);
+                                 the comparison schemes of Sec. 4.1.1,
+                                 WC_SCHEME_W (Eq. 15 weights) and
+                                 WC_SCHEME_JS (Jiang-Shu weights with js_eps):
+                                 every primitive variable with its own
+                                 weights, no coupling (Eq. 16), no limiters
+                                 (Eq. 17-21; energy_limiter is ignored) and
+                                 no bound restored after a stage; FP64
+                                 only (WC_ERR_UNSUPPORTED otherwise) */
   int kmodel;                 /* K_p of Eq. 2-3: WC_KMODEL_ALLAIRE (K_p = 0,
                                  default) or WC_KMODEL_KAPILA (K_p = rho c^2 /
                                  (rho_p c_p^2) - 1 with Wood's mixture speed
                                  1/(rho c^2) = sum_p alpha_p/(rho_p c_p^2),
                                  which sum_p alpha_p K_p = 0 implies) */
+  double js_eps;              /* epsilon of WC_SCHEME_JS (> 0; 0 = 1e-6, the
+                                 value of Sec. 3.2) */
 } wc_grid_desc;
 
 typedef struct wc_grid wc_grid;
@@ -136,16 +146,19 @@ wc_status wc_cons_to_prim(const wc_grid *g, const double *U_dev, double *V_dev, 
 wc_status wc_rhs(wc_grid *g, const double *U_dev, double *L_dev, void *stream);
 
 /* L = dU/dt of the Phase-Field step (Eq. 5), + div F^PF, for the state U_dev
- * and the auxiliary fields Q_dev [N][ncell] of Eq. 4 (given; the Q-map solve
- * is not part of this library).  Face gradients are central differences of
- * Q; the face states are the WENO-C reconstructions of U.  The numerical
- * flux (not printed in the paper, which cites it) is the bound-preserving
- * upwinding J_p = max(G,0) a_R (1-a_L) + min(G,0) a_L (1-a_R) of
- * phi_p (1 - phi_p) grad Q_p, masses alike with (alpha rho)_p in the outgoing
- * factor, corrected to sum_p J_p = 0 in proportion to the face fractions;
- * momentum and energy as in the last line of Eq. 1. */
-wc_status wc_rhs_pf(wc_grid *g, const double *U_dev, const double *Q_dev, double *L_dev,
-                    void *stream);
+ * and the auxiliary fields Q_dev [N][ncell] of Eq. 4 (wc_qmap computes them).
+ * Face gradients G are central differences of Q, zero on a face where both
+ * cells have phi_p (1 - phi_p) <= 0 (Eq. 4 does not couple it), and, when
+ * dt_limit > 0, limited to |G| <= dx / (12 d dt_limit) (the Phase-Field
+ * step's sufficient condition for bounds at that time step); dt_limit = 0:
+ * no limit.  The face states are the WENO-C reconstructions of U.  The
+ * numerical flux (not printed in the paper, which cites it) is the
+ * bound-preserving upwinding J_p = max(G,0) a_R (1-a_L) + min(G,0) a_L (1-a_R)
+ * of phi_p (1 - phi_p) grad Q_p, masses alike with (alpha rho)_p in the
+ * outgoing factor, corrected to sum_p J_p = 0 in proportion to the face
+ * fractions; momentum and energy as in the last line of Eq. 1. */
+wc_status wc_rhs_pf(wc_grid *g, const double *U_dev, const double *Q_dev, double dt_limit,
+                    double *L_dev, void *stream);
 
 /* Time step from the bound state: dt = cfl / max_cells sum_d (|u_d| + c)/dx_d,
  * written to dt_dev (one double, device). */

@@ -103,13 +103,18 @@ extern "C" wc_status wc_init_grid(const wc_grid_desc* desc, wc_grid** out) {
   if (d.precision == WC_PREC_LEARNED && d.nphase > 3) return WC_ERR_UNSUPPORTED;
   if (d.seg < 0 || d.block < 0 || d.block > 128 || (d.block % 32) != 0) return WC_ERR_ARG;
   if (d.blocks_per_sm < 0 || d.blocks_per_sm > 4) return WC_ERR_ARG;
-  if (d.scheme != WC_SCHEME_C && d.scheme != WC_SCHEME_CL) return WC_ERR_ARG;
+  if (d.scheme < WC_SCHEME_C || d.scheme > WC_SCHEME_JS) return WC_ERR_ARG;
+  const bool comparison = d.scheme == WC_SCHEME_W || d.scheme == WC_SCHEME_JS;
+  if (comparison && d.precision != WC_PREC_FP64) return WC_ERR_UNSUPPORTED;
+  if (d.scheme == WC_SCHEME_JS && d.js_eps < 0.0) return WC_ERR_ARG;
   if (d.kmodel != WC_KMODEL_ALLAIRE && d.kmodel != WC_KMODEL_KAPILA) return WC_ERR_ARG;
   for (int p = 0; p < d.nphase; p++)
     if (!(d.gamma[p] > 1.0) || !(d.pinf[p] >= 0.0)) return WC_ERR_ARG;
   wc_grid* g = new (std::nothrow) wc_grid();
   if (!g) return WC_ERR_ARG;
   g->d = d;
+  if (comparison) g->d.energy_limiter = 0;
+  if (d.scheme == WC_SCHEME_JS && !(d.js_eps > 0.0)) g->d.js_eps = 1e-6;
   g->nv = 2 * d.nphase + d.dim + 1;
   g->ncell = (long)d.n[0] * d.n[1] * d.n[2];
   Mat& m = g->mat;
@@ -117,6 +122,8 @@ extern "C" wc_status wc_init_grid(const wc_grid_desc* desc, wc_grid** out) {
   m.N = d.nphase;
   m.cl = d.scheme == WC_SCHEME_CL;
   m.kapila = d.kmodel == WC_KMODEL_KAPILA;
+  m.cmp = d.scheme == WC_SCHEME_W ? CMP_W : (d.scheme == WC_SCHEME_JS ? CMP_JS : CMP_NONE);
+  m.js_eps = g->d.js_eps;
   for (int p = 0; p < d.nphase; p++) {
     m.A[p] = 1.0 / (d.gamma[p] - 1.0);
     m.B[p] = d.gamma[p] * d.pinf[p] / (d.gamma[p] - 1.0);
@@ -299,7 +306,9 @@ static cudaError_t launch(const wc_grid* gc, const SweepArgs& a0, cudaStream_t s
       a.lcount = g->lcount;
       e = launch_sweep_learned(g->d.nphase, g->d.dim, a, g->mat, sweep_block(g), st);
     }
-  } else if (g->d.precision == WC_PREC_MIXED)
+  } else if (g->mat.cmp != CMP_NONE)
+    e = launch_sweep_compare(g->d.nphase, g->d.dim, a, g->mat, sweep_block(g), st);
+  else if (g->d.precision == WC_PREC_MIXED)
     e = launch_sweep_mixed(g->d.nphase, g->d.dim, a, g->mat, sweep_block(g), st);
   else
     e = launch_sweep_fp64(g->d.nphase, g->d.dim, a, g->mat, sweep_block(g), st);
@@ -361,15 +370,16 @@ extern "C" wc_status wc_rhs(wc_grid* g, const double* U, double* L, void* stream
   return WC_OK;
 }
 
-extern "C" wc_status wc_rhs_pf(wc_grid* g, const double* U, const double* Q, double* L,
-                               void* stream) {
-  if (!g || !U || !Q || !L) return WC_ERR_ARG;
+extern "C" wc_status wc_rhs_pf(wc_grid* g, const double* U, const double* Q, double dt_limit,
+                               double* L, void* stream) {
+  if (!g || !U || !Q || !L || dt_limit < 0.0) return WC_ERR_ARG;
   if (!g->status) return fail(g, WC_ERR_STATE, "wc_rhs_pf needs a bound workspace (status word)");
   for (int dir = 0; dir < g->d.dim; dir++) {
     SweepArgs a = make_args(g, dir, U, L);
     a.mode = dir == 0 ? 0 : 1;
     a.kind = 1;
     a.Q = Q;
+    a.gmax = dt_limit > 0.0 ? g->d.dx[dir] / (12.0 * g->d.dim * dt_limit) : 0.0;
     cudaError_t e = launch(g, a, S(stream));
     if (e != cudaSuccess) return cuda_fail(g, e, "pf sweep");
   }

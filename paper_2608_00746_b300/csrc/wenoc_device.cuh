@@ -33,7 +33,14 @@ struct Mat {
   int cl;                   // 1: WENO-CL (Eq. 23-25 instead of Eq. 19)
   int kapila;               // K_p of Eq. 2-3: 0 Allaire (K_p = 0), 1 Kapila (Wood speed)
   double gam[MAXP];         // gamma_p
+  int cmp;                  // CMP_NONE, or a comparison scheme without Eq. 16-21
+  double js_eps;            // epsilon of the WENO-JS comparison
 };
+
+// Comparison schemes (Sec. 3.2, Sec. 4.1.1): every primitive variable with
+// its own weights, no coupling (Eq. 16) and no limiters (Eq. 17-21); run by
+// the sweep variant V = 2.
+enum : int { CMP_NONE = 0, CMP_W = 1, CMP_JS = 2 };
 
 template <int N, int D>
 struct Idx {
@@ -368,6 +375,43 @@ __device__ __forceinline__ W6<T> weights_of(const Stencil<T>& st) {
   return w;
 }
 
+// Comparison weights (Sec. 3.2, the fifth-order form of Eq. 12): omega_s
+// proportional to d_s / (IS_s + eps)^2 with the Jiang-Shu indicators IS_s =
+// (13/12) b_s.  Each term is taken relative to the smallest IS_k + eps, so it
+// lies in (0, d_s] whatever the scale of f (the normalised weights are the
+// same).
+template <typename T>
+__device__ __forceinline__ W6<T> weights_js(const Stencil<T>& st, T eps) {
+  T b0, b1, b2;
+  smoothness(st, b0, b1, b2);
+  const T k = T(13) / T(12);
+  const T e0 = fma(k, b0, eps), e1 = fma(k, b1, eps), e2 = fma(k, b2, eps);
+  const T mn = fmin(e0, fmin(e1, e2));
+  const T r0 = mn / e0, r1 = mn / e1, r2 = mn / e2;
+  const T q0 = r0 * r0, q1 = r1 * r1, q2 = r2 * r2;
+  const T sixth = T(1) / T(6);
+  W6<T> w;
+  w.aL0 = T(0.1) * q0;
+  w.aL1 = T(0.6) * q1;
+  w.aL2 = T(0.3) * q2;
+  w.aR0 = T(0.1) * q2;
+  w.aR1 = T(0.6) * q1;
+  w.aR2 = T(0.3) * q0;
+  w.invL = sixth / (w.aL0 + w.aL1 + w.aL2);
+  w.invR = sixth / (w.aR0 + w.aR1 + w.aR2);
+  return w;
+}
+
+// The weights of a sweep variant: Eq. 15, or for the comparison variant
+// (V = 2) the configured comparison scheme's.
+template <int V, typename T>
+__device__ __forceinline__ W6<T> sweep_weights(const Mat& m, const Stencil<T>& st) {
+  if constexpr (V == 2) {
+    if (m.cmp == CMP_JS) return weights_js<T>(st, T(m.js_eps));
+  }
+  return weights_of<T>(st);
+}
+
 // Eq. 10 at x_{i+1/2} (fL) and x_{i-1/2} (fR): the candidates' values minus
 // f_i, times 6, are 2da-7db, 2dd-db, 5dd-de (left face) and the mirror images.
 // The operations are written as explicit fused multiply-adds, so every
@@ -446,11 +490,32 @@ struct Face {
 // x_{i+1/2} (x_{i-1/2}); uL, PL (uR, PR) reconstructed velocity and pressure.
 // Produces the two limited face states.  th (optional) receives
 // (min_p theta_p of Eq. 17, theta_i of Eq. 20, theta^(psi) of Eq. 21).
-// Rounding residue below a bound: the limited face values of Eq. 18 / Eq. 20
-// and the updated cell masses and fractions are non-negative in exact
-// arithmetic, but theta (f - fbar) + fbar that should land on zero can land
-// an ulp below it.  x < 0 becomes 0; a NaN stays a NaN.
-__device__ __forceinline__ double nonneg(double x) { return x < 0.0 ? 0.0 : x; }
+// Rounding residue below a bound: with fbar >= 0 the limited face values
+// fbar + theta (f - fbar) of Eq. 18, Eq. 20, Eq. 21 and Eq. 25 are
+// non-negative in exact arithmetic, but a value that should land on zero can
+// land an ulp below it; it becomes 0.  With fbar < 0 (a stage that left the
+// bound, theta = 0) the value is fbar itself and stays.  A NaN stays a NaN.
+__device__ __forceinline__ double nonneg(double x, double fb) {
+  return x < 0.0 && fb >= 0.0 ? 0.0 : x;
+}
+
+// The same rule at the end of a Runge-Kutta stage x = t0 + t1 + t2: a mass
+// or fraction outside its bound (0; 1 for a fraction) by at most 2^-48 of
+// |t0| + |t1| + |t2| is rounding of the stage sum and becomes the bound; a
+// larger excursion (a time step above the sufficient CFL bound) stays for
+// the next limiter.  A phase's mass and fraction have terms in the ratio
+// rho_p, so they are kept or clamped together.
+constexpr double STAGE_TOL = 0x1p-48;
+__device__ __forceinline__ double stage_bound(double x, double t0, double t1, double t2,
+                                              bool frac) {
+  const bool lo = x < 0.0, hi = frac && x > 1.0;
+  if (lo || hi) {
+    const double tol = STAGE_TOL * (fabs(t0) + fabs(t1) + fabs(t2));
+    if (lo && -x <= tol) return 0.0;
+    if (hi && x - 1.0 <= tol) return 1.0;
+  }
+  return x;
+}
 
 // Eq. 23-25 (WENO-CL) on one face: S_p = alpha_p,face - alpha_p,bar (the
 // factor 2/dx of Eq. 24 cancels), p-hat the first phase of largest |S_p|,
@@ -491,32 +556,34 @@ __device__ __forceinline__ bool consistent_face(const double* Ub, double* mf, do
     const double th = is_ph ? tph : to;
     if (lt_nonneg(th, 1.0)) {
       const double mb = Ub[p], ab = Ub[I::A(p)];
-      mf[p] = nonneg(fma(th, mf[p] - mb, mb));
-      af[p] = nonneg(fma(th, af[p] - ab, ab));
+      mf[p] = nonneg(fma(th, mf[p] - mb, mb), mb);
+      af[p] = nonneg(fma(th, af[p] - ab, ab), ab);
       moved = true;
     }
   }
   return moved;
 }
 
-template <int N, int D>
+template <int N, int D, bool LIMIT = true>
 __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, double Pb,
                                             double* mL, double* aL, double* mR, double* aR,
                                             const double* uL, double PL, const double* uR,
                                             double PR, int energy_limiter, Face<N, D>& FL,
                                             Face<N, D>& FR, double* th) {
   using I = Idx<N, D>;
-  double th17 = 1.0;
+  double th17 = 1.0, thi = 1.0;
+  // (LIMIT = false, the comparison schemes: raw faces to the Riemann solver)
+  if constexpr (LIMIT) {
   // Eq. 17-18: common theta_p for (alpha rho)_p and alpha_p
 #pragma unroll
   for (int p = 0; p < N; p++) {
     double mb = Ub[p], ab = Ub[I::A(p)];
     double tp = min_nonneg(theta_pos(mb, mL[p], mR[p]), theta_pos(ab, aL[p], aR[p]));
     if (lt_nonneg(tp, 1.0)) {
-      mL[p] = nonneg(fma(tp, mL[p] - mb, mb));
-      mR[p] = nonneg(fma(tp, mR[p] - mb, mb));
-      aL[p] = nonneg(fma(tp, aL[p] - ab, ab));
-      aR[p] = nonneg(fma(tp, aR[p] - ab, ab));
+      mL[p] = nonneg(fma(tp, mL[p] - mb, mb), mb);
+      mR[p] = nonneg(fma(tp, mR[p] - mb, mb), mb);
+      aL[p] = nonneg(fma(tp, aL[p] - ab, ab), ab);
+      aR[p] = nonneg(fma(tp, aR[p] - ab, ab), ab);
       th17 = min_nonneg(th17, tp);
     }
   }
@@ -566,7 +633,6 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
   // Eq. 20: theta_i = min_p theta_p recomputed on the normalised faces (when
   // Eq. 17 and Eq. 19 left every face value unchanged, the recomputed thetas
   // are those of Eq. 17, all one)
-  double thi = 1.0;
   if (lt_nonneg(th17, 1.0) || cl_moved || dbits(SL) != dbits(1.0) ||
       dbits(SR) != dbits(1.0)) {
 #pragma unroll
@@ -580,11 +646,12 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
 #pragma unroll
     for (int p = 0; p < N; p++) {
       double mb = Ub[p], ab = Ub[I::A(p)];
-      mL[p] = nonneg(fma(thi, mL[p] - mb, mb));
-      mR[p] = nonneg(fma(thi, mR[p] - mb, mb));
-      aL[p] = nonneg(fma(thi, aL[p] - ab, ab));
-      aR[p] = nonneg(fma(thi, aR[p] - ab, ab));
+      mL[p] = nonneg(fma(thi, mL[p] - mb, mb), mb);
+      mR[p] = nonneg(fma(thi, mR[p] - mb, mb), mb);
+      aL[p] = nonneg(fma(thi, aL[p] - ab, ab), ab);
+      aR[p] = nonneg(fma(thi, aR[p] - ab, ab), ab);
     }
+  }
   }
   // V -> U at both faces
   double VL[I::NV], VR[I::NV];
@@ -628,8 +695,8 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
         FL.U[v] = fma(thpsi, FL.U[v] - Ub[v], Ub[v]);
         FR.U[v] = fma(thpsi, FR.U[v] - Ub[v], Ub[v]);
         if (v < N || v >= I::A(0)) {
-          FL.U[v] = nonneg(FL.U[v]);
-          FR.U[v] = nonneg(FR.U[v]);
+          FL.U[v] = nonneg(FL.U[v], Ub[v]);
+          FR.U[v] = nonneg(FR.U[v], Ub[v]);
         }
       }
       double W[I::NV];
@@ -916,6 +983,18 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
 // proportion to the face fractions (masses in proportion to the face
 // masses), which leaves an absent phase untouched.  Momentum and energy
 // follow the last line of Eq. 1 with the mean face velocity and pressure.
+// The face gradient of Q_p handed to the Phase-Field flux (Eq. 4-5, reading
+// R17): zero on a face Eq. 4 does not couple (both cells with
+// phi (1 - phi) <= 0), else (q_r - q_l)/dx limited to |G| <= gmax (gmax > 0,
+// the Phase-Field step's sufficient condition for bounds).
+__device__ __forceinline__ double pf_gradient(double ql, double qr, double al, double ar,
+                                              double inv_dx, double gmax) {
+  const bool coupled = al * (1.0 - al) > 0.0 || ar * (1.0 - ar) > 0.0;
+  double G = coupled ? (qr - ql) * inv_dx : 0.0;
+  if (gmax > 0.0) G = G > gmax ? gmax : (G < -gmax ? -gmax : G);
+  return G;
+}
+
 template <int N, int D>
 __device__ __forceinline__ void pf_flux(const Mat& m, const Face<N, D>& L, const Face<N, D>& R,
                                         const double* G, double* F) {

@@ -124,12 +124,14 @@ __global__ void k_limit(const double* __restrict__ Ub, const double* __restrict_
 }
 
 // Per-precision sweep dispatch (defined in wenoc_fp64.cu / wenoc_mixed.cu /
-// wenoc_learned.cu).
+// wenoc_learned.cu; the FP64 comparison schemes in wenoc_compare.cu).
 cudaError_t launch_sweep_fp64(int N, int D, const SweepArgs& a, const Mat& m, int block,
                               cudaStream_t st);
 cudaError_t launch_sweep_mixed(int N, int D, const SweepArgs& a, const Mat& m, int block,
                                cudaStream_t st);
 cudaError_t launch_sweep_learned(int N, int D, const SweepArgs& a, const Mat& m, int block,
+                                 cudaStream_t st);
+cudaError_t launch_sweep_compare(int N, int D, const SweepArgs& a, const Mat& m, int block,
                                  cudaStream_t st);
 int sweep_smem_bytes_fp64(int N, int D);
 int sweep_smem_bytes_mixed(int N, int D);

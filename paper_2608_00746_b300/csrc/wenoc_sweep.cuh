@@ -35,6 +35,7 @@ struct SweepArgs {
   int nseg, seg;       // segments per pencil, cells per segment
   long max_threads;    // launch size cap (whole blocks per SM); items loop beyond it
   const double* Q;     // Phase-Field auxiliary fields [N][ncell] (kind 1)
+  double gmax;         // kind 1: limit of |grad Q| on a face (0 = none)
   int kind;            // 0: hyperbolic step (Eq. 3); 1: Phase-Field step (Eq. 5)
   double inv_dx;
   int bclo, bchi;
@@ -94,7 +95,9 @@ struct Ring {
 // March through cells [s, e) of one pencil (first cell at index `base`,
 // step `a.stride`, `a.n` cells, boundary conditions a.bclo/a.bchi):
 // reconstruct, limit, solve the Riemann problems and update per a.mode.
-// `ring` is this thread's five-slot stencil ring in shared memory.
+// `ring` is this thread's five-slot stencil ring in shared memory.  Variant
+// LW: 0 the scheme (WENO-C / WENO-CL), 1 with learned mass weights, 2 the
+// comparison schemes (own weights per variable, no limiters, no stage bound).
 template <int N, int D, typename T, typename TF, int LW = 0>
 __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, long base, int s,
                                               int e, double* ring, double dt, unsigned& bad,
@@ -161,8 +164,8 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
 #pragma unroll
     for (int p = 0; p < N; p++) {
       Stencil<T> st = stencil<T>(V[0][p], V[1][p], V[2][p], V[3][p], V[4][p]);
-      W6<T> w = weights_of<T>(st);
-      if constexpr (LW != 0) {
+      W6<T> w = sweep_weights<LW, T>(m, st);
+      if constexpr (LW == 1) {
         // learned weights of an interior cell, accepted per face side when
         // the mass and the fraction reconstructed with them are each within
         // tau times their stencil's range of the plain reconstructions
@@ -215,15 +218,18 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
       }
       const int ia = I::A(p);
       const Stencil<T> sa = stencil<T>(V[0][ia], V[1][ia], V[2][ia], V[3][ia], V[4][ia]);
+      // (the comparison schemes: the fraction with its own weights)
+      W6<T> wa = w;
+      if constexpr (LW == 2) wa = sweep_weights<LW, T>(m, sa);
       if constexpr (OFFSET) {
         reconstruct_offset(w, st, Ub[p], mL[p], mR[p]);
-        reconstruct_offset(w, sa, Ub[ia], aL[p], aR[p]);
+        reconstruct_offset(wa, sa, Ub[ia], aL[p], aR[p]);
       } else {
         T fl, fr;
         reconstruct(w, st, fl, fr);
         mL[p] = double(fl);
         mR[p] = double(fr);
-        reconstruct(w, sa, fl, fr);
+        reconstruct(wa, sa, fl, fr);
         aL[p] = double(fl);
         aR[p] = double(fr);
       }
@@ -233,7 +239,7 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
 #pragma unroll
     for (int v = N; v <= N + D; v++) {
       Stencil<T> st = stencil<T>(V[0][v], V[1][v], V[2][v], V[3][v], V[4][v]);
-      W6<T> w = weights_of<T>(st);
+      W6<T> w = sweep_weights<LW, T>(m, st);
       // velocity and pressure in value form in every precision: a uniform
       // field (FP64 noise below the FP32 resolution) gives uniform faces
       T tl, tr;
@@ -248,7 +254,7 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
       }
     }
     Face<N, D> fL, fR;
-    limit_chain<N, D>(m, Ub, Pb, mL, aL, mR, aR, uL, PL, uR, PR, a.energy_limiter, fL, fR,
+    limit_chain<N, D, LW != 2>(m, Ub, Pb, mL, aL, mR, aR, uL, PL, uR, PR, a.energy_limiter, fL, fR,
                       nullptr);
     if (a.kind == 1) load_q(c, Qcur);
     if (c >= s) {
@@ -256,7 +262,8 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
       if (a.kind == 1) {
         double G[N];
 #pragma unroll
-        for (int p = 0; p < N; p++) G[p] = (Qcur[p] - Qprev[p]) * a.inv_dx;
+        for (int p = 0; p < N; p++)
+          G[p] = pf_gradient(Qprev[p], Qcur[p], Uprev[I::A(p)], Ub[I::A(p)], a.inv_dx, a.gmax);
         pf_flux<N, D>(m, prevL, fR, G, F);
       } else {
         riemann<N, D, TF>(m, a.dir, a.hllc, prevL, fR, F, uh);
@@ -279,11 +286,16 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
           } else {
             double Lt = a.mode == 2 ? a.L[idx] + val : val;
             double u0 = a.U0[idx];
-            double un = a.rk0 * u0 + a.rk1 * Uprev[v] + a.rk2 * dt * Lt;
-            // masses >= 0 and fractions in [0, 1] up to rounding: remove the
-            // residue (NaN passes through)
-            if (v < N || v >= I::A(0)) un = nonneg(un);
-            if (v >= I::A(0)) un = un > 1.0 ? 1.0 : un;
+            // (rounded term by term, without contraction)
+            const double t0 = __dmul_rn(a.rk0, u0), t1 = __dmul_rn(a.rk1, Uprev[v]),
+                         t2 = __dmul_rn(__dmul_rn(a.rk2, dt), Lt);
+            double un = __dadd_rn(__dadd_rn(t0, t1), t2);
+            // masses >= 0 and fractions in [0, 1] up to the rounding of the
+            // stage sum (not in the comparison schemes, which have no bounds)
+            if constexpr (LW != 2) {
+              if (v < N || v >= I::A(0))
+                un = stage_bound(un, t0, t1, t2, v >= I::A(0));
+            }
             a.Uout[idx] = un;
           }
         }
@@ -331,7 +343,7 @@ __global__ void __launch_bounds__(128) k_sweep(SweepArgs a, Mat m) {
     sweep_segment<N, D, T, TF, LW>(a, m, base, s, e, ring, dt, bad, lstat);
   }
   if (bad) atomicOr(a.status, bad);
-  if constexpr (LW != 0) {
+  if constexpr (LW == 1) {
     if (a.lcount) {
 #pragma unroll
       for (int k = 0; k < 2; k++) {

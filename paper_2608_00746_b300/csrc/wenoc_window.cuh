@@ -35,7 +35,8 @@ __device__ __forceinline__ void shfl_face_down(const Face<N, D>& f, Face<N, D>& 
 
 // One window: lane k owns cell c = c0 - 1 + k; slot s of `slots` holds the
 // primitive state of cell c0 - 3 + s (pressure in FP64, V in T).  Lanes
-// 1..30 update cells c0 .. c0 + 29 (those below a.n).
+// 1..30 update cells c0 .. c0 + 29 (those below a.n).  Variant LW as in
+// sweep_segment (0 scheme, 1 learned weights, 2 comparison schemes).
 template <int N, int D, typename T, typename TF, int LW>
 __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, long base, int c0,
                                              double* slots, double dt, unsigned& bad,
@@ -89,10 +90,10 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
 #pragma unroll
   for (int p = 0; p < N; p++) {
     Stencil<T> st = stencil<T>(V[0][p], V[1][p], V[2][p], V[3][p], V[4][p]);
-    W6<T> w = weights_of<T>(st);
+    W6<T> w = sweep_weights<LW, T>(m, st);
     const int ia = I::A(p);
     const Stencil<T> sa = stencil<T>(V[0][ia], V[1][ia], V[2][ia], V[3][ia], V[4][ia]);
-    if constexpr (LW != 0) {
+    if constexpr (LW == 1) {
       // learned weights of an interior cell, accepted per face side when the
       // mass and the fraction reconstructed with them are each within tau
       // times their stencil's range of the plain reconstructions (boundary
@@ -140,15 +141,18 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
         }
       }
     }
+    // (the comparison schemes: the fraction with its own weights)
+    W6<T> wa = w;
+    if constexpr (LW == 2) wa = sweep_weights<LW, T>(m, sa);
     if constexpr (OFFSET) {
       reconstruct_offset(w, st, Ub[p], mL[p], mR[p]);
-      reconstruct_offset(w, sa, Ub[ia], aL[p], aR[p]);
+      reconstruct_offset(wa, sa, Ub[ia], aL[p], aR[p]);
     } else {
       T fl, fr;
       reconstruct(w, st, fl, fr);
       mL[p] = double(fl);
       mR[p] = double(fr);
-      reconstruct(w, sa, fl, fr);
+      reconstruct(wa, sa, fl, fr);
       aL[p] = double(fl);
       aR[p] = double(fr);
     }
@@ -158,7 +162,7 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
 #pragma unroll
   for (int v = N; v <= N + D; v++) {
     Stencil<T> st = stencil<T>(V[0][v], V[1][v], V[2][v], V[3][v], V[4][v]);
-    W6<T> w = weights_of<T>(st);
+    W6<T> w = sweep_weights<LW, T>(m, st);
     // velocity and pressure in value form in every precision: a uniform
     // field (FP64 noise below the FP32 resolution) gives uniform faces
     T tl, tr;
@@ -173,7 +177,7 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
     }
   }
   Face<N, D> fL, fR;
-  limit_chain<N, D>(m, Ub, Pb, mL, aL, mR, aR, uL, PL, uR, PR, a.energy_limiter, fL, fR,
+  limit_chain<N, D, LW != 2>(m, Ub, Pb, mL, aL, mR, aR, uL, PL, uR, PR, a.energy_limiter, fL, fR,
                     nullptr);
   // the face x_{c+1/2}: this lane's fL and the right neighbour's fR
   Face<N, D> fRn;
@@ -186,7 +190,11 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
 #pragma unroll
     for (int p = 0; p < N; p++) q[p] = __ldg(a.Q + (long)p * a.ncell + cell);
 #pragma unroll
-    for (int p = 0; p < N; p++) G[p] = (__shfl_down_sync(0xffffffffu, q[p], 1) - q[p]) * a.inv_dx;
+    for (int p = 0; p < N; p++) {
+      const double qn = __shfl_down_sync(0xffffffffu, q[p], 1);
+      const double an = __shfl_down_sync(0xffffffffu, Ub[I::A(p)], 1);
+      G[p] = pf_gradient(q[p], qn, Ub[I::A(p)], an, a.inv_dx, a.gmax);
+    }
     pf_flux<N, D>(m, fL, fRn, G, F);
   } else {
     riemann<N, D, TF>(m, a.dir, a.hllc, fL, fRn, F, uh);
@@ -215,11 +223,16 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
         a.L[idx] += val;
       } else {
         const double Lt = a.mode == 2 ? a.L[idx] + val : val;
-        double un = a.rk0 * a.U0[idx] + a.rk1 * Ub[v] + a.rk2 * dt * Lt;
-        // masses >= 0 and fractions in [0, 1] up to rounding: remove the
-        // residue (NaN passes through)
-        if (v < N || v >= I::A(0)) un = nonneg(un);
-        if (v >= I::A(0)) un = un > 1.0 ? 1.0 : un;
+        // (rounded term by term, without contraction)
+        const double t0 = __dmul_rn(a.rk0, a.U0[idx]), t1 = __dmul_rn(a.rk1, Ub[v]),
+                     t2 = __dmul_rn(__dmul_rn(a.rk2, dt), Lt);
+        double un = __dadd_rn(__dadd_rn(t0, t1), t2);
+        // masses >= 0 and fractions in [0, 1] up to the rounding of the
+        // stage sum (not in the comparison schemes, which have no bounds)
+        if constexpr (LW != 2) {
+          if (v < N || v >= I::A(0))
+            un = stage_bound(un, t0, t1, t2, v >= I::A(0));
+        }
         a.Uout[idx] = un;
       }
     }
@@ -262,7 +275,7 @@ __global__ void __launch_bounds__(128) k_sweep_win(SweepArgs a, Mat m) {
     }
   }
   if (bad) atomicOr(a.status, bad);
-  if constexpr (LW != 0) {
+  if constexpr (LW == 1) {
     if (a.lcount) {
 #pragma unroll
       for (int k = 0; k < 2; k++) {

@@ -19,7 +19,7 @@ MAX_PHASE = 8
 BC = {"periodic": 0, "reflective": 1, "outflow": 2}
 FLUX = {"hll": 0, "hllc": 1}
 PREC = {"fp64": 0, "mixed": 1, "learned": 2}
-SCHEME = {"c": 0, "cl": 1}
+SCHEME = {"c": 0, "cl": 1, "w": 2, "js": 3}
 KMODEL = {"allaire": 0, "kapila": 1}
 STATUS = {0: "WC_OK", 1: "WC_ERR_ARG", 2: "WC_ERR_CUDA", 3: "WC_ERR_INADMISSIBLE",
           4: "WC_ERR_NAN", 5: "WC_ERR_UNSUPPORTED", 6: "WC_ERR_STATE", 7: "WC_ERR_TIMEOUT"}
@@ -50,6 +50,7 @@ class GridDesc(ctypes.Structure):
         ("blocks_per_sm", ctypes.c_int),
         ("scheme", ctypes.c_int),
         ("kmodel", ctypes.c_int),
+        ("js_eps", ctypes.c_double),
     ]
 
 
@@ -82,7 +83,7 @@ _SIGS = {
     "wc_cons_to_prim": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "wc_rhs": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "wc_compute_dt": (ctypes.c_int, [_VP, ctypes.c_double, _VP, _VP]),
-    "wc_rhs_pf": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "wc_rhs_pf": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, _VP, _VP]),
     "wc_rk_step": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_double), _VP]),
     "wc_limit": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_long, _VP, _VP, _VP, _VP, _VP, _VP,
@@ -186,7 +187,7 @@ class Grid:
 
     def __init__(self, shape, dx, gamma, pinf, D=None, pmin=None, flux="hll",
                  bc=("periodic",) * 6, precision="fp64", energy_limiter=True, seg=0, block=0,
-                 blocks_per_sm=0, scheme="c", kmodel="allaire"):
+                 blocks_per_sm=0, scheme="c", kmodel="allaire", js_eps=1e-6):
         N = len(gamma)
         d = GridDesc()
         d.dim = len(shape)
@@ -208,6 +209,7 @@ class Grid:
         d.blocks_per_sm = int(blocks_per_sm)
         d.scheme = SCHEME[scheme]
         d.kmodel = KMODEL[kmodel]
+        d.js_eps = float(js_eps)
         self.desc = d
         self.shape = tuple(shape)
         h = _VP()
@@ -268,10 +270,12 @@ class Grid:
         self._check(lib().wc_rhs(self.h, _ptr(U), _ptr(L), _stream(stream)))
         return L
 
-    def rhs_pf(self, U, Q, L=None, stream=None):
-        """Phase-Field step operator (Eq. 5) for auxiliary fields Q [N][...]."""
+    def rhs_pf(self, U, Q, L=None, dt_limit=0.0, stream=None):
+        """Phase-Field step operator (Eq. 5) for auxiliary fields Q [N][...];
+        dt_limit > 0 limits the face gradients for that time step."""
         L = torch.empty_like(U) if L is None else L
-        self._check(lib().wc_rhs_pf(self.h, _ptr(U), _ptr(Q), _ptr(L), _stream(stream)))
+        self._check(lib().wc_rhs_pf(self.h, _ptr(U), _ptr(Q), float(dt_limit), _ptr(L),
+                                    _stream(stream)))
         return L
 
     def compute_dt(self, cfl, out=None, stream=None):

@@ -47,6 +47,9 @@ def desc(**kw):
     d.energy_limiter = 1
     for k in range(6):
         d.bc[k] = kw.get("bc", 0)
+    d.scheme = kw.get("scheme", 0)
+    d.kmodel = kw.get("kmodel", 0)
+    d.js_eps = kw.get("js_eps", 0.0)
     return d
 
 
@@ -72,10 +75,18 @@ def test_init_grid_accepts_valid_and_sizes():
 @pytest.mark.parametrize("bad,status", [
     (dict(dim=4), 1), (dict(nphase=0), 5), (dict(nphase=6), 5),
     (dict(n=(2, 8, 1)), 1), (dict(n=(16, 8, 2)), 1), (dict(flux=7), 1),
-    (dict(precision=9), 5), (dict(bc=5), 1),
+    (dict(precision=9), 5), (dict(bc=5), 1), (dict(scheme=4), 1), (dict(scheme=-1), 1),
+    (dict(kmodel=2), 1), (dict(scheme=3, js_eps=-1.0), 1),
+    # the comparison schemes (WENO-W, WENO-JS) are built in FP64 only
+    (dict(scheme=2, precision=1), 5), (dict(scheme=3, precision=2), 5),
 ])
 def test_init_grid_rejects(bad, status):
     assert init(desc(**bad))[0] == status
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+def test_init_grid_accepts_every_scheme(scheme):
+    assert init(desc(scheme=scheme))[0] == 0
 
 
 def test_periodic_must_pair():

@@ -58,11 +58,11 @@ def test_kapila_rk_parity(gpu, name):
     assert (err <= TOL).all(), err
     V = g.cons_to_prim(Ud).cpu().numpy()
     a0 = case.N + case.dim + 1
-    a = V[a0:]
-    assert a.min() >= 0.0 and a.max() <= 1.0
-    # the rhs keeps sum_p alpha_p (sum_p alpha_p (1 + K_p) = 1); over whole
-    # stages the stiff source of a dilute phase (1 + K_air ~ 2e4 in water)
-    # can overshoot below zero, and removing that residue moves the sum
+    # the rhs keeps sum_p alpha_p (sum_p alpha_p (1 + K_p) = 1), and so do
+    # whole steps: the stiff source of a dilute phase (1 + K_air ~ 2e4 in
+    # water) can take a trace fraction below zero (the method's own
+    # excursion, ~1e-4 here, left to the next limiter), but no clamp moves it
+    assert np.abs(V[a0:].sum(0) - 1.0).max() < 1e-13
     L = g.rhs(Ud).cpu().numpy()
     rate = oracle.max_rate(go, U)
     assert np.abs(L[a0:].sum(0)).max() / rate < 1e-13
