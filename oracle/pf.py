@@ -29,14 +29,18 @@ Readings (R17), where the paper is silent:
     (A Q)_i = sum_faces c_f (Q_nbr - Q_i)/dx^2.  Reflective and outflow
     boundaries carry no flux (the mirrored cell has the same Q).
   * A is singular on every region that faces with c_f > 0 connect (its
-    constants), and its right-hand side need not have zero mean there (the
-    multiplier L^c moves mass between separated interfaces).  Q is a
-    least-squares solution: on each connected region the right-hand side
-    minus its mean over the region's cells; the cells of a region with one
-    cell get Q = 0.  Only the face gradients G = (Q_b - Q_a)/dx on faces with
-    c_f > 0 are defined by this; on faces with c_f = 0 the Phase-Field flux
-    takes G = 0 (R12, ``or_pf_rhs``).  The region means removed are the part
-    of [div J_p]^ that no flux phi_p (1 - phi_p) grad Q_p can carry.
+    constants), and its right-hand side need not sum to zero there (the
+    multiplier L^c moves mass between separated interfaces).  Q is the
+    least-squares solution weighted by the inverse of the coupling D_i =
+    sum_faces c_f/dx^2 (the diagonal of -A): on each region k the
+    right-hand side minus D_i s_k, s_k = sum_k r / sum_k D, is solved
+    exactly; the removed part sits where the coupling is strong, not in the
+    weakly coupled edge cells.  (This is also the limit of Krylov solvers
+    preconditioned by D.)  A region of one cell (D = 0) gets Q = 0.  Only
+    the face gradients G = (Q_b - Q_a)/dx on faces with c_f > 0 are defined
+    by this; on faces with c_f = 0 the Phase-Field flux takes G = 0 (R12,
+    ``or_pf_rhs``).  The removed part is the share of [div J_p]^ that no flux
+    phi_p (1 - phi_p) grad Q_p can carry.
   * Near the edges of an interface c_f is tiny and G = flux / c_f is
     unbounded (and a fraction just outside [0, 1] has c = 0 while Eq. 28
     does not vanish there).  R12's flux keeps the bounds when, summed over
@@ -192,13 +196,14 @@ def qmap_operator(g: Grid, phi: np.ndarray):
 
 def qmap(g: Grid, phi: np.ndarray, R: np.ndarray):
     """Q_p of Eq. 4 for every phase ([N][...]), the R17 least-squares
-    solution; also returns the right-hand sides after the region means were
-    removed (what A Q reproduces)."""
+    solution; also returns the right-hand sides after the regions' parts
+    D s_k were removed (what A Q reproduces)."""
     Q = np.zeros_like(R)
     Rp = np.zeros_like(R)
     for p in range(g.N):
         A, adj = qmap_operator(g, phi[p])
         ncomp, lab = connected_components(adj, directed=False)
+        Dg = -A.diagonal()
         r = R[p].reshape(-1)
         q = np.zeros_like(r)
         rp = np.zeros_like(r)
@@ -206,7 +211,7 @@ def qmap(g: Grid, phi: np.ndarray, R: np.ndarray):
             cells = np.flatnonzero(lab == k)
             if len(cells) < 2:
                 continue
-            rk = r[cells] - r[cells].mean()
+            rk = r[cells] - Dg[cells] * (r[cells].sum() / Dg[cells].sum())
             rp[cells] = rk
             Ak = A[cells][:, cells].tocsc()
             # pin the first cell of the region (its constant is free)

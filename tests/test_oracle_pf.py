@@ -161,7 +161,9 @@ def test_qmap_1d_periodic_matches_integration():
     for p in range(2):
         Gq = (np.roll(Q[p], -1) - Q[p]) / g.dx[0]
         c = phi[p] * (1 - phi[p])
-        rr = R[p] - R[p].mean()
+        cf = 0.5 * (c + np.roll(c, -1))
+        D = (cf + np.roll(cf, 1)) / g.dx[0] ** 2          # coupling of each cell
+        rr = R[p] - D * R[p].sum() / D.sum()
         G = _cumsum_solution(rr, c, g.dx[0], True)
         assert np.abs(Gq - G).max() <= 1e-9 * np.abs(G).max()
 
@@ -169,8 +171,8 @@ def test_qmap_1d_periodic_matches_integration():
 def test_qmap_separated_regions_drop_their_means():
     """Interfaces separated by cells with phi exactly 0 or 1 (c = 0): a
     region is the cells that faces with c_f > 0 connect (its c > 0 cells and
-    their direct neighbours); each is solved on its own with its mean
-    removed (R17)."""
+    their direct neighbours); each is solved on its own with D s_k removed,
+    D the cell's coupling, s_k = sum r / sum D over the region (R17)."""
     n = 96
     g = _grid((n,), 2, bc="reflective")
     f = np.zeros(n)
@@ -184,10 +186,15 @@ def test_qmap_separated_regions_drop_their_means():
     Q, Rp = pf.qmap(g, phi, R)
     dx = g.dx[0]
     c = phi[0] * (1 - phi[0])
+    cf = 0.5 * (c[:-1] + c[1:])
+    D = np.zeros(n)
+    D[:-1] += cf / dx ** 2
+    D[1:] += cf / dx ** 2
     for lo, hi in ((9, 31), (47, 51), (79, 84)):
         r = R[0, lo:hi]
-        assert np.allclose(Rp[0, lo:hi], r - r.mean(), atol=1e-14)
-        G = _cumsum_solution(r - r.mean(), c[lo:hi], dx, False)
+        rr = r - D[lo:hi] * r.sum() / D[lo:hi].sum()
+        assert np.allclose(Rp[0, lo:hi], rr, atol=1e-14 * np.abs(r).max())
+        G = _cumsum_solution(rr, c[lo:hi], dx, False)
         Gq = np.diff(Q[0, lo:hi]) / dx
         assert np.abs(Gq - G).max() <= 1e-9 * max(np.abs(G).max(), 1e-300)
 
@@ -202,8 +209,9 @@ def test_qmap_2d_reproduces_projected_rhs():
         A, _ = pf.qmap_operator(g, phi[p])
         AQ = A @ Q[p].reshape(-1)
         assert np.abs(AQ - Rp[p].reshape(-1)).max() <= 1e-9 * np.abs(R[p]).max()
-    # one connected region (c > 0 everywhere): nothing but the mean is removed
-    assert np.abs(Rp - (R - R.mean(axis=(1, 2), keepdims=True))).max() <= 1e-15 * np.abs(R).max()
+    # one connected region (c > 0 everywhere), and int R = 0 (Eq. 28's
+    # constraint): nothing is removed
+    assert np.abs(Rp - R).max() <= 1e-12 * np.abs(R).max()
 
 
 # ---------------------------------------------------------------- the time step
