@@ -160,6 +160,61 @@ wc_status wc_rhs(wc_grid *g, const double *U_dev, double *L_dev, void *stream);
 wc_status wc_rhs_pf(wc_grid *g, const double *U_dev, const double *Q_dev, double dt_limit,
                     double *L_dev, void *stream);
 
+/* ---- The Phase-Field mechanism of the time step (Sec. 2.2) ----
+ * One time step is: the hyperbolic step (Eq. 3), then [div J_p]^ of Eq. 28
+ * from the fractions phi_p = alpha_p of its result, the auxiliary fields Q_p
+ * of Eq. 4, and the Phase-Field step (Eq. 5) with Q fixed.  Readings where
+ * the paper is silent: eta = dx of the first axis; M = 0.5 eta max|u|;
+ * second-order central Laplacian (mirrored cells at reflective/outflow
+ * sides); midpoint-rule integrals; Eq. 28's singular N x N system solved with
+ * B = 0 for absent phases and for the last present one.  Eq. 4 with the face
+ * coefficient (c_a + c_b)/2, c = max(phi (1 - phi), 0); on each region that
+ * coupled faces connect the part D_i s_k (D_i = sum_faces c_f/dx^2, s_k =
+ * sum r / sum D) that no flux phi(1 - phi) grad Q can carry is removed, and
+ * the rest is solved by conjugate gradients preconditioned with D; only the
+ * face gradients of coupled faces are used (wc_rhs_pf). */
+
+/* Device scratch of the mechanism: ten [N][ncell] FP64 fields, one
+ * [N][ncell] int32 field and about 0.5 MB of reduction partials. */
+size_t wc_pf_workspace_bytes(const wc_grid *g);
+/* Binds that scratch (256-byte aligned, at least wc_pf_workspace_bytes). */
+wc_status wc_set_pf_workspace(wc_grid *g, void *ws_dev, size_t bytes);
+
+/* [div J_p]^ of Eq. 28 for the fractions of U_dev into R_dev ([N][ncell];
+ * may be null: kept in the scratch for wc_qmap).  eta <= 0: dx of the first
+ * axis; M < 0: 0.5 eta max|u| (a reproducible device reduction), M >= 0: as
+ * given.  Asynchronous on stream. */
+wc_status wc_cac_rhs(wc_grid *g, const double *U_dev, double eta, double M, double *R_dev,
+                     void *stream);
+
+/* Q_dev ([N][ncell]) of Eq. 4 for the fractions of U_dev and the right-hand
+ * sides R_dev (null: those of the last wc_cac_rhs).  Conjugate gradients stop
+ * when every phase has sqrt(r.z / r0.z0) <= tol (D-weighted residual) or
+ * after maxit iterations; *iters and *resid (may be null) report them.
+ * Synchronizes stream (the region labelling and the stopping test read
+ * device flags).  The values of Q are fixed up to a constant per region;
+ * the region sums use FP64 atomics, so Q varies at rounding level between
+ * runs. */
+wc_status wc_qmap(wc_grid *g, const double *U_dev, const double *R_dev, double *Q_dev,
+                  double tol, int maxit, int *iters, double *resid, void *stream);
+
+/* The Phase-Field step (Eq. 5) over dt on the bound state: SSP-RK3 with Q
+ * fixed, face gradients limited to dx / (12 d dt). */
+wc_status wc_pf_step(wc_grid *g, const double *Q_dev, double dt, void *stream);
+
+/* nsteps full time steps on the bound state (wc_rk_step, wc_cac_rhs with the
+ * default eta and M, wc_qmap with tol and maxit, wc_pf_step with the same
+ * time step: dt_fixed, or cfl over the hyperbolic step's rate).  Needs both
+ * workspaces; synchronizes stream once per step (wc_qmap).  *dt_host (may be
+ * null) receives the last time step. */
+wc_status wc_step(wc_grid *g, double cfl, double dt_fixed, int nsteps, double tol, int maxit,
+                  double *dt_host, void *stream);
+
+/* Statistics of the last Q-map: CG iterations, labelling rounds, residual. */
+wc_status wc_pf_stats(const wc_grid *g, int *cg_iters, int *label_rounds, double *resid);
+/* Device pointer to the Q of the last wc_step (inside the scratch), or null. */
+const double *wc_pf_q(const wc_grid *g);
+
 /* Time step from the bound state: dt = cfl / max_cells sum_d (|u_d| + c)/dx_d,
  * written to dt_dev (one double, device). */
 wc_status wc_compute_dt(wc_grid *g, double cfl, double *dt_dev, void *stream);

@@ -10,6 +10,7 @@
 #include "../../include/wenoc.h"
 #include "wenoc_kernels.cuh"
 #include "wenoc_mlp.cuh"
+#include "wenoc_pf.cuh"
 #include "wenoc_window.cuh"
 
 using namespace wc;
@@ -40,6 +41,14 @@ struct wc_grid {
   // sweep timing (wc_sweep_timing_begin / _read)
   std::vector<cudaEvent_t> tev;
   int tmax = 0, tcount = 0;
+  // Phase-Field mechanism (wc_set_pf_workspace): scratch, geometry, the
+  // auxiliary fields Q of the last wc_step, statistics of the last Q-map
+  bool pf_bound = false;
+  PfWork pw;
+  PfGeom pg;
+  double* Qbuf = nullptr;
+  int pf_iters = 0, pf_label_rounds = 0;
+  double pf_resid = 0.0;
 };
 
 static wc_status fail(wc_grid* g, wc_status s, const char* msg) {
@@ -297,7 +306,7 @@ static cudaError_t launch(const wc_grid* gc, const SweepArgs& a0, cudaStream_t s
   if (timed) cudaEventRecord(g->tev[2 * g->tcount], st);
   cudaError_t e;
   SweepArgs a = a0;
-  if (g->d.precision == WC_PREC_LEARNED) {
+  if (g->d.precision == WC_PREC_LEARNED && a.kind == 0) {
     // weights of this direction from the surrogate, then the sweep
     e = launch_mlp_infer(mlp_geom(g, a.dir, a.U), g->mlp, g->Wbuf, g->status, st);
     if (e == cudaSuccess) {
@@ -411,12 +420,20 @@ extern "C" wc_status wc_compute_dt(wc_grid* g, double cfl, double* dt_dev, void*
   return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "dt");
 }
 
-// One SSP-RK3 stage: dst = r0 U0 + r1 src + r2 dt L(src).
+// One SSP-RK3 stage: dst = r0 U0 + r1 src + r2 dt L(src); L of Eq. 3, or of
+// Eq. 5 with the auxiliary fields Q (kind 1; face gradients limited to
+// dx / (12 d dt), reading R17).
 static wc_status stage(wc_grid* g, const double* src, double* dst, double r0, double r1,
-                       double r2, double cfl, double dt_fixed, cudaStream_t st) {
+                       double r2, double cfl, double dt_fixed, cudaStream_t st, int kind = 0,
+                       const double* Q = nullptr) {
   int D = g->d.dim;
   for (int dir = 0; dir < D; dir++) {
     SweepArgs a = make_args(g, dir, src, g->Lacc);
+    if (kind == 1) {
+      a.kind = 1;
+      a.Q = Q;
+      a.gcoef = g->d.dx[dir] / (12.0 * g->d.dim);
+    }
     a.U0 = g->U;
     a.Uout = dst;
     a.rate = (const double*)g->rate;
@@ -464,6 +481,191 @@ extern "C" wc_status wc_rk_step(wc_grid* g, double cfl, double dt_fixed, int nst
   }
   return WC_OK;
 }
+
+// ------------------------------------------------------------------ Phase-Field mechanism
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+extern "C" size_t wc_pf_workspace_bytes(const wc_grid* g) {
+  if (!g) return 0;
+  const size_t f = align256(sizeof(double) * (size_t)g->d.nphase * g->ncell);
+  const size_t li = align256(sizeof(int) * (size_t)g->d.nphase * g->ncell);
+  // R c D sumR sumD r z p q Qbuf, labels, partials, scalars, flags
+  return 10 * f + li + align256(sizeof(double) * pf_part_doubles()) + 256 + 256;
+}
+
+extern "C" wc_status wc_set_pf_workspace(wc_grid* g, void* ws_dev, size_t bytes) {
+  if (!g || !ws_dev) return WC_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(ws_dev) & 255) != 0) return fail(g, WC_ERR_ARG, "workspace not 256-byte aligned");
+  if (bytes < wc_pf_workspace_bytes(g)) return fail(g, WC_ERR_ARG, "pf workspace too small");
+  const size_t f = align256(sizeof(double) * (size_t)g->d.nphase * g->ncell);
+  const size_t li = align256(sizeof(int) * (size_t)g->d.nphase * g->ncell);
+  char* w = static_cast<char*>(ws_dev);
+  double** fields[] = {&g->pw.R, &g->pw.c, &g->pw.D, &g->pw.sumR, &g->pw.sumD,
+                       &g->pw.r, &g->pw.z, &g->pw.p, &g->pw.q, &g->Qbuf};
+  for (double** d : fields) {
+    *d = reinterpret_cast<double*>(w);
+    w += f;
+  }
+  g->pw.lab = reinterpret_cast<int*>(w);
+  w += li;
+  g->pw.part = reinterpret_cast<double*>(w);
+  w += align256(sizeof(double) * pf_part_doubles());
+  g->pw.scal = reinterpret_cast<double*>(w);
+  w += 256;
+  g->pw.flag = reinterpret_cast<int*>(w);
+  PfGeom& pg = g->pg;
+  pg.nx = g->d.n[0];
+  pg.ny = g->d.n[1];
+  pg.nz = g->d.n[2];
+  pg.dim = g->d.dim;
+  for (int a = 0; a < 3; a++) {
+    pg.per[a] = a < g->d.dim && g->d.bc[2 * a] == WC_BC_PERIODIC;
+    pg.idx2[a] = a < g->d.dim ? 1.0 / (g->d.dx[a] * g->d.dx[a]) : 0.0;
+  }
+  pg.ncell = g->ncell;
+  pg.N = g->d.nphase;
+  pg.nv = g->nv;
+  pg.a0 = g->d.nphase + g->d.dim + 1;
+  g->pf_bound = true;
+  return WC_OK;
+}
+
+static double cell_volume(const wc_grid* g) {
+  double v = 1.0;
+  for (int a = 0; a < g->d.dim; a++) v *= g->d.dx[a];
+  return v;
+}
+
+extern "C" wc_status wc_cac_rhs(wc_grid* g, const double* U, double eta, double M, double* R,
+                                void* stream) {
+  if (!g || !U) return WC_ERR_ARG;
+  if (!g->pf_bound) return fail(g, WC_ERR_STATE, "wc_cac_rhs needs wc_set_pf_workspace");
+  const double et = eta > 0.0 ? eta : g->d.dx[0];
+  cudaStream_t st = S(stream);
+  cudaError_t e = pf_cac(U, g->pg, g->pw, cell_volume(g), et, M, st);
+  if (e == cudaSuccess && R && R != g->pw.R)
+    e = cudaMemcpyAsync(R, g->pw.R, sizeof(double) * (size_t)g->d.nphase * g->ncell,
+                        cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "cac_rhs");
+}
+
+// Eq. 4 for the fractions of U and the right-hand sides R ([N][ncell];
+// null: those of the last wc_cac_rhs); Q receives the solution.
+static wc_status qmap(wc_grid* g, const double* U, const double* R, double* Q, double tol,
+                      int maxit, cudaStream_t st) {
+  const size_t fb = sizeof(double) * (size_t)g->d.nphase * g->ncell;
+  cudaError_t e = cudaSuccess;
+  if (R && R != g->pw.R) e = cudaMemcpyAsync(g->pw.R, R, fb, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = pf_qmap_setup(U, g->pg, g->pw, st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "qmap setup");
+  // label rounds until one changes nothing (at most ncell rounds: every
+  // changing round lowers some label)
+  const int LR = 8;
+  int rounds = 0;
+  for (;;) {
+    e = pf_label_rounds(g->pg, g->pw, LR, st);
+    int moved = 0;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&moved, g->pw.flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(g, e, "qmap labels");
+    rounds += LR;
+    if (!moved) break;
+    if (rounds > g->ncell + LR) return fail(g, WC_ERR_STATE, "qmap labels did not settle");
+  }
+  g->pf_label_rounds = rounds;
+  e = pf_qmap_project(g->pg, g->pw, Q, st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "qmap project");
+  const int CR = 25;
+  const int N = g->d.nphase;
+  int it = 0;
+  int flags[8] = {0};
+  for (; it < maxit; it += CR) {
+    e = pf_cg_rounds(g->pg, g->pw, Q, it, CR, tol * tol, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(flags, g->pw.flag, sizeof(int) * (1 + N), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(g, e, "qmap cg");
+    int all = 1;
+    for (int p = 0; p < N; p++) all &= flags[1 + p];
+    if (all) break;
+  }
+  double sc[32];
+  e = cudaMemcpyAsync(sc, g->pw.scal, sizeof(sc), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "qmap residual");
+  double res = 0.0;
+  for (int p = 0; p < N; p++)
+    if (sc[16 + p] > 0.0) res = fmax(res, sqrt(fmax(sc[24 + p], 0.0) / sc[16 + p]));
+  g->pf_iters = it + CR < maxit ? it + CR : maxit;
+  g->pf_resid = res;
+  return WC_OK;
+}
+
+extern "C" wc_status wc_qmap(wc_grid* g, const double* U, const double* R, double* Q, double tol,
+                             int maxit, int* iters, double* resid, void* stream) {
+  if (!g || !U || !Q || !(tol > 0.0) || maxit < 1) return WC_ERR_ARG;
+  if (!g->pf_bound) return fail(g, WC_ERR_STATE, "wc_qmap needs wc_set_pf_workspace");
+  wc_status s = qmap(g, U, R, Q, tol, maxit, S(stream));
+  if (s) return s;
+  if (iters) *iters = g->pf_iters;
+  if (resid) *resid = g->pf_resid;
+  return WC_OK;
+}
+
+// SSP-RK3 of Eq. 5 on the bound state with Q fixed (time step dt_fixed, or
+// cfl over the rate of the last hyperbolic step on the device).
+static wc_status pf_stages(wc_grid* g, const double* Q, double cfl, double dt_fixed,
+                           cudaStream_t st) {
+  wc_status r;
+  if ((r = stage(g, g->U, g->B1, 0.0, 1.0, 1.0, cfl, dt_fixed, st, 1, Q))) return r;
+  if ((r = stage(g, g->B1, g->B2, 0.75, 0.25, 0.25, cfl, dt_fixed, st, 1, Q))) return r;
+  return stage(g, g->B2, g->U, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, cfl, dt_fixed, st, 1, Q);
+}
+
+extern "C" wc_status wc_pf_step(wc_grid* g, const double* Q, double dt, void* stream) {
+  if (!g || !Q || !(dt > 0.0)) return WC_ERR_ARG;
+  if (!g->U || !g->ws) return fail(g, WC_ERR_STATE, "state/workspace not bound");
+  return pf_stages(g, Q, 0.0, dt, S(stream));
+}
+
+extern "C" wc_status wc_step(wc_grid* g, double cfl, double dt_fixed, int nsteps, double tol,
+                             int maxit, double* dt_host, void* stream) {
+  if (!g || nsteps < 0 || !(tol > 0.0) || maxit < 1) return WC_ERR_ARG;
+  if (!g->pf_bound) return fail(g, WC_ERR_STATE, "wc_step needs wc_set_pf_workspace");
+  cudaStream_t st = S(stream);
+  for (int s = 0; s < nsteps; s++) {
+    wc_status r = wc_rk_step(g, cfl, dt_fixed, 1, nullptr, stream);
+    if (r) return r;
+    cudaError_t e = pf_cac(g->U, g->pg, g->pw, cell_volume(g), g->d.dx[0], -1.0, st);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cac_rhs");
+    if ((r = qmap(g, g->U, nullptr, g->Qbuf, tol, maxit, st))) return r;
+    if ((r = pf_stages(g, g->Qbuf, cfl, dt_fixed, st))) return r;
+  }
+  if (dt_host) {
+    if (dt_fixed > 0.0) {
+      *dt_host = dt_fixed;
+    } else {
+      double rate = 0.0;
+      cudaError_t e = cudaMemcpyAsync(&rate, g->rate, sizeof(double), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(g, e, "dt readback");
+      *dt_host = cfl / rate;
+    }
+  }
+  return WC_OK;
+}
+
+extern "C" wc_status wc_pf_stats(const wc_grid* g, int* cg_iters, int* label_rounds,
+                                 double* resid) {
+  if (!g) return WC_ERR_ARG;
+  if (cg_iters) *cg_iters = g->pf_iters;
+  if (label_rounds) *label_rounds = g->pf_label_rounds;
+  if (resid) *resid = g->pf_resid;
+  return WC_OK;
+}
+
+extern "C" const double* wc_pf_q(const wc_grid* g) { return g && g->pf_bound ? g->Qbuf : nullptr; }
 
 extern "C" wc_status wc_limit(const wc_grid* gc, int dir, long ncell, const double* Ubar,
                               const double* VL, const double* VR, double* UL, double* UR,

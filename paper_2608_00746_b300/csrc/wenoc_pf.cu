@@ -1,0 +1,560 @@
+// wenoc_pf.cu -- kernels of the Phase-Field mechanism (Eq. 28 and Eq. 4,
+// readings in wenoc_pf.cuh).  All memory-bound stencil and reduction passes
+// over [N][ncell] fields; grid-stride loops on a fixed grid of PF_BLOCKS
+// blocks so that every reduction has one fixed order.
+#include "wenoc_pf.cuh"
+
+namespace wc {
+
+// ------------------------------------------------------------------ helpers
+template <int K>
+__device__ __forceinline__ void block_sum_to(double (&v)[K], double* out) {
+  // fixed-order block reduction: warp trees, then warps in order
+  __shared__ double sm[PF_THREADS / 32][K > 0 ? K : 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sm[w][k] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double s = 0.0;
+    for (int j = 0; j < PF_THREADS / 32; j++) s += sm[j][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double block_max(double v) {
+  __shared__ double sm[PF_THREADS / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  if (lane == 0) sm[w] = v;
+  __syncthreads();
+  double m = 0.0;
+  for (int j = 0; j < PF_THREADS / 32; j++) m = fmax(m, sm[j]);
+  __syncthreads();
+  return m;
+}
+
+__device__ __forceinline__ double gprime(double f) { return 2.0 * f * (1.0 - f) * (1.0 - 2.0 * f); }
+
+template <int N>
+struct CacLayout {
+  static constexpr int NW = N * (N + 1) / 2;  // W_pq, p <= q
+  static constexpr int K = NW + N;           // + sums of g'_p - phi_p sum g'
+};
+
+// ------------------------------------------------------------------ Eq. 28
+// Pass 1: per block, max |u|^2 and the sums of W_pq (p <= q) and of
+// g'(phi_p) - phi_p sum_q g'(phi_q) over its cells.
+template <int N>
+__global__ void __launch_bounds__(PF_THREADS) k_cac_reduce(const double* __restrict__ U,
+                                                           PfGeom g, double* part) {
+  using L = CacLayout<N>;
+  double acc[L::K];
+#pragma unroll
+  for (int k = 0; k < L::K; k++) acc[k] = 0.0;
+  double umax = 0.0;
+  const long n = g.ncell;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    double rho = 0.0;
+#pragma unroll
+    for (int p = 0; p < N; p++) rho += U[(long)p * n + i];
+    double u2 = 0.0;
+    for (int j = 0; j < g.dim; j++) {
+      const double u = U[(long)(N + j) * n + i] / rho;
+      u2 += u * u;
+    }
+    umax = fmax(umax, u2);
+    double phi[N], gp[N], sg = 0.0;
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      phi[p] = U[(long)(g.a0 + p) * n + i];
+      gp[p] = gprime(phi[p]);
+      sg += gp[p];
+    }
+    int k = 0;
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+#pragma unroll
+      for (int q = p; q < N; q++) acc[k++] += p == q ? phi[p] * (1.0 - phi[p]) : -phi[p] * phi[q];
+    }
+#pragma unroll
+    for (int p = 0; p < N; p++) acc[L::NW + p] += gp[p] - phi[p] * sg;
+  }
+  double* out = part + (long)blockIdx.x * 32;
+  block_sum_to<L::K>(acc, out);
+  const double m = block_max(umax);
+  if (threadIdx.x == 0) out[31] = m;
+}
+
+// Pass 2 (one block): totals, M, the N x N system and its solution B.
+template <int N>
+__global__ void k_cac_solve(const double* part, double vol, double eta, double M_in, double* scal) {
+  using L = CacLayout<N>;
+  __shared__ double tot[32];
+  const int t = threadIdx.x;
+  if (t < L::K) {
+    double s = 0.0;
+    for (int b = 0; b < PF_BLOCKS; b++) s += part[(long)b * 32 + t];
+    tot[t] = s;
+  } else if (t == 31) {
+    double m = 0.0;
+    for (int b = 0; b < PF_BLOCKS; b++) m = fmax(m, part[(long)b * 32 + 31]);
+    tot[31] = m;
+  }
+  __syncthreads();
+  if (t != 0) return;
+  const double M = M_in >= 0.0 ? M_in : 0.5 * eta * sqrt(tot[31]);
+  double W[N][N], b[N], B[N];
+  int k = 0;
+  for (int p = 0; p < N; p++)
+    for (int q = p; q < N; q++) {
+      W[p][q] = W[q][p] = tot[k++] * vol;
+    }
+  for (int p = 0; p < N; p++) {
+    b[p] = (M / (eta * eta)) * tot[L::NW + p] * vol;
+    B[p] = 0.0;
+  }
+  // present phases (int W_pp > 0); the last one keeps B = 0, its equation
+  // (implied by the others) is dropped
+  int keep[N], m = 0;
+  for (int p = 0; p < N; p++)
+    if (W[p][p] > 0.0) keep[m++] = p;
+  m -= 1;
+  if (m >= 1) {
+    double A[N][N + 1];
+    for (int i = 0; i < m; i++) {
+      for (int j = 0; j < m; j++) A[i][j] = W[keep[i]][keep[j]];
+      A[i][m] = b[keep[i]];
+    }
+    // Gaussian elimination with partial pivoting
+    for (int c = 0; c < m; c++) {
+      int piv = c;
+      for (int i = c + 1; i < m; i++)
+        if (fabs(A[i][c]) > fabs(A[piv][c])) piv = i;
+      if (piv != c)
+        for (int j = c; j <= m; j++) {
+          const double tmp = A[c][j];
+          A[c][j] = A[piv][j];
+          A[piv][j] = tmp;
+        }
+      for (int i = c + 1; i < m; i++) {
+        const double f = A[i][c] / A[c][c];
+        for (int j = c; j <= m; j++) A[i][j] -= f * A[c][j];
+      }
+    }
+    for (int i = m - 1; i >= 0; i--) {
+      double s = A[i][m];
+      for (int j = i + 1; j < m; j++) s -= A[i][j] * B[keep[j]];
+      B[keep[i]] = s / A[i][i];
+    }
+  }
+  scal[0] = M;
+  for (int p = 0; p < N; p++) scal[1 + p] = B[p];
+}
+
+// Pass 3: [div J_p]^ = M lap(phi_p) - (M/eta^2)(g'_p - phi_p sum g') + L^c_p.
+template <int N>
+__global__ void __launch_bounds__(PF_THREADS) k_cac_rhs(const double* __restrict__ U, PfGeom g,
+                                                        const double* scal, double eta,
+                                                        double* __restrict__ R) {
+  const long n = g.ncell;
+  const double M = scal[0];
+  double B[N];
+#pragma unroll
+  for (int p = 0; p < N; p++) B[p] = scal[1 + p];
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    double phi[N], gp[N], sg = 0.0;
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      phi[p] = U[(long)(g.a0 + p) * n + i];
+      gp[p] = gprime(phi[p]);
+      sg += gp[p];
+    }
+    long nb[3][2];
+    for (int ax = 0; ax < g.dim; ax++) {
+      nb[ax][0] = pf_nbr(g, i, ax, -1);
+      nb[ax][1] = pf_nbr(g, i, ax, +1);
+    }
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      const double* f = U + (long)(g.a0 + p) * n;
+      double lap = 0.0;
+      for (int ax = 0; ax < g.dim; ax++) {
+        const double fm = nb[ax][0] >= 0 ? f[nb[ax][0]] : phi[p];
+        const double fp = nb[ax][1] >= 0 ? f[nb[ax][1]] : phi[p];
+        lap += (fp - 2.0 * phi[p] + fm) * g.idx2[ax];
+      }
+      const double S = (M / (eta * eta)) * (gp[p] - phi[p] * sg);
+      double Lc = 0.0;
+#pragma unroll
+      for (int q = 0; q < N; q++) Lc += (p == q ? phi[p] * (1.0 - phi[q]) : -phi[p] * phi[q]) * B[q];
+      R[(long)p * n + i] = M * lap - S + Lc;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ Eq. 4
+template <int N>
+__global__ void __launch_bounds__(PF_THREADS) k_qm_coef(const double* __restrict__ U, PfGeom g,
+                                                        double* __restrict__ c) {
+  const long n = g.ncell;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      const double f = U[(long)(g.a0 + p) * n + i];
+      c[(long)p * n + i] = fmax(f * (1.0 - f), 0.0);
+    }
+  }
+}
+
+// D_i = sum_faces c_f / dx^2 and the initial labels (own index where D > 0).
+template <int N>
+__global__ void __launch_bounds__(PF_THREADS) k_qm_diag(PfGeom g, const double* __restrict__ c,
+                                                        double* __restrict__ D, int* lab) {
+  const long n = g.ncell;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    long nb[3][2];
+    for (int ax = 0; ax < g.dim; ax++) {
+      nb[ax][0] = pf_nbr(g, i, ax, -1);
+      nb[ax][1] = pf_nbr(g, i, ax, +1);
+    }
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      const double* cp = c + (long)p * n;
+      const double ci = cp[i];
+      double d = 0.0;
+      for (int ax = 0; ax < g.dim; ax++)
+        for (int s = 0; s < 2; s++)
+          if (nb[ax][s] >= 0) d += 0.5 * (ci + cp[nb[ax][s]]) * g.idx2[ax];
+      D[(long)p * n + i] = d;
+      lab[(long)p * n + i] = d > 0.0 ? (int)i : -1;
+    }
+  }
+}
+
+// One round of minimum-label propagation over coupled faces with pointer
+// jumping.  Labels only decrease and always name a cell of the same region,
+// so the rounds end (the host stops at a round without change) with every
+// cell of a region labelled by the region's smallest cell index.
+template <int N>
+__global__ void __launch_bounds__(PF_THREADS) k_qm_label(PfGeom g, const double* __restrict__ c,
+                                                         int* lab, int* flag) {
+  const long n = g.ncell;
+  int changed = 0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    long nb[3][2];
+    for (int ax = 0; ax < g.dim; ax++) {
+      nb[ax][0] = pf_nbr(g, i, ax, -1);
+      nb[ax][1] = pf_nbr(g, i, ax, +1);
+    }
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      int* lp = lab + (long)p * n;
+      const int li = __ldcg(lp + i);
+      if (li < 0) continue;
+      const double* cp = c + (long)p * n;
+      const double ci = cp[i];
+      int m = li;
+      for (int ax = 0; ax < g.dim; ax++)
+        for (int s = 0; s < 2; s++) {
+          const long j = nb[ax][s];
+          if (j >= 0 && (ci > 0.0 || cp[j] > 0.0)) m = min(m, __ldcg(lp + j));
+        }
+      m = min(m, __ldcg(lp + m));
+      if (m < li) {
+        atomicMin(lp + i, m);
+        changed = 1;
+      }
+    }
+  }
+  if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+template <int N>
+__global__ void __launch_bounds__(PF_THREADS) k_qm_sums(PfGeom g, const double* __restrict__ R,
+                                                        const double* __restrict__ D,
+                                                        const int* __restrict__ lab, double* sumR,
+                                                        double* sumD) {
+  const long n = g.ncell;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      const int l = lab[(long)p * n + i];
+      if (l < 0) continue;
+      atomicAdd(sumR + (long)p * n + l, R[(long)p * n + i]);
+      atomicAdd(sumD + (long)p * n + l, D[(long)p * n + i]);
+    }
+  }
+}
+
+// Offsets into the partials buffer.
+constexpr long PART_CAC = 0;
+constexpr long PART_PQ = (long)PF_BLOCKS * 32;
+constexpr long PART_RZ = PART_PQ + (long)PF_BLOCKS * 8;  // [2][PF_BLOCKS][8]
+constexpr long PART_TOTAL = PART_RZ + 2L * PF_BLOCKS * 8;
+
+// Right-hand side of K Q = b with K = -A (positive semi-definite): b = -(r -
+// D s_k) on cells with a label; conjugate-gradient start x = 0.
+template <int N>
+__global__ void __launch_bounds__(PF_THREADS) k_cg_init(PfGeom g, const double* __restrict__ R,
+                                                        const double* __restrict__ D,
+                                                        const int* __restrict__ lab,
+                                                        const double* __restrict__ sumR,
+                                                        const double* __restrict__ sumD,
+                                                        double* x, double* r, double* z, double* pv,
+                                                        double* part) {
+  const long n = g.ncell;
+  double acc[N];
+#pragma unroll
+  for (int p = 0; p < N; p++) acc[p] = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      const long k = (long)p * n + i;
+      const int l = lab[k];
+      double b = 0.0, zz = 0.0;
+      if (l >= 0) {
+        const double s = sumR[(long)p * n + l] / sumD[(long)p * n + l];
+        b = -(R[k] - D[k] * s);
+        zz = b / D[k];
+      }
+      x[k] = 0.0;
+      r[k] = b;
+      z[k] = zz;
+      pv[k] = zz;
+      acc[p] += b * zz;
+    }
+  }
+  block_sum_to<N>(acc, part + PART_RZ + (long)blockIdx.x * 8);  // parity 0
+}
+
+// rz0 per phase (one block): the start of the convergence test; a phase
+// with rz0 = 0 (nothing to solve) is converged from the start.
+template <int N>
+__global__ void k_cg_start(const double* part, double* scal, int* flag) {
+  const int p = threadIdx.x;
+  if (p >= N) return;
+  double s = 0.0;
+  for (int b = 0; b < PF_BLOCKS; b++) s += part[PART_RZ + (long)b * 8 + p];
+  scal[16 + p] = s;
+  scal[24 + p] = s;
+  flag[1 + p] = !(s > 0.0);
+}
+
+__device__ __forceinline__ bool all_converged(const int* flag, int N) {
+  int all = 1;
+  for (int p = 0; p < N; p++) all &= flag[1 + p];
+  return all;
+}
+
+// q = K p and the partial sums of p . q.
+template <int N>
+__global__ void __launch_bounds__(PF_THREADS) k_cg_matvec(PfGeom g, const double* __restrict__ c,
+                                                          const double* __restrict__ pv,
+                                                          double* __restrict__ q, double* part,
+                                                          const int* flag) {
+  if (all_converged(flag, N)) return;
+  const long n = g.ncell;
+  double acc[N];
+#pragma unroll
+  for (int p = 0; p < N; p++) acc[p] = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    long nb[3][2];
+    for (int ax = 0; ax < g.dim; ax++) {
+      nb[ax][0] = pf_nbr(g, i, ax, -1);
+      nb[ax][1] = pf_nbr(g, i, ax, +1);
+    }
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      const double* cp = c + (long)p * n;
+      const double* pp = pv + (long)p * n;
+      const double ci = cp[i], pi = pp[i];
+      double s = 0.0;
+      for (int ax = 0; ax < g.dim; ax++)
+        for (int k = 0; k < 2; k++) {
+          const long j = nb[ax][k];
+          if (j >= 0) s += 0.5 * (ci + cp[j]) * g.idx2[ax] * (pi - pp[j]);
+        }
+      q[(long)p * n + i] = s;
+      acc[p] += pi * s;
+    }
+  }
+  block_sum_to<N>(acc, part + PART_PQ + (long)blockIdx.x * 8);
+}
+
+// Sum of one column of partials (every block the same fixed order).
+__device__ __forceinline__ void sum_partials(const double* part, long off, int N, double* out) {
+  if (threadIdx.x < N) {
+    double s = 0.0;
+    for (int b = 0; b < PF_BLOCKS; b++) s += part[off + (long)b * 8 + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// x += alpha p, r -= alpha q, z = r / D; partial sums of r . z into the
+// buffer of parity (it + 1) % 2.
+template <int N>
+__global__ void __launch_bounds__(PF_THREADS) k_cg_update(PfGeom g, const double* __restrict__ D,
+                                                          const int* __restrict__ lab, double* x,
+                                                          double* r, double* z,
+                                                          const double* __restrict__ pv,
+                                                          const double* __restrict__ q,
+                                                          double* part, const int* flag, int it) {
+  if (all_converged(flag, N)) return;
+  __shared__ double pq[N], rz[N];
+  sum_partials(part, PART_PQ, N, pq);
+  sum_partials(part, PART_RZ + (long)(it & 1) * PF_BLOCKS * 8, N, rz);
+  double alpha[N];
+  bool live[N];
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    live[p] = !flag[1 + p] && pq[p] > 0.0;
+    alpha[p] = live[p] ? rz[p] / pq[p] : 0.0;
+  }
+  const long n = g.ncell;
+  double acc[N];
+#pragma unroll
+  for (int p = 0; p < N; p++) acc[p] = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      const long k = (long)p * n + i;
+      if (lab[k] < 0) continue;
+      double rk = r[k], zk = z[k];
+      if (live[p]) {
+        x[k] = fma(alpha[p], pv[k], x[k]);
+        rk = fma(-alpha[p], q[k], rk);
+        zk = rk / D[k];
+        r[k] = rk;
+        z[k] = zk;
+      }
+      acc[p] += rk * zk;
+    }
+  }
+  block_sum_to<N>(acc, part + PART_RZ + (long)((it + 1) & 1) * PF_BLOCKS * 8 + (long)blockIdx.x * 8);
+}
+
+// p = z + beta p, beta = rz_new / rz_old; block 0 records rz_new and marks
+// the phases whose rz_new <= tol2 rz0 as converged.
+template <int N>
+__global__ void __launch_bounds__(PF_THREADS) k_cg_dir(PfGeom g, const double* __restrict__ z,
+                                                       const int* __restrict__ lab, double* pv,
+                                                       const double* part, double* scal, int* flag,
+                                                       int it, double tol2) {
+  if (all_converged(flag, N)) return;
+  __shared__ double rn[N], ro[N];
+  sum_partials(part, PART_RZ + (long)((it + 1) & 1) * PF_BLOCKS * 8, N, rn);
+  sum_partials(part, PART_RZ + (long)(it & 1) * PF_BLOCKS * 8, N, ro);
+  double beta[N];
+  bool live[N];
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    live[p] = !flag[1 + p] && ro[p] > 0.0;
+    beta[p] = live[p] ? rn[p] / ro[p] : 0.0;
+  }
+  const long n = g.ncell;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      const long k = (long)p * n + i;
+      if (live[p] && lab[k] >= 0) pv[k] = fma(beta[p], pv[k], z[k]);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x < N) {
+    const int p = threadIdx.x;
+    if (!flag[1 + p]) {
+      scal[24 + p] = rn[p];
+      if (!(rn[p] > tol2 * scal[16 + p])) flag[1 + p] = 1;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+#define PF_DISPATCH(N, call)                   \
+  switch (N) {                                 \
+    case 1: { constexpr int N_ = 1; call; break; } \
+    case 2: { constexpr int N_ = 2; call; break; } \
+    case 3: { constexpr int N_ = 3; call; break; } \
+    case 4: { constexpr int N_ = 4; call; break; } \
+    case 5: { constexpr int N_ = 5; call; break; } \
+    default: return cudaErrorInvalidValue;     \
+  }
+
+static int pf_grid(long n) {
+  long b = (n + PF_THREADS - 1) / PF_THREADS;
+  return (int)(b < PF_BLOCKS ? (b < 1 ? 1 : b) : PF_BLOCKS);
+}
+
+size_t pf_part_doubles() { return (size_t)PART_TOTAL; }
+
+cudaError_t pf_cac(const double* U, const PfGeom& g, const PfWork& w, double vol, double eta,
+                   double M_in, cudaStream_t st) {
+  PF_DISPATCH(g.N, (k_cac_reduce<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(U, g, w.part + PART_CAC)));
+  PF_DISPATCH(g.N, (k_cac_solve<N_><<<1, 32, 0, st>>>(w.part + PART_CAC, vol, eta, M_in, w.scal)));
+  PF_DISPATCH(g.N, (k_cac_rhs<N_><<<pf_grid(g.ncell), PF_THREADS, 0, st>>>(U, g, w.scal, eta, w.R)));
+  return cudaGetLastError();
+}
+
+cudaError_t pf_qmap_setup(const double* U, const PfGeom& g, const PfWork& w, cudaStream_t st) {
+  const int nb = pf_grid(g.ncell);
+  PF_DISPATCH(g.N, (k_qm_coef<N_><<<nb, PF_THREADS, 0, st>>>(U, g, w.c)));
+  PF_DISPATCH(g.N, (k_qm_diag<N_><<<nb, PF_THREADS, 0, st>>>(g, w.c, w.D, w.lab)));
+  return cudaGetLastError();
+}
+
+cudaError_t pf_label_rounds(const PfGeom& g, const PfWork& w, int rounds, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(w.flag, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const int nb = pf_grid(g.ncell);
+  for (int k = 0; k < rounds; k++)
+    PF_DISPATCH(g.N, (k_qm_label<N_><<<nb, PF_THREADS, 0, st>>>(g, w.c, w.lab, w.flag)));
+  return cudaGetLastError();
+}
+
+cudaError_t pf_qmap_project(const PfGeom& g, const PfWork& w, double* Q, cudaStream_t st) {
+  const size_t bytes = sizeof(double) * (size_t)g.N * g.ncell;
+  cudaError_t e = cudaMemsetAsync(w.sumR, 0, bytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.sumD, 0, bytes, st);
+  if (e != cudaSuccess) return e;
+  const int nb = pf_grid(g.ncell);
+  PF_DISPATCH(g.N, (k_qm_sums<N_><<<nb, PF_THREADS, 0, st>>>(g, w.R, w.D, w.lab, w.sumR, w.sumD)));
+  PF_DISPATCH(g.N, (k_cg_init<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(g, w.R, w.D, w.lab, w.sumR,
+                                                                     w.sumD, Q, w.r, w.z, w.p,
+                                                                     w.part)));
+  PF_DISPATCH(g.N, (k_cg_start<N_><<<1, 32, 0, st>>>(w.part, w.scal, w.flag)));
+  return cudaGetLastError();
+}
+
+cudaError_t pf_cg_rounds(const PfGeom& g, const PfWork& w, double* Q, int it0, int rounds,
+                         double tol2, cudaStream_t st) {
+  for (int k = 0; k < rounds; k++) {
+    const int it = it0 + k;
+    PF_DISPATCH(g.N, (k_cg_matvec<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(g, w.c, w.p, w.q,
+                                                                         w.part, w.flag)));
+    PF_DISPATCH(g.N, (k_cg_update<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(
+                          g, w.D, w.lab, Q, w.r, w.z, w.p, w.q, w.part, w.flag, it)));
+    PF_DISPATCH(g.N, (k_cg_dir<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(g, w.z, w.lab, w.p, w.part,
+                                                                      w.scal, w.flag, it, tol2)));
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace wc

@@ -35,7 +35,8 @@ struct SweepArgs {
   int nseg, seg;       // segments per pencil, cells per segment
   long max_threads;    // launch size cap (whole blocks per SM); items loop beyond it
   const double* Q;     // Phase-Field auxiliary fields [N][ncell] (kind 1)
-  double gmax;         // kind 1: limit of |grad Q| on a face (0 = none)
+  double gmax;         // kind 1: limit of |grad Q| on a face (0 = none) ...
+  double gcoef;        // ... or, in the stage modes, gcoef / dt when gcoef > 0
   int kind;            // 0: hyperbolic step (Eq. 3); 1: Phase-Field step (Eq. 5)
   double inv_dx;
   int bclo, bchi;
@@ -263,7 +264,8 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
         double G[N];
 #pragma unroll
         for (int p = 0; p < N; p++)
-          G[p] = pf_gradient(Qprev[p], Qcur[p], Uprev[I::A(p)], Ub[I::A(p)], a.inv_dx, a.gmax);
+          G[p] = pf_gradient(Qprev[p], Qcur[p], Uprev[I::A(p)], Ub[I::A(p)], a.inv_dx,
+                             a.gcoef > 0.0 ? a.gcoef / dt : a.gmax);
         pf_flux<N, D>(m, prevL, fR, G, F);
       } else {
         riemann<N, D, TF>(m, a.dir, a.hllc, prevL, fR, F, uh);
@@ -326,7 +328,9 @@ __global__ void __launch_bounds__(128) k_sweep(SweepArgs a, Mat m) {
   unsigned bad = 0u;
   unsigned lstat[2] = {0u, 0u};
   double dt = 0.0;
-  if (a.mode >= 2) dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.cfl / *a.rate;
+  // the stage modes, and every direction of a Phase-Field stage (its gradient
+  // limit is gcoef / dt)
+  if (a.mode >= 2 || a.gcoef > 0.0) dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.cfl / *a.rate;
 
   // work item = (pencil, segment); consecutive threads take consecutive
   // pencils of one segment row, so y and z sweeps read coalesced

@@ -193,7 +193,8 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
     for (int p = 0; p < N; p++) {
       const double qn = __shfl_down_sync(0xffffffffu, q[p], 1);
       const double an = __shfl_down_sync(0xffffffffu, Ub[I::A(p)], 1);
-      G[p] = pf_gradient(q[p], qn, Ub[I::A(p)], an, a.inv_dx, a.gmax);
+      G[p] = pf_gradient(q[p], qn, Ub[I::A(p)], an, a.inv_dx,
+                         a.gcoef > 0.0 ? a.gcoef / dt : a.gmax);
     }
     pf_flux<N, D>(m, fL, fRn, G, F);
   } else {
@@ -252,7 +253,9 @@ __global__ void __launch_bounds__(128) k_sweep_win(SweepArgs a, Mat m) {
   unsigned bad = 0u;
   unsigned lstat[2] = {0u, 0u};
   double dt = 0.0;
-  if (a.mode >= 2) dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.cfl / *a.rate;
+  // the stage modes, and every direction of a Phase-Field stage (its gradient
+  // limit is gcoef / dt)
+  if (a.mode >= 2 || a.gcoef > 0.0) dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.cfl / *a.rate;
   for (;;) {
     unsigned it = 0u;
     if (lane == 0) it = atomicAdd(a.ticket, 1u);

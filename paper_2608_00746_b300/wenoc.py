@@ -71,6 +71,17 @@ class PatchesDesc(ctypes.Structure):
 # name -> (restype, argtypes)
 _VP = ctypes.c_void_p
 _SIGS = {
+    "wc_pf_workspace_bytes": (ctypes.c_size_t, [_VP]),
+    "wc_set_pf_workspace": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    "wc_cac_rhs": (ctypes.c_int, [_VP, _VP, ctypes.c_double, ctypes.c_double, _VP, _VP]),
+    "wc_qmap": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _VP]),
+    "wc_pf_step": (ctypes.c_int, [_VP, _VP, ctypes.c_double, _VP]),
+    "wc_step": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                               ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _VP]),
+    "wc_pf_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_double)]),
+    "wc_pf_q": (_VP, [_VP]),
     "wc_init_grid": (ctypes.c_int, [ctypes.POINTER(GridDesc), ctypes.POINTER(_VP)]),
     "wc_destroy": (None, [_VP]),
     "wc_nvar": (ctypes.c_int, [_VP]),
@@ -239,6 +250,10 @@ class Grid:
     def state_shape(self):
         return (self.nv,) + tuple(reversed(self.shape))
 
+    @property
+    def N(self):
+        return self.desc.nphase
+
     def workspace_bytes(self):
         return lib().wc_workspace_bytes(self.h)
 
@@ -319,6 +334,51 @@ class Grid:
 
     def sync_status(self, stream=None):
         self._check(lib().wc_sync_status(self.h, _stream(stream)))
+
+    # Phase-Field mechanism (Eq. 28, Eq. 4, Eq. 5) ---------------------------
+    def set_pf_workspace(self, device="cuda"):
+        """Allocates and binds the mechanism's scratch (torch memory)."""
+        n = (lib().wc_pf_workspace_bytes(self.h) + 7) // 8
+        self.pfws = torch.empty(n, dtype=torch.float64, device=device)
+        self._check(lib().wc_set_pf_workspace(self.h, _ptr(self.pfws), n * 8))
+        return self
+
+    def cac_rhs(self, U, eta=0.0, M=-1.0, R=None, stream=None):
+        """[div J_p]^ of Eq. 28, [N][...] (eta <= 0: dx; M < 0: 0.5 eta max|u|)."""
+        R = torch.empty((self.N,) + tuple(U.shape[1:]), dtype=torch.float64,
+                        device=U.device) if R is None else R
+        self._check(lib().wc_cac_rhs(self.h, _ptr(U), float(eta), float(M), _ptr(R),
+                                     _stream(stream)))
+        return R
+
+    def qmap(self, U, R=None, Q=None, tol=1e-12, maxit=20000, stream=None):
+        """Q of Eq. 4 ([N][...]) for the fractions of U and right-hand sides R
+        (None: the last cac_rhs); returns (Q, CG iterations, residual)."""
+        Q = torch.empty((self.N,) + tuple(U.shape[1:]), dtype=torch.float64,
+                        device=U.device) if Q is None else Q
+        it, res = ctypes.c_int(0), ctypes.c_double(0.0)
+        self._check(lib().wc_qmap(self.h, _ptr(U), _dptr(R), _ptr(Q), float(tol), int(maxit),
+                                  ctypes.byref(it), ctypes.byref(res), _stream(stream)))
+        return Q, it.value, res.value
+
+    def pf_step(self, Q, dt, stream=None):
+        """The Phase-Field step (Eq. 5) over dt on the bound state."""
+        self._check(lib().wc_pf_step(self.h, _ptr(Q), float(dt), _stream(stream)))
+
+    def step(self, cfl=0.0, dt=0.0, nsteps=1, tol=1e-12, maxit=20000, want_dt=False,
+             stream=None):
+        """nsteps full time steps (hyperbolic step, Eq. 28, Eq. 4, Phase-Field step)."""
+        dth = ctypes.c_double(0.0)
+        self._check(lib().wc_step(self.h, float(cfl), float(dt), int(nsteps), float(tol),
+                                  int(maxit), ctypes.byref(dth) if want_dt else None,
+                                  _stream(stream)))
+        return dth.value if want_dt else None
+
+    def pf_stats(self):
+        it, lr, res = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+        self._check(lib().wc_pf_stats(self.h, ctypes.byref(it), ctypes.byref(lr),
+                                      ctypes.byref(res)))
+        return it.value, lr.value, res.value
 
     # learned weights ------------------------------------------------------
     def set_mlp(self, params, tau=1e-4, counters=None):

@@ -1,0 +1,156 @@
+"""The Phase-Field mechanism of the time step on the GPU (Eq. 28, Eq. 4 and
+the Phase-Field step Eq. 5; reading R17) against the oracle: [div J_p]^ to
+1e-12, the Q-map's solution checked with the oracle's operator and against
+the oracle's face fluxes, the Phase-Field step to 1e-12 with a common Q,
+full time steps to the Q-map's tolerance, and the invariants of long runs
+(conservation, fraction sum, bounds, the equilibrium interface band)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import pf
+from paper_2608_00746_b300 import inputs, wenoc
+
+from gpu_util import SMALL_CASES, state_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _grids(case):
+    go = oracle.Grid(case.shape, case.dx, case.gamma, case.pinf, case.D, flux=case.flux,
+                     bc=case.bc)
+    g = wenoc.Grid(case.shape, case.dx, case.gamma, case.pinf, case.D, flux=case.flux,
+                   bc=case.bc)
+    return go, g
+
+
+CASES = {
+    "two_phase_advection": lambda: inputs.two_phase_advection_2d(n=40),
+    "five_phase_2d": SMALL_CASES["five_phase_2d"],
+    "shock_bubble_2d_ragged": SMALL_CASES["shock_bubble_2d_ragged"],
+    "spheres_3d_ragged": SMALL_CASES["spheres_3d_ragged"],
+    "slab_1d_hllc": SMALL_CASES["slab_1d_hllc"],
+}
+
+
+def _evolved(name, steps=3):
+    case = CASES[name]()
+    go, g = _grids(case)
+    U = oracle.prim_to_cons(go, case.V)
+    dt = case.meta.get("dt") if case.meta else None
+    for _ in range(steps):
+        U, _ = oracle.rk3_step(go, U, cfl=case.cfl or 0.2, dt=dt or 0.0)
+    return case, go, g, U
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_cac_rhs_parity(gpu, name):
+    case, go, g, U = _evolved(name)
+    Ud = to_dev(U)
+    g.bind(Ud).set_pf_workspace(Ud.device)
+    R = g.cac_rhs(Ud).cpu().numpy()
+    R_or, B_or, M_or = pf.cac_rhs(go, U)
+    scale = max(np.abs(R_or).max(), M_or / case.dx[0] ** 2 * 1e-3)
+    assert np.abs(R - R_or).max() <= 1e-12 * scale, (np.abs(R - R_or).max(), scale)
+    # a given mobility is used as given
+    R1 = g.cac_rhs(Ud, M=1.0).cpu().numpy()
+    R1_or, _, _ = pf.cac_rhs(go, U, M=1.0)
+    assert np.abs(R1 - R1_or).max() <= 1e-12 * np.abs(R1_or).max()
+
+
+def _face_flux(go, phi, Q):
+    """c_f (Q_b - Q_a)/dx on every coupled face, per phase and direction."""
+    out = []
+    for p in range(go.N):
+        for d, (cf, a, b) in enumerate(pf.face_coefficients(go, phi[p])):
+            q = Q[p].reshape(-1)
+            on = cf > 0.0
+            out.append(cf[on] * (q[b[on]] - q[a[on]]) / go.dx[d])
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("name", ["two_phase_advection", "five_phase_2d",
+                                  "shock_bubble_2d_ragged", "spheres_3d_ragged"])
+def test_qmap_solution(gpu, name):
+    """The GPU's Q solves the oracle's discrete Eq. 4 (the region-consistent
+    right-hand side) to the requested tolerance, and its face fluxes
+    c_f grad Q agree with the oracle's exact solution."""
+    case, go, g, U = _evolved(name, steps=5)
+    Ud = to_dev(U)
+    g.bind(Ud).set_pf_workspace(Ud.device)
+    R = g.cac_rhs(Ud)
+    Q, iters, res = g.qmap(Ud, tol=1e-13)
+    assert res <= 1e-13 and iters > 0
+    Q = Q.cpu().numpy()
+    phi = pf.fractions(go, U)
+    R_or, _, _ = pf.cac_rhs(go, U)
+    Q_or, Rp = pf.qmap(go, phi, R_or)
+    for p in range(go.N):
+        A, _ = pf.qmap_operator(go, phi[p])
+        AQ = A @ Q[p].reshape(-1)
+        assert np.abs(AQ - Rp[p].reshape(-1)).max() <= 1e-9 * max(np.abs(R_or).max(), 1e-300)
+    F, F_or = _face_flux(go, phi, Q), _face_flux(go, phi, Q_or)
+    assert np.abs(F - F_or).max() <= 1e-8 * max(np.abs(F_or).max(), 1e-300)
+
+
+@pytest.mark.parametrize("qscale", [1.0, 1e4])
+@pytest.mark.parametrize("name", ["two_phase_advection", "five_phase_2d", "spheres_3d_ragged"])
+def test_pf_step_parity_with_common_q(gpu, name, qscale):
+    """The Phase-Field step (SSP-RK3 of Eq. 5, gradients limited for dt) with
+    the oracle's Q on both sides: 1e-12.  Q x 1e4 makes the gradient limit
+    act on most coupled faces, in every direction's sweep."""
+    case, go, g, U = _evolved(name)
+    R_or, _, _ = pf.cac_rhs(go, U)
+    Q, _ = pf.qmap(go, pf.fractions(go, U), R_or)
+    Q = Q * qscale
+    dt = 1e-3 if name == "two_phase_advection" else 0.5 * oracle.rk3_step(go, U, cfl=0.2)[1]
+    Un = pf.pf_step(go, U, Q, dt)
+    Ud = to_dev(U)
+    g.bind(Ud)
+    g.pf_step(to_dev(Q), dt)
+    g.sync_status()
+    err = state_err(Ud.cpu().numpy(), Un, case.N, case.dim)
+    assert (err <= 1e-12).all(), err
+
+
+def test_full_steps_match_oracle(gpu):
+    """Ten time steps of Sec. 2.2 (hyperbolic, Eq. 28, Eq. 4, Phase-Field) on
+    the Sec. 4.1.1 layout, 40^2: the states agree to the Q-map's accuracy."""
+    case = inputs.two_phase_advection_2d(n=40)
+    go, g = _grids(case)
+    U = oracle.prim_to_cons(go, case.V)
+    Ud = to_dev(U)
+    g.bind(Ud).set_pf_workspace(Ud.device)
+    for _ in range(10):
+        U, _, _ = pf.full_step(go, U, dt=case.meta["dt"])
+        g.step(dt=case.meta["dt"], tol=1e-13)
+    g.sync_status()
+    err = state_err(Ud.cpu().numpy(), U, case.N, case.dim)
+    assert (err <= 1e-9).all(), err
+
+
+def test_full_steps_keep_invariants_and_the_equilibrium_band(gpu):
+    """Sec. 4.1.1 air circle on the paper's 100^2 grid, one period (1000
+    steps) with the mechanism: each phase's mass and fraction, momentum and
+    energy conserved, fractions within rounding of [0, 1] summing to one, and
+    the 0.05 < phi < 0.95 band at the equilibrium width (4.16 cells around
+    the radius of 20 cells: 2 pi 20 x 4.16 = 523 cells)."""
+    case = inputs.two_phase_advection_2d(n=100)
+    go, g = _grids(case)
+    Ud = to_dev(oracle.prim_to_cons(go, case.V))
+    g.bind(Ud).set_pf_workspace(Ud.device)
+    tot0 = Ud.sum(dim=(1, 2))
+    g.step(dt=case.meta["dt"], nsteps=1000, tol=1e-10)
+    g.sync_status()
+    tot = Ud.sum(dim=(1, 2))
+    scale = Ud.abs().sum(dim=(1, 2))
+    assert ((tot - tot0).abs() <= 1e-11 * scale).all()
+    a = Ud[5:7]
+    assert a.min().item() >= -1e-10 and a.max().item() <= 1 + 1e-10
+    assert (a.sum(0) - 1).abs().max().item() < 1e-12
+    band = int(((a[0] > 0.05) & (a[0] < 0.95)).sum().item())
+    expect = 2 * np.pi * 20 * 2 * np.sqrt(2) * np.arctanh(0.9)
+    assert 0.85 * expect <= band <= 1.15 * expect, (band, expect)
+    V = g.cons_to_prim(Ud).cpu().numpy()
+    assert np.abs(V[2:4] - 1.0).max() < 1e-9
