@@ -174,8 +174,9 @@ wc_status wc_rhs_pf(wc_grid *g, const double *U_dev, const double *Q_dev, double
  * the rest is solved by conjugate gradients preconditioned with D; only the
  * face gradients of coupled faces are used (wc_rhs_pf). */
 
-/* Device scratch of the mechanism: ten [N][ncell] FP64 fields, one
- * [N][ncell] int32 field and about 0.5 MB of reduction partials. */
+/* Device scratch of the mechanism: thirteen [N][ncell] FP64 fields, one
+ * [N][ncell] int32 field and about 0.3 MB of reduction partials; grids up to
+ * 2^30 cells (WC_ERR_UNSUPPORTED beyond). */
 size_t wc_pf_workspace_bytes(const wc_grid *g);
 /* Binds that scratch (256-byte aligned, at least wc_pf_workspace_bytes). */
 wc_status wc_set_pf_workspace(wc_grid *g, void *ws_dev, size_t bytes);
@@ -188,22 +189,25 @@ wc_status wc_cac_rhs(wc_grid *g, const double *U_dev, double eta, double M, doub
                      void *stream);
 
 /* Q_dev ([N][ncell]) of Eq. 4 for the fractions of U_dev and the right-hand
- * sides R_dev (null: those of the last wc_cac_rhs).  Conjugate gradients stop
- * when every phase has sqrt(r.z / r0.z0) <= tol (D-weighted residual) or
- * after maxit iterations; *iters and *resid (may be null) report them.
- * Synchronizes stream (the region labelling and the stopping test read
- * device flags).  The values of Q are fixed up to a constant per region;
- * the region sums use FP64 atomics, so Q varies at rounding level between
- * runs. */
+ * sides R_dev (null: those of the last wc_cac_rhs).  warm != 0: Q_dev holds a
+ * starting guess (e.g. the previous step's Q), else the iteration starts
+ * from 0.  Conjugate gradients stop when every phase has sqrt(r.z / b.b/D)
+ * <= tol (the D-weighted residual relative to the right-hand side b) or
+ * after maxit iterations (checked every 25); *iters and *resid (may be null)
+ * report them.  Synchronizes stream (the region labelling and the stopping
+ * test read device flags).  The values of Q are fixed up to a constant per
+ * region; the region sums use FP64 atomics, so Q varies at rounding level
+ * between runs. */
 wc_status wc_qmap(wc_grid *g, const double *U_dev, const double *R_dev, double *Q_dev,
-                  double tol, int maxit, int *iters, double *resid, void *stream);
+                  double tol, int maxit, int warm, int *iters, double *resid, void *stream);
 
 /* The Phase-Field step (Eq. 5) over dt on the bound state: SSP-RK3 with Q
  * fixed, face gradients limited to dx / (12 d dt). */
 wc_status wc_pf_step(wc_grid *g, const double *Q_dev, double dt, void *stream);
 
 /* nsteps full time steps on the bound state (wc_rk_step, wc_cac_rhs with the
- * default eta and M, wc_qmap with tol and maxit, wc_pf_step with the same
+ * default eta and M, wc_qmap with tol and maxit started from the previous
+ * step's Q after the first step of a bound scratch, wc_pf_step with the same
  * time step: dt_fixed, or cfl over the hyperbolic step's rate).  Needs both
  * workspaces; synchronizes stream once per step (wc_qmap).  *dt_host (may be
  * null) receives the last time step. */

@@ -46,8 +46,7 @@ struct wc_grid {
   bool pf_bound = false;
   PfWork pw;
   PfGeom pg;
-  double* Qbuf = nullptr;
-  int pf_iters = 0, pf_label_rounds = 0;
+  int pf_iters = 0, pf_label_rounds = 0, pf_have_q = 0;
   double pf_resid = 0.0;
 };
 
@@ -489,23 +488,27 @@ extern "C" size_t wc_pf_workspace_bytes(const wc_grid* g) {
   if (!g) return 0;
   const size_t f = align256(sizeof(double) * (size_t)g->d.nphase * g->ncell);
   const size_t li = align256(sizeof(int) * (size_t)g->d.nphase * g->ncell);
-  // R c D sumR sumD r z p q Qbuf, labels, partials, scalars, flags
-  return 10 * f + li + align256(sizeof(double) * pf_part_doubles()) + 256 + 256;
+  // R c D 1/D sumR sumD x r p q, three face-weight fields, labels,
+  // partials, scalars, flags
+  return 13 * f + li + align256(sizeof(double) * pf_part_doubles()) + 256 + 256;
 }
 
 extern "C" wc_status wc_set_pf_workspace(wc_grid* g, void* ws_dev, size_t bytes) {
   if (!g || !ws_dev) return WC_ERR_ARG;
   if ((reinterpret_cast<uintptr_t>(ws_dev) & 255) != 0) return fail(g, WC_ERR_ARG, "workspace not 256-byte aligned");
   if (bytes < wc_pf_workspace_bytes(g)) return fail(g, WC_ERR_ARG, "pf workspace too small");
+  if (g->ncell > 2147483647L / 2) return fail(g, WC_ERR_UNSUPPORTED, "pf mechanism: grid too large");
   const size_t f = align256(sizeof(double) * (size_t)g->d.nphase * g->ncell);
   const size_t li = align256(sizeof(int) * (size_t)g->d.nphase * g->ncell);
   char* w = static_cast<char*>(ws_dev);
-  double** fields[] = {&g->pw.R, &g->pw.c, &g->pw.D, &g->pw.sumR, &g->pw.sumD,
-                       &g->pw.r, &g->pw.z, &g->pw.p, &g->pw.q, &g->Qbuf};
+  double** fields[] = {&g->pw.R, &g->pw.c, &g->pw.D, &g->pw.Dinv, &g->pw.sumR, &g->pw.sumD,
+                       &g->pw.x, &g->pw.r, &g->pw.p, &g->pw.q};
   for (double** d : fields) {
     *d = reinterpret_cast<double*>(w);
     w += f;
   }
+  g->pw.w = reinterpret_cast<double*>(w);  // [3][N][ncell]
+  w += 3 * f;
   g->pw.lab = reinterpret_cast<int*>(w);
   w += li;
   g->pw.part = reinterpret_cast<double*>(w);
@@ -527,6 +530,7 @@ extern "C" wc_status wc_set_pf_workspace(wc_grid* g, void* ws_dev, size_t bytes)
   pg.nv = g->nv;
   pg.a0 = g->d.nphase + g->d.dim + 1;
   g->pf_bound = true;
+  g->pf_have_q = 0;
   return WC_OK;
 }
 
@@ -550,12 +554,15 @@ extern "C" wc_status wc_cac_rhs(wc_grid* g, const double* U, double eta, double 
 }
 
 // Eq. 4 for the fractions of U and the right-hand sides R ([N][ncell];
-// null: those of the last wc_cac_rhs); Q receives the solution.
+// null: those of the last wc_cac_rhs); Q receives the solution (and holds
+// the start when warm); Q may be the iterate buffer itself.
 static wc_status qmap(wc_grid* g, const double* U, const double* R, double* Q, double tol,
-                      int maxit, cudaStream_t st) {
+                      int maxit, int warm, cudaStream_t st) {
   const size_t fb = sizeof(double) * (size_t)g->d.nphase * g->ncell;
   cudaError_t e = cudaSuccess;
   if (R && R != g->pw.R) e = cudaMemcpyAsync(g->pw.R, R, fb, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && warm && Q != g->pw.x)
+    e = cudaMemcpyAsync(g->pw.x, Q, fb, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = pf_qmap_setup(U, g->pg, g->pw, st);
   if (e != cudaSuccess) return cuda_fail(g, e, "qmap setup");
   // label rounds until one changes nothing (at most ncell rounds: every
@@ -574,39 +581,47 @@ static wc_status qmap(wc_grid* g, const double* U, const double* R, double* Q, d
     if (rounds > g->ncell + LR) return fail(g, WC_ERR_STATE, "qmap labels did not settle");
   }
   g->pf_label_rounds = rounds;
-  e = pf_qmap_project(g->pg, g->pw, Q, st);
+  e = pf_qmap_project(g->pg, g->pw, warm, tol * tol, st);
   if (e != cudaSuccess) return cuda_fail(g, e, "qmap project");
   const int CR = 25;
   const int N = g->d.nphase;
   int it = 0;
   int flags[8] = {0};
-  for (; it < maxit; it += CR) {
-    e = pf_cg_rounds(g->pg, g->pw, Q, it, CR, tol * tol, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(flags, g->pw.flag, sizeof(int) * (1 + N), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(g, e, "qmap cg");
+  auto all_done = [&]() -> int {
+    cudaError_t ee =
+        cudaMemcpyAsync(flags, g->pw.flag, sizeof(int) * (1 + N), cudaMemcpyDeviceToHost, st);
+    if (ee == cudaSuccess) ee = cudaStreamSynchronize(st);
+    if (ee != cudaSuccess) return -1;
     int all = 1;
     for (int p = 0; p < N; p++) all &= flags[1 + p];
-    if (all) break;
+    return all;
+  };
+  int done = all_done();  // the start may meet the test already
+  while (done == 0 && it < maxit) {
+    e = pf_cg_rounds(g->pg, g->pw, it, CR, st);
+    if (e != cudaSuccess) return cuda_fail(g, e, "qmap cg");
+    it += CR;
+    done = all_done();
   }
+  if (done < 0) return cuda_fail(g, cudaGetLastError(), "qmap cg flags");
+  if (Q != g->pw.x) e = cudaMemcpyAsync(Q, g->pw.x, fb, cudaMemcpyDeviceToDevice, st);
   double sc[32];
-  e = cudaMemcpyAsync(sc, g->pw.scal, sizeof(sc), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sc, g->pw.scal, sizeof(sc), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(g, e, "qmap residual");
-  double res = 0.0;
+  double res = 0.0;  // sqrt(r.r/D / b.b/D): the D-weighted residual relative to b
   for (int p = 0; p < N; p++)
     if (sc[16 + p] > 0.0) res = fmax(res, sqrt(fmax(sc[24 + p], 0.0) / sc[16 + p]));
-  g->pf_iters = it + CR < maxit ? it + CR : maxit;
+  g->pf_iters = it;  // in whole rounds of CR iterations
   g->pf_resid = res;
   return WC_OK;
 }
 
 extern "C" wc_status wc_qmap(wc_grid* g, const double* U, const double* R, double* Q, double tol,
-                             int maxit, int* iters, double* resid, void* stream) {
+                             int maxit, int warm, int* iters, double* resid, void* stream) {
   if (!g || !U || !Q || !(tol > 0.0) || maxit < 1) return WC_ERR_ARG;
   if (!g->pf_bound) return fail(g, WC_ERR_STATE, "wc_qmap needs wc_set_pf_workspace");
-  wc_status s = qmap(g, U, R, Q, tol, maxit, S(stream));
+  wc_status s = qmap(g, U, R, Q, tol, maxit, warm, S(stream));
   if (s) return s;
   if (iters) *iters = g->pf_iters;
   if (resid) *resid = g->pf_resid;
@@ -639,8 +654,10 @@ extern "C" wc_status wc_step(wc_grid* g, double cfl, double dt_fixed, int nsteps
     if (r) return r;
     cudaError_t e = pf_cac(g->U, g->pg, g->pw, cell_volume(g), g->d.dx[0], -1.0, st);
     if (e != cudaSuccess) return cuda_fail(g, e, "cac_rhs");
-    if ((r = qmap(g, g->U, nullptr, g->Qbuf, tol, maxit, st))) return r;
-    if ((r = pf_stages(g, g->Qbuf, cfl, dt_fixed, st))) return r;
+    // Q in the iterate buffer, started from the previous step's Q
+    if ((r = qmap(g, g->U, nullptr, g->pw.x, tol, maxit, g->pf_have_q, st))) return r;
+    g->pf_have_q = 1;
+    if ((r = pf_stages(g, g->pw.x, cfl, dt_fixed, st))) return r;
   }
   if (dt_host) {
     if (dt_fixed > 0.0) {
@@ -665,7 +682,7 @@ extern "C" wc_status wc_pf_stats(const wc_grid* g, int* cg_iters, int* label_rou
   return WC_OK;
 }
 
-extern "C" const double* wc_pf_q(const wc_grid* g) { return g && g->pf_bound ? g->Qbuf : nullptr; }
+extern "C" const double* wc_pf_q(const wc_grid* g) { return g && g->pf_bound ? g->pw.x : nullptr; }
 
 extern "C" wc_status wc_limit(const wc_grid* gc, int dir, long ncell, const double* Ubar,
                               const double* VL, const double* VR, double* UL, double* UR,

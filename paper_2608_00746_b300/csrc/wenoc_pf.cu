@@ -67,7 +67,9 @@ __global__ void __launch_bounds__(PF_THREADS) k_cac_reduce(const double* __restr
 #pragma unroll
     for (int p = 0; p < N; p++) rho += U[(long)p * n + i];
     double u2 = 0.0;
-    for (int j = 0; j < g.dim; j++) {
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      if (j >= g.dim) break;
       const double u = U[(long)(N + j) * n + i] / rho;
       u2 += u * u;
     }
@@ -179,16 +181,15 @@ __global__ void __launch_bounds__(PF_THREADS) k_cac_rhs(const double* __restrict
       gp[p] = gprime(phi[p]);
       sg += gp[p];
     }
-    long nb[3][2];
-    for (int ax = 0; ax < g.dim; ax++) {
-      nb[ax][0] = pf_nbr(g, i, ax, -1);
-      nb[ax][1] = pf_nbr(g, i, ax, +1);
-    }
+    int nb[3][2];
+    pf_stencil(g, (int)i, nb);
 #pragma unroll
     for (int p = 0; p < N; p++) {
       const double* f = U + (long)(g.a0 + p) * n;
       double lap = 0.0;
-      for (int ax = 0; ax < g.dim; ax++) {
+#pragma unroll
+      for (int ax = 0; ax < 3; ax++) {
+        if (ax >= g.dim) break;
         const double fm = nb[ax][0] >= 0 ? f[nb[ax][0]] : phi[p];
         const double fp = nb[ax][1] >= 0 ? f[nb[ax][1]] : phi[p];
         lap += (fp - 2.0 * phi[p] + fm) * g.idx2[ax];
@@ -217,30 +218,58 @@ __global__ void __launch_bounds__(PF_THREADS) k_qm_coef(const double* __restrict
   }
 }
 
-// D_i = sum_faces c_f / dx^2 and the initial labels (own index where D > 0).
+// Face weights w_ax = c_f / dx^2 of the face above each cell along each
+// axis (0 where a reflective or outflow side ends the axis), the coupling
+// D_i = sum_faces c_f / dx^2 (the same weights summed), 1/D (0 where D = 0)
+// and the initial labels (own index where D > 0).
 template <int N>
 __global__ void __launch_bounds__(PF_THREADS) k_qm_diag(PfGeom g, const double* __restrict__ c,
-                                                        double* __restrict__ D, int* lab) {
-  const long n = g.ncell;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long)gridDim.x * blockDim.x) {
-    long nb[3][2];
-    for (int ax = 0; ax < g.dim; ax++) {
-      nb[ax][0] = pf_nbr(g, i, ax, -1);
-      nb[ax][1] = pf_nbr(g, i, ax, +1);
-    }
+                                                        double* __restrict__ w,
+                                                        double* __restrict__ D,
+                                                        double* __restrict__ Dinv, int* lab) {
+  const int n = (int)g.ncell;
+  const long nn = (long)N * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int nb[3][2];
+    pf_stencil(g, i, nb);
 #pragma unroll
     for (int p = 0; p < N; p++) {
       const double* cp = c + (long)p * n;
       const double ci = cp[i];
       double d = 0.0;
-      for (int ax = 0; ax < g.dim; ax++)
-        for (int s = 0; s < 2; s++)
-          if (nb[ax][s] >= 0) d += 0.5 * (ci + cp[nb[ax][s]]) * g.idx2[ax];
+#pragma unroll
+      for (int ax = 0; ax < 3; ax++) {
+        if (ax >= g.dim) break;
+        const int jm = nb[ax][0], jp = nb[ax][1];
+        const double wm = jm >= 0 ? 0.5 * (cp[jm] + ci) * g.idx2[ax] : 0.0;
+        const double wp = jp >= 0 ? 0.5 * (ci + cp[jp]) * g.idx2[ax] : 0.0;
+        w[ax * nn + (long)p * n + i] = wp;
+        d += wm + wp;
+      }
       D[(long)p * n + i] = d;
-      lab[(long)p * n + i] = d > 0.0 ? (int)i : -1;
+      Dinv[(long)p * n + i] = d > 0.0 ? 1.0 / d : 0.0;
+      lab[(long)p * n + i] = d > 0.0 ? i : -1;
     }
   }
+}
+
+// (K v)_i = D_i v_i - sum_faces w_f v_nbr with K = -A (positive
+// semi-definite), from the stored face weights.
+template <int N>
+__device__ __forceinline__ double k_apply(const PfGeom& g, const int (&nb)[3][2], int i, long o,
+                                          long nn, const double* __restrict__ w,
+                                          const double* __restrict__ D,
+                                          const double* __restrict__ v) {
+  double s = D[o + i] * v[o + i];
+#pragma unroll
+  for (int ax = 0; ax < 3; ax++) {
+    if (ax >= g.dim) break;
+    const double* wa = w + ax * nn + o;
+    const int jm = nb[ax][0], jp = nb[ax][1];
+    if (jp >= 0) s = fma(-wa[i], v[o + jp], s);
+    if (jm >= 0) s = fma(-wa[jm], v[o + jm], s);
+  }
+  return s;
 }
 
 // One round of minimum-label propagation over coupled faces with pointer
@@ -250,15 +279,11 @@ __global__ void __launch_bounds__(PF_THREADS) k_qm_diag(PfGeom g, const double* 
 template <int N>
 __global__ void __launch_bounds__(PF_THREADS) k_qm_label(PfGeom g, const double* __restrict__ c,
                                                          int* lab, int* flag) {
-  const long n = g.ncell;
+  const int n = (int)g.ncell;
   int changed = 0;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long)gridDim.x * blockDim.x) {
-    long nb[3][2];
-    for (int ax = 0; ax < g.dim; ax++) {
-      nb[ax][0] = pf_nbr(g, i, ax, -1);
-      nb[ax][1] = pf_nbr(g, i, ax, +1);
-    }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int nb[3][2];
+    pf_stencil(g, i, nb);
 #pragma unroll
     for (int p = 0; p < N; p++) {
       int* lp = lab + (long)p * n;
@@ -267,11 +292,15 @@ __global__ void __launch_bounds__(PF_THREADS) k_qm_label(PfGeom g, const double*
       const double* cp = c + (long)p * n;
       const double ci = cp[i];
       int m = li;
-      for (int ax = 0; ax < g.dim; ax++)
+#pragma unroll
+      for (int ax = 0; ax < 3; ax++) {
+        if (ax >= g.dim) break;
+#pragma unroll
         for (int s = 0; s < 2; s++) {
-          const long j = nb[ax][s];
+          const int j = nb[ax][s];
           if (j >= 0 && (ci > 0.0 || cp[j] > 0.0)) m = min(m, __ldcg(lp + j));
         }
+      }
       m = min(m, __ldcg(lp + m));
       if (m < li) {
         atomicMin(lp + i, m);
@@ -287,9 +316,8 @@ __global__ void __launch_bounds__(PF_THREADS) k_qm_sums(PfGeom g, const double* 
                                                         const double* __restrict__ D,
                                                         const int* __restrict__ lab, double* sumR,
                                                         double* sumD) {
-  const long n = g.ncell;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long)gridDim.x * blockDim.x) {
+  const int n = (int)g.ncell;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
 #pragma unroll
     for (int p = 0; p < N; p++) {
       const int l = lab[(long)p * n + i];
@@ -300,202 +328,223 @@ __global__ void __launch_bounds__(PF_THREADS) k_qm_sums(PfGeom g, const double* 
   }
 }
 
-// Offsets into the partials buffer.
+// Offsets into the partials buffer: Eq. 28 totals [PF_BLOCKS][32]; p . K p
+// [PF_BLOCKS][8]; r . z [2 parities][PF_BLOCKS][8]; b . b/D [PF_BLOCKS][8].
 constexpr long PART_CAC = 0;
 constexpr long PART_PQ = (long)PF_BLOCKS * 32;
-constexpr long PART_RZ = PART_PQ + (long)PF_BLOCKS * 8;  // [2][PF_BLOCKS][8]
-constexpr long PART_TOTAL = PART_RZ + 2L * PF_BLOCKS * 8;
+constexpr long PART_RZ = PART_PQ + (long)PF_BLOCKS * 8;
+constexpr long PART_REF = PART_RZ + 2L * PF_BLOCKS * 8;
+constexpr long PART_TOTAL = PART_REF + (long)PF_BLOCKS * 8;
 
-// Right-hand side of K Q = b with K = -A (positive semi-definite): b = -(r -
-// D s_k) on cells with a label; conjugate-gradient start x = 0.
+// Sums of the per-block partials [PF_BLOCKS][8] of N phases, the same in
+// every block and in a fixed order: thread t adds blocks t, t + 256, ...
+// (parallel loads), then the block tree of block_sum_to.
+template <int N>
+__device__ __forceinline__ void sum_partials(const double* part, long off, double* out) {
+  double v[N];
+#pragma unroll
+  for (int p = 0; p < N; p++) v[p] = 0.0;
+  for (int b = threadIdx.x; b < PF_BLOCKS; b += PF_THREADS) {
+#pragma unroll
+    for (int p = 0; p < N; p++) v[p] += part[off + (long)b * 8 + p];
+  }
+  block_sum_to<N>(v, out);
+}
+
+// K Q = b with K = -A (positive semi-definite): b = -(r - D s_k) on cells
+// with a label.  Start x0 = 0, or (warm) the x given; r0 = b - K x0.
+// Partials of r0 . r0/D (parity 0) and of the reference b . b/D of the
+// stopping test.
 template <int N>
 __global__ void __launch_bounds__(PF_THREADS) k_cg_init(PfGeom g, const double* __restrict__ R,
+                                                        const double* __restrict__ w,
                                                         const double* __restrict__ D,
+                                                        const double* __restrict__ Dinv,
                                                         const int* __restrict__ lab,
                                                         const double* __restrict__ sumR,
                                                         const double* __restrict__ sumD,
-                                                        double* x, double* r, double* z, double* pv,
-                                                        double* part) {
-  const long n = g.ncell;
-  double acc[N];
+                                                        double* x, double* r, double* part,
+                                                        int warm) {
+  const int n = (int)g.ncell;
+  const long nn = (long)N * n;
+  double acc[N], ref[N];
 #pragma unroll
-  for (int p = 0; p < N; p++) acc[p] = 0.0;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long)gridDim.x * blockDim.x) {
+  for (int p = 0; p < N; p++) acc[p] = ref[p] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int nb[3][2];
+    pf_stencil(g, i, nb);
 #pragma unroll
     for (int p = 0; p < N; p++) {
-      const long k = (long)p * n + i;
+      const long o = (long)p * n, k = o + i;
       const int l = lab[k];
-      double b = 0.0, zz = 0.0;
+      double b = 0.0, rr = 0.0;
       if (l >= 0) {
-        const double s = sumR[(long)p * n + l] / sumD[(long)p * n + l];
+        const double s = sumR[o + l] / sumD[o + l];
         b = -(R[k] - D[k] * s);
-        zz = b / D[k];
+        rr = warm ? b - k_apply<N>(g, nb, i, o, nn, w, D, x) : b;
+        ref[p] += b * (b * Dinv[k]);
       }
-      x[k] = 0.0;
-      r[k] = b;
-      z[k] = zz;
-      pv[k] = zz;
-      acc[p] += b * zz;
+      r[k] = rr;
+      acc[p] += rr * (rr * Dinv[k]);
     }
   }
+  if (!warm) {
+    // x0 = 0 (no block reads x when cold)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+#pragma unroll
+      for (int p = 0; p < N; p++) x[(long)p * n + i] = 0.0;
+  }
   block_sum_to<N>(acc, part + PART_RZ + (long)blockIdx.x * 8);  // parity 0
+  block_sum_to<N>(ref, part + PART_REF + (long)blockIdx.x * 8);
 }
 
-// rz0 per phase (one block): the start of the convergence test; a phase
-// with rz0 = 0 (nothing to solve) is converged from the start.
+// The reference b . b/D and r0 . r0/D per phase and tol^2 into scal (one
+// block); a phase whose start already meets the test is converged.
 template <int N>
-__global__ void k_cg_start(const double* part, double* scal, int* flag) {
+__global__ void __launch_bounds__(PF_THREADS) k_cg_start(const double* part, double* scal,
+                                                         int* flag, double tol2) {
+  __shared__ double rz[N], ref[N];
+  sum_partials<N>(part, PART_RZ, rz);
+  sum_partials<N>(part, PART_REF, ref);
   const int p = threadIdx.x;
+  if (p == 0) scal[8] = tol2;
   if (p >= N) return;
-  double s = 0.0;
-  for (int b = 0; b < PF_BLOCKS; b++) s += part[PART_RZ + (long)b * 8 + p];
-  scal[16 + p] = s;
-  scal[24 + p] = s;
-  flag[1 + p] = !(s > 0.0);
+  scal[16 + p] = ref[p];
+  scal[24 + p] = rz[p];
+  flag[1 + p] = !(rz[p] > tol2 * ref[p]);
 }
 
-__device__ __forceinline__ bool all_converged(const int* flag, int N) {
-  int all = 1;
-  for (int p = 0; p < N; p++) all &= flag[1 + p];
-  return all;
-}
-
-// q = K p and the partial sums of p . q.
+// Iteration it, step 1: rz_it = r . r/D (partials of parity it & 1); a
+// phase is live while rz_it > tol^2 b.b/D (every block decides alike from
+// the same fixed-order sums; block 0 records the decision in flag for the
+// next two kernels and the host).  Live phases: p = r/D + beta p, beta =
+// rz_it / rz_{it-1} (p = r/D at it = 0).
 template <int N>
-__global__ void __launch_bounds__(PF_THREADS) k_cg_matvec(PfGeom g, const double* __restrict__ c,
+__global__ void __launch_bounds__(PF_THREADS) k_cg_dir(PfGeom g, const double* __restrict__ r,
+                                                       const double* __restrict__ Dinv, double* pv,
+                                                       const double* part, double* scal, int* flag,
+                                                       int it) {
+  __shared__ double rn[N], ro[N];
+  sum_partials<N>(part, PART_RZ + (long)(it & 1) * PF_BLOCKS * 8, rn);
+  sum_partials<N>(part, PART_RZ + (long)((it + 1) & 1) * PF_BLOCKS * 8, ro);
+  const double tol2 = scal[8];
+  bool live[N], any = false;
+  double beta[N];
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    live[p] = rn[p] > tol2 * scal[16 + p];
+    any = any || live[p];
+    beta[p] = (it > 0 && ro[p] > 0.0) ? rn[p] / ro[p] : 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < N) {
+    scal[24 + threadIdx.x] = rn[threadIdx.x];
+    flag[1 + threadIdx.x] = !live[threadIdx.x];
+  }
+  if (!any) return;
+  const int n = (int)g.ncell;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      if (!live[p]) continue;
+      const long k = (long)p * n + i;
+      const double zk = r[k] * Dinv[k];
+      pv[k] = it > 0 ? fma(beta[p], pv[k], zk) : zk;
+    }
+  }
+}
+
+// Step 2: q = K p for the live phases, and the partials of p . q.
+template <int N>
+__global__ void __launch_bounds__(PF_THREADS) k_cg_matvec(PfGeom g, const double* __restrict__ w,
+                                                          const double* __restrict__ D,
                                                           const double* __restrict__ pv,
                                                           double* __restrict__ q, double* part,
                                                           const int* flag) {
-  if (all_converged(flag, N)) return;
-  const long n = g.ncell;
+  bool live[N], any = false;
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    live[p] = !flag[1 + p];
+    any = any || live[p];
+  }
+  if (!any) return;
+  const int n = (int)g.ncell;
+  const long nn = (long)N * n;
   double acc[N];
 #pragma unroll
   for (int p = 0; p < N; p++) acc[p] = 0.0;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long)gridDim.x * blockDim.x) {
-    long nb[3][2];
-    for (int ax = 0; ax < g.dim; ax++) {
-      nb[ax][0] = pf_nbr(g, i, ax, -1);
-      nb[ax][1] = pf_nbr(g, i, ax, +1);
-    }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int nb[3][2];
+    pf_stencil(g, i, nb);
 #pragma unroll
     for (int p = 0; p < N; p++) {
-      const double* cp = c + (long)p * n;
-      const double* pp = pv + (long)p * n;
-      const double ci = cp[i], pi = pp[i];
-      double s = 0.0;
-      for (int ax = 0; ax < g.dim; ax++)
-        for (int k = 0; k < 2; k++) {
-          const long j = nb[ax][k];
-          if (j >= 0) s += 0.5 * (ci + cp[j]) * g.idx2[ax] * (pi - pp[j]);
-        }
-      q[(long)p * n + i] = s;
-      acc[p] += pi * s;
+      if (!live[p]) continue;
+      const long o = (long)p * n;
+      const double s = k_apply<N>(g, nb, i, o, nn, w, D, pv);
+      q[o + i] = s;
+      acc[p] = fma(pv[o + i], s, acc[p]);
     }
   }
   block_sum_to<N>(acc, part + PART_PQ + (long)blockIdx.x * 8);
 }
 
-// Sum of one column of partials (every block the same fixed order).
-__device__ __forceinline__ void sum_partials(const double* part, long off, int N, double* out) {
-  if (threadIdx.x < N) {
-    double s = 0.0;
-    for (int b = 0; b < PF_BLOCKS; b++) s += part[off + (long)b * 8 + threadIdx.x];
-    out[threadIdx.x] = s;
-  }
-  __syncthreads();
-}
-
-// x += alpha p, r -= alpha q, z = r / D; partial sums of r . z into the
-// buffer of parity (it + 1) % 2.
+// Step 3: alpha = rz_it / p . q; x += alpha p, r -= alpha q; partials of
+// r . r/D into parity (it + 1) & 1 (for every phase, so a converged phase
+// keeps its test).
 template <int N>
-__global__ void __launch_bounds__(PF_THREADS) k_cg_update(PfGeom g, const double* __restrict__ D,
-                                                          const int* __restrict__ lab, double* x,
-                                                          double* r, double* z,
+__global__ void __launch_bounds__(PF_THREADS) k_cg_update(PfGeom g,
+                                                          const double* __restrict__ Dinv,
+                                                          double* x, double* r,
                                                           const double* __restrict__ pv,
                                                           const double* __restrict__ q,
                                                           double* part, const int* flag, int it) {
-  if (all_converged(flag, N)) return;
-  __shared__ double pq[N], rz[N];
-  sum_partials(part, PART_PQ, N, pq);
-  sum_partials(part, PART_RZ + (long)(it & 1) * PF_BLOCKS * 8, N, rz);
+  __shared__ double pq[N], rn[N];
+  sum_partials<N>(part, PART_PQ, pq);
+  sum_partials<N>(part, PART_RZ + (long)(it & 1) * PF_BLOCKS * 8, rn);
+  bool live[N], any = false;
   double alpha[N];
-  bool live[N];
 #pragma unroll
   for (int p = 0; p < N; p++) {
     live[p] = !flag[1 + p] && pq[p] > 0.0;
-    alpha[p] = live[p] ? rz[p] / pq[p] : 0.0;
+    any = any || live[p];
+    alpha[p] = live[p] ? rn[p] / pq[p] : 0.0;
   }
-  const long n = g.ncell;
+  if (!any) {
+    // nothing moves: r . r/D of the next iteration is this one's (copied
+    // exactly, block by block, so the next test sums the same values)
+    if (threadIdx.x < N)
+      part[PART_RZ + (long)((it + 1) & 1) * PF_BLOCKS * 8 + (long)blockIdx.x * 8 + threadIdx.x] =
+          part[PART_RZ + (long)(it & 1) * PF_BLOCKS * 8 + (long)blockIdx.x * 8 + threadIdx.x];
+    return;
+  }
+  const int n = (int)g.ncell;
   double acc[N];
 #pragma unroll
   for (int p = 0; p < N; p++) acc[p] = 0.0;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long)gridDim.x * blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
 #pragma unroll
     for (int p = 0; p < N; p++) {
       const long k = (long)p * n + i;
-      if (lab[k] < 0) continue;
-      double rk = r[k], zk = z[k];
+      double rk = r[k];
       if (live[p]) {
         x[k] = fma(alpha[p], pv[k], x[k]);
         rk = fma(-alpha[p], q[k], rk);
-        zk = rk / D[k];
         r[k] = rk;
-        z[k] = zk;
       }
-      acc[p] += rk * zk;
+      acc[p] = fma(rk, rk * Dinv[k], acc[p]);
     }
   }
   block_sum_to<N>(acc, part + PART_RZ + (long)((it + 1) & 1) * PF_BLOCKS * 8 + (long)blockIdx.x * 8);
 }
 
-// p = z + beta p, beta = rz_new / rz_old; block 0 records rz_new and marks
-// the phases whose rz_new <= tol2 rz0 as converged.
-template <int N>
-__global__ void __launch_bounds__(PF_THREADS) k_cg_dir(PfGeom g, const double* __restrict__ z,
-                                                       const int* __restrict__ lab, double* pv,
-                                                       const double* part, double* scal, int* flag,
-                                                       int it, double tol2) {
-  if (all_converged(flag, N)) return;
-  __shared__ double rn[N], ro[N];
-  sum_partials(part, PART_RZ + (long)((it + 1) & 1) * PF_BLOCKS * 8, N, rn);
-  sum_partials(part, PART_RZ + (long)(it & 1) * PF_BLOCKS * 8, N, ro);
-  double beta[N];
-  bool live[N];
-#pragma unroll
-  for (int p = 0; p < N; p++) {
-    live[p] = !flag[1 + p] && ro[p] > 0.0;
-    beta[p] = live[p] ? rn[p] / ro[p] : 0.0;
-  }
-  const long n = g.ncell;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int p = 0; p < N; p++) {
-      const long k = (long)p * n + i;
-      if (live[p] && lab[k] >= 0) pv[k] = fma(beta[p], pv[k], z[k]);
-    }
-  }
-  if (blockIdx.x == 0 && threadIdx.x < N) {
-    const int p = threadIdx.x;
-    if (!flag[1 + p]) {
-      scal[24 + p] = rn[p];
-      if (!(rn[p] > tol2 * scal[16 + p])) flag[1 + p] = 1;
-    }
-  }
-}
-
 // ------------------------------------------------------------------ launchers
-#define PF_DISPATCH(N, call)                   \
-  switch (N) {                                 \
+#define PF_DISPATCH(N, call)                       \
+  switch (N) {                                     \
     case 1: { constexpr int N_ = 1; call; break; } \
     case 2: { constexpr int N_ = 2; call; break; } \
     case 3: { constexpr int N_ = 3; call; break; } \
     case 4: { constexpr int N_ = 4; call; break; } \
     case 5: { constexpr int N_ = 5; call; break; } \
-    default: return cudaErrorInvalidValue;     \
+    default: return cudaErrorInvalidValue;         \
   }
 
 static int pf_grid(long n) {
@@ -516,7 +565,7 @@ cudaError_t pf_cac(const double* U, const PfGeom& g, const PfWork& w, double vol
 cudaError_t pf_qmap_setup(const double* U, const PfGeom& g, const PfWork& w, cudaStream_t st) {
   const int nb = pf_grid(g.ncell);
   PF_DISPATCH(g.N, (k_qm_coef<N_><<<nb, PF_THREADS, 0, st>>>(U, g, w.c)));
-  PF_DISPATCH(g.N, (k_qm_diag<N_><<<nb, PF_THREADS, 0, st>>>(g, w.c, w.D, w.lab)));
+  PF_DISPATCH(g.N, (k_qm_diag<N_><<<nb, PF_THREADS, 0, st>>>(g, w.c, w.w, w.D, w.Dinv, w.lab)));
   return cudaGetLastError();
 }
 
@@ -529,30 +578,29 @@ cudaError_t pf_label_rounds(const PfGeom& g, const PfWork& w, int rounds, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t pf_qmap_project(const PfGeom& g, const PfWork& w, double* Q, cudaStream_t st) {
+cudaError_t pf_qmap_project(const PfGeom& g, const PfWork& w, int warm, double tol2,
+                            cudaStream_t st) {
   const size_t bytes = sizeof(double) * (size_t)g.N * g.ncell;
   cudaError_t e = cudaMemsetAsync(w.sumR, 0, bytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.sumD, 0, bytes, st);
   if (e != cudaSuccess) return e;
   const int nb = pf_grid(g.ncell);
   PF_DISPATCH(g.N, (k_qm_sums<N_><<<nb, PF_THREADS, 0, st>>>(g, w.R, w.D, w.lab, w.sumR, w.sumD)));
-  PF_DISPATCH(g.N, (k_cg_init<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(g, w.R, w.D, w.lab, w.sumR,
-                                                                     w.sumD, Q, w.r, w.z, w.p,
-                                                                     w.part)));
-  PF_DISPATCH(g.N, (k_cg_start<N_><<<1, 32, 0, st>>>(w.part, w.scal, w.flag)));
+  PF_DISPATCH(g.N, (k_cg_init<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(
+                        g, w.R, w.w, w.D, w.Dinv, w.lab, w.sumR, w.sumD, w.x, w.r, w.part, warm)));
+  PF_DISPATCH(g.N, (k_cg_start<N_><<<1, PF_THREADS, 0, st>>>(w.part, w.scal, w.flag, tol2)));
   return cudaGetLastError();
 }
 
-cudaError_t pf_cg_rounds(const PfGeom& g, const PfWork& w, double* Q, int it0, int rounds,
-                         double tol2, cudaStream_t st) {
+cudaError_t pf_cg_rounds(const PfGeom& g, const PfWork& w, int it0, int rounds, cudaStream_t st) {
   for (int k = 0; k < rounds; k++) {
     const int it = it0 + k;
-    PF_DISPATCH(g.N, (k_cg_matvec<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(g, w.c, w.p, w.q,
+    PF_DISPATCH(g.N, (k_cg_dir<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(g, w.r, w.Dinv, w.p, w.part,
+                                                                      w.scal, w.flag, it)));
+    PF_DISPATCH(g.N, (k_cg_matvec<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(g, w.w, w.D, w.p, w.q,
                                                                          w.part, w.flag)));
     PF_DISPATCH(g.N, (k_cg_update<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(
-                          g, w.D, w.lab, Q, w.r, w.z, w.p, w.q, w.part, w.flag, it)));
-    PF_DISPATCH(g.N, (k_cg_dir<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(g, w.z, w.lab, w.p, w.part,
-                                                                      w.scal, w.flag, it, tol2)));
+                          g, w.Dinv, w.x, w.r, w.p, w.q, w.part, w.flag, it)));
   }
   return cudaGetLastError();
 }

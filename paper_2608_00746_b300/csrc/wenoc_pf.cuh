@@ -33,46 +33,45 @@ struct PfGeom {
   int N, nv, a0;     // phases, variables, row of alpha_1
 };
 
-// Neighbour of cell i along axis ax in direction s (+1 / -1), or -1 where a
+// The face neighbours of cell i (32-bit indices: the host requires ncell <
+// 2^31): nb[ax][0] below and nb[ax][1] above along each used axis, -1 where a
 // reflective or outflow side mirrors the cell onto itself (no face).
-__device__ __forceinline__ long pf_nbr(const PfGeom& g, long i, int ax, int s) {
-  const long sx = 1, sy = g.nx, sz = (long)g.nx * g.ny;
-  if (ax == 0) {
-    const int x = (int)(i % g.nx);
-    const int xn = x + s;
-    if (xn < 0) return g.per[0] ? i + (g.nx - 1) * sx : -1;
-    if (xn >= g.nx) return g.per[0] ? i - (g.nx - 1) * sx : -1;
-    return i + s * sx;
+__device__ __forceinline__ void pf_stencil(const PfGeom& g, int i, int (&nb)[3][2]) {
+  const unsigned ui = (unsigned)i, nx = (unsigned)g.nx, ny = (unsigned)g.ny;
+  const unsigned x = ui % nx, r = ui / nx;
+  nb[0][0] = x > 0u ? i - 1 : (g.per[0] ? i + g.nx - 1 : -1);
+  nb[0][1] = x + 1u < nx ? i + 1 : (g.per[0] ? i - (g.nx - 1) : -1);
+  if (g.dim > 1) {
+    const unsigned y = r % ny;
+    const int sy = g.nx;
+    nb[1][0] = y > 0u ? i - sy : (g.per[1] ? i + (g.ny - 1) * sy : -1);
+    nb[1][1] = y + 1u < ny ? i + sy : (g.per[1] ? i - (g.ny - 1) * sy : -1);
   }
-  if (ax == 1) {
-    const int y = (int)((i / g.nx) % g.ny);
-    const int yn = y + s;
-    if (yn < 0) return g.per[1] ? i + (long)(g.ny - 1) * sy : -1;
-    if (yn >= g.ny) return g.per[1] ? i - (long)(g.ny - 1) * sy : -1;
-    return i + s * sy;
+  if (g.dim > 2) {
+    const unsigned z = r / ny;
+    const int sz = g.nx * g.ny;
+    nb[2][0] = z > 0u ? i - sz : (g.per[2] ? i + (g.nz - 1) * sz : -1);
+    nb[2][1] = z + 1u < (unsigned)g.nz ? i + sz : (g.per[2] ? i - (g.nz - 1) * sz : -1);
   }
-  const int z = (int)(i / sz);
-  const int zn = z + s;
-  if (zn < 0) return g.per[2] ? i + (long)(g.nz - 1) * sz : -1;
-  if (zn >= g.nz) return g.per[2] ? i - (long)(g.nz - 1) * sz : -1;
-  return i + s * sz;
 }
 
 // Scratch of the mechanism, [N][ncell] each unless noted.
 struct PfWork {
   double* R;        // [div J_p]^ (Eq. 28)
   double* c;        // max(phi (1 - phi), 0)
+  double* w;        // face weights c_f / dx^2 of the face above, [3][N][ncell]
   double* D;        // coupling sum_faces c_f / dx^2
+  double* Dinv;     // 1 / D, 0 where D = 0 (cells without a coupled face)
   int* lab;         // region label (smallest cell index of the region), -1: none
   double* sumR;     // per region (indexed by label): sum r
   double* sumD;     //                                 sum D
-  double* r;        // conjugate-gradient residual
-  double* z;        //                    preconditioned residual
+  double* x;        // conjugate-gradient iterate (Q)
+  double* r;        //                    residual
   double* p;        //                    direction
   double* q;        //                    K p
-  double* part;     // reduction partials [PF_BLOCKS][32] + [2][PF_BLOCKS][N] + [PF_BLOCKS][N]
-  double* scal;     // [32]: M, B[0..N-1], rz0[N] ...
-  int* flag;        // [8]: label change, converged per phase
+  double* part;     // reduction partials (offsets in wenoc_pf.cu)
+  double* scal;     // [32]: M, B[0..N-1] | tol^2 at 8 | b.b/D at 16+p | r.r/D at 24+p
+  int* flag;        // [8]: label change, converged per phase at 1+p
 };
 
 // Launchers (wenoc_pf.cu), all asynchronous on st.
@@ -80,15 +79,18 @@ size_t pf_part_doubles();
 // Eq. 28 into w.R (M into w.scal[0], B into w.scal[1..N]); M_in >= 0 fixes M.
 cudaError_t pf_cac(const double* U, const PfGeom& g, const PfWork& w, double vol, double eta,
                    double M_in, cudaStream_t st);
-// Eq. 4: coefficients, coupling D and initial labels.
+// Eq. 4: coefficients, coupling D, 1/D and initial labels.
 cudaError_t pf_qmap_setup(const double* U, const PfGeom& g, const PfWork& w, cudaStream_t st);
 // rounds of label propagation; w.flag[0] != 0 afterwards if any label moved.
 cudaError_t pf_label_rounds(const PfGeom& g, const PfWork& w, int rounds, cudaStream_t st);
-// region sums, the consistent right-hand side from R, and the CG start (Q = 0).
-cudaError_t pf_qmap_project(const PfGeom& g, const PfWork& w, double* Q, cudaStream_t st);
-// CG iterations it0 .. it0 + rounds - 1; w.flag[1 + p] set when phase p
-// reached rz <= tol2 rz0; w.scal[24 + p] holds the last rz, w.scal[16 + p] rz0.
-cudaError_t pf_cg_rounds(const PfGeom& g, const PfWork& w, double* Q, int it0, int rounds,
-                         double tol2, cudaStream_t st);
+// region sums, the consistent right-hand side b from R, and the CG start in
+// w.x (0, or when warm the values already in w.x); w.flag[1 + p] set for
+// the phases whose start meets the test r.r/D <= tol2 b.b/D.
+cudaError_t pf_qmap_project(const PfGeom& g, const PfWork& w, int warm, double tol2,
+                            cudaStream_t st);
+// CG iterations it0 .. it0 + rounds - 1 (iteration 0 starts the directions);
+// w.flag[1 + p] set once phase p meets the test; w.scal[24 + p] holds its
+// last r.r/D and w.scal[16 + p] the reference b.b/D.
+cudaError_t pf_cg_rounds(const PfGeom& g, const PfWork& w, int it0, int rounds, cudaStream_t st);
 
 }  // namespace wc

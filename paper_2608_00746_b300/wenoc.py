@@ -74,7 +74,7 @@ _SIGS = {
     "wc_pf_workspace_bytes": (ctypes.c_size_t, [_VP]),
     "wc_set_pf_workspace": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "wc_cac_rhs": (ctypes.c_int, [_VP, _VP, ctypes.c_double, ctypes.c_double, _VP, _VP]),
-    "wc_qmap": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
+    "wc_qmap": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _VP]),
     "wc_pf_step": (ctypes.c_int, [_VP, _VP, ctypes.c_double, _VP]),
     "wc_step": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -351,14 +351,17 @@ class Grid:
                                      _stream(stream)))
         return R
 
-    def qmap(self, U, R=None, Q=None, tol=1e-12, maxit=20000, stream=None):
+    def qmap(self, U, R=None, Q=None, tol=1e-12, maxit=20000, warm=False, stream=None):
         """Q of Eq. 4 ([N][...]) for the fractions of U and right-hand sides R
-        (None: the last cac_rhs); returns (Q, CG iterations, residual)."""
-        Q = torch.empty((self.N,) + tuple(U.shape[1:]), dtype=torch.float64,
-                        device=U.device) if Q is None else Q
+        (None: the last cac_rhs); warm: start from the Q given; returns (Q,
+        CG iterations, residual)."""
+        if Q is None:
+            warm = False
+            Q = torch.empty((self.N,) + tuple(U.shape[1:]), dtype=torch.float64, device=U.device)
         it, res = ctypes.c_int(0), ctypes.c_double(0.0)
         self._check(lib().wc_qmap(self.h, _ptr(U), _dptr(R), _ptr(Q), float(tol), int(maxit),
-                                  ctypes.byref(it), ctypes.byref(res), _stream(stream)))
+                                  int(bool(warm)), ctypes.byref(it), ctypes.byref(res),
+                                  _stream(stream)))
         return Q, it.value, res.value
 
     def pf_step(self, Q, dt, stream=None):

@@ -94,6 +94,27 @@ def test_qmap_solution(gpu, name):
     assert np.abs(F - F_or).max() <= 1e-8 * max(np.abs(F_or).max(), 1e-300)
 
 
+def test_qmap_warm_start(gpu):
+    """Started from its own solution the Q-map does no iteration and keeps
+    Q; started from that solution plus noise of size 1e-6 it converges to
+    the same face fluxes in fewer iterations than from zero."""
+    case, go, g, U = _evolved("shock_bubble_2d_ragged", steps=5)
+    Ud = to_dev(U)
+    g.bind(Ud).set_pf_workspace(Ud.device)
+    g.cac_rhs(Ud)
+    Q, it0, _ = g.qmap(Ud, tol=1e-12)
+    Q1 = Q.clone()
+    _, it1, res1 = g.qmap(Ud, Q=Q1, tol=1e-12, warm=True)
+    assert it1 == 0 and res1 <= 1e-12 and torch.equal(Q1, Q)
+    rng = np.random.default_rng(3)
+    Q2 = Q + to_dev(rng.normal(size=Q.shape) * 1e-6)
+    _, it2, res2 = g.qmap(Ud, Q=Q2, tol=1e-12, warm=True)
+    assert res2 <= 1e-12 and it2 < it0, (it0, it2, res2)
+    phi = pf.fractions(go, U)
+    F, F2 = _face_flux(go, phi, Q.cpu().numpy()), _face_flux(go, phi, Q2.cpu().numpy())
+    assert np.abs(F - F2).max() <= 1e-8 * np.abs(F).max()
+
+
 @pytest.mark.parametrize("qscale", [1.0, 1e4])
 @pytest.mark.parametrize("name", ["two_phase_advection", "five_phase_2d", "spheres_3d_ragged"])
 def test_pf_step_parity_with_common_q(gpu, name, qscale):
