@@ -15,7 +15,11 @@ on the same workload (speed and group L1 against FP64 after the same steps),
 the learned-weight workload (2-D circles and shock, 2048 x 2048, N = 3) in all
 three precisions, and the surrogate's training record: before the timed
 region the surrogate is trained on the GPU from shock-bubble and 3-D
-spheres-and-shock states (``--no-learned`` skips all of this).
+spheres-and-shock states (``--no-learned`` skips all of this).  The scheme
+variants follow (``--no-variants`` skips them): WENO-C, WENO-CL and the
+WENO-W / WENO-JS comparison schemes on the Sec. 4.1.1 advection, the Kapila
+model, and the full time step with the Phase-Field mechanism (Eq. 28, the
+Q-map of Eq. 4, the Phase-Field step) on the headline workload.
 
 ``--impl reference`` times the FP64 CPU oracle on this host's cores on the same
 workload (the oracle is the only other implementation of the method).
@@ -542,7 +546,54 @@ def run_variants(args, rank, make_grid, timed_steps):
                      "value": round(cells_h * 3 / (ms * 1e-3) / 1e6, 3),
                      "ms_per_step": round(ms, 4), "ms_per_direction": round(sw, 4)}
     del g, U
+    out["phase_field"] = time_phase_field(make_grid)
     return out
+
+
+def time_phase_field(make_grid, K=20):
+    """Full time steps of Sec. 2.2 on the headline shock-bubble: the
+    hyperbolic step, Eq. 28, the Q-map of Eq. 4 (conjugate gradients to a
+    D-weighted residual of 1e-10, started from the previous step's Q) and
+    the Phase-Field step, FP64; then each part timed alone."""
+    import torch
+    g, U = make_grid("fp64")
+    g.set_pf_workspace(U.device)
+    g.step(cfl=0.2, nsteps=3, tol=1e-10)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    g.step(cfl=0.2, nsteps=K, tol=1e-10)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    iters, rounds, res = g.pf_stats()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    parts = np.zeros(4)
+    Q = None
+    for _ in range(5):
+        ev[0].record(s)
+        dt = g.rk_step(cfl=0.2, want_dt=True)
+        ev[1].record(s)
+        g.cac_rhs(U)
+        ev[2].record(s)
+        Q, _, _ = g.qmap(U, Q=Q, tol=1e-10, warm=Q is not None)
+        ev[3].record(s)
+        g.pf_step(Q, dt)
+        ev[4].record(s)
+        torch.cuda.synchronize()
+        parts += [ev[k].elapsed_time(ev[k + 1]) for k in range(4)]
+    g.sync_status()
+    parts /= 5
+    cells = int(np.prod(g.shape))
+    del g, U
+    return {"workload": "headline shock-bubble, full time step (hyperbolic + Eq. 28 + Eq. 4 + "
+                        "Phase-Field step), Q-map tolerance 1e-10",
+            "steps": K, "value": round(cells * 3 / (ms * 1e-3) / 1e6, 3), "unit": "Mcell/s",
+            "ms_per_step": round(ms, 4), "qmap_cg_iterations_last": iters,
+            "qmap_label_rounds_last": rounds, "qmap_residual_last": res,
+            "ms_hyperbolic": round(parts[0], 4), "ms_eq28": round(parts[1], 4),
+            "ms_qmap": round(parts[2], 4), "ms_pf_step": round(parts[3], 4)}
 
 
 def run_profile_mlp(args):
