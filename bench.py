@@ -190,12 +190,17 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+# the sources the FP64 window sweep (the roofline kernel) is built from
+SWEEP_SOURCES = ("wenoc_device.cuh", "wenoc_sweep.cuh", "wenoc_window.cuh", "wenoc_fp64.cu")
+
+
 def csrc_hash():
+    """Hash of the roofline kernel's sources: a traffic record taken on other
+    sources does not describe the kernel that runs."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2608_00746_b300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in SWEEP_SOURCES:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
