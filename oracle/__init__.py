@@ -273,6 +273,34 @@ def max_rate(g, U):
     return out.value
 
 
+def heat_capacities(g: Grid, rho, P0, T0):
+    """C_p^T of the thermal-equilibrium rule of Sec. 4.1.1: C_p^T = (A_p P0 +
+    B_p - B_p^T) / (rho_p T0), with A_p = 1/(gamma_p - 1), B_p = gamma_p
+    Pinf_p/(gamma_p - 1) and B_p^T = Pinf_p (Eq. 26), so a state at uniform
+    P0 with phasic densities rho_p has T = T0 in every phase."""
+    out = []
+    for p in range(g.N):
+        A = 1.0 / (g.gamma[p] - 1.0)
+        B = g.gamma[p] * g.pinf[p] / (g.gamma[p] - 1.0)
+        out.append((A * P0 + B - g.pinf[p]) / (rho[p] * T0))
+    return out
+
+
+def temperature(g: Grid, U, cT):
+    """Mixture temperature of Eq. 29 (numpy, per cell): (rho E - |rho u|^2 /
+    (2 rho) - sum_p B_p^T alpha_p - sum_p D_p (alpha rho)_p) / sum_p C_p^T
+    (alpha rho)_p, B_p^T = Pinf_p (Eq. 26)."""
+    N, d = g.N, g.dim
+    rho = sum(U[p] for p in range(N))
+    mom2 = sum(U[N + j] ** 2 for j in range(d))
+    num = U[N + d] - 0.5 * mom2 / rho
+    den = np.zeros_like(rho)
+    for p in range(N):
+        num = num - g.pinf[p] * U[N + d + 1 + p] - g.D[p] * U[p]
+        den = den + cT[p] * U[p]
+    return num / den
+
+
 def flux(g: Grid, direction, UL, VL, UR, VR):
     arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (UL, VL, UR, VR)]
     F = np.empty(g.nv)

@@ -639,3 +639,25 @@ def test_two_phase_advection_js_oscillates_in_mass_not_fraction():
     V = oracle.cons_to_prim(g, U)
     assert np.abs(V[2:4] - 1.0).max() < 1e-12
     assert np.abs(V[4] / 4.819e-5 - 1.0).max() < 1e-8
+
+
+def test_temperature_of_eq29_and_the_scheme_ordering():
+    """Eq. 29 with B_p^T = Pinf_p (Eq. 26) and the Sec. 4.1.1 rule C_p^T =
+    (A_p P0 + B_p - B_p^T)/(rho_p T0): the initial state is at T0 = 300 in
+    every cell; over 200 steps the temperature error ranks JS >> W >> C,
+    W's above its own consistency error (round-off, as Sec. 4.1.1 notes)."""
+    case = inputs.two_phase_advection_2d(n=50)
+    rho = case.meta["rho"]
+    err = {}
+    for name, kw in COMPARATORS.items():
+        g = grid_of(case, **kw)
+        cT = oracle.heat_capacities(g, rho, 4.819e-5, 300.0)
+        U = oracle.prim_to_cons(g, case.V)
+        assert np.abs(oracle.temperature(g, U, cT) / 300.0 - 1.0).max() < 1e-13
+        for _ in range(200):
+            U, _ = oracle.rk3_step(g, U, dt=case.meta["dt"])
+        err[name] = (np.abs(oracle.temperature(g, U, cT) / 300.0 - 1.0).max(),
+                     np.abs(U[0] / rho[0] - U[5]).max())
+    assert err["js"][0] > 1e-3
+    assert err["w"][0] < 1e-6 and err["w"][0] > err["w"][1]
+    assert err["c"][0] < 0.1 * err["w"][0]
