@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="only the FP64 timed steps (a short run for profilers); prints the "
                          "per-launch sweep time")
+    ap.add_argument("--profile-pf", action="store_true",
+                    help="only full time steps with the Phase-Field mechanism on the headline "
+                         "workload (--steps of them after --warmup), for profilers")
     ap.add_argument("--profile-mlp", action="store_true",
                     help="only the surrogate kernels on the circles state (inference of one "
                          "direction, one training step of train_batch rows), for profilers")
@@ -292,7 +295,7 @@ def run_ours(args):
     case = make_case(args, rank)
     N, D = case.N, case.dim
     cells = int(np.prod(case.shape))
-    learned = not (args.no_learned or args.profile)
+    learned = not (args.no_learned or args.profile or args.profile_pf)
     S, train_info = train_surrogate(args, dev) if learned else (None, None)
 
     def make_grid(precision, c=None, counters=None, scheme="c", kmodel="allaire"):
@@ -334,6 +337,22 @@ def run_ours(args):
         total = sum(e0.elapsed_time(e1) for e0, e1 in evs)
         g.sync_status()
         return total / K, tot_sw / max(nl, 1)  # ms per step, ms per sweep launch
+
+    if args.profile_pf:
+        g, U = make_grid("fp64")
+        g.set_pf_workspace(U.device)
+        g.step(cfl=case.cfl, nsteps=args.warmup, tol=1e-10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(cfl=case.cfl, nsteps=args.steps, tol=1e-10)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / max(args.steps, 1)
+        g.sync_status()
+        it, rounds, res = g.pf_stats()
+        print(json.dumps({"profile_pf": True, "ms_per_step": ms, "qmap_cg_iterations_last": it,
+                          "qmap_label_rounds_last": rounds, "qmap_residual_last": res,
+                          "steps": args.steps, "warmup": args.warmup}), flush=True)
+        return 0
 
     if args.profile:
         g, U = make_grid("fp64")
