@@ -558,9 +558,14 @@ def run_variants(args, rank, make_grid, timed_steps):
         g, U = make_grid("fp64", cA, scheme=scheme)
         ms, sw = timed_steps(g, args.steps, 3, cA, dt=dtA)
         cons = (U[0] / rho1 - U[5]).abs().max().item()
+        # Eq. 29 with the Sec. 4.1.1 heat capacities (T = 300 at P0 = 4.819e-5)
+        A = [1.0 / (gm - 1.0) for gm in cA.gamma]
+        cT = [(A[p] * 4.819e-5 + cA.gamma[p] * cA.pinf[p] * A[p] - cA.pinf[p])
+              / (cA.meta["rho"][p] * 300.0) for p in range(2)]
+        temp = (g.temperature(U, cT) / 300.0 - 1.0).abs().max().item()
         adv[scheme] = {"value": round(cells * 3 / (ms * 1e-3) / 1e6, 3),
                        "ms_per_step": round(ms, 4), "ms_per_direction": round(sw, 4),
-                       "consistency_error_max": cons}
+                       "consistency_error_max": cons, "temperature_error_max": temp}
         del g, U
     out["advection"] = adv
     g, U = make_grid("fp64", kmodel="kapila")

@@ -141,6 +141,15 @@ wc_status wc_download_state(const wc_grid *g, double *U_host, void *stream);
 wc_status wc_prim_to_cons(const wc_grid *g, const double *V_dev, double *U_dev, void *stream);
 wc_status wc_cons_to_prim(const wc_grid *g, const double *U_dev, double *V_dev, void *stream);
 
+/* Mixture temperature of Eq. 29 into T_dev ([ncell]) for the state U_dev:
+ * (rho E - |rho u|^2/(2 rho) - sum_p B_p^T alpha_p - sum_p D_p (alpha rho)_p) /
+ * sum_p C_p^T (alpha rho)_p with B_p^T = Pinf_p (Eq. 26) and the caller's heat
+ * capacities cT[N] (host array, > 0; Sec. 4.1.1 derives them from a
+ * reference state: C_p^T = (A_p P0 + B_p - Pinf_p)/(rho_p T0)).  A diagnostic
+ * of thermal equilibrium; asynchronous on stream. */
+wc_status wc_temperature(const wc_grid *g, const double *U_dev, const double *cT, double *T_dev,
+                         void *stream);
+
 /* L = dU/dt of the hyperbolic step (Eq. 3) for the state U_dev (not the bound
  * state), summed over the directions; L_dev is overwritten. */
 wc_status wc_rhs(wc_grid *g, const double *U_dev, double *L_dev, void *stream);

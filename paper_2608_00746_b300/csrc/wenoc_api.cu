@@ -236,6 +236,23 @@ extern "C" wc_status wc_cons_to_prim(const wc_grid* gc, const double* U, double*
   return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "cons_to_prim");
 }
 
+extern "C" wc_status wc_temperature(const wc_grid* gc, const double* U, const double* cT,
+                                    double* T, void* stream) {
+  wc_grid* g = const_cast<wc_grid*>(gc);
+  if (!g || !U || !cT || !T) return WC_ERR_ARG;
+  HeatCap h;
+  memset(&h, 0, sizeof(h));
+  for (int p = 0; p < g->d.nphase; p++) {
+    if (!(cT[p] > 0.0)) return fail(g, WC_ERR_ARG, "heat capacities must be positive");
+    h.cT[p] = cT[p];
+  }
+  int blocks = grid_blocks(g->ncell, 256);
+  WC_DISPATCH(g->d.nphase, g->d.dim,
+              (k_temperature<N_, D_><<<blocks, 256, 0, S(stream)>>>(U, T, g->ncell, g->mat, h)));
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "temperature");
+}
+
 // ------------------------------------------------------------------ sweeps
 static int sweep_block(const wc_grid* g) { return g->d.block > 0 ? g->d.block : 128; }
 

@@ -82,6 +82,41 @@ __global__ void k_cons_to_prim(const double* __restrict__ U, double* __restrict_
   }
 }
 
+// Per-phase heat capacities C_p^T of the temperature law (Eq. 26).
+struct HeatCap {
+  double cT[MAXP];
+};
+
+// Mixture temperature of Eq. 29: (rho E - |rho u|^2 / (2 rho) - sum_p B_p^T
+// alpha_p - sum_p D_p (alpha rho)_p) / sum_p C_p^T (alpha rho)_p with
+// B_p^T = Pinf_p (Eq. 26).
+template <int N, int D>
+__global__ void k_temperature(const double* __restrict__ U, double* __restrict__ T, long ncell,
+                              Mat m, HeatCap h) {
+  using I = Idx<N, D>;
+  for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+       c += (long)gridDim.x * blockDim.x) {
+    double rho = 0.0, den = 0.0;
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      const double mp = U[(long)p * ncell + c];
+      rho += mp;
+      den += h.cT[p] * mp;
+    }
+    double mom2 = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+      const double mj = U[(long)I::U(j) * ncell + c];
+      mom2 += mj * mj;
+    }
+    double num = U[(long)I::E * ncell + c] - 0.5 * mom2 / rho;
+#pragma unroll
+    for (int p = 0; p < N; p++)
+      num -= m.pinf[p] * U[(long)I::A(p) * ncell + c] + m.D[p] * U[(long)p * ncell + c];
+    T[c] = num / den;
+  }
+}
+
 // Eq. 17-21 on caller-given raw primitive faces of independent cells.
 template <int N, int D>
 __global__ void k_limit(const double* __restrict__ Ub, const double* __restrict__ VL,

@@ -336,19 +336,58 @@ constexpr long PART_RZ = PART_PQ + (long)PF_BLOCKS * 8;
 constexpr long PART_REF = PART_RZ + 2L * PF_BLOCKS * 8;
 constexpr long PART_TOTAL = PART_REF + (long)PF_BLOCKS * 8;
 
-// Sums of the per-block partials [PF_BLOCKS][8] of N phases, the same in
-// every block and in a fixed order: thread t adds blocks t, t + 256, ...
-// (parallel loads), then the block tree of block_sum_to.
+// On B300 a warp's FP64 instruction occupies the FP64 pipe for the same time
+// however few lanes are active, so the reductions of the CG kernels are
+// written to issue few FP64 warp instructions.
+//
+// Sums of the per-block partials [PF_BLOCKS][8] of N phases, by warp 0 of
+// every block in the same fixed order (lane l adds blocks l, l + 32, ...,
+// then a shuffle tree); lane 0 writes out[p].  The caller synchronises
+// before other warps read out.
 template <int N>
-__device__ __forceinline__ void sum_partials(const double* part, long off, double* out) {
+__device__ __forceinline__ void sum_partials_warp(const double* part, long off, double* out) {
+  const int lane = threadIdx.x & 31;
   double v[N];
 #pragma unroll
   for (int p = 0; p < N; p++) v[p] = 0.0;
-  for (int b = threadIdx.x; b < PF_BLOCKS; b += PF_THREADS) {
+  for (int b = lane; b < PF_BLOCKS; b += 32) {
 #pragma unroll
     for (int p = 0; p < N; p++) v[p] += part[off + (long)b * 8 + p];
   }
-  block_sum_to<N>(v, out);
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[p] += __shfl_down_sync(0xffffffffu, v[p], o);
+    if (lane == 0) out[p] = v[p];
+  }
+}
+
+// Block sum of N values per thread into out[0..N-1] (fixed order): a shared
+// tree over the 256 threads down to one warp, then its shuffle tree.
+template <int N>
+__device__ __forceinline__ void block_sum_small(const double (&v)[N], double* out) {
+  __shared__ double sm[N][PF_THREADS];
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int p = 0; p < N; p++) sm[p][t] = v[p];
+  __syncthreads();
+#pragma unroll
+  for (int s = PF_THREADS / 2; s >= 32; s >>= 1) {
+    if (t < s)
+#pragma unroll
+      for (int p = 0; p < N; p++) sm[p][t] += sm[p][t + s];
+    __syncthreads();
+  }
+  if (t < 32) {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      double x = sm[p][t];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (t == 0) out[p] = x;
+    }
+  }
+  __syncthreads();
 }
 
 // K Q = b with K = -A (positive semi-definite): b = -(r - D s_k) on cells
@@ -394,8 +433,8 @@ __global__ void __launch_bounds__(PF_THREADS) k_cg_init(PfGeom g, const double* 
 #pragma unroll
       for (int p = 0; p < N; p++) x[(long)p * n + i] = 0.0;
   }
-  block_sum_to<N>(acc, part + PART_RZ + (long)blockIdx.x * 8);  // parity 0
-  block_sum_to<N>(ref, part + PART_REF + (long)blockIdx.x * 8);
+  block_sum_small<N>(acc, part + PART_RZ + (long)blockIdx.x * 8);  // parity 0
+  block_sum_small<N>(ref, part + PART_REF + (long)blockIdx.x * 8);
 }
 
 // The reference b . b/D and r0 . r0/D per phase and tol^2 into scal (one
@@ -404,8 +443,11 @@ template <int N>
 __global__ void __launch_bounds__(PF_THREADS) k_cg_start(const double* part, double* scal,
                                                          int* flag, double tol2) {
   __shared__ double rz[N], ref[N];
-  sum_partials<N>(part, PART_RZ, rz);
-  sum_partials<N>(part, PART_REF, ref);
+  if (threadIdx.x < 32) {
+    sum_partials_warp<N>(part, PART_RZ, rz);
+    sum_partials_warp<N>(part, PART_REF, ref);
+  }
+  __syncthreads();
   const int p = threadIdx.x;
   if (p == 0) scal[8] = tol2;
   if (p >= N) return;
@@ -424,21 +466,31 @@ __global__ void __launch_bounds__(PF_THREADS) k_cg_dir(PfGeom g, const double* _
                                                        const double* __restrict__ Dinv, double* pv,
                                                        const double* part, double* scal, int* flag,
                                                        int it) {
-  __shared__ double rn[N], ro[N];
-  sum_partials<N>(part, PART_RZ + (long)(it & 1) * PF_BLOCKS * 8, rn);
-  sum_partials<N>(part, PART_RZ + (long)((it + 1) & 1) * PF_BLOCKS * 8, ro);
-  const double tol2 = scal[8];
+  __shared__ double rn[N], ro[N], sb[N];
+  __shared__ int sl[N];
+  if (threadIdx.x < 32) {
+    // warp 0: the sums, then lane p decides phase p
+    sum_partials_warp<N>(part, PART_RZ + (long)(it & 1) * PF_BLOCKS * 8, rn);
+    sum_partials_warp<N>(part, PART_RZ + (long)((it + 1) & 1) * PF_BLOCKS * 8, ro);
+    __syncwarp();
+    const int p = threadIdx.x;
+    if (p < N) {
+      sl[p] = rn[p] > scal[8] * scal[16 + p];
+      sb[p] = (it > 0 && ro[p] > 0.0) ? rn[p] / ro[p] : 0.0;
+      if (blockIdx.x == 0) {
+        scal[24 + p] = rn[p];
+        flag[1 + p] = !sl[p];
+      }
+    }
+  }
+  __syncthreads();
   bool live[N], any = false;
   double beta[N];
 #pragma unroll
   for (int p = 0; p < N; p++) {
-    live[p] = rn[p] > tol2 * scal[16 + p];
+    live[p] = sl[p];
     any = any || live[p];
-    beta[p] = (it > 0 && ro[p] > 0.0) ? rn[p] / ro[p] : 0.0;
-  }
-  if (blockIdx.x == 0 && threadIdx.x < N) {
-    scal[24 + threadIdx.x] = rn[threadIdx.x];
-    flag[1 + threadIdx.x] = !live[threadIdx.x];
+    beta[p] = sb[p];
   }
   if (!any) return;
   const int n = (int)g.ncell;
@@ -484,7 +536,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_cg_matvec(PfGeom g, const double
       acc[p] = fma(pv[o + i], s, acc[p]);
     }
   }
-  block_sum_to<N>(acc, part + PART_PQ + (long)blockIdx.x * 8);
+  block_sum_small<N>(acc, part + PART_PQ + (long)blockIdx.x * 8);
 }
 
 // Step 3: alpha = rz_it / p . q; x += alpha p, r -= alpha q; partials of
@@ -497,16 +549,27 @@ __global__ void __launch_bounds__(PF_THREADS) k_cg_update(PfGeom g,
                                                           const double* __restrict__ pv,
                                                           const double* __restrict__ q,
                                                           double* part, const int* flag, int it) {
-  __shared__ double pq[N], rn[N];
-  sum_partials<N>(part, PART_PQ, pq);
-  sum_partials<N>(part, PART_RZ + (long)(it & 1) * PF_BLOCKS * 8, rn);
+  __shared__ double pq[N], rn[N], sa[N];
+  __shared__ int sl[N];
+  if (threadIdx.x < 32) {
+    // warp 0: the sums, then lane p forms alpha of phase p
+    sum_partials_warp<N>(part, PART_PQ, pq);
+    sum_partials_warp<N>(part, PART_RZ + (long)(it & 1) * PF_BLOCKS * 8, rn);
+    __syncwarp();
+    const int p = threadIdx.x;
+    if (p < N) {
+      sl[p] = !flag[1 + p] && pq[p] > 0.0;
+      sa[p] = sl[p] ? rn[p] / pq[p] : 0.0;
+    }
+  }
+  __syncthreads();
   bool live[N], any = false;
   double alpha[N];
 #pragma unroll
   for (int p = 0; p < N; p++) {
-    live[p] = !flag[1 + p] && pq[p] > 0.0;
+    live[p] = sl[p];
     any = any || live[p];
-    alpha[p] = live[p] ? rn[p] / pq[p] : 0.0;
+    alpha[p] = sa[p];
   }
   if (!any) {
     // nothing moves: r . r/D of the next iteration is this one's (copied
@@ -533,7 +596,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_cg_update(PfGeom g,
       acc[p] = fma(rk, rk * Dinv[k], acc[p]);
     }
   }
-  block_sum_to<N>(acc, part + PART_RZ + (long)((it + 1) & 1) * PF_BLOCKS * 8 + (long)blockIdx.x * 8);
+  block_sum_small<N>(acc, part + PART_RZ + (long)((it + 1) & 1) * PF_BLOCKS * 8 + (long)blockIdx.x * 8);
 }
 
 // ------------------------------------------------------------------ launchers

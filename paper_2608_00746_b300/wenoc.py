@@ -71,6 +71,7 @@ class PatchesDesc(ctypes.Structure):
 # name -> (restype, argtypes)
 _VP = ctypes.c_void_p
 _SIGS = {
+    "wc_temperature": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double), _VP, _VP]),
     "wc_pf_workspace_bytes": (ctypes.c_size_t, [_VP]),
     "wc_set_pf_workspace": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "wc_cac_rhs": (ctypes.c_int, [_VP, _VP, ctypes.c_double, ctypes.c_double, _VP, _VP]),
@@ -334,6 +335,14 @@ class Grid:
 
     def sync_status(self, stream=None):
         self._check(lib().wc_sync_status(self.h, _stream(stream)))
+
+    def temperature(self, U, cT, T=None, stream=None):
+        """Mixture temperature of Eq. 29 per cell for heat capacities cT[N]."""
+        T = torch.empty(tuple(U.shape[1:]), dtype=torch.float64, device=U.device) \
+            if T is None else T
+        arr = (ctypes.c_double * self.N)(*[float(c) for c in cT])
+        self._check(lib().wc_temperature(self.h, _ptr(U), arr, _ptr(T), _stream(stream)))
+        return T
 
     # Phase-Field mechanism (Eq. 28, Eq. 4, Eq. 5) ---------------------------
     def set_pf_workspace(self, device="cuda"):

@@ -89,11 +89,14 @@ def _one_period(scheme):
     U = to_dev(oracle.prim_to_cons(go, case.V))
     g.bind(U)
     rho1 = case.meta["rho"][0]
-    hist = []
+    cT = oracle.heat_capacities(go, case.meta["rho"], 4.819e-5, 300.0)
+    hist, temp = [], []
     for _ in range(10):
         g.rk_step(dt=case.meta["dt"], nsteps=100)
         hist.append((U[0] / rho1 - U[5]).abs().max().item())
+        temp.append((g.temperature(U, cT) / 300.0 - 1.0).abs().max().item())
     g.sync_status()
+    _one_period.temperature = np.array(temp)
     return np.array(hist), g.cons_to_prim(U).cpu().numpy()
 
 
@@ -104,15 +107,35 @@ def test_two_phase_advection_ordering_one_period(gpu):
     nine at the end of the period (the paper: about nine); C is lower than
     W throughout (the oracle on this grid: JS 0.11, W <= 1.8e-8, C <=
     2.3e-11).  Velocity and pressure stay uniform in all three."""
-    h = {}
+    h, t = {}, {}
     for scheme in ("js", "w", "c"):
         h[scheme], V = _one_period(scheme)
+        t[scheme] = _one_period.temperature
         assert np.abs(V[2:4] - 1.0).max() < 1e-11, scheme
         assert np.abs(V[4] / 4.819e-5 - 1.0).max() < 1e-7, scheme
     assert h["js"].min() > 1e-2
     assert h["w"].max() < 1e-6 * h["js"].max()
     assert h["w"][-1] < 1e-8 * h["js"][-1]
     assert (h["c"] < h["w"]).all() and h["c"].max() < 1e-10
+    # the temperature error of Eq. 29 (Sec. 4.1.1): same ranking; W's is set
+    # by round-off and stays above its consistency error
+    assert t["js"].max() > 1e-3 and t["w"].max() < 1e-5 * t["js"].max()
+    assert t["c"].max() < t["w"].max()
+
+
+@pytest.mark.parametrize("scheme", ["c", "w", "js"])
+def test_temperature_parity(gpu, scheme):
+    """Eq. 29 on the GPU against the oracle's, after 20 steps of the
+    Sec. 4.1.1 advection with each scheme: 1e-12 relative."""
+    case = inputs.two_phase_advection_2d(n=40)
+    go, g = _grids(case, scheme)
+    U = oracle.prim_to_cons(go, case.V)
+    for _ in range(20):
+        U, _ = oracle.rk3_step(go, U, dt=case.meta["dt"])
+    cT = oracle.heat_capacities(go, case.meta["rho"], 4.819e-5, 300.0)
+    T_or = oracle.temperature(go, U, cT)
+    T = g.temperature(to_dev(U), cT).cpu().numpy()
+    assert np.abs(T - T_or).max() <= 1e-12 * np.abs(T_or).max()
 
 
 @pytest.mark.parametrize("scheme", ["w", "js"])
