@@ -507,7 +507,7 @@ extern "C" size_t wc_pf_workspace_bytes(const wc_grid* g) {
   const size_t li = align256(sizeof(int) * (size_t)g->d.nphase * g->ncell);
   // R c D 1/D sumR sumD x r p q, three face-weight fields, labels,
   // partials, scalars, flags
-  return 13 * f + li + align256(sizeof(double) * pf_part_doubles()) + 256 + 256;
+  return 13 * f + li + align256(sizeof(double) * pf_part_doubles()) + 512 + 256;
 }
 
 extern "C" wc_status wc_set_pf_workspace(wc_grid* g, void* ws_dev, size_t bytes) {
@@ -530,9 +530,12 @@ extern "C" wc_status wc_set_pf_workspace(wc_grid* g, void* ws_dev, size_t bytes)
   w += li;
   g->pw.part = reinterpret_cast<double*>(w);
   w += align256(sizeof(double) * pf_part_doubles());
-  g->pw.scal = reinterpret_cast<double*>(w);
-  w += 256;
+  g->pw.scal = reinterpret_cast<double*>(w);  // 64 doubles
+  w += 512;
   g->pw.flag = reinterpret_cast<int*>(w);
+  // the tickets of the reducing CG kernels start at zero (and return to it)
+  cudaError_t e0 = cudaMemset(g->pw.flag, 0, 256);
+  if (e0 != cudaSuccess) return cuda_fail(g, e0, "pf workspace flags");
   PfGeom& pg = g->pg;
   pg.nx = g->d.n[0];
   pg.ny = g->d.n[1];

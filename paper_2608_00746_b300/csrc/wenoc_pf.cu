@@ -328,37 +328,44 @@ __global__ void __launch_bounds__(PF_THREADS) k_qm_sums(PfGeom g, const double* 
   }
 }
 
-// Offsets into the partials buffer: Eq. 28 totals [PF_BLOCKS][32]; p . K p
-// [PF_BLOCKS][8]; r . z [2 parities][PF_BLOCKS][8]; b . b/D [PF_BLOCKS][8].
+// The conjugate-gradient kernels reduce over a fixed grid of PF_CG_BLOCKS
+// blocks (8 per SM: the elementwise passes need many loads in flight).
+// Partials: p . K p [PF_CG_BLOCKS][8]; r . r/D [2 parities][PF_CG_BLOCKS][8];
+// b . b/D [PF_CG_BLOCKS][8], after the Eq. 28 totals [PF_BLOCKS][32].  The
+// last block of a reducing kernel to finish (atomic ticket, no waiting)
+// sums the partials in a fixed order and writes the scalars the next kernel
+// reads: alpha after the matrix-vector pass, the convergence test and beta
+// after the update.
+constexpr int PF_CG_BLOCKS = 148 * 8;
 constexpr long PART_CAC = 0;
 constexpr long PART_PQ = (long)PF_BLOCKS * 32;
-constexpr long PART_RZ = PART_PQ + (long)PF_BLOCKS * 8;
-constexpr long PART_REF = PART_RZ + 2L * PF_BLOCKS * 8;
-constexpr long PART_TOTAL = PART_REF + (long)PF_BLOCKS * 8;
+constexpr long PART_RZ = PART_PQ + (long)PF_CG_BLOCKS * 8;
+constexpr long PART_REF = PART_RZ + 2L * PF_CG_BLOCKS * 8;
+constexpr long PART_TOTAL = PART_REF + (long)PF_CG_BLOCKS * 8;
+// scalars: scal[16 + p] b.b/D, [24 + p] r.r/D of the current iteration,
+// [32 + p] beta, [40 + p] alpha; flags: [1 + p] converged, [6] and [7] the
+// tickets of the matrix-vector and update passes (zero between launches)
 
 // On B300 a warp's FP64 instruction occupies the FP64 pipe for the same time
-// however few lanes are active, so the reductions of the CG kernels are
-// written to issue few FP64 warp instructions.
+// however few lanes are active, so the reductions here are written to issue
+// few FP64 warp instructions.
 //
-// Sums of the per-block partials [PF_BLOCKS][8] of N phases, by warp 0 of
-// every block in the same fixed order (lane l adds blocks l, l + 32, ...,
-// then a shuffle tree); lane 0 writes out[p].  The caller synchronises
-// before other warps read out.
+// Sums of the per-block partials [PF_CG_BLOCKS][8] of N phases by one warp,
+// in a fixed order (lane l adds blocks l, l + 32, ..., then a shuffle tree;
+// loads bypass L1: other blocks wrote them); returns the sums in lane 0.
 template <int N>
-__device__ __forceinline__ void sum_partials_warp(const double* part, long off, double* out) {
+__device__ __forceinline__ void sum_partials_warp(const double* part, long off, double (&v)[N]) {
   const int lane = threadIdx.x & 31;
-  double v[N];
 #pragma unroll
   for (int p = 0; p < N; p++) v[p] = 0.0;
-  for (int b = lane; b < PF_BLOCKS; b += 32) {
+  for (int b = lane; b < PF_CG_BLOCKS; b += 32) {
 #pragma unroll
-    for (int p = 0; p < N; p++) v[p] += part[off + (long)b * 8 + p];
+    for (int p = 0; p < N; p++) v[p] += __ldcg(part + off + (long)b * 8 + p);
   }
 #pragma unroll
   for (int p = 0; p < N; p++) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[p] += __shfl_down_sync(0xffffffffu, v[p], o);
-    if (lane == 0) out[p] = v[p];
   }
 }
 
@@ -388,6 +395,21 @@ __device__ __forceinline__ void block_sum_small(const double (&v)[N], double* ou
     }
   }
   __syncthreads();
+}
+
+// True in the block that finishes last (after its partials are written);
+// that block also resets the ticket for the next launch.
+__device__ __forceinline__ bool last_block(int* ticket) {
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const int t = atomicAdd(ticket, 1);
+    last = t == (int)gridDim.x - 1;
+    if (last) *ticket = 0;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
 }
 
 // K Q = b with K = -A (positive semi-definite): b = -(r - D s_k) on cells
@@ -438,87 +460,62 @@ __global__ void __launch_bounds__(PF_THREADS) k_cg_init(PfGeom g, const double* 
 }
 
 // The reference b . b/D and r0 . r0/D per phase and tol^2 into scal (one
-// block); a phase whose start already meets the test is converged.
+// warp); beta = 0 for the first directions; a phase whose start already
+// meets the test is converged.
 template <int N>
-__global__ void __launch_bounds__(PF_THREADS) k_cg_start(const double* part, double* scal,
-                                                         int* flag, double tol2) {
-  __shared__ double rz[N], ref[N];
-  if (threadIdx.x < 32) {
-    sum_partials_warp<N>(part, PART_RZ, rz);
-    sum_partials_warp<N>(part, PART_REF, ref);
-  }
-  __syncthreads();
-  const int p = threadIdx.x;
-  if (p == 0) scal[8] = tol2;
-  if (p >= N) return;
-  scal[16 + p] = ref[p];
-  scal[24 + p] = rz[p];
-  flag[1 + p] = !(rz[p] > tol2 * ref[p]);
-}
-
-// Iteration it, step 1: rz_it = r . r/D (partials of parity it & 1); a
-// phase is live while rz_it > tol^2 b.b/D (every block decides alike from
-// the same fixed-order sums; block 0 records the decision in flag for the
-// next two kernels and the host).  Live phases: p = r/D + beta p, beta =
-// rz_it / rz_{it-1} (p = r/D at it = 0).
-template <int N>
-__global__ void __launch_bounds__(PF_THREADS) k_cg_dir(PfGeom g, const double* __restrict__ r,
-                                                       const double* __restrict__ Dinv, double* pv,
-                                                       const double* part, double* scal, int* flag,
-                                                       int it) {
-  __shared__ double rn[N], ro[N], sb[N];
-  __shared__ int sl[N];
-  if (threadIdx.x < 32) {
-    // warp 0: the sums, then lane p decides phase p
-    sum_partials_warp<N>(part, PART_RZ + (long)(it & 1) * PF_BLOCKS * 8, rn);
-    sum_partials_warp<N>(part, PART_RZ + (long)((it + 1) & 1) * PF_BLOCKS * 8, ro);
-    __syncwarp();
-    const int p = threadIdx.x;
-    if (p < N) {
-      sl[p] = rn[p] > scal[8] * scal[16 + p];
-      sb[p] = (it > 0 && ro[p] > 0.0) ? rn[p] / ro[p] : 0.0;
-      if (blockIdx.x == 0) {
-        scal[24 + p] = rn[p];
-        flag[1 + p] = !sl[p];
-      }
-    }
-  }
-  __syncthreads();
-  bool live[N], any = false;
-  double beta[N];
+__global__ void k_cg_start(const double* part, double* scal, int* flag, double tol2) {
+  double rz[N], ref[N];
+  sum_partials_warp<N>(part, PART_RZ, rz);
+  sum_partials_warp<N>(part, PART_REF, ref);
+  if (threadIdx.x != 0) return;
+  scal[8] = tol2;
 #pragma unroll
   for (int p = 0; p < N; p++) {
-    live[p] = sl[p];
-    any = any || live[p];
-    beta[p] = sb[p];
-  }
-  if (!any) return;
-  const int n = (int)g.ncell;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int p = 0; p < N; p++) {
-      if (!live[p]) continue;
-      const long k = (long)p * n + i;
-      const double zk = r[k] * Dinv[k];
-      pv[k] = it > 0 ? fma(beta[p], pv[k], zk) : zk;
-    }
+    scal[16 + p] = ref[p];
+    scal[24 + p] = rz[p];
+    scal[32 + p] = 0.0;
+    flag[1 + p] = !(rz[p] > tol2 * ref[p]);
   }
 }
 
-// Step 2: q = K p for the live phases, and the partials of p . q.
+__device__ __forceinline__ bool all_converged(const int* flag, int N) {
+  int all = 1;
+  for (int p = 0; p < N; p++) all &= flag[1 + p];
+  return all;
+}
+
+// Step 1 (elementwise, any grid): p = r/D + beta p for the live phases
+// (beta = 0 at the first iteration).
+template <int N>
+__global__ void __launch_bounds__(PF_THREADS) k_cg_dir(PfGeom g, const double* __restrict__ r,
+                                                       const double* __restrict__ Dinv,
+                                                       double* __restrict__ pv,
+                                                       const double* __restrict__ scal,
+                                                       const int* __restrict__ flag) {
+  if (all_converged(flag, N)) return;
+  const long n = g.ncell;
+  for (int p = 0; p < N; p++) {
+    if (flag[1 + p]) continue;
+    const double beta = scal[32 + p];
+    const long o = (long)p * n;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long)gridDim.x * blockDim.x)
+      pv[o + i] = fma(beta, pv[o + i], r[o + i] * Dinv[o + i]);
+  }
+}
+
+// Step 2: q = K p for the live phases and the partials of p . q; the last
+// block forms alpha = r.r/D / p.q per live phase.
 template <int N>
 __global__ void __launch_bounds__(PF_THREADS) k_cg_matvec(PfGeom g, const double* __restrict__ w,
                                                           const double* __restrict__ D,
                                                           const double* __restrict__ pv,
                                                           double* __restrict__ q, double* part,
-                                                          const int* flag) {
-  bool live[N], any = false;
+                                                          double* scal, int* flag) {
+  if (all_converged(flag, N)) return;
+  bool live[N];
 #pragma unroll
-  for (int p = 0; p < N; p++) {
-    live[p] = !flag[1 + p];
-    any = any || live[p];
-  }
-  if (!any) return;
+  for (int p = 0; p < N; p++) live[p] = !flag[1 + p];
   const int n = (int)g.ncell;
   const long nn = (long)N * n;
   double acc[N];
@@ -537,47 +534,35 @@ __global__ void __launch_bounds__(PF_THREADS) k_cg_matvec(PfGeom g, const double
     }
   }
   block_sum_small<N>(acc, part + PART_PQ + (long)blockIdx.x * 8);
+  if (!last_block(flag + 6) || threadIdx.x >= 32) return;
+  double pq[N];
+  sum_partials_warp<N>(part, PART_PQ, pq);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int p = 0; p < N; p++)
+      scal[40 + p] = (live[p] && pq[p] > 0.0) ? scal[24 + p] / pq[p] : 0.0;
 }
 
-// Step 3: alpha = rz_it / p . q; x += alpha p, r -= alpha q; partials of
-// r . r/D into parity (it + 1) & 1 (for every phase, so a converged phase
-// keeps its test).
+// Step 3 (iteration it): x += alpha p, r -= alpha q for the live phases;
+// partials of r . r/D into parity (it + 1) & 1 for every phase.  The last
+// block sums them and sets, for the next iteration, r.r/D, the test
+// (converged: r.r/D <= tol^2 b.b/D) and beta = new r.r/D / old.
 template <int N>
 __global__ void __launch_bounds__(PF_THREADS) k_cg_update(PfGeom g,
                                                           const double* __restrict__ Dinv,
-                                                          double* x, double* r,
+                                                          double* __restrict__ x,
+                                                          double* __restrict__ r,
                                                           const double* __restrict__ pv,
                                                           const double* __restrict__ q,
-                                                          double* part, const int* flag, int it) {
-  __shared__ double pq[N], rn[N], sa[N];
-  __shared__ int sl[N];
-  if (threadIdx.x < 32) {
-    // warp 0: the sums, then lane p forms alpha of phase p
-    sum_partials_warp<N>(part, PART_PQ, pq);
-    sum_partials_warp<N>(part, PART_RZ + (long)(it & 1) * PF_BLOCKS * 8, rn);
-    __syncwarp();
-    const int p = threadIdx.x;
-    if (p < N) {
-      sl[p] = !flag[1 + p] && pq[p] > 0.0;
-      sa[p] = sl[p] ? rn[p] / pq[p] : 0.0;
-    }
-  }
-  __syncthreads();
-  bool live[N], any = false;
+                                                          double* part, double* scal, int* flag,
+                                                          int it) {
+  if (all_converged(flag, N)) return;
+  bool live[N];
   double alpha[N];
 #pragma unroll
   for (int p = 0; p < N; p++) {
-    live[p] = sl[p];
-    any = any || live[p];
-    alpha[p] = sa[p];
-  }
-  if (!any) {
-    // nothing moves: r . r/D of the next iteration is this one's (copied
-    // exactly, block by block, so the next test sums the same values)
-    if (threadIdx.x < N)
-      part[PART_RZ + (long)((it + 1) & 1) * PF_BLOCKS * 8 + (long)blockIdx.x * 8 + threadIdx.x] =
-          part[PART_RZ + (long)(it & 1) * PF_BLOCKS * 8 + (long)blockIdx.x * 8 + threadIdx.x];
-    return;
+    live[p] = !flag[1 + p];
+    alpha[p] = scal[40 + p];
   }
   const int n = (int)g.ncell;
   double acc[N];
@@ -596,7 +581,23 @@ __global__ void __launch_bounds__(PF_THREADS) k_cg_update(PfGeom g,
       acc[p] = fma(rk, rk * Dinv[k], acc[p]);
     }
   }
-  block_sum_small<N>(acc, part + PART_RZ + (long)((it + 1) & 1) * PF_BLOCKS * 8 + (long)blockIdx.x * 8);
+  const long onew = PART_RZ + (long)((it + 1) & 1) * PF_CG_BLOCKS * 8;
+  block_sum_small<N>(acc, part + onew + (long)blockIdx.x * 8);
+  if (!last_block(flag + 7) || threadIdx.x >= 32) return;
+  double rn[N];
+  sum_partials_warp<N>(part, onew, rn);
+  if (threadIdx.x == 0) {
+    const double tol2 = scal[8];
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      const double ro = scal[24 + p];
+      const bool conv = !(rn[p] > tol2 * scal[16 + p]);
+      scal[32 + p] = ro > 0.0 ? rn[p] / ro : 0.0;
+      scal[24 + p] = rn[p];
+      // a phase that no longer moves (alpha = 0) stays where it is
+      flag[1 + p] = flag[1 + p] || conv || !(scal[40 + p] > 0.0);
+    }
+  }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -649,21 +650,23 @@ cudaError_t pf_qmap_project(const PfGeom& g, const PfWork& w, int warm, double t
   if (e != cudaSuccess) return e;
   const int nb = pf_grid(g.ncell);
   PF_DISPATCH(g.N, (k_qm_sums<N_><<<nb, PF_THREADS, 0, st>>>(g, w.R, w.D, w.lab, w.sumR, w.sumD)));
-  PF_DISPATCH(g.N, (k_cg_init<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(
+  PF_DISPATCH(g.N, (k_cg_init<N_><<<PF_CG_BLOCKS, PF_THREADS, 0, st>>>(
                         g, w.R, w.w, w.D, w.Dinv, w.lab, w.sumR, w.sumD, w.x, w.r, w.part, warm)));
-  PF_DISPATCH(g.N, (k_cg_start<N_><<<1, PF_THREADS, 0, st>>>(w.part, w.scal, w.flag, tol2)));
+  PF_DISPATCH(g.N, (k_cg_start<N_><<<1, 32, 0, st>>>(w.part, w.scal, w.flag, tol2)));
   return cudaGetLastError();
 }
 
 cudaError_t pf_cg_rounds(const PfGeom& g, const PfWork& w, int it0, int rounds, cudaStream_t st) {
+  long eb = (g.ncell + PF_THREADS - 1) / PF_THREADS;
+  const int dir_blocks = (int)(eb < 148 * 16 ? (eb < 1 ? 1 : eb) : 148 * 16);
   for (int k = 0; k < rounds; k++) {
     const int it = it0 + k;
-    PF_DISPATCH(g.N, (k_cg_dir<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(g, w.r, w.Dinv, w.p, w.part,
-                                                                      w.scal, w.flag, it)));
-    PF_DISPATCH(g.N, (k_cg_matvec<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(g, w.w, w.D, w.p, w.q,
-                                                                         w.part, w.flag)));
-    PF_DISPATCH(g.N, (k_cg_update<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(
-                          g, w.Dinv, w.x, w.r, w.p, w.q, w.part, w.flag, it)));
+    PF_DISPATCH(g.N, (k_cg_dir<N_><<<dir_blocks, PF_THREADS, 0, st>>>(g, w.r, w.Dinv, w.p,
+                                                                       w.scal, w.flag)));
+    PF_DISPATCH(g.N, (k_cg_matvec<N_><<<PF_CG_BLOCKS, PF_THREADS, 0, st>>>(
+                          g, w.w, w.D, w.p, w.q, w.part, w.scal, w.flag)));
+    PF_DISPATCH(g.N, (k_cg_update<N_><<<PF_CG_BLOCKS, PF_THREADS, 0, st>>>(
+                          g, w.Dinv, w.x, w.r, w.p, w.q, w.part, w.scal, w.flag, it)));
   }
   return cudaGetLastError();
 }

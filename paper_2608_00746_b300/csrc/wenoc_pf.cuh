@@ -70,8 +70,9 @@ struct PfWork {
   double* p;        //                    direction
   double* q;        //                    K p
   double* part;     // reduction partials (offsets in wenoc_pf.cu)
-  double* scal;     // [32]: M, B[0..N-1] | tol^2 at 8 | b.b/D at 16+p | r.r/D at 24+p
-  int* flag;        // [8]: label change, converged per phase at 1+p
+  double* scal;     // [64]: M, B[0..N-1] | tol^2 at 8 | b.b/D at 16+p | r.r/D at 24+p
+                    //       | beta at 32+p | alpha at 40+p
+  int* flag;        // [64]: label change, converged per phase at 1+p, CG tickets at 6, 7
 };
 
 // Launchers (wenoc_pf.cu), all asynchronous on st.
