@@ -354,13 +354,26 @@ constexpr long PART_TOTAL = PART_REF + (long)PF_CG_BLOCKS * 8;
 // in a fixed order (lane l adds blocks l, l + 32, ..., then a shuffle tree;
 // loads bypass L1: other blocks wrote them); returns the sums in lane 0.
 template <int N>
-__device__ __forceinline__ void sum_partials_warp(const double* part, long off, double (&v)[N]) {
+__device__ __forceinline__ void sum_partials_warp(const double* part, long off, int count,
+                                                  double (&v)[N]) {
   const int lane = threadIdx.x & 31;
+  constexpr int B = 8;
+  // one warp's critical path: loads go out in batches of B rows (in flight
+  // together), then their adds in block order
 #pragma unroll
   for (int p = 0; p < N; p++) v[p] = 0.0;
-  for (int b = lane; b < PF_CG_BLOCKS; b += 32) {
+  for (int b0 = 0; b0 < count; b0 += 32 * B) {
+    double t[B][N];
 #pragma unroll
-    for (int p = 0; p < N; p++) v[p] += __ldcg(part + off + (long)b * 8 + p);
+    for (int j = 0; j < B; j++) {
+      const int b = b0 + lane + 32 * j;
+#pragma unroll
+      for (int p = 0; p < N; p++) t[j][p] = b < count ? __ldcg(part + off + (long)b * 8 + p) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < B; j++)
+#pragma unroll
+      for (int p = 0; p < N; p++) v[p] += t[j][p];
   }
 #pragma unroll
   for (int p = 0; p < N; p++) {
@@ -465,8 +478,8 @@ __global__ void __launch_bounds__(PF_THREADS) k_cg_init(PfGeom g, const double* 
 template <int N>
 __global__ void k_cg_start(const double* part, double* scal, int* flag, double tol2) {
   double rz[N], ref[N];
-  sum_partials_warp<N>(part, PART_RZ, rz);
-  sum_partials_warp<N>(part, PART_REF, ref);
+  sum_partials_warp<N>(part, PART_RZ, PF_CG_BLOCKS, rz);
+  sum_partials_warp<N>(part, PART_REF, PF_CG_BLOCKS, ref);
   if (threadIdx.x != 0) return;
   scal[8] = tol2;
 #pragma unroll
@@ -536,7 +549,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_cg_matvec(PfGeom g, const double
   block_sum_small<N>(acc, part + PART_PQ + (long)blockIdx.x * 8);
   if (!last_block(flag + 6) || threadIdx.x >= 32) return;
   double pq[N];
-  sum_partials_warp<N>(part, PART_PQ, pq);
+  sum_partials_warp<N>(part, PART_PQ, (int)gridDim.x, pq);
   if (threadIdx.x == 0)
 #pragma unroll
     for (int p = 0; p < N; p++)
@@ -548,7 +561,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_cg_matvec(PfGeom g, const double
 // block sums them and sets, for the next iteration, r.r/D, the test
 // (converged: r.r/D <= tol^2 b.b/D) and beta = new r.r/D / old.
 template <int N>
-__global__ void __launch_bounds__(PF_THREADS) k_cg_update(PfGeom g,
+__global__ void __launch_bounds__(PF_THREADS, 8) k_cg_update(PfGeom g,
                                                           const double* __restrict__ Dinv,
                                                           double* __restrict__ x,
                                                           double* __restrict__ r,
@@ -585,7 +598,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_cg_update(PfGeom g,
   block_sum_small<N>(acc, part + onew + (long)blockIdx.x * 8);
   if (!last_block(flag + 7) || threadIdx.x >= 32) return;
   double rn[N];
-  sum_partials_warp<N>(part, onew, rn);
+  sum_partials_warp<N>(part, onew, (int)gridDim.x, rn);
   if (threadIdx.x == 0) {
     const double tol2 = scal[8];
 #pragma unroll
@@ -659,11 +672,24 @@ cudaError_t pf_qmap_project(const PfGeom& g, const PfWork& w, int warm, double t
 cudaError_t pf_cg_rounds(const PfGeom& g, const PfWork& w, int it0, int rounds, cudaStream_t st) {
   long eb = (g.ncell + PF_THREADS - 1) / PF_THREADS;
   const int dir_blocks = (int)(eb < 148 * 16 ? (eb < 1 ? 1 : eb) : 148 * 16);
+  // the matrix-vector pass: one wave of as many blocks as fit on the SMs
+  static int mv_per_sm[8] = {0};
+  int& mps = mv_per_sm[g.N];
+  if (mps == 0) {
+    int k = 0;
+    cudaError_t e = cudaSuccess;
+    PF_DISPATCH(g.N, (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_cg_matvec<N_>,
+                                                                       PF_THREADS, 0)));
+    if (e != cudaSuccess) return e;
+    mps = k < 1 ? 1 : (k > 8 ? 8 : k);
+  }
+  const int mv_blocks = 148 * mps;
+  if (mv_blocks > PF_CG_BLOCKS) return cudaErrorInvalidValue;  // partial rows
   for (int k = 0; k < rounds; k++) {
     const int it = it0 + k;
     PF_DISPATCH(g.N, (k_cg_dir<N_><<<dir_blocks, PF_THREADS, 0, st>>>(g, w.r, w.Dinv, w.p,
                                                                        w.scal, w.flag)));
-    PF_DISPATCH(g.N, (k_cg_matvec<N_><<<PF_CG_BLOCKS, PF_THREADS, 0, st>>>(
+    PF_DISPATCH(g.N, (k_cg_matvec<N_><<<mv_blocks, PF_THREADS, 0, st>>>(
                           g, w.w, w.D, w.p, w.q, w.part, w.scal, w.flag)));
     PF_DISPATCH(g.N, (k_cg_update<N_><<<PF_CG_BLOCKS, PF_THREADS, 0, st>>>(
                           g, w.Dinv, w.x, w.r, w.p, w.q, w.part, w.scal, w.flag, it)));
