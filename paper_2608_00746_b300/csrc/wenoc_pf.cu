@@ -350,38 +350,6 @@ constexpr long PART_TOTAL = PART_REF + (long)PF_CG_BLOCKS * 8;
 // however few lanes are active, so the reductions here are written to issue
 // few FP64 warp instructions.
 //
-// Sums of the per-block partials [PF_CG_BLOCKS][8] of N phases by one warp,
-// in a fixed order (lane l adds blocks l, l + 32, ..., then a shuffle tree;
-// loads bypass L1: other blocks wrote them); returns the sums in lane 0.
-template <int N>
-__device__ __forceinline__ void sum_partials_warp(const double* part, long off, int count,
-                                                  double (&v)[N]) {
-  const int lane = threadIdx.x & 31;
-  constexpr int B = 8;
-  // one warp's critical path: loads go out in batches of B rows (in flight
-  // together), then their adds in block order
-#pragma unroll
-  for (int p = 0; p < N; p++) v[p] = 0.0;
-  for (int b0 = 0; b0 < count; b0 += 32 * B) {
-    double t[B][N];
-#pragma unroll
-    for (int j = 0; j < B; j++) {
-      const int b = b0 + lane + 32 * j;
-#pragma unroll
-      for (int p = 0; p < N; p++) t[j][p] = b < count ? __ldcg(part + off + (long)b * 8 + p) : 0.0;
-    }
-#pragma unroll
-    for (int j = 0; j < B; j++)
-#pragma unroll
-      for (int p = 0; p < N; p++) v[p] += t[j][p];
-  }
-#pragma unroll
-  for (int p = 0; p < N; p++) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[p] += __shfl_down_sync(0xffffffffu, v[p], o);
-  }
-}
-
 // Block sum of N values per thread into out[0..N-1] (fixed order): a shared
 // tree over the 256 threads down to one warp, then its shuffle tree.
 template <int N>
@@ -408,6 +376,30 @@ __device__ __forceinline__ void block_sum_small(const double (&v)[N], double* ou
     }
   }
   __syncthreads();
+}
+
+// Sums of count per-block partial rows (8 doubles, N used) by the whole
+// block, in a fixed order: thread t adds rows t, t + 256, ... (their loads
+// in flight together), then block_sum_small; out[p] (shared) for every
+// thread afterwards.
+template <int N>
+__device__ __forceinline__ void sum_partials_block(const double* part, long off, int count,
+                                                   double* out) {
+  constexpr int R = (PF_CG_BLOCKS + PF_THREADS - 1) / PF_THREADS;
+  double t[R][N], v[N];
+#pragma unroll
+  for (int j = 0; j < R; j++) {
+    const int b = threadIdx.x + PF_THREADS * j;
+#pragma unroll
+    for (int p = 0; p < N; p++) t[j][p] = b < count ? __ldcg(part + off + (long)b * 8 + p) : 0.0;
+  }
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    v[p] = 0.0;
+#pragma unroll
+    for (int j = 0; j < R; j++) v[p] += t[j][p];
+  }
+  block_sum_small<N>(v, out);
 }
 
 // True in the block that finishes last (after its partials are written);
@@ -476,10 +468,11 @@ __global__ void __launch_bounds__(PF_THREADS) k_cg_init(PfGeom g, const double* 
 // warp); beta = 0 for the first directions; a phase whose start already
 // meets the test is converged.
 template <int N>
-__global__ void k_cg_start(const double* part, double* scal, int* flag, double tol2) {
-  double rz[N], ref[N];
-  sum_partials_warp<N>(part, PART_RZ, PF_CG_BLOCKS, rz);
-  sum_partials_warp<N>(part, PART_REF, PF_CG_BLOCKS, ref);
+__global__ void __launch_bounds__(PF_THREADS) k_cg_start(const double* part, double* scal,
+                                                         int* flag, double tol2) {
+  __shared__ double rz[N], ref[N];
+  sum_partials_block<N>(part, PART_RZ, PF_CG_BLOCKS, rz);
+  sum_partials_block<N>(part, PART_REF, PF_CG_BLOCKS, ref);
   if (threadIdx.x != 0) return;
   scal[8] = tol2;
 #pragma unroll
@@ -547,9 +540,9 @@ __global__ void __launch_bounds__(PF_THREADS) k_cg_matvec(PfGeom g, const double
     }
   }
   block_sum_small<N>(acc, part + PART_PQ + (long)blockIdx.x * 8);
-  if (!last_block(flag + 6) || threadIdx.x >= 32) return;
-  double pq[N];
-  sum_partials_warp<N>(part, PART_PQ, (int)gridDim.x, pq);
+  if (!last_block(flag + 6)) return;
+  __shared__ double pq[N];
+  sum_partials_block<N>(part, PART_PQ, (int)gridDim.x, pq);
   if (threadIdx.x == 0)
 #pragma unroll
     for (int p = 0; p < N; p++)
@@ -596,9 +589,9 @@ __global__ void __launch_bounds__(PF_THREADS, 8) k_cg_update(PfGeom g,
   }
   const long onew = PART_RZ + (long)((it + 1) & 1) * PF_CG_BLOCKS * 8;
   block_sum_small<N>(acc, part + onew + (long)blockIdx.x * 8);
-  if (!last_block(flag + 7) || threadIdx.x >= 32) return;
-  double rn[N];
-  sum_partials_warp<N>(part, onew, (int)gridDim.x, rn);
+  if (!last_block(flag + 7)) return;
+  __shared__ double rn[N];
+  sum_partials_block<N>(part, onew, (int)gridDim.x, rn);
   if (threadIdx.x == 0) {
     const double tol2 = scal[8];
 #pragma unroll
@@ -665,7 +658,7 @@ cudaError_t pf_qmap_project(const PfGeom& g, const PfWork& w, int warm, double t
   PF_DISPATCH(g.N, (k_qm_sums<N_><<<nb, PF_THREADS, 0, st>>>(g, w.R, w.D, w.lab, w.sumR, w.sumD)));
   PF_DISPATCH(g.N, (k_cg_init<N_><<<PF_CG_BLOCKS, PF_THREADS, 0, st>>>(
                         g, w.R, w.w, w.D, w.Dinv, w.lab, w.sumR, w.sumD, w.x, w.r, w.part, warm)));
-  PF_DISPATCH(g.N, (k_cg_start<N_><<<1, 32, 0, st>>>(w.part, w.scal, w.flag, tol2)));
+  PF_DISPATCH(g.N, (k_cg_start<N_><<<1, PF_THREADS, 0, st>>>(w.part, w.scal, w.flag, tol2)));
   return cudaGetLastError();
 }
 
