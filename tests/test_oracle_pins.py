@@ -661,3 +661,80 @@ def test_temperature_of_eq29_and_the_scheme_ordering():
     assert err["js"][0] > 1e-3
     assert err["w"][0] < 1e-6 and err["w"][0] > err["w"][1]
     assert err["c"][0] < 0.1 * err["w"][0]
+
+
+# ---------------------------------------------------------------- Sec. 4.1.5 air-helium shock tube
+from exact_riemann import sample as _riemann  # noqa: E402
+
+AIR = (1.4, 1.0, 0.0, 1.0)          # (gamma, rho, u, P) on 0 < x <= 1 (Eq. 31)
+HELIUM = (1.6, 0.125, 0.0, 0.1)     # on 1 < x < 2
+
+
+def _shock_tube(n, T=0.4, phase_field=False):
+    """Eq. 31 on [0, 2] with n cells, outflow, HLLC, CFL 0.4, to t = T
+    (the figure's t = 0.4: at t = 1 the shock would have left the domain);
+    phase 1 helium, phase 2 air.  Returns x, the state and the grid."""
+    from oracle import pf
+    dx = 2.0 / n
+    x = (np.arange(n) + 0.5) * dx
+    g = oracle.Grid((n,), (dx,), [1.6, 1.4], [0.0, 0.0], [0.0, 0.0], flux="hllc",
+                    bc=("outflow",) * 6)
+    a1 = (x > 1.0).astype(float)
+    V = np.array([0.125 * a1, 1.0 * (1 - a1), np.zeros(n), np.where(x > 1.0, 0.1, 1.0), a1, 1 - a1])
+    U = oracle.prim_to_cons(g, V)
+    t = 0.0
+    while t < T - 1e-14:
+        dt = min(0.4 / oracle.max_rate(g, U), T - t)
+        if phase_field:
+            U, _, _ = pf.full_step(g, U, dt=dt)
+        else:
+            U, _ = oracle.rk3_step(g, U, dt=dt)
+        t += dt
+    return x, U, g
+
+
+def test_exact_riemann_solution_is_consistent():
+    """The exact solution used below: the shock satisfies the
+    Rankine-Hugoniot mass and momentum conditions and the left star state
+    lies on the air isentrope."""
+    _, st = _riemann(np.array([0.0]), AIR, HELIUM)
+    s, p, u = st["shock"], st["p"], st["u"]
+    rR, uR, pR = HELIUM[1:]
+    assert rR * (s - uR) == pytest.approx(st["rho_r"] * (s - u), rel=1e-12)
+    assert pR + rR * (s - uR) ** 2 == pytest.approx(p + st["rho_r"] * (s - u) ** 2, rel=1e-12)
+    assert p / st["rho_l"] ** 1.4 == pytest.approx(AIR[3] / AIR[1] ** 1.4, rel=1e-12)
+
+
+@pytest.mark.parametrize("phase_field", [False, True])
+def test_air_helium_shock_tube_converges_to_the_exact_solution(phase_field):
+    """Sec. 4.1.5: the density and helium fraction converge to the exact
+    two-gas Riemann solution in L1 at about first order (the optimal rate
+    with a shock and an interface), with and without the Phase-Field
+    mechanism; fractions stay in [0, 1]."""
+    errs = []
+    for n in (100, 400):
+        x, U, g = _shock_tube(n, phase_field=phase_field)
+        ex, _ = _riemann((x - 1.0) / 0.4, AIR, HELIUM)
+        dx = 2.0 / n
+        errs.append((dx * np.abs(U[0] + U[1] - ex[0]).sum(), dx * np.abs(U[4] - ex[3]).sum()))
+        assert U[4:6].min() >= -1e-12 and U[4:6].max() <= 1 + 1e-12
+    (r1, a1), (r4, a4) = errs
+    assert r1 < 1.5e-2 and a1 < 2.5e-2
+    assert np.log2(r1 / r4) / 2 > 0.8 and np.log2(a1 / a4) / 2 > 0.6
+
+
+def _interface_thickness(a, dx):
+    """N_I of Eq. 30: int H(alpha) / (dx int |grad alpha|), H = 1 on
+    [0.05, 0.95] (1-D, midpoint integrals)."""
+    H = ((a >= 0.05) & (a <= 0.95)).sum() * dx
+    return H / (dx * np.abs(np.diff(a)).sum())
+
+
+def test_air_helium_interface_thickness():
+    """Sec. 4.1.5 (Fig. of N_I): with the Phase-Field mechanism the
+    interface stays 4 to 5 cells thick (Eq. 30) to t = 0.4 at dx = 0.01;
+    without it the interface has spread further."""
+    _, Up, _ = _shock_tube(200, phase_field=True)
+    _, Uh, _ = _shock_tube(200, phase_field=False)
+    n_pf, n_hb = _interface_thickness(Up[4], 0.01), _interface_thickness(Uh[4], 0.01)
+    assert 4.0 <= n_pf <= 5.0 and n_hb > n_pf
