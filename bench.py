@@ -341,10 +341,10 @@ def run_ours(args):
     if args.profile_pf:
         g, U = make_grid("fp64")
         g.set_pf_workspace(U.device)
-        g.step(cfl=case.cfl, nsteps=args.warmup, tol=1e-10)
+        g.step(cfl=case.cfl, nsteps=args.warmup, tol=1e-12)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        g.step(cfl=case.cfl, nsteps=args.steps, tol=1e-10)
+        g.step(cfl=case.cfl, nsteps=args.steps, tol=1e-12)
         torch.cuda.synchronize()
         ms = (time.perf_counter() - t0) * 1e3 / max(args.steps, 1)
         g.sync_status()
@@ -582,17 +582,17 @@ def run_variants(args, rank, make_grid, timed_steps):
 def time_phase_field(make_grid, K=20):
     """Full time steps of Sec. 2.2 on the headline shock-bubble: the
     hyperbolic step, Eq. 28, the Q-map of Eq. 4 (conjugate gradients to a
-    D-weighted residual of 1e-10, started from the previous step's Q) and
+    D-weighted residual of 1e-12, started from the previous step's Q) and
     the Phase-Field step, FP64; then each part timed alone."""
     import torch
     g, U = make_grid("fp64")
     g.set_pf_workspace(U.device)
-    g.step(cfl=0.2, nsteps=3, tol=1e-10)
+    g.step(cfl=0.2, nsteps=3, tol=1e-12)
     torch.cuda.synchronize()
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(s)
-    g.step(cfl=0.2, nsteps=K, tol=1e-10)
+    g.step(cfl=0.2, nsteps=K, tol=1e-12)
     e1.record(s)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / K
@@ -606,7 +606,7 @@ def time_phase_field(make_grid, K=20):
         ev[1].record(s)
         g.cac_rhs(U)
         ev[2].record(s)
-        Q, _, _ = g.qmap(U, Q=Q, tol=1e-10, warm=Q is not None)
+        Q, _, _ = g.qmap(U, Q=Q, tol=1e-12, warm=Q is not None)
         ev[3].record(s)
         g.pf_step(Q, dt)
         ev[4].record(s)
@@ -617,7 +617,7 @@ def time_phase_field(make_grid, K=20):
     cells = int(np.prod(g.shape))
     del g, U
     return {"workload": "headline shock-bubble, full time step (hyperbolic + Eq. 28 + Eq. 4 + "
-                        "Phase-Field step), Q-map tolerance 1e-10",
+                        "Phase-Field step), Q-map tolerance 1e-12",
             "steps": K, "value": round(cells * 3 / (ms * 1e-3) / 1e6, 3), "unit": "Mcell/s",
             "ms_per_step": round(ms, 4), "qmap_cg_iterations_last": iters,
             "qmap_label_rounds_last": rounds, "qmap_residual_last": res,

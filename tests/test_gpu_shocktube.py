@@ -1,0 +1,99 @@
+"""The air-helium shock tube of Sec. 4.1.5 on the GPU.
+
+Parity is checked on the operators, at states along the oracle's run: the
+hyperbolic rhs, Eq. 28 and the Phase-Field step with a common Q, all to
+1e-12 (this is also the 1-D coverage of the mechanism).  Whole trajectories
+are not compared step by step: where a phase is absent on one side of the
+tube its mass is exactly 0 in one implementation and a rounding residue
+(~1e-17) in the other, and Eq. 16 reconstructs the fraction with the
+weights of that mass, so the two runs part at the 1e-5 level within a step
+while both stay correct.  Instead each run is held against the exact
+two-gas Riemann solution at t = 0.4, with the interface 4-5 cells thick
+(Eq. 30) when the mechanism is on."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import pf
+from paper_2608_00746_b300 import wenoc
+
+from exact_riemann import sample
+from gpu_util import rhs_err, state_err, to_dev
+
+pytestmark = pytest.mark.gpu
+AIR = (1.4, 1.0, 0.0, 1.0)
+HELIUM = (1.6, 0.125, 0.0, 0.1)
+
+
+def _setup(n):
+    dx = 2.0 / n
+    x = (np.arange(n) + 0.5) * dx
+    args = ((n,), (dx,), [1.6, 1.4], [0.0, 0.0], [0.0, 0.0])
+    go = oracle.Grid(*args, flux="hllc", bc=("outflow",) * 6)
+    g = wenoc.Grid(*args, flux="hllc", bc=("outflow",) * 6)
+    a1 = (x > 1.0).astype(float)
+    V = np.array([0.125 * a1, 1.0 - a1, np.zeros(n), np.where(x > 1.0, 0.1, 1.0), a1, 1 - a1])
+    return x, go, g, oracle.prim_to_cons(go, V)
+
+
+def _oracle_states(go, U, steps=(0, 5, 20, 60)):
+    out, k = [], 0
+    for s in steps:
+        while k < s:
+            U, _ = oracle.rk3_step(go, U, cfl=0.4)
+            k += 1
+        out.append(U.copy())
+    return out
+
+
+def test_shock_tube_operators_match_oracle(gpu):
+    """Hyperbolic rhs, Eq. 28 and the Phase-Field step (common Q, limits on)
+    at oracle states of steps 0, 5, 20 and 60."""
+    x, go, g, U0 = _setup(200)
+    for U in _oracle_states(go, U0):
+        Ud = to_dev(U)
+        g.bind(Ud).set_pf_workspace(Ud.device)
+        L = g.rhs(Ud).cpu().numpy()
+        err = rhs_err(L, oracle.rhs(go, U), U, oracle.max_rate(go, U), 2, 1)
+        assert (err <= 1e-12).all(), err
+        R = g.cac_rhs(Ud).cpu().numpy()
+        R_or, _, _ = pf.cac_rhs(go, U)
+        assert np.abs(R - R_or).max() <= 1e-12 * max(np.abs(R_or).max(), 1e-300)
+        Q, _ = pf.qmap(go, pf.fractions(go, U), R_or)
+        dt = 0.4 / oracle.max_rate(go, U)
+        Un = pf.pf_step(go, U, Q * 1e3, dt)     # gradients large enough to be limited
+        g.pf_step(to_dev(Q * 1e3), dt)
+        g.sync_status()
+        err = state_err(Ud.cpu().numpy(), Un, 2, 1)
+        assert (err <= 1e-12).all(), err
+
+
+@pytest.mark.parametrize("phase_field", [False, True])
+def test_shock_tube_against_exact_solution(gpu, phase_field):
+    n, T = 200, 0.4
+    x, go, g, U0 = _setup(n)
+    Ud = to_dev(U0)
+    g.bind(Ud)
+    if phase_field:
+        g.set_pf_workspace(Ud.device)
+    t = 0.0
+    while t < T - 1e-14:
+        # the time step from the GPU's own state (CFL 0.4), the last one cut to T
+        dt = min(0.4 / oracle.max_rate(go, Ud.cpu().numpy()), T - t)
+        if phase_field:
+            g.step(dt=dt, tol=1e-12)
+        else:
+            g.rk_step(dt=dt)
+        t += dt
+    g.sync_status()
+    U = Ud.cpu().numpy()
+    ex, _ = sample((x - 1.0) / T, AIR, HELIUM)
+    dx = 2.0 / n
+    l1_rho = dx * np.abs(U[0] + U[1] - ex[0]).sum()
+    l1_a = dx * np.abs(U[4] - ex[3]).sum()
+    assert l1_rho < 8e-3 and l1_a < 1.5e-2, (l1_rho, l1_a)
+    assert U[4:6].min() >= -1e-12 and U[4:6].max() <= 1 + 1e-12
+    a = U[4]
+    N_I = ((a >= 0.05) & (a <= 0.95)).sum() / np.abs(np.diff(a)).sum()
+    if phase_field:
+        assert 4.0 <= N_I <= 5.0, N_I
