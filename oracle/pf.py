@@ -213,9 +213,14 @@ def qmap(g: Grid, phi: np.ndarray, R: np.ndarray):
                 continue
             rk = r[cells] - Dg[cells] * (r[cells].sum() / Dg[cells].sum())
             rp[cells] = rk
-            Ak = A[cells][:, cells].tocsc()
+            # the same system scaled symmetrically by D^-1/2 (unit diagonal):
+            # with coefficients down to denormal sizes the unscaled
+            # factorisation breaks down; the solution is unchanged
+            sc = 1.0 / np.sqrt(Dg[cells])
+            Ak = (sp.diags(sc) @ A[cells][:, cells] @ sp.diags(sc)).tocsc()
+            rk = rk * sc
             # pin the first cell of the region (its constant is free)
-            q[cells[1:]] = spla.spsolve(Ak[1:, 1:], rk[1:])
+            q[cells[1:]] = spla.spsolve(Ak[1:, 1:], rk[1:]) * sc[1:]
         Q[p] = q.reshape(R[p].shape)
         Rp[p] = rp.reshape(R[p].shape)
     return Q, Rp
