@@ -413,14 +413,15 @@ def test_equilibrium_and_conservation_five_phase_2d():
 
 
 @pytest.mark.slow
-def test_fifth_order_on_smooth_advection():
+@pytest.mark.parametrize("scheme", ["c", "cl"])
+def test_fifth_order_on_smooth_advection(scheme):
     """Sec. 4.1.4: WENO-C is fifth order on alpha_1 = 0.2 (3 + sin 2 pi x),
-    dt = dx^(5/3), t = 1."""
+    dt = dx^(5/3), t = 1; and WENO-CL too (App. A repeats the test)."""
     errs = []
     ns = [20, 40, 80]
     for n in ns:
         c = inputs.smooth_advection_1d(n)
-        g = grid_of(c)
+        g = grid_of(c, scheme=scheme)
         U = oracle.prim_to_cons(g, c.V)
         dt = c.meta["dt"]
         nstep = int(np.ceil(1.0 / dt))
@@ -670,7 +671,7 @@ AIR = (1.4, 1.0, 0.0, 1.0)          # (gamma, rho, u, P) on 0 < x <= 1 (Eq. 31)
 HELIUM = (1.6, 0.125, 0.0, 0.1)     # on 1 < x < 2
 
 
-def _shock_tube(n, T=0.4, phase_field=False):
+def _shock_tube(n, T=0.4, phase_field=False, scheme="c"):
     """Eq. 31 on [0, 2] with n cells, outflow, HLLC, CFL 0.4, to t = T
     (the figure's t = 0.4: at t = 1 the shock would have left the domain);
     phase 1 helium, phase 2 air.  Returns x, the state and the grid."""
@@ -678,7 +679,7 @@ def _shock_tube(n, T=0.4, phase_field=False):
     dx = 2.0 / n
     x = (np.arange(n) + 0.5) * dx
     g = oracle.Grid((n,), (dx,), [1.6, 1.4], [0.0, 0.0], [0.0, 0.0], flux="hllc",
-                    bc=("outflow",) * 6)
+                    bc=("outflow",) * 6, scheme=scheme)
     a1 = (x > 1.0).astype(float)
     V = np.array([0.125 * a1, 1.0 * (1 - a1), np.zeros(n), np.where(x > 1.0, 0.1, 1.0), a1, 1 - a1])
     U = oracle.prim_to_cons(g, V)
@@ -705,15 +706,15 @@ def test_exact_riemann_solution_is_consistent():
     assert p / st["rho_l"] ** 1.4 == pytest.approx(AIR[3] / AIR[1] ** 1.4, rel=1e-12)
 
 
-@pytest.mark.parametrize("phase_field", [False, True])
-def test_air_helium_shock_tube_converges_to_the_exact_solution(phase_field):
+@pytest.mark.parametrize("scheme,phase_field", [("c", False), ("c", True), ("cl", False)])
+def test_air_helium_shock_tube_converges_to_the_exact_solution(scheme, phase_field):
     """Sec. 4.1.5: the density and helium fraction converge to the exact
     two-gas Riemann solution in L1 at about first order (the optimal rate
     with a shock and an interface), with and without the Phase-Field
-    mechanism; fractions stay in [0, 1]."""
+    mechanism, and with WENO-CL (App. A); fractions stay in [0, 1]."""
     errs = []
     for n in (100, 400):
-        x, U, g = _shock_tube(n, phase_field=phase_field)
+        x, U, g = _shock_tube(n, phase_field=phase_field, scheme=scheme)
         ex, _ = _riemann((x - 1.0) / 0.4, AIR, HELIUM)
         dx = 2.0 / n
         errs.append((dx * np.abs(U[0] + U[1] - ex[0]).sum(), dx * np.abs(U[4] - ex[3]).sum()))
