@@ -84,10 +84,11 @@ typedef struct {
                                  a pencil (30 updated) from a dynamic queue;
                                  > 0: each thread marches segments of seg
                                  cells of one pencil */
-  int block;                  /* threads per block of the segment sweep
-                                 (32..128); 0 = automatic; the window sweep
-                                 uses 128 */
-  int blocks_per_sm;          /* resident sweep blocks per SM (1..4); 0 = automatic */
+  int block;                  /* threads per sweep block, a multiple of 32
+                                 in 32..128; 0 = automatic (128) */
+  int blocks_per_sm;          /* resident sweep blocks per SM (1..32); 0 =
+                                 automatic (the window sweep: as many as
+                                 fit) */
   int scheme;                 /* WC_SCHEME_C: unity sum by Eq. 19 (WENO-C,
                                  default); WC_SCHEME_CL: the consistent limiter
                                  of Eq. 23-25 instead (WENO-CL, Sec. 3.4);

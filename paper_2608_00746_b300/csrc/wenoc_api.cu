@@ -110,7 +110,7 @@ extern "C" wc_status wc_init_grid(const wc_grid_desc* desc, wc_grid** out) {
     return WC_ERR_UNSUPPORTED;
   if (d.precision == WC_PREC_LEARNED && d.nphase > 3) return WC_ERR_UNSUPPORTED;
   if (d.seg < 0 || d.block < 0 || d.block > 128 || (d.block % 32) != 0) return WC_ERR_ARG;
-  if (d.blocks_per_sm < 0 || d.blocks_per_sm > 4) return WC_ERR_ARG;
+  if (d.blocks_per_sm < 0 || d.blocks_per_sm > 32) return WC_ERR_ARG;
   if (d.scheme < WC_SCHEME_C || d.scheme > WC_SCHEME_JS) return WC_ERR_ARG;
   const bool comparison = d.scheme == WC_SCHEME_W || d.scheme == WC_SCHEME_JS;
   if (comparison && d.precision != WC_PREC_FP64) return WC_ERR_UNSUPPORTED;
@@ -254,7 +254,12 @@ extern "C" wc_status wc_temperature(const wc_grid* gc, const double* U, const do
 }
 
 // ------------------------------------------------------------------ sweeps
-static int sweep_block(const wc_grid* g) { return g->d.block > 0 ? g->d.block : 128; }
+// Threads per sweep block: as given, else 128 for the segment march and
+// WIN_BLOCK for the window sweep.
+static int sweep_block(const wc_grid* g) {
+  if (g->d.block > 0) return g->d.block;
+  return g->d.seg > 0 ? 128 : WIN_BLOCK;
+}
 
 // Threads of one sweep launch: a whole number of blocks per SM on all 148
 // SMs, so every SM sub-partition gets the same number of warps (the sweep is

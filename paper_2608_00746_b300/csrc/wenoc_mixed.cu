@@ -8,8 +8,8 @@ namespace wc {
 template <int N, int D>
 static cudaError_t go(const SweepArgs& a, const Mat& m, int block, cudaStream_t st) {
   if (a.nwin > 0) {
-    const int bps = (int)(a.max_threads / (148L * 128));  // 0: occupancy limit
-    return launch_window<N, D, float, float, 0>(a, m, bps, st);
+    const int bps = (int)(a.max_threads / (148L * block));  // 0: occupancy limit
+    return launch_window<N, D, float, float, 0>(a, m, block, bps, st);
   }
   const int smem = Ring<N, D, float>::BYTES * block;
   auto k = k_sweep<N, D, float, float>;

@@ -16,6 +16,7 @@ namespace wc {
 
 constexpr int WIN = 30;        // cells updated per window
 constexpr int WIN_SLOTS = 36;  // cells c0-3 .. c0+32 held in shared memory
+constexpr int WIN_BLOCK = 128;  // threads per block unless configured
 
 template <int N, int D, typename T>
 struct WinSmem {
@@ -291,11 +292,16 @@ __global__ void __launch_bounds__(128) k_sweep_win(SweepArgs a, Mat m) {
   }
 }
 
-// Launch of the window sweep: bps resident blocks of 128 threads on every SM
-// (persistent; bps <= 0: the occupancy limit), at most one warp per window.
+// Launch of the window sweep: bps resident blocks of `block` threads (32,
+// 64, 96 or 128: one to four warps) on every SM (persistent; bps <= 0: the
+// occupancy limit), at most one warp per window.  Smaller blocks let the
+// register file hold more warps (at 104 registers a thread an SM takes 19
+// one-warp blocks but only 4 blocks of four warps); the FP64 sweep runs
+// equally fast with either, its FP64 pipe being as busy at 16 warps as at 19.
 template <int N, int D, typename T, typename TF, int LW>
-cudaError_t launch_window(const SweepArgs& a0, const Mat& m, int bps, cudaStream_t st) {
-  constexpr int block = 128;
+cudaError_t launch_window(const SweepArgs& a0, const Mat& m, int block, int bps,
+                          cudaStream_t st) {
+  if (block < 32 || block > 128 || block % 32 != 0) return cudaErrorInvalidValue;
   const int smem = WinSmem<N, D, T>::WARP_DOUBLES * 8 * (block / 32);
   auto k = k_sweep_win<N, D, T, TF, LW>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -303,15 +309,17 @@ cudaError_t launch_window(const SweepArgs& a0, const Mat& m, int bps, cudaStream
   const long items = a0.npencil * a0.nwin;
   if (bps <= 0) {
     // as many resident blocks as registers and shared memory allow (queried
-    // once per instantiation; every caller gets the same answer)
-    static int occ = 0;
-    if (occ == 0) {
+    // once per instantiation and block size; every caller gets the same
+    // answer)
+    static int occ[4] = {0, 0, 0, 0};
+    int& o = occ[block / 32 - 1];
+    if (o == 0) {
       int q = 0;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k, block, smem);
       if (e != cudaSuccess) return e;
-      occ = q < 1 ? 1 : q;
+      o = q < 1 ? 1 : q;
     }
-    bps = occ;
+    bps = o;
   }
   long blocks = 148L * bps;
   const long need = (items + block / 32 - 1) / (block / 32);

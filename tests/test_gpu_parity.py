@@ -145,3 +145,20 @@ def test_rhs_parity_segment_schedule(gpu, name, seg):
     gg.sync_status()
     err = rhs_err(L, L_or, U, oracle.max_rate(go, U), case.N, case.dim)
     assert (err <= TOL).all(), (name, seg, err)
+
+
+@pytest.mark.parametrize("block", [32, 64, 128])
+@pytest.mark.parametrize("name", ["shock_bubble_2d_ragged", "spheres_3d_ragged"])
+def test_rhs_parity_window_block_sizes(gpu, name, block):
+    """The window sweep gives the same dU/dt whatever the warps per block
+    (each warp takes whole windows; the block size only changes residency)."""
+    case = SMALL_CASES[name]()
+    go, gg = grids(case, block=block)
+    U = oracle.prim_to_cons(go, case.V)
+    L_or = oracle.rhs(go, U)
+    Ud = to_dev(U)
+    gg.bind(Ud)
+    L = gg.rhs(Ud).cpu().numpy()
+    gg.sync_status()
+    err = rhs_err(L, L_or, U, oracle.max_rate(go, U), case.N, case.dim)
+    assert (err <= TOL).all(), (name, block, err)
