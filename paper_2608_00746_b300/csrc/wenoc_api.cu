@@ -48,7 +48,16 @@ struct wc_grid {
   PfGeom pg;
   int pf_iters = 0, pf_label_rounds = 0, pf_have_q = 0;
   double pf_resid = 0.0;
+  // one round of CG iterations as a graph (made at the first Q-map after a
+  // workspace is bound) and the stream it is captured on
+  cudaStream_t pf_cap = nullptr;
+  cudaGraphExec_t pf_cg_exec = nullptr;
 };
+
+static void drop_cg_graph(wc_grid* g) {
+  if (g->pf_cg_exec) cudaGraphExecDestroy(g->pf_cg_exec);
+  g->pf_cg_exec = nullptr;
+}
 
 static wc_status fail(wc_grid* g, wc_status s, const char* msg) {
   if (g) snprintf(g->err, sizeof(g->err), "%s", msg);
@@ -151,6 +160,8 @@ extern "C" wc_status wc_init_grid(const wc_grid_desc* desc, wc_grid** out) {
 extern "C" void wc_destroy(wc_grid* g) {
   if (!g) return;
   for (cudaEvent_t ev : g->tev) cudaEventDestroy(ev);
+  drop_cg_graph(g);
+  if (g->pf_cap) cudaStreamDestroy(g->pf_cap);
   delete g;
 }
 extern "C" int wc_nvar(const wc_grid* g) { return g ? g->nv : 0; }
@@ -554,6 +565,7 @@ extern "C" wc_status wc_set_pf_workspace(wc_grid* g, void* ws_dev, size_t bytes)
   pg.N = g->d.nphase;
   pg.nv = g->nv;
   pg.a0 = g->d.nphase + g->d.dim + 1;
+  drop_cg_graph(g);  // it holds the previous workspace's pointers
   g->pf_bound = true;
   g->pf_have_q = 0;
   return WC_OK;
@@ -608,7 +620,17 @@ static wc_status qmap(wc_grid* g, const double* U, const double* R, double* Q, d
   g->pf_label_rounds = rounds;
   e = pf_qmap_project(g->pg, g->pw, warm, tol * tol, st);
   if (e != cudaSuccess) return cuda_fail(g, e, "qmap project");
-  const int CR = 25;
+  // CG in rounds of CR iterations, each round one graph launch (its 3 CR
+  // kernels without a host launch between them), the test read after each
+  const int CR = 24;
+  if (!g->pf_cg_exec) {
+    if (!g->pf_cap) e = cudaStreamCreateWithFlags(&g->pf_cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = pf_cg_graph(g->pg, g->pw, CR, g->pf_cap, &g->pf_cg_exec);
+    if (e != cudaSuccess) {
+      g->pf_cg_exec = nullptr;
+      return cuda_fail(g, e, "qmap cg graph");
+    }
+  }
   const int N = g->d.nphase;
   int it = 0;
   int flags[8] = {0};
@@ -623,7 +645,7 @@ static wc_status qmap(wc_grid* g, const double* U, const double* R, double* Q, d
   };
   int done = all_done();  // the start may meet the test already
   while (done == 0 && it < maxit) {
-    e = pf_cg_rounds(g->pg, g->pw, it, CR, st);
+    e = cudaGraphLaunch(g->pf_cg_exec, st);
     if (e != cudaSuccess) return cuda_fail(g, e, "qmap cg");
     it += CR;
     done = all_done();

@@ -662,10 +662,9 @@ cudaError_t pf_qmap_project(const PfGeom& g, const PfWork& w, int warm, double t
   return cudaGetLastError();
 }
 
-cudaError_t pf_cg_rounds(const PfGeom& g, const PfWork& w, int it0, int rounds, cudaStream_t st) {
-  long eb = (g.ncell + PF_THREADS - 1) / PF_THREADS;
-  const int dir_blocks = (int)(eb < 148 * 16 ? (eb < 1 ? 1 : eb) : 148 * 16);
-  // the matrix-vector pass: one wave of as many blocks as fit on the SMs
+// Blocks of the matrix-vector pass: one wave of as many blocks as fit on
+// the SMs (queried once per phase count), fewer on a small grid.
+cudaError_t pf_cg_matvec_blocks(const PfGeom& g, int* blocks) {
   static int mv_per_sm[8] = {0};
   int& mps = mv_per_sm[g.N];
   if (mps == 0) {
@@ -676,18 +675,55 @@ cudaError_t pf_cg_rounds(const PfGeom& g, const PfWork& w, int it0, int rounds, 
     if (e != cudaSuccess) return e;
     mps = k < 1 ? 1 : (k > 8 ? 8 : k);
   }
-  const int mv_blocks = 148 * mps;
-  if (mv_blocks > PF_CG_BLOCKS) return cudaErrorInvalidValue;  // partial rows
+  const long eb = (g.ncell + PF_THREADS - 1) / PF_THREADS;
+  *blocks = (int)(eb < 148L * mps ? (eb < 1 ? 1 : eb) : 148L * mps);
+  return *blocks > PF_CG_BLOCKS ? cudaErrorInvalidValue : cudaSuccess;  // partial rows
+}
+
+cudaError_t pf_cg_rounds(const PfGeom& g, const PfWork& w, int it0, int rounds, cudaStream_t st) {
+  const long eb = (g.ncell + PF_THREADS - 1) / PF_THREADS;
+  const int dir_blocks = (int)(eb < 148 * 16 ? (eb < 1 ? 1 : eb) : 148 * 16);
+  // the update pass: PF_CG_BLOCKS blocks, fewer on a small grid (its last
+  // block sums one partial per block launched)
+  const int up_blocks = (int)(eb < PF_CG_BLOCKS ? (eb < 1 ? 1 : eb) : PF_CG_BLOCKS);
+  int mv_blocks = 0;
+  cudaError_t e = pf_cg_matvec_blocks(g, &mv_blocks);
+  if (e != cudaSuccess) return e;
   for (int k = 0; k < rounds; k++) {
     const int it = it0 + k;
     PF_DISPATCH(g.N, (k_cg_dir<N_><<<dir_blocks, PF_THREADS, 0, st>>>(g, w.r, w.Dinv, w.p,
                                                                        w.scal, w.flag)));
     PF_DISPATCH(g.N, (k_cg_matvec<N_><<<mv_blocks, PF_THREADS, 0, st>>>(
                           g, w.w, w.D, w.p, w.q, w.part, w.scal, w.flag)));
-    PF_DISPATCH(g.N, (k_cg_update<N_><<<PF_CG_BLOCKS, PF_THREADS, 0, st>>>(
+    PF_DISPATCH(g.N, (k_cg_update<N_><<<up_blocks, PF_THREADS, 0, st>>>(
                           g, w.Dinv, w.x, w.r, w.p, w.q, w.part, w.scal, w.flag, it)));
   }
   return cudaGetLastError();
+}
+
+// The launches of pf_cg_rounds(g, w, 0, rounds) recorded on `cap` (a stream
+// of the caller's, not the legacy default stream) as one executable graph:
+// replayed on any stream, it runs `rounds` iterations from any even
+// iteration count (the kernels read the iteration only for the parity of
+// the reduction buffer).  It holds the pointers of w and the geometry g.
+cudaError_t pf_cg_graph(const PfGeom& g, const PfWork& w, int rounds, cudaStream_t cap,
+                        cudaGraphExec_t* exec) {
+  if (rounds % 2 != 0) return cudaErrorInvalidValue;
+  int mv_blocks = 0;
+  cudaError_t e = pf_cg_matvec_blocks(g, &mv_blocks);  // the query stays out of the capture
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const cudaError_t el = pf_cg_rounds(g, w, 0, rounds, cap);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cap, &graph);
+  if (el != cudaSuccess || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return el != cudaSuccess ? el : e;
+  }
+  e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  return e;
 }
 
 }  // namespace wc

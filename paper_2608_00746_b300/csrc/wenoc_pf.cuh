@@ -93,5 +93,9 @@ cudaError_t pf_qmap_project(const PfGeom& g, const PfWork& w, int warm, double t
 // w.flag[1 + p] set once phase p meets the test; w.scal[24 + p] holds its
 // last r.r/D and w.scal[16 + p] the reference b.b/D.
 cudaError_t pf_cg_rounds(const PfGeom& g, const PfWork& w, int it0, int rounds, cudaStream_t st);
+// The same launches for iterations 0 .. rounds-1 (rounds even) as an
+// executable graph captured on `cap`.
+cudaError_t pf_cg_graph(const PfGeom& g, const PfWork& w, int rounds, cudaStream_t cap,
+                        cudaGraphExec_t* exec);
 
 }  // namespace wc
