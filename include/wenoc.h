@@ -440,6 +440,16 @@ void wc_last_error(const wc_grid *g, char *buf, size_t n);
 wc_status wc_fp64_peak_kernel(int blocks, int threads, int iters, double *sink_dev,
                               double *flops, void *stream);
 
+/* The binary64 <-> binary32 conversions of the reduced-precision sweeps
+ * (integer-pipe arithmetic on the IEEE 754 formats, the hardware conversion
+ * for zeros, subnormals, infinities, NaNs and overflow): f_dev[i] = x_dev[i]
+ * rounded to binary32 (nearest, ties to even) and back_dev[i] = f_dev[i]
+ * widened to binary64, for i < n (device arrays of n elements).  The paper
+ * has no counterpart; it lets a test hold them to the hardware conversions
+ * bit for bit.  Asynchronous on stream. */
+wc_status wc_convert_f32(const double *x_dev, float *f_dev, double *back_dev, long n,
+                         void *stream);
+
 #ifdef __cplusplus
 }
 #endif

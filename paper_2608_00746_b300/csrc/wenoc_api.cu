@@ -832,6 +832,25 @@ extern "C" wc_status wc_fp64_peak_kernel(int blocks, int threads, int iters, dou
   return cudaGetLastError() == cudaSuccess ? WC_OK : WC_ERR_CUDA;
 }
 
+// ------------------------------------------------------------------ conversion check
+__global__ void k_convert_f32(const double* x, float* f, double* back, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    const float v = f64_to_f32(x[i]);
+    f[i] = v;
+    back[i] = f32_to_f64(v);
+  }
+}
+
+extern "C" wc_status wc_convert_f32(const double* x, float* f, double* back, long n,
+                                    void* stream) {
+  if (n < 0 || (n > 0 && (!x || !f || !back))) return WC_ERR_ARG;
+  if (n == 0) return WC_OK;
+  const long blocks = (n + 255) / 256 < 148L * 8 ? (n + 255) / 256 : 148L * 8;
+  k_convert_f32<<<(unsigned)blocks, 256, 0, S(stream)>>>(x, f, back, n);
+  return cudaGetLastError() == cudaSuccess ? WC_OK : WC_ERR_CUDA;
+}
+
 // ------------------------------------------------------------------ fixed-scratch stepping
 // Used by wc_rk_step_noalloc (wenoc_noalloc.cu): runs wc_rk_step on state U
 // with the stage buffers, accumulator, rate and status words placed in the

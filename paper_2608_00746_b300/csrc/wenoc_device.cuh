@@ -132,10 +132,67 @@ __device__ __forceinline__ double dmin(double a, double b) { return dkey(b) < dk
 __device__ __forceinline__ double dmax(double a, double b) { return dkey(b) > dkey(a) ? b : a; }
 __device__ __forceinline__ float dmin(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ float dmax(float a, float b) { return fmaxf(a, b); }
+// x < 0, x >= 0 and x > 1 with the IEEE results for every double (-0 is not
+// below zero; a NaN compares false), decided on the bit pattern
+__device__ __forceinline__ bool lt0_ieee(double x) {
+  const long long b = dbits(x);
+  const unsigned long long mag = (unsigned long long)(b & 0x7FFFFFFFFFFFFFFFLL);
+  return b < 0 && mag - 1ull < 0x7FF0000000000000ull;  // nonzero, not NaN
+}
+__device__ __forceinline__ bool ge0_ieee(double x) {
+  const long long b = dbits(x);
+  return (b >= 0 && b <= 0x7FF0000000000000LL) || b == (long long)0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool gt1_ieee(double x) {
+  const long long b = dbits(x);
+  return b > 0x3FF0000000000000LL && b <= 0x7FF0000000000000LL;
+}
 // infinite or NaN
 __device__ __forceinline__ bool not_finite(double x) {
   return (__double2hiint(x) & 0x7ff00000) == 0x7ff00000;
 }
+
+// ------------------------------------------------------------------ conversions
+// Between binary64 and binary32 on the integer pipe (hardware conversions
+// run on the FP64 pipe, the sweep's bottleneck), from the IEEE 754 formats:
+// sign, 11-bit exponent biased by 1023 and 52-bit fraction against sign,
+// 8-bit exponent biased by 127 and 23-bit fraction.  Values whose binary32
+// image is normal, and zeros (frequent: a uniform region has zero velocity
+// components and flat stencils), are converted here; subnormal results,
+// infinities, NaNs and overflowing values take the hardware conversion.
+//
+// binary64 -> binary32, round to nearest, ties to even: keep the top 23
+// fraction bits, add one when the 29 dropped bits are above half, or exactly
+// half with the kept bits odd (a carry into the exponent is the correct
+// result, up to infinity above the largest binary32).
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e - 897u < 254u) {  // binary32 exponent e - 896 in 1..254
+    unsigned r = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;
+    r += (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ? 1u : 0u;
+    return __uint_as_float(r | (hi & 0x80000000u));
+  }
+  if (e < 873u) return __uint_as_float(hi & 0x80000000u);  // |x| < 2^-150: a signed zero
+  return (float)x;
+}
+// binary32 -> binary64 (exact): exponent rebased by 1023 - 127 = 896, the 23
+// fraction bits on top of the 52.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned b = __float_as_uint(x), em = b & 0x7fffffffu;
+  if (em - 0x00800000u < 0x7f000000u)  // normal
+    return __hiloint2double((int)((b & 0x80000000u) | ((em >> 3) + (896u << 20))),
+                            (int)(em << 29));
+  if (em == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);  // a signed zero
+  return (double)x;
+}
+// T(x) and double(x) of the precision templates through the helpers above
+template <typename T> __device__ __forceinline__ T cvt(double x);
+template <> __device__ __forceinline__ double cvt<double>(double x) { return x; }
+template <> __device__ __forceinline__ float cvt<float>(double x) { return f64_to_f32(x); }
+__device__ __forceinline__ double wide(double x) { return x; }
+__device__ __forceinline__ double wide(float x) { return f32_to_f64(x); }
 
 // 2^-e(m) with e(m) the binary exponent of m > 0 (m * scale in [1, 2)), or 0
 // when m is outside [2^-1000, 2^1000] (caller takes a slower exact path).
@@ -447,8 +504,8 @@ __device__ __forceinline__ void reconstruct_offset(const W6<T>& w, const Stencil
                                                    double cd, double& fL, double& fR) {
   T oL, oR;
   offsets(w, s, oL, oR);
-  fL = cd + double(oL);
-  fR = cd + double(oR);
+  fL = cd + wide(oL);
+  fR = cd + wide(oR);
 }
 
 // ------------------------------------------------------------------ limiters
@@ -496,7 +553,7 @@ struct Face {
 // land an ulp below it; it becomes 0.  With fbar < 0 (a stage that left the
 // bound, theta = 0) the value is fbar itself and stays.  A NaN stays a NaN.
 __device__ __forceinline__ double nonneg(double x, double fb) {
-  return x < 0.0 && fb >= 0.0 ? 0.0 : x;
+  return lt0_ieee(x) && ge0_ieee(fb) ? 0.0 : x;
 }
 
 // The same rule at the end of a Runge-Kutta stage x = t0 + t1 + t2: a mass
@@ -508,7 +565,7 @@ __device__ __forceinline__ double nonneg(double x, double fb) {
 constexpr double STAGE_TOL = 0x1p-48;
 __device__ __forceinline__ double stage_bound(double x, double t0, double t1, double t2,
                                               bool frac) {
-  const bool lo = x < 0.0, hi = frac && x > 1.0;
+  const bool lo = lt0_ieee(x), hi = frac && gt1_ieee(x);
   if (lo || hi) {
     const double tol = STAGE_TOL * (fabs(t0) + fabs(t1) + fabs(t2));
     if (lo && -x <= tol) return 0.0;
@@ -720,7 +777,7 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
 // 1 / (rho_p c_p^2) = 1 / (gamma_p (P + Pinf_p)) of the stiffened gas
 template <typename TF>
 __device__ __forceinline__ TF inv_rhoc2_phase(const Mat& m, int p, TF P) {
-  const TF x = TF(m.gam[p]) * (P + TF(m.pinf[p]));
+  const TF x = cvt<TF>(m.gam[p]) * (P + cvt<TF>(m.pinf[p]));
   if constexpr (sizeof(TF) == 8) {
     return in_range(x, 1e-300, 1e300) ? rcp_nr(x) : 1.0 / x;
   } else {
@@ -762,7 +819,7 @@ __device__ __forceinline__ TF sound_speed(const Mat& m, const double* U, TF rho,
     // gives Wood's 1 / (rho c^2) = sum_p alpha_p / (rho_p c_p^2)
     TF sw = TF(0);
 #pragma unroll
-    for (int p = 0; p < N; p++) sw = sw + TF(U[I::A(p)]) * inv_rhoc2_phase<TF>(m, p, P);
+    for (int p = 0; p < N; p++) sw = sw + cvt<TF>(U[I::A(p)]) * inv_rhoc2_phase<TF>(m, p, P);
     const TF xw = rho * sw;
     if (in_range(xw, TF(1e-30), TF(1e30))) return rsqrt_nr(xw);
     return TF(1) / sqrt(xw);
@@ -770,9 +827,9 @@ __device__ __forceinline__ TF sound_speed(const Mat& m, const double* U, TF rho,
   TF num = TF(0), den = TF(0);
 #pragma unroll
   for (int p = 0; p < N; p++) {
-    TF a = TF(U[I::A(p)]);
-    num = num + TF(m.Ag[p]) * a * (P + TF(m.pinf[p]));
-    den = den + TF(m.A[p]) * a;
+    TF a = cvt<TF>(U[I::A(p)]);
+    num = num + cvt<TF>(m.Ag[p]) * a * (P + cvt<TF>(m.pinf[p]));
+    den = den + cvt<TF>(m.A[p]) * a;
   }
   // c = sqrt(num / (den rho)) = num / sqrt(num den rho)
   TF x = num * den * rho;
@@ -882,8 +939,8 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
 #pragma unroll
   for (int j = 0; j < D; j++) ub[j] = 0.5 * (L.u[j] + R.u[j]);
   const double dPd = L.P - R.P;  // exact when P_L, P_R are close
-  const TF rL = TF(rLd), rR = TF(rRd), uL = TF(uLd), uR = TF(uRd);
-  const TF PL = TF(L.P), PR = TF(R.P);
+  const TF rL = cvt<TF>(rLd), rR = cvt<TF>(rRd), uL = cvt<TF>(uLd), uR = cvt<TF>(uRd);
+  const TF PL = cvt<TF>(L.P), PR = cvt<TF>(R.P);
   const TF cL = sound_speed<N, D, TF>(m, L.U, rL, PL);
   const TF cR = sound_speed<N, D, TF>(m, R.U, rR, PR);
   const TF sL = dmin(uL - cL, uR - cR);
@@ -892,19 +949,19 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
   TF AaL = TF(0), AaR = TF(0);
 #pragma unroll
   for (int p = 0; p < N; p++) {
-    AaL += TF(m.A[p]) * TF(L.U[I::A(p)]);
-    AaR += TF(m.A[p]) * TF(R.U[I::A(p)]);
+    AaL += cvt<TF>(m.A[p]) * cvt<TF>(L.U[I::A(p)]);
+    AaR += cvt<TF>(m.A[p]) * cvt<TF>(R.U[I::A(p)]);
   }
   TF wL[D], wR[D];
   TF kinL = TF(0), kinR = TF(0);
 #pragma unroll
   for (int j = 0; j < D; j++) {
-    wL[j] = TF(L.u[j] - ub[j]);
-    wR[j] = TF(R.u[j] - ub[j]);
-    kinL += wL[j] * TF(L.u[j] + ub[j]);
-    kinR += wR[j] * TF(R.u[j] + ub[j]);
+    wL[j] = cvt<TF>(L.u[j] - ub[j]);
+    wR[j] = cvt<TF>(R.u[j] - ub[j]);
+    kinL += wL[j] * cvt<TF>(L.u[j] + ub[j]);
+    kinR += wR[j] * cvt<TF>(R.u[j] + ub[j]);
   }
-  const TF halfdP = TF(0.5 * dPd);
+  const TF halfdP = cvt<TF>(0.5 * dPd);
   const TF EtL = halfdP * AaL + TF(0.5) * rL * kinL;
   const TF EtR = -halfdP * AaR + TF(0.5) * rR * kinR;
 
@@ -921,8 +978,8 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
       k = sL * rcp_nr(sR - sL);
     }
     const TF sRu = le0(sR) ? TF(0) : sR;
-    kd = double(k);
-    sRd = double(sRu);
+    kd = wide(k);
+    sRd = wide(sRu);
     uhat = uLd + kd * (uLd - uRd);
 #pragma unroll
     for (int p = 0; p < N; p++) {
@@ -942,14 +999,14 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
       TF qL = rL * wL[j], qR = rR * wR[j];
       TF fl = qL * uL, fr = qR * uR;
       TF fw = fl + k * ((fl - fr) + sRu * (qR - qL));
-      double f = ub[j] * Frho + double(fw);
+      double f = ub[j] * Frho + wide(fw);
       if (j == dir) f += L.P + kd * dPd;
       F[I::U(j)] = f;
     }
     // energy remainder
     TF gl = uL * (EtL + PL), gr = uR * (EtR + PR);
     TF g = gl + k * ((gl - gr) + sRu * (EtR - EtL));
-    double fe = double(g);
+    double fe = wide(g);
     double ub2 = 0.0;
 #pragma unroll
     for (int j = 0; j < D; j++) ub2 = fma(ub[j], ub[j], ub2);
@@ -978,23 +1035,23 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
     sSd = left ? uLd : uRd;
   } else {
     // contact speed relative to ub_n (exact for uniform u and P)
-    TF num = TF(-dPd) + rL * TF(uLd - ubn) * (sL - uL) - rR * TF(uRd - ubn) * (sR - uR);
+    TF num = cvt<TF>(-dPd) + rL * cvt<TF>(uLd - ubn) * (sL - uL) - rR * cvt<TF>(uRd - ubn) * (sR - uR);
     TF den = rL * (sL - uL) - rR * (sR - uR);
     TF rel = num / den;
-    sS = TF(ubn) + rel;
-    sSd = ubn + double(rel);
+    sS = cvt<TF>(ubn) + rel;
+    sSd = ubn + wide(rel);
     left = sS >= TF(0);
     sK = left ? sL : sR;
     TF uK = left ? uL : uR;
     // u_K - S* = (u_K - ub_n) - rel
-    TF uKmS = TF((left ? uLd : uRd) - ubn) - rel;
+    TF uKmS = cvt<TF>((left ? uLd : uRd) - ubn) - rel;
     chi = (sK - uK) / (sK - uK + uKmS);
   }
   const TF uK = left ? uL : uR, rK = left ? rL : rR, PK = left ? PL : PR;
   const TF EtK = left ? EtL : EtR;
   const double uKd = left ? uLd : uRd;
   // u_hat = u_K + s_K (chi - 1)
-  uhat = uKd + double(sK * (chi - TF(1)));
+  uhat = uKd + wide(sK * (chi - TF(1)));
 #pragma unroll
   for (int p = 0; p < N; p++) {
     double aK = left ? L.U[I::A(p)] : R.U[I::A(p)];
@@ -1009,7 +1066,7 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
     if (j == dir) {
       // S* F^rho + P_K + rho_K (u_K - s_K)(u_K - S*)
       double f = sSd * Frho + (left ? L.P : R.P);
-      f += double(rK * (uK - sK) * uKmS);
+      f += wide(rK * (uK - sK) * uKmS);
       F[I::U(j)] = f;
     } else {
       F[I::U(j)] = (left ? L.u[j] : R.u[j]) * Frho;
@@ -1019,7 +1076,7 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
   TF Es = chi * (EtK + (sS - uK) * (rK * sS + PK / (sK - uK)));
   if (sK == TF(0)) Es = EtK;
   TF g = uK * (EtK + PK) + sK * (Es - EtK);
-  double fe = double(g);
+  double fe = wide(g);
   double ub2 = 0.0;
 #pragma unroll
   for (int j = 0; j < D; j++) ub2 = fma(ub[j], ub[j], ub2);

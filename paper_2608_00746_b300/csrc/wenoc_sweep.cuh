@@ -130,7 +130,7 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
     sl[0] = v[I::E];
     T* Vs = reinterpret_cast<T*>(sl + 1);
 #pragma unroll
-    for (int k = 0; k < NV; k++) Vs[k] = T(v[k]);
+    for (int k = 0; k < NV; k++) Vs[k] = cvt<T>(v[k]);
   };
 
   for (int c = s - 3; c <= s; c++) load(c);
@@ -228,11 +228,11 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
       } else {
         T fl, fr;
         reconstruct(w, st, fl, fr);
-        mL[p] = double(fl);
-        mR[p] = double(fr);
+        mL[p] = wide(fl);
+        mR[p] = wide(fr);
         reconstruct(wa, sa, fl, fr);
-        aL[p] = double(fl);
-        aR[p] = double(fr);
+        aL[p] = wide(fl);
+        aR[p] = wide(fr);
       }
     }
     // velocity and pressure, each with its own weights
@@ -245,7 +245,7 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
       // field (FP64 noise below the FP32 resolution) gives uniform faces
       T tl, tr;
       reconstruct(w, st, tl, tr);
-      const double fl = double(tl), fr = double(tr);
+      const double fl = wide(tl), fr = wide(tr);
       if (v < N + D) {
         uL[v - N] = fl;
         uR[v - N] = fr;

@@ -64,7 +64,7 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
     sl[0] = v[I::E];
     T* Vs = reinterpret_cast<T*>(sl + 1);
 #pragma unroll
-    for (int k = 0; k < NV; k++) Vs[k] = T(v[k]);
+    for (int k = 0; k < NV; k++) Vs[k] = cvt<T>(v[k]);
   };
   // reduced precision: mass and fraction faces = FP64 cell value (a
   // conservative and primitive variable alike) + offset in T
@@ -151,11 +151,11 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
     } else {
       T fl, fr;
       reconstruct(w, st, fl, fr);
-      mL[p] = double(fl);
-      mR[p] = double(fr);
+      mL[p] = wide(fl);
+      mR[p] = wide(fr);
       reconstruct(wa, sa, fl, fr);
-      aL[p] = double(fl);
-      aR[p] = double(fr);
+      aL[p] = wide(fl);
+      aR[p] = wide(fr);
     }
   }
   // velocity and pressure, each with its own weights
@@ -168,7 +168,7 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
     // field (FP64 noise below the FP32 resolution) gives uniform faces
     T tl, tr;
     reconstruct(w, st, tl, tr);
-    const double fl = double(tl), fr = double(tr);
+    const double fl = wide(tl), fr = wide(tr);
     if (v < N + D) {
       uL[v - N] = fl;
       uR[v - N] = fr;

@@ -104,6 +104,7 @@ _SIGS = {
     "wc_last_error": (None, [_VP, ctypes.c_char_p, ctypes.c_size_t]),
     "wc_fp64_peak_kernel": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
                                            ctypes.POINTER(ctypes.c_double), _VP]),
+    "wc_convert_f32": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_long, _VP]),
     "wc_sweep_timing_begin": (ctypes.c_int, [_VP, ctypes.c_int]),
     "wc_sweep_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_double),
@@ -434,6 +435,19 @@ def fp64_peak(blocks=148 * 8, threads=256, iters=20000, reps=5):
         if r > 0:
             best = max(best, fl.value / (e0.elapsed_time(e1) * 1e-3))
     return best
+
+
+def convert_f32(x):
+    """The reduced-precision sweeps' binary64 -> binary32 -> binary64
+    conversions applied to the float64 CUDA tensor ``x``: (f32, back)."""
+    x = x.contiguous()
+    f = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    back = torch.empty_like(x)
+    st = lib().wc_convert_f32(_ptr(x), _dptr(f), _ptr(back), x.numel(),
+                              _stream(torch.cuda.current_stream()))
+    if st != 0:
+        raise WcError(st, "convert_f32")
+    return f, back
 
 
 class Patches:
