@@ -303,6 +303,12 @@ static SweepArgs make_args(const wc_grid* g, int dir, const double* U, double* L
     // one cell per lane, windows of WIN cells from a dynamic queue
     a.nwin = (a.n + WIN - 1) / WIN;
     a.ticket = g->ticket;
+    const WinPlan w = win_plan(a.n, a.npencil);
+    a.wfull = w.wfull;
+    a.wtail = w.wtail;
+    a.wgrp = w.wgrp;
+    a.wslots = w.slots;
+    a.nitems = w.nitems;
   }
   // window schedule: blocks_per_sm when given, else the occupancy limit
   a.max_threads = (g->d.seg > 0 || g->d.blocks_per_sm > 0) ? sweep_threads(g) : 0;

@@ -52,10 +52,14 @@ struct SweepArgs {
   float tau;
   unsigned long long* lcount;
   // window schedule (nwin > 0, wenoc_window.cuh): windows per pencil, the
-  // two-word queue (next window, warps finished) and the launched warps
+  // two-word queue (next window, warps finished) and the launched warps;
+  // the queue's plan (WinPlan: full windows per pencil, tail cells, tails
+  // per warp, queue items) and the slots a warp holds
   int nwin;
   unsigned* ticket;
   unsigned nwarps;
+  int wfull, wtail, wgrp, wslots;
+  unsigned nitems;
 };
 
 enum { BC_PERIODIC = 0, BC_REFLECTIVE = 1, BC_OUTFLOW = 2 };

@@ -16,12 +16,35 @@ namespace wc {
 
 constexpr int WIN = 30;        // cells updated per window
 constexpr int WIN_SLOTS = 36;  // cells c0-3 .. c0+32 held in shared memory
+constexpr int WIN_SLOTS_MAX = 72;  // slots of a warp whose groups hold pencil tails
 constexpr int WIN_BLOCK = 128;  // threads per block unless configured
+
+// The queue of a direction sweep: wfull full windows of WIN cells per pencil
+// (window-major, pencil fastest), then the tails, wtail = n - WIN wfull cells
+// of each pencil.  A tail of up to 14 cells takes a group of wtail + 2 lanes
+// (the two outer lanes reconstruct its neighbours), and one warp takes the
+// tails of wgrp = 32 / (wtail + 2) pencils at once; a longer tail takes a
+// whole warp (wgrp = 1).  Bundling the tails saves the passes that a 32-lane
+// window spends on a few cells: 18 -> 17.1 warp passes per 512-cell pencil.
+struct WinPlan {
+  int wfull, wtail, wgrp, slots;
+  unsigned nitems;
+};
+inline WinPlan win_plan(int n, long npencil) {
+  WinPlan w;
+  w.wfull = n / WIN;
+  w.wtail = n - WIN * w.wfull;
+  w.wgrp = w.wtail == 0 ? 0 : (w.wtail + 2 <= 16 ? 32 / (w.wtail + 2) : 1);
+  const long ntail = w.wtail == 0 ? 0 : (npencil + w.wgrp - 1) / w.wgrp;
+  w.nitems = (unsigned)(npencil * w.wfull + ntail);
+  w.slots = w.wgrp > 1 ? w.wgrp * (w.wtail + 6) : WIN_SLOTS;
+  if (w.slots < WIN_SLOTS) w.slots = WIN_SLOTS;
+  return w;
+}
 
 template <int N, int D, typename T>
 struct WinSmem {
   static constexpr int SLOTD = Ring<N, D, T>::SLOTD;     // doubles per cell slot
-  static constexpr int WARP_DOUBLES = WIN_SLOTS * SLOTD;  // per warp
 };
 
 template <int N, int D>
@@ -34,21 +57,29 @@ __device__ __forceinline__ void shfl_face_down(const Face<N, D>& f, Face<N, D>& 
   g.P = __shfl_down_sync(0xffffffffu, f.P, 1);
 }
 
-// One window: lane k owns cell c = c0 - 1 + k; slot s of `slots` holds the
-// primitive state of cell c0 - 3 + s (pressure in FP64, V in T).  Lanes
-// 1..30 update cells c0 .. c0 + 29 (those below a.n).  Variant LW as in
-// sweep_segment (0 scheme, 1 learned weights, 2 comparison schemes).
+// One window: the warp's lanes form groups of G consecutive lanes (one group
+// of 32 for a full window); lane j of a group owns cell c = c0 - 1 + j of the
+// pencil at `base`, and slot sb + s of `slots` holds the primitive state of
+// cell c0 - 3 + s (pressure in FP64, V in T), s = 0 .. G + 3.  Lanes
+// 1 .. G - 2 of an active group update cells c0 .. c0 + G - 3 (those below
+// a.n).  A lane with store = false (beyond the last group) keeps its slots
+// untouched and updates nothing.  Variant LW as in sweep_segment (0 scheme,
+// 1 learned weights, 2 comparison schemes).
 template <int N, int D, typename T, typename TF, int LW>
 __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, long base, int c0,
+                                             int j, int G, int sb, bool active, bool store,
                                              double* slots, double dt, unsigned& bad,
                                              unsigned* lstat) {
   using I = Idx<N, D>;
   constexpr int NV = I::NV;
   constexpr int SLOTD = WinSmem<N, D, T>::SLOTD;
-  const int lane = threadIdx.x & 31;
+  // cells beyond the three ghost layers (lanes past the end of a short
+  // pencil, whose results are not used) read the outermost ghost: the
+  // boundary maps stay inside the pencil
+  auto ghost_clamp = [&](int c) { return c < -3 ? -3 : (c > a.n + 2 ? a.n + 2 : c); };
   auto load_cons = [&](int c, double* u) {
     bool flip;
-    const int j = bc_index(c, a.n, a.bclo, a.bchi, flip);
+    const int j = bc_index(ghost_clamp(c), a.n, a.bclo, a.bchi, flip);
     const long cell = base + (long)j * a.stride;
 #pragma unroll
     for (int k = 0; k < NV; k++) u[k] = __ldg(a.U + (long)k * a.ncell + cell);
@@ -70,21 +101,25 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
   // conservative and primitive variable alike) + offset in T
   constexpr bool OFFSET = !std::is_same<T, double>::value;
 
-  const int c = c0 - 1 + lane;
+  const int c = c0 - 1 + j;
   double Ub[NV], Vtmp[NV];
   load_cons(c, Ub);
-  store_slot(lane + 2, Ub, Vtmp);
-  if (lane < 4) {
-    const int s = lane < 2 ? lane : 32 + lane;  // slots 0, 1, 34, 35
-    double u[NV], v[NV];
-    load_cons(c0 - 3 + s, u);
-    store_slot(s, u, v);
+  if (store) {
+    store_slot(sb + j + 2, Ub, Vtmp);
+    // the group's outer stencil cells: slots 0, 1, G + 2, G + 3
+    for (int e = j; e < 4; e += G) {
+      const int s = e < 2 ? e : G + e;
+      double u[NV], v[NV];
+      load_cons(c0 - 3 + s, u);
+      store_slot(sb + s, u, v);
+    }
   }
   __syncwarp();
   const T* V[5];
 #pragma unroll
-  for (int k = 0; k < 5; k++) V[k] = reinterpret_cast<const T*>(slots + (lane + k) * SLOTD + 1);
-  const double Pb = slots[(lane + 2) * SLOTD];
+  for (int k = 0; k < 5; k++)
+    V[k] = reinterpret_cast<const T*>(slots + (sb + j + k) * SLOTD + 1);
+  const double Pb = slots[(sb + j + 2) * SLOTD];
 
   // Eq. 16: masses and fractions with the weights of the masses
   double mL[N], mR[N], aL[N], aR[N];
@@ -187,7 +222,8 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
   if (a.kind == 1) {
     double q[N], G[N];
     bool flip;
-    const long cell = base + (long)bc_index(c, a.n, a.bclo, a.bchi, flip) * a.stride;
+    const long cell =
+        base + (long)bc_index(ghost_clamp(c), a.n, a.bclo, a.bchi, flip) * a.stride;
 #pragma unroll
     for (int p = 0; p < N; p++) q[p] = __ldg(a.Q + (long)p * a.ncell + cell);
 #pragma unroll
@@ -206,7 +242,7 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
 #pragma unroll
   for (int v = 0; v < NV; v++) Fl[v] = __shfl_up_sync(0xffffffffu, F[v], 1);
   const double uhl = __shfl_up_sync(0xffffffffu, uh, 1);
-  if (lane >= 1 && lane <= WIN && c < a.n) {
+  if (active && j >= 1 && j <= G - 2 && c < a.n) {
     const long cell = base + (long)c * a.stride;
     const double du = (uh - uhl) * a.inv_dx;
     // Eq. 3: -div F + alpha (1 + K) div u_hat;  Eq. 5: +div F^PF
@@ -249,8 +285,9 @@ template <int N, int D, typename T, typename TF, int LW = 0>
 __global__ void __launch_bounds__(128) k_sweep_win(SweepArgs a, Mat m) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31;
-  double* slots = smem + (threadIdx.x >> 5) * WinSmem<N, D, T>::WARP_DOUBLES;
-  const unsigned nitems = (unsigned)(a.npencil * a.nwin);
+  double* slots = smem + (threadIdx.x >> 5) * (a.wslots * WinSmem<N, D, T>::SLOTD);
+  const unsigned nitems = a.nitems;
+  const unsigned nfull = (unsigned)(a.npencil * a.wfull);
   unsigned bad = 0u;
   unsigned lstat[2] = {0u, 0u};
   double dt = 0.0;
@@ -262,13 +299,41 @@ __global__ void __launch_bounds__(128) k_sweep_win(SweepArgs a, Mat m) {
     if (lane == 0) it = atomicAdd(a.ticket, 1u);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= nitems) break;
-    const long tr = (long)(it % (unsigned)a.npencil);
-    const int win = (int)(it / (unsigned)a.npencil);
+    long tr;
+    int c0, G = 32, j = lane, sb = 0;
+    bool active = true, store = true;
+    if (it < nfull) {
+      tr = (long)(it % (unsigned)a.npencil);
+      c0 = (int)(it / (unsigned)a.npencil) * WIN;
+    } else {
+      const unsigned t = it - nfull;
+      c0 = a.wfull * WIN;
+      if (a.wgrp <= 1) {
+        tr = (long)t;
+      } else {
+        // tails of pencils t wgrp .. t wgrp + wgrp - 1, one per group
+        G = a.wtail + 2;
+        int gi = lane / G;
+        j = lane - gi * G;
+        if (gi >= a.wgrp) {  // lanes past the last group: read its slots only
+          gi = a.wgrp - 1;
+          j = G - 1;
+          active = store = false;
+        }
+        sb = gi * (G + 4);
+        tr = (long)t * a.wgrp + gi;
+        if (tr >= a.npencil) {  // past the last pencil: a copy of it, no update
+          tr = a.npencil - 1;
+          active = false;
+        }
+      }
+    }
     long base;
     if (a.dir == 0) base = tr * a.nx;
     else if (a.dir == 1) base = (tr / a.nx) * ((long)a.nx * a.ny) + tr % a.nx;
     else base = tr;
-    sweep_window<N, D, T, TF, LW>(a, m, base, win * WIN, slots, dt, bad, lstat);
+    sweep_window<N, D, T, TF, LW>(a, m, base, c0, j, G, sb, active, store, slots, dt, bad,
+                                  lstat);
   }
   if (lane == 0) {
     __threadfence();
@@ -302,11 +367,12 @@ template <int N, int D, typename T, typename TF, int LW>
 cudaError_t launch_window(const SweepArgs& a0, const Mat& m, int block, int bps,
                           cudaStream_t st) {
   if (block < 32 || block > 128 || block % 32 != 0) return cudaErrorInvalidValue;
-  const int smem = WinSmem<N, D, T>::WARP_DOUBLES * 8 * (block / 32);
+  if (a0.wslots < WIN_SLOTS || a0.wslots > WIN_SLOTS_MAX) return cudaErrorInvalidValue;
+  const int smem = a0.wslots * WinSmem<N, D, T>::SLOTD * 8 * (block / 32);
   auto k = k_sweep_win<N, D, T, TF, LW>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  const long items = a0.npencil * a0.nwin;
+  const long items = a0.nitems;
   if (bps <= 0) {
     // as many resident blocks as registers and shared memory allow (queried
     // once per instantiation and block size; every caller gets the same

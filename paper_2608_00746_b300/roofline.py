@@ -33,10 +33,14 @@ def flops_per_cell_dir(N: int, D: int, hllc: bool = False, rk_stage: bool = True
     eq21 = 4 * NV + 12 * N + (3 * N + 2 * D + 3)
     limiter = eq17 + eq19 + eq20 + v2u + eq21
     if not hllc:
-        # HLL with u-hat: densities, mean velocity, sound speeds (Eq. 2),
-        # wave speeds, remainder energies, fraction and mass fluxes,
-        # momentum and energy assembly
-        flux = 39 * N + 24 * D + 40
+        # HLL with u-hat from the physical fluxes of Eq. 1: densities
+        # 2(N-1); sound speeds of Eq. 2, 6N + 1 a side (P + Pinf, A gamma
+        # alpha, product and sum per phase; sum A alpha; rho sum A alpha,
+        # divide, square root); wave speeds 4; k = s_L/(s_R - s_L) 2; u-hat 3;
+        # per component F_L + k((F_L - F_R) + s_R (U_R - U_L)) 6 plus the two
+        # physical fluxes: 2 for masses, fractions and tangential momentum,
+        # 4 for the normal momentum and the energy
+        flux = 2 * (N - 1) + 2 * (6 * N + 1) + 4 + 2 + 3 + 2 * N * 8 + 10 + (D - 1) * 8 + 10
     else:
         flux = 2 * (N - 1) + 2 * D + 1 + 12 * N + 6 + 4 + 4 * N + 8 * D + 9 \
             + 20 + 3 + 3 * N + 3 * D + 6 + 4 * N + 2 * D + 5 + 12

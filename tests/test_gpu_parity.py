@@ -162,3 +162,26 @@ def test_rhs_parity_window_block_sizes(gpu, name, block):
     gg.sync_status()
     err = rhs_err(L, L_or, U, oracle.max_rate(go, U), case.N, case.dim)
     assert (err <= TOL).all(), (name, block, err)
+
+
+@pytest.mark.parametrize("shape", [(91, 8), (64, 31), (62, 40), (33, 17)])
+def test_rhs_parity_window_tails(gpu, shape):
+    """Pencils whose last cells are taken several pencils to a warp (tails of
+    1, 2, 3, 4, 8 and 10 cells, a partly filled last warp, lanes past the
+    last group) and short reflective pencils (8 and 17 cells) whose window
+    lanes run past the ghost layers: dU/dt and three Runge-Kutta steps."""
+    case = inputs.shock_bubble_2d(nx=shape[0], ny=shape[1], seed=5)
+    go, gg = grids(case)
+    U = oracle.prim_to_cons(go, case.V)
+    Ud = to_dev(U)
+    gg.bind(Ud)
+    L = gg.rhs(Ud).cpu().numpy()
+    gg.sync_status()
+    err = rhs_err(L, oracle.rhs(go, U), U, oracle.max_rate(go, U), case.N, case.dim)
+    assert (err <= TOL).all(), (shape, err)
+    for _ in range(3):
+        U, dt = oracle.rk3_step(go, U, cfl=0.2)
+        gg.rk_step(dt=dt)
+    gg.sync_status()
+    err = state_err(Ud.cpu().numpy(), U, case.N, case.dim)
+    assert (err <= TOL).all(), (shape, err)
