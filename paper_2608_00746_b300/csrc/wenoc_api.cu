@@ -48,16 +48,7 @@ struct wc_grid {
   PfGeom pg;
   int pf_iters = 0, pf_label_rounds = 0, pf_have_q = 0;
   double pf_resid = 0.0;
-  // one round of CG iterations as a graph (made at the first Q-map after a
-  // workspace is bound) and the stream it is captured on
-  cudaStream_t pf_cap = nullptr;
-  cudaGraphExec_t pf_cg_exec = nullptr;
 };
-
-static void drop_cg_graph(wc_grid* g) {
-  if (g->pf_cg_exec) cudaGraphExecDestroy(g->pf_cg_exec);
-  g->pf_cg_exec = nullptr;
-}
 
 static wc_status fail(wc_grid* g, wc_status s, const char* msg) {
   if (g) snprintf(g->err, sizeof(g->err), "%s", msg);
@@ -160,8 +151,6 @@ extern "C" wc_status wc_init_grid(const wc_grid_desc* desc, wc_grid** out) {
 extern "C" void wc_destroy(wc_grid* g) {
   if (!g) return;
   for (cudaEvent_t ev : g->tev) cudaEventDestroy(ev);
-  drop_cg_graph(g);
-  if (g->pf_cap) cudaStreamDestroy(g->pf_cap);
   delete g;
 }
 extern "C" int wc_nvar(const wc_grid* g) { return g ? g->nv : 0; }
@@ -527,9 +516,9 @@ extern "C" size_t wc_pf_workspace_bytes(const wc_grid* g) {
   if (!g) return 0;
   const size_t f = align256(sizeof(double) * (size_t)g->d.nphase * g->ncell);
   const size_t li = align256(sizeof(int) * (size_t)g->d.nphase * g->ncell);
-  // R c D 1/D sumR sumD x r p q, three face-weight fields, labels,
-  // partials, scalars, flags
-  return 13 * f + li + align256(sizeof(double) * pf_part_doubles()) + 512 + 256;
+  // R c D 1/D sumR sumD x r p q xk, three face-weight fields, labels, the
+  // unknowns' list and its inverse, partials, scalars, flags
+  return 14 * f + 3 * li + align256(sizeof(double) * pf_part_doubles()) + 512 + 256;
 }
 
 extern "C" wc_status wc_set_pf_workspace(wc_grid* g, void* ws_dev, size_t bytes) {
@@ -541,7 +530,7 @@ extern "C" wc_status wc_set_pf_workspace(wc_grid* g, void* ws_dev, size_t bytes)
   const size_t li = align256(sizeof(int) * (size_t)g->d.nphase * g->ncell);
   char* w = static_cast<char*>(ws_dev);
   double** fields[] = {&g->pw.R, &g->pw.c, &g->pw.D, &g->pw.Dinv, &g->pw.sumR, &g->pw.sumD,
-                       &g->pw.x, &g->pw.r, &g->pw.p, &g->pw.q};
+                       &g->pw.x, &g->pw.r, &g->pw.p, &g->pw.q, &g->pw.xk};
   for (double** d : fields) {
     *d = reinterpret_cast<double*>(w);
     w += f;
@@ -549,6 +538,10 @@ extern "C" wc_status wc_set_pf_workspace(wc_grid* g, void* ws_dev, size_t bytes)
   g->pw.w = reinterpret_cast<double*>(w);  // [3][N][ncell]
   w += 3 * f;
   g->pw.lab = reinterpret_cast<int*>(w);
+  w += li;
+  g->pw.idx = reinterpret_cast<int*>(w);
+  w += li;
+  g->pw.pos = reinterpret_cast<int*>(w);
   w += li;
   g->pw.part = reinterpret_cast<double*>(w);
   w += align256(sizeof(double) * pf_part_doubles());
@@ -571,7 +564,6 @@ extern "C" wc_status wc_set_pf_workspace(wc_grid* g, void* ws_dev, size_t bytes)
   pg.N = g->d.nphase;
   pg.nv = g->nv;
   pg.a0 = g->d.nphase + g->d.dim + 1;
-  drop_cg_graph(g);  // it holds the previous workspace's pointers
   g->pf_bound = true;
   g->pf_have_q = 0;
   return WC_OK;
@@ -624,48 +616,25 @@ static wc_status qmap(wc_grid* g, const double* U, const double* R, double* Q, d
     if (rounds > g->ncell + LR) return fail(g, WC_ERR_STATE, "qmap labels did not settle");
   }
   g->pf_label_rounds = rounds;
-  e = pf_qmap_project(g->pg, g->pw, warm, tol * tol, st);
-  if (e != cudaSuccess) return cuda_fail(g, e, "qmap project");
-  // CG in rounds of CR iterations, each round one graph launch (its 3 CR
-  // kernels without a host launch between them), the test read after each
-  const int CR = 24;
-  if (!g->pf_cg_exec) {
-    if (!g->pf_cap) e = cudaStreamCreateWithFlags(&g->pf_cap, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = pf_cg_graph(g->pg, g->pw, CR, g->pf_cap, &g->pf_cg_exec);
-    if (e != cudaSuccess) {
-      g->pf_cg_exec = nullptr;
-      return cuda_fail(g, e, "qmap cg graph");
-    }
-  }
+  e = pf_qmap_solve(g->pg, g->pw, warm, tol * tol, maxit, st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "qmap cg");
   const int N = g->d.nphase;
-  int it = 0;
-  int flags[8] = {0};
-  auto all_done = [&]() -> int {
-    cudaError_t ee =
-        cudaMemcpyAsync(flags, g->pw.flag, sizeof(int) * (1 + N), cudaMemcpyDeviceToHost, st);
-    if (ee == cudaSuccess) ee = cudaStreamSynchronize(st);
-    if (ee != cudaSuccess) return -1;
-    int all = 1;
-    for (int p = 0; p < N; p++) all &= flags[1 + p];
-    return all;
-  };
-  int done = all_done();  // the start may meet the test already
-  while (done == 0 && it < maxit) {
-    e = cudaGraphLaunch(g->pf_cg_exec, st);
-    if (e != cudaSuccess) return cuda_fail(g, e, "qmap cg");
-    it += CR;
-    done = all_done();
-  }
-  if (done < 0) return cuda_fail(g, cudaGetLastError(), "qmap cg flags");
-  if (Q != g->pw.x) e = cudaMemcpyAsync(Q, g->pw.x, fb, cudaMemcpyDeviceToDevice, st);
+  int flags[16] = {0};
   double sc[32];
+  e = cudaMemcpyAsync(flags, g->pw.flag, sizeof(flags), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(sc, g->pw.scal, sizeof(sc), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(g, e, "qmap residual");
+  if (flags[10]) return fail(g, WC_ERR_TIMEOUT, "qmap: a grid barrier wait gave up");
+  if (Q != g->pw.x) {
+    e = cudaMemcpyAsync(Q, g->pw.x, fb, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(g, e, "qmap result");
+  }
   double res = 0.0;  // sqrt(r.r/D / b.b/D): the D-weighted residual relative to b
   for (int p = 0; p < N; p++)
     if (sc[16 + p] > 0.0) res = fmax(res, sqrt(fmax(sc[24 + p], 0.0) / sc[16 + p]));
-  g->pf_iters = it;  // in whole rounds of CR iterations
+  const int it = flags[11];
+  g->pf_iters = it;
   g->pf_resid = res;
   return WC_OK;
 }

@@ -328,23 +328,23 @@ __global__ void __launch_bounds__(PF_THREADS) k_qm_sums(PfGeom g, const double* 
   }
 }
 
-// The conjugate-gradient kernels reduce over a fixed grid of PF_CG_BLOCKS
-// blocks (8 per SM: the elementwise passes need many loads in flight).
-// Partials: p . K p [PF_CG_BLOCKS][8]; r . r/D [2 parities][PF_CG_BLOCKS][8];
-// b . b/D [PF_CG_BLOCKS][8], after the Eq. 28 totals [PF_BLOCKS][32].  The
-// last block of a reducing kernel to finish (atomic ticket, no waiting)
-// sums the partials in a fixed order and writes the scalars the next kernel
-// reads: alpha after the matrix-vector pass, the convergence test and beta
-// after the update.
+// The conjugate gradients of Eq. 4 run on the listed unknowns (the cells of
+// some region, in cell order per phase) in one cooperative launch of
+// CG_BLOCKS <= PF_CG_BLOCKS blocks that meet at grid barriers.  Partials:
+// p . K p, r . r/D, b . b/D [PF_CG_BLOCKS][8] each, the list counts after
+// them, and before all of them the Eq. 28 totals [PF_BLOCKS][32].  Every
+// block sums the partials itself, in the same fixed order, so all blocks
+// hold the same scalars and take the same loop decisions.
 constexpr int PF_CG_BLOCKS = 148 * 8;
 constexpr long PART_CAC = 0;
 constexpr long PART_PQ = (long)PF_BLOCKS * 32;
 constexpr long PART_RZ = PART_PQ + (long)PF_CG_BLOCKS * 8;
-constexpr long PART_REF = PART_RZ + 2L * PF_CG_BLOCKS * 8;
-constexpr long PART_TOTAL = PART_REF + (long)PF_CG_BLOCKS * 8;
-// scalars: scal[16 + p] b.b/D, [24 + p] r.r/D of the current iteration,
-// [32 + p] beta, [40 + p] alpha; flags: [1 + p] converged, [6] and [7] the
-// tickets of the matrix-vector and update passes (zero between launches)
+constexpr long PART_REF = PART_RZ + (long)PF_CG_BLOCKS * 8;
+constexpr long PART_LIST = PART_REF + (long)PF_CG_BLOCKS * 8;
+constexpr long PART_TOTAL = PART_LIST + (long)PF_CG_BLOCKS * 8;
+// results: scal[16 + p] b.b/D, [24 + p] r.r/D; flags: [1 + p] converged,
+// [8] [9] [10] the grid barrier (arrivals, generation, error), [11] the
+// iterations done
 
 // On B300 a warp's FP64 instruction occupies the FP64 pipe for the same time
 // however few lanes are active, so the reductions here are written to issue
@@ -381,7 +381,7 @@ __device__ __forceinline__ void block_sum_small(const double (&v)[N], double* ou
 // Sums of count per-block partial rows (8 doubles, N used) by the whole
 // block, in a fixed order: thread t adds rows t, t + 256, ... (their loads
 // in flight together), then block_sum_small; out[p] (shared) for every
-// thread afterwards.
+// thread afterwards.  The rows are read from L2 (other blocks wrote them).
 template <int N>
 __device__ __forceinline__ void sum_partials_block(const double* part, long off, int count,
                                                    double* out) {
@@ -402,207 +402,276 @@ __device__ __forceinline__ void sum_partials_block(const double* part, long off,
   block_sum_small<N>(v, out);
 }
 
-// True in the block that finishes last (after its partials are written);
-// that block also resets the ticket for the next launch.
-__device__ __forceinline__ bool last_block(int* ticket) {
-  __shared__ int last;
+// Grid barrier of the cooperative launch (every block resident): an arrival
+// count and a generation word.  The last block to arrive resets the count
+// and advances the generation; the others poll the generation, at most
+// PF_SPIN_LIMIT times, and stop waiting when any block has set the error
+// word (a timed-out wait sets it).  Returns false after an error: the
+// caller leaves its iterations, and the host reports WC_ERR_TIMEOUT.
+constexpr unsigned PF_SPIN_LIMIT = 1u << 22;
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* err) {
+  __shared__ int ok;
+  __syncthreads();
   if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    volatile int* verr = err;
+    const unsigned g0 = *gen;
     __threadfence();
-    const int t = atomicAdd(ticket, 1);
-    last = t == (int)gridDim.x - 1;
-    if (last) *ticket = 0;
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned spins = 0;
+      while (*gen == g0) {
+        if (*verr) break;
+        if (++spins > PF_SPIN_LIMIT) {
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok = *verr == 0;
   }
   __syncthreads();
-  if (last) __threadfence();
-  return last;
+  return ok;
 }
 
-// K Q = b with K = -A (positive semi-definite): b = -(r - D s_k) on cells
-// with a label.  Start x0 = 0, or (warm) the x given; r0 = b - K x0.
-// Partials of r0 . r0/D (parity 0) and of the reference b . b/D of the
-// stopping test.
+// The unknowns of one phase taken by block b of G: [k0, k1) of m.
+__device__ __forceinline__ void own_range(int m, int b, int G, int& k0, int& k1) {
+  const int cp = (m + G - 1) / G;
+  k0 = min(m, b * cp);
+  k1 = min(m, k0 + cp);
+}
+
+// Eq. 4 by conjugate gradients preconditioned with D, in one launch:
+//  1. list: each block counts the cells of its chunk of the grid that carry
+//     a label; after a barrier it knows its offset, and it writes the list
+//     (idx: cell of each unknown, in cell order) and its inverse (pos, -1
+//     for cells off the list);
+//  2. start: b = -(R - D s_k) (s_k the region's sum R / sum D), x0 = 0 or
+//     (warm) the x given, r0 = b - K x0, and the sums r0 . r0/D, b . b/D;
+//  3. iterations until every phase has r.r/D <= tol2 b.b/D or maxit: the
+//     direction p = r/D + beta p, q = K p with p . q, alpha, x and r, the
+//     new r.r/D and beta, a barrier after each step that the next one needs
+//     (the matrix-vector product reads neighbours' p);
+//  4. x written back to the grid (cold start: 0 off the list).
+// A phase whose alpha is not positive stops where it is.
 template <int N>
-__global__ void __launch_bounds__(PF_THREADS) k_cg_init(PfGeom g, const double* __restrict__ R,
-                                                        const double* __restrict__ w,
-                                                        const double* __restrict__ D,
-                                                        const double* __restrict__ Dinv,
-                                                        const int* __restrict__ lab,
-                                                        const double* __restrict__ sumR,
-                                                        const double* __restrict__ sumD,
-                                                        double* x, double* r, double* part,
-                                                        int warm) {
+__global__ void __launch_bounds__(PF_THREADS) k_qmap_cg(PfGeom g, PfWork w, double tol2, int warm,
+                                                        int maxit) {
   const int n = (int)g.ncell;
   const long nn = (long)N * n;
+  const int G = (int)gridDim.x, b = (int)blockIdx.x, t = (int)threadIdx.x;
+  unsigned* bar = reinterpret_cast<unsigned*>(w.flag + 8);
+  int* err = w.flag + 10;
+  __shared__ int wtot[PF_THREADS / 32], soff[N], scnt[N];
+  __shared__ double s_rz[N], s_ref[N], s_new[N];
+
+  // 1. list
+  const int cc = (n + G - 1) / G, c0 = min(n, b * cc), c1 = min(n, c0 + cc);
+  for (int p = 0; p < N; p++) {
+    int cnt = 0;
+    for (int i = c0 + t; i < c1; i += PF_THREADS) cnt += w.lab[(long)p * n + i] >= 0 ? 1 : 0;
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if ((t & 31) == 0) wtot[t >> 5] = cnt;
+    __syncthreads();
+    if (t == 0) {
+      int sum = 0;
+      for (int k = 0; k < PF_THREADS / 32; k++) sum += wtot[k];
+      w.part[PART_LIST + (long)b * 8 + p] = (double)sum;
+    }
+    __syncthreads();
+  }
+  if (!grid_sync(bar, err)) return;
+  if (t < 32) {
+    for (int p = 0; p < N; p++) {
+      int o = 0, m = 0;
+      for (int bb = t; bb < G; bb += 32) {
+        const int c = (int)__ldcg(w.part + PART_LIST + (long)bb * 8 + p);
+        m += c;
+        if (bb < b) o += c;
+      }
+      o = __reduce_add_sync(0xffffffffu, o);
+      m = __reduce_add_sync(0xffffffffu, m);
+      if (t == 0) {
+        soff[p] = o;
+        scnt[p] = m;
+      }
+    }
+  }
+  __syncthreads();
+  for (int p = 0; p < N; p++) {
+    const long o = (long)p * n;
+    int base = soff[p];
+    for (int i0 = c0; i0 < c1; i0 += PF_THREADS) {
+      const int i = i0 + t;
+      const bool act = i < c1 && w.lab[o + i] >= 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, act);
+      if ((t & 31) == 0) wtot[t >> 5] = __popc(bal);
+      __syncthreads();
+      int before = 0, tot = 0;
+      for (int k = 0; k < PF_THREADS / 32; k++) {
+        const int v = wtot[k];
+        tot += v;
+        if (k < (t >> 5)) before += v;
+      }
+      const int k = base + before + __popc(bal & ((1u << (t & 31)) - 1u));
+      if (i < c1) w.pos[o + i] = act ? k : -1;
+      if (act) w.idx[o + k] = i;
+      base += tot;
+      __syncthreads();
+    }
+  }
+  if (!grid_sync(bar, err)) return;
+
+  // 2. start
   double acc[N], ref[N];
 #pragma unroll
-  for (int p = 0; p < N; p++) acc[p] = ref[p] = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int nb[3][2];
-    pf_stencil(g, i, nb);
-#pragma unroll
-    for (int p = 0; p < N; p++) {
-      const long o = (long)p * n, k = o + i;
-      const int l = lab[k];
-      double b = 0.0, rr = 0.0;
-      if (l >= 0) {
-        const double s = sumR[o + l] / sumD[o + l];
-        b = -(R[k] - D[k] * s);
-        rr = warm ? b - k_apply<N>(g, nb, i, o, nn, w, D, x) : b;
-        ref[p] += b * (b * Dinv[k]);
-      }
-      r[k] = rr;
-      acc[p] += rr * (rr * Dinv[k]);
-    }
-  }
-  if (!warm) {
-    // x0 = 0 (no block reads x when cold)
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-#pragma unroll
-      for (int p = 0; p < N; p++) x[(long)p * n + i] = 0.0;
-  }
-  block_sum_small<N>(acc, part + PART_RZ + (long)blockIdx.x * 8);  // parity 0
-  block_sum_small<N>(ref, part + PART_REF + (long)blockIdx.x * 8);
-}
-
-// The reference b . b/D and r0 . r0/D per phase and tol^2 into scal (one
-// warp); beta = 0 for the first directions; a phase whose start already
-// meets the test is converged.
-template <int N>
-__global__ void __launch_bounds__(PF_THREADS) k_cg_start(const double* part, double* scal,
-                                                         int* flag, double tol2) {
-  __shared__ double rz[N], ref[N];
-  sum_partials_block<N>(part, PART_RZ, PF_CG_BLOCKS, rz);
-  sum_partials_block<N>(part, PART_REF, PF_CG_BLOCKS, ref);
-  if (threadIdx.x != 0) return;
-  scal[8] = tol2;
-#pragma unroll
   for (int p = 0; p < N; p++) {
-    scal[16 + p] = ref[p];
-    scal[24 + p] = rz[p];
-    scal[32 + p] = 0.0;
-    flag[1 + p] = !(rz[p] > tol2 * ref[p]);
-  }
-}
-
-__device__ __forceinline__ bool all_converged(const int* flag, int N) {
-  int all = 1;
-  for (int p = 0; p < N; p++) all &= flag[1 + p];
-  return all;
-}
-
-// Step 1 (elementwise, any grid): p = r/D + beta p for the live phases
-// (beta = 0 at the first iteration).
-template <int N>
-__global__ void __launch_bounds__(PF_THREADS) k_cg_dir(PfGeom g, const double* __restrict__ r,
-                                                       const double* __restrict__ Dinv,
-                                                       double* __restrict__ pv,
-                                                       const double* __restrict__ scal,
-                                                       const int* __restrict__ flag) {
-  if (all_converged(flag, N)) return;
-  const long n = g.ncell;
-  for (int p = 0; p < N; p++) {
-    if (flag[1 + p]) continue;
-    const double beta = scal[32 + p];
+    acc[p] = ref[p] = 0.0;
     const long o = (long)p * n;
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long)gridDim.x * blockDim.x)
-      pv[o + i] = fma(beta, pv[o + i], r[o + i] * Dinv[o + i]);
-  }
-}
-
-// Step 2: q = K p for the live phases and the partials of p . q; the last
-// block forms alpha = r.r/D / p.q per live phase.
-template <int N>
-__global__ void __launch_bounds__(PF_THREADS) k_cg_matvec(PfGeom g, const double* __restrict__ w,
-                                                          const double* __restrict__ D,
-                                                          const double* __restrict__ pv,
-                                                          double* __restrict__ q, double* part,
-                                                          double* scal, int* flag) {
-  if (all_converged(flag, N)) return;
-  bool live[N];
-#pragma unroll
-  for (int p = 0; p < N; p++) live[p] = !flag[1 + p];
-  const int n = (int)g.ncell;
-  const long nn = (long)N * n;
-  double acc[N];
-#pragma unroll
-  for (int p = 0; p < N; p++) acc[p] = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int nb[3][2];
-    pf_stencil(g, i, nb);
-#pragma unroll
-    for (int p = 0; p < N; p++) {
-      if (!live[p]) continue;
-      const long o = (long)p * n;
-      const double s = k_apply<N>(g, nb, i, o, nn, w, D, pv);
-      q[o + i] = s;
-      acc[p] = fma(pv[o + i], s, acc[p]);
+    int k0, k1;
+    own_range(scnt[p], b, G, k0, k1);
+    for (int k = k0 + t; k < k1; k += PF_THREADS) {
+      const int i = __ldcg(w.idx + o + k);
+      const int l = w.lab[o + i];
+      const double s = w.sumR[o + l] / w.sumD[o + l];
+      const double bv = -(w.R[o + i] - w.D[o + i] * s);
+      double x0 = 0.0, rr = bv;
+      if (warm) {
+        int nb[3][2];
+        pf_stencil(g, i, nb);
+        x0 = w.x[o + i];
+        rr = bv - k_apply<N>(g, nb, i, o, nn, w.w, w.D, w.x);
+      }
+      w.xk[o + k] = x0;
+      w.r[o + k] = rr;
+      const double di = w.Dinv[o + i];
+      acc[p] += rr * (rr * di);
+      ref[p] += bv * (bv * di);
     }
   }
-  block_sum_small<N>(acc, part + PART_PQ + (long)blockIdx.x * 8);
-  if (!last_block(flag + 6)) return;
-  __shared__ double pq[N];
-  sum_partials_block<N>(part, PART_PQ, (int)gridDim.x, pq);
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int p = 0; p < N; p++)
-      scal[40 + p] = (live[p] && pq[p] > 0.0) ? scal[24 + p] / pq[p] : 0.0;
-}
-
-// Step 3 (iteration it): x += alpha p, r -= alpha q for the live phases;
-// partials of r . r/D into parity (it + 1) & 1 for every phase.  The last
-// block sums them and sets, for the next iteration, r.r/D, the test
-// (converged: r.r/D <= tol^2 b.b/D) and beta = new r.r/D / old.
-template <int N>
-__global__ void __launch_bounds__(PF_THREADS, 8) k_cg_update(PfGeom g,
-                                                          const double* __restrict__ Dinv,
-                                                          double* __restrict__ x,
-                                                          double* __restrict__ r,
-                                                          const double* __restrict__ pv,
-                                                          const double* __restrict__ q,
-                                                          double* part, double* scal, int* flag,
-                                                          int it) {
-  if (all_converged(flag, N)) return;
-  bool live[N];
-  double alpha[N];
+  block_sum_small<N>(acc, w.part + PART_RZ + (long)b * 8);
+  block_sum_small<N>(ref, w.part + PART_REF + (long)b * 8);
+  if (!grid_sync(bar, err)) return;
+  sum_partials_block<N>(w.part, PART_RZ, G, s_rz);
+  sum_partials_block<N>(w.part, PART_REF, G, s_ref);
+  bool conv[N];
+  double rz[N], refv[N], beta[N], alpha[N];
 #pragma unroll
   for (int p = 0; p < N; p++) {
-    live[p] = !flag[1 + p];
-    alpha[p] = scal[40 + p];
+    rz[p] = s_rz[p];
+    refv[p] = s_ref[p];
+    conv[p] = !(rz[p] > tol2 * refv[p]);
+    beta[p] = 0.0;
   }
-  const int n = (int)g.ncell;
-  double acc[N];
+
+  // 3. iterations
+  int it = 0;
+  bool ok = true;
+  while (it < maxit) {
+    bool all = true;
 #pragma unroll
-  for (int p = 0; p < N; p++) acc[p] = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int p = 0; p < N; p++) all = all && conv[p];
+    if (all) break;
 #pragma unroll
     for (int p = 0; p < N; p++) {
-      const long k = (long)p * n + i;
-      double rk = r[k];
-      if (live[p]) {
-        x[k] = fma(alpha[p], pv[k], x[k]);
-        rk = fma(-alpha[p], q[k], rk);
-        r[k] = rk;
+      if (conv[p]) continue;
+      const long o = (long)p * n;
+      int k0, k1;
+      own_range(scnt[p], b, G, k0, k1);
+      for (int k = k0 + t; k < k1; k += PF_THREADS) {
+        const int i = __ldcg(w.idx + o + k);
+        const double z = w.r[o + k] * w.Dinv[o + i];
+        w.p[o + k] = it == 0 ? z : fma(beta[p], w.p[o + k], z);
       }
-      acc[p] = fma(rk, rk * Dinv[k], acc[p]);
     }
-  }
-  const long onew = PART_RZ + (long)((it + 1) & 1) * PF_CG_BLOCKS * 8;
-  block_sum_small<N>(acc, part + onew + (long)blockIdx.x * 8);
-  if (!last_block(flag + 7)) return;
-  __shared__ double rn[N];
-  sum_partials_block<N>(part, onew, (int)gridDim.x, rn);
-  if (threadIdx.x == 0) {
-    const double tol2 = scal[8];
+    if (!(ok = grid_sync(bar, err))) break;
 #pragma unroll
     for (int p = 0; p < N; p++) {
-      const double ro = scal[24 + p];
-      const bool conv = !(rn[p] > tol2 * scal[16 + p]);
-      scal[32 + p] = ro > 0.0 ? rn[p] / ro : 0.0;
-      scal[24 + p] = rn[p];
-      // a phase that no longer moves (alpha = 0) stays where it is
-      flag[1 + p] = flag[1 + p] || conv || !(scal[40 + p] > 0.0);
+      acc[p] = 0.0;
+      if (conv[p]) continue;
+      const long o = (long)p * n;
+      int k0, k1;
+      own_range(scnt[p], b, G, k0, k1);
+      for (int k = k0 + t; k < k1; k += PF_THREADS) {
+        const int i = __ldcg(w.idx + o + k);
+        int nb[3][2];
+        pf_stencil(g, i, nb);
+        const double pk = w.p[o + k];
+        double s = w.D[o + i] * pk;
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+          if (ax >= g.dim) break;
+          const double* wa = w.w + ax * nn + o;
+          const int jm = nb[ax][0], jp = nb[ax][1];
+          // a neighbour off the list shares no coupled face (weight 0)
+          const int kp = jp >= 0 ? __ldcg(w.pos + o + jp) : -1;
+          const int km = jm >= 0 ? __ldcg(w.pos + o + jm) : -1;
+          if (kp >= 0) s = fma(-wa[i], __ldcg(w.p + o + kp), s);
+          if (km >= 0) s = fma(-wa[jm], __ldcg(w.p + o + km), s);
+        }
+        w.q[o + k] = s;
+        acc[p] = fma(pk, s, acc[p]);
+      }
     }
+    block_sum_small<N>(acc, w.part + PART_PQ + (long)b * 8);
+    if (!(ok = grid_sync(bar, err))) break;
+    sum_partials_block<N>(w.part, PART_PQ, G, s_new);
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      alpha[p] = (!conv[p] && s_new[p] > 0.0) ? rz[p] / s_new[p] : 0.0;
+      acc[p] = 0.0;
+      if (conv[p]) continue;
+      const long o = (long)p * n;
+      int k0, k1;
+      own_range(scnt[p], b, G, k0, k1);
+      for (int k = k0 + t; k < k1; k += PF_THREADS) {
+        const int i = __ldcg(w.idx + o + k);
+        w.xk[o + k] = fma(alpha[p], w.p[o + k], w.xk[o + k]);
+        const double rk = fma(-alpha[p], w.q[o + k], w.r[o + k]);
+        w.r[o + k] = rk;
+        acc[p] = fma(rk, rk * w.Dinv[o + i], acc[p]);
+      }
+    }
+    block_sum_small<N>(acc, w.part + PART_RZ + (long)b * 8);
+    if (!(ok = grid_sync(bar, err))) break;
+    sum_partials_block<N>(w.part, PART_RZ, G, s_new);
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      if (conv[p]) continue;
+      const double rn = s_new[p];
+      beta[p] = rz[p] > 0.0 ? rn / rz[p] : 0.0;
+      rz[p] = rn;
+      conv[p] = !(rn > tol2 * refv[p]) || !(alpha[p] > 0.0);
+    }
+    it++;
+  }
+
+  // 4. x back to the grid
+  if (ok) {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      const long o = (long)p * n;
+      int k0, k1;
+      own_range(scnt[p], b, G, k0, k1);
+      for (int k = k0 + t; k < k1; k += PF_THREADS) w.x[o + __ldcg(w.idx + o + k)] = w.xk[o + k];
+      if (!warm)
+        for (int i = c0 + t; i < c1; i += PF_THREADS)
+          if (w.pos[o + i] < 0) w.x[o + i] = 0.0;
+    }
+  }
+  if (b == 0 && t == 0) {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      w.scal[16 + p] = refv[p];
+      w.scal[24 + p] = rz[p];
+      w.flag[1 + p] = conv[p] ? 1 : 0;
+    }
+    w.flag[11] = it;
   }
 }
 
@@ -648,81 +717,30 @@ cudaError_t pf_label_rounds(const PfGeom& g, const PfWork& w, int rounds, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t pf_qmap_project(const PfGeom& g, const PfWork& w, int warm, double tol2,
-                            cudaStream_t st) {
+cudaError_t pf_qmap_solve(const PfGeom& g, const PfWork& w, int warm, double tol2, int maxit,
+                          cudaStream_t st) {
   const size_t bytes = sizeof(double) * (size_t)g.N * g.ncell;
   cudaError_t e = cudaMemsetAsync(w.sumR, 0, bytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.sumD, 0, bytes, st);
+  // the grid barrier's arrival count, generation and error word
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.flag + 8, 0, 3 * sizeof(int), st);
   if (e != cudaSuccess) return e;
   const int nb = pf_grid(g.ncell);
   PF_DISPATCH(g.N, (k_qm_sums<N_><<<nb, PF_THREADS, 0, st>>>(g, w.R, w.D, w.lab, w.sumR, w.sumD)));
-  PF_DISPATCH(g.N, (k_cg_init<N_><<<PF_CG_BLOCKS, PF_THREADS, 0, st>>>(
-                        g, w.R, w.w, w.D, w.Dinv, w.lab, w.sumR, w.sumD, w.x, w.r, w.part, warm)));
-  PF_DISPATCH(g.N, (k_cg_start<N_><<<1, PF_THREADS, 0, st>>>(w.part, w.scal, w.flag, tol2)));
-  return cudaGetLastError();
-}
-
-// Blocks of the matrix-vector pass: one wave of as many blocks as fit on
-// the SMs (queried once per phase count), fewer on a small grid.
-cudaError_t pf_cg_matvec_blocks(const PfGeom& g, int* blocks) {
-  static int mv_per_sm[8] = {0};
-  int& mps = mv_per_sm[g.N];
-  if (mps == 0) {
-    int k = 0;
-    cudaError_t e = cudaSuccess;
-    PF_DISPATCH(g.N, (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_cg_matvec<N_>,
-                                                                       PF_THREADS, 0)));
+  // one block per SM, all resident (a cooperative launch fails otherwise)
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    mps = k < 1 ? 1 : (k > 8 ? 8 : k);
   }
-  const long eb = (g.ncell + PF_THREADS - 1) / PF_THREADS;
-  *blocks = (int)(eb < 148L * mps ? (eb < 1 ? 1 : eb) : 148L * mps);
-  return *blocks > PF_CG_BLOCKS ? cudaErrorInvalidValue : cudaSuccess;  // partial rows
-}
-
-cudaError_t pf_cg_rounds(const PfGeom& g, const PfWork& w, int it0, int rounds, cudaStream_t st) {
-  const long eb = (g.ncell + PF_THREADS - 1) / PF_THREADS;
-  const int dir_blocks = (int)(eb < 148 * 16 ? (eb < 1 ? 1 : eb) : 148 * 16);
-  // the update pass: PF_CG_BLOCKS blocks, fewer on a small grid (its last
-  // block sums one partial per block launched)
-  const int up_blocks = (int)(eb < PF_CG_BLOCKS ? (eb < 1 ? 1 : eb) : PF_CG_BLOCKS);
-  int mv_blocks = 0;
-  cudaError_t e = pf_cg_matvec_blocks(g, &mv_blocks);
-  if (e != cudaSuccess) return e;
-  for (int k = 0; k < rounds; k++) {
-    const int it = it0 + k;
-    PF_DISPATCH(g.N, (k_cg_dir<N_><<<dir_blocks, PF_THREADS, 0, st>>>(g, w.r, w.Dinv, w.p,
-                                                                       w.scal, w.flag)));
-    PF_DISPATCH(g.N, (k_cg_matvec<N_><<<mv_blocks, PF_THREADS, 0, st>>>(
-                          g, w.w, w.D, w.p, w.q, w.part, w.scal, w.flag)));
-    PF_DISPATCH(g.N, (k_cg_update<N_><<<up_blocks, PF_THREADS, 0, st>>>(
-                          g, w.Dinv, w.x, w.r, w.p, w.q, w.part, w.scal, w.flag, it)));
-  }
-  return cudaGetLastError();
-}
-
-// The launches of pf_cg_rounds(g, w, 0, rounds) recorded on `cap` (a stream
-// of the caller's, not the legacy default stream) as one executable graph:
-// replayed on any stream, it runs `rounds` iterations from any even
-// iteration count (the kernels read the iteration only for the parity of
-// the reduction buffer).  It holds the pointers of w and the geometry g.
-cudaError_t pf_cg_graph(const PfGeom& g, const PfWork& w, int rounds, cudaStream_t cap,
-                        cudaGraphExec_t* exec) {
-  if (rounds % 2 != 0) return cudaErrorInvalidValue;
-  int mv_blocks = 0;
-  cudaError_t e = pf_cg_matvec_blocks(g, &mv_blocks);  // the query stays out of the capture
-  if (e != cudaSuccess) return e;
-  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return e;
-  const cudaError_t el = pf_cg_rounds(g, w, 0, rounds, cap);
-  cudaGraph_t graph = nullptr;
-  e = cudaStreamEndCapture(cap, &graph);
-  if (el != cudaSuccess || e != cudaSuccess) {
-    if (graph) cudaGraphDestroy(graph);
-    return el != cudaSuccess ? el : e;
-  }
-  e = cudaGraphInstantiate(exec, graph, 0);
-  cudaGraphDestroy(graph);
+  int blocks = sms < 1 ? 1 : (sms > PF_CG_BLOCKS ? PF_CG_BLOCKS : sms);
+  PfGeom gg = g;
+  PfWork ww = w;
+  void* args[] = {&gg, &ww, &tol2, &warm, &maxit};
+  PF_DISPATCH(g.N, (e = cudaLaunchCooperativeKernel((const void*)k_qmap_cg<N_>, dim3(blocks),
+                                                    dim3(PF_THREADS), args, 0, st)));
   return e;
 }
 

@@ -65,14 +65,17 @@ struct PfWork {
   int* lab;         // region label (smallest cell index of the region), -1: none
   double* sumR;     // per region (indexed by label): sum r
   double* sumD;     //                                 sum D
-  double* x;        // conjugate-gradient iterate (Q)
-  double* r;        //                    residual
-  double* p;        //                    direction
-  double* q;        //                    K p
+  double* x;        // Q on the grid (the conjugate gradients' start and result)
+  double* r;        // conjugate gradients on the listed unknowns: residual,
+  double* p;        //   direction,
+  double* q;        //   K p,
+  double* xk;       //   iterate (position k of phase p at p ncell + k)
+  int* idx;         // the list: cell of unknown k of phase p
+  int* pos;         // its inverse: position of cell i, -1 off the list
   double* part;     // reduction partials (offsets in wenoc_pf.cu)
-  double* scal;     // [64]: M, B[0..N-1] | tol^2 at 8 | b.b/D at 16+p | r.r/D at 24+p
-                    //       | beta at 32+p | alpha at 40+p
-  int* flag;        // [64]: label change, converged per phase at 1+p, CG tickets at 6, 7
+  double* scal;     // [64]: M, B[0..N-1] | b.b/D at 16+p | r.r/D at 24+p
+  int* flag;        // [64]: label change, converged per phase at 1+p, grid barrier at
+                    //       8..10 (arrivals, generation, error), iterations at 11
 };
 
 // Launchers (wenoc_pf.cu), all asynchronous on st.
@@ -84,18 +87,14 @@ cudaError_t pf_cac(const double* U, const PfGeom& g, const PfWork& w, double vol
 cudaError_t pf_qmap_setup(const double* U, const PfGeom& g, const PfWork& w, cudaStream_t st);
 // rounds of label propagation; w.flag[0] != 0 afterwards if any label moved.
 cudaError_t pf_label_rounds(const PfGeom& g, const PfWork& w, int rounds, cudaStream_t st);
-// region sums, the consistent right-hand side b from R, and the CG start in
-// w.x (0, or when warm the values already in w.x); w.flag[1 + p] set for
-// the phases whose start meets the test r.r/D <= tol2 b.b/D.
-cudaError_t pf_qmap_project(const PfGeom& g, const PfWork& w, int warm, double tol2,
-                            cudaStream_t st);
-// CG iterations it0 .. it0 + rounds - 1 (iteration 0 starts the directions);
-// w.flag[1 + p] set once phase p meets the test; w.scal[24 + p] holds its
+// Region sums, the consistent right-hand side b from R, and conjugate
+// gradients on the listed unknowns to r.r/D <= tol2 b.b/D per phase or
+// maxit iterations, from 0 or (warm) the values in w.x; the result in w.x.
+// One cooperative launch (one block per SM, grid barriers with bounded
+// waits: w.flag[10] != 0 afterwards if a wait gave up); w.flag[1 + p] set
+// for the converged phases, w.flag[11] the iterations, w.scal[24 + p] the
 // last r.r/D and w.scal[16 + p] the reference b.b/D.
-cudaError_t pf_cg_rounds(const PfGeom& g, const PfWork& w, int it0, int rounds, cudaStream_t st);
-// The same launches for iterations 0 .. rounds-1 (rounds even) as an
-// executable graph captured on `cap`.
-cudaError_t pf_cg_graph(const PfGeom& g, const PfWork& w, int rounds, cudaStream_t cap,
-                        cudaGraphExec_t* exec);
+cudaError_t pf_qmap_solve(const PfGeom& g, const PfWork& w, int warm, double tol2, int maxit,
+                          cudaStream_t st);
 
 }  // namespace wc
