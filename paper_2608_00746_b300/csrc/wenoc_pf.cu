@@ -341,7 +341,8 @@ constexpr long PART_PQ = (long)PF_BLOCKS * 32;
 constexpr long PART_RZ = PART_PQ + (long)PF_CG_BLOCKS * 8;
 constexpr long PART_REF = PART_RZ + (long)PF_CG_BLOCKS * 8;
 constexpr long PART_LIST = PART_REF + (long)PF_CG_BLOCKS * 8;
-constexpr long PART_TOTAL = PART_LIST + (long)PF_CG_BLOCKS * 8;
+constexpr long PART_CG1 = PART_LIST + (long)PF_CG_BLOCKS * 8;  // [PF_CG_BLOCKS][16]
+constexpr long PART_TOTAL = PART_CG1 + (long)PF_CG_BLOCKS * 16;
 // results: scal[16 + p] b.b/D, [24 + p] r.r/D; flags: [1 + p] converged,
 // [8] [9] [10] the grid barrier (arrivals, generation, error), [11] the
 // iterations done
@@ -350,29 +351,30 @@ constexpr long PART_TOTAL = PART_LIST + (long)PF_CG_BLOCKS * 8;
 // however few lanes are active, so the reductions here are written to issue
 // few FP64 warp instructions.
 //
-// Block sum of N values per thread into out[0..N-1] (fixed order): a shared
-// tree over the 256 threads down to one warp, then its shuffle tree.
+// Block sum of N values per thread into out[0..N-1] (fixed order): a
+// shuffle tree in each warp, then the eight warp sums by a shuffle tree in
+// warp 0.  out is written by thread 0 and read by the block after the
+// closing barrier.
 template <int N>
 __device__ __forceinline__ void block_sum_small(const double (&v)[N], double* out) {
-  __shared__ double sm[N][PF_THREADS];
-  const int t = threadIdx.x;
+  constexpr int W = PF_THREADS / 32;
+  __shared__ double sm[N][W];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
 #pragma unroll
-  for (int p = 0; p < N; p++) sm[p][t] = v[p];
-  __syncthreads();
+  for (int p = 0; p < N; p++) {
+    double x = v[p];
 #pragma unroll
-  for (int s = PF_THREADS / 2; s >= 32; s >>= 1) {
-    if (t < s)
-#pragma unroll
-      for (int p = 0; p < N; p++) sm[p][t] += sm[p][t + s];
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sm[p][wid] = x;
   }
-  if (t < 32) {
+  __syncthreads();
+  if (wid == 0) {
 #pragma unroll
     for (int p = 0; p < N; p++) {
-      double x = sm[p][t];
+      double y = lane < W ? sm[p][lane] : 0.0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-      if (t == 0) out[p] = x;
+      for (int o = W / 2; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
+      if (lane == 0) out[p] = y;
     }
   }
   __syncthreads();
@@ -400,6 +402,17 @@ __device__ __forceinline__ void sum_partials_block(const double* part, long off,
     for (int j = 0; j < R; j++) v[p] += t[j][p];
   }
   block_sum_small<N>(v, out);
+}
+
+// Sums of count <= PF_THREADS partial rows (16 doubles, M <= 16 used) by the
+// whole block in a fixed order: row t to thread t, then block_sum_small.
+template <int M>
+__device__ __forceinline__ void sum_rows_small(const double* part, int count, double* out) {
+  double v[M];
+#pragma unroll
+  for (int j = 0; j < M; j++)
+    v[j] = (int)threadIdx.x < count ? __ldcg(part + (long)threadIdx.x * 16 + j) : 0.0;
+  block_sum_small<M>(v, out);
 }
 
 // Grid barrier of the cooperative launch (every block resident): an arrival
@@ -444,6 +457,176 @@ __device__ __forceinline__ void own_range(int m, int b, int G, int& k0, int& k1)
   const int cp = (m + G - 1) / G;
   k0 = min(m, b * cp);
   k1 = min(m, k0 + cp);
+}
+
+// The iterations of k_qmap_cg when every phase has at most one unknown per
+// thread (G x 256 unknowns: interface bands): thread t of block b takes
+// unknown b 256 + t of each phase and keeps its state in registers (cell,
+// D, 1/D, the neighbours' list positions and face weights, x, r, u, w, p,
+// s).  The iteration is Chronopoulos and Gear's form of preconditioned
+// conjugate gradients (the same iterates as the textbook form in exact
+// arithmetic), whose two inner products r . u and w . u (u = r/D, w = K u)
+// are summed together: two grid barriers an iteration, one before the
+// product K u reads the neighbours' u and one before the sums.
+//   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = r/D,
+//   w = K u, gamma' = r . u, delta = w . u, beta = gamma'/gamma,
+//   alpha = gamma' / (delta - beta gamma' / alpha).
+template <int N>
+__device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double tol2, int warm,
+                                       int maxit, const int* scnt, int c0, int c1, unsigned* bar,
+                                       int* err) {
+  const int n = (int)g.ncell;
+  const long nn = (long)N * n;
+  const int G = (int)gridDim.x, t = (int)threadIdx.x;
+  const int k = (int)blockIdx.x * PF_THREADS + t;
+  __shared__ double s_sum[3 * N];
+  bool has[N];
+  int cell[N], nbk[N][6];
+  double Dv[N], Di[N], wg[N][6], x[N], r[N], u[N], wv[N], pv[N], sv[N];
+  double acc[3 * N];
+#pragma unroll
+  for (int j = 0; j < 3 * N; j++) acc[j] = 0.0;
+  // start: b, x0, r0 = b - K x0, u0 = r0/D
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    const long o = (long)p * n;
+    has[p] = k < scnt[p];
+    x[p] = r[p] = u[p] = wv[p] = pv[p] = sv[p] = 0.0;
+    Dv[p] = Di[p] = 0.0;
+    cell[p] = 0;
+#pragma unroll
+    for (int f = 0; f < 6; f++) {
+      nbk[p][f] = -1;
+      wg[p][f] = 0.0;
+    }
+    if (!has[p]) continue;
+    const int i = __ldcg(w.idx + o + k);
+    cell[p] = i;
+    int nb[3][2];
+    pf_stencil(g, i, nb);
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+      if (ax >= g.dim) break;
+      const double* wa = w.w + ax * nn + o;
+      const int jm = nb[ax][0], jp = nb[ax][1];
+      // a neighbour off the list shares no coupled face (weight 0)
+      if (jp >= 0) {
+        nbk[p][2 * ax + 1] = __ldcg(w.pos + o + jp);
+        wg[p][2 * ax + 1] = wa[i];
+      }
+      if (jm >= 0) {
+        nbk[p][2 * ax] = __ldcg(w.pos + o + jm);
+        wg[p][2 * ax] = wa[jm];
+      }
+    }
+    const int l = w.lab[o + i];
+    const double sk = w.sumR[o + l] / w.sumD[o + l];
+    Dv[p] = w.D[o + i];
+    Di[p] = w.Dinv[o + i];
+    const double bv = -(w.R[o + i] - Dv[p] * sk);
+    r[p] = bv;
+    if (warm) {
+      x[p] = w.x[o + i];
+      r[p] = bv - k_apply<N>(g, nb, i, o, nn, w.w, w.D, w.x);
+    }
+    u[p] = r[p] * Di[p];
+    w.p[o + k] = u[p];  // the shared copy of u
+    acc[2 * N + p] = bv * (bv * Di[p]);
+  }
+  bool ok = grid_sync(bar, err);
+  auto product = [&]() {  // w = K u from the neighbours' shared u; r . u, w . u
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      acc[p] = acc[N + p] = 0.0;
+      if (!has[p]) continue;
+      const long o = (long)p * n;
+      double q = Dv[p] * u[p];
+#pragma unroll
+      for (int f = 0; f < 6; f++)
+        if (nbk[p][f] >= 0) q = fma(-wg[p][f], __ldcg(w.p + o + nbk[p][f]), q);
+      wv[p] = q;
+      acc[p] = r[p] * u[p];
+      acc[N + p] = q * u[p];
+    }
+  };
+  double gam[N], alpha[N], beta[N], ref[N];
+  bool conv[N];
+  int it = 0;
+  if (ok) {
+    product();
+    double v3[3 * N];
+#pragma unroll
+    for (int j = 0; j < 3 * N; j++) v3[j] = acc[j];
+    block_sum_small<3 * N>(v3, w.part + PART_CG1 + (long)blockIdx.x * 16);
+    ok = grid_sync(bar, err);
+  }
+  if (ok) {
+    sum_rows_small<3 * N>(w.part + PART_CG1, G, s_sum);
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      gam[p] = s_sum[p];
+      ref[p] = s_sum[2 * N + p];
+      alpha[p] = s_sum[N + p] > 0.0 ? gam[p] / s_sum[N + p] : 0.0;
+      beta[p] = 0.0;
+      conv[p] = !(gam[p] > tol2 * ref[p]) || !(alpha[p] > 0.0);
+    }
+    // the start may meet the test already; the others iterate
+    while (it < maxit) {
+      bool all = true;
+#pragma unroll
+      for (int p = 0; p < N; p++) all = all && conv[p];
+      if (all) break;
+#pragma unroll
+      for (int p = 0; p < N; p++) {
+        if (conv[p] || !has[p]) continue;
+        pv[p] = fma(beta[p], pv[p], u[p]);
+        sv[p] = fma(beta[p], sv[p], wv[p]);
+        x[p] = fma(alpha[p], pv[p], x[p]);
+        r[p] = fma(-alpha[p], sv[p], r[p]);
+        u[p] = r[p] * Di[p];
+        w.p[(long)p * n + k] = u[p];
+      }
+      if (!(ok = grid_sync(bar, err))) break;
+      product();
+      double v2[2 * N];
+#pragma unroll
+      for (int j = 0; j < 2 * N; j++) v2[j] = acc[j];
+      block_sum_small<2 * N>(v2, w.part + PART_CG1 + (long)blockIdx.x * 16);
+      if (!(ok = grid_sync(bar, err))) break;
+      sum_rows_small<2 * N>(w.part + PART_CG1, G, s_sum);
+#pragma unroll
+      for (int p = 0; p < N; p++) {
+        if (conv[p]) continue;
+        const double gn = s_sum[p], dn = s_sum[N + p];
+        const double bt = gam[p] > 0.0 ? gn / gam[p] : 0.0;
+        const double den = dn - bt * gn / alpha[p];
+        beta[p] = bt;
+        gam[p] = gn;
+        alpha[p] = den > 0.0 ? gn / den : 0.0;
+        conv[p] = !(gn > tol2 * ref[p]) || !(alpha[p] > 0.0);
+      }
+      it++;
+    }
+  }
+  if (ok) {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      const long o = (long)p * n;
+      if (has[p]) w.x[o + cell[p]] = x[p];
+      if (!warm)
+        for (int i = c0 + t; i < c1; i += PF_THREADS)
+          if (w.pos[o + i] < 0) w.x[o + i] = 0.0;
+    }
+  }
+  if (blockIdx.x == 0 && t == 0 && ok) {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      w.scal[16 + p] = ref[p];
+      w.scal[24 + p] = gam[p];
+      w.flag[1 + p] = conv[p] ? 1 : 0;
+    }
+    w.flag[11] = it;
+  }
 }
 
 // Eq. 4 by conjugate gradients preconditioned with D, in one launch:
@@ -526,6 +709,13 @@ __global__ void __launch_bounds__(PF_THREADS) k_qmap_cg(PfGeom g, PfWork w, doub
     }
   }
   if (!grid_sync(bar, err)) return;
+  bool fits = true;
+#pragma unroll
+  for (int p = 0; p < N; p++) fits = fits && scnt[p] <= G * PF_THREADS;
+  if (fits) {
+    cg_one<N>(g, w, tol2, warm, maxit, scnt, c0, c1, bar, err);
+    return;
+  }
 
   // 2. start
   double acc[N], ref[N];

@@ -175,3 +175,33 @@ def test_full_steps_keep_invariants_and_the_equilibrium_band(gpu):
     assert 0.85 * expect <= band <= 1.15 * expect, (band, expect)
     V = g.cons_to_prim(Ud).cpu().numpy()
     assert np.abs(V[2:4] - 1.0).max() < 1e-9
+
+
+def test_qmap_solution_on_a_fully_mixed_grid(gpu):
+    """Fractions inside (0, 1) on every cell of a 200^2 periodic grid: one
+    region of 40,000 unknowns a phase, more than the register-resident
+    iteration takes (one unknown per thread), so the general listed-unknowns
+    iteration runs; its Q solves the oracle's discrete Eq. 4."""
+    case = inputs.two_phase_advection_2d(n=200)
+    go, g = _grids(case)
+    V = case.V.copy()
+    ny, nx = V.shape[1:]
+    yy, xx = np.meshgrid((np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx, indexing="ij")
+    a1 = 0.5 + 0.3 * np.sin(2 * np.pi * xx) * np.sin(2 * np.pi * yy)
+    rho = case.meta["rho"]
+    V[0], V[1] = rho[0] * a1, rho[1] * (1 - a1)
+    V[5], V[6] = a1, 1 - a1
+    U = oracle.prim_to_cons(go, V)
+    Ud = to_dev(U)
+    g.bind(Ud).set_pf_workspace(Ud.device)
+    g.cac_rhs(Ud)
+    Q, iters, res = g.qmap(Ud, tol=1e-12, maxit=20000)
+    assert res <= 1e-12 and iters > 0
+    Q = Q.cpu().numpy()
+    phi = pf.fractions(go, U)
+    R_or, _, _ = pf.cac_rhs(go, U)
+    _, Rp = pf.qmap(go, phi, R_or)
+    for p in range(go.N):
+        A, _ = pf.qmap_operator(go, phi[p])
+        AQ = A @ Q[p].reshape(-1)
+        assert np.abs(AQ - Rp[p].reshape(-1)).max() <= 1e-8 * max(np.abs(R_or).max(), 1e-300)
