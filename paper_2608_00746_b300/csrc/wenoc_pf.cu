@@ -356,16 +356,21 @@ constexpr long PART_TOTAL = PART_CG1 + (long)PF_CG_BLOCKS * 16;
 // warp 0.  out is written by thread 0 and read by the block after the
 // closing barrier.
 template <int N>
-__device__ __forceinline__ void block_sum_small(const double (&v)[N], double* out) {
+__device__ __forceinline__ void block_sum_small(const double (&v)[N], double* out,
+                                                bool warp_zero = false) {
   constexpr int W = PF_THREADS / 32;
   __shared__ double sm[N][W];
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  // (warp_zero: the caller knows every value of this warp is +0; its sum
+  // is +0 without the shuffles)
 #pragma unroll
   for (int p = 0; p < N; p++) {
     double x = v[p];
+    if (!warp_zero) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) sm[p][wid] = x;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    }
+    if (lane == 0) sm[p][wid] = warp_zero ? 0.0 : x;
   }
   __syncthreads();
   if (wid == 0) {
@@ -404,14 +409,21 @@ __device__ __forceinline__ void sum_partials_block(const double* part, long off,
   block_sum_small<N>(v, out);
 }
 
-// Sums of count <= PF_THREADS partial rows (16 doubles, M <= 16 used) by the
-// whole block in a fixed order: row t to thread t, then block_sum_small.
+// Sums of count <= 4 PF_THREADS partial rows (16 doubles, M <= 16 used) by
+// the whole block in a fixed order: rows t, t + 256, ... to thread t, then
+// block_sum_small.
 template <int M>
 __device__ __forceinline__ void sum_rows_small(const double* part, int count, double* out) {
   double v[M];
 #pragma unroll
-  for (int j = 0; j < M; j++)
-    v[j] = (int)threadIdx.x < count ? __ldcg(part + (long)threadIdx.x * 16 + j) : 0.0;
+  for (int j = 0; j < M; j++) v[j] = 0.0;
+#pragma unroll
+  for (int rrow = 0; rrow < 4; rrow++) {
+    const int row = (int)threadIdx.x + rrow * PF_THREADS;
+    if (row < count)
+#pragma unroll
+      for (int j = 0; j < M; j++) v[j] += __ldcg(part + (long)row * 16 + j);
+  }
   block_sum_small<M>(v, out);
 }
 
@@ -426,26 +438,28 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* err) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
+    // release of this block's writes with the arrival, acquire of the
+    // others' with the generation (PTX memory model, gpu scope)
     volatile int* verr = err;
-    const unsigned g0 = *gen;
-    __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+    unsigned g0, arrived;
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(g0) : "l"(bar + 1) : "memory");
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(bar) : "memory");
+    if (arrived == gridDim.x - 1) {
       atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
+      asm volatile("red.release.gpu.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
     } else {
       unsigned spins = 0;
-      while (*gen == g0) {
-        if (*verr) break;
+      for (;;) {
+        unsigned gv;
+        asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(gv) : "l"(bar + 1) : "memory");
+        if (gv != g0) break;
+        if ((spins & 255u) == 0u && *verr) break;
         if (++spins > PF_SPIN_LIMIT) {
           atomicExch(err, 1);
           break;
         }
-        __nanosleep(64);
       }
     }
-    __threadfence();
     ok = *verr == 0;
   }
   __syncthreads();
@@ -480,6 +494,11 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
   const int G = (int)gridDim.x, t = (int)threadIdx.x;
   const int k = (int)blockIdx.x * PF_THREADS + t;
   __shared__ double s_sum[3 * N];
+  int maxm = 0;
+#pragma unroll
+  for (int p = 0; p < N; p++) maxm = max(maxm, scnt[p]);
+  // a warp whose unknowns are all past the lists contributes zeros
+  const bool idle_warp = (int)blockIdx.x * PF_THREADS + (t & ~31) >= maxm;
   bool has[N];
   int cell[N], nbk[N][6];
   double Dv[N], Di[N], wg[N][6], x[N], r[N], u[N], wv[N], pv[N], sv[N];
@@ -557,7 +576,7 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
     double v3[3 * N];
 #pragma unroll
     for (int j = 0; j < 3 * N; j++) v3[j] = acc[j];
-    block_sum_small<3 * N>(v3, w.part + PART_CG1 + (long)blockIdx.x * 16);
+    block_sum_small<3 * N>(v3, w.part + PART_CG1 + (long)blockIdx.x * 16, idle_warp);
     ok = grid_sync(bar, err);
   }
   if (ok) {
@@ -591,7 +610,7 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
       double v2[2 * N];
 #pragma unroll
       for (int j = 0; j < 2 * N; j++) v2[j] = acc[j];
-      block_sum_small<2 * N>(v2, w.part + PART_CG1 + (long)blockIdx.x * 16);
+      block_sum_small<2 * N>(v2, w.part + PART_CG1 + (long)blockIdx.x * 16, idle_warp);
       if (!(ok = grid_sync(bar, err))) break;
       sum_rows_small<2 * N>(w.part + PART_CG1, G, s_sum);
 #pragma unroll
@@ -712,6 +731,11 @@ __global__ void __launch_bounds__(PF_THREADS) k_qmap_cg(PfGeom g, PfWork w, doub
   bool fits = true;
 #pragma unroll
   for (int p = 0; p < N; p++) fits = fits && scnt[p] <= G * PF_THREADS;
+  if (b == 0 && t == 0) {
+#pragma unroll
+    for (int p = 0; p < N; p++) w.flag[12 + p] = scnt[p];
+    w.flag[17] = fits ? 1 : 0;
+  }
   if (fits) {
     cg_one<N>(g, w, tol2, warm, maxit, scnt, c0, c1, bar, err);
     return;
@@ -917,15 +941,25 @@ cudaError_t pf_qmap_solve(const PfGeom& g, const PfWork& w, int warm, double tol
   if (e != cudaSuccess) return e;
   const int nb = pf_grid(g.ncell);
   PF_DISPATCH(g.N, (k_qm_sums<N_><<<nb, PF_THREADS, 0, st>>>(g, w.R, w.D, w.lab, w.sumR, w.sumD)));
-  // one block per SM, all resident (a cooperative launch fails otherwise)
-  static int sms = 0;
+  // one or two blocks per SM as registers allow, all resident (a
+  // cooperative launch fails otherwise); the register-resident iteration
+  // takes up to 256 unknowns a block and phase
+  static int sms = 0, per_sm[8] = {0};
   if (sms == 0) {
     int dev = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
   }
-  int blocks = sms < 1 ? 1 : (sms > PF_CG_BLOCKS ? PF_CG_BLOCKS : sms);
+  if (per_sm[g.N] == 0) {
+    int k = 0;
+    PF_DISPATCH(g.N, (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_qmap_cg<N_>,
+                                                                       PF_THREADS, 0)));
+    if (e != cudaSuccess) return e;
+    per_sm[g.N] = k < 1 ? 1 : (k > 2 ? 2 : k);
+  }
+  long want = (long)sms * per_sm[g.N];
+  int blocks = (int)(want < 1 ? 1 : (want > 4 * PF_THREADS ? 4 * PF_THREADS : want));
   PfGeom gg = g;
   PfWork ww = w;
   void* args[] = {&gg, &ww, &tol2, &warm, &maxit};
