@@ -466,67 +466,11 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* err) {
   return ok;
 }
 
-// The same barrier where the last block to arrive first runs last() (the
-// whole block; it reads what the others wrote before arriving, from L2) and
-// only then releases the others, which then read its results from L2.
-template <typename F>
-__device__ __forceinline__ bool grid_sync_last(unsigned* bar, int* err, F&& last) {
-  __shared__ int ok, is_last;
-  __syncthreads();
-  unsigned g0 = 0;
-  if (threadIdx.x == 0) {
-    unsigned arrived;
-    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(g0) : "l"(bar + 1) : "memory");
-    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(bar) : "memory");
-    is_last = arrived == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (is_last) {
-    last();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      atomicExch(bar, 0u);
-      asm volatile("red.release.gpu.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
-    }
-  } else if (threadIdx.x == 0) {
-    volatile int* verr = err;
-    unsigned spins = 0;
-    for (;;) {
-      unsigned gv;
-      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(gv) : "l"(bar + 1) : "memory");
-      if (gv != g0) break;
-      if ((spins & 255u) == 0u && *verr) break;
-      if (++spins > PF_SPIN_LIMIT) {
-        atomicExch(err, 1);
-        break;
-      }
-    }
-  }
-  if (threadIdx.x == 0) ok = *(volatile int*)err == 0;
-  __syncthreads();
-  return ok;
-}
-
 // The unknowns of one phase taken by block b of G: [k0, k1) of m.
 __device__ __forceinline__ void own_range(int m, int b, int G, int& k0, int& k1) {
   const int cp = (m + G - 1) / G;
   k0 = min(m, b * cp);
   k1 = min(m, k0 + cp);
-}
-
-// The sums of the G partial rows (fixed order, by the last block at a
-// barrier) into w.scal[48 ..], and their reading by every block.
-template <int M>
-__device__ __forceinline__ void publish_sums(const PfWork& w, int G, double* s_sum) {
-  sum_rows_small<M>(w.part + PART_CG1, G, s_sum);
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int j = 0; j < M; j++) w.scal[48 + j] = s_sum[j];
-}
-template <int M>
-__device__ __forceinline__ void read_sums(const PfWork& w, double* s_sum) {
-  if (threadIdx.x < M) s_sum[threadIdx.x] = __ldcg(w.scal + 48 + threadIdx.x);
-  __syncthreads();
 }
 
 // The iterations of k_qmap_cg when every phase has at most one unknown per
@@ -633,10 +577,10 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
 #pragma unroll
     for (int j = 0; j < 3 * N; j++) v3[j] = acc[j];
     block_sum_small<3 * N>(v3, w.part + PART_CG1 + (long)blockIdx.x * 16, idle_warp);
-    ok = grid_sync_last(bar, err, [&]() { publish_sums<3 * N>(w, G, s_sum); });
+    ok = grid_sync(bar, err);
   }
   if (ok) {
-    read_sums<3 * N>(w, s_sum);
+    sum_rows_small<3 * N>(w.part + PART_CG1, G, s_sum);
 #pragma unroll
     for (int p = 0; p < N; p++) {
       gam[p] = s_sum[p];
@@ -667,8 +611,8 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
 #pragma unroll
       for (int j = 0; j < 2 * N; j++) v2[j] = acc[j];
       block_sum_small<2 * N>(v2, w.part + PART_CG1 + (long)blockIdx.x * 16, idle_warp);
-      if (!(ok = grid_sync_last(bar, err, [&]() { publish_sums<2 * N>(w, G, s_sum); }))) break;
-      read_sums<2 * N>(w, s_sum);
+      if (!(ok = grid_sync(bar, err))) break;
+      sum_rows_small<2 * N>(w.part + PART_CG1, G, s_sum);
 #pragma unroll
       for (int p = 0; p < N; p++) {
         if (conv[p]) continue;
@@ -997,25 +941,18 @@ cudaError_t pf_qmap_solve(const PfGeom& g, const PfWork& w, int warm, double tol
   if (e != cudaSuccess) return e;
   const int nb = pf_grid(g.ncell);
   PF_DISPATCH(g.N, (k_qm_sums<N_><<<nb, PF_THREADS, 0, st>>>(g, w.R, w.D, w.lab, w.sumR, w.sumD)));
-  // one or two blocks per SM as registers allow, all resident (a
-  // cooperative launch fails otherwise); the register-resident iteration
-  // takes up to 256 unknowns a block and phase
-  static int sms = 0, per_sm[8] = {0};
+  // one block per SM, all resident (a cooperative launch fails otherwise);
+  // the register-resident iteration takes up to 256 unknowns a block and
+  // phase.  (Two blocks per SM, where registers allow, measured slower: 25
+  // against 15 us an iteration on the shock-bubble bands.)
+  static int sms = 0;
   if (sms == 0) {
     int dev = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
   }
-  if (per_sm[g.N] == 0) {
-    int k = 0;
-    PF_DISPATCH(g.N, (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_qmap_cg<N_>,
-                                                                       PF_THREADS, 0)));
-    if (e != cudaSuccess) return e;
-    per_sm[g.N] = k < 1 ? 1 : (k > 2 ? 2 : k);
-  }
-  long want = (long)sms * per_sm[g.N];
-  int blocks = (int)(want < 1 ? 1 : (want > 4 * PF_THREADS ? 4 * PF_THREADS : want));
+  const int blocks = sms < 1 ? 1 : (sms > 4 * PF_THREADS ? 4 * PF_THREADS : sms);
   PfGeom gg = g;
   PfWork ww = w;
   void* args[] = {&gg, &ww, &tol2, &warm, &maxit};

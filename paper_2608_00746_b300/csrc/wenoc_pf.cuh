@@ -73,7 +73,7 @@ struct PfWork {
   int* idx;         // the list: cell of unknown k of phase p
   int* pos;         // its inverse: position of cell i, -1 off the list
   double* part;     // reduction partials (offsets in wenoc_pf.cu)
-  double* scal;     // [64]: M, B[0..N-1] | b.b/D at 16+p | r.r/D at 24+p | sums at 48..
+  double* scal;     // [64]: M, B[0..N-1] | b.b/D at 16+p | r.r/D at 24+p
   int* flag;        // [64]: label change, converged per phase at 1+p, grid barrier at
                     //       8..10 (arrivals, generation, error), iterations at 11,
                     //       unknowns per phase at 12+p, register-resident path at 17
