@@ -473,9 +473,10 @@ __device__ __forceinline__ void own_range(int m, int b, int G, int& k0, int& k1)
   k1 = min(m, k0 + cp);
 }
 
-// The iterations of k_qmap_cg when every phase has at most one unknown per
-// thread (G x 256 unknowns: interface bands): thread t of block b takes
-// unknown b 256 + t of each phase and keeps its state in registers (cell,
+// The iterations of k_qmap_cg when every phase has at most R unknowns per
+// thread (R G 256 unknowns: interface bands): thread t of block b takes
+// unknowns b 256 + t + j G 256, j < R, of each phase and keeps their state
+// in registers (cell,
 // D, 1/D, the neighbours' list positions and face weights, x, r, u, w, p,
 // s).  The iteration is Chronopoulos and Gear's form of preconditioned
 // conjugate gradients (the same iterates as the textbook form in exact
@@ -485,42 +486,46 @@ __device__ __forceinline__ void own_range(int m, int b, int G, int& k0, int& k1)
 //   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = r/D,
 //   w = K u, gamma' = r . u, delta = w . u, beta = gamma'/gamma,
 //   alpha = gamma' / (delta - beta gamma' / alpha).
-template <int N>
+template <int N, int R>
 __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double tol2, int warm,
                                        int maxit, const int* scnt, int c0, int c1, unsigned* bar,
                                        int* err) {
+  constexpr int E = N * R;  // slot e: phase e / R, unknown k + (e % R) G 256
   const int n = (int)g.ncell;
   const long nn = (long)N * n;
   const int G = (int)gridDim.x, t = (int)threadIdx.x;
   const int k = (int)blockIdx.x * PF_THREADS + t;
+  const int span = G * PF_THREADS;
   __shared__ double s_sum[3 * N];
   int maxm = 0;
 #pragma unroll
   for (int p = 0; p < N; p++) maxm = max(maxm, scnt[p]);
   // a warp whose unknowns are all past the lists contributes zeros
   const bool idle_warp = (int)blockIdx.x * PF_THREADS + (t & ~31) >= maxm;
-  bool has[N];
-  int cell[N], nbk[N][6];
-  double Dv[N], Di[N], wg[N][6], x[N], r[N], u[N], wv[N], pv[N], sv[N];
+  bool has[E];
+  int cell[E], ke[E], nbk[E][6];
+  double Dv[E], Di[E], wg[E][6], x[E], r[E], u[E], wv[E], pv[E], sv[E];
   double acc[3 * N];
 #pragma unroll
   for (int j = 0; j < 3 * N; j++) acc[j] = 0.0;
   // start: b, x0, r0 = b - K x0, u0 = r0/D
 #pragma unroll
-  for (int p = 0; p < N; p++) {
+  for (int e = 0; e < E; e++) {
+    const int p = e / R;
     const long o = (long)p * n;
-    has[p] = k < scnt[p];
-    x[p] = r[p] = u[p] = wv[p] = pv[p] = sv[p] = 0.0;
-    Dv[p] = Di[p] = 0.0;
-    cell[p] = 0;
+    ke[e] = k + (e % R) * span;
+    has[e] = ke[e] < scnt[p];
+    x[e] = r[e] = u[e] = wv[e] = pv[e] = sv[e] = 0.0;
+    Dv[e] = Di[e] = 0.0;
+    cell[e] = 0;
 #pragma unroll
     for (int f = 0; f < 6; f++) {
-      nbk[p][f] = -1;
-      wg[p][f] = 0.0;
+      nbk[e][f] = -1;
+      wg[e][f] = 0.0;
     }
-    if (!has[p]) continue;
-    const int i = __ldcg(w.idx + o + k);
-    cell[p] = i;
+    if (!has[e]) continue;
+    const int i = __ldcg(w.idx + o + ke[e]);
+    cell[e] = i;
     int nb[3][2];
     pf_stencil(g, i, nb);
 #pragma unroll
@@ -530,42 +535,44 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
       const int jm = nb[ax][0], jp = nb[ax][1];
       // a neighbour off the list shares no coupled face (weight 0)
       if (jp >= 0) {
-        nbk[p][2 * ax + 1] = __ldcg(w.pos + o + jp);
-        wg[p][2 * ax + 1] = wa[i];
+        nbk[e][2 * ax + 1] = __ldcg(w.pos + o + jp);
+        wg[e][2 * ax + 1] = wa[i];
       }
       if (jm >= 0) {
-        nbk[p][2 * ax] = __ldcg(w.pos + o + jm);
-        wg[p][2 * ax] = wa[jm];
+        nbk[e][2 * ax] = __ldcg(w.pos + o + jm);
+        wg[e][2 * ax] = wa[jm];
       }
     }
     const int l = w.lab[o + i];
     const double sk = w.sumR[o + l] / w.sumD[o + l];
-    Dv[p] = w.D[o + i];
-    Di[p] = w.Dinv[o + i];
-    const double bv = -(w.R[o + i] - Dv[p] * sk);
-    r[p] = bv;
+    Dv[e] = w.D[o + i];
+    Di[e] = w.Dinv[o + i];
+    const double bv = -(w.R[o + i] - Dv[e] * sk);
+    r[e] = bv;
     if (warm) {
-      x[p] = w.x[o + i];
-      r[p] = bv - k_apply<N>(g, nb, i, o, nn, w.w, w.D, w.x);
+      x[e] = w.x[o + i];
+      r[e] = bv - k_apply<N>(g, nb, i, o, nn, w.w, w.D, w.x);
     }
-    u[p] = r[p] * Di[p];
-    w.p[o + k] = u[p];  // the shared copy of u
-    acc[2 * N + p] = bv * (bv * Di[p]);
+    u[e] = r[e] * Di[e];
+    w.p[o + ke[e]] = u[e];  // the shared copy of u
+    acc[2 * N + p] = fma(bv, bv * Di[e], acc[2 * N + p]);
   }
   bool ok = grid_sync(bar, err);
   auto product = [&]() {  // w = K u from the neighbours' shared u; r . u, w . u
 #pragma unroll
-    for (int p = 0; p < N; p++) {
-      acc[p] = acc[N + p] = 0.0;
-      if (!has[p]) continue;
+    for (int p = 0; p < N; p++) acc[p] = acc[N + p] = 0.0;
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+      if (!has[e]) continue;
+      const int p = e / R;
       const long o = (long)p * n;
-      double q = Dv[p] * u[p];
+      double q = Dv[e] * u[e];
 #pragma unroll
       for (int f = 0; f < 6; f++)
-        if (nbk[p][f] >= 0) q = fma(-wg[p][f], __ldcg(w.p + o + nbk[p][f]), q);
-      wv[p] = q;
-      acc[p] = r[p] * u[p];
-      acc[N + p] = q * u[p];
+        if (nbk[e][f] >= 0) q = fma(-wg[e][f], __ldcg(w.p + o + nbk[e][f]), q);
+      wv[e] = q;
+      acc[p] = fma(r[e], u[e], acc[p]);
+      acc[N + p] = fma(q, u[e], acc[N + p]);
     }
   };
   double gam[N], alpha[N], beta[N], ref[N];
@@ -596,14 +603,15 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
       for (int p = 0; p < N; p++) all = all && conv[p];
       if (all) break;
 #pragma unroll
-      for (int p = 0; p < N; p++) {
-        if (conv[p] || !has[p]) continue;
-        pv[p] = fma(beta[p], pv[p], u[p]);
-        sv[p] = fma(beta[p], sv[p], wv[p]);
-        x[p] = fma(alpha[p], pv[p], x[p]);
-        r[p] = fma(-alpha[p], sv[p], r[p]);
-        u[p] = r[p] * Di[p];
-        w.p[(long)p * n + k] = u[p];
+      for (int e = 0; e < E; e++) {
+        const int p = e / R;
+        if (conv[p] || !has[e]) continue;
+        pv[e] = fma(beta[p], pv[e], u[e]);
+        sv[e] = fma(beta[p], sv[e], wv[e]);
+        x[e] = fma(alpha[p], pv[e], x[e]);
+        r[e] = fma(-alpha[p], sv[e], r[e]);
+        u[e] = r[e] * Di[e];
+        w.p[(long)p * n + ke[e]] = u[e];
       }
       if (!(ok = grid_sync(bar, err))) break;
       product();
@@ -629,13 +637,15 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
   }
   if (ok) {
 #pragma unroll
-    for (int p = 0; p < N; p++) {
-      const long o = (long)p * n;
-      if (has[p]) w.x[o + cell[p]] = x[p];
-      if (!warm)
+    for (int e = 0; e < E; e++)
+      if (has[e]) w.x[(long)(e / R) * n + cell[e]] = x[e];
+    if (!warm)
+#pragma unroll
+      for (int p = 0; p < N; p++) {
+        const long o = (long)p * n;
         for (int i = c0 + t; i < c1; i += PF_THREADS)
           if (w.pos[o + i] < 0) w.x[o + i] = 0.0;
-    }
+      }
   }
   if (blockIdx.x == 0 && t == 0 && ok) {
 #pragma unroll
@@ -728,17 +738,26 @@ __global__ void __launch_bounds__(PF_THREADS) k_qmap_cg(PfGeom g, PfWork w, doub
     }
   }
   if (!grid_sync(bar, err)) return;
-  bool fits = true;
+  // unknowns a thread keeps in registers: one, two (N <= 2), else the
+  // iteration on the lists in memory below
+  int maxm = 0;
 #pragma unroll
-  for (int p = 0; p < N; p++) fits = fits && scnt[p] <= G * PF_THREADS;
+  for (int p = 0; p < N; p++) maxm = max(maxm, scnt[p]);
+  const int per_thread = maxm <= G * PF_THREADS ? 1 : (N <= 2 && maxm <= 2 * G * PF_THREADS ? 2 : 0);
   if (b == 0 && t == 0) {
 #pragma unroll
     for (int p = 0; p < N; p++) w.flag[12 + p] = scnt[p];
-    w.flag[17] = fits ? 1 : 0;
+    w.flag[17] = per_thread;
   }
-  if (fits) {
-    cg_one<N>(g, w, tol2, warm, maxit, scnt, c0, c1, bar, err);
+  if (per_thread == 1) {
+    cg_one<N, 1>(g, w, tol2, warm, maxit, scnt, c0, c1, bar, err);
     return;
+  }
+  if constexpr (N <= 2) {
+    if (per_thread == 2) {
+      cg_one<N, 2>(g, w, tol2, warm, maxit, scnt, c0, c1, bar, err);
+      return;
+    }
   }
 
   // 2. start

@@ -76,7 +76,8 @@ struct PfWork {
   double* scal;     // [64]: M, B[0..N-1] | b.b/D at 16+p | r.r/D at 24+p
   int* flag;        // [64]: label change, converged per phase at 1+p, grid barrier at
                     //       8..10 (arrivals, generation, error), iterations at 11,
-                    //       unknowns per phase at 12+p, register-resident path at 17
+                    //       unknowns per phase at 12+p, unknowns a thread keeps in
+                    //       registers at 17 (0: the lists in memory)
 };
 
 // Launchers (wenoc_pf.cu), all asynchronous on st.

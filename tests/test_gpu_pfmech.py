@@ -177,12 +177,15 @@ def test_full_steps_keep_invariants_and_the_equilibrium_band(gpu):
     assert np.abs(V[2:4] - 1.0).max() < 1e-9
 
 
-def test_qmap_solution_on_a_fully_mixed_grid(gpu):
-    """Fractions inside (0, 1) on every cell of a 200^2 periodic grid: one
-    region of 40,000 unknowns a phase, more than the register-resident
-    iteration takes (one unknown per thread), so the general listed-unknowns
-    iteration runs; its Q solves the oracle's discrete Eq. 4."""
-    case = inputs.two_phase_advection_2d(n=200)
+@pytest.mark.parametrize("n", [200, 300])
+def test_qmap_solution_on_a_fully_mixed_grid(gpu, n):
+    """Fractions inside (0, 1) on every cell of an n^2 periodic grid: one
+    region of n^2 unknowns a phase.  40,000 (n = 200) take the
+    register-resident iteration with two unknowns a thread (one a thread
+    holds 148 x 256 = 37,888); 90,000 (n = 300) are more than two a thread
+    and take the iteration on the lists in memory.  Either way Q solves the
+    oracle's discrete Eq. 4."""
+    case = inputs.two_phase_advection_2d(n=n)
     go, g = _grids(case)
     V = case.V.copy()
     ny, nx = V.shape[1:]
@@ -197,6 +200,8 @@ def test_qmap_solution_on_a_fully_mixed_grid(gpu):
     g.cac_rhs(Ud)
     Q, iters, res = g.qmap(Ud, tol=1e-12, maxit=20000)
     assert res <= 1e-12 and iters > 0
+    flags = g.pfws.view(torch.int32)[-64:].cpu().numpy()
+    assert list(flags[12:14]) == [n * n, n * n] and flags[17] == (2 if n == 200 else 0)
     Q = Q.cpu().numpy()
     phi = pf.fractions(go, U)
     R_or, _, _ = pf.cac_rhs(go, U)
