@@ -451,6 +451,16 @@ wc_status wc_fp64_peak_kernel(int blocks, int threads, int iters, double *sink_d
 wc_status wc_convert_f32(const double *x_dev, float *f_dev, double *back_dev, long n,
                          void *stream);
 
+/* The grid barrier of the Q-map's cooperative launch on its own: one block
+ * of 256 threads per SM passes `rounds` barriers (words_dev: 4 device ints,
+ * cleared by the call).  skip_block >= 0 makes that block leave before the
+ * first barrier, so every other block's bounded wait runs out: the call then
+ * returns WC_ERR_TIMEOUT (after a few seconds) and the context stays usable.
+ * skip_block = -1: every block arrives, WC_OK.  The paper has no
+ * counterpart; it lets a test exercise the barrier and its time-out.
+ * Synchronizes stream. */
+wc_status wc_grid_barrier_check(int *words_dev, int skip_block, int rounds, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -807,6 +807,18 @@ extern "C" wc_status wc_fp64_peak_kernel(int blocks, int threads, int iters, dou
   return cudaGetLastError() == cudaSuccess ? WC_OK : WC_ERR_CUDA;
 }
 
+// ------------------------------------------------------------------ grid barrier check
+extern "C" wc_status wc_grid_barrier_check(int* words, int skip_block, int rounds, void* stream) {
+  if (!words || rounds < 1 || skip_block < -1) return WC_ERR_ARG;
+  cudaStream_t st = S(stream);
+  cudaError_t e = pf_barrier_check(words, skip_block, rounds, st);
+  int h[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, words, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return WC_ERR_CUDA;
+  return h[2] ? WC_ERR_TIMEOUT : WC_OK;
+}
+
 // ------------------------------------------------------------------ conversion check
 __global__ void k_convert_f32(const double* x, float* f, double* back, long n) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;

@@ -908,6 +908,16 @@ __global__ void __launch_bounds__(PF_THREADS) k_qmap_cg(PfGeom g, PfWork w, doub
   }
 }
 
+// The grid barrier alone, for its test: rounds barriers, except that block
+// skip (>= 0) leaves before the first, so every other block's wait runs
+// out and sets the error word.
+__global__ void __launch_bounds__(PF_THREADS) k_barrier_check(unsigned* bar, int* err, int skip,
+                                                              int rounds) {
+  if ((int)blockIdx.x == skip) return;
+  for (int r = 0; r < rounds; r++)
+    if (!grid_sync(bar, err)) return;
+}
+
 // ------------------------------------------------------------------ launchers
 #define PF_DISPATCH(N, call)                       \
   switch (N) {                                     \
@@ -978,6 +988,20 @@ cudaError_t pf_qmap_solve(const PfGeom& g, const PfWork& w, int warm, double tol
   PF_DISPATCH(g.N, (e = cudaLaunchCooperativeKernel((const void*)k_qmap_cg<N_>, dim3(blocks),
                                                     dim3(PF_THREADS), args, 0, st)));
   return e;
+}
+
+cudaError_t pf_barrier_check(int* words, int skip, int rounds, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(words, 0, 4 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  unsigned* bar = reinterpret_cast<unsigned*>(words);
+  int* err = words + 2;
+  void* args[] = {&bar, &err, &skip, &rounds};
+  return cudaLaunchCooperativeKernel((const void*)k_barrier_check, dim3(sms < 1 ? 1 : sms),
+                                     dim3(PF_THREADS), args, 0, st);
 }
 
 }  // namespace wc

@@ -98,5 +98,9 @@ cudaError_t pf_label_rounds(const PfGeom& g, const PfWork& w, int rounds, cudaSt
 // last r.r/D and w.scal[16 + p] the reference b.b/D.
 cudaError_t pf_qmap_solve(const PfGeom& g, const PfWork& w, int warm, double tol2, int maxit,
                           cudaStream_t st);
+// The Q-map's grid barrier on its own (words: 4 device ints, cleared here):
+// rounds barriers of one block per SM; block skip >= 0 never arrives, so
+// the others' waits run out and words[2] becomes nonzero.
+cudaError_t pf_barrier_check(int* words, int skip, int rounds, cudaStream_t st);
 
 }  // namespace wc

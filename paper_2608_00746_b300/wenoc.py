@@ -105,6 +105,7 @@ _SIGS = {
     "wc_fp64_peak_kernel": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
                                            ctypes.POINTER(ctypes.c_double), _VP]),
     "wc_convert_f32": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_long, _VP]),
+    "wc_grid_barrier_check": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP]),
     "wc_sweep_timing_begin": (ctypes.c_int, [_VP, ctypes.c_int]),
     "wc_sweep_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_double),
@@ -435,6 +436,14 @@ def fp64_peak(blocks=148 * 8, threads=256, iters=20000, reps=5):
         if r > 0:
             best = max(best, fl.value / (e0.elapsed_time(e1) * 1e-3))
     return best
+
+
+def grid_barrier_check(skip_block=-1, rounds=100):
+    """Runs the Q-map's grid barrier alone (see wc_grid_barrier_check);
+    returns the status code (0 = WC_OK, 7 = WC_ERR_TIMEOUT)."""
+    words = torch.zeros(4, dtype=torch.int32, device="cuda")
+    return lib().wc_grid_barrier_check(_dptr(words), int(skip_block), int(rounds),
+                                       _stream(torch.cuda.current_stream()))
 
 
 def convert_f32(x):
