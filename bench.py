@@ -349,7 +349,9 @@ def run_ours(args):
         ms = (time.perf_counter() - t0) * 1e3 / max(args.steps, 1)
         g.sync_status()
         it, rounds, res = g.pf_stats()
+        band, per_thread = g.pf_band()
         print(json.dumps({"profile_pf": True, "ms_per_step": ms, "qmap_cg_iterations_last": it,
+                          "qmap_unknowns_last": band, "qmap_unknowns_per_thread_last": per_thread,
                           "qmap_label_rounds_last": rounds, "qmap_residual_last": res,
                           "steps": args.steps, "warmup": args.warmup}), flush=True)
         return 0
@@ -597,6 +599,7 @@ def time_phase_field(make_grid, K=20):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / K
     iters, rounds, res = g.pf_stats()
+    band, per_thread = g.pf_band()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     parts = np.zeros(4)
     Q = None
@@ -621,6 +624,7 @@ def time_phase_field(make_grid, K=20):
             "steps": K, "value": round(cells * 3 / (ms * 1e-3) / 1e6, 3), "unit": "Mcell/s",
             "ms_per_step": round(ms, 4), "qmap_cg_iterations_last": iters,
             "qmap_label_rounds_last": rounds, "qmap_residual_last": res,
+            "qmap_unknowns_last": band, "qmap_unknowns_per_thread_last": per_thread,
             "ms_hyperbolic": round(parts[0], 4), "ms_eq28": round(parts[1], 4),
             "ms_qmap": round(parts[2], 4), "ms_pf_step": round(parts[3], 4)}
 

@@ -229,6 +229,12 @@ wc_status wc_step(wc_grid *g, double cfl, double dt_fixed, int nsteps, double to
 
 /* Statistics of the last Q-map: CG iterations, labelling rounds, residual. */
 wc_status wc_pf_stats(const wc_grid *g, int *cg_iters, int *label_rounds, double *resid);
+
+/* The band of the last wc_qmap: unknowns[p] (p < N; may be null) the cells
+ * of phase p that belong to a region (the unknowns of Eq. 4 the iteration
+ * ran on), *per_thread (may be null) the unknowns a thread kept in
+ * registers (1 or 2; 0: the iteration ran on the lists in memory). */
+wc_status wc_pf_band(const wc_grid *g, int *unknowns, int *per_thread);
 /* Device pointer to the Q of the last wc_step (inside the scratch), or null. */
 const double *wc_pf_q(const wc_grid *g);
 

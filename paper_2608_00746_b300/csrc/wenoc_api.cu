@@ -48,6 +48,8 @@ struct wc_grid {
   PfGeom pg;
   int pf_iters = 0, pf_label_rounds = 0, pf_have_q = 0;
   double pf_resid = 0.0;
+  int pf_unknowns[8] = {0};  // listed unknowns per phase of the last Q-map
+  int pf_per_thread = 0;     // and the unknowns a thread kept in registers
 };
 
 static wc_status fail(wc_grid* g, wc_status s, const char* msg) {
@@ -516,9 +518,9 @@ extern "C" size_t wc_pf_workspace_bytes(const wc_grid* g) {
   if (!g) return 0;
   const size_t f = align256(sizeof(double) * (size_t)g->d.nphase * g->ncell);
   const size_t li = align256(sizeof(int) * (size_t)g->d.nphase * g->ncell);
-  // R c D 1/D sumR sumD x r p q xk, three face-weight fields, labels, the
-  // unknowns' list and its inverse, partials, scalars, flags
-  return 14 * f + 3 * li + align256(sizeof(double) * pf_part_doubles()) + 512 + 256;
+  // R c D 1/D sumR sumD x r p q xk pd sd, three face-weight fields, labels,
+  // the unknowns' list and its inverse, partials, scalars, flags
+  return 16 * f + 3 * li + align256(sizeof(double) * pf_part_doubles()) + 512 + 256;
 }
 
 extern "C" wc_status wc_set_pf_workspace(wc_grid* g, void* ws_dev, size_t bytes) {
@@ -530,7 +532,8 @@ extern "C" wc_status wc_set_pf_workspace(wc_grid* g, void* ws_dev, size_t bytes)
   const size_t li = align256(sizeof(int) * (size_t)g->d.nphase * g->ncell);
   char* w = static_cast<char*>(ws_dev);
   double** fields[] = {&g->pw.R, &g->pw.c, &g->pw.D, &g->pw.Dinv, &g->pw.sumR, &g->pw.sumD,
-                       &g->pw.x, &g->pw.r, &g->pw.p, &g->pw.q, &g->pw.xk};
+                       &g->pw.x, &g->pw.r, &g->pw.p, &g->pw.q, &g->pw.xk, &g->pw.pd,
+                       &g->pw.sd};
   for (double** d : fields) {
     *d = reinterpret_cast<double*>(w);
     w += f;
@@ -619,7 +622,7 @@ static wc_status qmap(wc_grid* g, const double* U, const double* R, double* Q, d
   e = pf_qmap_solve(g->pg, g->pw, warm, tol * tol, maxit, st);
   if (e != cudaSuccess) return cuda_fail(g, e, "qmap cg");
   const int N = g->d.nphase;
-  int flags[16] = {0};
+  int flags[32] = {0};
   double sc[32];
   e = cudaMemcpyAsync(flags, g->pw.flag, sizeof(flags), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(sc, g->pw.scal, sizeof(sc), cudaMemcpyDeviceToHost, st);
@@ -634,6 +637,8 @@ static wc_status qmap(wc_grid* g, const double* U, const double* R, double* Q, d
   for (int p = 0; p < N; p++)
     if (sc[16 + p] > 0.0) res = fmax(res, sqrt(fmax(sc[24 + p], 0.0) / sc[16 + p]));
   const int it = flags[11];
+  for (int p = 0; p < N; p++) g->pf_unknowns[p] = flags[12 + p];
+  g->pf_per_thread = flags[17];
   g->pf_iters = it;
   g->pf_resid = res;
   return WC_OK;
@@ -701,6 +706,14 @@ extern "C" wc_status wc_pf_stats(const wc_grid* g, int* cg_iters, int* label_rou
   if (cg_iters) *cg_iters = g->pf_iters;
   if (label_rounds) *label_rounds = g->pf_label_rounds;
   if (resid) *resid = g->pf_resid;
+  return WC_OK;
+}
+
+extern "C" wc_status wc_pf_band(const wc_grid* g, int* unknowns, int* per_thread) {
+  if (!g) return WC_ERR_ARG;
+  if (unknowns)
+    for (int p = 0; p < g->d.nphase; p++) unknowns[p] = g->pf_unknowns[p];
+  if (per_thread) *per_thread = g->pf_per_thread;
   return WC_OK;
 }
 

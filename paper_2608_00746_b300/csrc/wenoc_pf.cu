@@ -329,19 +329,16 @@ __global__ void __launch_bounds__(PF_THREADS) k_qm_sums(PfGeom g, const double* 
 }
 
 // The conjugate gradients of Eq. 4 run on the listed unknowns (the cells of
-// some region, in cell order per phase) in one cooperative launch of
-// CG_BLOCKS <= PF_CG_BLOCKS blocks that meet at grid barriers.  Partials:
-// p . K p, r . r/D, b . b/D [PF_CG_BLOCKS][8] each, the list counts after
-// them, and before all of them the Eq. 28 totals [PF_BLOCKS][32].  Every
-// block sums the partials itself, in the same fixed order, so all blocks
-// hold the same scalars and take the same loop decisions.
+// some region, in cell order per phase) in one cooperative launch of at
+// most PF_CG_BLOCKS blocks that meet at grid barriers.  Partials: the Eq. 28
+// totals [PF_BLOCKS][32], the list counts [PF_CG_BLOCKS][8] and the
+// iteration's sums [PF_CG_BLOCKS][16].  Every block sums the partials
+// itself, in the same fixed order, so all blocks hold the same scalars and
+// take the same loop decisions.
 constexpr int PF_CG_BLOCKS = 148 * 8;
 constexpr long PART_CAC = 0;
-constexpr long PART_PQ = (long)PF_BLOCKS * 32;
-constexpr long PART_RZ = PART_PQ + (long)PF_CG_BLOCKS * 8;
-constexpr long PART_REF = PART_RZ + (long)PF_CG_BLOCKS * 8;
-constexpr long PART_LIST = PART_REF + (long)PF_CG_BLOCKS * 8;
-constexpr long PART_CG1 = PART_LIST + (long)PF_CG_BLOCKS * 8;  // [PF_CG_BLOCKS][16]
+constexpr long PART_LIST = (long)PF_BLOCKS * 32;
+constexpr long PART_CG1 = PART_LIST + (long)PF_CG_BLOCKS * 8;
 constexpr long PART_TOTAL = PART_CG1 + (long)PF_CG_BLOCKS * 16;
 // results: scal[16 + p] b.b/D, [24 + p] r.r/D; flags: [1 + p] converged,
 // [8] [9] [10] the grid barrier (arrivals, generation, error), [11] the
@@ -383,30 +380,6 @@ __device__ __forceinline__ void block_sum_small(const double (&v)[N], double* ou
     }
   }
   __syncthreads();
-}
-
-// Sums of count per-block partial rows (8 doubles, N used) by the whole
-// block, in a fixed order: thread t adds rows t, t + 256, ... (their loads
-// in flight together), then block_sum_small; out[p] (shared) for every
-// thread afterwards.  The rows are read from L2 (other blocks wrote them).
-template <int N>
-__device__ __forceinline__ void sum_partials_block(const double* part, long off, int count,
-                                                   double* out) {
-  constexpr int R = (PF_CG_BLOCKS + PF_THREADS - 1) / PF_THREADS;
-  double t[R][N], v[N];
-#pragma unroll
-  for (int j = 0; j < R; j++) {
-    const int b = threadIdx.x + PF_THREADS * j;
-#pragma unroll
-    for (int p = 0; p < N; p++) t[j][p] = b < count ? __ldcg(part + off + (long)b * 8 + p) : 0.0;
-  }
-#pragma unroll
-  for (int p = 0; p < N; p++) {
-    v[p] = 0.0;
-#pragma unroll
-    for (int j = 0; j < R; j++) v[p] += t[j][p];
-  }
-  block_sum_small<N>(v, out);
 }
 
 // Sums of count <= 4 PF_THREADS partial rows (16 doubles, M <= 16 used) by
@@ -658,17 +631,181 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
   }
 }
 
+// The same iteration with the state in memory, for bands larger than the
+// registers take: block b takes a contiguous range of each phase's list
+// (own_range), its threads the same unknowns every iteration; x, r, the
+// direction p (pd), s, w = K u (q) and the shared copy of u (p) in the
+// workspace's list layout (p ncell + k).
+template <int N>
+__device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double tol2, int warm,
+                                       int maxit, const int* scnt, int c0, int c1, unsigned* bar,
+                                       int* err) {
+  const int n = (int)g.ncell;
+  const long nn = (long)N * n;
+  const int G = (int)gridDim.x, b = (int)blockIdx.x, t = (int)threadIdx.x;
+  __shared__ double s_sum[3 * N];
+  double acc[3 * N];
+#pragma unroll
+  for (int j = 0; j < 3 * N; j++) acc[j] = 0.0;
+  // start: b, x0, r0 = b - K x0, u0 = r0/D
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    const long o = (long)p * n;
+    int k0, k1;
+    own_range(scnt[p], b, G, k0, k1);
+    for (int k = k0 + t; k < k1; k += PF_THREADS) {
+      const int i = __ldcg(w.idx + o + k);
+      const int l = w.lab[o + i];
+      const double sk = w.sumR[o + l] / w.sumD[o + l];
+      const double bv = -(w.R[o + i] - w.D[o + i] * sk);
+      double x0 = 0.0, r0 = bv;
+      if (warm) {
+        int nb[3][2];
+        pf_stencil(g, i, nb);
+        x0 = w.x[o + i];
+        r0 = bv - k_apply<N>(g, nb, i, o, nn, w.w, w.D, w.x);
+      }
+      const double di = w.Dinv[o + i];
+      w.xk[o + k] = x0;
+      w.r[o + k] = r0;
+      w.p[o + k] = r0 * di;
+      acc[2 * N + p] = fma(bv, bv * di, acc[2 * N + p]);
+    }
+  }
+  bool ok = grid_sync(bar, err);
+  auto product = [&](const bool* skip) {  // q = K u; r . u, q . u
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      acc[p] = acc[N + p] = 0.0;
+      if (skip[p]) continue;
+      const long o = (long)p * n;
+      int k0, k1;
+      own_range(scnt[p], b, G, k0, k1);
+      for (int k = k0 + t; k < k1; k += PF_THREADS) {
+        const int i = __ldcg(w.idx + o + k);
+        int nb[3][2];
+        pf_stencil(g, i, nb);
+        const double uk = w.p[o + k];
+        double q = w.D[o + i] * uk;
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+          if (ax >= g.dim) break;
+          const double* wa = w.w + ax * nn + o;
+          const int jm = nb[ax][0], jp = nb[ax][1];
+          // a neighbour off the list shares no coupled face (weight 0)
+          const int kp = jp >= 0 ? __ldcg(w.pos + o + jp) : -1;
+          const int km = jm >= 0 ? __ldcg(w.pos + o + jm) : -1;
+          if (kp >= 0) q = fma(-wa[i], __ldcg(w.p + o + kp), q);
+          if (km >= 0) q = fma(-wa[jm], __ldcg(w.p + o + km), q);
+        }
+        w.q[o + k] = q;
+        acc[p] = fma(w.r[o + k], uk, acc[p]);
+        acc[N + p] = fma(q, uk, acc[N + p]);
+      }
+    }
+  };
+  double gam[N], alpha[N], beta[N], ref[N];
+  bool conv[N];
+  int it = 0;
+  if (ok) {
+    bool none[N];
+#pragma unroll
+    for (int p = 0; p < N; p++) none[p] = false;
+    product(none);
+    double v3[3 * N];
+#pragma unroll
+    for (int j = 0; j < 3 * N; j++) v3[j] = acc[j];
+    block_sum_small<3 * N>(v3, w.part + PART_CG1 + (long)b * 16);
+    ok = grid_sync(bar, err);
+  }
+  if (ok) {
+    sum_rows_small<3 * N>(w.part + PART_CG1, G, s_sum);
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      gam[p] = s_sum[p];
+      ref[p] = s_sum[2 * N + p];
+      alpha[p] = s_sum[N + p] > 0.0 ? gam[p] / s_sum[N + p] : 0.0;
+      beta[p] = 0.0;
+      conv[p] = !(gam[p] > tol2 * ref[p]) || !(alpha[p] > 0.0);
+    }
+    while (it < maxit) {
+      bool all = true;
+#pragma unroll
+      for (int p = 0; p < N; p++) all = all && conv[p];
+      if (all) break;
+#pragma unroll
+      for (int p = 0; p < N; p++) {
+        if (conv[p]) continue;
+        const long o = (long)p * n;
+        int k0, k1;
+        own_range(scnt[p], b, G, k0, k1);
+        for (int k = k0 + t; k < k1; k += PF_THREADS) {
+          const double uk = w.p[o + k], qk = w.q[o + k];
+          // (the first directions are u and K u themselves)
+          const double pk = it == 0 ? uk : fma(beta[p], w.pd[o + k], uk);
+          const double sk = it == 0 ? qk : fma(beta[p], w.sd[o + k], qk);
+          w.pd[o + k] = pk;
+          w.sd[o + k] = sk;
+          w.xk[o + k] = fma(alpha[p], pk, w.xk[o + k]);
+          const double rk = fma(-alpha[p], sk, w.r[o + k]);
+          w.r[o + k] = rk;
+          w.p[o + k] = rk * w.Dinv[o + __ldcg(w.idx + o + k)];
+        }
+      }
+      if (!(ok = grid_sync(bar, err))) break;
+      product(conv);
+      double v2[2 * N];
+#pragma unroll
+      for (int j = 0; j < 2 * N; j++) v2[j] = acc[j];
+      block_sum_small<2 * N>(v2, w.part + PART_CG1 + (long)b * 16);
+      if (!(ok = grid_sync(bar, err))) break;
+      sum_rows_small<2 * N>(w.part + PART_CG1, G, s_sum);
+#pragma unroll
+      for (int p = 0; p < N; p++) {
+        if (conv[p]) continue;
+        const double gn = s_sum[p], dn = s_sum[N + p];
+        const double bt = gam[p] > 0.0 ? gn / gam[p] : 0.0;
+        const double den = dn - bt * gn / alpha[p];
+        beta[p] = bt;
+        gam[p] = gn;
+        alpha[p] = den > 0.0 ? gn / den : 0.0;
+        conv[p] = !(gn > tol2 * ref[p]) || !(alpha[p] > 0.0);
+      }
+      it++;
+    }
+  }
+  if (ok) {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      const long o = (long)p * n;
+      int k0, k1;
+      own_range(scnt[p], b, G, k0, k1);
+      for (int k = k0 + t; k < k1; k += PF_THREADS) w.x[o + __ldcg(w.idx + o + k)] = w.xk[o + k];
+      if (!warm)
+        for (int i = c0 + t; i < c1; i += PF_THREADS)
+          if (w.pos[o + i] < 0) w.x[o + i] = 0.0;
+    }
+  }
+  if (b == 0 && t == 0 && ok) {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      w.scal[16 + p] = ref[p];
+      w.scal[24 + p] = gam[p];
+      w.flag[1 + p] = conv[p] ? 1 : 0;
+    }
+    w.flag[11] = it;
+  }
+}
+
 // Eq. 4 by conjugate gradients preconditioned with D, in one launch:
 //  1. list: each block counts the cells of its chunk of the grid that carry
 //     a label; after a barrier it knows its offset, and it writes the list
 //     (idx: cell of each unknown, in cell order) and its inverse (pos, -1
 //     for cells off the list);
 //  2. start: b = -(R - D s_k) (s_k the region's sum R / sum D), x0 = 0 or
-//     (warm) the x given, r0 = b - K x0, and the sums r0 . r0/D, b . b/D;
-//  3. iterations until every phase has r.r/D <= tol2 b.b/D or maxit: the
-//     direction p = r/D + beta p, q = K p with p . q, alpha, x and r, the
-//     new r.r/D and beta, a barrier after each step that the next one needs
-//     (the matrix-vector product reads neighbours' p);
+//     (warm) the x given, r0 = b - K x0, u0 = r0/D, and the sums;
+//  3. iterations until every phase has r.r/D <= tol2 b.b/D or maxit
+//     (cg_one: state in registers; cg_mem: in memory);
 //  4. x written back to the grid (cold start: 0 off the list).
 // A phase whose alpha is not positive stops where it is.
 template <int N>
@@ -760,152 +897,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_qmap_cg(PfGeom g, PfWork w, doub
     }
   }
 
-  // 2. start
-  double acc[N], ref[N];
-#pragma unroll
-  for (int p = 0; p < N; p++) {
-    acc[p] = ref[p] = 0.0;
-    const long o = (long)p * n;
-    int k0, k1;
-    own_range(scnt[p], b, G, k0, k1);
-    for (int k = k0 + t; k < k1; k += PF_THREADS) {
-      const int i = __ldcg(w.idx + o + k);
-      const int l = w.lab[o + i];
-      const double s = w.sumR[o + l] / w.sumD[o + l];
-      const double bv = -(w.R[o + i] - w.D[o + i] * s);
-      double x0 = 0.0, rr = bv;
-      if (warm) {
-        int nb[3][2];
-        pf_stencil(g, i, nb);
-        x0 = w.x[o + i];
-        rr = bv - k_apply<N>(g, nb, i, o, nn, w.w, w.D, w.x);
-      }
-      w.xk[o + k] = x0;
-      w.r[o + k] = rr;
-      const double di = w.Dinv[o + i];
-      acc[p] += rr * (rr * di);
-      ref[p] += bv * (bv * di);
-    }
-  }
-  block_sum_small<N>(acc, w.part + PART_RZ + (long)b * 8);
-  block_sum_small<N>(ref, w.part + PART_REF + (long)b * 8);
-  if (!grid_sync(bar, err)) return;
-  sum_partials_block<N>(w.part, PART_RZ, G, s_rz);
-  sum_partials_block<N>(w.part, PART_REF, G, s_ref);
-  bool conv[N];
-  double rz[N], refv[N], beta[N], alpha[N];
-#pragma unroll
-  for (int p = 0; p < N; p++) {
-    rz[p] = s_rz[p];
-    refv[p] = s_ref[p];
-    conv[p] = !(rz[p] > tol2 * refv[p]);
-    beta[p] = 0.0;
-  }
-
-  // 3. iterations
-  int it = 0;
-  bool ok = true;
-  while (it < maxit) {
-    bool all = true;
-#pragma unroll
-    for (int p = 0; p < N; p++) all = all && conv[p];
-    if (all) break;
-#pragma unroll
-    for (int p = 0; p < N; p++) {
-      if (conv[p]) continue;
-      const long o = (long)p * n;
-      int k0, k1;
-      own_range(scnt[p], b, G, k0, k1);
-      for (int k = k0 + t; k < k1; k += PF_THREADS) {
-        const int i = __ldcg(w.idx + o + k);
-        const double z = w.r[o + k] * w.Dinv[o + i];
-        w.p[o + k] = it == 0 ? z : fma(beta[p], w.p[o + k], z);
-      }
-    }
-    if (!(ok = grid_sync(bar, err))) break;
-#pragma unroll
-    for (int p = 0; p < N; p++) {
-      acc[p] = 0.0;
-      if (conv[p]) continue;
-      const long o = (long)p * n;
-      int k0, k1;
-      own_range(scnt[p], b, G, k0, k1);
-      for (int k = k0 + t; k < k1; k += PF_THREADS) {
-        const int i = __ldcg(w.idx + o + k);
-        int nb[3][2];
-        pf_stencil(g, i, nb);
-        const double pk = w.p[o + k];
-        double s = w.D[o + i] * pk;
-#pragma unroll
-        for (int ax = 0; ax < 3; ax++) {
-          if (ax >= g.dim) break;
-          const double* wa = w.w + ax * nn + o;
-          const int jm = nb[ax][0], jp = nb[ax][1];
-          // a neighbour off the list shares no coupled face (weight 0)
-          const int kp = jp >= 0 ? __ldcg(w.pos + o + jp) : -1;
-          const int km = jm >= 0 ? __ldcg(w.pos + o + jm) : -1;
-          if (kp >= 0) s = fma(-wa[i], __ldcg(w.p + o + kp), s);
-          if (km >= 0) s = fma(-wa[jm], __ldcg(w.p + o + km), s);
-        }
-        w.q[o + k] = s;
-        acc[p] = fma(pk, s, acc[p]);
-      }
-    }
-    block_sum_small<N>(acc, w.part + PART_PQ + (long)b * 8);
-    if (!(ok = grid_sync(bar, err))) break;
-    sum_partials_block<N>(w.part, PART_PQ, G, s_new);
-#pragma unroll
-    for (int p = 0; p < N; p++) {
-      alpha[p] = (!conv[p] && s_new[p] > 0.0) ? rz[p] / s_new[p] : 0.0;
-      acc[p] = 0.0;
-      if (conv[p]) continue;
-      const long o = (long)p * n;
-      int k0, k1;
-      own_range(scnt[p], b, G, k0, k1);
-      for (int k = k0 + t; k < k1; k += PF_THREADS) {
-        const int i = __ldcg(w.idx + o + k);
-        w.xk[o + k] = fma(alpha[p], w.p[o + k], w.xk[o + k]);
-        const double rk = fma(-alpha[p], w.q[o + k], w.r[o + k]);
-        w.r[o + k] = rk;
-        acc[p] = fma(rk, rk * w.Dinv[o + i], acc[p]);
-      }
-    }
-    block_sum_small<N>(acc, w.part + PART_RZ + (long)b * 8);
-    if (!(ok = grid_sync(bar, err))) break;
-    sum_partials_block<N>(w.part, PART_RZ, G, s_new);
-#pragma unroll
-    for (int p = 0; p < N; p++) {
-      if (conv[p]) continue;
-      const double rn = s_new[p];
-      beta[p] = rz[p] > 0.0 ? rn / rz[p] : 0.0;
-      rz[p] = rn;
-      conv[p] = !(rn > tol2 * refv[p]) || !(alpha[p] > 0.0);
-    }
-    it++;
-  }
-
-  // 4. x back to the grid
-  if (ok) {
-#pragma unroll
-    for (int p = 0; p < N; p++) {
-      const long o = (long)p * n;
-      int k0, k1;
-      own_range(scnt[p], b, G, k0, k1);
-      for (int k = k0 + t; k < k1; k += PF_THREADS) w.x[o + __ldcg(w.idx + o + k)] = w.xk[o + k];
-      if (!warm)
-        for (int i = c0 + t; i < c1; i += PF_THREADS)
-          if (w.pos[o + i] < 0) w.x[o + i] = 0.0;
-    }
-  }
-  if (b == 0 && t == 0) {
-#pragma unroll
-    for (int p = 0; p < N; p++) {
-      w.scal[16 + p] = refv[p];
-      w.scal[24 + p] = rz[p];
-      w.flag[1 + p] = conv[p] ? 1 : 0;
-    }
-    w.flag[11] = it;
-  }
+  cg_mem<N>(g, w, tol2, warm, maxit, scnt, c0, c1, bar, err);
 }
 
 // The grid barrier alone, for its test: rounds barriers, except that block

@@ -67,9 +67,11 @@ struct PfWork {
   double* sumD;     //                                 sum D
   double* x;        // Q on the grid (the conjugate gradients' start and result)
   double* r;        // conjugate gradients on the listed unknowns: residual,
-  double* p;        //   direction,
-  double* q;        //   K p,
-  double* xk;       //   iterate (position k of phase p at p ncell + k)
+  double* p;        //   u = r/D (read by the neighbours),
+  double* q;        //   K u,
+  double* xk;       //   iterate (position k of phase p at p ncell + k),
+  double* pd;       //   direction and
+  double* sd;       //   its product (the in-memory iteration)
   int* idx;         // the list: cell of unknown k of phase p
   int* pos;         // its inverse: position of cell i, -1 off the list
   double* part;     // reduction partials (offsets in wenoc_pf.cu)

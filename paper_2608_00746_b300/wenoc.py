@@ -80,6 +80,7 @@ _SIGS = {
     "wc_pf_step": (ctypes.c_int, [_VP, _VP, ctypes.c_double, _VP]),
     "wc_step": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _VP]),
+    "wc_pf_band": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int)]),
     "wc_pf_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_double)]),
     "wc_pf_q": (_VP, [_VP]),
@@ -393,6 +394,14 @@ class Grid:
         self._check(lib().wc_pf_stats(self.h, ctypes.byref(it), ctypes.byref(lr),
                                       ctypes.byref(res)))
         return it.value, lr.value, res.value
+
+    def pf_band(self):
+        """(unknowns per phase, unknowns a thread kept in registers) of the
+        last Q-map."""
+        arr = (ctypes.c_int * 8)()
+        pt = ctypes.c_int(0)
+        self._check(lib().wc_pf_band(self.h, arr, ctypes.byref(pt)))
+        return [arr[p] for p in range(self.N)], pt.value
 
     # learned weights ------------------------------------------------------
     def set_mlp(self, params, tau=1e-4, counters=None):
