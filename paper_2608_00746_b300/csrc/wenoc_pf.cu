@@ -673,6 +673,8 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
     }
   }
   bool ok = grid_sync(bar, err);
+  // the unknowns of a thread in batches of MB, their loads issued together
+  constexpr int MB = 4;
   auto product = [&](const bool* skip) {  // q = K u; r . u, q . u
 #pragma unroll
     for (int p = 0; p < N; p++) {
@@ -681,26 +683,62 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
       const long o = (long)p * n;
       int k0, k1;
       own_range(scnt[p], b, G, k0, k1);
-      for (int k = k0 + t; k < k1; k += PF_THREADS) {
-        const int i = __ldcg(w.idx + o + k);
-        int nb[3][2];
-        pf_stencil(g, i, nb);
-        const double uk = w.p[o + k];
-        double q = w.D[o + i] * uk;
+      for (int kb = k0 + t; kb < k1; kb += MB * PF_THREADS) {
+        int ii[MB], kn[MB][6];
+        double wt[MB][6], un[MB][6], uk[MB], dk[MB], rk[MB];
 #pragma unroll
-        for (int ax = 0; ax < 3; ax++) {
-          if (ax >= g.dim) break;
-          const double* wa = w.w + ax * nn + o;
-          const int jm = nb[ax][0], jp = nb[ax][1];
-          // a neighbour off the list shares no coupled face (weight 0)
-          const int kp = jp >= 0 ? __ldcg(w.pos + o + jp) : -1;
-          const int km = jm >= 0 ? __ldcg(w.pos + o + jm) : -1;
-          if (kp >= 0) q = fma(-wa[i], __ldcg(w.p + o + kp), q);
-          if (km >= 0) q = fma(-wa[jm], __ldcg(w.p + o + km), q);
+        for (int j = 0; j < MB; j++) {
+          const int k = kb + j * PF_THREADS;
+          ii[j] = k < k1 ? __ldcg(w.idx + o + k) : -1;
         }
-        w.q[o + k] = q;
-        acc[p] = fma(w.r[o + k], uk, acc[p]);
-        acc[N + p] = fma(q, uk, acc[N + p]);
+#pragma unroll
+        for (int j = 0; j < MB; j++) {
+          const int k = kb + j * PF_THREADS;
+#pragma unroll
+          for (int f = 0; f < 6; f++) {
+            kn[j][f] = -1;
+            wt[j][f] = 0.0;
+          }
+          uk[j] = dk[j] = rk[j] = 0.0;
+          if (ii[j] < 0) continue;
+          const int i = ii[j];
+          int nb[3][2];
+          pf_stencil(g, i, nb);
+#pragma unroll
+          for (int ax = 0; ax < 3; ax++) {
+            if (ax >= g.dim) break;
+            const double* wa = w.w + ax * nn + o;
+            const int jm = nb[ax][0], jp = nb[ax][1];
+            // a neighbour off the list shares no coupled face (weight 0)
+            if (jp >= 0) {
+              kn[j][2 * ax] = __ldcg(w.pos + o + jp);
+              wt[j][2 * ax] = wa[i];
+            }
+            if (jm >= 0) {
+              kn[j][2 * ax + 1] = __ldcg(w.pos + o + jm);
+              wt[j][2 * ax + 1] = wa[jm];
+            }
+          }
+          uk[j] = w.p[o + k];
+          dk[j] = w.D[o + i];
+          rk[j] = w.r[o + k];
+        }
+#pragma unroll
+        for (int j = 0; j < MB; j++)
+#pragma unroll
+          for (int f = 0; f < 6; f++)
+            un[j][f] = kn[j][f] >= 0 ? __ldcg(w.p + o + kn[j][f]) : 0.0;
+#pragma unroll
+        for (int j = 0; j < MB; j++) {
+          if (ii[j] < 0) continue;
+          double q = dk[j] * uk[j];
+#pragma unroll
+          for (int f = 0; f < 6; f++)
+            if (kn[j][f] >= 0) q = fma(-wt[j][f], un[j][f], q);
+          w.q[o + kb + j * PF_THREADS] = q;
+          acc[p] = fma(rk[j], uk[j], acc[p]);
+          acc[N + p] = fma(q, uk[j], acc[N + p]);
+        }
       }
     }
   };
@@ -739,17 +777,28 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
         const long o = (long)p * n;
         int k0, k1;
         own_range(scnt[p], b, G, k0, k1);
-        for (int k = k0 + t; k < k1; k += PF_THREADS) {
-          const double uk = w.p[o + k], qk = w.q[o + k];
-          // (the first directions are u and K u themselves)
-          const double pk = it == 0 ? uk : fma(beta[p], w.pd[o + k], uk);
-          const double sk = it == 0 ? qk : fma(beta[p], w.sd[o + k], qk);
-          w.pd[o + k] = pk;
-          w.sd[o + k] = sk;
-          w.xk[o + k] = fma(alpha[p], pk, w.xk[o + k]);
-          const double rk = fma(-alpha[p], sk, w.r[o + k]);
-          w.r[o + k] = rk;
-          w.p[o + k] = rk * w.Dinv[o + __ldcg(w.idx + o + k)];
+        for (int kb = k0 + t; kb < k1; kb += MB * PF_THREADS) {
+          double di[MB];
+#pragma unroll
+          for (int j = 0; j < MB; j++) {
+            const int k = kb + j * PF_THREADS;
+            di[j] = k < k1 ? w.Dinv[o + __ldcg(w.idx + o + k)] : 0.0;
+          }
+#pragma unroll
+          for (int j = 0; j < MB; j++) {
+            const int k = kb + j * PF_THREADS;
+            if (k >= k1) continue;
+            const double uk = w.p[o + k], qk = w.q[o + k];
+            // (the first directions are u and K u themselves)
+            const double pk = it == 0 ? uk : fma(beta[p], w.pd[o + k], uk);
+            const double sk = it == 0 ? qk : fma(beta[p], w.sd[o + k], qk);
+            w.pd[o + k] = pk;
+            w.sd[o + k] = sk;
+            w.xk[o + k] = fma(alpha[p], pk, w.xk[o + k]);
+            const double rk = fma(-alpha[p], sk, w.r[o + k]);
+            w.r[o + k] = rk;
+            w.p[o + k] = rk * di[j];
+          }
         }
       }
       if (!(ok = grid_sync(bar, err))) break;
