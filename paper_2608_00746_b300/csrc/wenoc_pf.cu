@@ -397,7 +397,8 @@ __device__ __forceinline__ void sum_rows_small(const double* part, int count, do
 #pragma unroll
       for (int j = 0; j < M; j++) v[j] += __ldcg(part + (long)row * 16 + j);
   }
-  block_sum_small<M>(v, out);
+  // warps whose threads hold no row hold zeros
+  block_sum_small<M>(v, out, (int)(threadIdx.x & ~31u) >= count);
 }
 
 // Grid barrier of the cooperative launch (every block resident): an arrival
