@@ -348,26 +348,45 @@ constexpr long PART_TOTAL = PART_CG1 + (long)PF_CG_BLOCKS * 16;
 // however few lanes are active, so the reductions here are written to issue
 // few FP64 warp instructions.
 //
-// Block sum of N values per thread into out[0..N-1] (fixed order): a
-// shuffle tree in each warp, then the eight warp sums by a shuffle tree in
-// warp 0.  out is written by thread 0 and read by the block after the
-// closing barrier.
+// Block sum of N values per thread into out[0..N-1] (fixed order).  In each
+// warp a reduce-scatter: with the values padded to P = 2^k >= N, the lanes
+// whose bit 16 is set keep the upper half, the others the lower half, each
+// adding its partner's copy; then bit 8 halves again, and so on until a
+// lane holds one value, which the remaining offsets sum as a butterfly.
+// That is P - 1 + 5 - k FP64 adds a warp instead of 5 N (a warp's FP64
+// instruction costs the same however few lanes it uses).  Lane v 32/P then
+// holds the warp's sum of value v; warp 0 adds the eight warp sums.  out is
+// written by thread 0 and read by the block after the closing barrier.
 template <int N>
 __device__ __forceinline__ void block_sum_small(const double (&v)[N], double* out,
                                                 bool warp_zero = false) {
   constexpr int W = PF_THREADS / 32;
+  constexpr int P = N <= 1 ? 1 : (N <= 2 ? 2 : (N <= 4 ? 4 : (N <= 8 ? 8 : 16)));
   __shared__ double sm[N][W];
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  // (warp_zero: the caller knows every value of this warp is +0; its sum
-  // is +0 without the shuffles)
+  // (warp_zero: the caller knows every value of this warp is +0; its sums
+  // are +0 without the shuffles)
+  if (warp_zero) {
+    if (lane < N) sm[lane][wid] = 0.0;
+  } else {
+    double x[P];
 #pragma unroll
-  for (int p = 0; p < N; p++) {
-    double x = v[p];
-    if (!warp_zero) {
+    for (int j = 0; j < P; j++) x[j] = j < N ? v[j] : 0.0;
+    int idx = 0;  // index of the first value this lane keeps
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    for (int c = P, o = 16; c > 1; c >>= 1, o >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < c / 2; i++) {
+        const double mine = up ? x[c / 2 + i] : x[i];
+        const double other = up ? x[i] : x[c / 2 + i];
+        x[i] = mine + __shfl_xor_sync(0xffffffffu, other, o);
+      }
+      if (up) idx += c / 2;
     }
-    if (lane == 0) sm[p][wid] = warp_zero ? 0.0 : x;
+#pragma unroll
+    for (int o = 16 / P; o > 0; o >>= 1) x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
+    if (lane % (32 / P) == 0 && idx < N) sm[idx][wid] = x[0];
   }
   __syncthreads();
   if (wid == 0) {
