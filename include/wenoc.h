@@ -184,9 +184,10 @@ wc_status wc_rhs_pf(wc_grid *g, const double *U_dev, const double *Q_dev, double
  * the rest is solved by conjugate gradients preconditioned with D; only the
  * face gradients of coupled faces are used (wc_rhs_pf). */
 
-/* Device scratch of the mechanism: thirteen [N][ncell] FP64 fields, one
- * [N][ncell] int32 field and about 0.3 MB of reduction partials; grids up to
- * 2^30 cells (WC_ERR_UNSUPPORTED beyond). */
+/* Device scratch of the mechanism: sixteen [N][ncell] FP64 fields, three
+ * [N][ncell] int32 fields (region labels, the list of unknowns and its
+ * inverse) and about 0.3 MB of reduction partials; grids up to 2^30 cells
+ * (WC_ERR_UNSUPPORTED beyond). */
 size_t wc_pf_workspace_bytes(const wc_grid *g);
 /* Binds that scratch (256-byte aligned, at least wc_pf_workspace_bytes). */
 wc_status wc_set_pf_workspace(wc_grid *g, void *ws_dev, size_t bytes);
