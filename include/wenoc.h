@@ -186,7 +186,7 @@ wc_status wc_rhs_pf(wc_grid *g, const double *U_dev, const double *Q_dev, double
 
 /* Device scratch of the mechanism: sixteen [N][ncell] FP64 fields, three
  * [N][ncell] int32 fields (region labels, the list of unknowns and its
- * inverse) and about 0.3 MB of reduction partials; grids up to 2^30 cells
+ * inverse) and about 0.4 MB of reduction partials; grids up to 2^30 cells
  * (WC_ERR_UNSUPPORTED beyond). */
 size_t wc_pf_workspace_bytes(const wc_grid *g);
 /* Binds that scratch (256-byte aligned, at least wc_pf_workspace_bytes). */
