@@ -68,8 +68,10 @@ def parse():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the scheme variants (WENO-CL, WENO-W, WENO-JS, Kapila)")
     ap.add_argument("--profile", action="store_true",
-                    help="only the FP64 timed steps (a short run for profilers); prints the "
-                         "per-launch sweep time")
+                    help="only the timed steps of one precision (a short run for profilers); "
+                         "prints the per-launch sweep time")
+    ap.add_argument("--profile-precision", default="fp64", choices=["fp64", "mixed"],
+                    help="precision of the --profile run")
     ap.add_argument("--profile-pf", action="store_true",
                     help="only full time steps with the Phase-Field mechanism on the headline "
                          "workload (--steps of them after --warmup), for profilers")
@@ -357,9 +359,10 @@ def run_ours(args):
         return 0
 
     if args.profile:
-        g, U = make_grid("fp64")
+        g, U = make_grid(args.profile_precision)
         ms, sw = timed_steps(g, args.steps, args.warmup)
-        print(json.dumps({"profile": True, "ms_per_step": ms, "sweep_ms_per_launch": sw,
+        print(json.dumps({"profile": True, "precision": args.profile_precision,
+                          "ms_per_step": ms, "sweep_ms_per_launch": sw,
                           "steps": args.steps, "warmup": args.warmup}), flush=True)
         return 0
 
