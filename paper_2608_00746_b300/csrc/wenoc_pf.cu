@@ -357,10 +357,10 @@ constexpr long PART_TOTAL = PART_CG1 + (long)PF_CG_BLOCKS * 16;
 // instruction costs the same however few lanes it uses).  Lane v 32/P then
 // holds the warp's sum of value v; warp 0 adds the eight warp sums.  out is
 // written by thread 0 and read by the block after the closing barrier.
-template <int N>
+template <int N, int BT = PF_THREADS>
 __device__ __forceinline__ void block_sum_small(const double (&v)[N], double* out,
                                                 bool warp_zero = false) {
-  constexpr int W = PF_THREADS / 32;
+  constexpr int W = BT / 32;
   constexpr int P = N <= 1 ? 1 : (N <= 2 ? 2 : (N <= 4 ? 4 : (N <= 8 ? 8 : 16)));
   __shared__ double sm[N][W];
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -404,20 +404,20 @@ __device__ __forceinline__ void block_sum_small(const double (&v)[N], double* ou
 // Sums of count <= 4 PF_THREADS partial rows (16 doubles, M <= 16 used) by
 // the whole block in a fixed order: rows t, t + 256, ... to thread t, then
 // block_sum_small.
-template <int M>
+template <int M, int BT = PF_THREADS>
 __device__ __forceinline__ void sum_rows_small(const double* part, int count, double* out) {
   double v[M];
 #pragma unroll
   for (int j = 0; j < M; j++) v[j] = 0.0;
 #pragma unroll
   for (int rrow = 0; rrow < 4; rrow++) {
-    const int row = (int)threadIdx.x + rrow * PF_THREADS;
+    const int row = (int)threadIdx.x + rrow * BT;
     if (row < count)
 #pragma unroll
       for (int j = 0; j < M; j++) v[j] += __ldcg(part + (long)row * 16 + j);
   }
   // warps whose threads hold no row hold zeros
-  block_sum_small<M>(v, out, (int)(threadIdx.x & ~31u) >= count);
+  block_sum_small<M, BT>(v, out, (int)(threadIdx.x & ~31u) >= count);
 }
 
 // Grid barrier of the cooperative launch (every block resident): an arrival
@@ -656,7 +656,7 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
 // (own_range), its threads the same unknowns every iteration; x, r, the
 // direction p (pd), s, w = K u (q) and the shared copy of u (p) in the
 // workspace's list layout (p ncell + k).
-template <int N>
+template <int N, int BT, int MB>
 __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double tol2, int warm,
                                        int maxit, const int* scnt, int c0, int c1, unsigned* bar,
                                        int* err) {
@@ -673,7 +673,7 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
     const long o = (long)p * n;
     int k0, k1;
     own_range(scnt[p], b, G, k0, k1);
-    for (int k = k0 + t; k < k1; k += PF_THREADS) {
+    for (int k = k0 + t; k < k1; k += BT) {
       const int i = __ldcg(w.idx + o + k);
       const int l = w.lab[o + i];
       const double sk = w.sumR[o + l] / w.sumD[o + l];
@@ -694,7 +694,6 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
   }
   bool ok = grid_sync(bar, err);
   // the unknowns of a thread in batches of MB, their loads issued together
-  constexpr int MB = 4;
   auto product = [&](const bool* skip) {  // q = K u; r . u, q . u
 #pragma unroll
     for (int p = 0; p < N; p++) {
@@ -703,17 +702,17 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
       const long o = (long)p * n;
       int k0, k1;
       own_range(scnt[p], b, G, k0, k1);
-      for (int kb = k0 + t; kb < k1; kb += MB * PF_THREADS) {
+      for (int kb = k0 + t; kb < k1; kb += MB * BT) {
         int ii[MB], kn[MB][6];
         double wt[MB][6], un[MB][6], uk[MB], dk[MB], rk[MB];
 #pragma unroll
         for (int j = 0; j < MB; j++) {
-          const int k = kb + j * PF_THREADS;
+          const int k = kb + j * BT;
           ii[j] = k < k1 ? __ldcg(w.idx + o + k) : -1;
         }
 #pragma unroll
         for (int j = 0; j < MB; j++) {
-          const int k = kb + j * PF_THREADS;
+          const int k = kb + j * BT;
 #pragma unroll
           for (int f = 0; f < 6; f++) {
             kn[j][f] = -1;
@@ -755,7 +754,7 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
 #pragma unroll
           for (int f = 0; f < 6; f++)
             if (kn[j][f] >= 0) q = fma(-wt[j][f], un[j][f], q);
-          w.q[o + kb + j * PF_THREADS] = q;
+          w.q[o + kb + j * BT] = q;
           acc[p] = fma(rk[j], uk[j], acc[p]);
           acc[N + p] = fma(q, uk[j], acc[N + p]);
         }
@@ -773,11 +772,11 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
     double v3[3 * N];
 #pragma unroll
     for (int j = 0; j < 3 * N; j++) v3[j] = acc[j];
-    block_sum_small<3 * N>(v3, w.part + PART_CG1 + (long)b * 16);
+    block_sum_small<3 * N, BT>(v3, w.part + PART_CG1 + (long)b * 16);
     ok = grid_sync(bar, err);
   }
   if (ok) {
-    sum_rows_small<3 * N>(w.part + PART_CG1, G, s_sum);
+    sum_rows_small<3 * N, BT>(w.part + PART_CG1, G, s_sum);
 #pragma unroll
     for (int p = 0; p < N; p++) {
       gam[p] = s_sum[p];
@@ -797,16 +796,16 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
         const long o = (long)p * n;
         int k0, k1;
         own_range(scnt[p], b, G, k0, k1);
-        for (int kb = k0 + t; kb < k1; kb += MB * PF_THREADS) {
+        for (int kb = k0 + t; kb < k1; kb += MB * BT) {
           double di[MB];
 #pragma unroll
           for (int j = 0; j < MB; j++) {
-            const int k = kb + j * PF_THREADS;
+            const int k = kb + j * BT;
             di[j] = k < k1 ? w.Dinv[o + __ldcg(w.idx + o + k)] : 0.0;
           }
 #pragma unroll
           for (int j = 0; j < MB; j++) {
-            const int k = kb + j * PF_THREADS;
+            const int k = kb + j * BT;
             if (k >= k1) continue;
             const double uk = w.p[o + k], qk = w.q[o + k];
             // (the first directions are u and K u themselves)
@@ -826,9 +825,9 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
       double v2[2 * N];
 #pragma unroll
       for (int j = 0; j < 2 * N; j++) v2[j] = acc[j];
-      block_sum_small<2 * N>(v2, w.part + PART_CG1 + (long)b * 16);
+      block_sum_small<2 * N, BT>(v2, w.part + PART_CG1 + (long)b * 16);
       if (!(ok = grid_sync(bar, err))) break;
-      sum_rows_small<2 * N>(w.part + PART_CG1, G, s_sum);
+      sum_rows_small<2 * N, BT>(w.part + PART_CG1, G, s_sum);
 #pragma unroll
       for (int p = 0; p < N; p++) {
         if (conv[p]) continue;
@@ -849,9 +848,9 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
       const long o = (long)p * n;
       int k0, k1;
       own_range(scnt[p], b, G, k0, k1);
-      for (int k = k0 + t; k < k1; k += PF_THREADS) w.x[o + __ldcg(w.idx + o + k)] = w.xk[o + k];
+      for (int k = k0 + t; k < k1; k += BT) w.x[o + __ldcg(w.idx + o + k)] = w.xk[o + k];
       if (!warm)
-        for (int i = c0 + t; i < c1; i += PF_THREADS)
+        for (int i = c0 + t; i < c1; i += BT)
           if (w.pos[o + i] < 0) w.x[o + i] = 0.0;
     }
   }
@@ -966,7 +965,25 @@ __global__ void __launch_bounds__(PF_THREADS) k_qmap_cg(PfGeom g, PfWork w, doub
     }
   }
 
-  cg_mem<N>(g, w, tol2, warm, maxit, scnt, c0, c1, bar, err);
+  // larger bands: k_qmap_cg_mem, launched next with more threads an SM
+  if (b == 0 && t == 0) w.flag[18] = 1;
+}
+
+// The iteration on the lists in memory (bands of more than two unknowns a
+// thread of k_qmap_cg): a cooperative launch of one 1024-thread block per SM
+// after k_qmap_cg has listed the unknowns (their counts in w.flag[12 + p]),
+// about one unknown a thread, so that 32 warps an SM hide the loads'
+// latency.
+template <int N>
+__global__ void __launch_bounds__(1024, 1) k_qmap_cg_mem(PfGeom g, PfWork w, double tol2,
+                                                         int warm, int maxit) {
+  __shared__ int scnt[N];
+  if (threadIdx.x < N) scnt[threadIdx.x] = __ldcg(w.flag + 12 + threadIdx.x);
+  __syncthreads();
+  const int n = (int)g.ncell, G = (int)gridDim.x, b = (int)blockIdx.x;
+  const int cc = (n + G - 1) / G, c0 = min(n, b * cc), c1 = min(n, c0 + cc);
+  cg_mem<N, 1024, 1>(g, w, tol2, warm, maxit, scnt, c0, c1,
+                     reinterpret_cast<unsigned*>(w.flag + 8), w.flag + 10);
 }
 
 // The grid barrier alone, for its test: rounds barriers, except that block
@@ -1026,8 +1043,10 @@ cudaError_t pf_qmap_solve(const PfGeom& g, const PfWork& w, int warm, double tol
   const size_t bytes = sizeof(double) * (size_t)g.N * g.ncell;
   cudaError_t e = cudaMemsetAsync(w.sumR, 0, bytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.sumD, 0, bytes, st);
-  // the grid barrier's arrival count, generation and error word
+  // the grid barrier's arrival count, generation and error word; the
+  // deferral word
   if (e == cudaSuccess) e = cudaMemsetAsync(w.flag + 8, 0, 3 * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.flag + 18, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   const int nb = pf_grid(g.ncell);
   PF_DISPATCH(g.N, (k_qm_sums<N_><<<nb, PF_THREADS, 0, st>>>(g, w.R, w.D, w.lab, w.sumR, w.sumD)));
@@ -1048,6 +1067,17 @@ cudaError_t pf_qmap_solve(const PfGeom& g, const PfWork& w, int warm, double tol
   void* args[] = {&gg, &ww, &tol2, &warm, &maxit};
   PF_DISPATCH(g.N, (e = cudaLaunchCooperativeKernel((const void*)k_qmap_cg<N_>, dim3(blocks),
                                                     dim3(PF_THREADS), args, 0, st)));
+  if (e != cudaSuccess) return e;
+  // a band too large for the registers: the in-memory iteration follows
+  int deferred = 0, errw = 0;
+  e = cudaMemcpyAsync(&deferred, w.flag + 18, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&errw, w.flag + 10, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess || !deferred || errw) return e;
+  e = cudaMemsetAsync(w.flag + 8, 0, 3 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  PF_DISPATCH(g.N, (e = cudaLaunchCooperativeKernel((const void*)k_qmap_cg_mem<N_>,
+                                                    dim3(blocks), dim3(1024), args, 0, st)));
   return e;
 }
 

@@ -79,7 +79,8 @@ struct PfWork {
   int* flag;        // [64]: label change, converged per phase at 1+p, grid barrier at
                     //       8..10 (arrivals, generation, error), iterations at 11,
                     //       unknowns per phase at 12+p, unknowns a thread keeps in
-                    //       registers at 17 (0: the lists in memory)
+                    //       registers at 17 (0: the lists in memory), the
+                    //       in-memory iteration deferred to its own launch at 18
 };
 
 // Launchers (wenoc_pf.cu), all asynchronous on st.
@@ -95,9 +96,11 @@ cudaError_t pf_label_rounds(const PfGeom& g, const PfWork& w, int rounds, cudaSt
 // gradients on the listed unknowns to r.r/D <= tol2 b.b/D per phase or
 // maxit iterations, from 0 or (warm) the values in w.x; the result in w.x.
 // One cooperative launch (one block per SM, grid barriers with bounded
-// waits: w.flag[10] != 0 afterwards if a wait gave up); w.flag[1 + p] set
-// for the converged phases, w.flag[11] the iterations, w.scal[24 + p] the
-// last r.r/D and w.scal[16 + p] the reference b.b/D.
+// waits: w.flag[10] != 0 afterwards if a wait gave up), and for a band
+// larger than the registers take a second one after reading w.flag[18]
+// (this synchronizes st); w.flag[1 + p] set for the converged phases,
+// w.flag[11] the iterations, w.scal[24 + p] the last r.r/D and
+// w.scal[16 + p] the reference b.b/D.
 cudaError_t pf_qmap_solve(const PfGeom& g, const PfWork& w, int warm, double tol2, int maxit,
                           cudaStream_t st);
 // The Q-map's grid barrier on its own (words: 4 device ints, cleared here):
