@@ -970,19 +970,21 @@ __global__ void __launch_bounds__(PF_THREADS) k_qmap_cg(PfGeom g, PfWork w, doub
 }
 
 // The iteration on the lists in memory (bands of more than two unknowns a
-// thread of k_qmap_cg): a cooperative launch of one 1024-thread block per SM
-// after k_qmap_cg has listed the unknowns (their counts in w.flag[12 + p]),
-// about one unknown a thread, so that 32 warps an SM hide the loads'
-// latency.
+// thread of k_qmap_cg): a cooperative launch of one 256-thread block per SM
+// after k_qmap_cg has listed the unknowns (their counts in w.flag[12 + p]).
+// Its own launch keeps k_qmap_cg's register-resident paths free of this
+// code (they run faster so).  1024-thread blocks with one unknown a thread
+// measured slower (35 against 24 us an iteration: 32 warps' reductions and
+// register spills).
 template <int N>
-__global__ void __launch_bounds__(1024, 1) k_qmap_cg_mem(PfGeom g, PfWork w, double tol2,
-                                                         int warm, int maxit) {
+__global__ void __launch_bounds__(PF_THREADS, 1) k_qmap_cg_mem(PfGeom g, PfWork w, double tol2,
+                                                               int warm, int maxit) {
   __shared__ int scnt[N];
   if (threadIdx.x < N) scnt[threadIdx.x] = __ldcg(w.flag + 12 + threadIdx.x);
   __syncthreads();
   const int n = (int)g.ncell, G = (int)gridDim.x, b = (int)blockIdx.x;
   const int cc = (n + G - 1) / G, c0 = min(n, b * cc), c1 = min(n, c0 + cc);
-  cg_mem<N, 1024, 1>(g, w, tol2, warm, maxit, scnt, c0, c1,
+  cg_mem<N, PF_THREADS, 4>(g, w, tol2, warm, maxit, scnt, c0, c1,
                      reinterpret_cast<unsigned*>(w.flag + 8), w.flag + 10);
 }
 
@@ -1077,7 +1079,7 @@ cudaError_t pf_qmap_solve(const PfGeom& g, const PfWork& w, int warm, double tol
   e = cudaMemsetAsync(w.flag + 8, 0, 3 * sizeof(int), st);
   if (e != cudaSuccess) return e;
   PF_DISPATCH(g.N, (e = cudaLaunchCooperativeKernel((const void*)k_qmap_cg_mem<N_>,
-                                                    dim3(blocks), dim3(1024), args, 0, st)));
+                                                    dim3(blocks), dim3(PF_THREADS), args, 0, st)));
   return e;
 }
 
