@@ -872,8 +872,10 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
 //     for cells off the list);
 //  2. start: b = -(R - D s_k) (s_k the region's sum R / sum D), x0 = 0 or
 //     (warm) the x given, r0 = b - K x0, u0 = r0/D, and the sums;
-//  3. iterations until every phase has r.r/D <= tol2 b.b/D or maxit
-//     (cg_one: state in registers; cg_mem: in memory);
+//  3. iterations until every phase has r.r/D <= tol2 b.b/D or maxit, with
+//     the state in registers (cg_one) when every phase has at most one
+//     unknown a thread, or two with N <= 2; a larger band is left to
+//     k_qmap_cg_mem (w.flag[18] set), which iterates with it in memory;
 //  4. x written back to the grid (cold start: 0 off the list).
 // A phase whose alpha is not positive stops where it is.
 template <int N>
