@@ -210,3 +210,38 @@ def test_qmap_solution_on_a_fully_mixed_grid(gpu, n):
         A, _ = pf.qmap_operator(go, phi[p])
         AQ = A @ Q[p].reshape(-1)
         assert np.abs(AQ - Rp[p].reshape(-1)).max() <= 1e-8 * max(np.abs(R_or).max(), 1e-300)
+
+
+def test_qmap_solution_three_phases_in_memory(gpu):
+    """Three phases mixed on every cell of a 210^2 periodic grid (44,100
+    unknowns a phase: more than one a thread, and N = 3 keeps at most one
+    in registers), so the in-memory launch runs for N = 3; its Q solves the
+    oracle's discrete Eq. 4 for every phase."""
+    case = inputs.multiphase_advection_2d(n=210, nphase=3)
+    go, g = _grids(case)
+    V = case.V.copy()
+    ny, nx = V.shape[1:]
+    yy, xx = np.meshgrid((np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx, indexing="ij")
+    a1 = 0.35 + 0.2 * np.sin(2 * np.pi * xx) * np.sin(2 * np.pi * yy)
+    a2 = 0.3 + 0.15 * np.cos(2 * np.pi * xx)
+    a = [a1, a2, 1.0 - a1 - a2]
+    rho = [inputs.TABLE1[p][0] for p in range(3)]
+    for p in range(3):
+        V[p] = rho[p] * a[p]
+        V[6 + p] = a[p]
+    U = oracle.prim_to_cons(go, V)
+    Ud = to_dev(U)
+    g.bind(Ud).set_pf_workspace(Ud.device)
+    g.cac_rhs(Ud)
+    Q, iters, res = g.qmap(Ud, tol=1e-12, maxit=20000)
+    assert res <= 1e-12 and iters > 0
+    band, per_thread = g.pf_band()
+    assert band == [nx * ny] * 3 and per_thread == 0
+    Q = Q.cpu().numpy()
+    phi = pf.fractions(go, U)
+    R_or, _, _ = pf.cac_rhs(go, U)
+    _, Rp = pf.qmap(go, phi, R_or)
+    for p in range(go.N):
+        A, _ = pf.qmap_operator(go, phi[p])
+        AQ = A @ Q[p].reshape(-1)
+        assert np.abs(AQ - Rp[p].reshape(-1)).max() <= 1e-8 * max(np.abs(R_or).max(), 1e-300)
