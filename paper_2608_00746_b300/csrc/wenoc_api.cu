@@ -603,22 +603,6 @@ static wc_status qmap(wc_grid* g, const double* U, const double* R, double* Q, d
     e = cudaMemcpyAsync(g->pw.x, Q, fb, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = pf_qmap_setup(U, g->pg, g->pw, st);
   if (e != cudaSuccess) return cuda_fail(g, e, "qmap setup");
-  // label rounds until one changes nothing (at most ncell rounds: every
-  // changing round lowers some label)
-  const int LR = 8;
-  int rounds = 0;
-  for (;;) {
-    e = pf_label_rounds(g->pg, g->pw, LR, st);
-    int moved = 0;
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(&moved, g->pw.flag, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(g, e, "qmap labels");
-    rounds += LR;
-    if (!moved) break;
-    if (rounds > g->ncell + LR) return fail(g, WC_ERR_STATE, "qmap labels did not settle");
-  }
-  g->pf_label_rounds = rounds;
   e = pf_qmap_solve(g->pg, g->pw, warm, tol * tol, maxit, st);
   if (e != cudaSuccess) return cuda_fail(g, e, "qmap cg");
   const int N = g->d.nphase;
@@ -629,6 +613,8 @@ static wc_status qmap(wc_grid* g, const double* U, const double* R, double* Q, d
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(g, e, "qmap residual");
   if (flags[10]) return fail(g, WC_ERR_TIMEOUT, "qmap: a grid barrier wait gave up");
+  if (flags[24]) return fail(g, WC_ERR_STATE, "qmap labels did not settle");
+  g->pf_label_rounds = flags[23];
   if (Q != g->pw.x) {
     e = cudaMemcpyAsync(Q, g->pw.x, fb, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(g, e, "qmap result");

@@ -272,61 +272,6 @@ __device__ __forceinline__ double k_apply(const PfGeom& g, const int (&nb)[3][2]
   return s;
 }
 
-// One round of minimum-label propagation over coupled faces with pointer
-// jumping.  Labels only decrease and always name a cell of the same region,
-// so the rounds end (the host stops at a round without change) with every
-// cell of a region labelled by the region's smallest cell index.
-template <int N>
-__global__ void __launch_bounds__(PF_THREADS) k_qm_label(PfGeom g, const double* __restrict__ c,
-                                                         int* lab, int* flag) {
-  const int n = (int)g.ncell;
-  int changed = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int nb[3][2];
-    pf_stencil(g, i, nb);
-#pragma unroll
-    for (int p = 0; p < N; p++) {
-      int* lp = lab + (long)p * n;
-      const int li = __ldcg(lp + i);
-      if (li < 0) continue;
-      const double* cp = c + (long)p * n;
-      const double ci = cp[i];
-      int m = li;
-#pragma unroll
-      for (int ax = 0; ax < 3; ax++) {
-        if (ax >= g.dim) break;
-#pragma unroll
-        for (int s = 0; s < 2; s++) {
-          const int j = nb[ax][s];
-          if (j >= 0 && (ci > 0.0 || cp[j] > 0.0)) m = min(m, __ldcg(lp + j));
-        }
-      }
-      m = min(m, __ldcg(lp + m));
-      if (m < li) {
-        atomicMin(lp + i, m);
-        changed = 1;
-      }
-    }
-  }
-  if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(flag, 1);
-}
-
-template <int N>
-__global__ void __launch_bounds__(PF_THREADS) k_qm_sums(PfGeom g, const double* __restrict__ R,
-                                                        const double* __restrict__ D,
-                                                        const int* __restrict__ lab, double* sumR,
-                                                        double* sumD) {
-  const int n = (int)g.ncell;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int p = 0; p < N; p++) {
-      const int l = lab[(long)p * n + i];
-      if (l < 0) continue;
-      atomicAdd(sumR + (long)p * n + l, R[(long)p * n + i]);
-      atomicAdd(sumD + (long)p * n + l, D[(long)p * n + i]);
-    }
-  }
-}
 
 // The conjugate gradients of Eq. 4 run on the listed unknowns (the cells of
 // some region, in cell order per phase) in one cooperative launch of at
@@ -536,8 +481,8 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
         wg[e][2 * ax] = wa[jm];
       }
     }
-    const int l = w.lab[o + i];
-    const double sk = w.sumR[o + l] / w.sumD[o + l];
+    const int l = __ldcg(w.lab + o + i);
+    const double sk = __ldcg(w.sumR + o + l) / __ldcg(w.sumD + o + l);
     Dv[e] = w.D[o + i];
     Di[e] = w.Dinv[o + i];
     const double bv = -(w.R[o + i] - Dv[e] * sk);
@@ -675,8 +620,8 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
     own_range(scnt[p], b, G, k0, k1);
     for (int k = k0 + t; k < k1; k += BT) {
       const int i = __ldcg(w.idx + o + k);
-      const int l = w.lab[o + i];
-      const double sk = w.sumR[o + l] / w.sumD[o + l];
+      const int l = __ldcg(w.lab + o + i);
+      const double sk = __ldcg(w.sumR + o + l) / __ldcg(w.sumD + o + l);
       const double bv = -(w.R[o + i] - w.D[o + i] * sk);
       double x0 = 0.0, r0 = bv;
       if (warm) {
@@ -945,6 +890,87 @@ __global__ void __launch_bounds__(PF_THREADS) k_qmap_cg(PfGeom g, PfWork w, doub
     }
   }
   if (!grid_sync(bar, err)) return;
+
+  // 1b. region labels: rounds of minimum-label propagation over coupled
+  // faces with pointer jumping, on the listed cells, until a round changes
+  // nothing.  Labels only decrease and always name a listed cell of the
+  // same region, so the rounds end with every cell of a region labelled by
+  // the region's smallest cell index.  A round's change word is one of
+  // three: it was last read two barriers before and is cleared a round
+  // ahead by block 0, so every block reads the same value.
+  int rounds = 0;
+  for (;;) {
+    int* chg = w.flag + 20 + rounds % 3;
+    if (b == 0 && t == 0) w.flag[20 + (rounds + 1) % 3] = 0;
+    int changed = 0;
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      const long o = (long)p * n;
+      int* lp = w.lab + o;
+      const double* cp = w.c + o;
+      int k0, k1;
+      own_range(scnt[p], b, G, k0, k1);
+      for (int k = k0 + t; k < k1; k += PF_THREADS) {
+        const int i = __ldcg(w.idx + o + k);
+        const int li = __ldcg(lp + i);
+        const double ci = cp[i];
+        int nb[3][2];
+        pf_stencil(g, i, nb);
+        int m = li;
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+          if (ax >= g.dim) break;
+#pragma unroll
+          for (int sd = 0; sd < 2; sd++) {
+            const int j = nb[ax][sd];
+            if (j >= 0 && (ci > 0.0 || cp[j] > 0.0)) m = min(m, __ldcg(lp + j));
+          }
+        }
+        m = min(m, __ldcg(lp + m));
+        if (m < li) {
+          atomicMin(lp + i, m);
+          changed = 1;
+        }
+      }
+    }
+    if (__syncthreads_or(changed) && t == 0) atomicOr(chg, 1);
+    if (!grid_sync(bar, err)) return;
+    rounds++;
+    if (__ldcg(chg) == 0) break;
+    if (rounds > n + 1) {  // cannot happen: a changing round lowers a label
+      if (b == 0 && t == 0) w.flag[24] = 1;
+      return;
+    }
+  }
+  if (b == 0 && t == 0) w.flag[23] = rounds;
+  // 1c. region sums of R and D over the listed cells (FP64 atomics, so
+  // their rounding varies between runs); the labels are listed cells
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    const long o = (long)p * n;
+    int k0, k1;
+    own_range(scnt[p], b, G, k0, k1);
+    for (int k = k0 + t; k < k1; k += PF_THREADS) {
+      const int i = __ldcg(w.idx + o + k);
+      w.sumR[o + i] = 0.0;
+      w.sumD[o + i] = 0.0;
+    }
+  }
+  if (!grid_sync(bar, err)) return;
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    const long o = (long)p * n;
+    int k0, k1;
+    own_range(scnt[p], b, G, k0, k1);
+    for (int k = k0 + t; k < k1; k += PF_THREADS) {
+      const int i = __ldcg(w.idx + o + k);
+      const int l = __ldcg(w.lab + o + i);
+      atomicAdd(w.sumR + o + l, w.R[o + i]);
+      atomicAdd(w.sumD + o + l, w.D[o + i]);
+    }
+  }
+  if (!grid_sync(bar, err)) return;
+
   // unknowns a thread keeps in registers: one, two (N <= 2), else the
   // iteration on the lists in memory below
   int maxm = 0;
@@ -1033,27 +1059,14 @@ cudaError_t pf_qmap_setup(const double* U, const PfGeom& g, const PfWork& w, cud
   return cudaGetLastError();
 }
 
-cudaError_t pf_label_rounds(const PfGeom& g, const PfWork& w, int rounds, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(w.flag, 0, sizeof(int), st);
-  if (e != cudaSuccess) return e;
-  const int nb = pf_grid(g.ncell);
-  for (int k = 0; k < rounds; k++)
-    PF_DISPATCH(g.N, (k_qm_label<N_><<<nb, PF_THREADS, 0, st>>>(g, w.c, w.lab, w.flag)));
-  return cudaGetLastError();
-}
 
 cudaError_t pf_qmap_solve(const PfGeom& g, const PfWork& w, int warm, double tol2, int maxit,
                           cudaStream_t st) {
-  const size_t bytes = sizeof(double) * (size_t)g.N * g.ncell;
-  cudaError_t e = cudaMemsetAsync(w.sumR, 0, bytes, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(w.sumD, 0, bytes, st);
   // the grid barrier's arrival count, generation and error word; the
-  // deferral word
-  if (e == cudaSuccess) e = cudaMemsetAsync(w.flag + 8, 0, 3 * sizeof(int), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(w.flag + 18, 0, sizeof(int), st);
+  // deferral word; the labelling's change words, rounds and error word
+  cudaError_t e = cudaMemsetAsync(w.flag + 8, 0, 3 * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.flag + 18, 0, 7 * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  const int nb = pf_grid(g.ncell);
-  PF_DISPATCH(g.N, (k_qm_sums<N_><<<nb, PF_THREADS, 0, st>>>(g, w.R, w.D, w.lab, w.sumR, w.sumD)));
   // one block per SM, all resident (a cooperative launch fails otherwise);
   // the register-resident iteration takes up to 256 unknowns a block and
   // phase.  (Two blocks per SM, where registers allow, measured slower: 25

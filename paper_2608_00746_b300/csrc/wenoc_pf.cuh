@@ -76,11 +76,12 @@ struct PfWork {
   int* pos;         // its inverse: position of cell i, -1 off the list
   double* part;     // reduction partials (offsets in wenoc_pf.cu)
   double* scal;     // [64]: M, B[0..N-1] | b.b/D at 16+p | r.r/D at 24+p
-  int* flag;        // [64]: label change, converged per phase at 1+p, grid barrier at
+  int* flag;        // [64]: converged per phase at 1+p, grid barrier at
                     //       8..10 (arrivals, generation, error), iterations at 11,
                     //       unknowns per phase at 12+p, unknowns a thread keeps in
                     //       registers at 17 (0: the lists in memory), the
-                    //       in-memory iteration deferred to its own launch at 18
+                    //       in-memory iteration deferred to its own launch at 18,
+                    //       labelling: change words 20..22, rounds 23, error 24
 };
 
 // Launchers (wenoc_pf.cu), all asynchronous on st.
@@ -90,11 +91,11 @@ cudaError_t pf_cac(const double* U, const PfGeom& g, const PfWork& w, double vol
                    double M_in, cudaStream_t st);
 // Eq. 4: coefficients, coupling D, 1/D and initial labels.
 cudaError_t pf_qmap_setup(const double* U, const PfGeom& g, const PfWork& w, cudaStream_t st);
-// rounds of label propagation; w.flag[0] != 0 afterwards if any label moved.
-cudaError_t pf_label_rounds(const PfGeom& g, const PfWork& w, int rounds, cudaStream_t st);
-// Region sums, the consistent right-hand side b from R, and conjugate
-// gradients on the listed unknowns to r.r/D <= tol2 b.b/D per phase or
-// maxit iterations, from 0 or (warm) the values in w.x; the result in w.x.
+// The list of unknowns, region labels (rounds until one changes nothing:
+// w.flag[23] rounds, w.flag[24] != 0 if they did not settle), region sums,
+// the consistent right-hand side b from R, and conjugate gradients on the
+// listed unknowns to r.r/D <= tol2 b.b/D per phase or maxit iterations, from
+// 0 or (warm) the values in w.x; the result in w.x.
 // One cooperative launch (one block per SM, grid barriers with bounded
 // waits: w.flag[10] != 0 afterwards if a wait gave up), and for a band
 // larger than the registers take a second one after reading w.flag[18]
