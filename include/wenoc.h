@@ -205,11 +205,12 @@ wc_status wc_cac_rhs(wc_grid *g, const double *U_dev, double eta, double M, doub
  * from 0.  Conjugate gradients stop when every phase has sqrt(r.z / b.b/D)
  * <= tol (the D-weighted residual relative to the right-hand side b) or
  * after maxit iterations; *iters and *resid (may be null) report them.  The
- * iterations run on the list of cells that belong to a region (the
- * interface bands) in one cooperative launch of one block per SM, whose
- * blocks meet at grid barriers with bounded waits (WC_ERR_TIMEOUT if one
- * gave up).  Synchronizes stream (the region labelling and the result read
- * device flags).  The values of Q are fixed up to a constant per
+ * region labelling, the region sums and the iterations run on the list of
+ * cells that belong to a region (the interface bands) in one cooperative
+ * launch of one block per SM (a second one when the band is too large for
+ * registers), whose blocks meet at grid barriers with bounded waits
+ * (WC_ERR_TIMEOUT if one gave up).  Synchronizes stream (the choice of the
+ * second launch and the result read device flags).  The values of Q are fixed up to a constant per
  * region; the region sums use FP64 atomics, so Q varies at rounding level
  * between runs. */
 wc_status wc_qmap(wc_grid *g, const double *U_dev, const double *R_dev, double *Q_dev,
