@@ -245,3 +245,33 @@ def test_qmap_solution_three_phases_in_memory(gpu):
         A, _ = pf.qmap_operator(go, phi[p])
         AQ = A @ Q[p].reshape(-1)
         assert np.abs(AQ - Rp[p].reshape(-1)).max() <= 1e-8 * max(np.abs(R_or).max(), 1e-300)
+
+
+def test_qmap_and_full_step_without_an_interface(gpu):
+    """A grid holding one pure phase (fractions exactly 0 and 1, no cell
+    with phi (1 - phi) > 0): the band is empty, the Q-map does no
+    iteration and returns Q = 0 (cold) or keeps the Q given (warm), and a
+    full time step equals the hyperbolic step alone, bit for bit."""
+    case = inputs.two_phase_advection_2d(n=40)
+    go, g = _grids(case)
+    V = case.V.copy()
+    V[0], V[1], V[5], V[6] = 0.0, case.meta["rho"][1], 0.0, 1.0
+    U = oracle.prim_to_cons(go, V)
+    Ud = to_dev(U)
+    g.bind(Ud).set_pf_workspace(Ud.device)
+    g.cac_rhs(Ud)
+    Q, iters, res = g.qmap(Ud, tol=1e-12)
+    assert iters == 0 and g.pf_band() == ([0, 0], 1)
+    assert not Q.any()
+    Qw = torch.full_like(Q, 3.0)
+    _, iters, _ = g.qmap(Ud, Q=Qw, tol=1e-12, warm=True)
+    assert iters == 0 and bool((Qw == 3.0).all())
+    U2 = Ud.clone()
+    g2 = wenoc.Grid(case.shape, case.dx, case.gamma, case.pinf, case.D, flux=case.flux,
+                    bc=case.bc)
+    g2.bind(U2)
+    g.step(dt=case.meta["dt"])
+    g2.rk_step(dt=case.meta["dt"])
+    g.sync_status()
+    g2.sync_status()
+    assert torch.equal(Ud, U2)
