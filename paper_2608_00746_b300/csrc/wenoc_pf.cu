@@ -98,18 +98,34 @@ __global__ void __launch_bounds__(PF_THREADS) k_cac_reduce(const double* __restr
 
 // Pass 2 (one block): totals, M, the N x N system and its solution B.
 template <int N>
-__global__ void k_cac_solve(const double* part, double vol, double eta, double M_in, double* scal) {
+__global__ void __launch_bounds__(PF_THREADS) k_cac_solve(const double* part, double vol,
+                                                          double eta, double M_in, double* scal) {
   using L = CacLayout<N>;
-  __shared__ double tot[32];
-  const int t = threadIdx.x;
-  if (t < L::K) {
+  __shared__ double red[32][PF_THREADS / 32], tot[32];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  // the PF_BLOCKS partial rows summed in a fixed order: rows t, t + 256, ...
+  // by thread t, then a shuffle tree in each warp and the eight warp sums
+  // (value 31 is a maximum)
+  for (int j = 0; j < 32; j++) {
+    if (j >= L::K && j != 31) continue;
+    const bool mx = j == 31;
     double s = 0.0;
-    for (int b = 0; b < PF_BLOCKS; b++) s += part[(long)b * 32 + t];
+    for (int r = t; r < PF_BLOCKS; r += PF_THREADS) {
+      const double v = part[(long)r * 32 + j];
+      s = mx ? fmax(s, v) : s + v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, s, o);
+      s = mx ? fmax(s, y) : s + y;
+    }
+    if (lane == 0) red[j][wid] = s;
+  }
+  __syncthreads();
+  if (t < 32 && (t < L::K || t == 31)) {
+    double s = red[t][0];
+    for (int k = 1; k < PF_THREADS / 32; k++) s = t == 31 ? fmax(s, red[t][k]) : s + red[t][k];
     tot[t] = s;
-  } else if (t == 31) {
-    double m = 0.0;
-    for (int b = 0; b < PF_BLOCKS; b++) m = fmax(m, part[(long)b * 32 + 31]);
-    tot[31] = m;
   }
   __syncthreads();
   if (t != 0) return;
@@ -1047,7 +1063,8 @@ size_t pf_part_doubles() { return (size_t)PART_TOTAL; }
 cudaError_t pf_cac(const double* U, const PfGeom& g, const PfWork& w, double vol, double eta,
                    double M_in, cudaStream_t st) {
   PF_DISPATCH(g.N, (k_cac_reduce<N_><<<PF_BLOCKS, PF_THREADS, 0, st>>>(U, g, w.part + PART_CAC)));
-  PF_DISPATCH(g.N, (k_cac_solve<N_><<<1, 32, 0, st>>>(w.part + PART_CAC, vol, eta, M_in, w.scal)));
+  PF_DISPATCH(g.N, (k_cac_solve<N_><<<1, PF_THREADS, 0, st>>>(w.part + PART_CAC, vol, eta, M_in,
+                                                              w.scal)));
   PF_DISPATCH(g.N, (k_cac_rhs<N_><<<pf_grid(g.ncell), PF_THREADS, 0, st>>>(U, g, w.scal, eta, w.R)));
   return cudaGetLastError();
 }
