@@ -184,7 +184,7 @@ def qmap_operator(g: Grid, phi: np.ndarray):
         rows += [a, b, a, b]
         cols += [b, a, a, b]
         vals += [w, w, -w, -w]
-        on = cf > 0.0
+        on = w > 0.0   # the faces that carry weight in A (Eq. 4)
         adj_r += [a[on], b[on]]
         adj_c += [b[on], a[on]]
     A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),

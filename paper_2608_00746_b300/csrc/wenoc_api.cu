@@ -842,11 +842,17 @@ extern "C" wc_status wc_convert_f32(const double* x, float* f, double* back, lon
 // with the stage buffers, accumulator, rate and status words placed in the
 // given scratch area (same layout as the bound workspace), then restores the
 // grid's own bindings.  Returns the device address of the status word used.
+wc_status wc_internal_scratch_supported(wc_grid* g) {
+  if (g->d.precision == WC_PREC_LEARNED)
+    return fail(g, WC_ERR_UNSUPPORTED, "the fixed scratch holds no learned-weight buffer");
+  return WC_OK;
+}
+
 wc_status wc_internal_rk_with_scratch(wc_grid* g, double* U, char* scratch, double cfl,
                                       double dt_fixed, int nsteps, cudaStream_t st,
                                       unsigned** status_out) {
-  if (g->d.precision == WC_PREC_LEARNED)
-    return fail(g, WC_ERR_UNSUPPORTED, "the fixed scratch holds no learned-weight buffer");
+  const wc_status sup = wc_internal_scratch_supported(g);
+  if (sup != WC_OK) return sup;
   // save and restore only the bindings (the grid also owns timing events)
   struct Bind {
     double* U; char* ws; size_t ws_bytes; double *B1, *B2, *Lacc;

@@ -49,12 +49,16 @@ wc_status wc_internal_rk_with_scratch(wc_grid* g, double* U, char* scratch, doub
                                       double dt_fixed, int nsteps, cudaStream_t st,
                                       unsigned** status_out);
 void wc_internal_set_error(wc_grid* g, const char* msg);
+wc_status wc_internal_scratch_supported(wc_grid* g);
 
 extern "C" wc_status wc_rk_step_noalloc(wc_grid* g, double* U_dev, double cfl, double dt_fixed,
                                         int nsteps, int* status_host, void* stream) {
   if (!g || !U_dev || nsteps < 0) return WC_ERR_ARG;
   if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return WC_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(U_dev) & 7) return WC_ERR_ARG;
+  // precisions the scratch cannot serve are refused before its size is
+  const wc_status sup = wc_internal_scratch_supported(g);
+  if (sup != WC_OK) return sup;
   size_t state = (size_t)wc_nvar(g) * (size_t)wc_ncell(g) * sizeof(double);
   state = (state + 255) / 256 * 256;
   if (3 * state > kScratchBytes) {

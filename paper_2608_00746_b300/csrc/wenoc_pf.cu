@@ -923,23 +923,27 @@ __global__ void __launch_bounds__(PF_THREADS) k_qmap_cg(PfGeom g, PfWork w, doub
     for (int p = 0; p < N; p++) {
       const long o = (long)p * n;
       int* lp = w.lab + o;
-      const double* cp = w.c + o;
       int k0, k1;
       own_range(scnt[p], b, G, k0, k1);
       for (int k = k0 + t; k < k1; k += PF_THREADS) {
         const int i = __ldcg(w.idx + o + k);
         const int li = __ldcg(lp + i);
-        const double ci = cp[i];
         int nb[3][2];
         pf_stencil(g, i, nb);
         int m = li;
+        // a face couples its cells when the operator's weight on it is
+        // positive (the test k_qm_diag lists cells by): then both cells
+        // are listed and carry labels >= 0.  (c_a + c_b)/2 of a denormal
+        // c next to c = 0 rounds to a zero weight, and such a neighbour
+        // is not listed.
 #pragma unroll
         for (int ax = 0; ax < 3; ax++) {
           if (ax >= g.dim) break;
+          const double* wa = w.w + ax * nn + o;
 #pragma unroll
           for (int sd = 0; sd < 2; sd++) {
             const int j = nb[ax][sd];
-            if (j >= 0 && (ci > 0.0 || cp[j] > 0.0)) m = min(m, __ldcg(lp + j));
+            if (j >= 0 && wa[sd ? i : j] > 0.0) m = min(m, __ldcg(lp + j));
           }
         }
         m = min(m, __ldcg(lp + m));
@@ -1088,13 +1092,12 @@ cudaError_t pf_qmap_solve(const PfGeom& g, const PfWork& w, int warm, double tol
   // the register-resident iteration takes up to 256 unknowns a block and
   // phase.  (Two blocks per SM, where registers allow, measured slower: 25
   // against 15 us an iteration on the shock-bubble bands.)
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-  }
+  // SM count of the current device, queried per call (a process may drive
+  // devices of different sizes)
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
   const int blocks = sms < 1 ? 1 : (sms > 4 * PF_THREADS ? 4 * PF_THREADS : sms);
   PfGeom gg = g;
   PfWork ww = w;

@@ -94,6 +94,44 @@ def test_qmap_solution(gpu, name):
     assert np.abs(F - F_or).max() <= 1e-8 * max(np.abs(F_or).max(), 1e-300)
 
 
+def test_qmap_denormal_coefficient_next_to_zero(gpu):
+    """A cell whose coefficient phi (1 - phi) is the smallest denormal,
+    beside cells with phi = 0: (c_a + c_b)/2 rounds to 0 on both of its
+    faces, so Eq. 4 couples it to nothing, while its neighbour belongs to
+    the interface band through its other face.  The region labelling must
+    follow the operator's face weights; Q then solves the oracle's Eq. 4."""
+    case = inputs.interface_advection_1d(n=200)
+    go, g = _grids(case)
+    U = oracle.prim_to_cons(go, case.V)
+    a0 = case.N + case.dim + 1
+    air = U[a0]
+    k = int(np.flatnonzero(air > 0.0)[0])      # first cell of the slab's band
+    i = k - 2                                   # two cells outside it
+    assert air[i - 1] == 0.0 and air[i] == 0.0 and air[i + 1] == 0.0
+    tiny = np.nextafter(0.0, 1.0)               # 4.9e-324
+    U[a0, i] = tiny
+    U[a0 + 1, i] = 1.0 - tiny                   # = 1.0
+    U[0, i] = tiny                              # the air mass (rho_air = 1)
+    phi = pf.fractions(go, U)
+    c = np.maximum(phi * (1.0 - phi), 0.0)
+    assert c[0, i] == tiny and 0.5 * (c[0, i] + c[0, i + 1]) == 0.0 and c[0, k] > 0.0
+    Ud = to_dev(U)
+    g.bind(Ud).set_pf_workspace(Ud.device)
+    g.cac_rhs(Ud)
+    Q, iters, res = g.qmap(Ud, tol=1e-13)
+    assert res <= 1e-13
+    Q = Q.cpu().numpy()
+    R_or, _, _ = pf.cac_rhs(go, U)
+    Q_or, Rp = pf.qmap(go, phi, R_or)
+    for p in range(go.N):
+        A, _ = pf.qmap_operator(go, phi[p])
+        AQ = A @ Q[p].reshape(-1)
+        assert np.abs(AQ - Rp[p].reshape(-1)).max() <= 1e-9 * max(np.abs(R_or).max(), 1e-300)
+    assert Q[0, i] == 0.0  # a cell that no face couples keeps Q = 0
+    F, F_or = _face_flux(go, phi, Q), _face_flux(go, phi, Q_or)
+    assert np.abs(F - F_or).max() <= 1e-8 * max(np.abs(F_or).max(), 1e-300)
+
+
 def test_qmap_warm_start(gpu):
     """Started from its own solution the Q-map does no iteration and keeps
     Q; started from that solution plus noise of size 1e-6 it converges to

@@ -60,3 +60,18 @@ def test_noalloc_rejects_grids_beyond_the_scratch(gpu):
     wenoc.lib().wc_last_error(g.h, buf, 256)
     assert b"too large" in buf.value
     assert not U.any()  # nothing was enqueued
+
+
+@pytest.mark.parametrize("nx,ny", [(96, 48), (1024, 512)])
+def test_noalloc_refuses_learned_precision_at_any_size(gpu, nx, ny):
+    """The fixed scratch holds no learned-weight buffer: a learned grid is
+    refused as unsupported, whether or not its stage buffers would fit."""
+    case = inputs.shock_bubble_2d(nx=nx, ny=ny, seed=0)
+    _, g = grids(case, precision="learned")
+    U = torch.zeros((g.nv, ny, nx), dtype=torch.float64, device="cuda")
+    rc, _ = _noalloc(g, U, cfl=0.2)
+    assert rc == 5  # WC_ERR_UNSUPPORTED
+    buf = ctypes.create_string_buffer(256)
+    wenoc.lib().wc_last_error(g.h, buf, 256)
+    assert b"learned" in buf.value
+    assert not U.any()
