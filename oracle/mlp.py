@@ -25,10 +25,10 @@ reading fixed here is the definition the GPU path is checked against:
   and fraction reconstructions (``loss_and_grads``); Adam (Kingma & Ba, beta1 0.9, beta2 0.999, eps 1e-8, bias
   corrected) on FP32 master parameters.
 
-Rounding of the features (see ``features``): differences in FP64, exact
-power-of-two scaling, FP32 normalisation, BF16 storage.  The GPU stores
-features, weights, hidden activations and the back-propagated
-deltas that enter a product in BF16 and accumulates in FP32.  ``rounded=True``
+Features (``features``): the normalised mass differences formed in FP64
+and every input rounded once to BF16.  The GPU stores features, weights,
+hidden activations and the back-propagated deltas that enter a product in
+BF16 and accumulates in FP32.  ``rounded=True``
 reproduces those rounding points here (BF16 = round to nearest even of the
 FP32 value) with every sum in FP64; ``rounded=False`` is the plain FP64
 network, the one the finite-difference pins check.
@@ -57,58 +57,36 @@ def bf16(x):
     return b.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-TINY = 2.0 ** -126   # feature values below this magnitude become zero
-
-
-def to_f32_flush(x):
-    """FP64 -> FP32, nearest even; magnitudes below 2^-126 become 0."""
+def bf16_round(x):
+    """x (FP64) rounded once to BF16: 8 significant bits with the exponent
+    range of binary32 (normal numbers from 2^-126, subnormal spacing
+    2^-133), to nearest with ties to even.  Value-based: x = m 2^e with
+    |m| in [1/2, 1) becomes a multiple of 2^max(e-8, -133).  (|x| < 2^128.)"""
     x = np.asarray(x, dtype=np.float64)
-    y = x.astype(np.float32)
-    y[np.abs(x) < TINY] = 0.0
-    return y
-
-
-def bf16_direct(x):
-    """FP64 rounded once to 8 significant bits (BF16), nearest even;
-    magnitudes below 2^-126 become 0.  Value-based: x = m 2^e with
-    |m| in [1/2, 1) is rounded to a multiple of 2^(e-8)."""
-    x = np.asarray(x, dtype=np.float64)
-    out = np.zeros_like(x)
-    nz = np.abs(x) >= TINY
-    _, e = np.frexp(x[nz])
-    q = np.ldexp(1.0, e - 8)
-    out[nz] = np.round(x[nz] / q) * q
-    return out
+    _, e = np.frexp(x)
+    q = np.ldexp(1.0, np.maximum(e - 8, -133))
+    return np.round(x / q) * q
 
 
 def features(ms, als):
     """Inputs of rows of oriented stencils: ms, als [rows][P][5] (P <= 3
     phases, masses and fractions) -> [rows][32] (BF16 values as float64).
-    Masses: differences d_k to the cell value in FP64 (subnormal d_k count as
-    zero); when max |d_k| >= 2^-1022 they are scaled by the power of two that
-    brings max |d_k| into [1, 2) (exact) and rounded to FP32 (below 2^-126:
-    0), divided in FP32 by the largest magnitude and rounded to BF16;
-    otherwise the stencil is flat (zeros).  Fractions: rounded once from FP64
-    to BF16 (below 2^-126: 0)."""
+
+    Reading 18 as written: for each phase the differences d_k = f_k - f_i of
+    the five masses to the cell's own (FP64), divided in FP64 by the largest
+    |d_k| (all zero when that is 0: a flat stencil), then the five
+    fractions; every value rounded once to BF16 (``bf16_round``)."""
     ms = np.asarray(ms, dtype=np.float64)
     als = np.asarray(als, dtype=np.float64)
     rows, P = ms.shape[0], ms.shape[1]
     X = np.zeros((rows, IN))
     for p in range(P):
         d = ms[:, p, :] - ms[:, p, 2:3]
-        d[:, 2] = 0.0
-        d[np.abs(d) < 2.0 ** -1022] = 0.0
         mx = np.max(np.abs(d), axis=1, keepdims=True)
         live = mx > 0.0
-        _, e = np.frexp(np.where(live, mx, 1.0))
-        ds = np.where(live, d * np.ldexp(1.0, 1 - e), 0.0)
-        d32 = to_f32_flush(ds)
-        m32 = np.max(np.abs(d32), axis=1, keepdims=True)
-        big = m32 > np.float32(0.0)
-        r = np.where(big, np.float32(1.0) / np.where(big, m32, np.float32(1.0)),
-                     np.float32(0.0)).astype(np.float32)
-        X[:, 10 * p:10 * p + 5] = bf16((d32 * r).astype(np.float32))
-        X[:, 10 * p + 5:10 * p + 10] = bf16_direct(als[:, p, :])
+        q = np.where(live, d / np.where(live, mx, 1.0), 0.0)
+        X[:, 10 * p:10 * p + 5] = bf16_round(q)
+        X[:, 10 * p + 5:10 * p + 10] = bf16_round(als[:, p, :])
     return X
 
 

@@ -87,21 +87,61 @@ def test_bf16_round_to_nearest_even():
     assert mlp.bf16(0.0) == 0.0
 
 
-def test_bf16_direct_rounding():
-    """One rounding from FP64 to 8 significant bits: equal to the FP32 route
-    where FP32 holds the value exactly; ties to even; tiny values flushed."""
+def _all_bf16_values():
+    """Every finite BF16 value (all 16-bit patterns but Inf/NaN), sorted,
+    with the parity of its last significand bit."""
+    pat = np.arange(1 << 16, dtype=np.uint32)
+    pat = pat[(pat & 0x7F80) != 0x7F80]
+    v = (pat << 16).view(np.float32).astype(np.float64)
+    order = np.argsort(v, kind="stable")
+    v, pat = v[order], pat[order]
+    keep = np.concatenate([[True], v[1:] != v[:-1]])   # +0 / -0
+    return v[keep], (pat[keep] & 1) == 0
+
+
+def test_bf16_round_is_the_nearest_bf16_value():
+    """bf16_round against brute force over the whole BF16 value set: the
+    nearest value, ties to the one with an even last bit; values inside the
+    subnormal range and exact ties included."""
+    vals, even = _all_bf16_values()
     rng = np.random.default_rng(5)
-    f32 = rng.standard_normal(1000).astype(np.float32).astype(np.float64)
-    assert np.array_equal(mlp.bf16_direct(f32), mlp.bf16(f32))
+    x = np.concatenate([
+        rng.standard_normal(3000) * 10.0 ** rng.integers(-6, 6, 3000),
+        rng.random(500) * 2.0 ** -126,                       # subnormal BF16 range
+        rng.random(200) * 2.0 ** -133,                       # below the smallest
+        vals[(vals > -1e30) & (vals < 1e30)][::97],          # representable values
+    ])
+    mids = 0.5 * (vals[1:] + vals[:-1])
+    x = np.concatenate([x, mids[np.abs(mids) < 1e30][::61]])   # exact ties
+    j = np.clip(np.searchsorted(vals, x), 1, len(vals) - 1)
+    lo, hi = vals[j - 1], vals[j]
+    dlo, dhi = x - lo, hi - x
+    pick = np.where(dlo < dhi, lo, np.where(dhi < dlo, hi, np.where(even[j - 1], lo, hi)))
+    got = mlp.bf16_round(x)
+    assert np.array_equal(got, pick)
     u = 2.0 ** -7
-    assert mlp.bf16_direct(1.0 + u / 2) == 1.0
-    assert mlp.bf16_direct(1.0 + 1.5 * u) == 1.0 + 2 * u
-    # just above a tie rounds up: a case where rounding through FP32 first
-    # (to the tie) would round down
+    assert mlp.bf16_round(1.0 + u / 2) == 1.0
+    # just above a tie rounds up; rounding through FP32 first would land on
+    # the tie and round down
     x = 1.0 + u / 2 + 2.0 ** -40
-    assert mlp.bf16_direct(x) == 1.0 + u and mlp.bf16(x) == 1.0
-    assert mlp.bf16_direct(2.0 ** -127) == 0.0 and mlp.bf16_direct(2.0 ** -126) == 2.0 ** -126
-    assert mlp.to_f32_flush(np.array([2.0 ** -127, 1.0 / 3.0]))[0] == 0.0
+    assert mlp.bf16_round(x) == 1.0 + u and mlp.bf16(x) == 1.0
+    assert mlp.bf16_round(2.0 ** -134) == 0.0 and mlp.bf16_round(1.5 * 2.0 ** -133) == 2.0 ** -132
+
+
+def test_features_hand_computed_stencil():
+    """Masses 1, 2, 4, 7, 5 around the cell value 4: differences -3, -2, 0,
+    3, 1 over the largest, 3, are -1, -2/3, 0, 1, 1/3; to 8 significant
+    bits 2/3 = 0.10101010|10..b rounds up to 171/256 and 1/3 to 171/512."""
+    ms = np.zeros((1, 3, 5))
+    ms[0, 0] = [1.0, 2.0, 4.0, 7.0, 5.0]
+    al = np.zeros((1, 3, 5))
+    al[0, 0] = [0.0, 0.1, 0.5, 0.9, 1.0]
+    X = mlp.features(ms, al)
+    assert X[0, 0:5].tolist() == [-1.0, -171.0 / 256.0, 0.0, 1.0, 171.0 / 512.0]
+    # 0.1 = 1.1001100|1100..b x 2^-4 -> 1.1001101b x 2^-4 = 205/2048; 0.9 =
+    # 1.1100110|0110..b x 2^-1 -> 1.1100110b x 2^-1 = 115/128
+    assert X[0, 5:10].tolist() == [0.0, 205.0 / 2048.0, 0.5, 115.0 / 128.0, 1.0]
+    assert np.all(X[0, 10:] == 0.0)
 
 
 def test_adam_first_step_is_signed_lr():
@@ -126,7 +166,7 @@ def test_features_affine_invariance_and_flat_stencil():
     assert np.all(np.abs(X[:, [0, 1, 3, 4, 10, 11, 13, 14]]) <= 1.0)
     assert np.all(X[:, [2, 12, 22]] == 0.0)
     assert np.all(X[:, 30:] == 0.0)
-    assert np.array_equal(X[:, 5:10], mlp.bf16_direct(al[:, 0, :]))
+    assert np.array_equal(X[:, 5:10], mlp.bf16_round(al[:, 0, :]))
     flat = np.full((1, 3, 5), 7.5)
     Xf = mlp.features(flat, np.full((1, 3, 5), 0.25))
     assert np.all(Xf[0, [0, 1, 2, 3, 4]] == 0.0)
