@@ -89,6 +89,16 @@ def lib():
             f = getattr(_lib, name)
             f.argtypes = args
             f.restype = ctypes.c_int
+        for name, args in {
+            "or_r13_set_stage_tol": [ctypes.c_double],
+            "or_r13_reset": [],
+            "or_r13_stats": [dp],
+            "or_rk_stage": [gp, ctypes.c_double, dp, ctypes.c_double, dp, ctypes.c_double,
+                            ctypes.c_double, dp, dp],
+        }.items():
+            f = getattr(_lib, name)
+            f.argtypes = args
+            f.restype = None
     return _lib
 
 
@@ -334,3 +344,39 @@ def wenojs_weights(beta, eps):
 
 def num_threads():
     return lib().or_num_threads()
+
+
+# ---------------------------------------------------------------- R13 hooks
+def r13_reset():
+    """Clears R13's bookkeeping (face residues and the stage histogram)."""
+    lib().or_r13_reset()
+
+
+def r13_stats():
+    """R13's bookkeeping since the last reset: ``face_n`` face values the
+    face rule set to 0, ``face_max`` their largest |x| / fbar, and ``hist``
+    {log2 bin: count} of the stage values found outside a bound, binned by
+    floor(log2(excursion / sum of the stage terms' magnitudes))."""
+    out = np.zeros(68)
+    lib().or_r13_stats(_p(out))
+    hist = {b - 64: int(out[2 + b]) for b in range(66) if out[2 + b] > 0}
+    return {"face_n": int(out[0]), "face_max": float(out[1]), "hist": hist}
+
+
+def set_stage_tol(tol):
+    """Tolerance of R13's stage rule (relative to the sum of the terms'
+    magnitudes); 2^-48 is the oracle's.  For tests that run the method with
+    another one."""
+    lib().or_r13_set_stage_tol(float(tol))
+
+
+def rk_stage(g: Grid, a, U0, b, U1, c, dt, L):
+    """One stage a U0 + b U1 + c dt L with R13's stage rule (the bounded
+    variables are the masses and fractions)."""
+    U0 = np.ascontiguousarray(U0, dtype=np.float64)
+    U1 = np.ascontiguousarray(U1, dtype=np.float64)
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    out = np.empty_like(U0)
+    lib().or_rk_stage(g.ref(), float(a), _p(U0), float(b), _p(U1), float(c), float(dt), _p(L),
+                      _p(out))
+    return out

@@ -292,10 +292,43 @@ static double theta_lower(double fbar, double fC, double fL, double fR, double f
   return t < 1.0 ? t : 1.0;
 }
 
+/* R13 bookkeeping for the tests (no effect on any result): the face values
+ * the face rule set to 0 (count, largest |x| / fbar) and a histogram of the
+ * stage values found outside a bound, by floor(log2(excursion / sum of the
+ * terms' magnitudes)) from -64 to +1, whether the stage rule clamped them
+ * or not.  The stage rule's tolerance is a parameter only so that the tests
+ * can run the method with another one. */
+static double or_stage_tol = 0x1p-48;
+static double r13_face_n, r13_face_max, r13_hist[66];
+
+void or_r13_set_stage_tol(double tol) { or_stage_tol = tol; }
+void or_r13_reset(void) {
+  r13_face_n = r13_face_max = 0.0;
+  for (int i = 0; i < 66; i++) r13_hist[i] = 0.0;
+}
+void or_r13_stats(double *out) {
+  out[0] = r13_face_n;
+  out[1] = r13_face_max;
+  for (int i = 0; i < 66; i++) out[2 + i] = r13_hist[i];
+}
+
 /* R13: fbar + theta (f - fbar) below the bound 0 is rounding residue when
  * fbar >= 0 and becomes 0; with fbar < 0 (theta = 0, a stage that left the
  * bound) the value is fbar itself and stays. */
-static double clamp0(double x, double fbar) { return x < 0.0 && fbar >= 0.0 ? 0.0 : x; }
+static double clamp0(double x, double fbar) {
+  if (x < 0.0 && fbar >= 0.0) {
+    double r = fbar > 0.0 ? -x / fbar : INFINITY;
+#ifdef _OPENMP
+#pragma omp critical(r13)
+#endif
+    {
+      r13_face_n += 1.0;
+      if (r > r13_face_max) r13_face_max = r;
+    }
+    return 0.0;
+  }
+  return x;
+}
 
 static double theta_pos(double fbar, double fL, double fR) {
   return theta_lower(fbar, center_value(fbar, fL, fR), fL, fR, 0.0);
@@ -949,7 +982,6 @@ int or_max_rate(const or_grid *g, const double *U, double *rate) {
  * negative average).  A mass and a fraction of one phase have terms in the
  * ratio rho_p, so they are kept or clamped together.  R16: no bound is
  * restored without Eq. 17-20. */
-#define OR_STAGE_TOL 0x1p-48
 static void rk_stage(const or_grid *g, double a, const double *U0, double b, const double *U1,
                      double c, double dt, const double *L, double *out) {
   long n = ncells(g), tot = n * nv(g);
@@ -959,12 +991,25 @@ static void rk_stage(const or_grid *g, double a, const double *U0, double b, con
     int v = (int)(k / n);
     int bounded = g->limiter && (v < g->N || v >= IALF(g, 0));
     if (bounded) {
-      double tol = OR_STAGE_TOL * (fabs(t0) + fabs(t1) + fabs(t2));
+      double mag = fabs(t0) + fabs(t1) + fabs(t2);
+      double exc = x < 0.0 ? -x : (v >= IALF(g, 0) && x > 1.0 ? x - 1.0 : 0.0);
+      if (exc > 0.0) {
+        int bin = mag > 0.0 ? (int)floor(log2(exc / mag)) : 1;
+        bin = bin < -64 ? -64 : (bin > 1 ? 1 : bin);
+        r13_hist[bin + 64] += 1.0;
+      }
+      double tol = or_stage_tol * mag;
       if (x < 0.0 && -x <= tol) x = 0.0;
       if (v >= IALF(g, 0) && x > 1.0 && x - 1.0 <= tol) x = 1.0;
     }
     out[k] = x;
   }
+}
+
+/* One stage alone, for the tests of R13's stage rule. */
+void or_rk_stage(const or_grid *g, double a, const double *U0, double b, const double *U1,
+                 double c, double dt, const double *L, double *out) {
+  rk_stage(g, a, U0, b, U1, c, dt, L, out);
 }
 
 /* One third-order SSP (TVD) Runge-Kutta step of Shu & Osher, in place.
