@@ -21,9 +21,9 @@ constexpr int MLP_NPARAM = MLP_NWEIGHT + MLP_NBIAS;
 constexpr size_t MLP_PARAM_BYTES = (size_t)MLP_NWEIGHT * 2 + (size_t)MLP_NBIAS * 4;
 
 // Roundings of FP64 values on the integer pipe (the FP64 pipe is slow on
-// this part): to FP32 and to BF16, to nearest with ties to even; magnitudes
-// below 2^-126 become zero.
-// x * 2^k (k >= -1023) rounded to FP32; subnormal x counts as zero
+// this part), to nearest with ties to even.
+// x * 2^k (k >= -1023) rounded to FP32; results below 2^-126 (and
+// subnormal x) become zero -- callers treat those as a slow case
 __device__ __forceinline__ float f64_to_f32_flush(double x, int k = 0) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7ff);
@@ -37,30 +37,50 @@ __device__ __forceinline__ float f64_to_f32_flush(double x, int k = 0) {
   if (ef < 255 && (rem > half || (rem == half && (q & 1u)))) r += 1u;
   return __uint_as_float(r | sign);
 }
-__device__ __forceinline__ __nv_bfloat16 f64_to_bf16_flush(double x) {
+// x rounded once to BF16 (8 significant bits, the exponent range of binary32
+// including its subnormals, spacing 2^-133 below 2^-126); |x| < 2^128
+__device__ __forceinline__ unsigned short f64_to_bf16_bits(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int ef = (int)((b >> 52) & 0x7ff) - 1023 + 127;
-  const unsigned short sign = (unsigned short)((b >> 48) & 0x8000u);
-  if (ef <= 0) return __ushort_as_bfloat16(sign);
+  const unsigned int sign = (unsigned int)(b >> 48) & 0x8000u;
+  const int e = (int)((b >> 52) & 0x7ff);
   const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-  const unsigned int q = (unsigned int)(m >> 45);
-  const unsigned long long rem = m & ((1ull << 45) - 1), half = 1ull << 44;
-  unsigned int r = ((unsigned int)(ef < 255 ? ef : 255) << 7) | (ef < 255 ? q : 0u);
-  if (ef < 255 && (rem > half || (rem == half && (q & 1u)))) r += 1u;
-  return __ushort_as_bfloat16((unsigned short)(r | sign));
+  const int ef = e - 1023 + 127;
+  if (ef >= 1) {
+    const unsigned int q = (unsigned int)(m >> 45);
+    const unsigned long long rem = m & ((1ull << 45) - 1), half = 1ull << 44;
+    unsigned int r = ((unsigned int)ef << 7) | q;
+    if (rem > half || (rem == half && (q & 1u))) r += 1u;
+    return (unsigned short)(r | sign);
+  }
+  // x = M 2^(e - 1075) with M = 2^52 + m: in units of 2^-133 that is
+  // M / 2^(942 - e); below 2^-134 (and FP64 subnormals) it rounds to 0
+  const int sh = 942 - e;  // >= 46 here
+  if (e == 0 || sh >= 54) return (unsigned short)sign;
+  const unsigned long long M = m | (1ull << 52);
+  const unsigned int q = (unsigned int)(M >> sh);
+  const unsigned long long rem = M & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+  unsigned int r = q;
+  if (rem > half || (rem == half && (q & 1u))) r += 1u;
+  return (unsigned short)(r | sign);
 }
 
 // Features of both face sides of one cell (reading of the learned-weight
-// workload): for each phase p the five masses of the stencil, ordered
-// towards the face, minus the cell's own mass (FP64 differences d_k), scaled
-// by the power of two 2^s that brings max |d_k| into [1, 2) and rounded to
-// FP32 (values below 2^-126 and subnormal d_k to zero), divided in FP32 by
-// their largest magnitude; a stencil with max |d_k| below 2^-1022 is flat
-// (all zero).  Then the five fractions rounded once from FP64 to BF16 (below
-// 2^-126 to zero).  Everything ends as BF16.  Side 0 (x_{i+1/2}) takes the
-// stencil f_{i-2..i+2}, side 1 (x_{i-1/2}) its mirror image.  Eq. 15 is
-// invariant under f -> a f + b, so the scaled masses lose nothing; only the
-// differences use the FP64 pipe.
+// workload): for each phase p the differences d_k = f_k - f_i (FP64) of the
+// five masses of the stencil, ordered towards the face, to the cell's own,
+// divided by the largest |d_k| (all zero for a flat stencil), then the five
+// fractions, each value rounded once to BF16.  Side 0 (x_{i+1/2}) takes the
+// stencil f_{i-2..i+2}, side 1 (x_{i-1/2}) its mirror image, whose features
+// are the same values reversed.
+//
+// The quotients are formed in FP32 from the differences scaled by the power
+// of two that brings max |d_k| into [1, 2): three roundings of 2^-24 and
+// one of the product, so the FP32 quotient is within 4 of its units in the
+// last place of d_k / max |d_k|.  Its BF16 rounding is then that of the FP64
+// quotient except within 16 such units of a BF16 halfway point (and for
+// quotients below 2^-126, where FP32 loses bits); those few values (about
+// one in 2,000) are divided in FP64 and rounded from there, so every
+// feature is the FP64 quotient rounded once to BF16.  Only the differences
+// use the FP64 pipe otherwise.
 template <int N>
 __device__ __forceinline__ void mlp_features2(const double (*m)[5], const double (*al)[5],
                                               __nv_bfloat16* x0, __nv_bfloat16* x1) {
@@ -84,8 +104,21 @@ __device__ __forceinline__ void mlp_features2(const double (*m)[5], const double
     const float r = mx > 0.0f ? 1.0f / mx : 0.0f;
 #pragma unroll
     for (int k = 0; k < 5; k++) {
-      const __nv_bfloat16 xm = __float2bfloat16(d[k] * r);
-      const __nv_bfloat16 xa = f64_to_bf16_flush(al[p][k]);
+      const unsigned int qb = __float_as_uint(d[k] * r);
+      const unsigned int rem = qb & 0xFFFFu;
+      // slow: near a halfway point, below 2^-126 in FP32 (flushed or
+      // subnormal), or a subnormal largest difference
+      const bool slow = (mxb != 0 && E == 0) ||
+                        (dd[k] != 0.0 && (qb & 0x7F800000u) == 0u) ||
+                        (rem >= 0x8000u - 16u && rem <= 0x8000u + 16u);
+      unsigned short xb;
+      if (!slow) {
+        xb = (unsigned short)((qb + 0x7FFFu + ((qb >> 16) & 1u)) >> 16);
+      } else {
+        xb = f64_to_bf16_bits(dd[k] / __longlong_as_double(mxb));
+      }
+      const __nv_bfloat16 xm = __ushort_as_bfloat16(mxb == 0 ? (unsigned short)0 : xb);
+      const __nv_bfloat16 xa = __ushort_as_bfloat16(f64_to_bf16_bits(al[p][k]));
       if (x0) {
         x0[p * 10 + k] = xm;
         x0[p * 10 + 5 + k] = xa;
