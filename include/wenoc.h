@@ -155,6 +155,17 @@ wc_status wc_temperature(const wc_grid *g, const double *U_dev, const double *cT
  * state), summed over the directions; L_dev is overwritten. */
 wc_status wc_rhs(wc_grid *g, const double *U_dev, double *L_dev, void *stream);
 
+/* The limited face states of one direction's sweep of wc_rhs for the state
+ * U_dev, as the grid's precision and scheme compute them: UL_dev[v][cell] =
+ * U^L_{i+1/2} and UR_dev[v][cell] = U^R_{i-1/2} ([NV][ncell] FP64 each,
+ * device), the conservative face states after Eq. 16-21 that the Riemann
+ * solver receives (Eq. 8 is what they must satisfy).  A diagnostic of the
+ * operator (the paper has no such call); the direction's rhs goes to the
+ * workspace's accumulator.  Window schedule only (seg = 0, else
+ * WC_ERR_UNSUPPORTED).  Asynchronous on stream. */
+wc_status wc_faces(wc_grid *g, int dir, const double *U_dev, double *UL_dev, double *UR_dev,
+                   void *stream);
+
 /* L = dU/dt of the Phase-Field step (Eq. 5), + div F^PF, for the state U_dev
  * and the auxiliary fields Q_dev [N][ncell] of Eq. 4 (wc_qmap computes them).
  * Face gradients G are central differences of Q, zero on a face where both

@@ -408,6 +408,23 @@ extern "C" wc_status wc_rhs(wc_grid* g, const double* U, double* L, void* stream
   return WC_OK;
 }
 
+extern "C" wc_status wc_faces(wc_grid* g, int dir, const double* U, double* UL, double* UR,
+                              void* stream) {
+  if (!g || !U || !UL || !UR) return WC_ERR_ARG;
+  if (dir < 0 || dir >= g->d.dim) return fail(g, WC_ERR_ARG, "bad direction");
+  if (!g->status || !g->Lacc)
+    return fail(g, WC_ERR_STATE, "wc_faces needs a bound workspace (its rhs goes there)");
+  if (g->d.seg > 0) return fail(g, WC_ERR_UNSUPPORTED, "wc_faces needs the window schedule (seg = 0)");
+  if (g->d.precision == WC_PREC_LEARNED && !g->mlp)
+    return fail(g, WC_ERR_STATE, "learned precision needs wc_set_mlp");
+  SweepArgs a = make_args(g, dir, U, g->Lacc);
+  a.mode = 0;
+  a.faceL = UL;
+  a.faceR = UR;
+  cudaError_t e = launch(g, a, S(stream));
+  return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "face sweep");
+}
+
 extern "C" wc_status wc_rhs_pf(wc_grid* g, const double* U, const double* Q, double dt_limit,
                                double* L, void* stream) {
   if (!g || !U || !Q || !L || dt_limit < 0.0) return WC_ERR_ARG;

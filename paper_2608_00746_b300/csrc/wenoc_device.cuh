@@ -906,9 +906,12 @@ __device__ __forceinline__ void hll_fp64(const Mat& m, int dir, const Face<N, D>
 //    = Pb sum A alpha + |ub|^2 rho / 2 + Et, so
 //      F^{rho u_j} = ub_j F^rho + F[rho (u_j - ub_j)] + delta_jn F[P],
 //      F^{rho E}   = sum_p (B_p + Pb A_p) F^{alpha_p} + sum_p D_p F^{(alpha rho)_p}
-//                    + |ub|^2 F^rho / 2 + F[Et];
+//                    + |ub|^2 F^rho / 2 + Pb u_hat + F[Et],
+//    where F[Et] is the flux of Et with the work term u (P - Pb) (the work
+//    u Pb has no state part, so its flux is Pb u_hat in both solvers);
 //    the bracketed remainders vanish exactly for uniform u and P, so an
-//    isolated interface keeps u and P uniform whatever TF is;
+//    isolated interface keeps u and P uniform whatever TF is, and pressure
+//    differences far below the TF resolution of P are still damped;
 //  * wave speeds, the HLLC contact speed and the remainders are in TF.
 // HLL is written as F_L + k ((F_L - F_R) + s_R (U_R - U_L)), k = s_L/(s_R - s_L),
 // which returns F_L exactly for equal states.
@@ -1003,14 +1006,18 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
       if (j == dir) f += L.P + kd * dPd;
       F[I::U(j)] = f;
     }
-    // energy remainder
-    TF gl = uL * (EtL + PL), gr = uR * (EtR + PR);
+    // energy remainder, with the pressure work of Pb taken out: the flux
+    // of u Pb (no state part) is Pb u_hat, added in FP64 below, so the
+    // remainder carries P - Pb = +-dP/2 and keeps the dissipation of
+    // pressure differences far below the TF resolution of P itself
+    TF gl = uL * (EtL + halfdP), gr = uR * (EtR - halfdP);
     TF g = gl + k * ((gl - gr) + sRu * (EtR - EtL));
     double fe = wide(g);
     double ub2 = 0.0;
 #pragma unroll
     for (int j = 0; j < D; j++) ub2 = fma(ub[j], ub[j], ub2);
     const double Pb = L.P - 0.5 * dPd;
+    fe = fma(Pb, uhat, fe);
 #pragma unroll
     for (int p = 0; p < N; p++) {
       fe = fma(fma(m.A[p], Pb, m.B[p]), F[I::A(p)], fe);
@@ -1025,12 +1032,18 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
   for (int j = 1; j < D; j++)
     if (j == dir) ubn = ub[j];
   bool left;
-  TF sK, chi, sS;
+  TF sK, chi, chim1, sS;
+  // u_K - S*, formed from the differences to ub_n (in TF, u_K and S* round
+  // to the same value when they differ by less than the TF resolution of
+  // u, and the star pressure P_K + rho_K (s_K - u_K)(S* - u_K) would lose
+  // its correction)
+  TF uKmS = TF(0);
   double sSd;  // contact speed in FP64 (ub_n + correction) for the momentum flux
   if (ge0(sL) || le0(sR)) {
     left = ge0(sL);
     sK = TF(0);
     chi = TF(1);
+    chim1 = TF(0);
     sS = left ? uL : uR;
     sSd = left ? uLd : uRd;
   } else {
@@ -1044,14 +1057,19 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
     sK = left ? sL : sR;
     TF uK = left ? uL : uR;
     // u_K - S* = (u_K - ub_n) - rel
-    TF uKmS = cvt<TF>((left ? uLd : uRd) - ubn) - rel;
-    chi = (sK - uK) / (sK - uK + uKmS);
+    uKmS = cvt<TF>((left ? uLd : uRd) - ubn) - rel;
+    // chi - 1 = (S* - u_K)/(s_K - S*) directly: chi itself rounds to 1 in
+    // TF when S* - u_K is below the TF resolution, and u_hat = u_K +
+    // s_K (chi - 1) would lose the contact's response to pressure jumps
+    const TF dK = sK - uK + uKmS;
+    chim1 = -uKmS / dK;
+    chi = (sK - uK) / dK;
   }
-  const TF uK = left ? uL : uR, rK = left ? rL : rR, PK = left ? PL : PR;
+  const TF uK = left ? uL : uR, rK = left ? rL : rR;
   const TF EtK = left ? EtL : EtR;
   const double uKd = left ? uLd : uRd;
   // u_hat = u_K + s_K (chi - 1)
-  uhat = uKd + wide(sK * (chi - TF(1)));
+  uhat = uKd + wide(sK * chim1);
 #pragma unroll
   for (int p = 0; p < N; p++) {
     double aK = left ? L.U[I::A(p)] : R.U[I::A(p)];
@@ -1060,7 +1078,6 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
     F[p] = mK * uhat;
     Frho += F[p];
   }
-  const TF uKmS = uK - sS;
 #pragma unroll
   for (int j = 0; j < D; j++) {
     if (j == dir) {
@@ -1072,15 +1089,20 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
       F[I::U(j)] = (left ? L.u[j] : R.u[j]) * Frho;
     }
   }
-  // remainder energy with the HLLC star state
-  TF Es = chi * (EtK + (sS - uK) * (rK * sS + PK / (sK - uK)));
+  // remainder energy with the HLLC star state.  The pressure work of the
+  // star flux is u_K P_K + s_K chi (S* - u_K) P_K / (s_K - u_K) = P_K u_hat;
+  // its part Pb u_hat is added in FP64 below and the remainder carries
+  // P_K - Pb = +-dP/2, far below the TF resolution of P itself
+  const TF pK = left ? halfdP : -halfdP;
+  TF Es = chi * (EtK - uKmS * (rK * sS + pK / (sK - uK)));
   if (sK == TF(0)) Es = EtK;
-  TF g = uK * (EtK + PK) + sK * (Es - EtK);
+  TF g = uK * (EtK + pK) + sK * (Es - EtK);
   double fe = wide(g);
   double ub2 = 0.0;
 #pragma unroll
   for (int j = 0; j < D; j++) ub2 = fma(ub[j], ub[j], ub2);
   const double Pb = L.P - 0.5 * dPd;
+  fe = fma(Pb, uhat, fe);
 #pragma unroll
   for (int p = 0; p < N; p++) {
     fe = fma(fma(m.A[p], Pb, m.B[p]), F[I::A(p)], fe);

@@ -60,6 +60,11 @@ struct SweepArgs {
   unsigned nwarps;
   int wfull, wtail, wgrp, wslots;
   unsigned nitems;
+  // face dump (window schedule only; null in the operator's own launches):
+  // the limited conservative face states U^L_{i+1/2} and U^R_{i-1/2} of
+  // every cell, [NV][ncell] each
+  double* faceL;
+  double* faceR;
 };
 
 enum { BC_PERIODIC = 0, BC_REFLECTIVE = 1, BC_OUTFLOW = 2 };
@@ -89,13 +94,82 @@ __device__ __forceinline__ int bc_index(int j, int n, int bclo, int bchi, bool& 
 // FP64 (for psi at the cell average) and the primitive state V[NV] in the
 // reconstruction precision T.  Conservative cell values are re-read from
 // global memory (L1-resident: each cell is read twice within 3 iterations).
+//
+// In reduced precision a slot also holds, after V, the residues
+// v - (double) cvt<T>(v) of the velocity components and the pressure in T
+// (hi/lo pairs), so their stencil differences are known to the precision of
+// the differences themselves, not of the values.
 template <int N, int D, typename T>
 struct Ring {
   static constexpr int NV = Idx<N, D>::NV;
-  static constexpr int SLOT_BYTES = 8 + NV * (int)sizeof(T);
+  static constexpr bool HILO = !std::is_same<T, double>::value;
+  static constexpr int SLOT_BYTES = 8 + (NV + (HILO ? D + 1 : 0)) * (int)sizeof(T);
   static constexpr int SLOTD = (SLOT_BYTES + 7) / 8;   // doubles per slot
   static constexpr int BYTES = 5 * SLOTD * 8;          // per thread
 };
+
+// Fills a slot from the FP64 primitive state v of a cell.
+template <int N, int D, typename T>
+__device__ __forceinline__ void put_slot(double* sl, const double* v) {
+  using I = Idx<N, D>;
+  sl[0] = v[I::E];
+  T* Vs = reinterpret_cast<T*>(sl + 1);
+#pragma unroll
+  for (int k = 0; k < I::NV; k++) Vs[k] = cvt<T>(v[k]);
+  if constexpr (Ring<N, D, T>::HILO) {
+#pragma unroll
+    for (int q = 0; q <= D; q++) Vs[I::NV + q] = cvt<T>(v[N + q] - wide(Vs[N + q]));
+  }
+}
+
+// Faces of the velocity components and the pressure, each with its own
+// weights (V[k] = the slots of the stencil's five cells, Pb the cell's FP64
+// pressure).  FP64: value form.  Reduced precision: the stencil of the
+// differences to the cell value, formed from the hi/lo pairs, reconstructed
+// in T as offsets that are added to the FP64 cell value; an offset below
+// the T resolution of the cell value (|value| 2^-24) is dropped.  So a
+// uniform stencil, or one that varies only below what T can resolve, gives
+// faces equal to the cell value, and the FP64 noise of a uniform field
+// stays a cell's own instead of being quantised to T steps.
+template <int N, int D, typename T, int LW>
+__device__ __forceinline__ void face_velocity_pressure(const Mat& m, const T* const* V, double Pb,
+                                                       double* uL, double* uR, double& PL,
+                                                       double& PR) {
+  using I = Idx<N, D>;
+#pragma unroll
+  for (int v = N; v <= N + D; v++) {
+    double fl, fr;
+    if constexpr (Ring<N, D, T>::HILO) {
+      const int q = v - N;
+      const T c = V[2][v], cl = V[2][I::NV + q];
+      auto dlt = [&](int k) { return (V[k][v] - c) + (V[k][I::NV + q] - cl); };
+      const Stencil<T> st{c, dlt(0), dlt(1), dlt(3), dlt(4)};
+      const W6<T> w = sweep_weights<LW, T>(m, st);
+      T oL, oR;
+      offsets(w, st, oL, oR);
+      const T res = fabs(c) * T(0x1p-24);
+      if (fabs(oL) < res) oL = T(0);
+      if (fabs(oR) < res) oR = T(0);
+      const double cv = v < N + D ? wide(c) + wide(cl) : Pb;
+      fl = cv + wide(oL);
+      fr = cv + wide(oR);
+    } else {
+      const Stencil<T> st = stencil<T>(V[0][v], V[1][v], V[2][v], V[3][v], V[4][v]);
+      const W6<T> w = sweep_weights<LW, T>(m, st);
+      T tl, tr;
+      reconstruct(w, st, tl, tr);
+      fl = wide(tl);
+      fr = wide(tr);
+    }
+    if (v < N + D) {
+      uL[v - N] = fl;
+      uR[v - N] = fr;
+    } else {
+      PL = fl;
+      PR = fr;
+    }
+  }
+}
 
 // March through cells [s, e) of one pencil (first cell at index `base`,
 // step `a.stride`, `a.n` cells, boundary conditions a.bclo/a.bchi):
@@ -130,11 +204,7 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
     double u[NV], v[NV];
     load_cons(c, u);
     cons_to_prim<N, D>(m, u, v);
-    double* sl = ring + ((c + 15) % 5) * SLOTD;
-    sl[0] = v[I::E];
-    T* Vs = reinterpret_cast<T*>(sl + 1);
-#pragma unroll
-    for (int k = 0; k < NV; k++) Vs[k] = cvt<T>(v[k]);
+    put_slot<N, D, T>(ring + ((c + 15) % 5) * SLOTD, v);
   };
 
   for (int c = s - 3; c <= s; c++) load(c);
@@ -241,23 +311,7 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
     }
     // velocity and pressure, each with its own weights
     double uL[D], uR[D], PL, PR;
-#pragma unroll
-    for (int v = N; v <= N + D; v++) {
-      Stencil<T> st = stencil<T>(V[0][v], V[1][v], V[2][v], V[3][v], V[4][v]);
-      W6<T> w = sweep_weights<LW, T>(m, st);
-      // velocity and pressure in value form in every precision: a uniform
-      // field (FP64 noise below the FP32 resolution) gives uniform faces
-      T tl, tr;
-      reconstruct(w, st, tl, tr);
-      const double fl = wide(tl), fr = wide(tr);
-      if (v < N + D) {
-        uL[v - N] = fl;
-        uR[v - N] = fr;
-      } else {
-        PL = fl;
-        PR = fr;
-      }
-    }
+    face_velocity_pressure<N, D, T, LW>(m, V, Pb, uL, uR, PL, PR);
     Face<N, D> fL, fR;
     limit_chain<N, D, LW != 2>(m, Ub, Pb, mL, aL, mR, aR, uL, PL, uR, PR, a.energy_limiter, fL, fR,
                       nullptr);

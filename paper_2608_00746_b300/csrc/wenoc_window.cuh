@@ -91,11 +91,7 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
   };
   auto store_slot = [&](int s, const double* u, double* v) {
     cons_to_prim<N, D>(m, u, v);
-    double* sl = slots + s * SLOTD;
-    sl[0] = v[I::E];
-    T* Vs = reinterpret_cast<T*>(sl + 1);
-#pragma unroll
-    for (int k = 0; k < NV; k++) Vs[k] = cvt<T>(v[k]);
+    put_slot<N, D, T>(slots + s * SLOTD, v);
   };
   // reduced precision: mass and fraction faces = FP64 cell value (a
   // conservative and primitive variable alike) + offset in T
@@ -195,26 +191,18 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
   }
   // velocity and pressure, each with its own weights
   double uL[D], uR[D], PL, PR;
-#pragma unroll
-  for (int v = N; v <= N + D; v++) {
-    Stencil<T> st = stencil<T>(V[0][v], V[1][v], V[2][v], V[3][v], V[4][v]);
-    W6<T> w = sweep_weights<LW, T>(m, st);
-    // velocity and pressure in value form in every precision: a uniform
-    // field (FP64 noise below the FP32 resolution) gives uniform faces
-    T tl, tr;
-    reconstruct(w, st, tl, tr);
-    const double fl = wide(tl), fr = wide(tr);
-    if (v < N + D) {
-      uL[v - N] = fl;
-      uR[v - N] = fr;
-    } else {
-      PL = fl;
-      PR = fr;
-    }
-  }
+  face_velocity_pressure<N, D, T, LW>(m, V, Pb, uL, uR, PL, PR);
   Face<N, D> fL, fR;
   limit_chain<N, D, LW != 2>(m, Ub, Pb, mL, aL, mR, aR, uL, PL, uR, PR, a.energy_limiter, fL, fR,
                     nullptr);
+  if (a.faceL && active && j >= 1 && j <= G - 2 && c < a.n) {
+    const long cell = base + (long)c * a.stride;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      a.faceL[(long)v * a.ncell + cell] = fL.U[v];
+      a.faceR[(long)v * a.ncell + cell] = fR.U[v];
+    }
+  }
   // the face x_{c+1/2}: this lane's fL and the right neighbour's fR
   Face<N, D> fRn;
   shfl_face_down<N, D>(fR, fRn);

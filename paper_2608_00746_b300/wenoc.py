@@ -95,6 +95,7 @@ _SIGS = {
     "wc_prim_to_cons": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "wc_cons_to_prim": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "wc_rhs": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "wc_faces": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "wc_compute_dt": (ctypes.c_int, [_VP, ctypes.c_double, _VP, _VP]),
     "wc_rhs_pf": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, _VP, _VP]),
     "wc_rk_step": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -288,6 +289,15 @@ class Grid:
         L = torch.empty_like(U) if L is None else L
         self._check(lib().wc_rhs(self.h, _ptr(U), _ptr(L), _stream(stream)))
         return L
+
+    def faces(self, U, direction, stream=None):
+        """The limited conservative face states (U^L_{i+1/2}, U^R_{i-1/2}) of
+        one direction's sweep, each shaped like U."""
+        UL = torch.empty_like(U)
+        UR = torch.empty_like(U)
+        self._check(lib().wc_faces(self.h, int(direction), _ptr(U), _ptr(UL), _ptr(UR),
+                                   _stream(stream)))
+        return UL, UR
 
     def rhs_pf(self, U, Q, L=None, dt_limit=0.0, stream=None):
         """Phase-Field step operator (Eq. 5) for auxiliary fields Q [N][...];

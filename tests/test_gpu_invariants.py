@@ -13,10 +13,18 @@ from gpu_util import grids, l1_group, to_dev
 
 pytestmark = pytest.mark.gpu
 MODES = ["fp64", "mixed"]
-# Fractions are bounded to within rounding of their scale: the blends and the
-# conservative update round, so values within 4 ulp of 0 and 1 count as
-# in bounds (no clamping is applied anywhere).
-EPS_BOUND = 4 * 2.0 ** -52
+# Unity sum of the cell averages: 2N 2^-53 per step on top of the initial
+# state's own (Eq. 19 normalises faces, not averages, so each step's
+# rounding stays; tests/test_gpu_bounds.py states the reading).  Bounds hold
+# with no slack (R13).
+U53 = 2.0 ** -53
+
+
+def _sum_err(a):
+    s = a[0].copy()
+    for p in range(1, a.shape[0]):
+        s = s + a[p]
+    return np.abs(s - 1.0).max()
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -64,7 +72,8 @@ def test_equilibrium_bounds_conservation_1d(gpu, mode):
     in [0, 1] summing to one, mass/momentum/energy conserved (periodic)."""
     c = inputs.interface_advection_1d(n=200)
     go, g = grids(c, precision=mode)
-    U = to_dev(oracle.prim_to_cons(go, c.V))
+    U0 = oracle.prim_to_cons(go, c.V)
+    U = to_dev(U0)
     g.bind(U)
     tot0 = U.sum(dim=1)
     g.rk_step(cfl=0.5, nsteps=50)
@@ -74,9 +83,10 @@ def test_equilibrium_bounds_conservation_1d(gpu, mode):
     assert np.abs(V[2] - 1.0).max() < 5e-11
     # FP64: the rho E round-off floor; mixed: FP32 flux remainders on top
     assert np.abs(V[3] - 1e5).max() / scale < (1e-14 if mode == "fp64" else 1e-13)
-    a = V[4:]
-    assert a.min() >= -EPS_BOUND and a.max() <= 1.0 + EPS_BOUND
-    assert np.abs(a.sum(0) - 1.0).max() < 1e-13
+    A = U.cpu().numpy()
+    a = A[4:]
+    assert A[:2].min() >= 0.0 and a.min() >= 0.0 and a.max() <= 1.0
+    assert _sum_err(a) <= _sum_err(U0[4:]) + 2 * 2 * U53 * 50
     tot = U.sum(dim=1)
     rel = ((tot - tot0).abs() / U.abs().sum(dim=1).clamp_min(1e-300)).cpu().numpy()
     assert (rel[:5] < 1e-13).all(), rel
@@ -93,12 +103,12 @@ def test_mixed_mode_l1_vs_fp64_oracle(gpu):
     for _ in range(10):
         U_or, dt = oracle.rk3_step(go, U_or, cfl=0.2)
         g.rk_step(dt=dt)
-    err = l1_group(U.cpu().numpy(), U_or, case.N, case.dim)
+    A = U.cpu().numpy()
+    err = l1_group(A, U_or, case.N, case.dim)
     assert (err <= 1e-5).all(), err
-    V = g.cons_to_prim(U).cpu().numpy()
-    a = V[-2:]
-    assert a.min() >= -EPS_BOUND and a.max() <= 1.0 + EPS_BOUND
-    assert np.abs(a.sum(0) - 1).max() < 1e-13
+    a = A[-2:]
+    assert A[:2].min() >= 0.0 and a.min() >= 0.0 and a.max() <= 1.0
+    assert _sum_err(a) <= _sum_err(oracle.prim_to_cons(go, case.V)[-2:]) + 2 * 2 * U53 * 10
 
 
 def test_rerun_bitwise_deterministic(gpu):

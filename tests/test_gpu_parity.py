@@ -108,6 +108,15 @@ def test_limit_parity(gpu, N, seed):
         assert (err <= 1e-12).all(), err
     # theta = fbar/(fbar - m) amplifies rounding of m when fbar - m is small
     assert np.abs(TH - TH_or)[:, ok].max() <= 1e-9
+    # Eq. 8 at every limited face, knife-edge cells included, with no slack:
+    # masses >= 0, fractions in [0, 1], unity sum to 2N 2^-53
+    for A in (UL, UR):
+        a = A[N + d + 1:]
+        s = a[0].copy()
+        for p in range(1, N):
+            s = s + a[p]
+        assert A[:N].min() >= 0.0 and a.min() >= 0.0 and a.max() <= 1.0
+        assert np.abs(s - 1.0).max() <= 2 * N * 2.0 ** -53
 
 
 def test_limit_degenerate_face_exact(gpu):
