@@ -3,28 +3,30 @@
 
 A step is one SSP-RK3 time step (three stages of the whole hot path: time-step
 reduction, cons->prim, WENO-W reconstruction, WENO-C limiter chain, Riemann
-flux, conservative update) on the 2-D two-phase shock-bubble workload,
-1024 x 512 cells, N = 2 (air bubble in water hit by a planar shock, seeded),
-inputs resident in device memory.  The metric is Mcell-updates/s per RK stage:
-interior cells x 3 stages / step time.
+flux, conservative update), inputs resident in device memory.  The metric is
+Mcell-updates/s per RK stage: interior cells x 3 stages / step time.
+
+Headline (``value``): the learned-weight workload, 2-D circles and a planar
+shock, 2048 x 2048 cells, N = 3 -- the one workload on which all three forms
+of the metric exist: plain FP64 (``value``), the mixed precision and the
+learned surrogate (``modes``), each with its L1 distance to the FP64 solution
+after the same steps (matched accuracy).  ``configs`` carries the other
+workloads with the same timing rules: the 1-D slab (a CUDA graph of 1,000
+steps), the 1024 x 512 shock-bubble (N = 2), the 256^3 spheres and shock
+(N = 3) and the 4,096 batched patches (graph replay, autotuned schedule),
+each in FP64 and mixed precision with the L1 between them and the roofline
+fraction of its sweeps.  Before the timed region the surrogate is trained on
+the GPU from shock-bubble and 3-D states (``--no-learned`` skips the learned
+lines); the scheme variants and the Phase-Field time step follow
+(``--no-variants``).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Beside the FP64 headline the line carries the mixed and learned precisions
-on the same workload (speed and group L1 against FP64 after the same steps),
-the learned-weight workload (2-D circles and shock, 2048 x 2048, N = 3) in all
-three precisions, and the surrogate's training record: before the timed
-region the surrogate is trained on the GPU from shock-bubble and 3-D
-spheres-and-shock states (``--no-learned`` skips all of this).  The scheme
-variants follow (``--no-variants`` skips them): WENO-C, WENO-CL and the
-WENO-W / WENO-JS comparison schemes on the Sec. 4.1.1 advection, the Kapila
-model, and the full time step with the Phase-Field mechanism (Eq. 28, the
-Q-map of Eq. 4, the Phase-Field step) on the headline workload.
-
-``--impl reference`` times the FP64 CPU oracle on this host's cores on the same
-workload (the oracle is the only other implementation of the method).
-Under torchrun each rank runs an independent replica (the workload has no
-exchange step on one GPU per problem); value = all cells updated / max time.
+``--impl reference`` times the FP64 CPU oracle on this host's cores on the
+headline workload (the oracle is the only other implementation of the
+method).  Under torchrun each rank runs an independent replica of the
+headline (the workload has no exchange step on one GPU per problem); value =
+all cells updated / max time over ranks.
 """
 from __future__ import annotations
 
@@ -34,6 +36,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -42,39 +45,44 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Mcell-updates/s per RK stage"
-WORKLOAD = "shock_bubble_2d 1024x512 N=2 HLL CFL 0.2 reflective (seeded)"
+WORKLOAD = ("circles_shock_2d {n}x{n} N=3 HLL CFL 0.2 outflow (64 circles, radii 10-80 "
+            "cells, shock ratio 1e3, seeded): FP64 value, mixed and learned in modes")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--nx", type=int, default=1024)
-    ap.add_argument("--ny", type=int, default=512)
+    ap.add_argument("--n5", type=int, default=2048, help="edge of the headline circles grid")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the surrogate training and the learned-precision lines")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (slab, shock-bubble, 3-D, patches)")
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--train-batch", type=int, default=16384)
     ap.add_argument("--tau", type=float, default=1e-4)
-    ap.add_argument("--n3d", type=int, default=256, help="edge of the 3-D training source")
-    ap.add_argument("--n5", type=int, default=2048, help="edge of the 2-D circles workload")
-    ap.add_argument("--steps5", type=int, default=20)
+    ap.add_argument("--n3d", type=int, default=256, help="edge of the 3-D workload")
+    ap.add_argument("--steps3d", type=int, default=7, help="timed steps of the 3-D workload")
+    ap.add_argument("--npatch", type=int, default=4096)
+    ap.add_argument("--steps4", type=int, default=6, help="timed steps of the patches")
     ap.add_argument("--n-adv", type=int, default=2048,
                     help="edge of the Sec. 4.1.1 advection grid that times the scheme variants")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the scheme variants (WENO-CL, WENO-W, WENO-JS, Kapila)")
     ap.add_argument("--profile", action="store_true",
-                    help="only the timed steps of one precision (a short run for profilers); "
-                         "prints the per-launch sweep time")
+                    help="only the timed steps of one precision on the headline workload "
+                         "(a short run for profilers); prints the per-launch sweep time")
     ap.add_argument("--profile-precision", default="fp64", choices=["fp64", "mixed"],
                     help="precision of the --profile run")
+    ap.add_argument("--profile-n", type=int, default=0,
+                    help="edge of the --profile grid (0: the headline's)")
     ap.add_argument("--profile-pf", action="store_true",
-                    help="only full time steps with the Phase-Field mechanism on the headline "
-                         "workload (--steps of them after --warmup), for profilers")
+                    help="only full time steps with the Phase-Field mechanism on the "
+                         "shock-bubble (--steps of them after --warmup), for profilers")
     ap.add_argument("--profile-mlp", action="store_true",
                     help="only the surrogate kernels on the circles state (inference of one "
                          "direction, one training step of train_batch rows), for profilers")
@@ -88,33 +96,42 @@ def dist_env():
     return ws, rank, local
 
 
-def make_case(args, rank):
+def make_case(args, rank, n=None):
     from paper_2608_00746_b300 import inputs
-    return inputs.shock_bubble_2d(nx=args.nx, ny=args.ny, seed=args.seed + rank)
+    return inputs.circles_shock_2d(n=n or args.n5, seed=args.seed + rank)
 
 
 def config_dict(args, ws, flush):
-    return {"workload": WORKLOAD, "cells": args.nx * args.ny, "nphase": 2, "dim": 2,
+    return {"workload": WORKLOAD.format(n=args.n5), "cells": args.n5 * args.n5, "nphase": 3,
+            "dim": 2,
             "flux": "hll", "cfl": 0.2, "step": "one SSP-RK3 step (3 stages)",
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
             "l2": flush}
 
 
 # ---------------------------------------------------------------- reference arm
-def oracle_step_rate(case, nsteps, warm=0):
-    """The FP64 CPU oracle as it stands, on this host's cores."""
+def oracle_step_rate(case, nsteps, warm=0, threads=0):
+    """The FP64 CPU oracle as it stands, on this host's cores (threads > 0:
+    that many)."""
     import oracle
     g = oracle.Grid(case.shape, case.dx, case.gamma, case.pinf, case.D, flux=case.flux,
                     bc=case.bc)
-    U = oracle.prim_to_cons(g, case.V)
-    for _ in range(warm):
-        U, _ = oracle.rk3_step(g, U, cfl=case.cfl)
-    t0 = time.perf_counter()
-    for _ in range(nsteps):
-        U, _ = oracle.rk3_step(g, U, cfl=case.cfl)
-    dt = time.perf_counter() - t0
+    all_threads = oracle.num_threads()
+    if threads > 0:
+        oracle.set_num_threads(threads)
+    try:
+        U = oracle.prim_to_cons(g, case.V)
+        for _ in range(warm):
+            U, _ = oracle.rk3_step(g, U, cfl=case.cfl)
+        used = oracle.num_threads()
+        t0 = time.perf_counter()
+        for _ in range(nsteps):
+            U, _ = oracle.rk3_step(g, U, cfl=case.cfl)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(all_threads)
     cells = int(np.prod(case.shape))
-    return cells * 3 * nsteps / dt / 1e6, dt, oracle.num_threads(), U
+    return cells * 3 * nsteps / dt / 1e6, dt, used, U
 
 
 def run_reference(args):
@@ -148,7 +165,7 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"wenoc_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -209,9 +226,10 @@ def csrc_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(kernel_hash):
-    """DRAM bytes per sweep launch from the committed ncu summary, when it was
-    taken on the current kernel sources."""
+def traffic_from_profile(kernel_hash, workload):
+    """DRAM bytes per sweep launch of the roofline kernel on this workload from
+    the committed ncu summary, when it was taken on the current kernel
+    sources."""
     p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     if not os.path.exists(p):
         return None
@@ -219,7 +237,7 @@ def traffic_from_profile(kernel_hash):
         d = json.load(open(p))
     except Exception:
         return None
-    if d.get("csrc_hash") != kernel_hash:
+    if d.get("csrc_hash") != kernel_hash or d.get("workload") != workload:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -294,14 +312,10 @@ def run_ours(args):
             tdist.barrier()
         torch.cuda.synchronize()
 
-    case = make_case(args, rank)
-    N, D = case.N, case.dim
-    cells = int(np.prod(case.shape))
     learned = not (args.no_learned or args.profile or args.profile_pf)
     S, train_info = train_surrogate(args, dev) if learned else (None, None)
 
-    def make_grid(precision, c=None, counters=None, scheme="c", kmodel="allaire"):
-        c = c or case
+    def make_grid(precision, c, counters=None, scheme="c", kmodel="allaire"):
         g = wenoc.Grid(c.shape, c.dx, c.gamma, c.pinf, c.D, flux=c.flux, bc=c.bc,
                        precision=precision, scheme=scheme, kmodel=kmodel)
         if precision == "learned":
@@ -314,13 +328,12 @@ def run_ours(args):
     # L2 flush buffer (larger than the 126 MB L2), written between timed steps
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
-    def timed_steps(g, K, W, c=None, dt=0.0):
+    def timed_steps(g, K, W, c, dt=0.0):
         """K timed RK steps (events per step, L2 flushed in between) and the
         mean duration of the sweep launches inside them (event pairs the
         library records around each direction's launches on the same
         stream: the sweep, preceded in learned precision by the surrogate).
         dt > 0: fixed time step, else from the CFL number on the device."""
-        c = c or case
         for _ in range(W):
             g.rk_step(cfl=c.cfl, dt=dt)
         barrier()
@@ -341,12 +354,14 @@ def run_ours(args):
         return total / K, tot_sw / max(nl, 1)  # ms per step, ms per sweep launch
 
     if args.profile_pf:
-        g, U = make_grid("fp64")
+        from paper_2608_00746_b300 import inputs
+        cb = inputs.shock_bubble_2d(nx=1024, ny=512, seed=args.seed)
+        g, U = make_grid("fp64", cb)
         g.set_pf_workspace(U.device)
-        g.step(cfl=case.cfl, nsteps=args.warmup, tol=1e-12)
+        g.step(cfl=cb.cfl, nsteps=args.warmup, tol=1e-12)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        g.step(cfl=case.cfl, nsteps=args.steps, tol=1e-12)
+        g.step(cfl=cb.cfl, nsteps=args.steps, tol=1e-12)
         torch.cuda.synchronize()
         ms = (time.perf_counter() - t0) * 1e3 / max(args.steps, 1)
         g.sync_status()
@@ -359,58 +374,40 @@ def run_ours(args):
         return 0
 
     if args.profile:
-        g, U = make_grid(args.profile_precision)
-        ms, sw = timed_steps(g, args.steps, args.warmup)
+        cp = make_case(args, 0, n=args.profile_n or None)
+        g, U = make_grid(args.profile_precision, cp)
+        ms, sw = timed_steps(g, args.steps, args.warmup, cp)
         print(json.dumps({"profile": True, "precision": args.profile_precision,
-                          "ms_per_step": ms, "sweep_ms_per_launch": sw,
-                          "steps": args.steps, "warmup": args.warmup}), flush=True)
+                          "cells": int(np.prod(cp.shape)), "ms_per_step": ms,
+                          "sweep_ms_per_launch": sw, "steps": args.steps,
+                          "warmup": args.warmup}), flush=True)
         return 0
 
-    # FP64 DFMA probe of this GPU (context for the derived peak below)
+    case = make_case(args, rank)
+    N, D = case.N, case.dim
+    cells = int(np.prod(case.shape))
+    peak64 = roofline.PEAK_FP64_TFLOPS
+    peak32 = roofline.PEAK_FP32_TFLOPS
+    peak_bf16 = measured_bf16_peak()
+    # FP64 DFMA probe of this GPU (context for the unit-count peak)
     peak_probe = wenoc.fp64_peak() / 1e12
 
     modes = ("fp64", "mixed", "learned") if learned else ("fp64", "mixed")
     results = {}
-    c5 = None
-    res5 = {}
+    configs = {}
+    infer = None
     with Clocks(local) as clk:
         time.sleep(1.0)  # let the sampler start before the timed region
         for prec in modes:
-            g, U = make_grid(prec)
-            ms, sw = timed_steps(g, args.steps, args.warmup)
-            results[prec] = (ms, sw)
+            g, U = make_grid(prec, case)
+            results[prec] = timed_steps(g, args.steps, args.warmup, case)
             del g, U
         if learned and rank == 0:
-            # the learned-weight workload: 2-D circles and shock, N = 3
-            from paper_2608_00746_b300 import inputs
-            c5 = inputs.circles_shock_2d(n=args.n5, seed=args.seed)
-            for prec in modes:
-                g, U = make_grid(prec, c5)
-                res5[prec] = timed_steps(g, args.steps5, 3, c5)
-                del g, U
-            # the surrogate's inference kernel alone (one direction)
-            g, U = make_grid("mixed", c5)
-            W5 = torch.empty((18, g.ncell), dtype=torch.float32, device=dev)
-            st5 = torch.zeros(1, dtype=torch.int32, device=dev)
-            for _ in range(3):
-                g.mlp_infer(U, 0, S.params, W5, st5)
-            barrier()
-            s_ = torch.cuda.current_stream()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(s_)
-            for _ in range(10):
-                g.mlp_infer(U, 0, S.params, W5, st5)
-            e1.record(s_)
-            barrier()
-            infer_ms = e0.elapsed_time(e1) / 10
-            infer_rows = 2 * g.ncell
-            del g, U, W5
+            infer = time_inference(case, S, make_grid, barrier, dev)
+        if rank == 0 and not args.no_configs:
+            configs = run_configs(args, make_grid, timed_steps, barrier, dev, learned)
         variants = run_variants(args, rank, make_grid, timed_steps)
     clocks = clk.summary()
-    # FP64 peak from unit counts and clock: 2 DFMA per clock per SM (ncu's
-    # sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained = 296 per
-    # cycle on 148 SMs), 2 flops each, at the maximum SM clock 2032 MHz.
-    peak_fp64 = 2 * 2 * 148 * 2032e6 / 1e12
 
     def matched_l1(c, K):
         """Reduced modes against FP64 after K steps from the same initial
@@ -430,14 +427,13 @@ def run_ours(args):
         acc = (1.0 - fb / dec) if dec else None
         for g, _ in others.values():
             g.sync_status()
+        del g64, U64, others
         return out, acc
 
-    # matched accuracy on the headline workload
-    l1s, acc2 = matched_l1(case, args.steps)
-    l1 = l1s["mixed"]
+    l1s, acc = matched_l1(case, args.steps)
 
     # end to end through the C ABI with host buffers: upload, step, download
-    g, U = make_grid("fp64")
+    g, U = make_grid("fp64", case)
     host = torch.empty(U.numel(), dtype=torch.float64, pin_memory=True)
     host.copy_(U.reshape(-1).cpu())
     nbytes = U.numel() * 8
@@ -452,42 +448,52 @@ def run_ours(args):
     e1.record(s)
     barrier()
     e2e_ms = e0.elapsed_time(e1) / args.steps
+    del g, U, host
 
-    ms64, sw64 = results["fp64"]
-    msmx, swmx = results["mixed"]
-    msl = results["learned"][0] if learned else 0.0
+    ms = {prec: results[prec][0] for prec in modes}
+    sw = {prec: results[prec][1] for prec in modes}
     # max over ranks (replicas: the job takes as long as the slowest rank)
-    ms64, msmx, e2e_ms, msl = replicas.max_over_ranks([ms64, msmx, e2e_ms, msl], device=dev)
-    value = replicas.weak_value(ws, cells, 3, ms64)
-    value_mx = replicas.weak_value(ws, cells, 3, msmx)
+    vals = replicas.max_over_ranks([ms[p] for p in modes] + [e2e_ms], device=dev)
+    ms = dict(zip(modes, vals[:len(modes)]))
+    e2e_ms = vals[len(modes)]
+    value = replicas.weak_value(ws, cells, 3, ms["fp64"])
     e2e = replicas.weak_value(ws, cells, 3, e2e_ms)
 
-    fl = roofline.flops_per_cell_dir(N, D, hllc=False)
-    achieved = fl * cells / (sw64 * 1e-3) / 1e12
+    fl = roofline.flops_per_cell_dir(N, D, "hll")
+    achieved = fl * cells / (sw["fp64"] * 1e-3) / 1e12
     khash = csrc_hash()
-    traffic = traffic_from_profile(khash)
-
+    traffic = traffic_from_profile(khash, f"circles_shock_2d {args.n5}x{args.n5}")
+    mode_lines = {"fp64": {"value": round(value, 3), "ms_per_step": round(ms["fp64"], 4),
+                           "ms_per_direction": round(sw["fp64"], 4)}}
+    rl_modes = {}
+    for prec in modes[1:]:
+        v = replicas.weak_value(ws, cells, 3, ms[prec])
+        mode_lines[prec] = {"value": round(v, 3), "ms_per_step": round(ms[prec], 4),
+                            "ms_per_direction": round(sw[prec], 4),
+                            "speedup_vs_fp64": round(ms["fp64"] / ms[prec], 3),
+                            "l1_rel_vs_fp64_max_var": l1s[prec], "l1_steps": args.steps}
+        rl_modes[prec] = mode_roofline(N, D, cells, sw[prec], peak64, peak32, peak_bf16,
+                                       learned=prec == "learned")
+    if learned:
+        mode_lines["learned"].update({"tau": args.tau, "accepted_face_sides": acc})
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mcell/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms64, 4),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms["fp64"], 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded shock-bubble initial condition)",
+        "data": "synthetic (seeded circles-and-shock initial condition)",
         "config": config_dict(args, ws, "flushed between timed steps (256 MB write)"),
-        "modes": {
-            "fp64": {"value": round(value, 3), "ms_per_step": round(ms64, 4)},
-            "mixed": {"value": round(value_mx, 3), "ms_per_step": round(msmx, 4),
-                      "speedup_vs_fp64": round(value_mx / value, 3),
-                      "l1_rel_vs_fp64_max_var": l1, "l1_steps": args.steps},
-        },
+        "modes": mode_lines,
         "roofline": {
-            "bound": "alu", "kernel": "k_sweep_win<N=2,D=2,double> (window direction sweep)",
-            "achieved": round(achieved, 4), "peak": round(peak_fp64, 4), "unit": "TFLOP/s",
-            "frac": round(achieved / peak_fp64, 4), "traffic": traffic,
-            "peak_source": "unit count x clock: 2 DFMA/clk/SM x 2 flop x 148 SM x 2032 MHz",
+            "bound": "alu", "kernel": "k_sweep_win<N=3,D=2,double> (window direction sweep)",
+            "achieved": round(achieved, 4), "peak": round(peak64, 4), "unit": "TFLOP/s",
+            "frac": round(achieved / peak64, 4), "traffic": traffic,
+            "peak_source": "unit count x clock: 2 DFMA/clk/SM x 2 flop x 148 SM x 2032 MHz "
+                           "(MEASURED_PEAKS.json has no FP64 figure)",
             "peak_probe_measured": round(peak_probe, 4),
-            "flops_per_cell_dir": fl, "sweep_ms_per_launch": round(sw64, 4),
-            "sweep_ms_per_launch_mixed": round(swmx, 4),
+            "flops_per_cell_dir": fl, "flops_source": "oracle op counter (op_counts.json)",
+            "sweep_ms_per_launch": round(sw["fp64"], 4),
             "hbm_bytes_per_cell_stage_min": roofline.bytes_per_cell_stage(N, D),
+            "modes": rl_modes,
         },
         "clocks": clocks,
         "e2e": {"value": round(e2e, 3), "unit": "Mcell/s", "h2d_bytes_per_step": nbytes,
@@ -496,46 +502,15 @@ def run_ours(args):
         "csrc_hash": khash,
     }
     if learned:
-        line["modes"]["learned"] = {
-            "value": round(replicas.weak_value(ws, cells, 3, msl), 3), "ms_per_step": round(msl, 4),
-            "speedup_vs_fp64": round(ms64 / msl, 3), "l1_rel_vs_fp64_max_var": l1s["learned"],
-            "l1_steps": args.steps, "tau": args.tau, "accepted_face_sides": acc2,
-            "ms_per_direction": round(results["learned"][1], 4)}
         line["surrogate_training"] = train_info
-    if learned and rank == 0:
-        l1_5, acc5 = matched_l1(c5, args.steps5)
-        cells5 = int(np.prod(c5.shape))
-        w5 = {}
-        for prec in modes:
-            ms5, sw5 = res5[prec]
-            w5[prec] = {"value": round(cells5 * 3 / (ms5 * 1e-3) / 1e6, 3),
-                        "ms_per_step": round(ms5, 4), "ms_per_direction": round(sw5, 4)}
-            if prec != "fp64":
-                w5[prec]["l1_rel_vs_fp64_max_var"] = l1_5[prec]
-                w5[prec]["speedup_vs_fp64"] = round(res5["fp64"][0] / ms5, 3)
-        w5["learned"]["tau"] = args.tau
-        w5["learned"]["accepted_face_sides"] = acc5
-        fl_row = 2 * (30 * 64 + 64 * 64 * 2 + 64 * 9)
-        infer_tf = fl_row * infer_rows / (infer_ms * 1e-3) / 1e12
-        w5["surrogate_inference"] = {
-            "kernel": "k_mlp_fwd<SrcState<3,2>> (feature gather + 4 tcgen05 layers)",
-            "rows": infer_rows, "ms_per_launch": round(infer_ms, 4),
-            "achieved_tflops": round(infer_tf, 2), "flops_per_row": fl_row,
-            "frac_of_bf16_measured": round(infer_tf / 1794.1, 4)}
-        line["learned_workload"] = {
-            "workload": f"circles_shock_2d {args.n5}x{args.n5} N=3 HLL CFL 0.2 outflow "
-                        "(64 circles, radii 10-80 cells, shock ratio 1e3, seeded)",
-            "steps": args.steps5, "l1_steps": args.steps5, "modes": w5}
+    if infer:
+        line["surrogate_inference"] = infer
+    if configs:
+        line["configs"] = configs
     if variants:
         line["scheme_variants"] = variants
     if rank == 0 and not args.no_cpu_baseline:
-        try:
-            small = make_case(args, 0)
-            v, t, cores, _ = oracle_step_rate(small, 2)
-            line["cpu_baseline"] = {"value": round(v, 4), "unit": "Mcell/s", "cores": cores,
-                                    "kind": "oracle", "sample": "full grid, 2 RK3 steps"}
-        except Exception as e:  # the oracle must be built on the host
-            line["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+        line["cpu_baseline"] = cpu_baselines(args, case)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -543,12 +518,240 @@ def run_ours(args):
     return 0
 
 
+def measured_bf16_peak():
+    """Dense BF16 peak (TFLOP/s) from MEASURED_PEAKS.json when present (the
+    burst figure: the inference is timed alone), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"])
+    except Exception:
+        return 1800.0
+
+
+def mode_roofline(N, D, cells, ms_dir, peak64, peak32, peak_bf16, learned=False):
+    """Roofline of one direction of the reduced-precision forms: the FP64 and
+    FP32 flops of the oracle's count split as the mixed form assigns them,
+    each at its pipe's peak, plus (learned) the surrogate's BF16 contraction
+    of both face sides at the measured BF16 peak; the bound is the slowest
+    of those times, and frac = bound time / measured time per direction."""
+    from paper_2608_00746_b300 import roofline
+    f64, f32 = roofline.mixed_split(N, D, "hll")
+    t64 = f64 * cells / (peak64 * 1e12)
+    t32 = f32 * cells / (peak32 * 1e12)
+    ttc = 2 * roofline.MLP_FLOPS_PER_FACE_SIDE * cells / (peak_bf16 * 1e12) if learned else 0.0
+    t = max(t64, t32, ttc)
+    bound = "alu (fp64)" if t == t64 else ("alu (fp32)" if t == t32 else "tensor (bf16)")
+    return {"bound": bound, "fp64_flops_per_cell_dir": f64, "fp32_flops_per_cell_dir": f32,
+            "tensor_flops_per_cell_dir": 2 * roofline.MLP_FLOPS_PER_FACE_SIDE if learned else 0,
+            "t_fp64_ms": round(t64 * 1e3, 4), "t_fp32_ms": round(t32 * 1e3, 4),
+            "t_tensor_ms": round(ttc * 1e3, 4), "ms_per_direction": round(ms_dir, 4),
+            "frac": round(t * 1e3 / ms_dir, 4),
+            "peaks_tflops": {"fp64": round(peak64, 3), "fp32": round(peak32, 3),
+                             "bf16_measured": peak_bf16}}
+
+
+def time_inference(case, S, make_grid, barrier, dev):
+    """The surrogate's inference kernel alone, one direction of the headline."""
+    import torch
+    from paper_2608_00746_b300 import roofline
+    g, U = make_grid("mixed", case)
+    W5 = torch.empty((18, g.ncell), dtype=torch.float32, device=dev)
+    st5 = torch.zeros(1, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        g.mlp_infer(U, 0, S.params, W5, st5)
+    barrier()
+    s_ = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s_)
+    for _ in range(10):
+        g.mlp_infer(U, 0, S.params, W5, st5)
+    e1.record(s_)
+    barrier()
+    ms = e0.elapsed_time(e1) / 10
+    rows = 2 * g.ncell
+    fl_row = roofline.MLP_FLOPS_PER_FACE_SIDE
+    tf = fl_row * rows / (ms * 1e-3) / 1e12
+    peak = measured_bf16_peak()
+    return {"kernel": "k_mlp_fwd<SrcState<3,2>> (feature gather + 4 tcgen05 layers)",
+            "rows": rows, "ms_per_launch": round(ms, 4), "achieved_tflops": round(tf, 2),
+            "flops_per_row": fl_row, "frac_of_bf16_measured": round(tf / peak, 4)}
+
+
+def run_configs(args, make_grid, timed_steps, barrier, dev, learned):
+    """The other workloads, FP64 and mixed precision (and learned on the
+    shock-bubble), each with the L1 of mixed against FP64 after the timed
+    steps' count and the roofline fraction of its FP64 sweeps."""
+    import torch
+    from paper_2608_00746_b300 import inputs, roofline, wenoc
+    peak64 = roofline.PEAK_FP64_TFLOPS
+    out = {}
+
+    def line(c, res, K, flux="hll", extra=None):
+        cells = int(np.prod(c.shape))
+        N, D = c.N, c.dim
+        d = {}
+        for prec, (ms, sw) in res.items():
+            d[prec] = {"value": round(cells * 3 / (ms * 1e-3) / 1e6, 3),
+                       "ms_per_step": round(ms, 4), "ms_per_direction": round(sw, 4)}
+        fl = roofline.flops_per_cell_dir(N, D, flux)
+        d["fp64"]["frac"] = round(fl * cells / (res["fp64"][1] * 1e-3) / 1e12 / peak64, 4)
+        d["mixed"]["speedup_vs_fp64"] = round(res["fp64"][0] / res["mixed"][0], 3)
+        if extra:
+            d.update(extra)
+        d["steps"] = K
+        return d
+
+    def l1_pair(c, K, flux_dt=None):
+        g64, U64 = make_grid("fp64", c)
+        gm, Um = make_grid("mixed", c)
+        for _ in range(K):
+            dt = g64.rk_step(cfl=c.cfl, dt=flux_dt or 0.0, want_dt=True)
+            gm.rk_step(dt=dt)
+        gm.sync_status()
+        g64.sync_status()
+        return group_l1(U64, Um, c.N, c.dim)
+
+    # config 2: 2-D shock-bubble 1024 x 512, N = 2 (all three forms)
+    c2 = inputs.shock_bubble_2d(nx=1024, ny=512, seed=args.seed)
+    res = {}
+    for prec in (("fp64", "mixed", "learned") if learned else ("fp64", "mixed")):
+        g, U = make_grid(prec, c2)
+        res[prec] = timed_steps(g, args.steps, 3, c2)
+        del g, U
+    d2 = line(c2, res, args.steps)
+    d2["mixed"]["l1_rel_vs_fp64_max_var"] = l1_pair(c2, args.steps)
+    if learned:
+        d2["learned"]["speedup_vs_fp64"] = round(res["fp64"][0] / res["learned"][0], 3)
+    out["shock_bubble_2d"] = dict(workload="shock_bubble_2d 1024x512 N=2 HLL CFL 0.2 "
+                                  "reflective (seeded)", **d2)
+
+    # config 3: 3-D spheres and shock, 256^3, N = 3
+    c3 = inputs.spheres_shock_3d(n=args.n3d, seed=args.seed)
+    res = {}
+    for prec in ("fp64", "mixed"):
+        g, U = make_grid(prec, c3)
+        res[prec] = timed_steps(g, args.steps3d, 2, c3)
+        del g, U
+        torch.cuda.empty_cache()
+    d3 = line(c3, res, args.steps3d)
+    d3["mixed"]["l1_rel_vs_fp64_max_var"] = l1_pair(c3, args.steps3d)
+    out["spheres_shock_3d"] = dict(workload=f"spheres_shock_3d {args.n3d}^3 N=3 HLL CFL 0.2 "
+                                   "outflow (16 spheres, shock ratio 1e3, seeded)", **d3)
+    del c3
+    torch.cuda.empty_cache()
+
+    # config 1: the 1-D slab, a CUDA graph of 1,000 steps replayed
+    c1 = inputs.interface_advection_1d(n=200)
+    res = {}
+    states = {}
+    for prec in ("fp64", "mixed"):
+        g, U = make_grid(prec, c1)
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            dt1 = g.rk_step(cfl=c1.cfl, nsteps=1, want_dt=True)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=st):
+            g.rk_step(dt=dt1, nsteps=1000)
+        graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        g.sync_status()
+        ms = e0.elapsed_time(e1) / 1000
+        res[prec] = (ms, ms / 3)
+        states[prec] = U
+    d1 = line(c1, res, 2001, flux="hllc")
+    d1["mixed"]["l1_rel_vs_fp64_max_var"] = group_l1(states["fp64"], states["mixed"], 2, 1)
+    V = {p: g.cons_to_prim(states[p]).cpu().numpy() for p in states}
+    d1["equilibrium_after_2001_steps"] = {
+        p: {"u_dev_max": float(np.abs(V[p][2] - 1.0).max()),
+            "P_dev_max_of_scale": float(np.abs(V[p][3] - 1e5).max() / (1e5 + 6e8))}
+        for p in V}
+    out["interface_advection_1d"] = dict(
+        workload="interface_advection_1d 200 cells N=2 HLLC CFL 0.5 periodic (CUDA graph "
+                 "of 1000 steps; latency-bound)", **d1)
+
+    # config 4: 4,096 batched patches, graph replay, autotuned schedule
+    from paper_2608_00746_b300 import autotune
+    edges, pstates, (gm_, pi_, Dm_) = inputs.patch_batch(npatch=args.npatch, seed=args.seed)
+    res = {}
+    finals = {}
+    sched = {}
+    for prec in ("fp64", "mixed"):
+        P = wenoc.Patches(edges, gm_, pi_, Dm_, precision=prec)
+        V4 = torch.from_numpy(P.pack(pstates)).to(dev)
+        U4 = P.prim_to_cons(V4)
+        del V4
+        P.bind(U4)
+        U_init = U4.clone()
+        sched[prec] = autotune.tuned_schedule(P, 0.2, prec, "hll", 3, steps=2)
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            P.rk_step(cfl=0.2, nsteps=1, use_graph=True)   # captures the step graph
+        torch.cuda.synchronize()
+        U4.copy_(U_init)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            P.rk_step(cfl=0.2, nsteps=args.steps4, use_graph=True)
+            e1.record(st)
+        torch.cuda.synchronize()
+        P.sync_status()
+        ms = e0.elapsed_time(e1) / args.steps4
+        res[prec] = (ms, ms / 3)
+        finals[prec] = U4
+        del U_init, P
+    ncell4 = finals["fp64"].shape[1]
+    fl = roofline.flops_per_cell_dir(3, 3, "hll")
+    d4 = {}
+    for prec, (ms, _) in res.items():
+        d4[prec] = {"value": round(ncell4 * 3 / (ms * 1e-3) / 1e6, 3), "ms_per_step": round(ms, 4),
+                    "schedule": sched[prec]}
+    d4["fp64"]["frac"] = round(fl * 3 * ncell4 * 3 / (res["fp64"][0] * 1e-3) / 1e12 / peak64, 4)
+    d4["mixed"]["speedup_vs_fp64"] = round(res["fp64"][0] / res["mixed"][0], 3)
+    d4["mixed"]["l1_rel_vs_fp64_max_var"] = group_l1(finals["fp64"], finals["mixed"], 3, 3)
+    d4["steps"] = args.steps4
+    d4["cells"] = int(ncell4)
+    out["patches"] = dict(workload=f"patch_batch {args.npatch} cube patches, edges "
+                          "{8,12,16,24,32}, N=3 HLL CFL 0.2 (dt on the device each step), one "
+                          "persistent launch per stage, CUDA graph replay, autotuned; L1 of "
+                          "mixed against FP64 after the timed steps", **d4)
+    del finals
+    torch.cuda.empty_cache()
+    return out
+
+
+def cpu_baselines(args, case):
+    """The FP64 oracle as it stands on this host: all cores on one RK3 step of
+    the headline grid, and one thread on one step of a 512 x 512 instance of
+    the same workload generator (seeded alike)."""
+    out = {}
+    try:
+        v, t, cores, _ = oracle_step_rate(case, 1)
+        out = {"value": round(v, 4), "unit": "Mcell/s", "cores": cores, "kind": "oracle",
+               "sample": f"one RK3 step of the full {args.n5}x{args.n5} grid ({t:.1f} s)"}
+        small = make_case(args, 0, n=512)
+        v1, t1, c1, _ = oracle_step_rate(small, 1, threads=1)
+        out["single_thread"] = {"value": round(v1, 4), "unit": "Mcell/s", "cores": c1,
+                                "sample": f"one RK3 step of a 512x512 circles-and-shock grid "
+                                          f"({t1:.1f} s)"}
+    except Exception as e:  # the oracle must be built on the host
+        out = {"value": None, "error": str(e)[:200]}
+    return out
+
+
 def run_variants(args, rank, make_grid, timed_steps):
     """The scheme variants, each on its own workload, FP64, same timing as the
     headline: WENO-C, WENO-CL and the WENO-W / WENO-JS comparison schemes on
     the Sec. 4.1.1 air-circle advection (n^2, dt = 0.1 n^-1, the paper's
     1e-3 at n = 100) with the consistency error after the run; the Kapila
-    model on the headline shock-bubble."""
+    model and the full time step with the Phase-Field mechanism on the
+    1024 x 512 shock-bubble."""
     if args.no_variants or rank != 0:
         return None
     from paper_2608_00746_b300 import inputs
@@ -573,24 +776,25 @@ def run_variants(args, rank, make_grid, timed_steps):
                        "consistency_error_max": cons, "temperature_error_max": temp}
         del g, U
     out["advection"] = adv
-    g, U = make_grid("fp64", kmodel="kapila")
-    ms, sw = timed_steps(g, args.steps, 3)
+    cb = inputs.shock_bubble_2d(nx=1024, ny=512, seed=args.seed)
+    g, U = make_grid("fp64", cb, kmodel="kapila")
+    ms, sw = timed_steps(g, args.steps, 3, cb)
     cells_h = int(np.prod(g.shape))
-    out["kapila"] = {"workload": "headline shock-bubble, K_p of the Kapila model",
+    out["kapila"] = {"workload": "shock_bubble_2d 1024x512, K_p of the Kapila model",
                      "value": round(cells_h * 3 / (ms * 1e-3) / 1e6, 3),
                      "ms_per_step": round(ms, 4), "ms_per_direction": round(sw, 4)}
     del g, U
-    out["phase_field"] = time_phase_field(make_grid)
+    out["phase_field"] = time_phase_field(make_grid, cb)
     return out
 
 
-def time_phase_field(make_grid, K=20):
-    """Full time steps of Sec. 2.2 on the headline shock-bubble: the
+def time_phase_field(make_grid, cb, K=20):
+    """Full time steps of Sec. 2.2 on the 1024 x 512 shock-bubble: the
     hyperbolic step, Eq. 28, the Q-map of Eq. 4 (conjugate gradients to a
     D-weighted residual of 1e-12, started from the previous step's Q) and
     the Phase-Field step, FP64; then each part timed alone."""
     import torch
-    g, U = make_grid("fp64")
+    g, U = make_grid("fp64", cb)
     g.set_pf_workspace(U.device)
     g.step(cfl=0.2, nsteps=3, tol=1e-12)
     torch.cuda.synchronize()
@@ -622,8 +826,8 @@ def time_phase_field(make_grid, K=20):
     parts /= 5
     cells = int(np.prod(g.shape))
     del g, U
-    return {"workload": "headline shock-bubble, full time step (hyperbolic + Eq. 28 + Eq. 4 + "
-                        "Phase-Field step), Q-map tolerance 1e-12",
+    return {"workload": "shock_bubble_2d 1024x512, full time step (hyperbolic + Eq. 28 + "
+                        "Eq. 4 + Phase-Field step), Q-map tolerance 1e-12",
             "steps": K, "value": round(cells * 3 / (ms * 1e-3) / 1e6, 3), "unit": "Mcell/s",
             "ms_per_step": round(ms, 4), "qmap_cg_iterations_last": iters,
             "qmap_label_rounds_last": rounds, "qmap_residual_last": res,

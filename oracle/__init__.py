@@ -90,6 +90,7 @@ def lib():
             f.argtypes = args
             f.restype = ctypes.c_int
         for name, args in {
+            "or_set_num_threads": [ctypes.c_int],
             "or_r13_set_stage_tol": [ctypes.c_double],
             "or_r13_reset": [],
             "or_r13_stats": [dp],
@@ -340,6 +341,11 @@ def wenojs_weights(beta, eps):
     w = np.empty(3)
     lib().or_wenojs_weights(_p(beta), eps, _p(w))
     return w
+
+
+def set_num_threads(n):
+    """Threads of the oracle's parallel sweeps (OpenMP)."""
+    lib().or_set_num_threads(int(n))
 
 
 def num_threads():

@@ -104,6 +104,23 @@
 #include <omp.h>
 #endif
 
+/* Operation counting (OR_COUNT, a C++ build with oracle/op_count.hpp forced
+ * in front): OR_CAT(c) attributes the arithmetic of the enclosing scope to
+ * category c.  In the plain C build it expands to nothing. */
+#ifdef OR_COUNT
+extern "C" {
+long long or_op_counts[OR_C_NCAT][OR_K_N];
+void or_op_counts_reset(void) { memset(or_op_counts, 0, sizeof(or_op_counts)); }
+void or_op_counts_read(long long *out) { memcpy(out, or_op_counts, sizeof(or_op_counts)); }
+}
+int or_op_cat = OR_C_OTHER;
+#else
+#define OR_CAT(c)
+#endif
+#ifdef __cplusplus
+extern "C" {
+#endif
+
 #define OR_MAXP 8
 #define OR_MAXV (2 * OR_MAXP + 4)
 
@@ -141,6 +158,15 @@ static int nv(const or_grid *g) { return 2 * g->N + g->dim + 1; }
 
 int or_nv(const or_grid *g) { return nv(g); }
 
+/* Threads of the parallel sweeps (the CPU baselines time 1 and all). */
+void or_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
@@ -150,13 +176,18 @@ int or_num_threads(void) {
 }
 
 /* Eq. 26: A_p = 1/(gamma_p - 1), B_p = gamma_p Pinf_p / (gamma_p - 1). */
-static double eos_A(const or_grid *g, int p) { return 1.0 / (g->gamma[p] - 1.0); }
+static double eos_A(const or_grid *g, int p) {
+  OR_CAT(OR_C_CONST);
+  return 1.0 / (g->gamma[p] - 1.0);
+}
 static double eos_B(const or_grid *g, int p) {
+  OR_CAT(OR_C_CONST);
   return g->gamma[p] * g->pinf[p] / (g->gamma[p] - 1.0);
 }
 
 /* Mixture rules (Sec. 2.1) and the pressure of Eq. 27. */
 static int cons_to_prim(const or_grid *g, const double *U, double *V) {
+  OR_CAT(OR_C_PRIM);
   int N = g->N, d = g->dim;
   double rho = 0.0;
   for (int p = 0; p < N; p++) rho += U[IMASS(p)];
@@ -181,6 +212,7 @@ static int cons_to_prim(const or_grid *g, const double *U, double *V) {
 
 /* psi_{V->U}: rho = sum (alpha rho)_p, rho u, and rho E from Eq. 26. */
 static void prim_to_cons(const or_grid *g, const double *V, double *U) {
+  OR_CAT(OR_C_V2U);
   int N = g->N, d = g->dim;
   double rho = 0.0;
   for (int p = 0; p < N; p++) rho += V[IMASS(p)];
@@ -220,19 +252,25 @@ static double psi_energy(const or_grid *g, const double *U) {
  * quadratic candidates of sub-stencils s = {i-2..i}, {i-1..i+1}, {i..i+2},
  * and their smoothness indicators. */
 void or_weno5_parts(const double *f, double *q, double *beta) {
-  q[0] = (2.0 * f[0] - 7.0 * f[1] + 11.0 * f[2]) / 6.0;
-  q[1] = (-f[1] + 5.0 * f[2] + 2.0 * f[3]) / 6.0;
-  q[2] = (2.0 * f[2] + 5.0 * f[3] - f[4]) / 6.0;
-  double a, b;
-  a = f[0] - 2.0 * f[1] + f[2];
-  b = f[0] - 4.0 * f[1] + 3.0 * f[2];
-  beta[0] = 13.0 / 12.0 * a * a + 0.25 * b * b;
-  a = f[1] - 2.0 * f[2] + f[3];
-  b = f[1] - f[3];
-  beta[1] = 13.0 / 12.0 * a * a + 0.25 * b * b;
-  a = f[2] - 2.0 * f[3] + f[4];
-  b = 3.0 * f[2] - 4.0 * f[3] + f[4];
-  beta[2] = 13.0 / 12.0 * a * a + 0.25 * b * b;
+  {
+    OR_CAT(OR_C_CAND);
+    q[0] = (2.0 * f[0] - 7.0 * f[1] + 11.0 * f[2]) / 6.0;
+    q[1] = (-f[1] + 5.0 * f[2] + 2.0 * f[3]) / 6.0;
+    q[2] = (2.0 * f[2] + 5.0 * f[3] - f[4]) / 6.0;
+  }
+  {
+    OR_CAT(OR_C_BETA);
+    double a, b;
+    a = f[0] - 2.0 * f[1] + f[2];
+    b = f[0] - 4.0 * f[1] + 3.0 * f[2];
+    beta[0] = 13.0 / 12.0 * a * a + 0.25 * b * b;
+    a = f[1] - 2.0 * f[2] + f[3];
+    b = f[1] - f[3];
+    beta[1] = 13.0 / 12.0 * a * a + 0.25 * b * b;
+    a = f[2] - 2.0 * f[3] + f[4];
+    b = 3.0 * f[2] - 4.0 * f[3] + f[4];
+    beta[2] = 13.0 / 12.0 * a * a + 0.25 * b * b;
+  }
 }
 
 static const double weno5_d[3] = {0.1, 0.6, 0.3};
@@ -266,12 +304,14 @@ void or_wenojs_weights(const double *beta, double eps, double *w) {
 }
 
 static void weights(const or_grid *g, const double *beta, double *w) {
+  OR_CAT(OR_C_WEIGHTS);
   if (g->weights == OR_WEIGHTS_JS) or_wenojs_weights(beta, g->js_eps, w);
   else or_wenow_weights(beta, w);
 }
 
 /* Eq. 10: f^L = sum_s omega_s f^(s). */
 static double combine(const double *w, const double *q) {
+  OR_CAT(OR_C_COMBINE);
   return w[0] * q[0] + w[1] * q[1] + w[2] * q[2];
 }
 
@@ -374,6 +414,7 @@ static void consistent_limiter(const or_grid *g, const double *Ubar, double *V) 
 
 static int limit_chain(const or_grid *g, const double *Ubar, double *VL, double *VR,
                        double *UL, double *UR, double *VfL, double *VfR, double *th) {
+  OR_CAT(OR_C_LIMIT);
   int N = g->N, nvar = nv(g);
   double th17 = 1.0, th20 = 1.0, thpsi = 1.0;
   if (g->limiter) {
@@ -479,6 +520,7 @@ static int limit_chain(const or_grid *g, const double *Ubar, double *VL, double 
  * cells i-2..i+2 (NV each).  Outputs the limited face states of the cell. */
 static int recon_cell(const or_grid *g, const double *Ust, double *UL, double *UR,
                       double *VfL, double *VfR, double *th) {
+  OR_CAT(OR_C_RECON);
   int N = g->N, d = g->dim, nvar = nv(g);
   double Vst[5][OR_MAXV];
   for (int k = 0; k < 5; k++) {
@@ -561,6 +603,7 @@ static void phys_flux(const or_grid *g, int dir, const double *U, const double *
 /* HLL / HLLC numerical flux and the consistent face velocity u-hat (R7). */
 int or_flux(const or_grid *g, int dir, const double *UL, const double *VL, const double *UR,
             const double *VR, double *F, double *uhat) {
+  OR_CAT(OR_C_FLUX);
   int N = g->N, d = g->dim, nvar = nv(g);
   double uL = VL[IMOM(g, dir)], uR = VR[IMOM(g, dir)];
   double cL = sound_speed(g, UL, VL), cR = sound_speed(g, UR, VR);
@@ -667,12 +710,12 @@ static int rhs_dir(const or_grid *g, int dir, const double *U, double *Lout) {
   int err = OR_OK;
 #pragma omp parallel
   {
-    double *FLs = malloc(sizeof(double) * nvar * (n + 2));
-    double *FRs = malloc(sizeof(double) * nvar * (n + 2));
-    double *VLs = malloc(sizeof(double) * nvar * (n + 2));
-    double *VRs = malloc(sizeof(double) * nvar * (n + 2));
-    double *Fx = malloc(sizeof(double) * nvar * (n + 1));
-    double *uh = malloc(sizeof(double) * (n + 1));
+    double *FLs = (double *)malloc(sizeof(double) * nvar * (n + 2));
+    double *FRs = (double *)malloc(sizeof(double) * nvar * (n + 2));
+    double *VLs = (double *)malloc(sizeof(double) * nvar * (n + 2));
+    double *VRs = (double *)malloc(sizeof(double) * nvar * (n + 2));
+    double *Fx = (double *)malloc(sizeof(double) * nvar * (n + 1));
+    double *uh = (double *)malloc(sizeof(double) * (n + 1));
 #pragma omp for schedule(dynamic, 4)
     for (long pc = 0; pc < npencil; pc++) {
       /* pencil pc -> linear index of its first cell */
@@ -691,6 +734,7 @@ static int rhs_dir(const or_grid *g, int dir, const double *U, double *Lout) {
         continue;
       }
       for (int m = 0; m < n; m++) {
+        OR_CAT(OR_C_UPDATE);
         long cell = base + m * stride;
         for (int v = 0; v < nvar; v++)
           Lout[v * nc + cell] += -(Fx[(m + 1) * nvar + v] - Fx[m * nvar + v]) / dx;
@@ -801,11 +845,11 @@ int or_pf_rhs(const or_grid *g, const double *U, const double *Q, double dt_limi
     long stride = dir == 0 ? 1 : (dir == 1 ? g->n[0] : (long)g->n[0] * g->n[1]);
     long npencil = nc / n;
     double dx = g->dx[dir];
-    double *FLs = malloc(sizeof(double) * nvar * (n + 2));
-    double *FRs = malloc(sizeof(double) * nvar * (n + 2));
-    double *VLs = malloc(sizeof(double) * nvar * (n + 2));
-    double *VRs = malloc(sizeof(double) * nvar * (n + 2));
-    double *Fx = malloc(sizeof(double) * nvar * (n + 1));
+    double *FLs = (double *)malloc(sizeof(double) * nvar * (n + 2));
+    double *FRs = (double *)malloc(sizeof(double) * nvar * (n + 2));
+    double *VLs = (double *)malloc(sizeof(double) * nvar * (n + 2));
+    double *VRs = (double *)malloc(sizeof(double) * nvar * (n + 2));
+    double *Fx = (double *)malloc(sizeof(double) * nvar * (n + 1));
     for (long pc = 0; pc < npencil && !e; pc++) {
       long base;
       if (dir == 0) base = pc * n;
@@ -858,11 +902,11 @@ int or_faces(const or_grid *g, int dir, const double *U, double *ULo, double *UR
   long nc = ncells(g);
   long stride = dir == 0 ? 1 : (dir == 1 ? g->n[0] : (long)g->n[0] * g->n[1]);
   long npencil = nc / n;
-  double *FLs = malloc(sizeof(double) * nvar * (n + 2));
-  double *FRs = malloc(sizeof(double) * nvar * (n + 2));
-  double *VLs = malloc(sizeof(double) * nvar * (n + 2));
-  double *VRs = malloc(sizeof(double) * nvar * (n + 2));
-  double *TH = malloc(sizeof(double) * 3 * (n + 2));
+  double *FLs = (double *)malloc(sizeof(double) * nvar * (n + 2));
+  double *FRs = (double *)malloc(sizeof(double) * nvar * (n + 2));
+  double *VLs = (double *)malloc(sizeof(double) * nvar * (n + 2));
+  double *VRs = (double *)malloc(sizeof(double) * nvar * (n + 2));
+  double *TH = (double *)malloc(sizeof(double) * 3 * (n + 2));
   for (long pc = 0; pc < npencil && !e; pc++) {
     long base;
     if (dir == 0) base = pc * n;
@@ -984,6 +1028,7 @@ int or_max_rate(const or_grid *g, const double *U, double *rate) {
  * restored without Eq. 17-20. */
 static void rk_stage(const or_grid *g, double a, const double *U0, double b, const double *U1,
                      double c, double dt, const double *L, double *out) {
+  OR_CAT(OR_C_RK);
   long n = ncells(g), tot = n * nv(g);
   for (long k = 0; k < tot; k++) {
     double t0 = a * U0[k], t1 = b * U1[k], t2 = c * dt * L[k];
@@ -1025,8 +1070,8 @@ int or_rk3_step(const or_grid *g, double *U, double cfl, double dt_fixed, double
     if (e) return e;
     dt = cfl / rate;
   }
-  double *U0 = malloc(sizeof(double) * tot), *U1 = malloc(sizeof(double) * tot);
-  double *L = malloc(sizeof(double) * tot);
+  double *U0 = (double *)malloc(sizeof(double) * tot), *U1 = (double *)malloc(sizeof(double) * tot);
+  double *L = (double *)malloc(sizeof(double) * tot);
   memcpy(U0, U, sizeof(double) * tot);
   e = or_rhs(g, U0, L);
   if (!e) {
@@ -1042,3 +1087,7 @@ int or_rk3_step(const or_grid *g, double *U, double cfl, double dt_fixed, double
   if (dt_used) *dt_used = dt;
   return e;
 }
+
+#ifdef __cplusplus
+}
+#endif

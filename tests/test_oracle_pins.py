@@ -849,3 +849,42 @@ def test_air_helium_interface_thickness():
     _, Uh, _ = _shock_tube(200, phase_field=False)
     n_pf, n_hb = _interface_thickness(Up[4], 0.01), _interface_thickness(Uh[4], 0.01)
     assert 3.9 <= n_pf <= 5.1 and n_hb > n_pf       # 4-5 cells (a ratio of sums)
+
+
+# ---------------------------------------------------------------- op counts
+def test_op_counts_file_matches_the_oracle_counter():
+    """The roofline's flop counts are the oracle's counting build's: re-derive
+    every (N, D, flux) entry of op_counts.json and compare; the counting build
+    computes the same dU/dt as the oracle (its numbers are plain doubles)."""
+    import json as _json
+    from oracle import op_count
+    from paper_2608_00746_b300 import roofline
+    stored = _json.load(open(op_count.OUT))["counts"]
+    assert {(c["N"], c["D"], c["flux"]) for c in stored} >= {(2, 2, "hll"), (3, 2, "hll"),
+                                                             (3, 3, "hll")}
+    for c in stored:
+        fresh = op_count.count(c["N"], c["D"], c["flux"])
+        assert fresh == c, (c["N"], c["D"], c["flux"])
+        assert roofline.flops_per_cell_dir(c["N"], c["D"], c["flux"]) == c["flops_per_cell_dir"]
+    # the counting build's rhs equals the oracle's, bit for bit
+    shape, gam, pinf, V = op_count.smooth_state(3, 2, 16)
+    g = oracle.Grid(tuple(reversed(shape)), (1 / 16, 1 / 16), gam, pinf)
+    U = np.ascontiguousarray(oracle.prim_to_cons(g, V))
+    L = np.zeros_like(U)
+    op_count.lib().or_rhs(g.ref(), op_count._p(U), op_count._p(L))
+    assert np.array_equal(L, oracle.rhs(g, U))
+
+
+def test_op_counts_by_hand_on_one_step():
+    """Two steps counted by hand from their definitions, against the counter:
+    the candidates of Eq. 11 as the oracle writes them, (2 f0 - 7 f1 + 11 f2)/6
+    (6 flops), (-f1 + 5 f2 + 2 f3)/6 and (2 f2 + 5 f3 - f4)/6 (5 each), on both
+    faces of all NV variables; the SSP-RK3 stage a U0 + b U1 + (c dt) L (4
+    products, 2 sums; masses and fractions add 2 sums and a product for
+    R13's tolerance), shared by the D = 2 sweeps."""
+    from oracle import op_count
+    e = op_count.count(2, 2, "hll")
+    NV = 7
+    assert e["flops_per_cell_dir_by_step"]["cand"] == (6 + 5 + 5) * 2 * NV
+    rk = (6 * NV + 3 * 4) / 2   # 4 bounded rows (2 masses, 2 fractions), 2 sweeps
+    assert e["flops_per_cell_dir_by_step"]["rk"] == rk
