@@ -123,13 +123,22 @@ int wc_nvar(const wc_grid *g);
 long wc_ncell(const wc_grid *g);
 
 /* Device scratch that wc_rk_step needs: three state-sized FP64 buffers
- * (two Runge-Kutta stages and the direction accumulator) plus 256 bytes, and
- * for WC_PREC_LEARNED one more buffer of 18 x ncell FP32 learned weights. */
+ * (two Runge-Kutta stages and the direction accumulator) plus 256 bytes; for
+ * WC_PREC_LEARNED one more buffer of 18 x ncell FP32 learned weights; and for
+ * the reduced precisions (window schedule) the face buffer of the split
+ * sweep, (2 NV + 1) x (n + 2) x ncell / n FP64 values for the direction with
+ * the most (n = its cell count): the face pass of each direction stores the
+ * limited face states and the cells' pressures there for its flux pass. */
 size_t wc_workspace_bytes(const wc_grid *g);
+/* The face buffer's part of wc_workspace_bytes (0 in FP64).  It is
+ * optional: a workspace of at least wc_workspace_bytes(g) minus this runs
+ * the single-pass sweep instead (same results, bit for bit). */
+size_t wc_face_buffer_bytes(const wc_grid *g);
 
 /* Binds the caller's device state array U_dev ([NV][ncell] FP64, advanced in
- * place by wc_rk_step) and a device workspace of at least
- * wc_workspace_bytes(g) bytes (256-byte aligned). */
+ * place by wc_rk_step) and a device workspace of wc_workspace_bytes(g) bytes
+ * (256-byte aligned; at least wc_workspace_bytes(g) - wc_face_buffer_bytes(g),
+ * which selects the single-pass sweep). */
 wc_status wc_set_state(wc_grid *g, double *U_dev, void *workspace_dev, size_t ws_bytes);
 
 /* Copies a host state (pinned memory recommended) into / out of the bound

@@ -37,6 +37,9 @@ struct wc_grid {
   float tau = 1e-4f;
   unsigned long long* lcount = nullptr;
   float* Wbuf = nullptr;
+  // reduced precision: the split sweep's face buffer (in the workspace,
+  // after the learned weights); null: the single-pass sweep
+  double* fbuf = nullptr;
   char err[256];
   // sweep timing (wc_sweep_timing_begin / _read)
   std::vector<cudaEvent_t> tev;
@@ -158,19 +161,38 @@ extern "C" void wc_destroy(wc_grid* g) {
 extern "C" int wc_nvar(const wc_grid* g) { return g ? g->nv : 0; }
 extern "C" long wc_ncell(const wc_grid* g) { return g ? g->ncell : 0; }
 
+// Bytes of the learned weights and of the split sweep's face buffer (the
+// largest direction's) in the workspace.
+static size_t learned_bytes(const wc_grid* g) {
+  if (g->d.precision != WC_PREC_LEARNED) return 0;
+  return ((size_t)2 * MLP_NW * g->ncell * sizeof(float) + 255) / 256 * 256;
+}
+static size_t face_buffer_bytes(const wc_grid* g) {
+  if (g->d.precision == WC_PREC_FP64 || g->d.seg > 0) return 0;
+  const int K = g->nv;  // FaceBuf<N, D, float>::K: masses, fractions, velocity, pressure
+  long most = 0;
+  for (int d = 0; d < g->d.dim; d++) {
+    const long n = g->d.n[d];
+    const long b = fbuf_doubles(K, g->ncell / n, (int)n);
+    if (b > most) most = b;
+  }
+  return ((size_t)most * sizeof(double) + 255) / 256 * 256;
+}
+
 extern "C" size_t wc_workspace_bytes(const wc_grid* g) {
   if (!g) return 0;
   size_t state = (size_t)g->nv * g->ncell * sizeof(double);
   state = (state + 255) / 256 * 256;
-  size_t w = 0;
-  if (g->d.precision == WC_PREC_LEARNED)
-    w = ((size_t)2 * MLP_NW * g->ncell * sizeof(float) + 255) / 256 * 256;
-  return 3 * state + 256 + w;
+  return 3 * state + 256 + learned_bytes(g) + face_buffer_bytes(g);
 }
+
+extern "C" size_t wc_face_buffer_bytes(const wc_grid* g) { return g ? face_buffer_bytes(g) : 0; }
 
 extern "C" wc_status wc_set_state(wc_grid* g, double* U_dev, void* ws, size_t ws_bytes) {
   if (!g || !U_dev) return WC_ERR_ARG;
-  if (ws && ws_bytes < wc_workspace_bytes(g)) return fail(g, WC_ERR_ARG, "workspace too small");
+  const bool with_faces = ws_bytes >= wc_workspace_bytes(g);
+  if (ws && ws_bytes < wc_workspace_bytes(g) - face_buffer_bytes(g))
+    return fail(g, WC_ERR_ARG, "workspace too small");
   if (ws && (reinterpret_cast<uintptr_t>(ws) & 255)) return fail(g, WC_ERR_ARG, "workspace not 256-byte aligned");
   if (reinterpret_cast<uintptr_t>(U_dev) & 7) return fail(g, WC_ERR_ARG, "state not 8-byte aligned");
   g->U = U_dev;
@@ -188,6 +210,8 @@ extern "C" wc_status wc_set_state(wc_grid* g, double* U_dev, void* ws, size_t ws
     g->status = (unsigned*)(tail + 16);
     g->ticket = (unsigned*)(tail + 32);
     g->Wbuf = g->d.precision == WC_PREC_LEARNED ? (float*)(tail + 256) : nullptr;
+    g->fbuf = face_buffer_bytes(g) && with_faces ? (double*)(tail + 256 + learned_bytes(g))
+                                                 : nullptr;
     // the workspace comes uninitialised: clear rate, dt and the status word
     cudaError_t e = cudaMemset(tail, 0, 256);
     if (e != cudaSuccess) return cuda_fail(g, e, "workspace clear");
@@ -198,6 +222,7 @@ extern "C" wc_status wc_set_state(wc_grid* g, double* U_dev, void* ws, size_t ws
     g->status = nullptr;
     g->ticket = nullptr;
     g->Wbuf = nullptr;
+    g->fbuf = nullptr;
   }
   return WC_OK;
 }
@@ -335,6 +360,9 @@ static cudaError_t launch(const wc_grid* gc, const SweepArgs& a0, cudaStream_t s
   if (timed) cudaEventRecord(g->tev[2 * g->tcount], st);
   cudaError_t e;
   SweepArgs a = a0;
+  // the split sweep where the workspace holds its face buffer (not for the
+  // comparison schemes, which are FP64)
+  if (g->mat.cmp == CMP_NONE && g->d.seg == 0) a.fbuf = g->fbuf;
   if (g->d.precision == WC_PREC_LEARNED && a.kind == 0) {
     // weights of this direction from the surrogate, then the sweep
     e = launch_mlp_infer(mlp_geom(g, a.dir, a.U), g->mlp, g->Wbuf, g->status, st);
@@ -873,8 +901,9 @@ wc_status wc_internal_rk_with_scratch(wc_grid* g, double* U, char* scratch, doub
   // save and restore only the bindings (the grid also owns timing events)
   struct Bind {
     double* U; char* ws; size_t ws_bytes; double *B1, *B2, *Lacc;
-    unsigned long long* rate; double* dt; unsigned* status; unsigned* ticket;
-  } saved{g->U, g->ws, g->ws_bytes, g->B1, g->B2, g->Lacc, g->rate, g->dt, g->status, g->ticket};
+    unsigned long long* rate; double* dt; unsigned* status; unsigned* ticket; double* fbuf;
+  } saved{g->U,    g->ws, g->ws_bytes, g->B1,     g->B2,     g->Lacc,
+          g->rate, g->dt, g->status,   g->ticket, g->fbuf};
   size_t state = (size_t)g->nv * g->ncell * sizeof(double);
   state = (state + 255) / 256 * 256;
   char* tail = scratch + 3 * state;
@@ -890,6 +919,7 @@ wc_status wc_internal_rk_with_scratch(wc_grid* g, double* U, char* scratch, doub
   g->dt = (double*)(tail + 8);
   g->status = (unsigned*)(tail + 16);
   g->ticket = (unsigned*)(tail + 32);
+  g->fbuf = nullptr;  // the single-pass sweep (no face buffer in the scratch)
   wc_status r = wc_rk_step(g, cfl, dt_fixed, nsteps, nullptr, reinterpret_cast<void*>(st));
   if (status_out) *status_out = g->status;
   g->U = saved.U;
@@ -902,6 +932,7 @@ wc_status wc_internal_rk_with_scratch(wc_grid* g, double* U, char* scratch, doub
   g->dt = saved.dt;
   g->status = saved.status;
   g->ticket = saved.ticket;
+  g->fbuf = saved.fbuf;
   return r;
 }
 

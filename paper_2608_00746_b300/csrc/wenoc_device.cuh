@@ -869,26 +869,26 @@ __device__ __forceinline__ void hll_fp64(const Mat& m, int dir, const Face<N, D>
   else if (le0(sR)) k = -1.0;  // F_R, with s_R taken as 0
   else k = sL * rcp_nr(sR - sL);
   const double sRu = le0(sR) ? 0.0 : sR;
-  auto hll = [&](double fl, double fr, double ul, double ur) {
-    return fl + k * ((fl - fr) + sRu * (ur - ul));
-  };
-  uhat = uL + k * (uL - uR);
+  // F_L + k ((F_L - F_R) + s_R (U_R - U_L)) for a component whose physical
+  // flux is u x is a x_L + b x_R with a = u_L + k (u_L - s_R) and b =
+  // k (s_R - u_R) (a + b = u_hat, the flux of alpha = 1); the pressure
+  // terms add (1 + k) P_L - k P_R to the normal momentum and (1 + k) u_L P_L
+  // - k u_R P_R to the energy
+  const double a = fma(k, uL - sRu, uL), b = k * (sRu - uR);
+  uhat = a + b;
 #pragma unroll
   for (int p = 0; p < N; p++) {
-    const double aL = L.U[I::A(p)], aR = R.U[I::A(p)];
-    F[I::A(p)] = hll(aL * uL, aR * uR, aL, aR);
-    const double mL = L.U[p], mR = R.U[p];
-    F[p] = hll(mL * uL, mR * uR, mL, mR);
+    F[I::A(p)] = fma(a, L.U[I::A(p)], b * R.U[I::A(p)]);
+    F[p] = fma(a, L.U[p], b * R.U[p]);
   }
+  const double kp = 1.0 + k;
+  const double pw = fma(kp, L.P, -k * R.P);
 #pragma unroll
   for (int j = 0; j < D; j++) {
-    const double qL = L.U[I::U(j)], qR = R.U[I::U(j)];
-    const double fl = j == dir ? fma(qL, uL, L.P) : qL * uL;
-    const double fr = j == dir ? fma(qR, uR, R.P) : qR * uR;
-    F[I::U(j)] = hll(fl, fr, qL, qR);
+    const double f = fma(a, L.U[I::U(j)], b * R.U[I::U(j)]);
+    F[I::U(j)] = j == dir ? f + pw : f;
   }
-  const double eL = L.U[I::E], eR = R.U[I::E];
-  F[I::E] = hll(uL * (eL + L.P), uR * (eR + R.P), eL, eR);
+  F[I::E] = fma(a, L.U[I::E], fma(b, R.U[I::E], fma(kp * uL, L.P, -k * (uR * R.P))));
 }
 
 // HLL or HLLC flux across the face between the left state L (from cell i) and
@@ -983,16 +983,13 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
     const TF sRu = le0(sR) ? TF(0) : sR;
     kd = wide(k);
     sRd = wide(sRu);
-    uhat = uLd + kd * (uLd - uRd);
+    // masses and fractions as a x_L + b x_R (see hll_fp64); a + b = u_hat
+    const double ad = fma(kd, uLd - sRd, uLd), bd = kd * (sRd - uRd);
+    uhat = ad + bd;
 #pragma unroll
     for (int p = 0; p < N; p++) {
-      double aL = L.U[I::A(p)], aR = R.U[I::A(p)];
-      double fl = aL * uLd, fr = aR * uRd;
-      F[I::A(p)] = fl + kd * ((fl - fr) + sRd * (aR - aL));
-      double mL = L.U[p], mR = R.U[p];
-      fl = mL * uLd;
-      fr = mR * uRd;
-      double fm = fl + kd * ((fl - fr) + sRd * (mR - mL));
+      F[I::A(p)] = fma(ad, L.U[I::A(p)], bd * R.U[I::A(p)]);
+      const double fm = fma(ad, L.U[p], bd * R.U[p]);
       F[p] = fm;
       Frho += fm;
     }

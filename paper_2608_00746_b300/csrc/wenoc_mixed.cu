@@ -8,6 +8,7 @@ namespace wc {
 template <int N, int D>
 static cudaError_t go(const SweepArgs& a, const Mat& m, int block, cudaStream_t st) {
   if (a.nwin > 0) {
+    if (a.fbuf) return launch_split<N, D, float, float, 0>(a, m, block, st);
     const int bps = (int)(a.max_threads / (148L * block));  // 0: occupancy limit
     return launch_window<N, D, float, float, 0>(a, m, block, bps, st);
   }

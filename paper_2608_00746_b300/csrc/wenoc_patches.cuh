@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(128) k_patch_stage(PatchArgs pa, Mat m) {
       a.hllc = pa.hllc;
       a.energy_limiter = pa.energy_limiter;
       a.status = pa.status;
+      a.faceL = a.faceR = nullptr;
       for (int pc = threadIdx.x; pc < e * e; pc += blockDim.x) {
         long base;
         if (dir == 0) base = off + (long)pc * e;

@@ -65,7 +65,28 @@ struct SweepArgs {
   // every cell, [NV][ncell] each
   double* faceL;
   double* faceR;
+  // split sweep (fbuf not null): the face pass writes the limited face
+  // states of the cells -1 .. n of every pencil (boundary cells included)
+  // and the cells' pressures there, and the flux pass reads them.  Layout:
+  // fbuf[((side * K + k) * npencil + pencil) * (n + 2) + c + 1], k < K the
+  // stored components of a face state (FaceBuf), then the pressures
+  // fbuf[(2 K * npencil + pencil) * (n + 2) + c + 1]
+  double* fbuf;
 };
+
+// The components of a face state that the flux pass needs: all of U, the
+// velocity and the pressure for an FP64 flux (the physical fluxes of Eq. 1);
+// for a reduced-precision flux (remainder form) the masses, fractions,
+// velocity and pressure only.
+template <int N, int D, typename TF>
+struct FaceBuf {
+  static constexpr int NV = 2 * N + D + 1;
+  static constexpr bool FULL = sizeof(TF) == 8;
+  static constexpr int K = FULL ? NV + D + 1 : NV;
+};
+__host__ __device__ inline long fbuf_doubles(int K, long npencil, int n) {
+  return (2L * K + 1) * npencil * (n + 2);
+}
 
 enum { BC_PERIODIC = 0, BC_REFLECTIVE = 1, BC_OUTFLOW = 2 };
 
@@ -119,6 +140,43 @@ __device__ __forceinline__ void put_slot(double* sl, const double* v) {
   if constexpr (Ring<N, D, T>::HILO) {
 #pragma unroll
     for (int q = 0; q <= D; q++) Vs[I::NV + q] = cvt<T>(v[N + q] - wide(Vs[N + q]));
+  }
+}
+
+// face_velocity_pressure with the loop over the variables not unrolled (one
+// copy of the code for all of them) and the faces written to out[k * 32]:
+// u_0 L, u_0 R, ..., P L, P R (a lane's column of the window scratch).
+template <int N, int D, typename T, int LW>
+__device__ __forceinline__ void face_velocity_pressure_rolled(const Mat& m, const T* const* V,
+                                                              double Pb, double* out) {
+  using I = Idx<N, D>;
+#pragma unroll 1
+  for (int v = N; v <= N + D; v++) {
+    double fl, fr;
+    if constexpr (Ring<N, D, T>::HILO) {
+      const int q = v - N;
+      const T c = V[2][v], cl = V[2][I::NV + q];
+      auto dlt = [&](int k) { return (V[k][v] - c) + (V[k][I::NV + q] - cl); };
+      const Stencil<T> st{c, dlt(0), dlt(1), dlt(3), dlt(4)};
+      const W6<T> w = sweep_weights<LW, T>(m, st);
+      T oL, oR;
+      offsets(w, st, oL, oR);
+      const T res = fabs(c) * T(0x1p-24);
+      if (fabs(oL) < res) oL = T(0);
+      if (fabs(oR) < res) oR = T(0);
+      const double cv = v < N + D ? wide(c) + wide(cl) : Pb;
+      fl = cv + wide(oL);
+      fr = cv + wide(oR);
+    } else {
+      const Stencil<T> st = stencil<T>(V[0][v], V[1][v], V[2][v], V[3][v], V[4][v]);
+      const W6<T> w = sweep_weights<LW, T>(m, st);
+      T tl, tr;
+      reconstruct(w, st, tl, tr);
+      fl = wide(tl);
+      fr = wide(tr);
+    }
+    out[2 * (v - N) * 32] = fl;
+    out[(2 * (v - N) + 1) * 32] = fr;
   }
 }
 

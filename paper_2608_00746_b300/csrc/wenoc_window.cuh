@@ -45,6 +45,7 @@ inline WinPlan win_plan(int n, long npencil) {
 template <int N, int D, typename T>
 struct WinSmem {
   static constexpr int SLOTD = Ring<N, D, T>::SLOTD;     // doubles per cell slot
+  static constexpr int FSC = 4 * N + 2 * (D + 1);        // face values per lane
 };
 
 template <int N, int D>
@@ -57,6 +58,98 @@ __device__ __forceinline__ void shfl_face_down(const Face<N, D>& f, Face<N, D>& 
   g.P = __shfl_down_sync(0xffffffffu, f.P, 1);
 }
 
+template <int N, int D, typename TF>
+__device__ __forceinline__ void put_face(const SweepArgs& a, int side, long pencil, int c,
+                                         const Face<N, D>& f) {
+  using B = FaceBuf<N, D, TF>;
+  using I = Idx<N, D>;
+  const long np2 = a.n + 2;
+  double* q = a.fbuf + ((long)side * B::K * a.npencil + pencil) * np2 + (c + 1);
+  const long ks = a.npencil * np2;  // component stride
+  if constexpr (B::FULL) {
+#pragma unroll
+    for (int v = 0; v < I::NV; v++) q[v * ks] = f.U[v];
+  } else {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      q[p * ks] = f.U[p];
+      q[(N + p) * ks] = f.U[I::A(p)];
+    }
+  }
+  const int o = B::FULL ? I::NV : 2 * N;
+#pragma unroll
+  for (int j = 0; j < D; j++) q[(o + j) * ks] = f.u[j];
+  q[(o + D) * ks] = f.P;
+}
+
+template <int N, int D, typename TF>
+__device__ __forceinline__ void get_face(const SweepArgs& a, int side, long pencil, int c,
+                                         Face<N, D>& f) {
+  using B = FaceBuf<N, D, TF>;
+  using I = Idx<N, D>;
+  const long np2 = a.n + 2;
+  const double* q = a.fbuf + ((long)side * B::K * a.npencil + pencil) * np2 + (c + 1);
+  const long ks = a.npencil * np2;
+  if constexpr (B::FULL) {
+#pragma unroll
+    for (int v = 0; v < I::NV; v++) f.U[v] = __ldg(q + v * ks);
+  } else {
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      f.U[p] = __ldg(q + p * ks);
+      f.U[I::A(p)] = __ldg(q + (N + p) * ks);
+    }
+#pragma unroll
+    for (int j = 0; j < D; j++) f.U[I::U(j)] = 0.0;  // not read by the remainder form
+    f.U[I::E] = 0.0;
+  }
+  const int o = B::FULL ? I::NV : 2 * N;
+#pragma unroll
+  for (int j = 0; j < D; j++) f.u[j] = __ldg(q + (o + j) * ks);
+  f.P = __ldg(q + (o + D) * ks);
+}
+
+// Eq. 3 (Eq. 5 for kind 1) for one cell from the fluxes at its two faces
+// (F right, Fl left) and u-hat there, applied per a.mode: L = part, L +=
+// part, or the Runge-Kutta stage with the direction accumulator.
+template <int N, int D, int LW>
+__device__ __forceinline__ void update_cell(const SweepArgs& a, const Mat& m, long cell,
+                                            const double* F, const double* Fl, double uh,
+                                            double uhl, const double* Ub, double Pb, double dt,
+                                            unsigned& bad) {
+  using I = Idx<N, D>;
+  constexpr int NV = I::NV;
+  const double du = (uh - uhl) * a.inv_dx;
+  // Eq. 3: -div F + alpha (1 + K) div u_hat;  Eq. 5: +div F^PF
+  const double sdx = a.kind == 1 ? a.inv_dx : -a.inv_dx;
+  double sf[N];
+  source_factors<N, D>(m, Ub, Pb, sf);
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    double val = (F[v] - Fl[v]) * sdx;
+    if (a.kind == 0 && v >= N + D + 1) val = fma(sf[v - (N + D + 1)], du, val);
+    const long idx = (long)v * a.ncell + cell;
+    if (not_finite(val)) bad |= ST_NAN;
+    if (a.mode == 0) {
+      a.L[idx] = val;
+    } else if (a.mode == 1) {
+      a.L[idx] += val;
+    } else {
+      const double Lt = a.mode == 2 ? a.L[idx] + val : val;
+      // (rounded term by term, without contraction)
+      const double t0 = __dmul_rn(a.rk0, a.U0[idx]), t1 = __dmul_rn(a.rk1, Ub[v]),
+                   t2 = __dmul_rn(__dmul_rn(a.rk2, dt), Lt);
+      double un = __dadd_rn(__dadd_rn(t0, t1), t2);
+      // masses >= 0 and fractions in [0, 1] up to the rounding of the
+      // stage sum (not in the comparison schemes, which have no bounds)
+      if constexpr (LW != 2) {
+        if (v < N || v >= I::A(0)) un = stage_bound(un, t0, t1, t2, v >= I::A(0));
+      }
+      a.Uout[idx] = un;
+    }
+  }
+}
+
 // One window: the warp's lanes form groups of G consecutive lanes (one group
 // of 32 for a full window); lane j of a group owns cell c = c0 - 1 + j of the
 // pencil at `base`, and slot sb + s of `slots` holds the primitive state of
@@ -65,10 +158,15 @@ __device__ __forceinline__ void shfl_face_down(const Face<N, D>& f, Face<N, D>& 
 // a.n).  A lane with store = false (beyond the last group) keeps its slots
 // untouched and updates nothing.  Variant LW as in sweep_segment (0 scheme,
 // 1 learned weights, 2 comparison schemes).
-template <int N, int D, typename T, typename TF, int LW>
-__device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, long base, int c0,
-                                             int j, int G, int sb, bool active, bool store,
-                                             double* slots, double dt, unsigned& bad,
+//
+// PART = 1 (the split sweep's face pass) stops after the limiter chain: the
+// face states of the cells -1 .. n go to a.fbuf with the cells' pressures,
+// and the flux pass (k_flux_win) does the rest.
+template <int N, int D, typename T, typename TF, int LW, int PART>
+__device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, long base,
+                                             long pencil, int c0, int j, int G, int sb,
+                                             bool active, bool store, double* slots,
+                                             double* fsc, double dt, unsigned& bad,
                                              unsigned* lstat) {
   using I = Idx<N, D>;
   constexpr int NV = I::NV;
@@ -117,81 +215,109 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
     V[k] = reinterpret_cast<const T*>(slots + (sb + j + k) * SLOTD + 1);
   const double Pb = slots[(sb + j + 2) * SLOTD];
 
-  // Eq. 16: masses and fractions with the weights of the masses
-  double mL[N], mR[N], aL[N], aR[N];
-#pragma unroll
-  for (int p = 0; p < N; p++) {
-    Stencil<T> st = stencil<T>(V[0][p], V[1][p], V[2][p], V[3][p], V[4][p]);
-    W6<T> w = sweep_weights<LW, T>(m, st);
-    const int ia = I::A(p);
-    const Stencil<T> sa = stencil<T>(V[0][ia], V[1][ia], V[2][ia], V[3][ia], V[4][ia]);
-    if constexpr (LW == 1) {
-      // learned weights of an interior cell, accepted per face side when the
-      // mass and the fraction reconstructed with them are each within tau
-      // times their stencil's range of the plain reconstructions (boundary
-      // cells keep the plain weights)
-      if (p < 3 && c >= 0 && c < a.n) {
-        const float* Wp = a.Wm + (long)(3 * p) * a.ncell + base + (long)c * a.stride;
-        W6<T> wl;
-        wl.aL0 = T(__ldg(Wp));
-        wl.aL1 = T(__ldg(Wp + a.ncell));
-        wl.aL2 = T(__ldg(Wp + 2 * a.ncell));
-        wl.aR0 = T(__ldg(Wp + 9 * a.ncell));
-        wl.aR1 = T(__ldg(Wp + 10 * a.ncell));
-        wl.aR2 = T(__ldg(Wp + 11 * a.ncell));
-        wl.invL = wl.invR = T(1) / T(6);
-        bool okL = true, okR = true, flat = true;
-        auto judge = [&](const Stencil<T>& q) {
-          // offsets from the cell value with the plain and the learned weights
-          T pl, pr, ql, qr;
-          offsets(w, q, pl, pr);
-          offsets(wl, q, ql, qr);
-          const T hi = fmax(fmax(fmax(T(0), q.da), fmax(q.db, q.dd)), q.de);
-          const T lo = fmin(fmin(fmin(T(0), q.da), fmin(q.db, q.dd)), q.de);
-          const T tol = T(a.tau) * (hi - lo);
-          okL = okL && fabs(ql - pl) <= tol;
-          okR = okR && fabs(qr - pr) <= tol;
-          flat = flat && !(hi > lo);
-        };
-        judge(st);
-        judge(sa);
-        if (okL) {
-          w.aL0 = wl.aL0;
-          w.aL1 = wl.aL1;
-          w.aL2 = wl.aL2;
-          w.invL = wl.invL;
-        }
-        if (okR) {
-          w.aR0 = wl.aR0;
-          w.aR1 = wl.aR1;
-          w.aR2 = wl.aR2;
-          w.invR = wl.invR;
-        }
-        if (!flat) {
-          lstat[0] += 2u;
-          lstat[1] += unsigned(!okL) + unsigned(!okR);
+  // The reconstructions of the variables run in loops that are not
+  // unrolled: one copy of the weight and candidate code serves every
+  // variable, which keeps the window's hot code small enough for the
+  // instruction cache.  Each lane's face values go through its column of the
+  // warp's scratch (fsc[k * 32]): masses L/R, fractions L/R, then the
+  // velocity components and the pressure L/R.
+  {
+    bool flip;
+    const long cellc = base + (long)bc_index(ghost_clamp(c), a.n, a.bclo, a.bchi, flip) * a.stride;
+    // Eq. 16: masses and fractions with the weights of the masses
+#pragma unroll 1
+    for (int p = 0; p < N; p++) {
+      const int ia = I::A(p);
+      Stencil<T> st = stencil<T>(V[0][p], V[1][p], V[2][p], V[3][p], V[4][p]);
+      W6<T> w = sweep_weights<LW, T>(m, st);
+      const Stencil<T> sa = stencil<T>(V[0][ia], V[1][ia], V[2][ia], V[3][ia], V[4][ia]);
+      if constexpr (LW == 1) {
+        // learned weights of an interior cell, accepted per face side when
+        // the mass and the fraction reconstructed with them are each within
+        // tau times their stencil's range of the plain reconstructions
+        // (boundary cells keep the plain weights)
+        if (p < 3 && c >= 0 && c < a.n) {
+          const float* Wp = a.Wm + (long)(3 * p) * a.ncell + base + (long)c * a.stride;
+          W6<T> wl;
+          wl.aL0 = T(__ldg(Wp));
+          wl.aL1 = T(__ldg(Wp + a.ncell));
+          wl.aL2 = T(__ldg(Wp + 2 * a.ncell));
+          wl.aR0 = T(__ldg(Wp + 9 * a.ncell));
+          wl.aR1 = T(__ldg(Wp + 10 * a.ncell));
+          wl.aR2 = T(__ldg(Wp + 11 * a.ncell));
+          wl.invL = wl.invR = T(1) / T(6);
+          bool okL = true, okR = true, flat = true;
+          auto judge = [&](const Stencil<T>& q) {
+            // offsets from the cell value with the plain and the learned weights
+            T pl, pr, ql, qr;
+            offsets(w, q, pl, pr);
+            offsets(wl, q, ql, qr);
+            const T hi = fmax(fmax(fmax(T(0), q.da), fmax(q.db, q.dd)), q.de);
+            const T lo = fmin(fmin(fmin(T(0), q.da), fmin(q.db, q.dd)), q.de);
+            const T tol = T(a.tau) * (hi - lo);
+            okL = okL && fabs(ql - pl) <= tol;
+            okR = okR && fabs(qr - pr) <= tol;
+            flat = flat && !(hi > lo);
+          };
+          judge(st);
+          judge(sa);
+          if (okL) {
+            w.aL0 = wl.aL0;
+            w.aL1 = wl.aL1;
+            w.aL2 = wl.aL2;
+            w.invL = wl.invL;
+          }
+          if (okR) {
+            w.aR0 = wl.aR0;
+            w.aR1 = wl.aR1;
+            w.aR2 = wl.aR2;
+            w.invR = wl.invR;
+          }
+          if (!flat) {
+            lstat[0] += 2u;
+            lstat[1] += unsigned(!okL) + unsigned(!okR);
+          }
         }
       }
-    }
-    // (the comparison schemes: the fraction with its own weights)
-    W6<T> wa = w;
-    if constexpr (LW == 2) wa = sweep_weights<LW, T>(m, sa);
-    if constexpr (OFFSET) {
-      reconstruct_offset(w, st, Ub[p], mL[p], mR[p]);
-      reconstruct_offset(wa, sa, Ub[ia], aL[p], aR[p]);
-    } else {
-      T fl, fr;
-      reconstruct(w, st, fl, fr);
-      mL[p] = wide(fl);
-      mR[p] = wide(fr);
-      reconstruct(wa, sa, fl, fr);
-      aL[p] = wide(fl);
-      aR[p] = wide(fr);
+      // (the comparison schemes: the fraction with its own weights)
+      W6<T> wa = w;
+      if constexpr (LW == 2) wa = sweep_weights<LW, T>(m, sa);
+      double ml, mr, al, ar;
+      if constexpr (OFFSET) {
+        reconstruct_offset(w, st, __ldg(a.U + (long)p * a.ncell + cellc), ml, mr);
+        reconstruct_offset(wa, sa, __ldg(a.U + (long)ia * a.ncell + cellc), al, ar);
+      } else {
+        T fl, fr;
+        reconstruct(w, st, fl, fr);
+        ml = wide(fl);
+        mr = wide(fr);
+        reconstruct(wa, sa, fl, fr);
+        al = wide(fl);
+        ar = wide(fr);
+      }
+      fsc[(4 * p + 0) * 32] = ml;
+      fsc[(4 * p + 1) * 32] = mr;
+      fsc[(4 * p + 2) * 32] = al;
+      fsc[(4 * p + 3) * 32] = ar;
     }
   }
   // velocity and pressure, each with its own weights
-  double uL[D], uR[D], PL, PR;
-  face_velocity_pressure<N, D, T, LW>(m, V, Pb, uL, uR, PL, PR);
+  face_velocity_pressure_rolled<N, D, T, LW>(m, V, Pb, fsc + 4 * N * 32);
+  double mL[N], mR[N], aL[N], aR[N], uL[D], uR[D], PL, PR;
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    mL[p] = fsc[(4 * p + 0) * 32];
+    mR[p] = fsc[(4 * p + 1) * 32];
+    aL[p] = fsc[(4 * p + 2) * 32];
+    aR[p] = fsc[(4 * p + 3) * 32];
+  }
+#pragma unroll
+  for (int q = 0; q < D; q++) {
+    uL[q] = fsc[(4 * N + 2 * q) * 32];
+    uR[q] = fsc[(4 * N + 2 * q + 1) * 32];
+  }
+  PL = fsc[(4 * N + 2 * D) * 32];
+  PR = fsc[(4 * N + 2 * D + 1) * 32];
   Face<N, D> fL, fR;
   limit_chain<N, D, LW != 2>(m, Ub, Pb, mL, aL, mR, aR, uL, PL, uR, PR, a.energy_limiter, fL, fR,
                     nullptr);
@@ -202,6 +328,18 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
       a.faceL[(long)v * a.ncell + cell] = fL.U[v];
       a.faceR[(long)v * a.ncell + cell] = fR.U[v];
     }
+  }
+  if constexpr (PART == 1) {
+    // the cells this group owns, and the boundary cells -1 and n at the
+    // pencil's ends (the first and the last window hold them)
+    const bool own = active && ((j >= 1 && j <= G - 2 && c < a.n) || c == -1 || c == a.n);
+    if (own) {
+      put_face<N, D, TF>(a, 0, pencil, c, fL);
+      put_face<N, D, TF>(a, 1, pencil, c, fR);
+      a.fbuf[(2L * FaceBuf<N, D, TF>::K * a.npencil + pencil) * (a.n + 2) + (c + 1)] = Pb;
+    }
+    __syncwarp();  // the slots are refilled by the next window
+    return;
   }
   // the face x_{c+1/2}: this lane's fL and the right neighbour's fR
   Face<N, D> fRn;
@@ -230,50 +368,28 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
 #pragma unroll
   for (int v = 0; v < NV; v++) Fl[v] = __shfl_up_sync(0xffffffffu, F[v], 1);
   const double uhl = __shfl_up_sync(0xffffffffu, uh, 1);
-  if (active && j >= 1 && j <= G - 2 && c < a.n) {
-    const long cell = base + (long)c * a.stride;
-    const double du = (uh - uhl) * a.inv_dx;
-    // Eq. 3: -div F + alpha (1 + K) div u_hat;  Eq. 5: +div F^PF
-    const double sdx = a.kind == 1 ? a.inv_dx : -a.inv_dx;
-    double sf[N];
-    source_factors<N, D>(m, Ub, Pb, sf);
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-      double val = (F[v] - Fl[v]) * sdx;
-      if (a.kind == 0 && v >= N + D + 1) val = fma(sf[v - (N + D + 1)], du, val);
-      const long idx = (long)v * a.ncell + cell;
-      if (not_finite(val)) bad |= ST_NAN;
-      if (a.mode == 0) {
-        a.L[idx] = val;
-      } else if (a.mode == 1) {
-        a.L[idx] += val;
-      } else {
-        const double Lt = a.mode == 2 ? a.L[idx] + val : val;
-        // (rounded term by term, without contraction)
-        const double t0 = __dmul_rn(a.rk0, a.U0[idx]), t1 = __dmul_rn(a.rk1, Ub[v]),
-                     t2 = __dmul_rn(__dmul_rn(a.rk2, dt), Lt);
-        double un = __dadd_rn(__dadd_rn(t0, t1), t2);
-        // masses >= 0 and fractions in [0, 1] up to the rounding of the
-        // stage sum (not in the comparison schemes, which have no bounds)
-        if constexpr (LW != 2) {
-          if (v < N || v >= I::A(0))
-            un = stage_bound(un, t0, t1, t2, v >= I::A(0));
-        }
-        a.Uout[idx] = un;
-      }
-    }
-  }
+  if (active && j >= 1 && j <= G - 2 && c < a.n)
+    update_cell<N, D, LW>(a, m, base + (long)c * a.stride, F, Fl, uh, uhl, Ub, Pb, dt, bad);
   __syncwarp();  // the slots are refilled by the next window
 }
 
 // Persistent launch: every warp takes windows (pencil fastest, so warps that
 // run together read neighbouring pencils) from the queue a.ticket[0] until
 // it is empty; the last warp to leave resets the queue for the next launch.
-template <int N, int D, typename T, typename TF, int LW = 0>
-__global__ void __launch_bounds__(128) k_sweep_win(SweepArgs a, Mat m) {
+#ifndef WC_WIN_MINB64
+#define WC_WIN_MINB64 1
+#endif
+#ifndef WC_WIN_MINB32
+#define WC_WIN_MINB32 1
+#endif
+template <int N, int D, typename T, typename TF, int LW = 0, int PART = 0>
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? WC_WIN_MINB64 : WC_WIN_MINB32)
+    k_sweep_win(SweepArgs a, Mat m) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31;
-  double* slots = smem + (threadIdx.x >> 5) * (a.wslots * WinSmem<N, D, T>::SLOTD);
+  using WS = WinSmem<N, D, T>;
+  double* slots = smem + (threadIdx.x >> 5) * (a.wslots * WS::SLOTD + 32 * WS::FSC);
+  double* fsc = slots + a.wslots * WS::SLOTD + lane;  // this lane's scratch column
   const unsigned nitems = a.nitems;
   const unsigned nfull = (unsigned)(a.npencil * a.wfull);
   unsigned bad = 0u;
@@ -281,7 +397,8 @@ __global__ void __launch_bounds__(128) k_sweep_win(SweepArgs a, Mat m) {
   double dt = 0.0;
   // the stage modes, and every direction of a Phase-Field stage (its gradient
   // limit is gcoef / dt)
-  if (a.mode >= 2 || a.gcoef > 0.0) dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.cfl / *a.rate;
+  if (PART == 0 && (a.mode >= 2 || a.gcoef > 0.0))
+    dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.cfl / *a.rate;
   for (;;) {
     unsigned it = 0u;
     if (lane == 0) it = atomicAdd(a.ticket, 1u);
@@ -320,8 +437,8 @@ __global__ void __launch_bounds__(128) k_sweep_win(SweepArgs a, Mat m) {
     if (a.dir == 0) base = tr * a.nx;
     else if (a.dir == 1) base = (tr / a.nx) * ((long)a.nx * a.ny) + tr % a.nx;
     else base = tr;
-    sweep_window<N, D, T, TF, LW>(a, m, base, c0, j, G, sb, active, store, slots, dt, bad,
-                                  lstat);
+    sweep_window<N, D, T, TF, LW, PART>(a, m, base, tr, c0, j, G, sb, active, store, slots, fsc,
+                                        dt, bad, lstat);
   }
   if (lane == 0) {
     __threadfence();
@@ -351,13 +468,93 @@ __global__ void __launch_bounds__(128) k_sweep_win(SweepArgs a, Mat m) {
 // register file hold more warps (at 104 registers a thread an SM takes 19
 // one-warp blocks but only 4 blocks of four warps); the FP64 sweep runs
 // equally fast with either, its FP64 pipe being as busy at 16 warps as at 19.
-template <int N, int D, typename T, typename TF, int LW>
+// Number of SMs of the current device (cached per device ordinal).
+inline int device_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (cache[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      return 148;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+// The flux pass of the split sweep: a warp takes windows of WINF cells of a
+// pencil (pencil fastest; a static grid-stride walk: the cost per face is
+// nearly uniform); lane j solves the Riemann problem at the face between
+// cells c = c0 - 1 + j and c + 1 from the face states the face pass stored
+// (the right state of cell c + 1 may be the boundary cell n), and lanes
+// 1 .. 31 update their cells with the left neighbour's flux.
+constexpr int WINF = 31;
+template <int N, int D, typename TF, int LW>
+__global__ void __launch_bounds__(128) k_flux_win(SweepArgs a, Mat m) {
+  using I = Idx<N, D>;
+  constexpr int NV = I::NV;
+  const int lane = threadIdx.x & 31;
+  const long nwf = (a.n + WINF - 1) / WINF;
+  const long items = a.npencil * nwf;
+  const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
+  unsigned bad = 0u;
+  double dt = 0.0;
+  if (a.mode >= 2 || a.gcoef > 0.0) dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.cfl / *a.rate;
+  for (long it = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
+    const long tr = it % a.npencil;
+    const int c0 = (int)(it / a.npencil) * WINF;
+    long base;
+    if (a.dir == 0) base = tr * a.nx;
+    else if (a.dir == 1) base = (tr / a.nx) * ((long)a.nx * a.ny) + tr % a.nx;
+    else base = tr;
+    const int c = c0 - 1 + lane;
+    const bool live = c <= a.n - 1;
+    const int cc = live ? c : a.n - 1;  // lanes past the pencil's end: a copy, no update
+    Face<N, D> fL, fR;
+    get_face<N, D, TF>(a, 0, tr, cc, fL);
+    get_face<N, D, TF>(a, 1, tr, cc + 1, fR);
+    double F[NV], uh = 0.0;
+    if (a.kind == 1) {
+      double G[N];
+      bool flip;
+      const long cl = base + (long)bc_index(cc, a.n, a.bclo, a.bchi, flip) * a.stride;
+      const long cr = base + (long)bc_index(cc + 1, a.n, a.bclo, a.bchi, flip) * a.stride;
+#pragma unroll
+      for (int p = 0; p < N; p++) {
+        const long o = (long)I::A(p) * a.ncell;
+        G[p] = pf_gradient(__ldg(a.Q + (long)p * a.ncell + cl), __ldg(a.Q + (long)p * a.ncell + cr),
+                           __ldg(a.U + o + cl), __ldg(a.U + o + cr), a.inv_dx,
+                           a.gcoef > 0.0 ? a.gcoef / dt : a.gmax);
+      }
+      pf_flux<N, D>(m, fL, fR, G, F);
+    } else {
+      riemann<N, D, TF>(m, a.dir, a.hllc, fL, fR, F, uh);
+    }
+    double Fl[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) Fl[v] = __shfl_up_sync(0xffffffffu, F[v], 1);
+    const double uhl = __shfl_up_sync(0xffffffffu, uh, 1);
+    if (lane >= 1 && live) {
+      const long cell = base + (long)c * a.stride;
+      double Ub[NV];
+#pragma unroll
+      for (int v = 0; v < NV; v++) Ub[v] = __ldg(a.U + (long)v * a.ncell + cell);
+      const double Pb = __ldg(a.fbuf + (2L * FaceBuf<N, D, TF>::K * a.npencil + tr) * (a.n + 2) +
+                              (c + 1));
+      update_cell<N, D, LW>(a, m, cell, F, Fl, uh, uhl, Ub, Pb, dt, bad);
+    }
+  }
+  if (bad) atomicOr(a.status, bad);
+}
+
+template <int N, int D, typename T, typename TF, int LW, int PART = 0>
 cudaError_t launch_window(const SweepArgs& a0, const Mat& m, int block, int bps,
                           cudaStream_t st) {
   if (block < 32 || block > 128 || block % 32 != 0) return cudaErrorInvalidValue;
   if (a0.wslots < WIN_SLOTS || a0.wslots > WIN_SLOTS_MAX) return cudaErrorInvalidValue;
-  const int smem = a0.wslots * WinSmem<N, D, T>::SLOTD * 8 * (block / 32);
-  auto k = k_sweep_win<N, D, T, TF, LW>;
+  const int smem =
+      (a0.wslots * WinSmem<N, D, T>::SLOTD + 32 * WinSmem<N, D, T>::FSC) * 8 * (block / 32);
+  auto k = k_sweep_win<N, D, T, TF, LW, PART>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const long items = a0.nitems;
@@ -375,13 +572,38 @@ cudaError_t launch_window(const SweepArgs& a0, const Mat& m, int block, int bps,
     }
     bps = o;
   }
-  long blocks = 148L * bps;
+  long blocks = (long)device_sms() * bps;
   const long need = (items + block / 32 - 1) / (block / 32);
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
   SweepArgs a = a0;
   a.nwarps = (unsigned)(blocks * (block / 32));
   k<<<(unsigned)blocks, block, smem, st>>>(a, m);
+  return cudaGetLastError();
+}
+
+// The split sweep: the face pass (reconstruction and limiter chain into
+// a.fbuf), then the flux pass (Riemann problems and update).  Two compact
+// kernels instead of one long loop body: more warps fit, and the hot code
+// of each fits the instruction cache.
+template <int N, int D, typename T, typename TF, int LW>
+cudaError_t launch_split(const SweepArgs& a, const Mat& m, int block, cudaStream_t st) {
+  cudaError_t e = launch_window<N, D, T, TF, LW, 1>(a, m, block, 0, st);
+  if (e != cudaSuccess) return e;
+  auto k = k_flux_win<N, D, TF, LW == 2 ? 2 : 0>;
+  static int occ = 0;
+  if (occ == 0) {
+    int q = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k, 128, 0);
+    if (e != cudaSuccess) return e;
+    occ = q < 1 ? 1 : q;
+  }
+  const long items = a.npencil * ((a.n + WINF - 1) / WINF);
+  long blocks = (long)device_sms() * occ;
+  const long need = (items + 3) / 4;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  k<<<(unsigned)blocks, 128, 0, st>>>(a, m);
   return cudaGetLastError();
 }
 

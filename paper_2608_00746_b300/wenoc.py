@@ -89,6 +89,7 @@ _SIGS = {
     "wc_nvar": (ctypes.c_int, [_VP]),
     "wc_ncell": (ctypes.c_long, [_VP]),
     "wc_workspace_bytes": (ctypes.c_size_t, [_VP]),
+    "wc_face_buffer_bytes": (ctypes.c_size_t, [_VP]),
     "wc_set_state": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_size_t]),
     "wc_upload_state": (ctypes.c_int, [_VP, _VP, _VP]),
     "wc_download_state": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -262,9 +263,13 @@ class Grid:
     def workspace_bytes(self):
         return lib().wc_workspace_bytes(self.h)
 
-    def new_workspace(self, device="cuda"):
-        n = (self.workspace_bytes() + 7) // 8
-        return torch.empty(n, dtype=torch.float64, device=device)
+    def new_workspace(self, device="cuda", faces=True):
+        """A workspace tensor; faces=False leaves out the split sweep's face
+        buffer (the single-pass sweep runs then)."""
+        nb = self.workspace_bytes()
+        if not faces:
+            nb -= lib().wc_face_buffer_bytes(self.h)
+        return torch.empty((nb + 7) // 8, dtype=torch.float64, device=device)
 
     def bind(self, U, workspace=None):
         """Binds the device state tensor (advanced in place by rk_step)."""
