@@ -24,8 +24,13 @@ Readings (R17), where the paper is silent:
     remaining system is solved directly.
   * Eq. 4, discretised with second-order central differences: on the face
     between cells a and b the coefficient is c_f = (c_a + c_b)/2 with
-    c = max(phi (1 - phi), 0) (the degenerate coefficient; a fraction just
-    outside [0, 1] gives 0, not a negative coefficient), and
+    c = phi (1 - phi) for phi in [2^-52, 1 - 2^-52] and 0 otherwise (the
+    degenerate coefficient; a fraction just outside [0, 1] gives 0, not a
+    negative coefficient, and so do traces within one unit of rounding of
+    0 or 1: the hyperbolic step leaves such traces (1e-20 .. 1e-300) in
+    cells far from any interface, below the resolution of the fraction sum,
+    and with them c > 0 would join those cells to the interface regions
+    with coefficients of that size), and
     (A Q)_i = sum_faces c_f (Q_nbr - Q_i)/dx^2.  Reflective and outflow
     boundaries carry no flux (the mirrored cell has the same Q).
   * A is singular on every region that faces with c_f > 0 connect (its
@@ -152,11 +157,21 @@ def cac_rhs(g: Grid, U: np.ndarray, eta: float = None, M: float = None):
     return R, B, M
 
 
+TRACE = 2.0 ** -52
+
+
+def coefficient(phi: np.ndarray) -> np.ndarray:
+    """c = phi (1 - phi) where phi is in [2^-52, 1 - 2^-52], else 0 (R17)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    on = (phi >= TRACE) & (1.0 - phi >= TRACE)
+    return np.where(on, phi * (1.0 - phi), 0.0)
+
+
 def face_coefficients(g: Grid, phi: np.ndarray):
     """Per direction d: (c_f, a, b) for every face with two distinct cells,
     flat cell indices a (lower) and b (upper), c_f = (c_a + c_b)/2 with
-    c = max(phi (1 - phi), 0) (R17)."""
-    c = np.maximum(phi * (1.0 - phi), 0.0).reshape(-1)
+    the coefficient of ``coefficient`` (R17)."""
+    c = coefficient(phi).reshape(-1)
     idx = np.arange(phi.size).reshape(phi.shape)
     out = []
     for d in range(g.dim):

@@ -762,6 +762,14 @@ static int rhs_dir(const or_grid *g, int dir, const double *U, double *Lout) {
   return err;
 }
 
+/* R17: the coefficient phi (1 - phi) of Eq. 4 is taken as 0 for fractions
+ * within one unit of rounding of 0 or 1 (phi < 2^-52 or 1 - phi < 2^-52):
+ * such traces, left by the hyperbolic step far from any interface, are
+ * below the resolution of the fraction sum.  A cell with an active fraction
+ * couples its faces. */
+#define OR_TRACE 0x1p-52
+static int pf_active(double a) { return a >= OR_TRACE && 1.0 - a >= OR_TRACE; }
+
 /* R12: Phase-Field flux at one face (Eq. 5), direction dir, from the face
  * states (UL, VL) of the left cell and (UR, VR) of the right cell and the face
  * gradients G[p] of Q_p.  F is the flux vector of Eq. 1 (last line). */
@@ -864,10 +872,10 @@ int or_pf_rhs(const or_grid *g, const double *U, const double *Q, double dt_limi
         double G[OR_MAXP];
         for (int p = 0; p < N; p++) {
           /* R17: G = 0 on a face that Eq. 4 does not couple, c_f = 0 (both
-           * cells with phi (1 - phi) <= 0) */
+           * cells with a zero coefficient) */
           double al = U[(long)IALF(g, p) * nc + base + jl * stride];
           double ar = U[(long)IALF(g, p) * nc + base + jr * stride];
-          int coupled = al * (1.0 - al) > 0.0 || ar * (1.0 - ar) > 0.0;
+          int coupled = pf_active(al) || pf_active(ar);
           G[p] = coupled ? (Q[(long)p * nc + base + jr * stride] -
                             Q[(long)p * nc + base + jl * stride]) / dx
                          : 0.0;

@@ -1121,12 +1121,19 @@ __device__ __forceinline__ void riemann(const Mat& m, int dir, int hllc, const F
 // masses), which leaves an absent phase untouched.  Momentum and energy
 // follow the last line of Eq. 1 with the mean face velocity and pressure.
 // The face gradient of Q_p handed to the Phase-Field flux (Eq. 4-5, reading
-// R17): zero on a face Eq. 4 does not couple (both cells with
-// phi (1 - phi) <= 0), else (q_r - q_l)/dx limited to |G| <= gmax (gmax > 0,
-// the Phase-Field step's sufficient condition for bounds).
+// R17): zero on a face Eq. 4 does not couple (both cells with a zero
+// coefficient), else (q_r - q_l)/dx limited to |G| <= gmax (gmax > 0, the
+// Phase-Field step's sufficient condition for bounds).
+// A fraction couples its cell's faces in Eq. 4 when its coefficient
+// phi (1 - phi) is nonzero; fractions within one unit of rounding of 0 or 1
+// (phi < 2^-52 or 1 - phi < 2^-52, traces the hyperbolic step leaves far
+// from any interface) count as 0 (reading R17).
+constexpr double PF_TRACE = 0x1p-52;
+__device__ __forceinline__ bool pf_active(double a) { return a >= PF_TRACE && 1.0 - a >= PF_TRACE; }
+
 __device__ __forceinline__ double pf_gradient(double ql, double qr, double al, double ar,
                                               double inv_dx, double gmax) {
-  const bool coupled = al * (1.0 - al) > 0.0 || ar * (1.0 - ar) > 0.0;
+  const bool coupled = pf_active(al) || pf_active(ar);
   double G = coupled ? (qr - ql) * inv_dx : 0.0;
   if (gmax > 0.0) G = G > gmax ? gmax : (G < -gmax ? -gmax : G);
   return G;

@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_qm_coef(const double* __restrict
 #pragma unroll
     for (int p = 0; p < N; p++) {
       const double f = U[(long)(g.a0 + p) * n + i];
-      c[(long)p * n + i] = fmax(f * (1.0 - f), 0.0);
+      c[(long)p * n + i] = pf_active(f) ? f * (1.0 - f) : 0.0;
     }
   }
 }

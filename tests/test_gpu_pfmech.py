@@ -94,12 +94,13 @@ def test_qmap_solution(gpu, name):
     assert np.abs(F - F_or).max() <= 1e-8 * max(np.abs(F_or).max(), 1e-300)
 
 
-def test_qmap_denormal_coefficient_next_to_zero(gpu):
-    """A cell whose coefficient phi (1 - phi) is the smallest denormal,
-    beside cells with phi = 0: (c_a + c_b)/2 rounds to 0 on both of its
-    faces, so Eq. 4 couples it to nothing, while its neighbour belongs to
-    the interface band through its other face.  The region labelling must
-    follow the operator's face weights; Q then solves the oracle's Eq. 4."""
+def test_qmap_trace_fraction_next_to_zero(gpu):
+    """A cell holding a trace fraction (the smallest denormal, below 2^-52:
+    coefficient 0 by R17) beside cells with phi = 0, while its neighbour
+    belongs to the interface band through its other face: Eq. 4 couples it
+    to nothing.  The region labelling follows the operator's face weights
+    (it never reads the label of a cell off the band); Q solves the
+    oracle's Eq. 4 and is 0 at the trace cell."""
     case = inputs.interface_advection_1d(n=200)
     go, g = _grids(case)
     U = oracle.prim_to_cons(go, case.V)
@@ -113,8 +114,8 @@ def test_qmap_denormal_coefficient_next_to_zero(gpu):
     U[a0 + 1, i] = 1.0 - tiny                   # = 1.0
     U[0, i] = tiny                              # the air mass (rho_air = 1)
     phi = pf.fractions(go, U)
-    c = np.maximum(phi * (1.0 - phi), 0.0)
-    assert c[0, i] == tiny and 0.5 * (c[0, i] + c[0, i + 1]) == 0.0 and c[0, k] > 0.0
+    c = pf.coefficient(phi)
+    assert phi[0, i] == tiny and c[0, i] == 0.0 and c[0, i + 1] == 0.0 and c[0, k] > 0.0
     Ud = to_dev(U)
     g.bind(Ud).set_pf_workspace(Ud.device)
     g.cac_rhs(Ud)
