@@ -141,6 +141,18 @@ size_t wc_face_buffer_bytes(const wc_grid *g);
  * which selects the single-pass sweep). */
 wc_status wc_set_state(wc_grid *g, double *U_dev, void *workspace_dev, size_t ws_bytes);
 
+/* Validates a state against the admissible set of Eq. 8 (the paper's
+ * definition of the states the scheme preserves): for every cell, masses
+ * >= 0, fractions in [0, 1] with |sum_p alpha_p - 1| <= sum_tol, a positive
+ * density, psi >= 0 (Eq. 9, the phasic minimum pressures of the grid), all
+ * values finite.  U_dev: [NV][ncell] device state (e.g. before binding it
+ * with wc_set_state); needs a bound workspace (two counters in its tail).
+ * Synchronises stream.  Returns WC_ERR_INADMISSIBLE (message in
+ * wc_last_error) when a cell is outside; *nbad and *first_bad (may be
+ * null) receive the count and the first such cell (-1 when none). */
+wc_status wc_check_state(wc_grid *g, const double *U_dev, double sum_tol, long *nbad,
+                         long *first_bad, void *stream);
+
 /* Copies a host state (pinned memory recommended) into / out of the bound
  * device state, asynchronously on stream. */
 wc_status wc_upload_state(wc_grid *g, const double *U_host, void *stream);

@@ -227,6 +227,35 @@ extern "C" wc_status wc_set_state(wc_grid* g, double* U_dev, void* ws, size_t ws
   return WC_OK;
 }
 
+extern "C" wc_status wc_check_state(wc_grid* g, const double* U_dev, double sum_tol,
+                                    long* nbad, long* first_bad, void* stream) {
+  if (!g || !U_dev || !(sum_tol >= 0.0)) return WC_ERR_ARG;
+  if (!g->ws) return fail(g, WC_ERR_STATE, "wc_check_state needs a bound workspace");
+  // two counters in the workspace tail (bytes 64..79, unused by the steps)
+  unsigned long long* bad = reinterpret_cast<unsigned long long*>(g->ws + 3 * ((g->nv * g->ncell * 8 + 255) / 256 * 256) + 64);
+  const unsigned long long init[2] = {0ull, ~0ull};
+  cudaStream_t st = S(stream);
+  cudaError_t e = cudaMemcpyAsync(bad, init, sizeof(init), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "check init");
+  int blocks = grid_blocks(g->ncell, 256);
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  WC_DISPATCH(g->d.nphase, g->d.dim,
+              (k_check_state<N_, D_><<<blocks, 256, 0, st>>>(U_dev, g->ncell, g->mat, sum_tol, bad)));
+  unsigned long long out[2] = {0ull, 0ull};
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, bad, sizeof(out), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "check");
+  if (nbad) *nbad = (long)out[0];
+  if (first_bad) *first_bad = out[0] ? (long)out[1] : -1;
+  if (out[0]) {
+    snprintf(g->err, sizeof(g->err), "%llu cell(s) outside the admissible set, first %llu",
+             out[0], out[1]);
+    return WC_ERR_INADMISSIBLE;
+  }
+  return WC_OK;
+}
+
 extern "C" wc_status wc_upload_state(wc_grid* g, const double* U_host, void* stream) {
   if (!g || !U_host) return WC_ERR_ARG;
   if (!g->U) return fail(g, WC_ERR_STATE, "no state bound");

@@ -117,6 +117,42 @@ __global__ void k_temperature(const double* __restrict__ U, double* __restrict__
   }
 }
 
+// Membership of each cell average in the admissible set of Eq. 8: masses
+// >= 0, fractions in [0, 1] summing to one within sum_tol, a positive
+// density and psi >= 0 (Eq. 9 with the phasic minimum pressures), every
+// value finite.  Counts the cells outside it (bad[0]) and the first such
+// cell (atomicMin on bad[1]).
+template <int N, int D>
+__global__ void k_check_state(const double* __restrict__ U, long ncell, Mat m, double sum_tol,
+                              unsigned long long* bad) {
+  using I = Idx<N, D>;
+  unsigned long long nbad = 0;
+  for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+       c += (long)gridDim.x * blockDim.x) {
+    double u[I::NV];
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < I::NV; k++) {
+      u[k] = __ldg(U + (long)k * ncell + c);
+      ok = ok && !not_finite(u[k]);
+    }
+    double rho = 0.0, s = 0.0;
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      ok = ok && u[p] >= 0.0 && u[I::A(p)] >= 0.0 && u[I::A(p)] <= 1.0;
+      rho += u[p];
+      s += u[I::A(p)];
+    }
+    ok = ok && rho > 0.0 && fabs(s - 1.0) <= sum_tol && psi_cons<N, D>(m, u) >= 0.0;
+    if (!ok) {
+      nbad++;
+      atomicMin(bad + 1, (unsigned long long)c);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
+  if ((threadIdx.x & 31) == 0 && nbad) atomicAdd(bad, nbad);
+}
+
 // Eq. 17-21 on caller-given raw primitive faces of independent cells.
 template <int N, int D>
 __global__ void k_limit(const double* __restrict__ Ub, const double* __restrict__ VL,

@@ -91,6 +91,8 @@ _SIGS = {
     "wc_workspace_bytes": (ctypes.c_size_t, [_VP]),
     "wc_face_buffer_bytes": (ctypes.c_size_t, [_VP]),
     "wc_set_state": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_size_t]),
+    "wc_check_state": (ctypes.c_int, [_VP, _VP, ctypes.c_double, ctypes.POINTER(ctypes.c_long),
+                                      ctypes.POINTER(ctypes.c_long), _VP]),
     "wc_upload_state": (ctypes.c_int, [_VP, _VP, _VP]),
     "wc_download_state": (ctypes.c_int, [_VP, _VP, _VP]),
     "wc_prim_to_cons": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
@@ -271,14 +273,27 @@ class Grid:
             nb -= lib().wc_face_buffer_bytes(self.h)
         return torch.empty((nb + 7) // 8, dtype=torch.float64, device=device)
 
-    def bind(self, U, workspace=None):
-        """Binds the device state tensor (advanced in place by rk_step)."""
+    def bind(self, U, workspace=None, validate=False, sum_tol=1e-10):
+        """Binds the device state tensor (advanced in place by rk_step);
+        validate: check it against the admissible set of Eq. 8 first
+        (WcError WC_ERR_INADMISSIBLE when a cell is outside)."""
         if workspace is None:
             workspace = self.new_workspace(U.device)
         self.U, self.ws = U, workspace
         self._check(lib().wc_set_state(self.h, _ptr(U), _ptr(workspace),
                                        workspace.numel() * 8))
+        if validate:
+            self.check_state(U, sum_tol)
         return self
+
+    def check_state(self, U, sum_tol=1e-10, stream=None):
+        """(cells outside the admissible set, first such cell); raises
+        WcError WC_ERR_INADMISSIBLE when there are any."""
+        nb, first = ctypes.c_long(0), ctypes.c_long(0)
+        st = lib().wc_check_state(self.h, _ptr(U), float(sum_tol), ctypes.byref(nb),
+                                  ctypes.byref(first), _stream(stream))
+        self._check(st)
+        return nb.value, first.value
 
     def prim_to_cons(self, V, U=None, stream=None):
         U = torch.empty_like(V) if U is None else U

@@ -139,3 +139,44 @@ def test_status_reports_inadmissible_state(gpu):
         g.sync_status()
     assert ei.value.status in (3, 4)
     g.sync_status()  # cleared
+
+
+@pytest.mark.parametrize("kind", ["negative_mass", "fraction_above_one", "sum", "psi", "nan"])
+def test_check_state_admissible_set(gpu, kind):
+    """wc_check_state against Eq. 8 on a state injected on the host: the
+    clean state passes, one spoiled cell is reported (count 1, its index)."""
+    c = inputs.shock_bubble_2d(nx=64, ny=32, seed=2)
+    go, g = grids(c)
+    U = oracle.prim_to_cons(go, c.V)
+    Ud = to_dev(U)
+    g.bind(Ud, validate=True)
+    assert g.check_state(Ud) == (0, -1)
+    N, d = c.N, c.dim
+    cell = 17 * 64 + 11
+    V = U.reshape(U.shape[0], -1).copy()
+    if kind == "negative_mass":
+        V[0, cell] = -1e-3
+    elif kind == "fraction_above_one":
+        V[N + d + 1, cell] = 1.0 + 1e-9
+        V[N + d + 2, cell] = -1e-9
+    elif kind == "sum":
+        V[N + d + 1, cell] += 1e-6
+    elif kind == "psi":
+        V[N + d, cell] = 0.0          # rho E = 0: far below the energy bound
+    else:
+        V[N, cell] = np.nan
+    Vd = to_dev(V.reshape(U.shape))
+    with pytest.raises(wenoc.WcError) as ei:
+        g.check_state(Vd)
+    assert ei.value.status == 3
+    nb, first = ctypes_check(g, Vd)
+    assert nb == 1 and first == cell
+
+
+def ctypes_check(g, U):
+    import ctypes
+    nb, first = ctypes.c_long(0), ctypes.c_long(0)
+    rc = wenoc.lib().wc_check_state(g.h, ctypes.c_void_p(U.data_ptr()), 1e-10,
+                                    ctypes.byref(nb), ctypes.byref(first), None)
+    assert rc == 3
+    return nb.value, first.value
