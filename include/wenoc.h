@@ -420,6 +420,9 @@ typedef struct {
   int precision;       /* WC_PREC_FP64 or WC_PREC_MIXED */
   int energy_limiter;  /* 1: Eq. 21 applied */
   int npatch;
+  int kmodel;          /* K_p of Eq. 2-3, as in wc_grid_desc: WC_KMODEL_ALLAIRE
+                          (0, the default of a zero-filled descriptor) or
+                          WC_KMODEL_KAPILA; anything else is WC_ERR_ARG */
 } wc_patches_desc;
 
 typedef struct wc_patches wc_patches;

@@ -104,6 +104,7 @@ extern "C" wc_status wc_patches_init(const wc_patches_desc* desc, const int* edg
   if (d.npatch < 1) return WC_ERR_ARG;
   if (d.flux != WC_FLUX_HLL && d.flux != WC_FLUX_HLLC) return WC_ERR_ARG;
   if (d.precision != WC_PREC_FP64 && d.precision != WC_PREC_MIXED) return WC_ERR_UNSUPPORTED;
+  if (d.kmodel != WC_KMODEL_ALLAIRE && d.kmodel != WC_KMODEL_KAPILA) return WC_ERR_ARG;
   for (int p = 0; p < d.nphase; p++)
     if (!(d.gamma[p] > 1.0) || !(d.pinf[p] >= 0.0)) return WC_ERR_ARG;
   for (int i = 0; i < d.npatch; i++)
@@ -115,6 +116,7 @@ extern "C" wc_status wc_patches_init(const wc_patches_desc* desc, const int* edg
   Mat& m = g->mat;
   memset(&m, 0, sizeof(m));
   m.N = d.nphase;
+  m.kapila = d.kmodel == WC_KMODEL_KAPILA;
   for (int p = 0; p < d.nphase; p++) {
     m.A[p] = 1.0 / (d.gamma[p] - 1.0);
     m.B[p] = d.gamma[p] * d.pinf[p] / (d.gamma[p] - 1.0);

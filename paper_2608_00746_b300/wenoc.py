@@ -65,6 +65,7 @@ class PatchesDesc(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("energy_limiter", ctypes.c_int),
         ("npatch", ctypes.c_int),
+        ("kmodel", ctypes.c_int),
     ]
 
 
@@ -503,7 +504,7 @@ class Patches:
     per Runge-Kutta stage)."""
 
     def __init__(self, edges, gamma, pinf, D=None, pmin=None, flux="hll", precision="mixed",
-                 energy_limiter=True):
+                 energy_limiter=True, kmodel="allaire"):
         N = len(gamma)
         d = PatchesDesc()
         d.nphase = N
@@ -515,6 +516,7 @@ class Patches:
         d.precision = PREC[precision]
         d.energy_limiter = int(bool(energy_limiter))
         d.npatch = len(edges)
+        d.kmodel = KMODEL[kmodel]
         self.edges = [int(e) for e in edges]
         arr = (ctypes.c_int * len(edges))(*self.edges)
         h = _VP()

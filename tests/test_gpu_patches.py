@@ -116,3 +116,60 @@ def test_patch_autotune_restores_state(gpu):
     assert best["block"] in (64, 128) and best["ctas_per_sm"] in (2, 3, 4, 6)
     assert best["ms_per_step"] > 0
     assert np.array_equal(Ud.cpu().numpy(), U)
+
+
+def test_patch_kapila_parity(gpu):
+    """K_p of the Kapila model (Eq. 2-3, Wood's mixture speed) on every patch:
+    rhs and one SSP-RK3 step against the oracle run with the same model, FP64;
+    the mixed form within the L1 bound of the Allaire patches; a model outside
+    the two is refused at setup."""
+    edges, states, g, pi, Dm = batch(npatch=12, seed=11)
+
+    def ogrid(e):
+        return oracle.Grid((e, e, e), (1.0 / e,) * 3, g, pi, Dm, flux="hll",
+                           bc=("outflow",) * 6, kmodel="kapila")
+
+    P = wenoc.Patches(edges, g, pi, Dm, precision="fp64", kmodel="kapila")
+    grids = [ogrid(e) for e in edges]
+    Us = [oracle.prim_to_cons(go, S) for go, S in zip(grids, states)]
+    U = P.pack(Us)
+    Ud = to_dev(U)
+    P.bind(Ud)
+    L = P.rhs(Ud).cpu().numpy()
+    P.sync_status()
+    for p, (go, Up) in enumerate(zip(grids, Us)):
+        err = rhs_err(P.unpack(L, p), oracle.rhs(go, Up), Up, oracle.max_rate(go, Up), N, D,
+                      mom_floor=momentum_floor(go, Up))
+        assert (err <= 1e-12).all(), (p, edges[p], err)
+    # the CFL rate of the Kapila model differs from the Allaire one on mixed cells
+    rate = max(oracle.max_rate(go, Up) for go, Up in zip(grids, Us))
+    dt = 0.2 / rate
+    P.rk_step(dt=dt)
+    torch.cuda.synchronize()
+    P.sync_status()
+    U1 = Ud.cpu().numpy()
+    for p, (go, Up) in enumerate(zip(grids, Us)):
+        Uo, _ = oracle.rk3_step(go, Up, dt=dt)
+        err = state_err(P.unpack(U1, p), Uo, N, D, mom_floor=momentum_floor(go, Uo))
+        assert (err <= 1e-12).all(), (p, err)
+    # the device CFL step uses Wood's speed: one step at cfl=0.2 matches the
+    # oracle step at the oracle's Kapila dt
+    Uc = to_dev(U)
+    P.bind(Uc)
+    P.rk_step(cfl=0.2)
+    torch.cuda.synchronize()
+    P.sync_status()
+    U2 = Uc.cpu().numpy()
+    for p, (go, Up) in enumerate(zip(grids, Us)):
+        Uo, _ = oracle.rk3_step(go, Up, dt=dt)
+        assert (state_err(P.unpack(U2, p), Uo, N, D, mom_floor=momentum_floor(go, Uo))
+                <= 1e-12).all(), p
+    Pm = wenoc.Patches(edges, g, pi, Dm, precision="mixed", kmodel="kapila")
+    Um = to_dev(U)
+    Pm.bind(Um)
+    Pm.rk_step(dt=dt)
+    torch.cuda.synchronize()
+    Pm.sync_status()
+    assert (l1_group(Um.cpu().numpy(), U1, N, D) <= 1e-5).all()
+    with pytest.raises(KeyError):
+        wenoc.Patches(edges, g, pi, Dm, kmodel="stiffened")
