@@ -839,6 +839,127 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
 //     k_qmap_cg_mem (w.flag[18] set), which iterates with it in memory;
 //  4. x written back to the grid (cold start: 0 off the list).
 // A phase whose alpha is not positive stops where it is.
+// x 2^k for |k| <= 2000 as two exact power-of-two factors (each in
+// [-1000, 1000], a normal double): exact unless the result leaves the
+// normal range.
+__device__ __forceinline__ double pf_pow2(int j) {
+  return __longlong_as_double((long long)(j + 1023) << 52);
+}
+__device__ __forceinline__ double pf_scale2(double x, int k) {
+  const int k1 = k / 2;
+  return (x * pf_pow2(k1)) * pf_pow2(k - k1);
+}
+
+// Exponent E of a positive finite double given by its bits: 2^E <= M < 2^(E+1).
+__device__ __forceinline__ int pf_exponent(unsigned long long bits) {
+  const int ef = (int)(bits >> 52);
+  return ef > 0 ? ef - 1023 : -1074 + (63 - __clzll((long long)bits));
+}
+
+// Region sums of R and D (the right-hand side's consistency shift of Eq. 4:
+// sum_region R / sum_region D), the same bit for bit whatever the order in
+// which threads add.  Per region and quantity the largest magnitude M,
+// 2^E <= M < 2^(E+1), fixes a scale; each value x becomes y = x 2^(31-E),
+// |y| < 2^32, split into hi = floor(y) and lo = floor((y - hi) 2^32) in
+// [0, 2^32) (both exact), and hi and lo are summed as 64-bit integers,
+// whose addition is associative and cannot overflow below 2^30 cells a
+// region.  The sum is then (sum hi 2^32 + sum lo) 2^(E-63): each value is
+// cut at 2^(E-63), below the 2^(E-53) rounding of one FP64 addition at
+// the region's scale.  Scratch: the iteration's vectors, which are written
+// before they are read once the sums are taken (maxima in r and xk, hi and
+// lo in p, q, pd and sd), at the region's label (a listed cell).  Three
+// grid barriers; false if one gave up.
+template <int N>
+__device__ __forceinline__ bool region_sums(const PfWork& w, int n, const int* scnt, int b, int G,
+                                            int t, unsigned* bar, int* err) {
+  typedef unsigned long long u64;
+  u64* mR = reinterpret_cast<u64*>(w.r);
+  u64* mD = reinterpret_cast<u64*>(w.xk);
+  u64* hR = reinterpret_cast<u64*>(w.p);
+  u64* lR = reinterpret_cast<u64*>(w.q);
+  u64* hD = reinterpret_cast<u64*>(w.pd);
+  u64* lD = reinterpret_cast<u64*>(w.sd);
+  // (i) clear, and the magnitudes of the region's values
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    const long o = (long)p * n;
+    int k0, k1;
+    own_range(scnt[p], b, G, k0, k1);
+    for (int k = k0 + t; k < k1; k += PF_THREADS) {
+      const long a = o + __ldcg(w.idx + o + k);
+      mR[a] = mD[a] = hR[a] = lR[a] = hD[a] = lD[a] = 0ull;
+    }
+  }
+  if (!grid_sync(bar, err)) return false;
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    const long o = (long)p * n;
+    int k0, k1;
+    own_range(scnt[p], b, G, k0, k1);
+    for (int k = k0 + t; k < k1; k += PF_THREADS) {
+      const int i = __ldcg(w.idx + o + k);
+      const long l = o + __ldcg(w.lab + o + i);
+      // the bits of |x| order as |x| does
+      atomicMax(mR + l, (u64)__double_as_longlong(fabs(w.R[o + i])));
+      atomicMax(mD + l, (u64)__double_as_longlong(fabs(w.D[o + i])));
+    }
+  }
+  if (!grid_sync(bar, err)) return false;
+  // (ii) the fixed-point parts, added as integers (two's complement wraps
+  // to the signed sum)
+  auto split = [](double x, u64 mbits, u64& hi, u64& lo) {
+    if (mbits == 0ull || mbits >= 0x7ff0000000000000ull) {
+      hi = lo = 0ull;
+      return;
+    }
+    const double y = pf_scale2(x, 31 - pf_exponent(mbits));
+    const double f = floor(y);
+    hi = (u64)(long long)f;
+    lo = (u64)(long long)floor((y - f) * 4294967296.0);
+  };
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    const long o = (long)p * n;
+    int k0, k1;
+    own_range(scnt[p], b, G, k0, k1);
+    for (int k = k0 + t; k < k1; k += PF_THREADS) {
+      const int i = __ldcg(w.idx + o + k);
+      const long l = o + __ldcg(w.lab + o + i);
+      u64 hi, lo;
+      split(w.R[o + i], __ldcg(mR + l), hi, lo);
+      atomicAdd(hR + l, hi);
+      atomicAdd(lR + l, lo);
+      split(w.D[o + i], __ldcg(mD + l), hi, lo);
+      atomicAdd(hD + l, hi);
+      atomicAdd(lD + l, lo);
+    }
+  }
+  if (!grid_sync(bar, err)) return false;
+  // (iii) back to FP64 at each region's label; a region holding a value
+  // that is not finite sums to NaN
+  auto join = [](u64 mbits, u64 hs, u64 ls) {
+    if (mbits == 0ull) return 0.0;
+    if (mbits >= 0x7ff0000000000000ull) return __longlong_as_double(0x7ff8000000000000ll);
+    const long long h = (long long)hs + (long long)(ls >> 32);
+    const double v = fma((double)h, 4294967296.0, (double)(long long)(ls & 0xffffffffull));
+    return pf_scale2(v, pf_exponent(mbits) - 63);
+  };
+#pragma unroll
+  for (int p = 0; p < N; p++) {
+    const long o = (long)p * n;
+    int k0, k1;
+    own_range(scnt[p], b, G, k0, k1);
+    for (int k = k0 + t; k < k1; k += PF_THREADS) {
+      const int i = __ldcg(w.idx + o + k);
+      if (__ldcg(w.lab + o + i) != i) continue;
+      const long a = o + i;
+      w.sumR[a] = join(__ldcg(mR + a), __ldcg(hR + a), __ldcg(lR + a));
+      w.sumD[a] = join(__ldcg(mD + a), __ldcg(hD + a), __ldcg(lD + a));
+    }
+  }
+  return grid_sync(bar, err);
+}
+
 template <int N>
 __global__ void __launch_bounds__(PF_THREADS) k_qmap_cg(PfGeom g, PfWork w, double tol2, int warm,
                                                         int maxit) {
@@ -963,33 +1084,9 @@ __global__ void __launch_bounds__(PF_THREADS) k_qmap_cg(PfGeom g, PfWork w, doub
     }
   }
   if (b == 0 && t == 0) w.flag[23] = rounds;
-  // 1c. region sums of R and D over the listed cells (FP64 atomics, so
-  // their rounding varies between runs); the labels are listed cells
-#pragma unroll
-  for (int p = 0; p < N; p++) {
-    const long o = (long)p * n;
-    int k0, k1;
-    own_range(scnt[p], b, G, k0, k1);
-    for (int k = k0 + t; k < k1; k += PF_THREADS) {
-      const int i = __ldcg(w.idx + o + k);
-      w.sumR[o + i] = 0.0;
-      w.sumD[o + i] = 0.0;
-    }
-  }
-  if (!grid_sync(bar, err)) return;
-#pragma unroll
-  for (int p = 0; p < N; p++) {
-    const long o = (long)p * n;
-    int k0, k1;
-    own_range(scnt[p], b, G, k0, k1);
-    for (int k = k0 + t; k < k1; k += PF_THREADS) {
-      const int i = __ldcg(w.idx + o + k);
-      const int l = __ldcg(w.lab + o + i);
-      atomicAdd(w.sumR + o + l, w.R[o + i]);
-      atomicAdd(w.sumD + o + l, w.D[o + i]);
-    }
-  }
-  if (!grid_sync(bar, err)) return;
+  // 1c. region sums of R and D over the listed cells, in fixed point so
+  // that the order of the additions does not matter (region_sums)
+  if (!region_sums<N>(w, n, scnt, b, G, t, bar, err)) return;
 
   // unknowns a thread keeps in registers: one, two (N <= 2), else the
   // iteration on the lists in memory below

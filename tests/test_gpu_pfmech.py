@@ -314,3 +314,52 @@ def test_qmap_and_full_step_without_an_interface(gpu):
     g.sync_status()
     g2.sync_status()
     assert torch.equal(Ud, U2)
+
+
+@pytest.mark.parametrize("name", ["shock_bubble_2d_ragged", "spheres_3d_ragged", "in_memory"])
+def test_qmap_and_full_steps_repeat_bit_for_bit(gpu, name):
+    """The Q-map's region sums are order-independent and its reductions run
+    in a fixed order, so Q (register-resident and in-memory iterations
+    alike) and full time steps are the same bit for bit on every run."""
+    if name == "in_memory":
+        case = inputs.multiphase_advection_2d(n=210, nphase=3)
+        go, g = _grids(case)
+        V = case.V.copy()
+        ny, nx = V.shape[1:]
+        yy, xx = np.meshgrid((np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx,
+                             indexing="ij")
+        a1 = 0.35 + 0.2 * np.sin(2 * np.pi * xx) * np.sin(2 * np.pi * yy)
+        a2 = 0.3 + 0.15 * np.cos(2 * np.pi * xx)
+        a = [a1, a2, 1.0 - a1 - a2]
+        for p in range(3):
+            V[p] = inputs.TABLE1[p][0] * a[p]
+            V[6 + p] = a[p]
+        U = oracle.prim_to_cons(go, V)
+        dt = None
+    else:
+        case, go, g, U = _evolved(name, steps=5)
+        dt = case.meta.get("dt") if case.meta else None
+    Ud = to_dev(U)
+    g.bind(Ud).set_pf_workspace(Ud.device)
+    g.cac_rhs(Ud)
+    runs = [g.qmap(Ud, tol=1e-12, maxit=20000) for _ in range(3)]
+    if name == "in_memory":
+        assert g.pf_band()[1] == 0
+    for Q, iters, res in runs[1:]:
+        assert iters == runs[0][1] and res == runs[0][2]
+        assert torch.equal(Q, runs[0][0])
+    if name == "in_memory":
+        return
+    # full steps start the Q-map from the grid's last Q: a fresh grid each
+    outs = []
+    for _ in range(2):
+        _, g = _grids(case)
+        Us = to_dev(U)
+        g.bind(Us).set_pf_workspace(Us.device)
+        if dt:
+            g.step(dt=dt, nsteps=3)
+        else:
+            g.step(cfl=case.cfl or 0.2, nsteps=3)
+        g.sync_status()
+        outs.append(Us)
+    assert torch.equal(outs[0], outs[1])
