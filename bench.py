@@ -710,17 +710,19 @@ def run_configs(args, make_grid, timed_steps, barrier, dev, learned):
     fl = roofline.flops_per_cell_dir(3, 3, "hll")
     d4 = {}
     for prec, (ms, _) in res.items():
+        kind = {0: "persistent, static", 1: "persistent, queue", 2: "window sweeps"}
         d4[prec] = {"value": round(ncell4 * 3 / (ms * 1e-3) / 1e6, 3), "ms_per_step": round(ms, 4),
-                    "schedule": sched[prec]}
+                    "schedule": dict(sched[prec], kind=kind.get(sched[prec]["dynamic"]))}
     d4["fp64"]["frac"] = round(fl * 3 * ncell4 * 3 / (res["fp64"][0] * 1e-3) / 1e12 / peak64, 4)
     d4["mixed"]["speedup_vs_fp64"] = round(res["fp64"][0] / res["mixed"][0], 3)
     d4["mixed"]["l1_rel_vs_fp64_max_var"] = group_l1(finals["fp64"], finals["mixed"], 3, 3)
     d4["steps"] = args.steps4
     d4["cells"] = int(ncell4)
     out["patches"] = dict(workload=f"patch_batch {args.npatch} cube patches, edges "
-                          "{8,12,16,24,32}, N=3 HLL CFL 0.2 (dt on the device each step), one "
-                          "persistent launch per stage, CUDA graph replay, autotuned; L1 of "
-                          "mixed against FP64 after the timed steps", **d4)
+                          "{8,12,16,24,32}, N=3 HLL CFL 0.2 (dt on the device each step), "
+                          "autotuned schedule (one persistent launch per stage, or window "
+                          "sweeps per group of equal patches), CUDA graph replay; L1 of mixed "
+                          "against FP64 after the timed steps", **d4)
     del finals
     torch.cuda.empty_cache()
     return out

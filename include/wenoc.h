@@ -436,16 +436,31 @@ long wc_patches_offset(const wc_patches *g, int patch);
 /* Four pooled state buffers (two stages, accumulator, autotune backup) plus
  * the patch table. */
 size_t wc_patches_workspace_bytes(const wc_patches *g);
+/* The part of wc_patches_workspace_bytes that holds the face buffer of the
+ * window schedule's split sweep (mixed precision; 0 for FP64): room for the
+ * face states of the largest group of equal patches, (2 NV + 1) e^2 (e + 2)
+ * doubles a patch of edge e. */
+size_t wc_patches_face_buffer_bytes(const wc_patches *g);
 /* Binds the pooled device state and workspace (256-byte aligned), uploads
- * the patch table on stream and synchronises it. */
+ * the patch table on stream and synchronises it.  A workspace of at least
+ * wc_patches_workspace_bytes - wc_patches_face_buffer_bytes is accepted:
+ * without the face buffer the window schedule's mixed-precision sweep runs
+ * in one pass (the same results, bit for bit); below that, WC_ERR_ARG. */
 wc_status wc_patches_set_state(wc_patches *g, double *U_dev, void *workspace_dev,
                                size_t ws_bytes, void *stream);
-/* Schedule: threads per CTA (32/64/96/128), CTAs per SM (1..16), dynamic
- * queue (1) or static round-robin (0). */
+/* Schedule: threads per CTA (32/64/96/128), CTAs per SM (1..16), and the
+ * kind: 1 one persistent launch per stage, CTAs taking whole patches from a
+ * queue (largest first), each thread marching whole pencils; 0 the same with
+ * a static round-robin; 2 window sweeps: per direction, one launch per
+ * group of equal patches over all their pencils, one cell per lane in
+ * windows of 32 (the grids' sweep, pencils mapped to patches through an
+ * offset table; outflow cells at every pencil end), in mixed precision the
+ * face and flux passes of the split sweep; block and CTAs per SM are then
+ * those of the window sweep.  Anything else: WC_ERR_ARG. */
 wc_status wc_patches_set_schedule(wc_patches *g, int block, int ctas_per_sm, int dynamic);
 /* nsteps SSP-RK3 steps of every patch, one global dt (cfl, or dt_fixed > 0)
  * from all patches.  use_graph = 1 captures one step (rate reduction, queue
- * reset, three stage launches) into a CUDA graph on the first call and
+ * reset, the stage launches) into a CUDA graph on the first call and
  * replays it; stream must then be a created stream, not the legacy default. */
 wc_status wc_patches_rk_step(wc_patches *g, double cfl, double dt_fixed, int nsteps,
                              int use_graph, void *stream);
@@ -456,8 +471,9 @@ wc_status wc_patches_prim_to_cons(const wc_patches *g, const double *V_dev, doub
 wc_status wc_patches_rhs(wc_patches *g, const double *U_dev, double *L_dev, void *stream);
 wc_status wc_patches_sync_status(wc_patches *g, void *stream);
 /* Times every candidate schedule (block 64/128 x CTAs per SM 2/3/4/6 x
- * dynamic/static) over `steps` steps on a copy of the bound state (the state
- * is restored), applies and returns the fastest. */
+ * dynamic/static persistent launches, and window sweeps of 128-thread
+ * blocks at 2/3/4 per SM) over `steps` steps on a copy of the bound state
+ * (the state is restored), applies and returns the fastest. */
 wc_status wc_patches_autotune(wc_patches *g, double cfl, int steps, void *stream, int *block,
                               int *ctas_per_sm, int *dynamic, double *ms_per_step);
 void wc_patches_last_error(const wc_patches *g, char *buf, size_t n);

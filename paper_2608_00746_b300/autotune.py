@@ -3,7 +3,8 @@
 ``wc_patches_autotune`` (native) times every candidate schedule on the bound
 state and keeps the fastest.  This module remembers the winner per GPU and
 workload so later runs skip the search: the key is the GPU name plus a hash
-of the patch-size histogram, phase count, flux and precision.
+of the patch-size histogram, phase count, flux, precision and the number of
+schedule kinds the library tries.
 """
 from __future__ import annotations
 
@@ -20,8 +21,10 @@ def key(patches, precision, flux, nphase):
     hist = {}
     for e in patches.edges:
         hist[e] = hist.get(e, 0) + 1
+    # "kinds": the schedule kinds the library tries (a cache written when it
+    # tried fewer is not reused)
     blob = json.dumps({"hist": sorted(hist.items()), "precision": precision, "flux": flux,
-                       "nphase": nphase}, sort_keys=True)
+                       "nphase": nphase, "kinds": 3}, sort_keys=True)
     gpu = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
     return gpu + ":" + hashlib.sha256(blob.encode()).hexdigest()[:16]
 

@@ -11,6 +11,7 @@
 #include "../../include/wenoc.h"
 #include "wenoc_kernels.cuh"
 #include "wenoc_patches.cuh"
+#include "wenoc_window.cuh"
 
 using namespace wc;
 
@@ -56,6 +57,12 @@ cudaError_t launch_patch_rate(int N, const double* U, long ncell, const int* edg
 
 }  // namespace wc
 
+// The patches of one edge e, for the window schedule: their first cells in
+// the pooled state at gpoff[first .. first + count).
+struct PatchGroup {
+  int e, first, count;
+};
+
 struct wc_patches {
   wc_patches_desc d;
   Mat mat;
@@ -63,6 +70,8 @@ struct wc_patches {
   std::vector<int> edge;
   std::vector<long> off;
   std::vector<int> order;
+  std::vector<PatchGroup> groups;  // by decreasing edge
+  std::vector<long> gpoff;
   long ncell = 0;
   // bindings
   double* U = nullptr;
@@ -72,10 +81,13 @@ struct wc_patches {
   int* d_edge = nullptr;
   long* d_off = nullptr;
   int* d_order = nullptr;
+  long* d_gpoff = nullptr;
+  double* fbuf = nullptr;    // face buffer of the split window sweep (mixed)
+  unsigned* d_ticket = nullptr;  // window queue (next window, warps finished)
   int* d_counter = nullptr;  // 3 queue heads (one per stage)
   unsigned long long* d_rate = nullptr;
   unsigned* d_status = nullptr;
-  // schedule
+  // schedule (dynamic: 1 queue of patches, 0 round-robin, 2 window sweeps)
   int block = 64, ctas_per_sm = 4, dynamic = 1;
   // captured step
   cudaGraphExec_t gexec = nullptr;
@@ -141,6 +153,16 @@ extern "C" wc_status wc_patches_init(const wc_patches_desc* desc, const int* edg
   // largest patch first (longest processing time first), ties by index
   std::stable_sort(g->order.begin(), g->order.end(),
                    [&](int a, int b) { return edges[a] > edges[b]; });
+  // window schedule: the patches of each edge, largest edge first, each
+  // group in patch order
+  for (int i : g->order) {
+    if (g->groups.empty() || g->groups.back().e != edges[i])
+      g->groups.push_back(PatchGroup{edges[i], (int)g->gpoff.size(), 0});
+    g->groups.back().count++;
+    g->gpoff.push_back(g->off[i]);
+  }
+  for (PatchGroup& gr : g->groups)
+    std::sort(g->gpoff.begin() + gr.first, g->gpoff.begin() + gr.first + gr.count);
   g->err[0] = 0;
   *out = g;
   return WC_OK;
@@ -160,19 +182,37 @@ extern "C" long wc_patches_offset(const wc_patches* g, int p) {
 static size_t table_bytes(const wc_patches* g) {
   size_t np = g->edge.size();
   return round256(np * sizeof(int)) + round256(np * sizeof(long)) + round256(np * sizeof(int)) +
-         256;
+         round256(np * sizeof(long)) + 256;
+}
+
+// The split window sweep's face buffer (mixed precision): room for the
+// largest group of patches, whose sweeps run one group at a time.
+static size_t face_buffer_bytes(const wc_patches* g) {
+  if (g->d.precision != WC_PREC_MIXED) return 0;
+  long most = 0;
+  for (const PatchGroup& gr : g->groups)
+    most = std::max(most, fbuf_doubles(g->nv, (long)gr.count * gr.e * gr.e, gr.e));
+  return round256((size_t)most * sizeof(double));
+}
+
+static size_t base_bytes(const wc_patches* g) {
+  size_t state = round256((size_t)g->nv * g->ncell * sizeof(double));
+  return 4 * state + table_bytes(g);
+}
+
+extern "C" size_t wc_patches_face_buffer_bytes(const wc_patches* g) {
+  return g ? face_buffer_bytes(g) : 0;
 }
 
 extern "C" size_t wc_patches_workspace_bytes(const wc_patches* g) {
   if (!g) return 0;
-  size_t state = round256((size_t)g->nv * g->ncell * sizeof(double));
-  return 4 * state + table_bytes(g);
+  return base_bytes(g) + face_buffer_bytes(g);
 }
 
 extern "C" wc_status wc_patches_set_state(wc_patches* g, double* U_dev, void* ws, size_t bytes,
                                           void* stream) {
   if (!g || !U_dev || !ws) return WC_ERR_ARG;
-  if (bytes < wc_patches_workspace_bytes(g)) return pfail(g, WC_ERR_ARG, "workspace too small");
+  if (bytes < base_bytes(g)) return pfail(g, WC_ERR_ARG, "workspace too small");
   if (reinterpret_cast<uintptr_t>(ws) & 255) return pfail(g, WC_ERR_ARG, "workspace alignment");
   size_t state = round256((size_t)g->nv * g->ncell * sizeof(double));
   size_t np = g->edge.size();
@@ -190,9 +230,16 @@ extern "C" wc_status wc_patches_set_state(wc_patches* g, double* U_dev, void* ws
   t += round256(np * sizeof(long));
   g->d_order = (int*)t;
   t += round256(np * sizeof(int));
+  g->d_gpoff = (long*)t;
+  t += round256(np * sizeof(long));
   g->d_counter = (int*)t;                 // 3 ints
   g->d_rate = (unsigned long long*)(t + 64);
   g->d_status = (unsigned*)(t + 128);
+  g->d_ticket = (unsigned*)(t + 192);     // 2 unsigned
+  // without room for the face buffer the mixed window sweep runs in one pass
+  g->fbuf = bytes >= wc_patches_workspace_bytes(g) && face_buffer_bytes(g)
+                ? (double*)(g->ws + base_bytes(g))
+                : nullptr;
   cudaStream_t st = PS(stream);
   cudaError_t e = cudaMemcpyAsync(g->d_edge, g->edge.data(), np * sizeof(int),
                                   cudaMemcpyHostToDevice, st);
@@ -200,6 +247,9 @@ extern "C" wc_status wc_patches_set_state(wc_patches* g, double* U_dev, void* ws
     e = cudaMemcpyAsync(g->d_off, g->off.data(), np * sizeof(long), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(g->d_order, g->order.data(), np * sizeof(int), cudaMemcpyHostToDevice,
+                        st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->d_gpoff, g->gpoff.data(), np * sizeof(long), cudaMemcpyHostToDevice,
                         st);
   if (e == cudaSuccess) e = cudaMemsetAsync(t, 0, 256, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -214,7 +264,7 @@ extern "C" wc_status wc_patches_set_state(wc_patches* g, double* U_dev, void* ws
 extern "C" wc_status wc_patches_set_schedule(wc_patches* g, int block, int ctas_per_sm,
                                              int dynamic) {
   if (!g || (block != 32 && block != 64 && block != 96 && block != 128) || ctas_per_sm < 1 ||
-      ctas_per_sm > 16 || (dynamic != 0 && dynamic != 1))
+      ctas_per_sm > 16 || dynamic < 0 || dynamic > 2)
     return WC_ERR_ARG;
   g->block = block;
   g->ctas_per_sm = ctas_per_sm;
@@ -257,6 +307,62 @@ static PatchArgs patch_args(wc_patches* g, const double* src, double* dst, doubl
 
 static int patch_grid(const wc_patches* g) { return 148 * g->ctas_per_sm; }
 
+// The window schedule: for each direction, the window sweep over the pencils
+// of each group of equal patches (pencil tr of a group in its patch
+// tr / e^2, at the offset table gpoff), outflow boundary cells at both ends
+// of every pencil; mixed precision splits each sweep into the face and the
+// flux pass when the workspace holds the face buffer.  Directions run in
+// order over all patches, so the accumulator modes are those of a grid:
+// L = x part, L += y part, then the stage (or L += z part for the rhs).
+static cudaError_t enqueue_windows(wc_patches* g, const double* src, double* dst, double* L,
+                                   double r0, double r1, double r2, double cfl, double dt,
+                                   int rhs_only, cudaStream_t st) {
+  const int mixed = g->d.precision == WC_PREC_MIXED;
+  for (int dir = 0; dir < 3; dir++) {
+    for (const PatchGroup& gr : g->groups) {
+      SweepArgs a;
+      memset(&a, 0, sizeof(a));
+      a.U = src;
+      a.L = L;
+      a.U0 = g->U;
+      a.Uout = dst;
+      a.rate = (const double*)g->d_rate;
+      a.cfl = cfl;
+      a.dt_fixed = dt;
+      a.rk0 = r0;
+      a.rk1 = r1;
+      a.rk2 = r2;
+      a.ncell = g->ncell;
+      a.nx = a.ny = a.nz = gr.e;
+      a.dir = dir;
+      a.n = gr.e;
+      a.stride = dir == 0 ? 1 : (dir == 1 ? (long)gr.e : (long)gr.e * gr.e);
+      a.npencil = (long)gr.count * gr.e * gr.e;
+      a.nwin = (gr.e + WIN - 1) / WIN;
+      a.ticket = g->d_ticket;
+      const WinPlan w = win_plan(gr.e, a.npencil);
+      a.wfull = w.wfull;
+      a.wtail = w.wtail;
+      a.wgrp = w.wgrp;
+      a.wslots = w.slots;
+      a.nitems = w.nitems;
+      a.max_threads = 148L * g->ctas_per_sm * g->block;  // ctas_per_sm resident blocks
+      a.inv_dx = (double)gr.e;  // unit-cube patch: dx = 1/e
+      a.bclo = a.bchi = BC_OUTFLOW;
+      a.mode = rhs_only ? (dir == 0 ? 0 : 1) : (dir == 0 ? 0 : (dir == 1 ? 1 : 2));
+      a.hllc = g->d.flux == WC_FLUX_HLLC;
+      a.energy_limiter = g->d.energy_limiter;
+      a.status = g->d_status;
+      a.poff = g->d_gpoff + gr.first;
+      a.fbuf = mixed ? g->fbuf : nullptr;
+      cudaError_t e = mixed ? launch_sweep_mixed(g->d.nphase, 3, a, g->mat, g->block, st)
+                            : launch_sweep_fp64(g->d.nphase, 3, a, g->mat, g->block, st);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
 // One SSP-RK3 step: rate reduction (unless dt is fixed), queue reset, three
 // persistent stage launches.
 static cudaError_t enqueue_step(wc_patches* g, double cfl, double dt, cudaStream_t st) {
@@ -276,7 +382,10 @@ static cudaError_t enqueue_step(wc_patches* g, double cfl, double dt, cudaStream
   PatchArgs a3 = patch_args(g, g->B2, g->U, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, cfl, dt, 2, 0,
                             g->Lacc);
   for (const PatchArgs* a : {&a1, &a2, &a3}) {
-    e = launch_patch_stage(g->d.nphase, mixed, *a, g->mat, g->block, patch_grid(g), st);
+    if (g->dynamic == 2)
+      e = enqueue_windows(g, a->U, a->Uout, a->L, a->rk0, a->rk1, a->rk2, cfl, dt, 0, st);
+    else
+      e = launch_patch_stage(g->d.nphase, mixed, *a, g->mat, g->block, patch_grid(g), st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -328,6 +437,10 @@ extern "C" wc_status wc_patches_rhs(wc_patches* g, const double* U, double* L, v
   cudaStream_t st = PS(stream);
   cudaError_t e = cudaMemsetAsync(g->d_counter, 0, 3 * sizeof(int), st);
   if (e != cudaSuccess) return pcuda(g, e, "counter reset");
+  if (g->dynamic == 2) {
+    e = enqueue_windows(g, U, nullptr, L, 0.0, 0.0, 0.0, 0.0, 0.0, 1, st);
+    return e == cudaSuccess ? WC_OK : pcuda(g, e, "patch rhs");
+  }
   PatchArgs a = patch_args(g, U, nullptr, 0, 0, 0, 0, 0, 0, 1, L);
   e = launch_patch_stage(g->d.nphase, g->d.precision == WC_PREC_MIXED, a, g->mat, g->block,
                          patch_grid(g), st);
@@ -362,14 +475,16 @@ extern "C" wc_status wc_patches_autotune(wc_patches* g, double cfl, int steps, v
   cudaEventCreate(&e1);
   const int blocks[] = {64, 128};
   const int ctas[] = {2, 3, 4, 6};
-  const int dyn[] = {1, 0};
+  const int dyn[] = {1, 0, 2};
   double best = -1.0;
   int bb = g->block, bc = g->ctas_per_sm, bd = g->dynamic;
   for (int b : blocks)
     for (int c : ctas)
       for (int d : dyn) {
-        // skip schedules whose resident CTAs cannot fit
+        // skip schedules whose resident CTAs cannot fit; the window sweep
+        // with 128-thread blocks at 2-4 per SM (its registers admit no more)
         if (b * c > 768) continue;
+        if (d == 2 && (b != 128 || c > 4)) continue;
         g->block = b;
         g->ctas_per_sm = c;
         g->dynamic = d;

@@ -90,6 +90,8 @@ __global__ void __launch_bounds__(128) k_patch_stage(PatchArgs pa, Mat m) {
       a.energy_limiter = pa.energy_limiter;
       a.status = pa.status;
       a.faceL = a.faceR = nullptr;
+      a.fbuf = nullptr;
+      a.poff = nullptr;
       for (int pc = threadIdx.x; pc < e * e; pc += blockDim.x) {
         long base;
         if (dir == 0) base = off + (long)pc * e;

@@ -72,7 +72,25 @@ struct SweepArgs {
   // stored components of a face state (FaceBuf), then the pressures
   // fbuf[(2 K * npencil + pencil) * (n + 2) + c + 1]
   double* fbuf;
+  // pencils of a set of equal cube patches (window schedule; null for a
+  // grid): pencil tr lies in patch tr / (nx ny), whose first cell in the
+  // pooled state is poff[tr / (nx ny)], at the patch's own pencil tr % (nx ny)
+  const long* poff;
 };
+
+// First cell of pencil tr of a direction sweep (x fastest; for dir 1 the
+// pencils run over x, then z).
+__device__ __forceinline__ long pencil_base(const SweepArgs& a, long tr) {
+  long o = 0;
+  if (a.poff) {
+    const long np = (long)a.nx * a.ny;  // pencils a patch (cube: every direction)
+    o = __ldg(a.poff + tr / np);
+    tr %= np;
+  }
+  if (a.dir == 0) return o + tr * a.nx;
+  if (a.dir == 1) return o + (tr / a.nx) * ((long)a.nx * a.ny) + tr % a.nx;
+  return o + tr;
+}
 
 // The components of a face state that the flux pass needs: all of U, the
 // velocity and the pressure for an FP64 flux (the physical fluxes of Eq. 1);

@@ -433,10 +433,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? WC_WIN_MINB64 : WC_WIN_M
         }
       }
     }
-    long base;
-    if (a.dir == 0) base = tr * a.nx;
-    else if (a.dir == 1) base = (tr / a.nx) * ((long)a.nx * a.ny) + tr % a.nx;
-    else base = tr;
+    const long base = pencil_base(a, tr);
     sweep_window<N, D, T, TF, LW, PART>(a, m, base, tr, c0, j, G, sb, active, store, slots, fsc,
                                         dt, bad, lstat);
   }
@@ -503,10 +500,7 @@ __global__ void __launch_bounds__(128) k_flux_win(SweepArgs a, Mat m) {
   for (long it = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
     const long tr = it % a.npencil;
     const int c0 = (int)(it / a.npencil) * WINF;
-    long base;
-    if (a.dir == 0) base = tr * a.nx;
-    else if (a.dir == 1) base = (tr / a.nx) * ((long)a.nx * a.ny) + tr % a.nx;
-    else base = tr;
+    const long base = pencil_base(a, tr);
     const int c = c0 - 1 + lane;
     const bool live = c <= a.n - 1;
     const int cc = live ? c : a.n - 1;  // lanes past the pencil's end: a copy, no update

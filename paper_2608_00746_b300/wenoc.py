@@ -122,6 +122,7 @@ _SIGS = {
     "wc_patches_ncell": (ctypes.c_long, [_VP]),
     "wc_patches_offset": (ctypes.c_long, [_VP, ctypes.c_int]),
     "wc_patches_workspace_bytes": (ctypes.c_size_t, [_VP]),
+    "wc_patches_face_buffer_bytes": (ctypes.c_size_t, [_VP]),
     "wc_patches_set_state": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_size_t, _VP]),
     "wc_patches_set_schedule": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "wc_patches_rk_step": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -554,8 +555,14 @@ class Patches:
         o = self.offsets[p]
         return pooled[:, o:o + e ** 3].reshape(self.nv, e, e, e)
 
-    def bind(self, U, stream=None):
-        n = (lib().wc_patches_workspace_bytes(self.h) + 7) // 8
+    def bind(self, U, stream=None, faces=True):
+        """Binds the pooled state with a new workspace; faces=False leaves out
+        the face buffer (the window schedule's mixed sweep then runs in one
+        pass)."""
+        b = lib().wc_patches_workspace_bytes(self.h)
+        if not faces:
+            b -= lib().wc_patches_face_buffer_bytes(self.h)
+        n = (b + 7) // 8
         self.ws = torch.empty(n, dtype=torch.float64, device=U.device)
         self.U = U
         self._check(lib().wc_patches_set_state(self.h, _ptr(U), _ptr(self.ws), n * 8,

@@ -57,9 +57,11 @@ def test_fullsize_spheres_256(gpu):
 
 
 def test_fullsize_patches_sampled(gpu):
-    """All 4096 patches on the GPU (one persistent launch per direction set);
-    12 seeded patches of every edge class checked against the oracle run on
-    each patch as its own grid (outflow boundaries, cell size 1/edge)."""
+    """All 4096 patches on the GPU, in the persistent schedule (one launch
+    for the direction set) and in the window schedule (window sweeps over
+    each group of equal patches); 12 seeded patches of every edge class
+    checked against the oracle run on each patch as its own grid (outflow
+    boundaries, cell size 1/edge)."""
     edges, states, (g3, pi, Dm) = inputs.patch_batch(npatch=4096, seed=0)
     edges = [int(e) for e in edges]
     P = wenoc.Patches(edges, g3, pi, Dm, precision="fp64")
@@ -74,6 +76,9 @@ def test_fullsize_patches_sampled(gpu):
     P.bind(Ud)
     L = P.rhs(Ud).cpu().numpy()
     P.sync_status()
+    P.set_schedule(128, 3, 2)
+    Lw = P.rhs(Ud).cpu().numpy()
+    P.sync_status()
     rng = np.random.default_rng(7)
     picks = []
     for e in sorted(set(edges)):
@@ -84,6 +89,7 @@ def test_fullsize_patches_sampled(gpu):
         go = grids[e]
         U = P.unpack(pooled, p)
         L_or = oracle.rhs(go, np.ascontiguousarray(U))
-        err = rhs_err(P.unpack(L, p), L_or, U, oracle.max_rate(go, U), 3, 3,
-                      momentum_floor(go, U))
-        assert (err <= TOL).all(), (p, e, err)
+        for LL in (L, Lw):
+            err = rhs_err(P.unpack(LL, p), L_or, U, oracle.max_rate(go, U), 3, 3,
+                          momentum_floor(go, U))
+            assert (err <= TOL).all(), (p, e, err)

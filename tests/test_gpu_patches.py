@@ -114,6 +114,7 @@ def test_patch_autotune_restores_state(gpu):
     P.bind(Ud)
     best = P.autotune(cfl=0.2, steps=1)
     assert best["block"] in (64, 128) and best["ctas_per_sm"] in (2, 3, 4, 6)
+    assert best["dynamic"] in (0, 1, 2)
     assert best["ms_per_step"] > 0
     assert np.array_equal(Ud.cpu().numpy(), U)
 
@@ -173,3 +174,97 @@ def test_patch_kapila_parity(gpu):
     assert (l1_group(Um.cpu().numpy(), U1, N, D) <= 1e-5).all()
     with pytest.raises(KeyError):
         wenoc.Patches(edges, g, pi, Dm, kmodel="stiffened")
+
+
+# edges for every window plan: groups of tails (3, 8, 31, 33), one tail a
+# warp (15, 24), a full window and no tail (30), a window and a tail (32)
+WIN_EDGES = (3, 8, 15, 24, 30, 31, 32, 33)
+
+
+def test_patch_window_schedule_fp64_parity(gpu):
+    """The window schedule (kind 2: per direction, the grids' window sweep
+    over the pencils of each group of equal patches) against the oracle on
+    every patch: rhs, an SSP-RK3 step at a given dt and at the device's CFL
+    dt, at 1e-12; direct launches, graph replay and two block shapes bit for
+    bit the same."""
+    edges, states, (g, pi, Dm) = inputs.patch_batch(npatch=24, seed=17, edges=WIN_EDGES)
+    edges = [int(e) for e in edges]
+    assert set(edges) == set(WIN_EDGES)
+    P = wenoc.Patches(edges, g, pi, Dm, precision="fp64")
+    U, Us = pooled_cons(P, edges, states, g, pi, Dm)
+    grids = [oracle_grid(e, g, pi, Dm) for e in edges]
+    Ud = to_dev(U)
+    P.bind(Ud)
+    P.set_schedule(128, 3, 2)
+    L = P.rhs(Ud).cpu().numpy()
+    P.sync_status()
+    for p, (go, Up) in enumerate(zip(grids, Us)):
+        err = rhs_err(P.unpack(L, p), oracle.rhs(go, Up), Up, oracle.max_rate(go, Up), N, D,
+                      mom_floor=momentum_floor(go, Up))
+        assert (err <= 1e-12).all(), (p, edges[p], err)
+    rate = max(oracle.max_rate(go, Up) for go, Up in zip(grids, Us))
+    dt = 0.2 / rate
+    outs = []
+    s = torch.cuda.Stream()
+    for sched, graph, kw in [((128, 3, 2), False, {"dt": dt}), ((64, 4, 2), False, {"dt": dt}),
+                             ((128, 2, 2), True, {"dt": dt}), ((128, 3, 2), True, {"cfl": 0.2})]:
+        Uw = to_dev(U)
+        with torch.cuda.stream(s):
+            P.bind(Uw, stream=s)
+            P.set_schedule(*sched)
+            P.rk_step(nsteps=1, use_graph=graph, stream=s, **kw)
+        s.synchronize()
+        P.sync_status(stream=s)
+        outs.append(Uw.cpu().numpy())
+    for k in (1, 2):
+        assert np.array_equal(outs[0], outs[k]), k
+    for U1 in (outs[0], outs[3]):
+        for p, (go, Up) in enumerate(zip(grids, Us)):
+            Uo, _ = oracle.rk3_step(go, Up, dt=dt)
+            err = state_err(P.unpack(U1, p), Uo, N, D, mom_floor=momentum_floor(go, Uo))
+            assert (err <= 1e-12).all(), (p, edges[p], err)
+
+
+def test_patch_window_schedule_mixed(gpu):
+    """Mixed precision on the window schedule: the split sweep (face buffer in
+    the workspace) and the one-pass sweep (workspace without it) give the
+    same bits; five steps stay within the L1 bound of the FP64 patches with
+    masses >= 0 and fractions in [0, 1] (exactly, at cell averages); the
+    persistent schedule's mixed sweep meets the same bound."""
+    edges, states, (g, pi, Dm) = inputs.patch_batch(npatch=16, seed=19, edges=WIN_EDGES)
+    edges = [int(e) for e in edges]
+    P64 = wenoc.Patches(edges, g, pi, Dm, precision="fp64")
+    Pmx = wenoc.Patches(edges, g, pi, Dm, precision="mixed")
+    assert wenoc.lib().wc_patches_face_buffer_bytes(P64.h) == 0
+    assert wenoc.lib().wc_patches_face_buffer_bytes(Pmx.h) > 0
+    U, _ = pooled_cons(P64, edges, states, g, pi, Dm)
+    A = to_dev(U)
+    P64.bind(A)
+    outs = []
+    for faces in (True, False):
+        B = to_dev(U)
+        Pmx.bind(B, faces=faces)
+        Pmx.set_schedule(128, 3, 2)
+        for _ in range(5):
+            Pmx.rk_step(dt=2e-7)
+        torch.cuda.synchronize()
+        Pmx.sync_status()
+        outs.append(B.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    for _ in range(5):
+        P64.rk_step(dt=2e-7)
+    torch.cuda.synchronize()
+    P64.sync_status()
+    a, b = A.cpu().numpy(), outs[0]
+    assert (l1_group(b, a, N, D) <= 1e-5).all()
+    assert b[:N].min() >= 0.0
+    frac = b[N + D + 1:]
+    assert frac.min() >= 0.0 and frac.max() <= 1.0
+    C = to_dev(U)
+    Pmx.bind(C)
+    Pmx.set_schedule(64, 4, 1)
+    for _ in range(5):
+        Pmx.rk_step(dt=2e-7)
+    torch.cuda.synchronize()
+    Pmx.sync_status()
+    assert (l1_group(C.cpu().numpy(), a, N, D) <= 1e-5).all()
