@@ -89,12 +89,17 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bia
     tmem_ld32(taddr + c, h);
 #pragma unroll
     for (int k = 0; k < 32; k += 8) {
-      uint4 q;
-      q.x = bf16x2_relu(h[k] + bias[c + k], h[k + 1] + bias[c + k + 1]);
-      q.y = bf16x2_relu(h[k + 2] + bias[c + k + 2], h[k + 3] + bias[c + k + 3]);
-      q.z = bf16x2_relu(h[k + 4] + bias[c + k + 4], h[k + 5] + bias[c + k + 5]);
-      q.w = bf16x2_relu(h[k + 6] + bias[c + k + 6], h[k + 7] + bias[c + k + 7]);
-      *reinterpret_cast<uint4*>(out + cm_offset(row, c + k, MLP_H)) = q;
+      // bias added two columns at a time (packed FP32, each sum rounded as
+      // a scalar add would be)
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const float2 s = __fadd2_rn(make_float2(h[k + 2 * q], h[k + 2 * q + 1]),
+                                    *reinterpret_cast<const float2*>(bias + c + k + 2 * q));
+        w[q] = bf16x2_relu(s.x, s.y);
+      }
+      *reinterpret_cast<uint4*>(out + cm_offset(row, c + k, MLP_H)) =
+          make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }
@@ -231,8 +236,18 @@ template <int N, int D>
 __device__ __forceinline__ void gather_stencil(const MlpGeom& g, long cell, int side,
                                                double (*ms)[5], double (*as)[5]) {
   using I = Idx<N, D>;
-  const int i = (int)(cell % g.nx), j = (int)((cell / g.nx) % g.ny),
-            k = (int)(cell / ((long)g.nx * g.ny));
+  int i, j, k;
+  if (g.ncell <= 0xFFFFFFFFL) {  // 32-bit index arithmetic
+    const unsigned c = (unsigned)cell, nx = (unsigned)g.nx, ny = (unsigned)g.ny;
+    const unsigned r = c / nx;
+    i = (int)(c - r * nx);
+    j = (int)(r % ny);
+    k = (int)(r / ny);
+  } else {
+    i = (int)(cell % g.nx);
+    j = (int)((cell / g.nx) % g.ny);
+    k = (int)(cell / ((long)g.nx * g.ny));
+  }
   const int pos = g.dir == 0 ? i : (g.dir == 1 ? j : k);
   const long base = cell - (long)pos * g.stride;
 #pragma unroll
