@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--tau", type=float, default=1e-4)
     ap.add_argument("--n3d", type=int, default=256, help="edge of the 3-D workload")
     ap.add_argument("--steps3d", type=int, default=7, help="timed steps of the 3-D workload")
+    ap.add_argument("--l1-steps2", type=int, default=200,
+                    help="steps of the shock-bubble's mixed-vs-FP64 L1 run (its 200 RK3 steps)")
+    ap.add_argument("--l1-steps3d", type=int, default=50,
+                    help="steps of the 3-D workload's mixed-vs-FP64 L1 run (its 50 RK3 steps)")
     ap.add_argument("--npatch", type=int, default=4096)
     ap.add_argument("--steps4", type=int, default=6, help="timed steps of the patches")
     ap.add_argument("--n-adv", type=int, default=2048,
@@ -572,7 +576,7 @@ def time_inference(case, S, make_grid, barrier, dev):
     fl_row = roofline.MLP_FLOPS_PER_FACE_SIDE
     tf = fl_row * rows / (ms * 1e-3) / 1e12
     peak = measured_bf16_peak()
-    return {"kernel": "k_mlp_fwd<SrcState<3,2>> (feature gather + 4 tcgen05 layers)",
+    return {"kernel": "k_mlp_infer2<3,2> (stencil gather, features of both face sides, 4 tcgen05 layers)",
             "rows": rows, "ms_per_launch": round(ms, 4), "achieved_tflops": round(tf, 2),
             "flops_per_row": fl_row, "frac_of_bf16_measured": round(tf / peak, 4)}
 
@@ -619,7 +623,8 @@ def run_configs(args, make_grid, timed_steps, barrier, dev, learned):
         res[prec] = timed_steps(g, args.steps, 3, c2)
         del g, U
     d2 = line(c2, res, args.steps)
-    d2["mixed"]["l1_rel_vs_fp64_max_var"] = l1_pair(c2, args.steps)
+    d2["mixed"]["l1_rel_vs_fp64_max_var"] = l1_pair(c2, args.l1_steps2)
+    d2["mixed"]["l1_after_steps"] = args.l1_steps2
     if learned:
         d2["learned"]["speedup_vs_fp64"] = round(res["fp64"][0] / res["learned"][0], 3)
     out["shock_bubble_2d"] = dict(workload="shock_bubble_2d 1024x512 N=2 HLL CFL 0.2 "
@@ -634,7 +639,8 @@ def run_configs(args, make_grid, timed_steps, barrier, dev, learned):
         del g, U
         torch.cuda.empty_cache()
     d3 = line(c3, res, args.steps3d)
-    d3["mixed"]["l1_rel_vs_fp64_max_var"] = l1_pair(c3, args.steps3d)
+    d3["mixed"]["l1_rel_vs_fp64_max_var"] = l1_pair(c3, args.l1_steps3d)
+    d3["mixed"]["l1_after_steps"] = args.l1_steps3d
     out["spheres_shock_3d"] = dict(workload=f"spheres_shock_3d {args.n3d}^3 N=3 HLL CFL 0.2 "
                                    "outflow (16 spheres, shock ratio 1e3, seeded)", **d3)
     del c3
