@@ -362,25 +362,6 @@ __device__ __forceinline__ void block_sum_small(const double (&v)[N], double* ou
   __syncthreads();
 }
 
-// Sums of count <= 4 PF_THREADS partial rows (16 doubles, M <= 16 used) by
-// the whole block in a fixed order: rows t, t + 256, ... to thread t, then
-// block_sum_small.
-template <int M, int BT = PF_THREADS>
-__device__ __forceinline__ void sum_rows_small(const double* part, int count, double* out) {
-  double v[M];
-#pragma unroll
-  for (int j = 0; j < M; j++) v[j] = 0.0;
-#pragma unroll
-  for (int rrow = 0; rrow < 4; rrow++) {
-    const int row = (int)threadIdx.x + rrow * BT;
-    if (row < count)
-#pragma unroll
-      for (int j = 0; j < M; j++) v[j] += __ldcg(part + (long)row * 16 + j);
-  }
-  // warps whose threads hold no row hold zeros
-  block_sum_small<M, BT>(v, out, (int)(threadIdx.x & ~31u) >= count);
-}
-
 // Grid barrier of the cooperative launch (every block resident): an arrival
 // count and a generation word.  The last block to arrive resets the count
 // and advances the generation; the others poll the generation, at most
@@ -427,6 +408,95 @@ __device__ __forceinline__ void own_range(int m, int b, int G, int& k0, int& k1)
   k1 = min(m, k0 + cp);
 }
 
+// The grid sums and scalars of a conjugate-gradient iteration (Chronopoulos
+// and Gear's form) for every phase, from the G block partials (rows of 16
+// doubles: r.u at p, w.u at N + p, and at the start the reference b.b/D at
+// 2N + p).  Warp p alone takes phase p: lane l sums rows l, l + 32, ... in
+// order, a fixed shuffle tree sums the lanes, and lane 0 computes the
+// scalars and publishes them in shared memory, from which every thread takes
+// its copy.  An FP64 warp instruction holds its sub-partition's FP64 unit as
+// long with one active lane as with 32, so the sums and divisions are paid
+// by one warp a phase, not by every warp of the block (an iteration on the
+// shock-bubble's band, measured: 14.1 us with every warp summing all rows
+// and dividing, 11.1 us with the divisions in one warp a phase, 9.8 us with
+// the sums there too).  The
+// reciprocals of gamma and alpha are carried from the previous iteration,
+// two divisions a phase:
+//   beta = gamma' (1/gamma),  s = delta - beta gamma' (1/alpha),
+//   alpha' = gamma' / s,  1/alpha' = s (1/gamma'),  1/gamma' for the next.
+template <int N>
+struct CgScal {
+  double gam[N], igam[N], alpha[N], ialpha[N], beta[N], ref[N];
+  int conv[N];
+};
+template <int N>
+__device__ __forceinline__ void cg_scalars(const double* part, int G, double tol2, bool start,
+                                           double* alpha, double* beta, double* gam,
+                                           double* ref, bool* conv) {
+  __shared__ CgScal<N> cs;
+  const int t = (int)threadIdx.x, p = t >> 5, lane = t & 31;
+  if (p < N) {
+    double g = 0.0, d = 0.0, rf = 0.0;
+    for (int r0 = 0; r0 < G; r0 += 8 * 32) {
+      double vg[8], vd[8], vr[8];  // loads of up to 8 rows issued together
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const int r = r0 + lane + 32 * k;
+        const double* row = part + (long)r * 16;
+        vg[k] = r < G ? __ldcg(row + p) : 0.0;
+        vd[k] = r < G ? __ldcg(row + N + p) : 0.0;
+        vr[k] = start && r < G ? __ldcg(row + 2 * N + p) : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        if (r0 + lane + 32 * k >= G) break;
+        g += vg[k];
+        d += vd[k];
+        rf += vr[k];
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      g += __shfl_down_sync(0xffffffffu, g, o);
+      d += __shfl_down_sync(0xffffffffu, d, o);
+      if (start) rf += __shfl_down_sync(0xffffffffu, rf, o);
+    }
+    if (lane == 0) {
+      if (start) {
+        const double ig = g > 0.0 ? 1.0 / g : 0.0;
+        const double a = d > 0.0 ? g / d : 0.0;
+        cs.gam[p] = g;
+        cs.igam[p] = ig;
+        cs.ref[p] = rf;
+        cs.alpha[p] = a;
+        cs.ialpha[p] = d * ig;
+        cs.beta[p] = 0.0;
+        cs.conv[p] = !(g > tol2 * rf) || !(a > 0.0);
+      } else if (!cs.conv[p]) {
+        const double bt = g * cs.igam[p];
+        const double den = d - bt * g * cs.ialpha[p];
+        const double ign = g > 0.0 ? 1.0 / g : 0.0;
+        const double a = den > 0.0 ? g / den : 0.0;
+        cs.beta[p] = bt;
+        cs.gam[p] = g;
+        cs.igam[p] = ign;
+        cs.alpha[p] = a;
+        cs.ialpha[p] = den * ign;
+        cs.conv[p] = !(g > tol2 * cs.ref[p]) || !(a > 0.0);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < N; q++) {
+    alpha[q] = cs.alpha[q];
+    beta[q] = cs.beta[q];
+    gam[q] = cs.gam[q];
+    ref[q] = cs.ref[q];
+    conv[q] = cs.conv[q] != 0;
+  }
+}
+
 // The iterations of k_qmap_cg when every phase has at most R unknowns per
 // thread (R G 256 unknowns: interface bands): thread t of block b takes
 // unknowns b 256 + t + j G 256, j < R, of each phase and keeps their state
@@ -450,11 +520,12 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
   const int G = (int)gridDim.x, t = (int)threadIdx.x;
   const int k = (int)blockIdx.x * PF_THREADS + t;
   const int span = G * PF_THREADS;
-  __shared__ double s_sum[3 * N];
   int maxm = 0;
 #pragma unroll
   for (int p = 0; p < N; p++) maxm = max(maxm, scnt[p]);
-  // a warp whose unknowns are all past the lists contributes zeros
+  // a warp whose unknowns are all past the lists contributes zeros (the
+  // blocks take consecutive runs of 256: spreading the lists evenly over
+  // every block measured no faster, the product being latency-bound)
   const bool idle_warp = (int)blockIdx.x * PF_THREADS + (t & ~31) >= maxm;
   bool has[E];
   int cell[E], ke[E], nbk[E][6];
@@ -541,15 +612,7 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
     ok = grid_sync(bar, err);
   }
   if (ok) {
-    sum_rows_small<3 * N>(w.part + PART_CG1, G, s_sum);
-#pragma unroll
-    for (int p = 0; p < N; p++) {
-      gam[p] = s_sum[p];
-      ref[p] = s_sum[2 * N + p];
-      alpha[p] = s_sum[N + p] > 0.0 ? gam[p] / s_sum[N + p] : 0.0;
-      beta[p] = 0.0;
-      conv[p] = !(gam[p] > tol2 * ref[p]) || !(alpha[p] > 0.0);
-    }
+    cg_scalars<N>(w.part + PART_CG1, G, tol2, true, alpha, beta, gam, ref, conv);
     // the start may meet the test already; the others iterate
     while (it < maxit) {
       bool all = true;
@@ -574,18 +637,7 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
       for (int j = 0; j < 2 * N; j++) v2[j] = acc[j];
       block_sum_small<2 * N>(v2, w.part + PART_CG1 + (long)blockIdx.x * 16, idle_warp);
       if (!(ok = grid_sync(bar, err))) break;
-      sum_rows_small<2 * N>(w.part + PART_CG1, G, s_sum);
-#pragma unroll
-      for (int p = 0; p < N; p++) {
-        if (conv[p]) continue;
-        const double gn = s_sum[p], dn = s_sum[N + p];
-        const double bt = gam[p] > 0.0 ? gn / gam[p] : 0.0;
-        const double den = dn - bt * gn / alpha[p];
-        beta[p] = bt;
-        gam[p] = gn;
-        alpha[p] = den > 0.0 ? gn / den : 0.0;
-        conv[p] = !(gn > tol2 * ref[p]) || !(alpha[p] > 0.0);
-      }
+      cg_scalars<N>(w.part + PART_CG1, G, tol2, false, alpha, beta, gam, ref, conv);
       it++;
     }
   }
@@ -624,7 +676,6 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
   const int n = (int)g.ncell;
   const long nn = (long)N * n;
   const int G = (int)gridDim.x, b = (int)blockIdx.x, t = (int)threadIdx.x;
-  __shared__ double s_sum[3 * N];
   double acc[3 * N];
 #pragma unroll
   for (int j = 0; j < 3 * N; j++) acc[j] = 0.0;
@@ -737,15 +788,7 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
     ok = grid_sync(bar, err);
   }
   if (ok) {
-    sum_rows_small<3 * N, BT>(w.part + PART_CG1, G, s_sum);
-#pragma unroll
-    for (int p = 0; p < N; p++) {
-      gam[p] = s_sum[p];
-      ref[p] = s_sum[2 * N + p];
-      alpha[p] = s_sum[N + p] > 0.0 ? gam[p] / s_sum[N + p] : 0.0;
-      beta[p] = 0.0;
-      conv[p] = !(gam[p] > tol2 * ref[p]) || !(alpha[p] > 0.0);
-    }
+    cg_scalars<N>(w.part + PART_CG1, G, tol2, true, alpha, beta, gam, ref, conv);
     while (it < maxit) {
       bool all = true;
 #pragma unroll
@@ -788,18 +831,7 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
       for (int j = 0; j < 2 * N; j++) v2[j] = acc[j];
       block_sum_small<2 * N, BT>(v2, w.part + PART_CG1 + (long)b * 16);
       if (!(ok = grid_sync(bar, err))) break;
-      sum_rows_small<2 * N, BT>(w.part + PART_CG1, G, s_sum);
-#pragma unroll
-      for (int p = 0; p < N; p++) {
-        if (conv[p]) continue;
-        const double gn = s_sum[p], dn = s_sum[N + p];
-        const double bt = gam[p] > 0.0 ? gn / gam[p] : 0.0;
-        const double den = dn - bt * gn / alpha[p];
-        beta[p] = bt;
-        gam[p] = gn;
-        alpha[p] = den > 0.0 ? gn / den : 0.0;
-        conv[p] = !(gn > tol2 * ref[p]) || !(alpha[p] > 0.0);
-      }
+      cg_scalars<N>(w.part + PART_CG1, G, tol2, false, alpha, beta, gam, ref, conv);
       it++;
     }
   }
@@ -969,7 +1001,6 @@ __global__ void __launch_bounds__(PF_THREADS) k_qmap_cg(PfGeom g, PfWork w, doub
   unsigned* bar = reinterpret_cast<unsigned*>(w.flag + 8);
   int* err = w.flag + 10;
   __shared__ int wtot[PF_THREADS / 32], soff[N], scnt[N];
-  __shared__ double s_rz[N], s_ref[N], s_new[N];
 
   // 1. list
   const int cc = (n + G - 1) / G, c0 = min(n, b * cc), c1 = min(n, c0 + cc);
