@@ -87,6 +87,12 @@ def parse():
     ap.add_argument("--profile-pf", action="store_true",
                     help="only full time steps with the Phase-Field mechanism on the "
                          "shock-bubble (--steps of them after --warmup), for profilers")
+    ap.add_argument("--profile-patches", action="store_true",
+                    help="only --steps graph-replayed steps of the batched patches (--npatch "
+                         "of them, --profile-precision, schedule kind --patch-kind), for "
+                         "profilers")
+    ap.add_argument("--patch-kind", type=int, default=2, choices=[0, 1, 2],
+                    help="schedule kind of --profile-patches (0/1 persistent, 2 windows)")
     ap.add_argument("--profile-mlp", action="store_true",
                     help="only the surrogate kernels on the circles state (inference of one "
                          "direction, one training step of train_batch rows), for profilers")
@@ -844,6 +850,37 @@ def time_phase_field(make_grid, cb, K=20):
             "ms_qmap": round(parts[2], 4), "ms_pf_step": round(parts[3], 4)}
 
 
+def run_profile_patches(args):
+    """The batched patches alone: --warmup then --steps steps (CFL 0.2, direct
+    launches: the kernels of the graph-replayed benchmark step) in one
+    precision and schedule kind (128-thread blocks, 2 per SM persistent or 4
+    per SM in windows), events around the timed steps."""
+    import torch
+    from paper_2608_00746_b300 import inputs, wenoc
+    dev = torch.device("cuda", 0)
+    edges, states, (gm, pi, Dm) = inputs.patch_batch(npatch=args.npatch, seed=args.seed)
+    P = wenoc.Patches(edges, gm, pi, Dm, precision=args.profile_precision)
+    V = torch.from_numpy(P.pack(states)).to(dev)
+    U = P.prim_to_cons(V)
+    del V
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        P.bind(U, stream=s)
+        P.set_schedule(128, 4 if args.patch_kind == 2 else 2, args.patch_kind)
+        P.rk_step(cfl=0.2, nsteps=max(args.warmup, 1), stream=s)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        P.rk_step(cfl=0.2, nsteps=args.steps, stream=s)
+        e1.record(s)
+    s.synchronize()
+    P.sync_status(stream=s)
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    print(json.dumps({"profile_patches": True, "precision": args.profile_precision,
+                      "kind": args.patch_kind, "npatch": args.npatch, "cells": int(P.ncell),
+                      "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup}), flush=True)
+    return 0
+
+
 def run_profile_mlp(args):
     """Surrogate kernels alone (untrained network: the timing does not depend
     on the weights): 3 + 5 inference launches of direction 0 of the circles
@@ -892,6 +929,8 @@ def main():
         return run_reference(args)
     if args.profile_mlp:
         return run_profile_mlp(args)
+    if args.profile_patches:
+        return run_profile_patches(args)
     return run_ours(args)
 
 
