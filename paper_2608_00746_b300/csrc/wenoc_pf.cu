@@ -433,6 +433,7 @@ template <int N>
 __device__ __forceinline__ void cg_scalars(const double* part, int G, double tol2, bool start,
                                            double* alpha, double* beta, double* gam,
                                            double* ref, bool* conv) {
+  static_assert(32 * N <= PF_THREADS, "one warp a phase");
   __shared__ CgScal<N> cs;
   const int t = (int)threadIdx.x, p = t >> 5, lane = t & 31;
   if (p < N) {
@@ -673,6 +674,7 @@ template <int N, int BT, int MB>
 __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double tol2, int warm,
                                        int maxit, const int* scnt, int c0, int c1, unsigned* bar,
                                        int* err) {
+  static_assert(32 * N <= BT, "cg_scalars takes one warp a phase");
   const int n = (int)g.ncell;
   const long nn = (long)N * n;
   const int G = (int)gridDim.x, b = (int)blockIdx.x, t = (int)threadIdx.x;

@@ -108,3 +108,84 @@ def test_calls_before_binding_fail_cleanly():
     buf = ctypes.create_string_buffer(64)
     L.wc_last_error(h, buf, 64)
     L.wc_destroy(h)
+
+
+@pytest.mark.parametrize("n", [(0, 8, 1), (-3, 8, 1), (16, 0, 1)])
+def test_init_grid_rejects_empty_grids(n):
+    assert init(desc(n=n))[0] == 1
+
+
+def pdesc(**kw):
+    d = wenoc.PatchesDesc()
+    d.nphase = kw.get("nphase", 3)
+    for p in range(min(d.nphase, wenoc.MAX_PHASE)):
+        d.gamma[p] = 1.4
+        d.pinf[p] = 0.0
+    d.flux = kw.get("flux", 0)
+    d.precision = kw.get("precision", 1)
+    d.energy_limiter = 1
+    d.kmodel = kw.get("kmodel", 0)
+    return d
+
+
+def pinit(d, edges):
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int * max(len(edges), 1))(*edges)
+    d.npatch = len(edges)
+    st = wenoc.lib().wc_patches_init(ctypes.byref(d), arr, ctypes.byref(h))
+    return st, h
+
+
+def test_patches_init_tables_and_workspace():
+    """Host-side patch tables: pooled offsets in patch order, the window
+    schedule's face buffer sized for the largest group of equal patches
+    (mixed precision only; (2 NV + 1) e^2 (e + 2) doubles a patch)."""
+    L = wenoc.lib()
+    edges = [8, 32, 8, 12, 32, 3]
+    st, h = pinit(pdesc(), edges)
+    assert st == 0
+    try:
+        assert L.wc_patches_ncell(h) == sum(e ** 3 for e in edges)
+        offs = [L.wc_patches_offset(h, p) for p in range(len(edges))]
+        assert offs == [sum(e ** 3 for e in edges[:p]) for p in range(len(edges))]
+        assert L.wc_patches_offset(h, len(edges)) == -1
+        nv = 2 * 3 + 4
+        most = max(edges.count(e) * (2 * nv + 1) * e * e * (e + 2) for e in set(edges))
+        fb = L.wc_patches_face_buffer_bytes(h)
+        assert most * 8 <= fb < most * 8 + 256
+        state = (nv * sum(e ** 3 for e in edges) * 8 + 255) // 256 * 256
+        assert L.wc_patches_workspace_bytes(h) >= 4 * state + fb
+    finally:
+        L.wc_patches_destroy(h)
+    st, h = pinit(pdesc(precision=0), edges)
+    assert st == 0
+    assert L.wc_patches_face_buffer_bytes(h) == 0
+    L.wc_patches_destroy(h)
+
+
+@pytest.mark.parametrize("kw,edges,status", [
+    ({}, [], 1),                      # no patch
+    ({}, [8, 2], 1),                  # an edge below the stencil's 3 cells
+    ({}, [8, 1025], 1),               # above 1024
+    ({"nphase": 0}, [8], 5), ({"nphase": 6}, [8], 5),
+    ({"flux": 3}, [8], 1), ({"precision": 2}, [8], 5),  # learned: grids only
+    ({"kmodel": 2}, [8], 1), ({"kmodel": -1}, [8], 1),
+])
+def test_patches_init_rejects(kw, edges, status):
+    st, h = pinit(pdesc(**kw), edges)
+    if st == 0:
+        wenoc.lib().wc_patches_destroy(h)
+    assert st == status
+
+
+def test_patches_schedule_kinds():
+    L = wenoc.lib()
+    st, h = pinit(pdesc(), [8, 16])
+    assert st == 0
+    try:
+        for b, c, k in [(128, 4, 2), (64, 3, 1), (32, 1, 0)]:
+            assert L.wc_patches_set_schedule(h, b, c, k) == 0
+        for b, c, k in [(128, 4, 3), (128, 4, -1), (100, 2, 1), (128, 0, 1), (128, 17, 2)]:
+            assert L.wc_patches_set_schedule(h, b, c, k) == 1
+    finally:
+        L.wc_patches_destroy(h)
