@@ -293,14 +293,15 @@ __device__ __forceinline__ double k_apply(const PfGeom& g, const int (&nb)[3][2]
 // some region, in cell order per phase) in one cooperative launch of at
 // most PF_CG_BLOCKS blocks that meet at grid barriers.  Partials: the Eq. 28
 // totals [PF_BLOCKS][32], the list counts [PF_CG_BLOCKS][8] and the
-// iteration's sums [PF_CG_BLOCKS][16].  Every block sums the partials
-// itself, in the same fixed order, so all blocks hold the same scalars and
-// take the same loop decisions.
+// iteration's sums [PF_CG_BLOCKS][PART_ROW] (up to four per phase).  Every
+// block sums the partials itself, in the same fixed order, so all blocks
+// hold the same scalars and take the same loop decisions.
 constexpr int PF_CG_BLOCKS = 148 * 8;
+constexpr int PART_ROW = 32;
 constexpr long PART_CAC = 0;
 constexpr long PART_LIST = (long)PF_BLOCKS * 32;
 constexpr long PART_CG1 = PART_LIST + (long)PF_CG_BLOCKS * 8;
-constexpr long PART_TOTAL = PART_CG1 + (long)PF_CG_BLOCKS * 16;
+constexpr long PART_TOTAL = PART_CG1 + (long)PF_CG_BLOCKS * PART_ROW;
 // results: scal[16 + p] b.b/D, [24 + p] r.r/D; flags: [1 + p] converged,
 // [8] [9] [10] the grid barrier (arrivals, generation, error), [11] the
 // iterations done
@@ -409,50 +410,56 @@ __device__ __forceinline__ void own_range(int m, int b, int G, int& k0, int& k1)
 }
 
 // The grid sums and scalars of a conjugate-gradient iteration (Chronopoulos
-// and Gear's form) for every phase, from the G block partials (rows of 16
-// doubles: r.u at p, w.u at N + p, and at the start the reference b.b/D at
-// 2N + p).  Warp p alone takes phase p: lane l sums rows l, l + 32, ... in
-// order, a fixed shuffle tree sums the lanes, and lane 0 computes the
+// and Gear's form) for every phase, from the G block partials (rows of
+// PART_ROW doubles: gamma = r.u at p, delta = w.u at N + p, with RHO the
+// residual measure rho = r.D^-1 r at 2N + p -- else rho = gamma, the
+// Jacobi-preconditioned case -- and at the start the reference b.D^-1 b
+// after them).  Warp p alone takes phase p: lane l sums rows l, l + 32, ...
+// in order, a fixed shuffle tree sums the lanes, and lane 0 computes the
 // scalars and publishes them in shared memory, from which every thread takes
 // its copy.  An FP64 warp instruction holds its sub-partition's FP64 unit as
 // long with one active lane as with 32, so the sums and divisions are paid
 // by one warp a phase, not by every warp of the block (an iteration on the
 // shock-bubble's band, measured: 14.1 us with every warp summing all rows
 // and dividing, 11.1 us with the divisions in one warp a phase, 9.8 us with
-// the sums there too).  The
-// reciprocals of gamma and alpha are carried from the previous iteration,
-// two divisions a phase:
+// the sums there too).  The reciprocals of gamma and alpha are carried from
+// the previous iteration, two divisions a phase:
 //   beta = gamma' (1/gamma),  s = delta - beta gamma' (1/alpha),
-//   alpha' = gamma' / s,  1/alpha' = s (1/gamma'),  1/gamma' for the next.
+//   alpha' = gamma' / s,  1/alpha' = s (1/gamma'),  1/gamma' for the next;
+// a phase has converged when rho <= tol2 b.D^-1 b (or alpha is not positive).
 template <int N>
 struct CgScal {
-  double gam[N], igam[N], alpha[N], ialpha[N], beta[N], ref[N];
+  double gam[N], igam[N], alpha[N], ialpha[N], beta[N], ref[N], rho[N];
   int conv[N];
 };
-template <int N>
+template <int N, bool RHO>
 __device__ __forceinline__ void cg_scalars(const double* part, int G, double tol2, bool start,
-                                           double* alpha, double* beta, double* gam,
+                                           double* alpha, double* beta, double* rho,
                                            double* ref, bool* conv) {
   static_assert(32 * N <= PF_THREADS, "one warp a phase");
+  static_assert((RHO ? 4 : 3) * N <= PART_ROW, "partial row");
+  constexpr int KREF = RHO ? 3 * N : 2 * N;  // reference b.D^-1 b at the start
   __shared__ CgScal<N> cs;
   const int t = (int)threadIdx.x, p = t >> 5, lane = t & 31;
   if (p < N) {
-    double g = 0.0, d = 0.0, rf = 0.0;
+    double g = 0.0, d = 0.0, rh = 0.0, rf = 0.0;
     for (int r0 = 0; r0 < G; r0 += 8 * 32) {
-      double vg[8], vd[8], vr[8];  // loads of up to 8 rows issued together
+      double vg[8], vd[8], vh[8], vr[8];  // loads of up to 8 rows issued together
 #pragma unroll
       for (int k = 0; k < 8; k++) {
         const int r = r0 + lane + 32 * k;
-        const double* row = part + (long)r * 16;
+        const double* row = part + (long)r * PART_ROW;
         vg[k] = r < G ? __ldcg(row + p) : 0.0;
         vd[k] = r < G ? __ldcg(row + N + p) : 0.0;
-        vr[k] = start && r < G ? __ldcg(row + 2 * N + p) : 0.0;
+        vh[k] = RHO && r < G ? __ldcg(row + 2 * N + p) : 0.0;
+        vr[k] = start && r < G ? __ldcg(row + KREF + p) : 0.0;
       }
 #pragma unroll
       for (int k = 0; k < 8; k++) {
         if (r0 + lane + 32 * k >= G) break;
         g += vg[k];
         d += vd[k];
+        if (RHO) rh += vh[k];
         rf += vr[k];
       }
     }
@@ -460,8 +467,10 @@ __device__ __forceinline__ void cg_scalars(const double* part, int G, double tol
     for (int o = 16; o > 0; o >>= 1) {
       g += __shfl_down_sync(0xffffffffu, g, o);
       d += __shfl_down_sync(0xffffffffu, d, o);
+      if (RHO) rh += __shfl_down_sync(0xffffffffu, rh, o);
       if (start) rf += __shfl_down_sync(0xffffffffu, rf, o);
     }
+    if (!RHO) rh = g;
     if (lane == 0) {
       if (start) {
         const double ig = g > 0.0 ? 1.0 / g : 0.0;
@@ -469,10 +478,11 @@ __device__ __forceinline__ void cg_scalars(const double* part, int G, double tol
         cs.gam[p] = g;
         cs.igam[p] = ig;
         cs.ref[p] = rf;
+        cs.rho[p] = rh;
         cs.alpha[p] = a;
         cs.ialpha[p] = d * ig;
         cs.beta[p] = 0.0;
-        cs.conv[p] = !(g > tol2 * rf) || !(a > 0.0);
+        cs.conv[p] = !(rh > tol2 * rf) || !(a > 0.0);
       } else if (!cs.conv[p]) {
         const double bt = g * cs.igam[p];
         const double den = d - bt * g * cs.ialpha[p];
@@ -481,9 +491,10 @@ __device__ __forceinline__ void cg_scalars(const double* part, int G, double tol
         cs.beta[p] = bt;
         cs.gam[p] = g;
         cs.igam[p] = ign;
+        cs.rho[p] = rh;
         cs.alpha[p] = a;
         cs.ialpha[p] = den * ign;
-        cs.conv[p] = !(g > tol2 * cs.ref[p]) || !(a > 0.0);
+        cs.conv[p] = !(rh > tol2 * cs.ref[p]) || !(a > 0.0);
       }
     }
   }
@@ -492,30 +503,73 @@ __device__ __forceinline__ void cg_scalars(const double* part, int G, double tol
   for (int q = 0; q < N; q++) {
     alpha[q] = cs.alpha[q];
     beta[q] = cs.beta[q];
-    gam[q] = cs.gam[q];
+    rho[q] = cs.rho[q];
     ref[q] = cs.ref[q];
     conv[q] = cs.conv[q] != 0;
   }
 }
 
+// Chebyshev preconditioner of the register-resident iteration: z = p(A) r
+// with A = D^-1 K and p the polynomial of the Chebyshev iteration of degree
+// CHEB_M - 1 for A z = D^-1 r on [2 / CHEB_ALPHA, 2] (A's eigenvalues lie in
+// [0, 2]: K = D - W with W >= 0 and D its row sums).  1 - lambda p(lambda)
+// is T_m((theta - lambda)/delta) / T_m(theta/delta), so lambda p(lambda) > 0
+// on (0, 2] and M^-1 = p(A) D^-1 is symmetric positive definite on K's range:
+// a valid preconditioner for conjugate gradients.  It squeezes the spectrum
+// on [2/alpha, 2] and leaves the smallest modes (the slow ones along a thin
+// band) for the outer iteration: on the 1024 x 512 shock-bubble's band
+// (oracle operator, CPU) 294 Jacobi iterations became 79 with CHEB_M = 4,
+// CHEB_ALPHA = 30.  Recurrence (theta, delta the interval's centre and
+// half-width, sigma = theta/delta, rho_0 = 1/sigma):
+//   d_0 = D^-1 r / theta,  z = d_0,  s = D^-1 r - A d_0,
+//   rho_j = 1/(2 sigma - rho_{j-1}),  d_j = rho_j rho_{j-1} d_{j-1}
+//   + (2 rho_j / delta) s,  z += d_j,  s -= A d_j   (j = 1 .. CHEB_M - 1);
+// the K d_j it forms give w = K z = sum_j K d_j for free.
+constexpr int CHEB_M = 4;
+constexpr double CHEB_ALPHA = 30.0;
+struct ChebCoef {
+  double c0, a[CHEB_M], b[CHEB_M];
+};
+constexpr ChebCoef cheb_coef() {
+  const double lo = 2.0 / CHEB_ALPHA, hi = 2.0;
+  const double th = 0.5 * (hi + lo), de = 0.5 * (hi - lo), sg = th / de;
+  ChebCoef c{};
+  c.c0 = 1.0 / th;
+  double r0 = 1.0 / sg;
+  for (int j = 1; j < CHEB_M; j++) {
+    const double r1 = 1.0 / (2.0 * sg - r0);
+    c.a[j] = r1 * r0;
+    c.b[j] = 2.0 * r1 / de;
+    r0 = r1;
+  }
+  return c;
+}
+
 // The iterations of k_qmap_cg when every phase has at most R unknowns per
 // thread (R G 256 unknowns: interface bands): thread t of block b takes
 // unknowns b 256 + t + j G 256, j < R, of each phase and keeps their state
-// in registers (cell,
-// D, 1/D, the neighbours' list positions and face weights, x, r, u, w, p,
-// s).  The iteration is Chronopoulos and Gear's form of preconditioned
-// conjugate gradients (the same iterates as the textbook form in exact
-// arithmetic), whose two inner products r . u and w . u (u = r/D, w = K u)
-// are summed together: two grid barriers an iteration, one before the
-// product K u reads the neighbours' u and one before the sums.
-//   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = r/D,
+// in registers (cell, D, 1/D, the neighbours' list positions and face
+// weights, x, r, u, w, p, s and the preconditioner's d and s).  The
+// iteration is Chronopoulos and Gear's form of preconditioned conjugate
+// gradients (the same iterates as the textbook form in exact arithmetic),
+// whose two inner products r . u and w . u (u = M^-1 r, w = K u) are summed
+// together with the residual measure r . D^-1 r:
+//   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = M^-1 r,
 //   w = K u, gamma' = r . u, delta = w . u, beta = gamma'/gamma,
-//   alpha = gamma' / (delta - beta gamma' / alpha).
+//   alpha = gamma' / (delta - beta gamma' / alpha),
+// with M^-1 the Chebyshev polynomial preconditioner above: CHEB_M products
+// K d_j an iteration, each after a grid barrier that makes the neighbours'
+// d_j visible (alternately in w.p and w.q: a buffer is rewritten only after
+// the next barrier, when every block has read it), then one barrier before
+// the sums.  Against Jacobi (u = D^-1 r: one product and two barriers an
+// iteration) it trades the sums, scalars and barrier of about three
+// iterations for three more products.
 template <int N, int R>
 __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double tol2, int warm,
                                        int maxit, const int* scnt, int c0, int c1, unsigned* bar,
                                        int* err) {
   constexpr int E = N * R;  // slot e: phase e / R, unknown k + (e % R) G 256
+  constexpr ChebCoef CC = cheb_coef();
   const int n = (int)g.ncell;
   const long nn = (long)N * n;
   const int G = (int)gridDim.x, t = (int)threadIdx.x;
@@ -530,18 +584,18 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
   const bool idle_warp = (int)blockIdx.x * PF_THREADS + (t & ~31) >= maxm;
   bool has[E];
   int cell[E], ke[E], nbk[E][6];
-  double Dv[E], Di[E], wg[E][6], x[E], r[E], u[E], wv[E], pv[E], sv[E];
-  double acc[3 * N];
+  double Dv[E], Di[E], wg[E][6], x[E], r[E], u[E], wv[E], pv[E], sv[E], dd[E], sr[E];
+  double acc[4 * N];
 #pragma unroll
-  for (int j = 0; j < 3 * N; j++) acc[j] = 0.0;
-  // start: b, x0, r0 = b - K x0, u0 = r0/D
+  for (int j = 0; j < 4 * N; j++) acc[j] = 0.0;
+  // start: b, x0, r0 = b - K x0
 #pragma unroll
   for (int e = 0; e < E; e++) {
     const int p = e / R;
     const long o = (long)p * n;
     ke[e] = k + (e % R) * span;
     has[e] = ke[e] < scnt[p];
-    x[e] = r[e] = u[e] = wv[e] = pv[e] = sv[e] = 0.0;
+    x[e] = r[e] = u[e] = wv[e] = pv[e] = sv[e] = dd[e] = sr[e] = 0.0;
     Dv[e] = Di[e] = 0.0;
     cell[e] = 0;
 #pragma unroll
@@ -579,41 +633,75 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
       x[e] = w.x[o + i];
       r[e] = bv - k_apply<N>(g, nb, i, o, nn, w.w, w.D, w.x);
     }
-    u[e] = r[e] * Di[e];
-    w.p[o + ke[e]] = u[e];  // the shared copy of u
-    acc[2 * N + p] = fma(bv, bv * Di[e], acc[2 * N + p]);
+    acc[3 * N + p] = fma(bv, bv * Di[e], acc[3 * N + p]);
   }
-  bool ok = grid_sync(bar, err);
-  auto product = [&]() {  // w = K u from the neighbours' shared u; r . u, w . u
+  bool conv[N];
 #pragma unroll
-    for (int p = 0; p < N; p++) acc[p] = acc[N + p] = 0.0;
+  for (int p = 0; p < N; p++) conv[p] = false;
+  // u = M^-1 r and w = K u for the phases not yet converged (CHEB_M grid
+  // barriers), then gamma = r.u, delta = w.u and rho = r.D^-1 r into acc
+  auto precondition = [&]() -> bool {
 #pragma unroll
     for (int e = 0; e < E; e++) {
-      if (!has[e]) continue;
       const int p = e / R;
-      const long o = (long)p * n;
-      double q = Dv[e] * u[e];
-#pragma unroll
-      for (int f = 0; f < 6; f++)
-        if (nbk[e][f] >= 0) q = fma(-wg[e][f], __ldcg(w.p + o + nbk[e][f]), q);
-      wv[e] = q;
-      acc[p] = fma(r[e], u[e], acc[p]);
-      acc[N + p] = fma(q, u[e], acc[N + p]);
+      if (conv[p] || !has[e]) continue;
+      const double rr = r[e] * Di[e];
+      dd[e] = rr * CC.c0;
+      u[e] = dd[e];
+      wv[e] = 0.0;
+      sr[e] = rr;
     }
-  };
-  double gam[N], alpha[N], beta[N], ref[N];
-  bool conv[N];
-  int it = 0;
-  if (ok) {
-    product();
-    double v3[3 * N];
 #pragma unroll
-    for (int j = 0; j < 3 * N; j++) v3[j] = acc[j];
-    block_sum_small<3 * N>(v3, w.part + PART_CG1 + (long)blockIdx.x * 16, idle_warp);
+    for (int j = 0; j < CHEB_M; j++) {
+      double* xb = (j & 1) ? w.q : w.p;
+#pragma unroll
+      for (int e = 0; e < E; e++) {
+        const int p = e / R;
+        if (conv[p] || !has[e]) continue;
+        xb[(long)p * n + ke[e]] = dd[e];
+      }
+      if (!grid_sync(bar, err)) return false;
+#pragma unroll
+      for (int e = 0; e < E; e++) {
+        const int p = e / R;
+        if (conv[p] || !has[e]) continue;
+        const long o = (long)p * n;
+        double q = Dv[e] * dd[e];  // K d_j
+#pragma unroll
+        for (int f = 0; f < 6; f++)
+          if (nbk[e][f] >= 0) q = fma(-wg[e][f], __ldcg(xb + o + nbk[e][f]), q);
+        wv[e] += q;
+        if (j + 1 < CHEB_M) {
+          sr[e] = fma(-Di[e], q, sr[e]);
+          dd[e] = fma(CC.a[j + 1], dd[e], CC.b[j + 1] * sr[e]);
+          u[e] += dd[e];
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < 3 * N; p++) acc[p] = 0.0;
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+      const int p = e / R;
+      if (conv[p] || !has[e]) continue;
+      acc[p] = fma(r[e], u[e], acc[p]);
+      acc[N + p] = fma(wv[e], u[e], acc[N + p]);
+      acc[2 * N + p] = fma(r[e], r[e] * Di[e], acc[2 * N + p]);
+    }
+    return true;
+  };
+  double rho[N], alpha[N], beta[N], ref[N];
+  int it = 0;
+  bool ok = precondition();
+  if (ok) {
+    double v4[4 * N];
+#pragma unroll
+    for (int j = 0; j < 4 * N; j++) v4[j] = acc[j];
+    block_sum_small<4 * N>(v4, w.part + PART_CG1 + (long)blockIdx.x * PART_ROW, idle_warp);
     ok = grid_sync(bar, err);
   }
   if (ok) {
-    cg_scalars<N>(w.part + PART_CG1, G, tol2, true, alpha, beta, gam, ref, conv);
+    cg_scalars<N, true>(w.part + PART_CG1, G, tol2, true, alpha, beta, rho, ref, conv);
     // the start may meet the test already; the others iterate
     while (it < maxit) {
       bool all = true;
@@ -628,17 +716,14 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
         sv[e] = fma(beta[p], sv[e], wv[e]);
         x[e] = fma(alpha[p], pv[e], x[e]);
         r[e] = fma(-alpha[p], sv[e], r[e]);
-        u[e] = r[e] * Di[e];
-        w.p[(long)p * n + ke[e]] = u[e];
       }
-      if (!(ok = grid_sync(bar, err))) break;
-      product();
-      double v2[2 * N];
+      if (!(ok = precondition())) break;
+      double v3[3 * N];
 #pragma unroll
-      for (int j = 0; j < 2 * N; j++) v2[j] = acc[j];
-      block_sum_small<2 * N>(v2, w.part + PART_CG1 + (long)blockIdx.x * 16, idle_warp);
+      for (int j = 0; j < 3 * N; j++) v3[j] = acc[j];
+      block_sum_small<3 * N>(v3, w.part + PART_CG1 + (long)blockIdx.x * PART_ROW, idle_warp);
       if (!(ok = grid_sync(bar, err))) break;
-      cg_scalars<N>(w.part + PART_CG1, G, tol2, false, alpha, beta, gam, ref, conv);
+      cg_scalars<N, true>(w.part + PART_CG1, G, tol2, false, alpha, beta, rho, ref, conv);
       it++;
     }
   }
@@ -658,7 +743,7 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
 #pragma unroll
     for (int p = 0; p < N; p++) {
       w.scal[16 + p] = ref[p];
-      w.scal[24 + p] = gam[p];
+      w.scal[24 + p] = rho[p];
       w.flag[1 + p] = conv[p] ? 1 : 0;
     }
     w.flag[11] = it;
@@ -786,11 +871,11 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
     double v3[3 * N];
 #pragma unroll
     for (int j = 0; j < 3 * N; j++) v3[j] = acc[j];
-    block_sum_small<3 * N, BT>(v3, w.part + PART_CG1 + (long)b * 16);
+    block_sum_small<3 * N, BT>(v3, w.part + PART_CG1 + (long)b * PART_ROW);
     ok = grid_sync(bar, err);
   }
   if (ok) {
-    cg_scalars<N>(w.part + PART_CG1, G, tol2, true, alpha, beta, gam, ref, conv);
+    cg_scalars<N, false>(w.part + PART_CG1, G, tol2, true, alpha, beta, gam, ref, conv);
     while (it < maxit) {
       bool all = true;
 #pragma unroll
@@ -831,9 +916,9 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
       double v2[2 * N];
 #pragma unroll
       for (int j = 0; j < 2 * N; j++) v2[j] = acc[j];
-      block_sum_small<2 * N, BT>(v2, w.part + PART_CG1 + (long)b * 16);
+      block_sum_small<2 * N, BT>(v2, w.part + PART_CG1 + (long)b * PART_ROW);
       if (!(ok = grid_sync(bar, err))) break;
-      cg_scalars<N>(w.part + PART_CG1, G, tol2, false, alpha, beta, gam, ref, conv);
+      cg_scalars<N, false>(w.part + PART_CG1, G, tol2, false, alpha, beta, gam, ref, conv);
       it++;
     }
   }
