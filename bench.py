@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="only the timed steps of one precision on the headline workload "
                          "(a short run for profilers); prints the per-launch sweep time")
+    ap.add_argument("--profile-3d", action="store_true",
+                    help="as --profile on the 3-D spheres-and-shock workload (--n3d or "
+                         "--profile-n cells a side)")
     ap.add_argument("--profile-precision", default="fp64", choices=["fp64", "mixed"],
                     help="precision of the --profile run")
     ap.add_argument("--profile-n", type=int, default=0,
@@ -322,7 +325,7 @@ def run_ours(args):
             tdist.barrier()
         torch.cuda.synchronize()
 
-    learned = not (args.no_learned or args.profile or args.profile_pf)
+    learned = not (args.no_learned or args.profile or args.profile_3d or args.profile_pf)
     S, train_info = train_surrogate(args, dev) if learned else (None, None)
 
     def make_grid(precision, c, counters=None, scheme="c", kmodel="allaire"):
@@ -383,8 +386,12 @@ def run_ours(args):
                           "steps": args.steps, "warmup": args.warmup}), flush=True)
         return 0
 
-    if args.profile:
-        cp = make_case(args, 0, n=args.profile_n or None)
+    if args.profile or args.profile_3d:
+        if args.profile_3d:
+            from paper_2608_00746_b300 import inputs
+            cp = inputs.spheres_shock_3d(n=args.profile_n or args.n3d, seed=args.seed)
+        else:
+            cp = make_case(args, 0, n=args.profile_n or None)
         g, U = make_grid(args.profile_precision, cp)
         ms, sw = timed_steps(g, args.steps, args.warmup, cp)
         print(json.dumps({"profile": True, "precision": args.profile_precision,
