@@ -847,14 +847,52 @@ def time_phase_field(make_grid, cb, K=20):
     parts /= 5
     cells = int(np.prod(g.shape))
     del g, U
+    mixed = time_phase_field_mixed(make_grid, cb, K)
     return {"workload": "shock_bubble_2d 1024x512, full time step (hyperbolic + Eq. 28 + "
                         "Eq. 4 + Phase-Field step), Q-map tolerance 1e-12",
+            "mixed": mixed,
             "steps": K, "value": round(cells * 3 / (ms * 1e-3) / 1e6, 3), "unit": "Mcell/s",
             "ms_per_step": round(ms, 4), "qmap_cg_iterations_last": iters,
             "qmap_label_rounds_last": rounds, "qmap_residual_last": res,
             "qmap_unknowns_last": band, "qmap_unknowns_per_thread_last": per_thread,
             "ms_hyperbolic": round(parts[0], 4), "ms_eq28": round(parts[1], 4),
             "ms_qmap": round(parts[2], 4), "ms_pf_step": round(parts[3], 4)}
+
+
+def time_phase_field_mixed(make_grid, cb, K):
+    """The same full time steps in the mixed precision (the sweeps of both
+    steps in the split mixed form, the Q-map in FP64): K steps at the fixed
+    time step of the FP64 grid's first CFL step, timed after 3 warm-up steps
+    from the same state, and the L1 distance to K FP64 steps at that time
+    step (matched accuracy)."""
+    import torch
+    g64, U64 = make_grid("fp64", cb)
+    g64.set_pf_workspace(U64.device)
+    gm, Um = make_grid("mixed", cb)
+    gm.set_pf_workspace(Um.device)
+    U0 = U64.clone()
+    dt = g64.step(cfl=0.2, nsteps=1, tol=1e-12, want_dt=True)
+    U64.copy_(U0)
+    g64.set_pf_workspace(U64.device)  # a fresh Q-map start
+    gm.step(dt=dt, nsteps=3, tol=1e-12)
+    Um.copy_(U0)
+    gm.set_pf_workspace(Um.device)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    gm.step(dt=dt, nsteps=K, tol=1e-12)
+    e1.record(s)
+    g64.step(dt=dt, nsteps=K, tol=1e-12)
+    torch.cuda.synchronize()
+    gm.sync_status()
+    g64.sync_status()
+    ms = e0.elapsed_time(e1) / K
+    cells = int(np.prod(gm.shape))
+    l1 = group_l1(U64, Um, cb.N, cb.dim)
+    del g64, U64, gm, Um, U0
+    return {"steps": K, "dt": dt, "value": round(cells * 3 / (ms * 1e-3) / 1e6, 3),
+            "unit": "Mcell/s", "ms_per_step": round(ms, 4), "l1_rel_vs_fp64_max_var": l1}
 
 
 def run_profile_patches(args):

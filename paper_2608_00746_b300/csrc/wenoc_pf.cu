@@ -301,7 +301,9 @@ constexpr int PART_ROW = 32;
 constexpr long PART_CAC = 0;
 constexpr long PART_LIST = (long)PF_BLOCKS * 32;
 constexpr long PART_CG1 = PART_LIST + (long)PF_CG_BLOCKS * 8;
-constexpr long PART_TOTAL = PART_CG1 + (long)PF_CG_BLOCKS * PART_ROW;
+// the neighbour flags of the preconditioner's exchanges: one 32-byte word a block
+constexpr long PART_NBR = PART_CG1 + (long)PF_CG_BLOCKS * PART_ROW;
+constexpr long PART_TOTAL = PART_NBR + (long)PF_CG_BLOCKS * 4;
 // results: scal[16 + p] b.b/D, [24 + p] r.r/D; flags: [1 + p] converged,
 // [8] [9] [10] the grid barrier (arrivals, generation, error), [11] the
 // iterations done
@@ -400,6 +402,50 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* err) {
   }
   __syncthreads();
   return ok;
+}
+
+// A barrier among neighbouring blocks only: this block publishes `epoch` in
+// its flag (flags[8 b], one 32-byte word a block; release after the block's
+// writes), then waits until every block of [lo, hi] has published it
+// (acquire; bounded polls, the error word stops every waiter).  Used for the
+// exchanges of the preconditioner, where a block reads the entries of the
+// blocks that own its unknowns' neighbours: the coupling is symmetric, so
+// the blocks it waits for are also the only ones that read its entries, and
+// an entry is rewritten (two exchanges later, in the other buffer's turn)
+// only after they have all published the exchange in between, that is,
+// after they have read it.  Every block publishes every epoch.  Returns
+// false after an error, as grid_sync.
+__device__ __forceinline__ bool nbr_sync(unsigned* flags, int lo, int hi, unsigned epoch,
+                                         int* err) {
+  __shared__ int bad;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bad = 0;
+    asm volatile("st.release.gpu.u32 [%0], %1;" ::"l"(flags + 8 * blockIdx.x), "r"(epoch)
+                 : "memory");
+  }
+  __syncthreads();
+  for (int q = lo + (int)threadIdx.x; q <= hi; q += (int)blockDim.x) {
+    if (q == (int)blockIdx.x) continue;
+    volatile int* verr = err;
+    unsigned spins = 0;
+    for (;;) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(flags + 8 * q) : "memory");
+      if (v >= epoch) break;
+      if ((spins & 255u) == 0u && *verr) {
+        bad = 1;
+        break;
+      }
+      if (++spins > PF_SPIN_LIMIT) {
+        atomicExch(err, 1);
+        bad = 1;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  return bad == 0;
 }
 
 // The unknowns of one phase taken by block b of G: [k0, k1) of m.
@@ -558,10 +604,10 @@ constexpr ChebCoef cheb_coef() {
 //   w = K u, gamma' = r . u, delta = w . u, beta = gamma'/gamma,
 //   alpha = gamma' / (delta - beta gamma' / alpha),
 // with M^-1 the Chebyshev polynomial preconditioner above: CHEB_M products
-// K d_j an iteration, each after a grid barrier that makes the neighbours'
-// d_j visible (alternately in w.p and w.q: a buffer is rewritten only after
-// the next barrier, when every block has read it), then one barrier before
-// the sums.  Against Jacobi (u = D^-1 r: one product and two barriers an
+// K d_j an iteration, each after a barrier among the neighbouring blocks
+// (nbr_sync) that makes the neighbours' d_j visible (alternately in w.p and
+// w.q: a buffer is rewritten only after the next exchange, when every block
+// that reads it has read it), then one grid barrier before the sums.  Against Jacobi (u = D^-1 r: one product and two barriers an
 // iteration) it trades the sums, scalars and barrier of about three
 // iterations for three more products.
 template <int N, int R>
@@ -638,8 +684,37 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
   bool conv[N];
 #pragma unroll
   for (int p = 0; p < N; p++) conv[p] = false;
-  // u = M^-1 r and w = K u for the phases not yet converged (CHEB_M grid
-  // barriers), then gamma = r.u, delta = w.u and rho = r.D^-1 r into acc
+  // the blocks owning this block's neighbours (list position k of a phase
+  // belongs to block (k mod G 256) / 256): the preconditioner's exchanges
+  // wait for them only (nbr_sync)
+  int lo, hi;
+  {
+    __shared__ int s_lo, s_hi;
+    if (t == 0) s_lo = s_hi = (int)blockIdx.x;
+    __syncthreads();
+    int ml = (int)blockIdx.x, mh = (int)blockIdx.x;
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+      if (!has[e]) continue;
+#pragma unroll
+      for (int f = 0; f < 6; f++) {
+        if (nbk[e][f] < 0) continue;
+        const int q = (nbk[e][f] % span) / PF_THREADS;
+        ml = min(ml, q);
+        mh = max(mh, q);
+      }
+    }
+    atomicMin(&s_lo, ml);
+    atomicMax(&s_hi, mh);
+    __syncthreads();
+    lo = s_lo;
+    hi = s_hi;
+  }
+  unsigned* nflag = reinterpret_cast<unsigned*>(w.part + PART_NBR);
+  unsigned epoch = 0u;
+  // u = M^-1 r and w = K u for the phases not yet converged (CHEB_M
+  // neighbour exchanges), then gamma = r.u, delta = w.u and rho = r.D^-1 r
+  // into acc
   auto precondition = [&]() -> bool {
 #pragma unroll
     for (int e = 0; e < E; e++) {
@@ -660,7 +735,7 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
         if (conv[p] || !has[e]) continue;
         xb[(long)p * n + ke[e]] = dd[e];
       }
-      if (!grid_sync(bar, err)) return false;
+      if (!nbr_sync(nflag, lo, hi, ++epoch, err)) return false;
 #pragma unroll
       for (int e = 0; e < E; e++) {
         const int p = e / R;
@@ -1088,6 +1163,9 @@ __global__ void __launch_bounds__(PF_THREADS) k_qmap_cg(PfGeom g, PfWork w, doub
   unsigned* bar = reinterpret_cast<unsigned*>(w.flag + 8);
   int* err = w.flag + 10;
   __shared__ int wtot[PF_THREADS / 32], soff[N], scnt[N];
+  // the preconditioner's neighbour flags start at epoch 0 (published by the
+  // grid barriers before the iteration)
+  if (t == 0) reinterpret_cast<unsigned*>(w.part + PART_NBR)[8 * b] = 0u;
 
   // 1. list
   const int cc = (n + G - 1) / G, c0 = min(n, b * cc), c1 = min(n, c0 + cc);

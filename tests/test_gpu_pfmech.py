@@ -12,7 +12,7 @@ import oracle
 from oracle import pf
 from paper_2608_00746_b300 import inputs, wenoc
 
-from gpu_util import SMALL_CASES, state_err, to_dev
+from gpu_util import SMALL_CASES, l1_group, state_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -363,3 +363,35 @@ def test_qmap_and_full_steps_repeat_bit_for_bit(gpu, name):
         g.sync_status()
         outs.append(Us)
     assert torch.equal(outs[0], outs[1])
+
+
+def test_full_steps_in_mixed_precision(gpu):
+    """Full time steps with the mechanism in the mixed precision (the split
+    sweep's face and flux passes for both the hyperbolic and the Phase-Field
+    step, the Q-map in FP64): after ten steps of the ragged shock-bubble the
+    state is within the L1 bound of the FP64 steps, masses >= 0 and fractions
+    in [0, 1] exactly at cell averages, and their sum one to round-off."""
+    case, go, g64, U = _evolved("shock_bubble_2d_ragged", steps=2)
+    gm = wenoc.Grid(case.shape, case.dx, case.gamma, case.pinf, case.D, flux=case.flux,
+                    bc=case.bc, precision="mixed")
+    A, B = to_dev(U), to_dev(U)
+    g64.bind(A).set_pf_workspace(A.device)
+    gm.bind(B).set_pf_workspace(B.device)
+    N, d = case.N, case.dim
+    for _ in range(10):
+        dt = g64.rk_step(cfl=case.cfl, want_dt=True)
+        g64.cac_rhs(A)
+        Q, _, _ = g64.qmap(A, tol=1e-12)
+        g64.pf_step(Q, dt)
+        gm.step(dt=dt, nsteps=1, tol=1e-12)
+    g64.sync_status()
+    gm.sync_status()
+    a, b = A.cpu().numpy(), B.cpu().numpy()
+    assert (l1_group(b, a, N, d) <= 1e-5).all(), l1_group(b, a, N, d)
+    assert b[:N].min() >= 0.0
+    frac = b[N + d + 1:]
+    assert frac.min() >= 0.0 and frac.max() <= 1.0
+    # the sum's drift: at most 2N units of 2^-53 a step of each of the two
+    # stepping stages (hyperbolic, Phase-Field), from the starting state's
+    sum0 = np.abs(U[N + d + 1:].sum(0) - 1.0).max()
+    assert np.abs(frac.sum(0) - 1.0).max() <= sum0 + 2 * 2 * N * 2.0 ** -53 * 10
