@@ -827,130 +827,207 @@ __device__ __forceinline__ void cg_one(const PfGeom& g, const PfWork& w, double 
 
 // The same iteration with the state in memory, for bands larger than the
 // registers take: block b takes a contiguous range of each phase's list
-// (own_range), its threads the same unknowns every iteration; x, r, the
-// direction p (pd), s, w = K u (q) and the shared copy of u (p) in the
-// workspace's list layout (p ncell + k).
+// (own_range: position k of a phase of m unknowns belongs to block
+// k / ceil(m / G)), its threads the same unknowns every iteration, in the
+// workspace's list layout (p ncell + k): x (xk), r, the directions p (pd)
+// and s (sd), u (p) and w = K u (q), and for the Chebyshev preconditioner
+// its residual (c, whose coefficients the set-up has consumed) and d_j,
+// exchanged among neighbouring blocks (nbr_sync) alternately in sumR and
+// sumD (read only to form the right-hand side, before the grid barrier that
+// follows the start).  Same preconditioner and form as the register path.
 template <int N, int BT, int MB>
 __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double tol2, int warm,
                                        int maxit, const int* scnt, int c0, int c1, unsigned* bar,
                                        int* err) {
   static_assert(32 * N <= BT, "cg_scalars takes one warp a phase");
+  constexpr ChebCoef CC = cheb_coef();
   const int n = (int)g.ncell;
   const long nn = (long)N * n;
   const int G = (int)gridDim.x, b = (int)blockIdx.x, t = (int)threadIdx.x;
-  double acc[3 * N];
+  double* const xbuf[2] = {w.sumR, w.sumD};
+  double acc[4 * N];
 #pragma unroll
-  for (int j = 0; j < 3 * N; j++) acc[j] = 0.0;
-  // start: b, x0, r0 = b - K x0, u0 = r0/D
+  for (int j = 0; j < 4 * N; j++) acc[j] = 0.0;
+  // start: b, x0, r0 = b - K x0; the neighbour blocks' range
+  int ml = b, mh = b;
 #pragma unroll
   for (int p = 0; p < N; p++) {
     const long o = (long)p * n;
     int k0, k1;
     own_range(scnt[p], b, G, k0, k1);
+    const int cp = (scnt[p] + G - 1) / G;
     for (int k = k0 + t; k < k1; k += BT) {
       const int i = __ldcg(w.idx + o + k);
       const int l = __ldcg(w.lab + o + i);
       const double sk = __ldcg(w.sumR + o + l) / __ldcg(w.sumD + o + l);
       const double bv = -(w.R[o + i] - w.D[o + i] * sk);
+      int nb[3][2];
+      pf_stencil(g, i, nb);
       double x0 = 0.0, r0 = bv;
       if (warm) {
-        int nb[3][2];
-        pf_stencil(g, i, nb);
         x0 = w.x[o + i];
         r0 = bv - k_apply<N>(g, nb, i, o, nn, w.w, w.D, w.x);
       }
-      const double di = w.Dinv[o + i];
+#pragma unroll
+      for (int ax = 0; ax < 3; ax++) {
+        if (ax >= g.dim) break;
+#pragma unroll
+        for (int sd = 0; sd < 2; sd++) {
+          const int j = nb[ax][sd];
+          if (j < 0) continue;
+          const int kq = __ldcg(w.pos + o + j);
+          if (kq < 0) continue;
+          ml = min(ml, kq / cp);
+          mh = max(mh, kq / cp);
+        }
+      }
       w.xk[o + k] = x0;
       w.r[o + k] = r0;
-      w.p[o + k] = r0 * di;
-      acc[2 * N + p] = fma(bv, bv * di, acc[2 * N + p]);
+      acc[3 * N + p] = fma(bv, bv * w.Dinv[o + i], acc[3 * N + p]);
     }
   }
-  bool ok = grid_sync(bar, err);
-  // the unknowns of a thread in batches of MB, their loads issued together
-  auto product = [&](const bool* skip) {  // q = K u; r . u, q . u
+  int lo, hi;
+  {
+    __shared__ int s_lo, s_hi;
+    if (t == 0) s_lo = s_hi = b;
+    __syncthreads();
+    atomicMin(&s_lo, ml);
+    atomicMax(&s_hi, mh);
+    __syncthreads();
+    lo = s_lo;
+    hi = s_hi;
+  }
+  unsigned* nflag = reinterpret_cast<unsigned*>(w.part + PART_NBR);
+  unsigned epoch = 0u;
+  bool conv[N];
 #pragma unroll
+  for (int p = 0; p < N; p++) conv[p] = false;
+  // (the right-hand side has read sumR and sumD: they become the exchange
+  // buffers after this barrier)
+  bool ok = grid_sync(bar, err);
+  // u = M^-1 r, w = K u for the phases not yet converged, then r.u, w.u and
+  // r.D^-1 r into acc; the unknowns of a thread in batches of MB, their
+  // loads issued together
+  auto precondition = [&]() -> bool {
+#pragma unroll 1
     for (int p = 0; p < N; p++) {
-      acc[p] = acc[N + p] = 0.0;
-      if (skip[p]) continue;
+      if (conv[p]) continue;
       const long o = (long)p * n;
       int k0, k1;
       own_range(scnt[p], b, G, k0, k1);
-      for (int kb = k0 + t; kb < k1; kb += MB * BT) {
-        int ii[MB], kn[MB][6];
-        double wt[MB][6], un[MB][6], uk[MB], dk[MB], rk[MB];
+      for (int k = k0 + t; k < k1; k += BT) {
+        const double rr = w.r[o + k] * w.Dinv[o + __ldcg(w.idx + o + k)];
+        const double d0 = rr * CC.c0;
+        xbuf[0][o + k] = d0;
+        w.p[o + k] = d0;
+        w.q[o + k] = 0.0;
+        w.c[o + k] = rr;
+      }
+    }
 #pragma unroll
-        for (int j = 0; j < MB; j++) {
-          const int k = kb + j * BT;
-          ii[j] = k < k1 ? __ldcg(w.idx + o + k) : -1;
-        }
+    for (int j = 0; j < CHEB_M; j++) {
+      const double* xb = xbuf[j & 1];
+      double* xn = xbuf[(j + 1) & 1];
+      if (!nbr_sync(nflag, lo, hi, ++epoch, err)) return false;
+#pragma unroll 1
+      for (int p = 0; p < N; p++) {
+        if (conv[p]) continue;
+        const long o = (long)p * n;
+        int k0, k1;
+        own_range(scnt[p], b, G, k0, k1);
+        for (int kb = k0 + t; kb < k1; kb += MB * BT) {
+          int ii[MB], kn[MB][6];
+          double wt[MB][6], un[MB][6];
 #pragma unroll
-        for (int j = 0; j < MB; j++) {
-          const int k = kb + j * BT;
-#pragma unroll
-          for (int f = 0; f < 6; f++) {
-            kn[j][f] = -1;
-            wt[j][f] = 0.0;
+          for (int m = 0; m < MB; m++) {
+            const int k = kb + m * BT;
+            ii[m] = k < k1 ? __ldcg(w.idx + o + k) : -1;
           }
-          uk[j] = dk[j] = rk[j] = 0.0;
-          if (ii[j] < 0) continue;
-          const int i = ii[j];
-          int nb[3][2];
-          pf_stencil(g, i, nb);
 #pragma unroll
-          for (int ax = 0; ax < 3; ax++) {
-            if (ax >= g.dim) break;
-            const double* wa = w.w + ax * nn + o;
-            const int jm = nb[ax][0], jp = nb[ax][1];
-            // a neighbour off the list shares no coupled face (weight 0)
-            if (jp >= 0) {
-              kn[j][2 * ax] = __ldcg(w.pos + o + jp);
-              wt[j][2 * ax] = wa[i];
+          for (int m = 0; m < MB; m++) {
+#pragma unroll
+            for (int f = 0; f < 6; f++) {
+              kn[m][f] = -1;
+              wt[m][f] = 0.0;
             }
-            if (jm >= 0) {
-              kn[j][2 * ax + 1] = __ldcg(w.pos + o + jm);
-              wt[j][2 * ax + 1] = wa[jm];
+            if (ii[m] < 0) continue;
+            const int i = ii[m];
+            int nb[3][2];
+            pf_stencil(g, i, nb);
+#pragma unroll
+            for (int ax = 0; ax < 3; ax++) {
+              if (ax >= g.dim) break;
+              const double* wa = w.w + ax * nn + o;
+              const int jm = nb[ax][0], jp = nb[ax][1];
+              // a neighbour off the list shares no coupled face (weight 0)
+              if (jp >= 0) {
+                kn[m][2 * ax] = __ldcg(w.pos + o + jp);
+                wt[m][2 * ax] = wa[i];
+              }
+              if (jm >= 0) {
+                kn[m][2 * ax + 1] = __ldcg(w.pos + o + jm);
+                wt[m][2 * ax + 1] = wa[jm];
+              }
             }
           }
-          uk[j] = w.p[o + k];
-          dk[j] = w.D[o + i];
-          rk[j] = w.r[o + k];
-        }
 #pragma unroll
-        for (int j = 0; j < MB; j++)
+          for (int m = 0; m < MB; m++)
 #pragma unroll
-          for (int f = 0; f < 6; f++)
-            un[j][f] = kn[j][f] >= 0 ? __ldcg(w.p + o + kn[j][f]) : 0.0;
+            for (int f = 0; f < 6; f++)
+              un[m][f] = kn[m][f] >= 0 ? __ldcg(xb + o + kn[m][f]) : 0.0;
 #pragma unroll
-        for (int j = 0; j < MB; j++) {
-          if (ii[j] < 0) continue;
-          double q = dk[j] * uk[j];
+          for (int m = 0; m < MB; m++) {
+            if (ii[m] < 0) continue;
+            const int k = kb + m * BT, i = ii[m];
+            const double dk = __ldcg(xb + o + k);
+            double q = w.D[o + i] * dk;  // K d_j
 #pragma unroll
-          for (int f = 0; f < 6; f++)
-            if (kn[j][f] >= 0) q = fma(-wt[j][f], un[j][f], q);
-          w.q[o + kb + j * BT] = q;
-          acc[p] = fma(rk[j], uk[j], acc[p]);
-          acc[N + p] = fma(q, uk[j], acc[N + p]);
+            for (int f = 0; f < 6; f++)
+              if (kn[m][f] >= 0) q = fma(-wt[m][f], un[m][f], q);
+            w.q[o + k] += q;
+            if (j + 1 < CHEB_M) {
+              const double sr = fma(-w.Dinv[o + i], q, w.c[o + k]);
+              w.c[o + k] = sr;
+              const double dn = fma(CC.a[j + 1], dk, CC.b[j + 1] * sr);
+              xn[o + k] = dn;
+              w.p[o + k] += dn;
+            }
+          }
         }
       }
     }
+#pragma unroll 1
+    for (int p = 0; p < N; p++) {
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+      if (!conv[p]) {
+        const long o = (long)p * n;
+        int k0, k1;
+        own_range(scnt[p], b, G, k0, k1);
+        for (int k = k0 + t; k < k1; k += BT) {
+          const double rk = w.r[o + k], uk = w.p[o + k];
+          s0 = fma(rk, uk, s0);
+          s1 = fma(w.q[o + k], uk, s1);
+          s2 = fma(rk, rk * w.Dinv[o + __ldcg(w.idx + o + k)], s2);
+        }
+      }
+      acc[p] = s0;
+      acc[N + p] = s1;
+      acc[2 * N + p] = s2;
+    }
+    return true;
   };
-  double gam[N], alpha[N], beta[N], ref[N];
-  bool conv[N];
+  double rho[N], alpha[N], beta[N], ref[N];
   int it = 0;
+  if (ok) ok = precondition();
   if (ok) {
-    bool none[N];
+    double v4[4 * N];
 #pragma unroll
-    for (int p = 0; p < N; p++) none[p] = false;
-    product(none);
-    double v3[3 * N];
-#pragma unroll
-    for (int j = 0; j < 3 * N; j++) v3[j] = acc[j];
-    block_sum_small<3 * N, BT>(v3, w.part + PART_CG1 + (long)b * PART_ROW);
+    for (int j = 0; j < 4 * N; j++) v4[j] = acc[j];
+    block_sum_small<4 * N, BT>(v4, w.part + PART_CG1 + (long)b * PART_ROW);
     ok = grid_sync(bar, err);
   }
   if (ok) {
-    cg_scalars<N, false>(w.part + PART_CG1, G, tol2, true, alpha, beta, gam, ref, conv);
+    cg_scalars<N, true>(w.part + PART_CG1, G, tol2, true, alpha, beta, rho, ref, conv);
     while (it < maxit) {
       bool all = true;
 #pragma unroll
@@ -962,38 +1039,24 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
         const long o = (long)p * n;
         int k0, k1;
         own_range(scnt[p], b, G, k0, k1);
-        for (int kb = k0 + t; kb < k1; kb += MB * BT) {
-          double di[MB];
-#pragma unroll
-          for (int j = 0; j < MB; j++) {
-            const int k = kb + j * BT;
-            di[j] = k < k1 ? w.Dinv[o + __ldcg(w.idx + o + k)] : 0.0;
-          }
-#pragma unroll
-          for (int j = 0; j < MB; j++) {
-            const int k = kb + j * BT;
-            if (k >= k1) continue;
-            const double uk = w.p[o + k], qk = w.q[o + k];
-            // (the first directions are u and K u themselves)
-            const double pk = it == 0 ? uk : fma(beta[p], w.pd[o + k], uk);
-            const double sk = it == 0 ? qk : fma(beta[p], w.sd[o + k], qk);
-            w.pd[o + k] = pk;
-            w.sd[o + k] = sk;
-            w.xk[o + k] = fma(alpha[p], pk, w.xk[o + k]);
-            const double rk = fma(-alpha[p], sk, w.r[o + k]);
-            w.r[o + k] = rk;
-            w.p[o + k] = rk * di[j];
-          }
+        for (int k = k0 + t; k < k1; k += BT) {
+          const double uk = w.p[o + k], qk = w.q[o + k];
+          // (the first directions are u and K u themselves)
+          const double pk = it == 0 ? uk : fma(beta[p], w.pd[o + k], uk);
+          const double sk = it == 0 ? qk : fma(beta[p], w.sd[o + k], qk);
+          w.pd[o + k] = pk;
+          w.sd[o + k] = sk;
+          w.xk[o + k] = fma(alpha[p], pk, w.xk[o + k]);
+          w.r[o + k] = fma(-alpha[p], sk, w.r[o + k]);
         }
       }
-      if (!(ok = grid_sync(bar, err))) break;
-      product(conv);
-      double v2[2 * N];
+      if (!(ok = precondition())) break;
+      double v3[3 * N];
 #pragma unroll
-      for (int j = 0; j < 2 * N; j++) v2[j] = acc[j];
-      block_sum_small<2 * N, BT>(v2, w.part + PART_CG1 + (long)b * PART_ROW);
+      for (int j = 0; j < 3 * N; j++) v3[j] = acc[j];
+      block_sum_small<3 * N, BT>(v3, w.part + PART_CG1 + (long)b * PART_ROW);
       if (!(ok = grid_sync(bar, err))) break;
-      cg_scalars<N, false>(w.part + PART_CG1, G, tol2, false, alpha, beta, gam, ref, conv);
+      cg_scalars<N, true>(w.part + PART_CG1, G, tol2, false, alpha, beta, rho, ref, conv);
       it++;
     }
   }
@@ -1013,26 +1076,13 @@ __device__ __forceinline__ void cg_mem(const PfGeom& g, const PfWork& w, double 
 #pragma unroll
     for (int p = 0; p < N; p++) {
       w.scal[16 + p] = ref[p];
-      w.scal[24 + p] = gam[p];
+      w.scal[24 + p] = rho[p];
       w.flag[1 + p] = conv[p] ? 1 : 0;
     }
     w.flag[11] = it;
   }
 }
 
-// Eq. 4 by conjugate gradients preconditioned with D, in one launch:
-//  1. list: each block counts the cells of its chunk of the grid that carry
-//     a label; after a barrier it knows its offset, and it writes the list
-//     (idx: cell of each unknown, in cell order) and its inverse (pos, -1
-//     for cells off the list);
-//  2. start: b = -(R - D s_k) (s_k the region's sum R / sum D), x0 = 0 or
-//     (warm) the x given, r0 = b - K x0, u0 = r0/D, and the sums;
-//  3. iterations until every phase has r.r/D <= tol2 b.b/D or maxit, with
-//     the state in registers (cg_one) when every phase has at most one
-//     unknown a thread, or two with N <= 2; a larger band is left to
-//     k_qmap_cg_mem (w.flag[18] set), which iterates with it in memory;
-//  4. x written back to the grid (cold start: 0 off the list).
-// A phase whose alpha is not positive stops where it is.
 // x 2^k for |k| <= 2000 as two exact power-of-two factors (each in
 // [-1000, 1000], a normal double): exact unless the result leaves the
 // normal range.
@@ -1322,6 +1372,9 @@ __global__ void __launch_bounds__(PF_THREADS, 1) k_qmap_cg_mem(PfGeom g, PfWork 
                                                                int warm, int maxit) {
   __shared__ int scnt[N];
   if (threadIdx.x < N) scnt[threadIdx.x] = __ldcg(w.flag + 12 + threadIdx.x);
+  // the neighbour flags start at epoch 0 (published by cg_mem's first grid
+  // barrier, before the first exchange)
+  if (threadIdx.x == 0) reinterpret_cast<unsigned*>(w.part + PART_NBR)[8 * blockIdx.x] = 0u;
   __syncthreads();
   const int n = (int)g.ncell, G = (int)gridDim.x, b = (int)blockIdx.x;
   const int cc = (n + G - 1) / G, c0 = min(n, b * cc), c1 = min(n, c0 + cc);
