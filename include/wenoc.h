@@ -520,6 +520,21 @@ wc_status wc_convert_f32(const double *x_dev, float *f_dev, double *back_dev, lo
  * Synchronizes stream. */
 wc_status wc_grid_barrier_check(int *words_dev, int skip_block, int rounds, void *stream);
 
+/* The neighbour barrier of the Q-map preconditioner's exchanges on its own:
+ * one block of 256 threads per SM, blocks on a line, block b waiting in each
+ * of `rounds` exchanges for the blocks within `span` (>= 1) of it (its
+ * neighbours' epoch flags, acquire loads, bounded polls).  words_dev: at
+ * least wc_neighbour_barrier_words() device ints (cleared by the call; 0 if
+ * the device cannot be queried), nwords their number (WC_ERR_ARG if fewer).
+ * skip_block >= 0 makes that block leave before the first exchange: its
+ * neighbours' waits run out, every other block stops waiting on the error
+ * word, and the call returns WC_ERR_TIMEOUT (after a few seconds) with the
+ * context usable; skip_block = -1: WC_OK.  The paper has no counterpart; it
+ * lets a test exercise the barrier and its time-out.  Synchronizes stream. */
+size_t wc_neighbour_barrier_words(void);
+wc_status wc_neighbour_barrier_check(int *words_dev, size_t nwords, int skip_block, int span,
+                                     int rounds, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -897,6 +897,23 @@ extern "C" wc_status wc_grid_barrier_check(int* words, int skip_block, int round
   return h[2] ? WC_ERR_TIMEOUT : WC_OK;
 }
 
+extern "C" size_t wc_neighbour_barrier_words(void) { return pf_nbr_check_words(); }
+
+extern "C" wc_status wc_neighbour_barrier_check(int* words, size_t nwords, int skip_block,
+                                                int span, int rounds, void* stream) {
+  if (!words || rounds < 1 || skip_block < -1 || span < 1) return WC_ERR_ARG;
+  const size_t need = pf_nbr_check_words();
+  if (need == 0) return WC_ERR_CUDA;
+  if (nwords < need) return WC_ERR_ARG;
+  cudaStream_t st = S(stream);
+  cudaError_t e = pf_nbr_check(words, skip_block, span, rounds, st);
+  int h[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, words, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return WC_ERR_CUDA;
+  return h[2] ? WC_ERR_TIMEOUT : WC_OK;
+}
+
 // ------------------------------------------------------------------ conversion check
 __global__ void k_convert_f32(const double* x, float* f, double* back, long n) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;

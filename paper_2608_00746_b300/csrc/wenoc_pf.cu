@@ -1392,6 +1392,19 @@ __global__ void __launch_bounds__(PF_THREADS) k_barrier_check(unsigned* bar, int
     if (!grid_sync(bar, err)) return;
 }
 
+// The neighbour barrier alone, for its test: blocks on a line, block b
+// waiting for the blocks within span of it, rounds exchanges; block skip
+// (>= 0) leaves before the first, so its neighbours' waits run out and set
+// the error word, and the others stop waiting when they see it.
+__global__ void __launch_bounds__(PF_THREADS) k_nbr_check(unsigned* flags, int* err, int skip,
+                                                          int span, int rounds) {
+  const int b = (int)blockIdx.x, G = (int)gridDim.x;
+  if (b == skip) return;
+  const int lo = max(0, b - span), hi = min(G - 1, b + span);
+  for (int r = 0; r < rounds; r++)
+    if (!nbr_sync(flags, lo, hi, (unsigned)(r + 1), err)) return;
+}
+
 // ------------------------------------------------------------------ launchers
 #define PF_DISPATCH(N, call)                       \
   switch (N) {                                     \
@@ -1476,6 +1489,27 @@ cudaError_t pf_barrier_check(int* words, int skip, int rounds, cudaStream_t st) 
   void* args[] = {&bar, &err, &skip, &rounds};
   return cudaLaunchCooperativeKernel((const void*)k_barrier_check, dim3(sms < 1 ? 1 : sms),
                                      dim3(PF_THREADS), args, 0, st);
+}
+
+size_t pf_nbr_check_words() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    return 0;
+  return 8 + 8 * (size_t)sms;
+}
+
+cudaError_t pf_nbr_check(int* words, int skip, int span, int rounds, cudaStream_t st) {
+  const size_t nw = pf_nbr_check_words();
+  if (nw == 0) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(words, 0, nw * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const unsigned sms = (unsigned)((nw - 8) / 8);
+  int* err = words + 2;
+  unsigned* flags = reinterpret_cast<unsigned*>(words + 8);
+  void* args[] = {&flags, &err, &skip, &span, &rounds};
+  return cudaLaunchCooperativeKernel((const void*)k_nbr_check, dim3(sms), dim3(PF_THREADS), args,
+                                     0, st);
 }
 
 }  // namespace wc

@@ -108,5 +108,9 @@ cudaError_t pf_qmap_solve(const PfGeom& g, const PfWork& w, int warm, double tol
 // rounds barriers of one block per SM; block skip >= 0 never arrives, so
 // the others' waits run out and words[2] becomes nonzero.
 cudaError_t pf_barrier_check(int* words, int skip, int rounds, cudaStream_t st);
+// The preconditioner's neighbour barrier alone: words of pf_nbr_check_words()
+// ints (0 if the device cannot be queried; cleared here), the error at [2].
+size_t pf_nbr_check_words();
+cudaError_t pf_nbr_check(int* words, int skip, int span, int rounds, cudaStream_t st);
 
 }  // namespace wc

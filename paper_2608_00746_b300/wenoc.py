@@ -112,6 +112,9 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_double), _VP]),
     "wc_convert_f32": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_long, _VP]),
     "wc_grid_barrier_check": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP]),
+    "wc_neighbour_barrier_words": (ctypes.c_size_t, []),
+    "wc_neighbour_barrier_check": (ctypes.c_int, [_VP, ctypes.c_size_t, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_int, _VP]),
     "wc_sweep_timing_begin": (ctypes.c_int, [_VP, ctypes.c_int]),
     "wc_sweep_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_double),
@@ -485,6 +488,15 @@ def grid_barrier_check(skip_block=-1, rounds=100):
     words = torch.zeros(4, dtype=torch.int32, device="cuda")
     return lib().wc_grid_barrier_check(_dptr(words), int(skip_block), int(rounds),
                                        _stream(torch.cuda.current_stream()))
+
+
+def neighbour_barrier_check(skip_block=-1, span=1, rounds=100):
+    """Runs the Q-map preconditioner's neighbour barrier alone (see
+    wc_neighbour_barrier_check); returns the status code."""
+    n = lib().wc_neighbour_barrier_words()
+    words = torch.zeros(max(n, 8), dtype=torch.int32, device="cuda")
+    return lib().wc_neighbour_barrier_check(_dptr(words), n, int(skip_block), int(span),
+                                            int(rounds), _stream(torch.cuda.current_stream()))
 
 
 def convert_f32(x):
