@@ -348,17 +348,12 @@ static SweepArgs make_args(const wc_grid* g, int dir, const double* U, double* L
     // one cell per lane, windows of WIN cells from a dynamic queue
     a.nwin = (a.n + WIN - 1) / WIN;
     a.ticket = g->ticket;
-    // segments of windows along a pencil for the FP64 sweep (measured 1.0-1.2 %
-    // faster, the same results bit for bit); one window an item in the
-    // reduced precisions (their face pass measured 0.2-1.6 % slower with the
-    // second state load a segment's windows take)
-    const WinPlan w = win_plan(a.n, a.npencil, g->d.precision == WC_PREC_FP64 ? WIN_SEG : 1);
+    const WinPlan w = win_plan(a.n, a.npencil);
     a.wfull = w.wfull;
     a.wtail = w.wtail;
     a.wgrp = w.wgrp;
     a.wslots = w.slots;
     a.nitems = w.nitems;
-    a.wseg = w.wseg;
   }
   // window schedule: blocks_per_sm when given, else the occupancy limit
   a.max_threads = (g->d.seg > 0 || g->d.blocks_per_sm > 0) ? sweep_threads(g) : 0;

@@ -340,13 +340,12 @@ static cudaError_t enqueue_windows(wc_patches* g, const double* src, double* dst
       a.npencil = (long)gr.count * gr.e * gr.e;
       a.nwin = (gr.e + WIN - 1) / WIN;
       a.ticket = g->d_ticket;
-      const WinPlan w = win_plan(gr.e, a.npencil, mixed ? 1 : WIN_SEG);
+      const WinPlan w = win_plan(gr.e, a.npencil);
       a.wfull = w.wfull;
       a.wtail = w.wtail;
       a.wgrp = w.wgrp;
       a.wslots = w.slots;
       a.nitems = w.nitems;
-      a.wseg = w.wseg;
       a.max_threads = 148L * g->ctas_per_sm * g->block;  // ctas_per_sm resident blocks
       a.inv_dx = (double)gr.e;  // unit-cube patch: dx = 1/e
       a.bclo = a.bchi = BC_OUTFLOW;

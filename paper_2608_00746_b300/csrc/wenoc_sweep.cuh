@@ -59,7 +59,6 @@ struct SweepArgs {
   unsigned* ticket;
   unsigned nwarps;
   int wfull, wtail, wgrp, wslots;
-  int wseg;            // full windows of one pencil a queue item takes in turn
   unsigned nitems;
   // face dump (window schedule only; null in the operator's own launches):
   // the limited conservative face states U^L_{i+1/2} and U^R_{i-1/2} of

@@ -18,31 +18,25 @@ constexpr int WIN = 30;        // cells updated per window
 constexpr int WIN_SLOTS = 36;  // cells c0-3 .. c0+32 held in shared memory
 constexpr int WIN_SLOTS_MAX = 72;  // slots of a warp whose groups hold pencil tails
 constexpr int WIN_BLOCK = 128;  // threads per block unless configured
-constexpr int WIN_SEG = 8;      // full windows of a pencil a queue item takes
 
-// The queue of a direction sweep: the wfull full windows of WIN cells of
-// each pencil in segments of up to wseg consecutive windows, a segment an
-// item (segment-major, pencil fastest), then the tails, wtail = n - WIN
-// wfull cells of each pencil.  A warp takes a segment's windows in turn,
-// each after the first reusing the last six converted cells of the one
-// before (sweep_window, cont).  A tail of up to 14 cells takes a group of wtail + 2 lanes
+// The queue of a direction sweep: wfull full windows of WIN cells per pencil
+// (window-major, pencil fastest), then the tails, wtail = n - WIN wfull cells
+// of each pencil.  A tail of up to 14 cells takes a group of wtail + 2 lanes
 // (the two outer lanes reconstruct its neighbours), and one warp takes the
 // tails of wgrp = 32 / (wtail + 2) pencils at once; a longer tail takes a
 // whole warp (wgrp = 1).  Bundling the tails saves the passes that a 32-lane
 // window spends on a few cells: 18 -> 17.1 warp passes per 512-cell pencil.
 struct WinPlan {
-  int wfull, wtail, wgrp, slots, wseg;
+  int wfull, wtail, wgrp, slots;
   unsigned nitems;
 };
-inline WinPlan win_plan(int n, long npencil, int wseg = WIN_SEG) {
+inline WinPlan win_plan(int n, long npencil) {
   WinPlan w;
   w.wfull = n / WIN;
   w.wtail = n - WIN * w.wfull;
   w.wgrp = w.wtail == 0 ? 0 : (w.wtail + 2 <= 16 ? 32 / (w.wtail + 2) : 1);
-  w.wseg = wseg < 1 ? 1 : wseg;
   const long ntail = w.wtail == 0 ? 0 : (npencil + w.wgrp - 1) / w.wgrp;
-  const long nseg = (w.wfull + w.wseg - 1) / w.wseg;  // segments a pencil
-  w.nitems = (unsigned)(npencil * nseg + ntail);
+  w.nitems = (unsigned)(npencil * w.wfull + ntail);
   w.slots = w.wgrp > 1 ? w.wgrp * (w.wtail + 6) : WIN_SLOTS;
   if (w.slots < WIN_SLOTS) w.slots = WIN_SLOTS;
   return w;
@@ -171,14 +165,12 @@ __device__ __forceinline__ void update_cell(const SweepArgs& a, const Mat& m, lo
 template <int N, int D, typename T, typename TF, int LW, int PART>
 __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, long base,
                                              long pencil, int c0, int j, int G, int sb,
-                                             bool active, bool store, bool cont, double* slots,
+                                             bool active, bool store, double* slots,
                                              double* fsc, double dt, unsigned& bad,
                                              unsigned* lstat) {
   using I = Idx<N, D>;
   constexpr int NV = I::NV;
   constexpr int SLOTD = WinSmem<N, D, T>::SLOTD;
-  // segments of windows (cont) in the FP64 sweeps only (win_plan's wseg)
-  constexpr bool STREAM = sizeof(T) == 8;
   // cells beyond the three ghost layers (lanes past the end of a short
   // pencil, whose results are not used) read the outermost ghost: the
   // boundary maps stay inside the pencil
@@ -206,21 +198,7 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
   const int c = c0 - 1 + j;
   double Ub[NV], Vtmp[NV];
   load_cons(c, Ub);
-  if (STREAM && cont) {
-    // a full window after the previous one of its pencil (c0 = previous c0
-    // + WIN): its slots 0..5 (cells c0 - 3 .. c0 + 2) are the previous
-    // window's 30..35, and lane j < 30 converts cell c0 + 3 + j into slot
-    // j + 6 -- one conversion pass on 30 lanes instead of a full pass and a
-    // second one of four lanes for the outer cells, for a second load of a
-    // cell's state (the lane's own average is still needed)
-    for (int x = j; x < 6 * SLOTD; x += 32) slots[x] = slots[30 * SLOTD + x];
-    __syncwarp();
-    if (j < 30) {
-      double u[NV], v[NV];
-      load_cons(c0 + 3 + j, u);
-      store_slot(j + 6, u, v);
-    }
-  } else if (store) {
+  if (store) {
     store_slot(sb + j + 2, Ub, Vtmp);
     // the group's outer stencil cells: slots 0, 1, G + 2, G + 3
     for (int e = j; e < 4; e += G) {
@@ -413,10 +391,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? WC_WIN_MINB64 : WC_WIN_M
   double* slots = smem + (threadIdx.x >> 5) * (a.wslots * WS::SLOTD + 32 * WS::FSC);
   double* fsc = slots + a.wslots * WS::SLOTD + lane;  // this lane's scratch column
   const unsigned nitems = a.nitems;
-  // segments of wseg full windows a pencil in the FP64 sweeps (the reduced
-  // precisions take one window an item: the host gives them wseg = 1)
-  const int wseg = sizeof(T) == 8 && a.wseg > 1 ? a.wseg : 1;
-  const unsigned nfull = (unsigned)(a.npencil * ((a.wfull + wseg - 1) / wseg));
+  const unsigned nfull = (unsigned)(a.npencil * a.wfull);
   unsigned bad = 0u;
   unsigned lstat[2] = {0u, 0u};
   double dt = 0.0;
@@ -434,18 +409,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? WC_WIN_MINB64 : WC_WIN_M
     bool active = true, store = true;
     if (it < nfull) {
       tr = (long)(it % (unsigned)a.npencil);
-      if constexpr (sizeof(T) == 8) {
-        // a segment: full windows w0 .. w1 - 1 of pencil tr in turn
-        const int w0 = (int)(it / (unsigned)a.npencil) * wseg;
-        const int w1 = min(w0 + wseg, a.wfull);
-        const long base = pencil_base(a, tr);
-        for (int wi = w0; wi < w1; wi++)
-          sweep_window<N, D, T, TF, LW, PART>(a, m, base, tr, wi * WIN, lane, 32, 0, true, true,
-                                              wi > w0, slots, fsc, dt, bad, lstat);
-        continue;
-      } else {
-        c0 = (int)(it / (unsigned)a.npencil) * WIN;  // (wseg is 1 here)
-      }
+      c0 = (int)(it / (unsigned)a.npencil) * WIN;
     } else {
       const unsigned t = it - nfull;
       c0 = a.wfull * WIN;
@@ -470,8 +434,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? WC_WIN_MINB64 : WC_WIN_M
       }
     }
     const long base = pencil_base(a, tr);
-    sweep_window<N, D, T, TF, LW, PART>(a, m, base, tr, c0, j, G, sb, active, store, false,
-                                        slots, fsc, dt, bad, lstat);
+    sweep_window<N, D, T, TF, LW, PART>(a, m, base, tr, c0, j, G, sb, active, store, slots, fsc,
+                                        dt, bad, lstat);
   }
   if (lane == 0) {
     __threadfence();
