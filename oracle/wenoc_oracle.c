@@ -69,7 +69,14 @@
  *      sum_p alpha_p / (rho_p c_p^2) (Wood), rho_p c_p^2 = gamma_p (P +
  *      Pinf_p).  The source factor alpha_p (1 + K_p) of Eq. 3 is evaluated
  *      at the cell average (as for K_p = 0); the wave speeds and the time
- *      step use this mixture sound speed.
+ *      step use this mixture sound speed.  In the sound speed a fraction
+ *      below zero (an excursion of the scheme above its bound-preserving CFL
+ *      number, or the rounding residue of R13) enters Wood's sum as zero: a
+ *      phase cannot add negative compressibility, and at a low-pressure face
+ *      state a gas fraction of -4e-4 beside water already turns the
+ *      unclipped sum negative, leaving no real speed.  The source factors
+ *      keep the sum over the fractions as they are: only then does sum_p
+ *      alpha_p (1 + K_p) = 1 hold, which keeps the fraction sum at one.
  *  R13 Rounding residue below the bounds.  In exact arithmetic the faces
  *      scaled by Eq. 18 (f_min = 0), Eq. 20 and Eq. 21 have non-negative
  *      masses and fractions, and every Runge-Kutta stage (a convex
@@ -560,12 +567,16 @@ static int recon_cell(const or_grid *g, const double *Ust, double *UL, double *U
 }
 
 /* rho c^2 of the mixture for the pressure P and fractions alpha: Eq. 2 with
- * K_p = 0 (R8), or Wood's formula for the Kapila model (R15). */
-static double mixture_rhoc2(const or_grid *g, const double *alpha, double P) {
+ * K_p = 0 (R8), or Wood's formula for the Kapila model (R15), whose sum takes
+ * a negative fraction as zero when clip is set (the sound speed). */
+static double mixture_rhoc2(const or_grid *g, const double *alpha, double P, int clip) {
   int N = g->N;
   if (g->kmodel) {
     double s = 0.0;
-    for (int p = 0; p < N; p++) s += alpha[p] / (g->gamma[p] * (P + g->pinf[p]));
+    for (int p = 0; p < N; p++) {
+      double a = clip && alpha[p] < 0.0 ? 0.0 : alpha[p];
+      s += a / (g->gamma[p] * (P + g->pinf[p]));
+    }
     return 1.0 / s;
   }
   double num = 0.0, den = 0.0;
@@ -585,7 +596,7 @@ static double sound_speed(const or_grid *g, const double *U, const double *V) {
     rho += U[IMASS(p)];
     alpha[p] = U[IALF(g, p)];
   }
-  return sqrt(mixture_rhoc2(g, alpha, V[IENE(g)]) / rho);
+  return sqrt(mixture_rhoc2(g, alpha, V[IENE(g)], 1) / rho);
 }
 
 /* Physical flux of Eq. 1 (hyperbolic part) in direction dir. */
@@ -746,7 +757,7 @@ static int rhs_dir(const or_grid *g, int dir, const double *U, double *Lout) {
           for (int v = 0; v < nvar; v++) uc[v] = U[(long)v * nc + cell];
           cons_to_prim(g, uc, vc);
           for (int p = 0; p < N; p++) alpha[p] = uc[IALF(g, p)];
-          double rhoc2 = mixture_rhoc2(g, alpha, vc[IENE(g)]);
+          double rhoc2 = mixture_rhoc2(g, alpha, vc[IENE(g)], 0);
           for (int p = 0; p < N; p++)
             onepk[p] = rhoc2 / (g->gamma[p] * (vc[IENE(g)] + g->pinf[p]));
         }

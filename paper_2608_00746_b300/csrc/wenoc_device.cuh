@@ -787,7 +787,9 @@ __device__ __forceinline__ TF inv_rhoc2_phase(const Mat& m, int p, TF P) {
 
 // Source factors alpha_p (1 + K_p) of Eq. 3 at a cell average (alpha from the
 // conservative state U, pressure P): alpha_p for K_p = 0; for the Kapila
-// model alpha_p rho c^2 / (rho_p c_p^2) with Wood's rho c^2.
+// model alpha_p rho c^2 / (rho_p c_p^2) with Wood's rho c^2 over the fractions
+// as they are (unlike the sound speed, no clip: sum_p alpha_p (1 + K_p) = 1
+// keeps the fraction sum at one).
 template <int N, int D>
 __device__ __forceinline__ void source_factors(const Mat& m, const double* U, double P,
                                                double* f) {
@@ -816,10 +818,13 @@ __device__ __forceinline__ TF sound_speed(const Mat& m, const double* U, TF rho,
   using I = Idx<N, D>;
   if (m.kapila) {
     // Kapila model: K_p = rho c^2 / (rho_p c_p^2) - 1 with sum alpha_p K_p = 0
-    // gives Wood's 1 / (rho c^2) = sum_p alpha_p / (rho_p c_p^2)
+    // gives Wood's 1 / (rho c^2) = sum_p alpha_p / (rho_p c_p^2).  A fraction
+    // below zero enters as zero: at a low-pressure face a gas fraction of
+    // -4e-4 beside water turns the unclipped sum negative (no real speed)
     TF sw = TF(0);
 #pragma unroll
-    for (int p = 0; p < N; p++) sw = sw + cvt<TF>(U[I::A(p)]) * inv_rhoc2_phase<TF>(m, p, P);
+    for (int p = 0; p < N; p++)
+      sw = sw + dmax(cvt<TF>(U[I::A(p)]), TF(0)) * inv_rhoc2_phase<TF>(m, p, P);
     const TF xw = rho * sw;
     if (in_range(xw, TF(1e-30), TF(1e30))) return rsqrt_nr(xw);
     return TF(1) / sqrt(xw);

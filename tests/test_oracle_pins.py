@@ -665,6 +665,40 @@ def test_kapila_wood_speed_air_water_half():
     assert ca > 20 * ck
 
 
+def test_kapila_speed_takes_negative_fraction_as_zero():
+    """A gas fraction below zero beside water at low pressure: the unclipped
+    Wood sum is negative (no real speed).  Taking the fraction as zero leaves
+    water alone in the sum, c^2 = gamma_w (P + Pinf_w) / (alpha_w rho)."""
+    g = [1.4, 4.4]
+    pi = [0.0, 6e8]
+    aair, P, rho_w = -4.2e-4, 6e5, 1000.0
+    aw = 1.0 - aair
+    assert aair / (g[0] * P) + aw / (g[1] * (P + pi[1])) < 0.0  # the unclipped sum
+    V = np.array([[1e-4], [aw * rho_w], [0.0], [P], [aair], [aw]])
+    gk = oracle.Grid((1,), (1.0,), g, pi, kmodel="kapila")
+    U = oracle.prim_to_cons(gk, V)
+    c = oracle.sound_speed(gk, U)[0]
+    rho = U[0, 0] + U[1, 0]
+    assert c == pytest.approx(np.sqrt(g[1] * (P + pi[1]) / (aw * rho)), rel=1e-14)
+    # zero fraction: the same speed as the clipped one
+    V0 = V.copy()
+    V0[4], V0[5] = 0.0, aw
+    assert oracle.sound_speed(gk, oracle.prim_to_cons(gk, V0))[0] == pytest.approx(c, rel=1e-14)
+    assert np.isfinite(oracle.max_rate(gk, U))
+    # the source factors keep the fractions as they are: with negative gas
+    # fractions in a compressing flow the rhs still sums to zero over phases
+    n = 32
+    x = (np.arange(n) + 0.5) / n
+    aa = 1e-3 * np.cos(2 * np.pi * x) - 2e-4  # dips below zero
+    Vn = np.stack([1.2 * aa, rho_w * (1 - aa), -50.0 * np.sin(2 * np.pi * x),
+                   np.full(n, 2e6), aa, 1 - aa])
+    gn = oracle.Grid((n,), (1.0 / n,), g, pi, flux="hllc", kmodel="kapila")
+    Un = oracle.prim_to_cons(gn, Vn)
+    L = oracle.rhs(gn, Un)
+    assert np.isfinite(L).all()
+    assert np.abs(L[4:6].sum(0)).max() / oracle.max_rate(gn, Un) < 1e-13
+
+
 def test_kapila_reduces_to_allaire_for_one_material():
     """Two phases of the same material (and one phase alone): K_p = 0, so the
     Kapila rhs equals the Allaire rhs to round-off."""
