@@ -574,6 +574,20 @@ __device__ __forceinline__ double stage_bound(double x, double t0, double t1, do
   return x;
 }
 
+// One Runge-Kutta stage value x = r0 u0 + r1 u1 + r2dt L (r2dt = r2 dt) as two
+// fused multiply-adds: three FP64 operations where the terms rounded one by
+// one take five, with a rounding error of at most three units of 2^-53 of
+// |r0 u0| + |r1 u1| + |r2dt L|, far inside the stage rule's 2^-48.  For a
+// bounded variable (mass or fraction) the terms of that rule are formed only
+// when x has left its bound.
+__device__ __forceinline__ double rk_combine(double r0, double u0, double r1, double u1,
+                                             double r2dt, double L, bool bounded, bool frac) {
+  double x = fma(r2dt, L, fma(r1, u1, r0 * u0));
+  if (bounded && (lt0_ieee(x) || (frac && gt1_ieee(x))))
+    x = stage_bound(x, r0 * u0, r1 * u1, r2dt * L, frac);
+  return x;
+}
+
 // Eq. 23-25 (WENO-CL) on one face: S_p = alpha_p,face - alpha_p,bar (the
 // factor 2/dx of Eq. 24 cancels), p-hat the first phase of largest |S_p|,
 // S-hat = S_phat - sum_p S_p, theta_phat = clamp(S-hat / S_phat),

@@ -421,18 +421,10 @@ __device__ __forceinline__ void sweep_segment(const SweepArgs& a, const Mat& m, 
             a.L[idx] += val;
           } else {
             double Lt = a.mode == 2 ? a.L[idx] + val : val;
-            double u0 = a.U0[idx];
-            // (rounded term by term, without contraction)
-            const double t0 = __dmul_rn(a.rk0, u0), t1 = __dmul_rn(a.rk1, Uprev[v]),
-                         t2 = __dmul_rn(__dmul_rn(a.rk2, dt), Lt);
-            double un = __dadd_rn(__dadd_rn(t0, t1), t2);
             // masses >= 0 and fractions in [0, 1] up to the rounding of the
             // stage sum (not in the comparison schemes, which have no bounds)
-            if constexpr (LW != 2) {
-              if (v < N || v >= I::A(0))
-                un = stage_bound(un, t0, t1, t2, v >= I::A(0));
-            }
-            a.Uout[idx] = un;
+            a.Uout[idx] = rk_combine(a.rk0, a.U0[idx], a.rk1, Uprev[v], a.rk2 * dt, Lt,
+                                     LW != 2 && (v < N || v >= I::A(0)), v >= I::A(0));
           }
         }
       }

@@ -124,6 +124,7 @@ __device__ __forceinline__ void update_cell(const SweepArgs& a, const Mat& m, lo
   const double sdx = a.kind == 1 ? a.inv_dx : -a.inv_dx;
   double sf[N];
   source_factors<N, D>(m, Ub, Pb, sf);
+  const double r2dt = a.rk2 * dt;
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     double val = (F[v] - Fl[v]) * sdx;
@@ -136,16 +137,10 @@ __device__ __forceinline__ void update_cell(const SweepArgs& a, const Mat& m, lo
       a.L[idx] += val;
     } else {
       const double Lt = a.mode == 2 ? a.L[idx] + val : val;
-      // (rounded term by term, without contraction)
-      const double t0 = __dmul_rn(a.rk0, a.U0[idx]), t1 = __dmul_rn(a.rk1, Ub[v]),
-                   t2 = __dmul_rn(__dmul_rn(a.rk2, dt), Lt);
-      double un = __dadd_rn(__dadd_rn(t0, t1), t2);
       // masses >= 0 and fractions in [0, 1] up to the rounding of the
       // stage sum (not in the comparison schemes, which have no bounds)
-      if constexpr (LW != 2) {
-        if (v < N || v >= I::A(0)) un = stage_bound(un, t0, t1, t2, v >= I::A(0));
-      }
-      a.Uout[idx] = un;
+      a.Uout[idx] = rk_combine(a.rk0, a.U0[idx], a.rk1, Ub[v], r2dt, Lt,
+                               LW != 2 && (v < N || v >= I::A(0)), v >= I::A(0));
     }
   }
 }
