@@ -284,6 +284,24 @@ wc_status wc_compute_dt(wc_grid *g, double cfl, double *dt_dev, void *stream);
 wc_status wc_rk_step(wc_grid *g, double cfl, double dt_fixed, int nsteps, double *dt_host,
                      void *stream);
 
+/* wc_rk_step from and to host memory: uploads U_in_host ([NV][ncell], the
+ * layout of the bound state) into the bound state, runs nsteps >= 1 steps of
+ * SSP-RK3 as wc_rk_step does (same results bit for bit), and downloads the
+ * final state into U_out_host (may equal U_in_host: every upload completes
+ * before the first download starts).  Asynchronous on stream; the host
+ * buffers must stay valid until the stream has been synchronised.  With
+ * page-locked buffers the copies overlap the sweeps: the first step's first
+ * direction (x, which needs no time step) runs in 8 bands of rows, each
+ * after its rows have arrived, and the last step's last direction in 8
+ * bands of pencils, each copied back while the next one runs (an internal
+ * stream and events; the caller's stream waits for the last copy).  1-D
+ * grids, the segment schedule and the learned precision copy, step and copy
+ * back in sequence.  Errors: WC_ERR_ARG (null buffer, nsteps < 1, neither
+ * cfl nor dt_fixed positive), WC_ERR_STATE (no state, workspace or
+ * surrogate bound), WC_ERR_CUDA. */
+wc_status wc_rk_step_host(wc_grid *g, const double *U_in_host, double *U_out_host, double cfl,
+                          double dt_fixed, int nsteps, void *stream);
+
 /* The limiter chain of WENO-C alone (Eq. 17-21) in direction dir on ncell
  * independent cells: Ubar [NV][ncell] conservative cell averages, VL / VR
  * [NV][ncell] raw reconstructed primitive values at x_{i+1/2} and x_{i-1/2};

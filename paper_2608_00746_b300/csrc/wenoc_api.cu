@@ -53,6 +53,9 @@ struct wc_grid {
   double pf_resid = 0.0;
   int pf_unknowns[8] = {0};  // listed unknowns per phase of the last Q-map
   int pf_per_thread = 0;     // and the unknowns a thread kept in registers
+  // host-buffer step (wc_rk_step_host): its copy stream and band events
+  cudaStream_t cstream = nullptr;
+  std::vector<cudaEvent_t> hev;
 };
 
 static wc_status fail(wc_grid* g, wc_status s, const char* msg) {
@@ -156,6 +159,8 @@ extern "C" wc_status wc_init_grid(const wc_grid_desc* desc, wc_grid** out) {
 extern "C" void wc_destroy(wc_grid* g) {
   if (!g) return;
   for (cudaEvent_t ev : g->tev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : g->hev) cudaEventDestroy(ev);
+  if (g->cstream) cudaStreamDestroy(g->cstream);
   delete g;
 }
 extern "C" int wc_nvar(const wc_grid* g) { return g ? g->nv : 0; }
@@ -523,12 +528,29 @@ extern "C" wc_status wc_compute_dt(wc_grid* g, double cfl, double* dt_dev, void*
   return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "dt");
 }
 
+// Band hooks of the host-buffer step (wc_rk_step_host): the first
+// direction's sweep runs as nb launches over consecutive pencils, band b
+// after the copy stream's event up[b] (its rows uploaded), then the time
+// step's rate from the whole state; or the last direction's sweep runs as nb
+// launches, event done[b] recorded after band b (its cells final).
+struct HostBands {
+  int nb = 0;
+  const cudaEvent_t* up = nullptr;
+  cudaEvent_t* done = nullptr;
+};
+
+// Pencils t0 .. t1 - 1 of band b of nb over np pencils.
+static void band_range(long np, int nb, int b, long& t0, long& t1) {
+  t0 = np * b / nb;
+  t1 = np * (b + 1) / nb;
+}
+
 // One SSP-RK3 stage: dst = r0 U0 + r1 src + r2 dt L(src); L of Eq. 3, or of
 // Eq. 5 with the auxiliary fields Q (kind 1; face gradients limited to
 // dx / (12 d dt), reading R17).
 static wc_status stage(wc_grid* g, const double* src, double* dst, double r0, double r1,
                        double r2, double cfl, double dt_fixed, cudaStream_t st, int kind = 0,
-                       const double* Q = nullptr) {
+                       const double* Q = nullptr, const HostBands* hb = nullptr) {
   int D = g->d.dim;
   for (int dir = 0; dir < D; dir++) {
     SweepArgs a = make_args(g, dir, src, g->Lacc);
@@ -547,8 +569,34 @@ static wc_status stage(wc_grid* g, const double* src, double* dst, double r0, do
     a.rk2 = r2;
     if (D == 1) a.mode = 3;
     else a.mode = dir == 0 ? 0 : (dir < D - 1 ? 1 : 2);
-    cudaError_t e = launch(g, a, st);
-    if (e != cudaSuccess) return cuda_fail(g, e, "sweep");
+    const bool up = hb && hb->up && dir == 0, down = hb && hb->done && dir == D - 1;
+    if (!up && !down) {
+      cudaError_t e = launch(g, a, st);
+      if (e != cudaSuccess) return cuda_fail(g, e, "sweep");
+      continue;
+    }
+    // (band launches: the window plan of each band's pencils; the split
+    // sweep's face buffer is indexed by the band's own pencils in both passes)
+    for (int b = 0; b < hb->nb; b++) {
+      long t0, t1;
+      band_range(a.npencil, hb->nb, b, t0, t1);
+      SweepArgs ab = a;
+      ab.tr0 = t0;
+      ab.npencil = t1 - t0;
+      const WinPlan w = win_plan(ab.n, ab.npencil);
+      ab.nitems = w.nitems;
+      ab.wslots = w.slots;
+      cudaError_t e = up ? cudaStreamWaitEvent(st, hb->up[b], 0) : cudaSuccess;
+      if (e == cudaSuccess) e = launch(g, ab, st);
+      if (e == cudaSuccess && down) e = cudaEventRecord(hb->done[b], st);
+      if (e != cudaSuccess) return cuda_fail(g, e, "band sweep");
+    }
+    // the first direction (mode 0) needs no time step; the others take it
+    // from the state, now uploaded in full
+    if (up && !(dt_fixed > 0.0)) {
+      wc_status r = launch_rate(g, g->U, st);
+      if (r) return r;
+    }
   }
   return WC_OK;
 }
@@ -583,6 +631,109 @@ extern "C" wc_status wc_rk_step(wc_grid* g, double cfl, double dt_fixed, int nst
     }
   }
   return WC_OK;
+}
+
+// ------------------------------------------------------------------ host buffers
+// Bands of the host-buffer step's overlapped sweeps.
+static constexpr int kHostBands = 8;
+
+static wc_status host_resources(wc_grid* g) {
+  if (!g->cstream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&g->cstream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      g->cstream = nullptr;
+      return cuda_fail(g, e, "copy stream");
+    }
+  }
+  while ((int)g->hev.size() < 2 * kHostBands + 2) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(g, e, "event");
+    g->hev.push_back(ev);
+  }
+  return WC_OK;
+}
+
+extern "C" wc_status wc_rk_step_host(wc_grid* g, const double* U_in_host, double* U_out_host,
+                                     double cfl, double dt_fixed, int nsteps, void* stream) {
+  if (!g || !U_in_host || !U_out_host || nsteps < 1) return WC_ERR_ARG;
+  if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return fail(g, WC_ERR_ARG, "need cfl > 0 or dt > 0");
+  if (!g->U || !g->ws) return fail(g, WC_ERR_STATE, "state/workspace not bound");
+  if (g->d.precision == WC_PREC_LEARNED && !g->mlp)
+    return fail(g, WC_ERR_STATE, "learned precision needs wc_set_mlp");
+  cudaStream_t st = S(stream);
+  const size_t nv = (size_t)g->nv, nc = (size_t)g->ncell;
+  const int D = g->d.dim;
+  // overlap needs a second direction after the banded first one and the
+  // window schedule; the learned weights come from one inference over the
+  // whole state per direction, so that precision runs the steps unbanded
+  if (D == 1 || g->d.seg > 0 || g->d.precision == WC_PREC_LEARNED) {
+    wc_status r = wc_upload_state(g, U_in_host, stream);
+    if (!r) r = wc_rk_step(g, cfl, dt_fixed, nsteps, nullptr, stream);
+    if (!r) r = wc_download_state(g, U_out_host, stream);
+    return r;
+  }
+  wc_status r = host_resources(g);
+  if (r) return r;
+  cudaStream_t cs = g->cstream;
+  cudaEvent_t* up = g->hev.data();
+  cudaEvent_t* done = up + kHostBands;
+  cudaEvent_t start = up[2 * kHostBands], fin = up[2 * kHostBands + 1];
+  // first-direction bands: rows of x-pencils, contiguous in every field
+  const int n0 = g->d.n[0];
+  const long np0 = g->ncell / n0;
+  const int nb0 = np0 < kHostBands ? (int)np0 : kHostBands;
+  // last-direction bands: pencils tr0 .. tr1 - 1 hold the cells tr + k P
+  // (k < n, P = the direction's stride = its pencil count), a strided block
+  const int nl = g->d.n[D - 1];
+  const long npl = g->ncell / nl;
+  const int nbl = npl < kHostBands ? (int)npl : kHostBands;
+  // the upload waits for the work already on the caller's stream
+  cudaError_t e = cudaEventRecord(start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, start, 0);
+  for (int b = 0; b < nb0 && e == cudaSuccess; b++) {
+    long t0, t1;
+    band_range(np0, nb0, b, t0, t1);
+    const size_t off = (size_t)t0 * n0, cnt = (size_t)(t1 - t0) * n0;
+    for (size_t v = 0; v < nv && e == cudaSuccess; v++)
+      e = cudaMemcpyAsync(g->U + v * nc + off, U_in_host + v * nc + off, cnt * sizeof(double),
+                          cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(up[b], cs);
+  }
+  if (e != cudaSuccess) return cuda_fail(g, e, "band upload");
+  HostBands hu, hd;
+  hu.nb = nb0;
+  hu.up = up;
+  hd.nb = nbl;
+  hd.done = done;
+  for (int s = 0; s < nsteps; s++) {
+    const bool first = s == 0, last = s == nsteps - 1;
+    if (!first && !(dt_fixed > 0.0)) {
+      r = launch_rate(g, g->U, st);
+      if (r) return r;
+    }
+    if ((r = stage(g, g->U, g->B1, 0.0, 1.0, 1.0, cfl, dt_fixed, st, 0, nullptr,
+                   first ? &hu : nullptr)))
+      return r;
+    if ((r = stage(g, g->B1, g->B2, 0.75, 0.25, 0.25, cfl, dt_fixed, st))) return r;
+    if ((r = stage(g, g->B2, g->U, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, cfl, dt_fixed, st, 0,
+                   nullptr, last ? &hd : nullptr)))
+      return r;
+  }
+  for (int b = 0; b < nbl && e == cudaSuccess; b++) {
+    long t0, t1;
+    band_range(npl, nbl, b, t0, t1);
+    const size_t pitch = (size_t)npl * sizeof(double);
+    e = cudaStreamWaitEvent(cs, done[b], 0);
+    for (size_t v = 0; v < nv && e == cudaSuccess; v++)
+      e = cudaMemcpy2DAsync(U_out_host + v * nc + t0, pitch, g->U + v * nc + t0, pitch,
+                            (size_t)(t1 - t0) * sizeof(double), (size_t)nl,
+                            cudaMemcpyDeviceToHost, cs);
+  }
+  // the caller's stream covers the downloads
+  if (e == cudaSuccess) e = cudaEventRecord(fin, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, fin, 0);
+  return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "band download");
 }
 
 // ------------------------------------------------------------------ Phase-Field mechanism

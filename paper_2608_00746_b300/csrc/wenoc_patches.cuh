@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(128) k_patch_stage(PatchArgs pa, Mat m) {
       a.faceL = a.faceR = nullptr;
       a.fbuf = nullptr;
       a.poff = nullptr;
+      a.tr0 = 0;
       for (int pc = threadIdx.x; pc < e * e; pc += blockDim.x) {
         long base;
         if (dir == 0) base = off + (long)pc * e;

@@ -76,12 +76,18 @@ struct SweepArgs {
   // grid): pencil tr lies in patch tr / (nx ny), whose first cell in the
   // pooled state is poff[tr / (nx ny)], at the patch's own pencil tr % (nx ny)
   const long* poff;
+  // first pencil of a band launch (pencils tr0 .. tr0 + npencil - 1 of the
+  // grid's direction sweep; 0 for the whole sweep): the host-buffer step
+  // starts the first sweep on the rows already uploaded and returns the
+  // last sweep's bands while the next ones run
+  long tr0;
 };
 
 // First cell of pencil tr of a direction sweep (x fastest; for dir 1 the
 // pencils run over x, then z).
 __device__ __forceinline__ long pencil_base(const SweepArgs& a, long tr) {
   long o = 0;
+  tr += a.tr0;
   if (a.poff) {
     const long np = (long)a.nx * a.ny;  // pencils a patch (cube: every direction)
     o = __ldg(a.poff + tr / np);

@@ -95,6 +95,8 @@ _SIGS = {
     "wc_check_state": (ctypes.c_int, [_VP, _VP, ctypes.c_double, ctypes.POINTER(ctypes.c_long),
                                       ctypes.POINTER(ctypes.c_long), _VP]),
     "wc_upload_state": (ctypes.c_int, [_VP, _VP, _VP]),
+    "wc_rk_step_host": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, _VP]),
     "wc_download_state": (ctypes.c_int, [_VP, _VP, _VP]),
     "wc_prim_to_cons": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "wc_cons_to_prim": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
@@ -342,6 +344,19 @@ class Grid:
         self._check(lib().wc_rk_step(self.h, float(cfl), float(dt), int(nsteps),
                                      ctypes.byref(dth) if want_dt else None, _stream(stream)))
         return dth.value if want_dt else None
+
+    def rk_step_host(self, U_in, U_out=None, cfl=0.0, dt=0.0, nsteps=1, stream=None):
+        """Upload U_in (host, [NV][ncell], pinned for overlap), nsteps SSP-RK3
+        steps, download into U_out (default U_in); asynchronous on stream."""
+        U_out = U_in if U_out is None else U_out
+        for t in (U_in, U_out):
+            if t.device.type != "cpu" or t.dtype != torch.float64 or not t.is_contiguous() \
+                    or t.numel() != self.nv * self.ncell:
+                raise ValueError("host buffers: contiguous CPU float64 of NV x ncell values")
+        self._check(lib().wc_rk_step_host(self.h, ctypes.c_void_p(U_in.data_ptr()),
+                                          ctypes.c_void_p(U_out.data_ptr()), float(cfl), float(dt),
+                                          int(nsteps), _stream(stream)))
+        return U_out
 
     def upload(self, U_host, stream=None):
         self._check(lib().wc_upload_state(self.h, ctypes.c_void_p(U_host.data_ptr()),

@@ -103,6 +103,11 @@ def test_calls_before_binding_fail_cleanly():
     dt = ctypes.c_double(0)
     assert L.wc_rk_step(h, 0.2, 0.0, 1, ctypes.byref(dt), None) == 6   # WC_ERR_STATE
     assert L.wc_rk_step(h, 0.0, 0.0, 1, None, None) == 1                # no cfl, no dt
+    hb = (ctypes.c_double * (L.wc_nvar(h) * L.wc_ncell(h)))()
+    assert L.wc_rk_step_host(h, hb, hb, 0.2, 0.0, 1, None) == 6          # nothing bound
+    assert L.wc_rk_step_host(h, None, hb, 0.2, 0.0, 1, None) == 1
+    assert L.wc_rk_step_host(h, hb, hb, 0.2, 0.0, 0, None) == 1          # nsteps < 1
+    assert L.wc_rk_step_host(h, hb, hb, 0.0, 0.0, 1, None) == 1
     assert L.wc_rhs(h, None, None, None) == 1
     assert L.wc_limit(h, 5, 1, None, None, None, None, None, None, None) == 1
     buf = ctypes.create_string_buffer(64)

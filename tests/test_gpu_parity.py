@@ -221,3 +221,43 @@ def test_split_sweep_equals_single_pass(gpu, name, precision):
         outs.append((L, U))
     assert wenoc.lib().wc_face_buffer_bytes(g.h) > 0
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "learned"])
+@pytest.mark.parametrize("name", ["shock_bubble_2d_ragged", "spheres_3d_ragged", "circles_2d_n3",
+                                  "slab_1d_hllc", "five_phase_2d"])
+def test_host_buffer_step_equals_device_step(gpu, name, precision):
+    """wc_rk_step_host (the upload overlapping the first sweep in bands of
+    rows, the download overlapping the last sweep in bands of pencils; 1-D
+    and the learned precision in sequence) gives the device step's states
+    bit for bit: in place over several CFL steps, and into a second host
+    buffer with a fixed time step."""
+    import torch
+    from paper_2608_00746_b300 import surrogate
+    case = SMALL_CASES[name]()
+    if precision == "learned" and case.N > 3:
+        pytest.skip("the surrogate takes N <= 3")
+    go, g = grids(case, precision=precision)
+    if precision == "learned":
+        g.set_mlp(surrogate.Surrogate(seed=5).params, tau=1.0)
+    U0 = oracle.prim_to_cons(go, case.V)
+    cfl = case.cfl or 0.2
+    dt = 0.3 / oracle.max_rate(go, U0)
+    for kw, nsteps, inplace in (({"cfl": cfl}, 3, True), ({"dt": dt}, 1, False)):
+        Ud = to_dev(U0)
+        g.bind(Ud)
+        g.rk_step(nsteps=nsteps, **kw)
+        torch.cuda.synchronize()
+        g.sync_status()
+        ref = Ud.cpu().reshape(-1)
+        h_in = torch.from_numpy(U0.copy()).reshape(-1).pin_memory()
+        h_out = h_in if inplace else torch.full_like(h_in, float("nan")).pin_memory()
+        Ub = torch.full_like(Ud, float("nan"))  # the upload fills the bound state
+        g.bind(Ub)
+        g.rk_step_host(h_in, h_out, nsteps=nsteps, **kw)
+        torch.cuda.synchronize()
+        g.sync_status()
+        assert torch.equal(h_out, ref), (kw, nsteps)
+        assert torch.equal(Ub.cpu().reshape(-1), ref)
+        if not inplace:
+            assert torch.equal(h_in, torch.from_numpy(U0.copy()).reshape(-1))
