@@ -292,9 +292,11 @@ wc_status wc_rk_step(wc_grid *g, double cfl, double dt_fixed, int nsteps, double
  * buffers must stay valid until the stream has been synchronised.  With
  * page-locked buffers the copies overlap the sweeps: the first step's first
  * direction (x, which needs no time step) runs in 8 bands of rows, each
- * after its rows have arrived, and the last step's last direction in 8
- * bands of pencils, each copied back while the next one runs (an internal
- * stream and events; the caller's stream waits for the last copy).  1-D
+ * after its rows have arrived, and the last step's last sweep in 8 bands
+ * of pencils (2-D: its last stage takes y first and x last, rows again; the
+ * sum of the two directions' parts is the same), each copied back while the
+ * next one runs (an internal stream and events; the caller's stream waits
+ * for the last copy).  1-D
  * grids, the segment schedule and the learned precision copy, step and copy
  * back in sequence.  Errors: WC_ERR_ARG (null buffer, nsteps < 1, neither
  * cfl nor dt_fixed positive), WC_ERR_STATE (no state, workspace or

@@ -539,10 +539,20 @@ struct HostBands {
   cudaEvent_t* done = nullptr;
 };
 
-// Pencils t0 .. t1 - 1 of band b of nb over np pencils.
-static void band_range(long np, int nb, int b, long& t0, long& t1) {
-  t0 = np * b / nb;
-  t1 = np * (b + 1) / nb;
+// Pencils t0 .. t1 - 1 of band b of nb over np pencils.  The band whose copy
+// nothing hides is small (np / 32): the first one of an upload (small < 0;
+// the sweep waits for it) and the last one of a download (small > 0; the
+// step ends with it); the others share the rest evenly.
+static long band_edge(long np, int nb, int e, int small) {
+  if (nb < 2) return e == 0 ? 0 : np;
+  long s = np / 32;
+  if (s < 1) s = 1;
+  if (small < 0) return e == 0 ? 0 : s + (np - s) * (e - 1) / (nb - 1);
+  return e == nb ? np : (np - s) * e / (nb - 1);
+}
+static void band_range(long np, int nb, int b, int small, long& t0, long& t1) {
+  t0 = band_edge(np, nb, b, small);
+  t1 = band_edge(np, nb, b + 1, small);
 }
 
 // One SSP-RK3 stage: dst = r0 U0 + r1 src + r2 dt L(src); L of Eq. 3, or of
@@ -552,7 +562,12 @@ static wc_status stage(wc_grid* g, const double* src, double* dst, double r0, do
                        double r2, double cfl, double dt_fixed, cudaStream_t st, int kind = 0,
                        const double* Q = nullptr, const HostBands* hb = nullptr) {
   int D = g->d.dim;
-  for (int dir = 0; dir < D; dir++) {
+  // directions x, y, z; a 2-D stage whose last sweep is banded for the
+  // download takes y first, so that the banded sweep runs over rows (x
+  // pencils, contiguous in every field): L_y + L_x is L_x + L_y bit for bit
+  const bool swap = hb && hb->done && D == 2;
+  for (int k = 0; k < D; k++) {
+    const int dir = swap ? 1 - k : k;
     SweepArgs a = make_args(g, dir, src, g->Lacc);
     if (kind == 1) {
       a.kind = 1;
@@ -568,8 +583,8 @@ static wc_status stage(wc_grid* g, const double* src, double* dst, double r0, do
     a.rk1 = r1;
     a.rk2 = r2;
     if (D == 1) a.mode = 3;
-    else a.mode = dir == 0 ? 0 : (dir < D - 1 ? 1 : 2);
-    const bool up = hb && hb->up && dir == 0, down = hb && hb->done && dir == D - 1;
+    else a.mode = k == 0 ? 0 : (k < D - 1 ? 1 : 2);
+    const bool up = hb && hb->up && k == 0, down = hb && hb->done && k == D - 1;
     if (!up && !down) {
       cudaError_t e = launch(g, a, st);
       if (e != cudaSuccess) return cuda_fail(g, e, "sweep");
@@ -579,7 +594,7 @@ static wc_status stage(wc_grid* g, const double* src, double* dst, double r0, do
     // sweep's face buffer is indexed by the band's own pencils in both passes)
     for (int b = 0; b < hb->nb; b++) {
       long t0, t1;
-      band_range(a.npencil, hb->nb, b, t0, t1);
+      band_range(a.npencil, hb->nb, b, up ? -1 : 1, t0, t1);
       SweepArgs ab = a;
       ab.tr0 = t0;
       ab.npencil = t1 - t0;
@@ -683,9 +698,11 @@ extern "C" wc_status wc_rk_step_host(wc_grid* g, const double* U_in_host, double
   const int n0 = g->d.n[0];
   const long np0 = g->ncell / n0;
   const int nb0 = np0 < kHostBands ? (int)np0 : kHostBands;
-  // last-direction bands: pencils tr0 .. tr1 - 1 hold the cells tr + k P
-  // (k < n, P = the direction's stride = its pencil count), a strided block
-  const int nl = g->d.n[D - 1];
+  // last-sweep bands: rows of x-pencils in 2-D (the last stage takes y
+  // first); in 3-D z-pencils tr0 .. tr1 - 1, which hold the cells tr + k P
+  // (k < nz, P = nx ny), a strided block of rows of (tr1 - tr0) values
+  const int dl = D == 2 ? 0 : D - 1;
+  const int nl = g->d.n[dl];
   const long npl = g->ncell / nl;
   const int nbl = npl < kHostBands ? (int)npl : kHostBands;
   // the upload waits for the work already on the caller's stream
@@ -693,7 +710,7 @@ extern "C" wc_status wc_rk_step_host(wc_grid* g, const double* U_in_host, double
   if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, start, 0);
   for (int b = 0; b < nb0 && e == cudaSuccess; b++) {
     long t0, t1;
-    band_range(np0, nb0, b, t0, t1);
+    band_range(np0, nb0, b, -1, t0, t1);
     const size_t off = (size_t)t0 * n0, cnt = (size_t)(t1 - t0) * n0;
     for (size_t v = 0; v < nv && e == cudaSuccess; v++)
       e = cudaMemcpyAsync(g->U + v * nc + off, U_in_host + v * nc + off, cnt * sizeof(double),
@@ -722,13 +739,20 @@ extern "C" wc_status wc_rk_step_host(wc_grid* g, const double* U_in_host, double
   }
   for (int b = 0; b < nbl && e == cudaSuccess; b++) {
     long t0, t1;
-    band_range(npl, nbl, b, t0, t1);
-    const size_t pitch = (size_t)npl * sizeof(double);
+    band_range(npl, nbl, b, 1, t0, t1);
     e = cudaStreamWaitEvent(cs, done[b], 0);
-    for (size_t v = 0; v < nv && e == cudaSuccess; v++)
-      e = cudaMemcpy2DAsync(U_out_host + v * nc + t0, pitch, g->U + v * nc + t0, pitch,
-                            (size_t)(t1 - t0) * sizeof(double), (size_t)nl,
-                            cudaMemcpyDeviceToHost, cs);
+    if (dl == 0) {
+      const size_t off = (size_t)t0 * nl, cnt = (size_t)(t1 - t0) * nl;
+      for (size_t v = 0; v < nv && e == cudaSuccess; v++)
+        e = cudaMemcpyAsync(U_out_host + v * nc + off, g->U + v * nc + off,
+                            cnt * sizeof(double), cudaMemcpyDeviceToHost, cs);
+    } else {
+      const size_t pitch = (size_t)npl * sizeof(double);
+      for (size_t v = 0; v < nv && e == cudaSuccess; v++)
+        e = cudaMemcpy2DAsync(U_out_host + v * nc + t0, pitch, g->U + v * nc + t0, pitch,
+                              (size_t)(t1 - t0) * sizeof(double), (size_t)nl,
+                              cudaMemcpyDeviceToHost, cs);
+    }
   }
   // the caller's stream covers the downloads
   if (e == cudaSuccess) e = cudaEventRecord(fin, cs);
