@@ -151,6 +151,7 @@ extern "C" wc_status wc_init_grid(const wc_grid_desc* desc, wc_grid** out) {
     m.Cmin[p] = m.A[p] * d.pmin[p] + m.B[p];
     if (d.D[p] != 0.0) m.hasD = 1;
   }
+  m.psi_floor = psi_face_floor(m);
   g->err[0] = 0;
   *out = g;
   return WC_OK;

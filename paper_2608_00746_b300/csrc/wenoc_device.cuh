@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 namespace wc {
 
 constexpr int MAXP = 8;
@@ -35,7 +37,29 @@ struct Mat {
   double gam[MAXP];         // gamma_p
   int cmp;                  // CMP_NONE, or a comparison scheme without Eq. 16-21
   double js_eps;            // epsilon of the WENO-JS comparison
+  double psi_floor;         // a pressure from which on psi at a face is >= 0 (psi_face_floor)
 };
+
+// The lowest pressure t from which on every phase's factor of psi at a face
+// (Eq. 9 with Eq. 26: alpha_p A_p (P - Pmin_p), formed as fma(A_p, P, -A_p
+// Pmin_p)) is >= 0: the largest Pmin_p, raised by ulps until each of those
+// fused multiply-adds is >= 0 at t (then also at every P >= t, A_p > 0).  A
+// face with fractions >= 0 and P >= t has psi >= 0, whatever the rounding
+// of its sum of non-negative terms.
+inline double psi_face_floor(const Mat& m) {
+  double t = -HUGE_VAL;
+  for (int p = 0; p < m.N; p++) {
+    double tp = m.Apmin[p] / m.A[p];
+    for (int k = 0; k < 64; k++) {
+      const double r = std::fma(m.A[p], tp, -m.Apmin[p]);
+      if (r >= 0.0 && !std::signbit(r)) break;
+      tp = std::nextafter(tp, HUGE_VAL);
+    }
+    if (!(std::fma(m.A[p], tp, -m.Apmin[p]) >= 0.0)) return HUGE_VAL;  // never taken
+    if (tp > t) t = tp;
+  }
+  return t;
+}
 
 // Comparison schemes (Sec. 3.2, Sec. 4.1.1): every primitive variable with
 // its own weights, no coupling (Eq. 16) and no limiters (Eq. 17-21); run by
@@ -127,6 +151,15 @@ __device__ __forceinline__ bool in_range(float x, float lo, float hi) { return x
 __device__ __forceinline__ long long dkey(double x) {
   const long long b = dbits(x);
   return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+// x >= t for a non-NaN t; false for a NaN x (integer pipe)
+__device__ __forceinline__ bool ge_floor(double x, double t) {
+  const long long k = dkey(x);
+  return k >= dkey(t) && k <= 0x7FF0000000000000LL;
+}
+// x is +0, positive or +inf (not NaN, no sign bit; integer pipe)
+__device__ __forceinline__ bool nonneg_num(double x) {
+  return (unsigned long long)dbits(x) <= 0x7FF0000000000000ULL;
 }
 __device__ __forceinline__ double dmin(double a, double b) { return dkey(b) < dkey(a) ? b : a; }
 __device__ __forceinline__ double dmax(double a, double b) { return dkey(b) > dkey(a) ? b : a; }
@@ -755,11 +788,21 @@ __device__ __forceinline__ void limit_chain(const Mat& m, const double* Ub, doub
     double UC[I::NV];
 #pragma unroll
     for (int v = 0; v < I::NV; v++) UC[v] = (Ub[v] - (FL.U[v] + FR.U[v]) * (1.0 / 12.0)) * 1.2;
-    double pb = psi_prim<N, D>(m, Ub + I::A(0), Pb);
-    double pL = psi_prim<N, D>(m, aL, PL);
-    double pR = psi_prim<N, D>(m, aR, PR);
-    double pC = psi_cons<N, D>(m, UC);
-    thpsi = theta_lower(pb, pC, pL, pR);
+    const double pC = psi_cons<N, D>(m, UC);
+    // psi at both faces is >= 0 without evaluating it when their fractions
+    // are >= 0 and their pressures at least m.psi_floor: then psi(U^C) alone
+    // decides theta_lower's common case, and psi at the average is not needed
+    bool faces_ok = ge_floor(PL, m.psi_floor) && ge_floor(PR, m.psi_floor);
+#pragma unroll
+    for (int p = 0; p < N; p++) faces_ok = faces_ok && nonneg_num(aL[p]) && nonneg_num(aR[p]);
+    if (faces_ok && !has_sign(pC)) {
+      thpsi = 1.0;
+    } else {
+      const double pb = psi_prim<N, D>(m, Ub + I::A(0), Pb);
+      const double pL = psi_prim<N, D>(m, aL, PL);
+      const double pR = psi_prim<N, D>(m, aR, PR);
+      thpsi = theta_lower(pb, pC, pL, pR);
+    }
     if (lt_nonneg(thpsi, 1.0)) {
 #pragma unroll
       for (int v = 0; v < I::NV; v++) {

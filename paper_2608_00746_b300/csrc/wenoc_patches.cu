@@ -140,6 +140,7 @@ extern "C" wc_status wc_patches_init(const wc_patches_desc* desc, const int* edg
     m.Cmin[p] = m.A[p] * d.pmin[p] + m.B[p];
     if (d.D[p] != 0.0) m.hasD = 1;
   }
+  m.psi_floor = psi_face_floor(m);
   g->edge.assign(edges, edges + d.npatch);
   g->off.resize(d.npatch);
   long o = 0;
