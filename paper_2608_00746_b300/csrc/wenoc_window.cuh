@@ -122,8 +122,9 @@ __device__ __forceinline__ void update_cell(const SweepArgs& a, const Mat& m, lo
   const double du = (uh - uhl) * a.inv_dx;
   // Eq. 3: -div F + alpha (1 + K) div u_hat;  Eq. 5: +div F^PF
   const double sdx = a.kind == 1 ? a.inv_dx : -a.inv_dx;
-  double sf[N];
-  source_factors<N, D>(m, Ub, Pb, sf);
+  // (the source factors serve Eq. 3 only; Eq. 5 has no source term)
+  double sf[N] = {};
+  if (a.kind == 0) source_factors<N, D>(m, Ub, Pb, sf);
   const double r2dt = a.rk2 * dt;
 #pragma unroll
   for (int v = 0; v < NV; v++) {
@@ -143,6 +144,35 @@ __device__ __forceinline__ void update_cell(const SweepArgs& a, const Mat& m, lo
                                LW != 2 && (v < N || v >= I::A(0)), v >= I::A(0));
     }
   }
+}
+
+// update_cell for a cell of the Phase-Field step (kind 1) whose two faces
+// carry no flux (G_p = 0 for every phase on both): F = Fl = 0, so the value
+// of each variable is (0 - 0) a.inv_dx = 0 and the cell takes the same
+// stage combination as update_cell gives it, without its face states.  A
+// non-finite cell value is reported as update_cell reports it through the
+// faces it spoils.  Kept out of line: the hot sweep's code stays as small.
+template <int N, int D, int LW>
+__device__ __noinline__ unsigned update_cell_still(const SweepArgs& a, long cell, double dt) {
+  using I = Idx<N, D>;
+  unsigned bad = 0u;
+  const double r2dt = a.rk2 * dt;
+#pragma unroll 1
+  for (int v = 0; v < I::NV; v++) {
+    const long idx = (long)v * a.ncell + cell;
+    const double ub = __ldg(a.U + idx);
+    if (not_finite(ub)) bad |= ST_NAN;
+    if (a.mode == 0) {
+      a.L[idx] = 0.0;
+    } else if (a.mode == 1) {
+      a.L[idx] += 0.0;
+    } else {
+      const double Lt = a.mode == 2 ? a.L[idx] + 0.0 : 0.0;
+      a.Uout[idx] = rk_combine(a.rk0, a.U0[idx], a.rk1, ub, r2dt, Lt,
+                               LW != 2 && (v < N || v >= I::A(0)), v >= I::A(0));
+    }
+  }
+  return bad;
 }
 
 // One window: the warp's lanes form groups of G consecutive lanes (one group
@@ -193,6 +223,44 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
   const int c = c0 - 1 + j;
   double Ub[NV], Vtmp[NV];
   load_cons(c, Ub);
+  // Phase-Field step (kind 1): the gradients G_p at x_{c+1/2} from Q and the
+  // cell fractions on both sides.  A face with G_p = 0 for every phase carries
+  // no flux (Eq. 5 with R12's flux: every term has a factor max(G_p, 0) or
+  // min(G_p, 0)), so a window in which every face that an owned cell touches
+  // has G = 0 leaves those cells unchanged: its cells take the update of a
+  // zero flux (the face pass writes no faces, which the flux pass then does
+  // not read), and the reconstruction, limiter and flux are skipped.  Only
+  // the interface band and its neighbours carry a flux.  (Not with the face
+  // dump of wc_faces, which wants every face.)
+  if (a.kind == 1 && !a.faceL) {
+    bool flip;
+    const long cq =
+        base + (long)bc_index(ghost_clamp(c), a.n, a.bclo, a.bchi, flip) * a.stride;
+    bool loud = false;
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      const double q = __ldg(a.Q + (long)p * a.ncell + cq);
+      const double qn = __shfl_down_sync(0xffffffffu, q, 1);
+      const double an = __shfl_down_sync(0xffffffffu, Ub[I::A(p)], 1);
+      // (unlimited here: a limit |G| <= g > 0 keeps G = 0 where it is 0, and
+      // the face pass has no time step for it)
+      const double gq = pf_gradient(q, qn, Ub[I::A(p)], an, a.inv_dx, 0.0);
+      loud = loud || (dbits(gq) & 0x7FFFFFFFFFFFFFFFLL) != 0;
+    }
+    // (lane j - 1 holds the face x_{c-1/2})
+    const bool loud_left = __shfl_up_sync(0xffffffffu, (int)loud, 1) != 0;
+    // the cells whose face states this window provides: the updated ones
+    // (PART 0), or the owned ones with the boundary cells -1 and n (PART 1)
+    bool need = active && j >= 1 && j <= G - 2 && c < a.n;
+    if constexpr (PART == 1) need = need || (active && (c == -1 || c == a.n));
+    if (__ballot_sync(0xffffffffu, need && (loud || loud_left)) == 0u) {
+      if constexpr (PART == 0) {
+        if (need) bad |= update_cell_still<N, D, LW>(a, base + (long)c * a.stride, dt);
+      }
+      __syncwarp();
+      return;
+    }
+  }
   if (store) {
     store_slot(sb + j + 2, Ub, Vtmp);
     // the group's outer stencil cells: slots 0, 1, G + 2, G + 3
@@ -500,12 +568,10 @@ __global__ void __launch_bounds__(128) k_flux_win(SweepArgs a, Mat m) {
     const bool live = c <= a.n - 1;
     const int cc = live ? c : a.n - 1;  // lanes past the pencil's end: a copy, no update
     Face<N, D> fL, fR;
-    get_face<N, D, TF>(a, 0, tr, cc, fL);
-    get_face<N, D, TF>(a, 1, tr, cc + 1, fR);
     double F[NV], uh = 0.0;
     if (a.kind == 1) {
       double G[N];
-      bool flip;
+      bool flip, loud = false;
       const long cl = base + (long)bc_index(cc, a.n, a.bclo, a.bchi, flip) * a.stride;
       const long cr = base + (long)bc_index(cc + 1, a.n, a.bclo, a.bchi, flip) * a.stride;
 #pragma unroll
@@ -514,9 +580,21 @@ __global__ void __launch_bounds__(128) k_flux_win(SweepArgs a, Mat m) {
         G[p] = pf_gradient(__ldg(a.Q + (long)p * a.ncell + cl), __ldg(a.Q + (long)p * a.ncell + cr),
                            __ldg(a.U + o + cl), __ldg(a.U + o + cr), a.inv_dx,
                            a.gcoef > 0.0 ? a.gcoef / dt : a.gmax);
+        loud = loud || (dbits(G[p]) & 0x7FFFFFFFFFFFFFFFLL) != 0;
       }
-      pf_flux<N, D>(m, fL, fR, G, F);
+      // a face with G = 0 carries no flux; its face states, which the face
+      // pass did not write where every face near them has G = 0, are not read
+      if (loud) {
+        get_face<N, D, TF>(a, 0, tr, cc, fL);
+        get_face<N, D, TF>(a, 1, tr, cc + 1, fR);
+        pf_flux<N, D>(m, fL, fR, G, F);
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; v++) F[v] = 0.0;
+      }
     } else {
+      get_face<N, D, TF>(a, 0, tr, cc, fL);
+      get_face<N, D, TF>(a, 1, tr, cc + 1, fR);
       riemann<N, D, TF>(m, a.dir, a.hllc, fL, fR, F, uh);
     }
     double Fl[NV];
