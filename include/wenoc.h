@@ -124,21 +124,31 @@ long wc_ncell(const wc_grid *g);
 
 /* Device scratch that wc_rk_step needs: three state-sized FP64 buffers
  * (two Runge-Kutta stages and the direction accumulator) plus 256 bytes; for
- * WC_PREC_LEARNED one more buffer of 18 x ncell FP32 learned weights; and for
- * the reduced precisions (window schedule) the face buffer of the split
- * sweep, (2 NV + 1) x (n + 2) x ncell / n FP64 values for the direction with
- * the most (n = its cell count): the face pass of each direction stores the
+ * WC_PREC_LEARNED one more buffer of 18 x ncell FP32 learned weights; for the
+ * window schedule (seg = 0) of a 2-D or 3-D grid the primitive slots of a
+ * stage's input, (NV + 1) x ncell FP64 words (Eq. 27 once a stage for every
+ * cell, read by the stage's direction sweeps); and for the reduced
+ * precisions (window schedule) the face buffer of the split sweep,
+ * (2 NV + 1) x (n + 2) x ncell / n FP64 values for the direction with the
+ * most (n = its cell count): the face pass of each direction stores the
  * limited face states and the cells' pressures there for its flux pass. */
 size_t wc_workspace_bytes(const wc_grid *g);
 /* The face buffer's part of wc_workspace_bytes (0 in FP64).  It is
  * optional: a workspace of at least wc_workspace_bytes(g) minus this runs
  * the single-pass sweep instead (same results, bit for bit). */
 size_t wc_face_buffer_bytes(const wc_grid *g);
+/* The primitive slots' part of wc_workspace_bytes (0 for the segment
+ * schedule and for 1-D grids).  Optional too: a workspace of at least
+ * wc_workspace_bytes(g) minus this and minus wc_face_buffer_bytes(g) runs
+ * sweeps that convert their cells themselves (same results, bit for bit). */
+size_t wc_prim_buffer_bytes(const wc_grid *g);
 
 /* Binds the caller's device state array U_dev ([NV][ncell] FP64, advanced in
  * place by wc_rk_step) and a device workspace of wc_workspace_bytes(g) bytes
- * (256-byte aligned; at least wc_workspace_bytes(g) - wc_face_buffer_bytes(g),
- * which selects the single-pass sweep). */
+ * (256-byte aligned).  Smaller workspaces drop the optional parts: at least
+ * wc_workspace_bytes(g) - wc_face_buffer_bytes(g) keeps the primitive slots
+ * and runs the single-pass sweep; at least that minus
+ * wc_prim_buffer_bytes(g) runs without either; less is WC_ERR_ARG. */
 wc_status wc_set_state(wc_grid *g, double *U_dev, void *workspace_dev, size_t ws_bytes);
 
 /* Validates a state against the admissible set of Eq. 8 (the paper's
@@ -500,10 +510,13 @@ void wc_patches_last_error(const wc_patches *g, char *buf, size_t n);
 
 /* Sweep timing (tracing): after wc_sweep_timing_begin(g, max_launches) the
  * library records a CUDA event pair on the launch stream around each of the
- * next max_launches direction-sweep launches of g (events are created here,
- * no device memory is allocated).  wc_sweep_timing_read synchronises on the
- * last event and returns the number of timed launches, their summed and
- * largest durations in milliseconds, and stops the timing. */
+ * next max_launches direction-sweep launches of g and around the
+ * primitive-slot passes of their stages (events are created here, no device
+ * memory is allocated).  wc_sweep_timing_read synchronises on the last event
+ * and returns the number of timed sweeps, the summed durations of the sweeps
+ * and passes (so total / launches is a sweep with its share of its stage's
+ * pass) and the largest sweep duration, in milliseconds, and stops the
+ * timing. */
 wc_status wc_sweep_timing_begin(wc_grid *g, int max_launches);
 wc_status wc_sweep_timing_read(wc_grid *g, int *launches, double *total_ms, double *max_ms);
 

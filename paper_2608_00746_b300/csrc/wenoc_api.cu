@@ -37,13 +37,18 @@ struct wc_grid {
   float tau = 1e-4f;
   unsigned long long* lcount = nullptr;
   float* Wbuf = nullptr;
+  // window schedule: the primitive slots of a stage's input (in the
+  // workspace, after the learned weights); null: each sweep converts its cells
+  double* vbuf = nullptr;
   // reduced precision: the split sweep's face buffer (in the workspace,
-  // after the learned weights); null: the single-pass sweep
+  // after the primitive slots); null: the single-pass sweep
   double* fbuf = nullptr;
   char err[256];
   // sweep timing (wc_sweep_timing_begin / _read)
   std::vector<cudaEvent_t> tev;
-  int tmax = 0, tcount = 0;
+  std::vector<char> tprim;     // event pair k times a primitive-slot pass
+  int tmax = 0, tcount = 0;    // sweeps to time; event pairs used
+  int tsweeps = 0;             // sweeps timed
   // Phase-Field mechanism (wc_set_pf_workspace): scratch, geometry, the
   // auxiliary fields Q of the last wc_step, statistics of the last Q-map
   bool pf_bound = false;
@@ -185,19 +190,37 @@ static size_t face_buffer_bytes(const wc_grid* g) {
   return ((size_t)most * sizeof(double) + 255) / 256 * 256;
 }
 
-extern "C" size_t wc_workspace_bytes(const wc_grid* g) {
-  if (!g) return 0;
+// The primitive slots of the window schedule: Ring<N, D, double>::SLOTD = 1 +
+// NV words a cell (the FP64 slot; the reduced precision's is smaller, and a
+// learned grid's Phase-Field sweeps take FP64 slots).
+static size_t prim_buffer_bytes(const wc_grid* g) {
+  // (the segment schedule converts in its ring; a 1-D stage has one sweep,
+  // whose own conversions a separate pass would not save, only relaunch)
+  if (g->d.seg > 0 || g->d.dim == 1) return 0;
+  return ((size_t)(1 + g->nv) * g->ncell * sizeof(double) + 255) / 256 * 256;
+}
+// The part of the workspace every step needs: two stage buffers, the
+// direction accumulator, 256 bytes of words and the learned weights.
+static size_t base_workspace_bytes(const wc_grid* g) {
   size_t state = (size_t)g->nv * g->ncell * sizeof(double);
   state = (state + 255) / 256 * 256;
-  return 3 * state + 256 + learned_bytes(g) + face_buffer_bytes(g);
+  return 3 * state + 256 + learned_bytes(g);
 }
+
+extern "C" size_t wc_workspace_bytes(const wc_grid* g) {
+  if (!g) return 0;
+  return base_workspace_bytes(g) + prim_buffer_bytes(g) + face_buffer_bytes(g);
+}
+
+extern "C" size_t wc_prim_buffer_bytes(const wc_grid* g) { return g ? prim_buffer_bytes(g) : 0; }
 
 extern "C" size_t wc_face_buffer_bytes(const wc_grid* g) { return g ? face_buffer_bytes(g) : 0; }
 
 extern "C" wc_status wc_set_state(wc_grid* g, double* U_dev, void* ws, size_t ws_bytes) {
   if (!g || !U_dev) return WC_ERR_ARG;
   const bool with_faces = ws_bytes >= wc_workspace_bytes(g);
-  if (ws && ws_bytes < wc_workspace_bytes(g) - face_buffer_bytes(g))
+  const bool with_prim = ws_bytes >= base_workspace_bytes(g) + prim_buffer_bytes(g);
+  if (ws && ws_bytes < base_workspace_bytes(g))
     return fail(g, WC_ERR_ARG, "workspace too small");
   if (ws && (reinterpret_cast<uintptr_t>(ws) & 255)) return fail(g, WC_ERR_ARG, "workspace not 256-byte aligned");
   if (reinterpret_cast<uintptr_t>(U_dev) & 7) return fail(g, WC_ERR_ARG, "state not 8-byte aligned");
@@ -216,8 +239,11 @@ extern "C" wc_status wc_set_state(wc_grid* g, double* U_dev, void* ws, size_t ws
     g->status = (unsigned*)(tail + 16);
     g->ticket = (unsigned*)(tail + 32);
     g->Wbuf = g->d.precision == WC_PREC_LEARNED ? (float*)(tail + 256) : nullptr;
-    g->fbuf = face_buffer_bytes(g) && with_faces ? (double*)(tail + 256 + learned_bytes(g))
-                                                 : nullptr;
+    g->vbuf = prim_buffer_bytes(g) && with_prim ? (double*)(tail + 256 + learned_bytes(g))
+                                                : nullptr;
+    g->fbuf = face_buffer_bytes(g) && with_faces
+                  ? (double*)(tail + 256 + learned_bytes(g) + prim_buffer_bytes(g))
+                  : nullptr;
     // the workspace comes uninitialised: clear rate, dt and the status word
     cudaError_t e = cudaMemset(tail, 0, 256);
     if (e != cudaSuccess) return cuda_fail(g, e, "workspace clear");
@@ -228,6 +254,7 @@ extern "C" wc_status wc_set_state(wc_grid* g, double* U_dev, void* ws, size_t ws
     g->status = nullptr;
     g->ticket = nullptr;
     g->Wbuf = nullptr;
+    g->vbuf = nullptr;
     g->fbuf = nullptr;
   }
   return WC_OK;
@@ -391,7 +418,7 @@ static MlpGeom mlp_geom(const wc_grid* g, int dir, const double* U) {
 
 static cudaError_t launch(const wc_grid* gc, const SweepArgs& a0, cudaStream_t st) {
   wc_grid* g = const_cast<wc_grid*>(gc);
-  const bool timed = g->tcount < g->tmax;
+  const bool timed = g->tsweeps < g->tmax && g->tcount < 2 * g->tmax;
   if (timed) cudaEventRecord(g->tev[2 * g->tcount], st);
   cudaError_t e;
   SweepArgs a = a0;
@@ -415,21 +442,62 @@ static cudaError_t launch(const wc_grid* gc, const SweepArgs& a0, cudaStream_t s
     e = launch_sweep_fp64(g->d.nphase, g->d.dim, a, g->mat, sweep_block(g), st);
   if (timed) {
     cudaEventRecord(g->tev[2 * g->tcount + 1], st);
+    g->tprim[g->tcount] = 0;
     g->tcount++;
+    g->tsweeps++;
   }
   return e;
 }
 
+// The primitive slots of cells c0 .. c1 - 1 of U into the workspace, in the
+// format of the sweep that reads them (kind as in launch: the FP64 and
+// comparison sweeps, and a learned grid's Phase-Field sweeps, hold FP64
+// slots).  Returns the slots, or null when the workspace has none (the
+// sweeps then convert their cells themselves).
+static const double* launch_prim(wc_grid* g, const double* U, int kind, long c0, long c1,
+                                 cudaStream_t st, cudaError_t& e) {
+  e = cudaSuccess;
+  if (!g->vbuf || g->d.seg > 0) return nullptr;
+  const bool fp64 = g->d.precision == WC_PREC_FP64 || g->mat.cmp != CMP_NONE ||
+                    (g->d.precision == WC_PREC_LEARNED && kind == 1);
+  const int blocks = grid_blocks(c1 - c0, 256);
+  // (timed with the sweeps: their per-launch time includes each direction's
+  // share of the pass)
+  const bool timed = g->tsweeps < g->tmax && g->tcount < 2 * g->tmax;
+  if (timed) cudaEventRecord(g->tev[2 * g->tcount], st);
+  if (fp64) {
+    WC_DISPATCH(g->d.nphase, g->d.dim,
+                (k_prim_slots<N_, D_, double><<<blocks, 256,
+                                               256 * Ring<N_, D_, double>::SLOTD * 8, st>>>(
+                    U, g->vbuf, g->ncell, c0, c1, g->mat)));
+  } else {
+    WC_DISPATCH(g->d.nphase, g->d.dim,
+                (k_prim_slots<N_, D_, float><<<blocks, 256,
+                                              256 * Ring<N_, D_, float>::SLOTD * 8, st>>>(
+                    U, g->vbuf, g->ncell, c0, c1, g->mat)));
+  }
+  e = cudaGetLastError();
+  if (timed) {
+    cudaEventRecord(g->tev[2 * g->tcount + 1], st);
+    g->tprim[g->tcount] = 1;
+    g->tcount++;
+  }
+  return e == cudaSuccess ? g->vbuf : nullptr;
+}
+
 extern "C" wc_status wc_sweep_timing_begin(wc_grid* g, int max_launches) {
   if (!g || max_launches < 0 || max_launches > 100000) return WC_ERR_ARG;
-  while ((int)g->tev.size() < 2 * max_launches) {
+  // pairs for the sweeps and as many primitive-slot passes
+  while ((int)g->tev.size() < 4 * max_launches) {
     cudaEvent_t ev;
     cudaError_t e = cudaEventCreate(&ev);
     if (e != cudaSuccess) return cuda_fail(g, e, "event create");
     g->tev.push_back(ev);
   }
+  g->tprim.assign(2 * (size_t)max_launches, 0);
   g->tmax = max_launches;
   g->tcount = 0;
+  g->tsweeps = 0;
   return WC_OK;
 }
 
@@ -442,18 +510,23 @@ extern "C" wc_status wc_sweep_timing_read(wc_grid* g, int* launches, double* tot
     cudaError_t e = cudaEventSynchronize(g->tev[2 * n - 1]);
     if (e != cudaSuccess) return cuda_fail(g, e, "event sync");
   }
+  int sweeps = 0;
   for (int k = 0; k < n; k++) {
     float ms = 0.f;
     cudaError_t e = cudaEventElapsedTime(&ms, g->tev[2 * k], g->tev[2 * k + 1]);
     if (e != cudaSuccess) return cuda_fail(g, e, "event time");
     tot += ms;
-    if (ms > mx) mx = ms;
+    if (!g->tprim[k]) {
+      sweeps++;
+      if (ms > mx) mx = ms;
+    }
   }
-  if (launches) *launches = n;
+  if (launches) *launches = sweeps;
   if (total_ms) *total_ms = tot;
   if (max_ms) *max_ms = mx;
   g->tmax = 0;
   g->tcount = 0;
+  g->tsweeps = 0;
   return WC_OK;
 }
 
@@ -462,10 +535,14 @@ extern "C" wc_status wc_rhs(wc_grid* g, const double* U, double* L, void* stream
   if (!g->status) return fail(g, WC_ERR_STATE, "wc_rhs needs a bound workspace (status word)");
   if (g->d.precision == WC_PREC_LEARNED && !g->mlp)
     return fail(g, WC_ERR_STATE, "learned precision needs wc_set_mlp");
+  cudaError_t e;
+  const double* Vs = launch_prim(g, U, 0, 0, g->ncell, S(stream), e);
+  if (e != cudaSuccess) return cuda_fail(g, e, "primitive slots");
   for (int dir = 0; dir < g->d.dim; dir++) {
     SweepArgs a = make_args(g, dir, U, L);
     a.mode = dir == 0 ? 0 : 1;
-    cudaError_t e = launch(g, a, S(stream));
+    a.Vs = Vs;
+    e = launch(g, a, S(stream));
     if (e != cudaSuccess) return cuda_fail(g, e, "sweep");
   }
   return WC_OK;
@@ -492,9 +569,13 @@ extern "C" wc_status wc_rhs_pf(wc_grid* g, const double* U, const double* Q, dou
                                double* L, void* stream) {
   if (!g || !U || !Q || !L || dt_limit < 0.0) return WC_ERR_ARG;
   if (!g->status) return fail(g, WC_ERR_STATE, "wc_rhs_pf needs a bound workspace (status word)");
+  cudaError_t e0;
+  const double* Vs = launch_prim(g, U, 1, 0, g->ncell, S(stream), e0);
+  if (e0 != cudaSuccess) return cuda_fail(g, e0, "primitive slots");
   for (int dir = 0; dir < g->d.dim; dir++) {
     SweepArgs a = make_args(g, dir, U, L);
     a.mode = dir == 0 ? 0 : 1;
+    a.Vs = Vs;
     a.kind = 1;
     a.Q = Q;
     a.gmax = dt_limit > 0.0 ? g->d.dx[dir] / (12.0 * g->d.dim * dt_limit) : 0.0;
@@ -567,9 +648,19 @@ static wc_status stage(wc_grid* g, const double* src, double* dst, double r0, do
   // download takes y first, so that the banded sweep runs over rows (x
   // pencils, contiguous in every field): L_y + L_x is L_x + L_y bit for bit
   const bool swap = hb && hb->done && D == 2;
+  // the primitive slots of src, once for the stage's directions (after the
+  // banded first direction when the upload is still arriving)
+  const double* Vs = nullptr;
+  const bool banded_up = hb && hb->up;
+  if (!banded_up) {
+    cudaError_t e;
+    Vs = launch_prim(g, src, kind, 0, g->ncell, st, e);
+    if (e != cudaSuccess) return cuda_fail(g, e, "primitive slots");
+  }
   for (int k = 0; k < D; k++) {
     const int dir = swap ? 1 - k : k;
     SweepArgs a = make_args(g, dir, src, g->Lacc);
+    a.Vs = Vs;
     if (kind == 1) {
       a.kind = 1;
       a.Q = Q;
@@ -608,10 +699,15 @@ static wc_status stage(wc_grid* g, const double* src, double* dst, double r0, do
       if (e != cudaSuccess) return cuda_fail(g, e, "band sweep");
     }
     // the first direction (mode 0) needs no time step; the others take it
-    // from the state, now uploaded in full
+    // from the state, now uploaded in full, and its primitive slots
     if (up && !(dt_fixed > 0.0)) {
       wc_status r = launch_rate(g, g->U, st);
       if (r) return r;
+    }
+    if (up) {
+      cudaError_t e;
+      Vs = launch_prim(g, src, kind, 0, g->ncell, st, e);
+      if (e != cudaSuccess) return cuda_fail(g, e, "primitive slots");
     }
   }
   return WC_OK;
@@ -1123,9 +1219,10 @@ wc_status wc_internal_rk_with_scratch(wc_grid* g, double* U, char* scratch, doub
   // save and restore only the bindings (the grid also owns timing events)
   struct Bind {
     double* U; char* ws; size_t ws_bytes; double *B1, *B2, *Lacc;
-    unsigned long long* rate; double* dt; unsigned* status; unsigned* ticket; double* fbuf;
-  } saved{g->U,    g->ws, g->ws_bytes, g->B1,     g->B2,     g->Lacc,
-          g->rate, g->dt, g->status,   g->ticket, g->fbuf};
+    unsigned long long* rate; double* dt; unsigned* status; unsigned* ticket; double* vbuf;
+    double* fbuf;
+  } saved{g->U,    g->ws, g->ws_bytes, g->B1,     g->B2,   g->Lacc,
+          g->rate, g->dt, g->status,   g->ticket, g->vbuf, g->fbuf};
   size_t state = (size_t)g->nv * g->ncell * sizeof(double);
   state = (state + 255) / 256 * 256;
   char* tail = scratch + 3 * state;
@@ -1141,6 +1238,7 @@ wc_status wc_internal_rk_with_scratch(wc_grid* g, double* U, char* scratch, doub
   g->dt = (double*)(tail + 8);
   g->status = (unsigned*)(tail + 16);
   g->ticket = (unsigned*)(tail + 32);
+  g->vbuf = nullptr;  // the sweeps convert their cells (no primitive slots in the scratch)
   g->fbuf = nullptr;  // the single-pass sweep (no face buffer in the scratch)
   wc_status r = wc_rk_step(g, cfl, dt_fixed, nsteps, nullptr, reinterpret_cast<void*>(st));
   if (status_out) *status_out = g->status;
@@ -1154,6 +1252,7 @@ wc_status wc_internal_rk_with_scratch(wc_grid* g, double* U, char* scratch, doub
   g->dt = saved.dt;
   g->status = saved.status;
   g->ticket = saved.ticket;
+  g->vbuf = saved.vbuf;
   g->fbuf = saved.fbuf;
   return r;
 }

@@ -81,6 +81,11 @@ struct SweepArgs {
   // starts the first sweep on the rows already uploaded and returns the
   // last sweep's bands while the next ones run
   long tr0;
+  // primitive slots of the state U (window schedule; null: each sweep
+  // converts its cells itself): the put_slot image of every cell, word k of
+  // cell c at Vs[k ncell + c], written once a stage by k_prim_slots and
+  // copied by the sweeps of its directions
+  const double* Vs;
 };
 
 // First cell of pencil tr of a direction sweep (x fastest; for dir 1 the
@@ -165,6 +170,41 @@ __device__ __forceinline__ void put_slot(double* sl, const double* v) {
 #pragma unroll
     for (int q = 0; q <= D; q++) Vs[I::NV + q] = cvt<T>(v[N + q] - wide(Vs[N + q]));
   }
+}
+
+// The primitive slots of cells c0 .. c1 - 1 of U (Eq. 27 and put_slot, the
+// same steps the sweeps take): word k of cell c to Vs[k ncell + c], through
+// the thread's part of shared memory.  One pass a Runge-Kutta stage with
+// every lane converting, where each direction sweep converted its cells and
+// with four lanes of a warp the two stencil cells beyond each end of a
+// window.
+template <int N, int D, typename T>
+__global__ void __launch_bounds__(256) k_prim_slots(const double* __restrict__ U,
+                                                    double* __restrict__ Vs, long ncell, long c0,
+                                                    long c1, Mat m) {
+  using I = Idx<N, D>;
+  constexpr int SLOTD = Ring<N, D, T>::SLOTD;
+  extern __shared__ double psl[];
+  double* sl = psl + threadIdx.x * SLOTD;
+  for (long c = c0 + (long)blockIdx.x * blockDim.x + threadIdx.x; c < c1;
+       c += (long)gridDim.x * blockDim.x) {
+    double u[I::NV], v[I::NV];
+#pragma unroll
+    for (int k = 0; k < I::NV; k++) u[k] = __ldg(U + (long)k * ncell + c);
+    cons_to_prim<N, D>(m, u, v);
+    put_slot<N, D, T>(sl, v);
+#pragma unroll
+    for (int k = 0; k < SLOTD; k++) Vs[(long)k * ncell + c] = sl[k];
+  }
+}
+
+// A slot copied from the primitive slots of cell `cell` (a cell of the
+// grid, not a mirrored boundary image: the sweep converts those itself).
+template <int N, int D, typename T>
+__device__ __forceinline__ void copy_slot(const SweepArgs& a, long cell, double* sl) {
+  constexpr int SLOTD = Ring<N, D, T>::SLOTD;
+#pragma unroll
+  for (int k = 0; k < SLOTD; k++) sl[k] = __ldg(a.Vs + (long)k * a.ncell + cell);
 }
 
 // face_velocity_pressure with the loop over the variables not unrolled (one

@@ -261,7 +261,31 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
       return;
     }
   }
-  if (store) {
+  if (store && a.Vs) {
+    // the slots from the stage's primitive slots; a mirrored boundary image
+    // (reflective side) is converted here from its flipped state
+    auto fill_slot = [&](int s, int cc, const double* u0) {
+      bool flip;
+      const int jj = bc_index(ghost_clamp(cc), a.n, a.bclo, a.bchi, flip);
+      if (!flip) {
+        copy_slot<N, D, T>(a, base + (long)jj * a.stride, slots + s * SLOTD);
+      } else {
+        double u[NV], v[NV];
+        if (u0) {
+#pragma unroll
+          for (int k = 0; k < NV; k++) u[k] = u0[k];
+        } else {
+          load_cons(cc, u);
+        }
+        store_slot(s, u, v);
+      }
+    };
+    fill_slot(sb + j + 2, c, Ub);
+    for (int e = j; e < 4; e += G) {
+      const int s = e < 2 ? e : G + e;
+      fill_slot(sb + s, c0 - 3 + s, nullptr);
+    }
+  } else if (store) {
     store_slot(sb + j + 2, Ub, Vtmp);
     // the group's outer stencil cells: slots 0, 1, G + 2, G + 3
     for (int e = j; e < 4; e += G) {

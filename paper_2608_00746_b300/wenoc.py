@@ -91,6 +91,7 @@ _SIGS = {
     "wc_ncell": (ctypes.c_long, [_VP]),
     "wc_workspace_bytes": (ctypes.c_size_t, [_VP]),
     "wc_face_buffer_bytes": (ctypes.c_size_t, [_VP]),
+    "wc_prim_buffer_bytes": (ctypes.c_size_t, [_VP]),
     "wc_set_state": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_size_t]),
     "wc_check_state": (ctypes.c_int, [_VP, _VP, ctypes.c_double, ctypes.POINTER(ctypes.c_long),
                                       ctypes.POINTER(ctypes.c_long), _VP]),
@@ -272,12 +273,15 @@ class Grid:
     def workspace_bytes(self):
         return lib().wc_workspace_bytes(self.h)
 
-    def new_workspace(self, device="cuda", faces=True):
+    def new_workspace(self, device="cuda", faces=True, prim=True):
         """A workspace tensor; faces=False leaves out the split sweep's face
-        buffer (the single-pass sweep runs then)."""
+        buffer (the single-pass sweep runs then), and with it prim=False the
+        primitive slots (each sweep converts its cells then)."""
         nb = self.workspace_bytes()
         if not faces:
             nb -= lib().wc_face_buffer_bytes(self.h)
+            if not prim:
+                nb -= lib().wc_prim_buffer_bytes(self.h)
         return torch.empty((nb + 7) // 8, dtype=torch.float64, device=device)
 
     def bind(self, U, workspace=None, validate=False, sum_tol=1e-10):

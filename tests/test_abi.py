@@ -72,6 +72,32 @@ def test_init_grid_accepts_valid_and_sizes():
     L.wc_destroy(h)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("seg", [0, 14])
+def test_workspace_parts(precision, seg):
+    """The workspace: three state buffers and 256 bytes, then the primitive
+    slots of the window schedule ((NV + 1) words a cell, none for the
+    segment schedule or a 1-D grid), then the reduced precision's face
+    buffer; each part rounded to 256 bytes."""
+    d = desc(precision=precision)
+    d.seg = seg
+    h = ctypes.c_void_p()
+    L = wenoc.lib()
+    assert L.wc_init_grid(ctypes.byref(d), ctypes.byref(h)) == 0
+    up = lambda b: (b + 255) // 256 * 256  # noqa: E731
+    nv, nc = 7, 128
+    prim = 0 if seg else up((nv + 1) * nc * 8)
+    assert L.wc_prim_buffer_bytes(h) == prim
+    face = L.wc_face_buffer_bytes(h)
+    assert (face > 0) == (precision == 1 and seg == 0)
+    assert L.wc_workspace_bytes(h) == 3 * up(nv * nc * 8) + 256 + prim + face
+    L.wc_destroy(h)
+    d1 = desc(precision=precision, dim=1, n=(128, 1, 1), nphase=2)
+    assert L.wc_init_grid(ctypes.byref(d1), ctypes.byref(h)) == 0
+    assert L.wc_prim_buffer_bytes(h) == 0
+    L.wc_destroy(h)
+
+
 @pytest.mark.parametrize("bad,status", [
     (dict(dim=4), 1), (dict(nphase=0), 5), (dict(nphase=6), 5),
     (dict(n=(2, 8, 1)), 1), (dict(n=(16, 8, 2)), 1), (dict(flux=7), 1),
