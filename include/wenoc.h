@@ -471,11 +471,16 @@ size_t wc_patches_workspace_bytes(const wc_patches *g);
  * face states of the largest group of equal patches, (2 NV + 1) e^2 (e + 2)
  * doubles a patch of edge e. */
 size_t wc_patches_face_buffer_bytes(const wc_patches *g);
+/* The part that holds the primitive slots of a stage's input for the window
+ * schedule ((NV + 1) FP64 words a pooled cell; see wc_prim_buffer_bytes). */
+size_t wc_patches_prim_buffer_bytes(const wc_patches *g);
 /* Binds the pooled device state and workspace (256-byte aligned), uploads
  * the patch table on stream and synchronises it.  A workspace of at least
  * wc_patches_workspace_bytes - wc_patches_face_buffer_bytes is accepted:
  * without the face buffer the window schedule's mixed-precision sweep runs
- * in one pass (the same results, bit for bit); below that, WC_ERR_ARG. */
+ * in one pass, and with less than that minus wc_patches_prim_buffer_bytes
+ * too the window sweeps convert their cells themselves (the same results,
+ * bit for bit); below that, WC_ERR_ARG. */
 wc_status wc_patches_set_state(wc_patches *g, double *U_dev, void *workspace_dev,
                                size_t ws_bytes, void *stream);
 /* Schedule: threads per CTA (32/64/96/128), CTAs per SM (1..16), and the

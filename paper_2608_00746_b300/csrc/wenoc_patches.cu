@@ -82,6 +82,7 @@ struct wc_patches {
   long* d_off = nullptr;
   int* d_order = nullptr;
   long* d_gpoff = nullptr;
+  double* vbuf = nullptr;    // primitive slots of a stage's input (window schedule)
   double* fbuf = nullptr;    // face buffer of the split window sweep (mixed)
   unsigned* d_ticket = nullptr;  // window queue (next window, warps finished)
   int* d_counter = nullptr;  // 3 queue heads (one per stage)
@@ -196,6 +197,12 @@ static size_t face_buffer_bytes(const wc_patches* g) {
   return round256((size_t)most * sizeof(double));
 }
 
+// The primitive slots of the window schedule: 1 + NV words a cell (the FP64
+// slot; the mixed precision's is smaller).
+static size_t prim_buffer_bytes(const wc_patches* g) {
+  return round256((size_t)(1 + g->nv) * g->ncell * sizeof(double));
+}
+
 static size_t base_bytes(const wc_patches* g) {
   size_t state = round256((size_t)g->nv * g->ncell * sizeof(double));
   return 4 * state + table_bytes(g);
@@ -205,9 +212,13 @@ extern "C" size_t wc_patches_face_buffer_bytes(const wc_patches* g) {
   return g ? face_buffer_bytes(g) : 0;
 }
 
+extern "C" size_t wc_patches_prim_buffer_bytes(const wc_patches* g) {
+  return g ? prim_buffer_bytes(g) : 0;
+}
+
 extern "C" size_t wc_patches_workspace_bytes(const wc_patches* g) {
   if (!g) return 0;
-  return base_bytes(g) + face_buffer_bytes(g);
+  return base_bytes(g) + prim_buffer_bytes(g) + face_buffer_bytes(g);
 }
 
 extern "C" wc_status wc_patches_set_state(wc_patches* g, double* U_dev, void* ws, size_t bytes,
@@ -237,9 +248,12 @@ extern "C" wc_status wc_patches_set_state(wc_patches* g, double* U_dev, void* ws
   g->d_rate = (unsigned long long*)(t + 64);
   g->d_status = (unsigned*)(t + 128);
   g->d_ticket = (unsigned*)(t + 192);     // 2 unsigned
-  // without room for the face buffer the mixed window sweep runs in one pass
+  // without room for the primitive slots the window sweeps convert their
+  // cells themselves; without the face buffer the mixed one runs in one pass
+  g->vbuf = bytes >= base_bytes(g) + prim_buffer_bytes(g) ? (double*)(g->ws + base_bytes(g))
+                                                          : nullptr;
   g->fbuf = bytes >= wc_patches_workspace_bytes(g) && face_buffer_bytes(g)
-                ? (double*)(g->ws + base_bytes(g))
+                ? (double*)(g->ws + base_bytes(g) + prim_buffer_bytes(g))
                 : nullptr;
   cudaStream_t st = PS(stream);
   cudaError_t e = cudaMemcpyAsync(g->d_edge, g->edge.data(), np * sizeof(int),
@@ -315,10 +329,39 @@ static int patch_grid(const wc_patches* g) { return 148 * g->ctas_per_sm; }
 // flux pass when the workspace holds the face buffer.  Directions run in
 // order over all patches, so the accumulator modes are those of a grid:
 // L = x part, L += y part, then the stage (or L += z part for the rhs).
+template <typename T>
+static cudaError_t launch_prim_patches(const wc_patches* g, const double* src, cudaStream_t st) {
+  long b = (g->ncell + 255) / 256;
+  if (b > 148L * 64) b = 148L * 64;
+  const int blocks = (int)(b < 1 ? 1 : b);
+  switch (g->d.nphase) {
+#define WC_PRIM_CASE(NP)                                                                   \
+  case NP:                                                                                 \
+    k_prim_slots<NP, 3, T><<<blocks, 256, 256 * Ring<NP, 3, T>::SLOTD * 8, st>>>(          \
+        src, g->vbuf, g->ncell, 0, g->ncell, g->mat);                                      \
+    break;
+    WC_PRIM_CASE(1)
+    WC_PRIM_CASE(2)
+    WC_PRIM_CASE(3)
+    WC_PRIM_CASE(4)
+    WC_PRIM_CASE(5)
+#undef WC_PRIM_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 static cudaError_t enqueue_windows(wc_patches* g, const double* src, double* dst, double* L,
                                    double r0, double r1, double r2, double cfl, double dt,
                                    int rhs_only, cudaStream_t st) {
   const int mixed = g->d.precision == WC_PREC_MIXED;
+  // the primitive slots of src, once for the stage's three directions
+  if (g->vbuf) {
+    const cudaError_t e = mixed ? launch_prim_patches<float>(g, src, st)
+                                : launch_prim_patches<double>(g, src, st);
+    if (e != cudaSuccess) return e;
+  }
   for (int dir = 0; dir < 3; dir++) {
     for (const PatchGroup& gr : g->groups) {
       SweepArgs a;
@@ -355,6 +398,7 @@ static cudaError_t enqueue_windows(wc_patches* g, const double* src, double* dst
       a.energy_limiter = g->d.energy_limiter;
       a.status = g->d_status;
       a.poff = g->d_gpoff + gr.first;
+      a.Vs = g->vbuf;
       a.fbuf = mixed ? g->fbuf : nullptr;
       cudaError_t e = mixed ? launch_sweep_mixed(g->d.nphase, 3, a, g->mat, g->block, st)
                             : launch_sweep_fp64(g->d.nphase, 3, a, g->mat, g->block, st);

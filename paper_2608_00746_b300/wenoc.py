@@ -92,6 +92,7 @@ _SIGS = {
     "wc_workspace_bytes": (ctypes.c_size_t, [_VP]),
     "wc_face_buffer_bytes": (ctypes.c_size_t, [_VP]),
     "wc_prim_buffer_bytes": (ctypes.c_size_t, [_VP]),
+    "wc_patches_prim_buffer_bytes": (ctypes.c_size_t, [_VP]),
     "wc_set_state": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_size_t]),
     "wc_check_state": (ctypes.c_int, [_VP, _VP, ctypes.c_double, ctypes.POINTER(ctypes.c_long),
                                       ctypes.POINTER(ctypes.c_long), _VP]),
@@ -586,13 +587,16 @@ class Patches:
         o = self.offsets[p]
         return pooled[:, o:o + e ** 3].reshape(self.nv, e, e, e)
 
-    def bind(self, U, stream=None, faces=True):
+    def bind(self, U, stream=None, faces=True, prim=True):
         """Binds the pooled state with a new workspace; faces=False leaves out
         the face buffer (the window schedule's mixed sweep then runs in one
-        pass)."""
+        pass), and with it prim=False the primitive slots (the window sweeps
+        convert their cells then)."""
         b = lib().wc_patches_workspace_bytes(self.h)
         if not faces:
             b -= lib().wc_patches_face_buffer_bytes(self.h)
+            if not prim:
+                b -= lib().wc_patches_prim_buffer_bytes(self.h)
         n = (b + 7) // 8
         self.ws = torch.empty(n, dtype=torch.float64, device=U.device)
         self.U = U

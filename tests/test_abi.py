@@ -184,8 +184,11 @@ def test_patches_init_tables_and_workspace():
         most = max(edges.count(e) * (2 * nv + 1) * e * e * (e + 2) for e in set(edges))
         fb = L.wc_patches_face_buffer_bytes(h)
         assert most * 8 <= fb < most * 8 + 256
-        state = (nv * sum(e ** 3 for e in edges) * 8 + 255) // 256 * 256
-        assert L.wc_patches_workspace_bytes(h) >= 4 * state + fb
+        nc = sum(e ** 3 for e in edges)
+        state = (nv * nc * 8 + 255) // 256 * 256
+        prim = L.wc_patches_prim_buffer_bytes(h)
+        assert prim == ((nv + 1) * nc * 8 + 255) // 256 * 256
+        assert L.wc_patches_workspace_bytes(h) >= 4 * state + prim + fb
     finally:
         L.wc_patches_destroy(h)
     st, h = pinit(pdesc(precision=0), edges)

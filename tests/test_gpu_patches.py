@@ -185,8 +185,8 @@ def test_patch_window_schedule_fp64_parity(gpu):
     """The window schedule (kind 2: per direction, the grids' window sweep
     over the pencils of each group of equal patches) against the oracle on
     every patch: rhs, an SSP-RK3 step at a given dt and at the device's CFL
-    dt, at 1e-12; direct launches, graph replay and two block shapes bit for
-    bit the same."""
+    dt, at 1e-12; direct launches, graph replay, two block shapes and a
+    workspace without the primitive slots bit for bit the same."""
     edges, states, (g, pi, Dm) = inputs.patch_batch(npatch=24, seed=17, edges=WIN_EDGES)
     edges = [int(e) for e in edges]
     assert set(edges) == set(WIN_EDGES)
@@ -206,17 +206,20 @@ def test_patch_window_schedule_fp64_parity(gpu):
     dt = 0.2 / rate
     outs = []
     s = torch.cuda.Stream()
-    for sched, graph, kw in [((128, 3, 2), False, {"dt": dt}), ((64, 4, 2), False, {"dt": dt}),
-                             ((128, 2, 2), True, {"dt": dt}), ((128, 3, 2), True, {"cfl": 0.2})]:
+    for sched, graph, kw, prim in [((128, 3, 2), False, {"dt": dt}, True),
+                                   ((64, 4, 2), False, {"dt": dt}, True),
+                                   ((128, 2, 2), True, {"dt": dt}, True),
+                                   ((128, 3, 2), True, {"cfl": 0.2}, True),
+                                   ((128, 3, 2), False, {"dt": dt}, False)]:
         Uw = to_dev(U)
         with torch.cuda.stream(s):
-            P.bind(Uw, stream=s)
+            P.bind(Uw, stream=s, faces=prim, prim=prim)
             P.set_schedule(*sched)
             P.rk_step(nsteps=1, use_graph=graph, stream=s, **kw)
         s.synchronize()
         P.sync_status(stream=s)
         outs.append(Uw.cpu().numpy())
-    for k in (1, 2):
+    for k in (1, 2, 4):
         assert np.array_equal(outs[0], outs[k]), k
     for U1 in (outs[0], outs[3]):
         for p, (go, Up) in enumerate(zip(grids, Us)):
@@ -227,8 +230,9 @@ def test_patch_window_schedule_fp64_parity(gpu):
 
 def test_patch_window_schedule_mixed(gpu):
     """Mixed precision on the window schedule: the split sweep (face buffer in
-    the workspace) and the one-pass sweep (workspace without it) give the
-    same bits; five steps stay within the L1 bound of the FP64 patches with
+    the workspace), the one-pass sweep (workspace without it) and the
+    one-pass sweep converting its cells itself (no primitive slots either)
+    give the same bits; five steps stay within the L1 bound of the FP64 patches with
     masses >= 0 and fractions in [0, 1] (exactly, at cell averages); the
     persistent schedule's mixed sweep meets the same bound."""
     edges, states, (g, pi, Dm) = inputs.patch_batch(npatch=16, seed=19, edges=WIN_EDGES)
@@ -241,16 +245,16 @@ def test_patch_window_schedule_mixed(gpu):
     A = to_dev(U)
     P64.bind(A)
     outs = []
-    for faces in (True, False):
+    for faces, prim in ((True, True), (False, True), (False, False)):
         B = to_dev(U)
-        Pmx.bind(B, faces=faces)
+        Pmx.bind(B, faces=faces, prim=prim)
         Pmx.set_schedule(128, 3, 2)
         for _ in range(5):
             Pmx.rk_step(dt=2e-7)
         torch.cuda.synchronize()
         Pmx.sync_status()
         outs.append(B.cpu().numpy())
-    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
     for _ in range(5):
         P64.rk_step(dt=2e-7)
     torch.cuda.synchronize()
