@@ -463,11 +463,17 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
 // Persistent launch: every warp takes windows (pencil fastest, so warps that
 // run together read neighbouring pencils) from the queue a.ticket[0] until
 // it is empty; the last warp to leave resets the queue for the next launch.
+// Minimum resident blocks for the register budget: the FP64 sweep is left
+// to the compiler (142 registers for N = 3, three blocks an SM; a cap costs
+// spills for under 1 %); the reduced precisions' sweeps are held to 128
+// registers, four blocks (16 warps) an SM, spilling 16-64 bytes a thread:
+// the face pass of the 2048^2 N = 3 circles keeps its FP64 pipe busier
+// (mixed step 18.24 -> 17.73 ms; 192^3 3-D spheres 57.5 -> 55.1 ms).
 #ifndef WC_WIN_MINB64
 #define WC_WIN_MINB64 1
 #endif
 #ifndef WC_WIN_MINB32
-#define WC_WIN_MINB32 1
+#define WC_WIN_MINB32 4
 #endif
 template <int N, int D, typename T, typename TF, int LW = 0, int PART = 0>
 __global__ void __launch_bounds__(128, sizeof(T) == 8 ? WC_WIN_MINB64 : WC_WIN_MINB32)
