@@ -2,8 +2,10 @@
 // takes a window of 32 consecutive cells of one pencil from a dynamic queue,
 // reconstructs and limits all 32 (Eq. 15-21), solves the Riemann problems at
 // the 31 faces between them with the neighbour's face state from a warp
-// shuffle, and updates the 30 inner cells.  The two stencil cells beyond
-// each end come from four extra conversions.  Windows are handed out one
+// shuffle, and updates the 30 inner cells.  The primitive states of the 32
+// cells and of the two stencil cells beyond each end are copied from the
+// stage's primitive slots (k_prim_slots), or, without them, converted here
+// (four extra conversions for the outer cells).  Windows are handed out one
 // at a time (an atomic ticket per warp), so warps that meet cheap cells take
 // more windows: the cost of the limiter branches, clustered in space, no
 // longer sets the time of whole SMs.
