@@ -453,11 +453,15 @@ static cudaError_t launch(const wc_grid* gc, const SweepArgs& a0, cudaStream_t s
 // format of the sweep that reads them (kind as in launch: the FP64 and
 // comparison sweeps, and a learned grid's Phase-Field sweeps, hold FP64
 // slots).  Returns the slots, or null when the workspace has none (the
-// sweeps then convert their cells themselves).
+// sweeps then convert their cells themselves).  rate: the pass also reduces
+// the CFL rate of U into g->rate (cleared by the caller), as k_max_rate does.
 static const double* launch_prim(wc_grid* g, const double* U, int kind, long c0, long c1,
-                                 cudaStream_t st, cudaError_t& e) {
+                                 cudaStream_t st, cudaError_t& e, bool rate = false) {
   e = cudaSuccess;
   if (!g->vbuf || g->d.seg > 0) return nullptr;
+  const double i0 = 1.0 / g->d.dx[0];
+  const double i1 = g->d.dim > 1 ? 1.0 / g->d.dx[1] : 0.0;
+  const double i2 = g->d.dim > 2 ? 1.0 / g->d.dx[2] : 0.0;
   const bool fp64 = g->d.precision == WC_PREC_FP64 || g->mat.cmp != CMP_NONE ||
                     (g->d.precision == WC_PREC_LEARNED && kind == 1);
   const int blocks = grid_blocks(c1 - c0, 256);
@@ -465,11 +469,21 @@ static const double* launch_prim(wc_grid* g, const double* U, int kind, long c0,
   // share of the pass)
   const bool timed = g->tsweeps < g->tmax && g->tcount < 2 * g->tmax;
   if (timed) cudaEventRecord(g->tev[2 * g->tcount], st);
-  if (fp64) {
+  if (fp64 && rate) {
+    WC_DISPATCH(g->d.nphase, g->d.dim,
+                (k_prim_slots<N_, D_, double, true>
+                 <<<blocks, 256, 256 * Ring<N_, D_, double>::SLOTD * 8, st>>>(
+                     U, g->vbuf, g->ncell, c0, c1, g->mat, i0, i1, i2, g->rate, g->status)));
+  } else if (fp64) {
     WC_DISPATCH(g->d.nphase, g->d.dim,
                 (k_prim_slots<N_, D_, double><<<blocks, 256,
                                                256 * Ring<N_, D_, double>::SLOTD * 8, st>>>(
                     U, g->vbuf, g->ncell, c0, c1, g->mat)));
+  } else if (rate) {
+    WC_DISPATCH(g->d.nphase, g->d.dim,
+                (k_prim_slots<N_, D_, float, true>
+                 <<<blocks, 256, 256 * Ring<N_, D_, float>::SLOTD * 8, st>>>(
+                     U, g->vbuf, g->ncell, c0, c1, g->mat, i0, i1, i2, g->rate, g->status)));
   } else {
     WC_DISPATCH(g->d.nphase, g->d.dim,
                 (k_prim_slots<N_, D_, float><<<blocks, 256,
@@ -585,6 +599,11 @@ extern "C" wc_status wc_rhs_pf(wc_grid* g, const double* U, const double* Q, dou
   return WC_OK;
 }
 
+static wc_status clear_rate(wc_grid* g, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(g->rate, 0, sizeof(unsigned long long), st);
+  return e == cudaSuccess ? WC_OK : cuda_fail(g, e, "memset");
+}
+
 static wc_status launch_rate(wc_grid* g, const double* U, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(g->rate, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return cuda_fail(g, e, "memset");
@@ -642,7 +661,8 @@ static void band_range(long np, int nb, int b, int small, long& t0, long& t1) {
 // dx / (12 d dt), reading R17).
 static wc_status stage(wc_grid* g, const double* src, double* dst, double r0, double r1,
                        double r2, double cfl, double dt_fixed, cudaStream_t st, int kind = 0,
-                       const double* Q = nullptr, const HostBands* hb = nullptr) {
+                       const double* Q = nullptr, const HostBands* hb = nullptr,
+                       bool rate = false) {
   int D = g->d.dim;
   // directions x, y, z; a 2-D stage whose last sweep is banded for the
   // download takes y first, so that the banded sweep runs over rows (x
@@ -654,7 +674,7 @@ static wc_status stage(wc_grid* g, const double* src, double* dst, double r0, do
   const bool banded_up = hb && hb->up;
   if (!banded_up) {
     cudaError_t e;
-    Vs = launch_prim(g, src, kind, 0, g->ncell, st, e);
+    Vs = launch_prim(g, src, kind, 0, g->ncell, st, e, rate);
     if (e != cudaSuccess) return cuda_fail(g, e, "primitive slots");
   }
   for (int k = 0; k < D; k++) {
@@ -721,13 +741,18 @@ extern "C" wc_status wc_rk_step(wc_grid* g, double cfl, double dt_fixed, int nst
   if (g->d.precision == WC_PREC_LEARNED && !g->mlp)
     return fail(g, WC_ERR_STATE, "learned precision needs wc_set_mlp");
   cudaStream_t st = S(stream);
+  // the CFL rate of U^n: in the first stage's primitive-slot pass when the
+  // workspace holds the slots (the state is read and converted once), else
+  // by k_max_rate
+  const bool fuse = !(dt_fixed > 0.0) && g->vbuf;
   for (int s = 0; s < nsteps; s++) {
     if (!(dt_fixed > 0.0)) {
-      wc_status r = launch_rate(g, g->U, st);
+      wc_status r = fuse ? clear_rate(g, st) : launch_rate(g, g->U, st);
       if (r) return r;
     }
     wc_status r;
-    if ((r = stage(g, g->U, g->B1, 0.0, 1.0, 1.0, cfl, dt_fixed, st))) return r;
+    if ((r = stage(g, g->U, g->B1, 0.0, 1.0, 1.0, cfl, dt_fixed, st, 0, nullptr, nullptr, fuse)))
+      return r;
     if ((r = stage(g, g->B1, g->B2, 0.75, 0.25, 0.25, cfl, dt_fixed, st))) return r;
     if ((r = stage(g, g->B2, g->U, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, cfl, dt_fixed, st))) return r;
   }
@@ -820,14 +845,17 @@ extern "C" wc_status wc_rk_step_host(wc_grid* g, const double* U_in_host, double
   hu.up = up;
   hd.nb = nbl;
   hd.done = done;
+  const bool fuse = !(dt_fixed > 0.0) && g->vbuf;
   for (int s = 0; s < nsteps; s++) {
     const bool first = s == 0, last = s == nsteps - 1;
+    // (the first step's rate follows its banded upload; later steps take it
+    // in the first stage's slot pass, as wc_rk_step does)
     if (!first && !(dt_fixed > 0.0)) {
-      r = launch_rate(g, g->U, st);
+      r = fuse ? clear_rate(g, st) : launch_rate(g, g->U, st);
       if (r) return r;
     }
     if ((r = stage(g, g->U, g->B1, 0.0, 1.0, 1.0, cfl, dt_fixed, st, 0, nullptr,
-                   first ? &hu : nullptr)))
+                   first ? &hu : nullptr, fuse && !first)))
       return r;
     if ((r = stage(g, g->B1, g->B2, 0.75, 0.25, 0.25, cfl, dt_fixed, st))) return r;
     if ((r = stage(g, g->B2, g->U, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, cfl, dt_fixed, st, 0,

@@ -177,15 +177,25 @@ __device__ __forceinline__ void put_slot(double* sl, const double* v) {
 // the thread's part of shared memory.  One pass a Runge-Kutta stage with
 // every lane converting, where each direction sweep converted its cells and
 // with four lanes of a warp the two stencil cells beyond each end of a
-// window.
-template <int N, int D, typename T>
+// window.  RATE: the pass over a step's first stage input also reduces the
+// CFL rate max_cells sum_d (|u_d| + c)/dx_d into *rate_bits (the caller
+// clears it) from the primitive state it has just formed, with the steps and
+// the status bits of k_max_rate (a cell with rho <= 0 is inadmissible and
+// left out of the rate, a non-finite rate is reported): the same rate bit
+// for bit, the maximum being independent of the order.
+template <int N, int D, typename T, bool RATE = false>
 __global__ void __launch_bounds__(256) k_prim_slots(const double* __restrict__ U,
                                                     double* __restrict__ Vs, long ncell, long c0,
-                                                    long c1, Mat m) {
+                                                    long c1, Mat m, double idx0 = 0.0,
+                                                    double idx1 = 0.0, double idx2 = 0.0,
+                                                    unsigned long long* rate_bits = nullptr,
+                                                    unsigned* status = nullptr) {
   using I = Idx<N, D>;
   constexpr int SLOTD = Ring<N, D, T>::SLOTD;
   extern __shared__ double psl[];
   double* sl = psl + threadIdx.x * SLOTD;
+  double best = 0.0;
+  unsigned bad = 0u;
   for (long c = c0 + (long)blockIdx.x * blockDim.x + threadIdx.x; c < c1;
        c += (long)gridDim.x * blockDim.x) {
     double u[I::NV], v[I::NV];
@@ -195,6 +205,34 @@ __global__ void __launch_bounds__(256) k_prim_slots(const double* __restrict__ U
     put_slot<N, D, T>(sl, v);
 #pragma unroll
     for (int k = 0; k < SLOTD; k++) Vs[(long)k * ncell + c] = sl[k];
+    if constexpr (RATE) {
+      double rho = u[0];
+#pragma unroll
+      for (int p = 1; p < N; p++) rho += u[p];
+      if (!(rho > 0.0)) {
+        bad |= ST_INADMISSIBLE;
+        continue;
+      }
+      const double cs = sound_speed<N, D, double>(m, u, rho, v[I::E]);
+      double r = (fabs(v[I::U(0)]) + cs) * idx0;
+      if (D > 1) r += (fabs(v[I::U(1)]) + cs) * idx1;
+      if (D > 2) r += (fabs(v[I::U(D > 2 ? 2 : 0)]) + cs) * idx2;
+      if (!(r <= 1.7e308)) bad |= ST_NAN;
+      else best = fmax(best, r);
+    }
+  }
+  if constexpr (RATE) {
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    __shared__ double wmax[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) wmax[wid] = best;
+    __syncthreads();
+    if (wid == 0) {
+      best = lane < (int)(blockDim.x >> 5) ? wmax[lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+      if (lane == 0) atomicMax(rate_bits, (unsigned long long)__double_as_longlong(best));
+    }
+    if (bad) atomicOr(status, bad);
   }
 }
 

@@ -232,7 +232,8 @@ def test_primitive_slots_equal_sweep_conversion(gpu, name, variant):
     converted in the sweep) against sweeps that convert their cells
     themselves (a workspace without the slots): the rhs, the Phase-Field rhs
     and Runge-Kutta steps bit for bit, in every precision, the comparison
-    scheme and WENO-CL with the Kapila model."""
+    scheme and WENO-CL with the Kapila model; the CFL time step taken in the
+    first stage's slot pass equals k_max_rate's bit for bit."""
     import torch
     from paper_2608_00746_b300 import surrogate, wenoc
     case = SMALL_CASES[name]()
@@ -251,15 +252,18 @@ def test_primitive_slots_equal_sweep_conversion(gpu, name, variant):
         L = g.rhs(U).clone()
         Q = to_dev(np.random.default_rng(3).normal(size=(case.N,) + tuple(U.shape[1:])) * 0.05)
         Lpf = g.rhs_pf(U, Q, dt_limit=2e-3).clone()
-        g.rk_step(cfl=case.cfl or 0.2, nsteps=3)
+        # (CFL steps: with the slots the first stage's slot pass also takes
+        # the rate, otherwise k_max_rate does)
+        dt = g.rk_step(cfl=case.cfl or 0.2, nsteps=3, want_dt=True)
         try:  # (the unlimited comparison scheme may fail at a shock: alike in both)
             g.sync_status()
             status = "ok"
         except wenoc.WcError as e:
             status = str(e)
-        outs.append((L, Lpf, U, status))
+        outs.append((L, Lpf, U, status, dt))
     assert (wenoc.lib().wc_prim_buffer_bytes(g.h) > 0) == (case.dim > 1)
     assert outs[0][3] == outs[1][3]
+    assert outs[0][4] == outs[1][4] or outs[0][3] != "ok"
     if variant != "weno_w":
         assert outs[0][3] == "ok"
     for a, b in zip(outs[0][:3], outs[1][:3]):
