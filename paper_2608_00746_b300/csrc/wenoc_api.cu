@@ -668,8 +668,8 @@ static wc_status stage(wc_grid* g, const double* src, double* dst, double r0, do
   // download takes y first, so that the banded sweep runs over rows (x
   // pencils, contiguous in every field): L_y + L_x is L_x + L_y bit for bit
   const bool swap = hb && hb->done && D == 2;
-  // the primitive slots of src, once for the stage's directions (after the
-  // banded first direction when the upload is still arriving)
+  // the primitive slots of src, once for the stage's directions (band by
+  // band with the first direction when the upload is still arriving)
   const double* Vs = nullptr;
   const bool banded_up = hb && hb->up;
   if (!banded_up) {
@@ -704,6 +704,15 @@ static wc_status stage(wc_grid* g, const double* src, double* dst, double r0, do
     }
     // (band launches: the window plan of each band's pencils; the split
     // sweep's face buffer is indexed by the band's own pencils in both passes)
+    // An upload band (rows of x-pencils, cells t0 nx .. t1 nx - 1, whose
+    // stencils stay in their rows) takes its rows' primitive slots, and the
+    // CFL rate over them, once they have arrived; the first direction (mode
+    // 0) needs no time step, the others read the rate of the whole state.
+    const bool band_rate = up && g->vbuf && !(dt_fixed > 0.0);
+    if (band_rate) {
+      wc_status r = clear_rate(g, st);
+      if (r) return r;
+    }
     for (int b = 0; b < hb->nb; b++) {
       long t0, t1;
       band_range(a.npencil, hb->nb, b, up ? -1 : 1, t0, t1);
@@ -714,21 +723,17 @@ static wc_status stage(wc_grid* g, const double* src, double* dst, double r0, do
       ab.nitems = w.nitems;
       ab.wslots = w.slots;
       cudaError_t e = up ? cudaStreamWaitEvent(st, hb->up[b], 0) : cudaSuccess;
+      if (e == cudaSuccess && up)
+        ab.Vs = launch_prim(g, src, kind, t0 * (long)ab.n, t1 * (long)ab.n, st, e, band_rate);
       if (e == cudaSuccess) e = launch(g, ab, st);
       if (e == cudaSuccess && down) e = cudaEventRecord(hb->done[b], st);
       if (e != cudaSuccess) return cuda_fail(g, e, "band sweep");
     }
-    // the first direction (mode 0) needs no time step; the others take it
-    // from the state, now uploaded in full, and its primitive slots
-    if (up && !(dt_fixed > 0.0)) {
+    if (up && !g->vbuf && !(dt_fixed > 0.0)) {
       wc_status r = launch_rate(g, g->U, st);
       if (r) return r;
     }
-    if (up) {
-      cudaError_t e;
-      Vs = launch_prim(g, src, kind, 0, g->ncell, st, e);
-      if (e != cudaSuccess) return cuda_fail(g, e, "primitive slots");
-    }
+    if (up) Vs = g->vbuf && g->d.seg == 0 ? g->vbuf : nullptr;
   }
   return WC_OK;
 }
@@ -848,8 +853,8 @@ extern "C" wc_status wc_rk_step_host(wc_grid* g, const double* U_in_host, double
   const bool fuse = !(dt_fixed > 0.0) && g->vbuf;
   for (int s = 0; s < nsteps; s++) {
     const bool first = s == 0, last = s == nsteps - 1;
-    // (the first step's rate follows its banded upload; later steps take it
-    // in the first stage's slot pass, as wc_rk_step does)
+    // (the first step's rate comes with its banded upload; later steps take
+    // it in the first stage's slot pass, as wc_rk_step does)
     if (!first && !(dt_fixed > 0.0)) {
       r = fuse ? clear_rate(g, st) : launch_rate(g, g->U, st);
       if (r) return r;
