@@ -465,14 +465,15 @@ __device__ __forceinline__ void sweep_window(const SweepArgs& a, const Mat& m, l
 // Persistent launch: every warp takes windows (pencil fastest, so warps that
 // run together read neighbouring pencils) from the queue a.ticket[0] until
 // it is empty; the last warp to leave resets the queue for the next launch.
-// Minimum resident blocks for the register budget: the FP64 sweep is left
-// to the compiler (142 registers for N = 3, three blocks an SM; a cap costs
-// spills for under 1 %); the reduced precisions' sweeps are held to 128
-// registers, four blocks (16 warps) an SM, spilling 16-64 bytes a thread:
-// the face pass of the 2048^2 N = 3 circles keeps its FP64 pipe busier
-// (mixed step 18.24 -> 17.73 ms; 192^3 3-D spheres 57.5 -> 55.1 ms).
+// Minimum resident blocks for the register budget: every window sweep is
+// held to 128 registers, four blocks (16 warps) an SM instead of three.  The
+// reduced precisions' face pass spills 16-64 bytes a thread and keeps its
+// FP64 pipe busier (mixed step on the 2048^2 N = 3 circles 18.24 -> 17.73
+// ms; 192^3 3-D spheres 57.5 -> 55.1 ms); the FP64 sweep (142 registers
+// otherwise, 56-116 bytes of spills) gains 0.6 % (36.00 -> 35.80 ms a step;
+// 3-D 108.85 -> 108.24 ms).
 #ifndef WC_WIN_MINB64
-#define WC_WIN_MINB64 1
+#define WC_WIN_MINB64 4
 #endif
 #ifndef WC_WIN_MINB32
 #define WC_WIN_MINB32 4
