@@ -198,6 +198,12 @@ __device__ __forceinline__ bool not_finite(double x) {
 // fraction bits, add one when the 29 dropped bits are above half, or exactly
 // half with the kept bits odd (a carry into the exponent is the correct
 // result, up to infinity above the largest binary32).
+// The hardware conversions for the rare values the integer paths leave to
+// them, out of line: inlined, the compiler may issue them, predicated off,
+// on every conversion, and each issue holds the FP64 pipe.
+static __device__ __noinline__ float f64_to_f32_hw(double x) { return (float)x; }
+static __device__ __noinline__ double f32_to_f64_hw(float x) { return (double)x; }
+
 __device__ __forceinline__ float f64_to_f32(double x) {
   const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
   const unsigned e = (hi >> 20) & 0x7ffu;
@@ -208,7 +214,7 @@ __device__ __forceinline__ float f64_to_f32(double x) {
     return __uint_as_float(r | (hi & 0x80000000u));
   }
   if (e < 873u) return __uint_as_float(hi & 0x80000000u);  // |x| < 2^-150: a signed zero
-  return (float)x;
+  return f64_to_f32_hw(x);
 }
 // binary32 -> binary64 (exact): exponent rebased by 1023 - 127 = 896, the 23
 // fraction bits on top of the 52.
@@ -218,7 +224,7 @@ __device__ __forceinline__ double f32_to_f64(float x) {
     return __hiloint2double((int)((b & 0x80000000u) | ((em >> 3) + (896u << 20))),
                             (int)(em << 29));
   if (em == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);  // a signed zero
-  return (double)x;
+  return f32_to_f64_hw(x);
 }
 // T(x) and double(x) of the precision templates through the helpers above
 template <typename T> __device__ __forceinline__ T cvt(double x);
